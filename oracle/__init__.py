@@ -1,0 +1,226 @@
+"""CPU oracle for the k-mismatch FM-index read search (MICA, Section 2).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the CPU-baseline leg
+of the benchmark are the only callers.  The product path (the CUDA library
+and its binding) never imports this package, and this package never imports
+the product.  The arithmetic lives in ``oracle.c`` (plain C, compiled with
+gcc by :func:`build`); this module only marshals numpy arrays.
+
+Functions and what pins them (tests/test_oracle_*.py):
+
+* :func:`sa_sort`, :func:`sa_is` -- suffix array of T = G$ by sorting and by
+  SA-IS; pinned against Python's ``sorted`` of the suffixes (the definition)
+  and against each other on random and periodic strings.
+* :class:`FMIndex` (BWT, C, Occ) -- pinned by LF consistency
+  (SA[LF(j)] = SA[j]-1), the column sums of Occ, and exact-pattern interval
+  sizes equal to brute-force occurrence counts.
+* :func:`align` -- pinned against a brute-force Hamming scan written in
+  numpy inside the tests, the generator's ground truth on the 1 Mbp random
+  genome (chance hits are vanishingly rare there), reverse-complement symmetry,
+  and for the hit cap by the properties that define it.
+* :func:`bruteforce` -- pinned against the numpy scan in the tests.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+HIT_DTYPE = np.dtype([("pos", "<u4"), ("strand", "u1"), ("mm", "u1"), ("pad", "<u2")])
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so next to it (gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-Wall",
+                               "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = ctypes.CDLL(build())
+    P = ctypes.c_void_p
+    u64, u32, i32 = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+    sig = {
+        "oracle_sa_sort": (i32, [P, u64, P]),
+        "oracle_sa_is": (i32, [P, u64, P]),
+        "oracle_fm_new": (P, [P, u64, i32, P]),
+        "oracle_fm_free": (None, [P]),
+        "oracle_occ": (u64, [P, i32, u64]),
+        "oracle_C": (u64, [P, i32]),
+        "oracle_rows": (u64, [P]),
+        "oracle_copy_sa": (None, [P, P]),
+        "oracle_copy_bwt": (None, [P, P]),
+        "oracle_exact_interval": (None, [P, P, u32, P, P]),
+        "oracle_align": (P, [P, P, P, P, P, u64, u32, i32]),
+        "oracle_bruteforce": (P, [P, u64, P, P, P, P, u64, i32]),
+        "oracle_result_free": (None, [P]),
+        "oracle_result_n": (u64, [P]),
+        "oracle_result_status": (i32, [P]),
+        "oracle_result_nodes": (u64, [P]),
+        "oracle_result_copy": (None, [P, P, P, P]),
+        "oracle_result_n_hits": (u64, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _codes(g) -> np.ndarray:
+    g = np.ascontiguousarray(g, dtype=np.uint8)
+    if g.size and g.max() > 3:
+        raise ValueError("genome codes must be 0..3")
+    return g
+
+
+def sa_sort(g) -> np.ndarray:
+    """Suffix array of G$ by sorting the suffixes (small inputs)."""
+    g = _codes(g)
+    sa = np.empty(len(g) + 1, dtype=np.uint32)
+    if _load().oracle_sa_sort(_ptr(g), len(g), _ptr(sa)):
+        raise MemoryError("oracle_sa_sort")
+    return sa
+
+
+def sa_is(g) -> np.ndarray:
+    """Suffix array of G$ by SA-IS."""
+    g = _codes(g)
+    sa = np.empty(len(g) + 1, dtype=np.uint32)
+    if _load().oracle_sa_is(_ptr(g), len(g), _ptr(sa)):
+        raise MemoryError("oracle_sa_is")
+    return sa
+
+
+class Result:
+    """Per-read hit lists in CSR form: ``hits[offsets[i]:offsets[i+1]]``."""
+
+    def __init__(self, total, offsets, hits, nodes=0):
+        self.total = total
+        self.offsets = offsets
+        self.hits = hits
+        self.nodes = nodes
+
+    def read_hits(self, i: int) -> np.ndarray:
+        return self.hits[int(self.offsets[i]):int(self.offsets[i + 1])]
+
+    def as_tuples(self, i: int) -> list:
+        h = self.read_hits(i)
+        return [(int(p), int(s), int(d)) for p, s, d in zip(h["pos"], h["strand"], h["mm"])]
+
+
+def _take_result(lib, handle) -> Result:
+    if not handle:
+        raise ValueError("oracle rejected the input (k > 3, empty read or read longer than genome)")
+    try:
+        if lib.oracle_result_status(handle) != 0:
+            raise MemoryError("oracle out of memory")
+        n = lib.oracle_result_n(handle)
+        total = np.empty(n, dtype=np.uint64)
+        offsets = np.empty(n + 1, dtype=np.uint64)
+        hits = np.empty(max(1, lib.oracle_result_n_hits(handle)), dtype=HIT_DTYPE)
+        lib.oracle_result_copy(handle, _ptr(total), _ptr(offsets), _ptr(hits))
+        hits = hits[:int(offsets[-1])].copy()
+        return Result(total, offsets, hits, int(lib.oracle_result_nodes(handle)))
+    finally:
+        lib.oracle_result_free(handle)
+
+
+class FMIndex:
+    """Plain FM index of G$ with the full suffix array (oracle side)."""
+
+    def __init__(self, g, sa_method: str = "auto", sa=None):
+        lib = _load()
+        self.g = _codes(g)
+        self.n = len(self.g)
+        if sa is not None:
+            sa = np.ascontiguousarray(sa, dtype=np.uint32)
+            meth, sap = 0, _ptr(sa)
+        else:
+            if sa_method == "auto":
+                sa_method = "sort" if self.n <= 200_000 else "sais"
+            meth, sap = (0 if sa_method == "sort" else 1), None
+        self._h = lib.oracle_fm_new(_ptr(self.g), self.n, meth, sap)
+        if not self._h:
+            raise MemoryError("oracle_fm_new")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.oracle_fm_free(h)
+            self._h = None
+
+    @property
+    def rows(self) -> int:
+        return self.n + 1
+
+    def C(self, c: int) -> int:
+        return int(_lib.oracle_C(self._h, c))
+
+    def occ(self, c: int, i: int) -> int:
+        return int(_lib.oracle_occ(self._h, c, i))
+
+    def sa(self) -> np.ndarray:
+        out = np.empty(self.rows, dtype=np.uint32)
+        _lib.oracle_copy_sa(self._h, _ptr(out))
+        return out
+
+    def bwt(self) -> np.ndarray:
+        """BWT symbols: 0..3 = A..T, 4 = $."""
+        out = np.empty(self.rows, dtype=np.uint8)
+        _lib.oracle_copy_bwt(self._h, _ptr(out))
+        return out
+
+    def exact_interval(self, p) -> tuple:
+        p = np.ascontiguousarray(p, dtype=np.uint8)
+        l, r = ctypes.c_uint64(), ctypes.c_uint64()
+        _lib.oracle_exact_interval(self._h, _ptr(p), len(p), ctypes.byref(l), ctypes.byref(r))
+        return int(l.value), int(r.value)
+
+    def align(self, batch, cap: int = 0, threads: int = 0) -> Result:
+        """All hits of every read of ``batch`` (a synth.ReadBatch or any object
+        with words/word_off/lengths/k arrays), both strands, <= k mismatches."""
+        words, off, lens, k = _batch_arrays(batch)
+        h = _lib.oracle_align(self._h, _ptr(words), _ptr(off), _ptr(lens), _ptr(k),
+                              len(lens), cap, threads)
+        return _take_result(_lib, h)
+
+
+def _batch_arrays(batch):
+    words = np.ascontiguousarray(batch.words, dtype=np.uint32)
+    if words.size == 0:
+        words = np.zeros(1, dtype=np.uint32)
+    off = np.ascontiguousarray(batch.word_off, dtype=np.uint64)
+    lens = np.ascontiguousarray(batch.lengths, dtype=np.uint16)
+    k = np.ascontiguousarray(batch.k, dtype=np.uint8)
+    return words, off, lens, k
+
+
+def bruteforce(g, batch, threads: int = 0) -> Result:
+    """Hamming scan of every window of both strands (tiny inputs only)."""
+    lib = _load()
+    g = _codes(g)
+    words, off, lens, k = _batch_arrays(batch)
+    h = lib.oracle_bruteforce(_ptr(g), len(g), _ptr(words), _ptr(off), _ptr(lens), _ptr(k),
+                              len(lens), threads)
+    return _take_result(lib, h)

@@ -1,0 +1,299 @@
+"""Seeded synthetic genomes and reads for the k-mismatch read search.
+
+This module only makes inputs: it holds none of the search arithmetic, and
+both the CPU oracle (``oracle/``) and the CUDA library are fed from it.  The
+paper's experiments (Section 3, Table 1 and Table 2) use real human data
+(YH PE150/PE100, 1000 Genomes lanes) that are not available here; the
+generators below produce stand-ins with the same read lengths (100/150 bp),
+the paper's batch size of about a million reads (Section 2), and genomes whose
+repeat structure makes the backtracking work uneven across reads.
+
+Encoding: a genome or read is a ``uint8`` array of base codes A=0, C=1, G=2,
+T=3.  A batch of reads is packed 2 bits per base, 16 bases per ``uint32`` word,
+least-significant bits first; read ``i`` starts at word ``word_off[i]``.
+
+Every generator draws from ``numpy.random.Generator(PCG64(seed))`` only.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+ACGT = np.frombuffer(b"ACGT", dtype=np.uint8)
+
+# Seeds of the five workloads (genome, reads, slice ...).
+SEED_GENOME_1M = 1
+SEED_READS_1M = 11
+SEED_SLICE_10K = 12
+SEED_GENOME_64M = 2
+SEED_READS_64M = 21
+SEED_READS_UNEVEN = 31
+SEED_GENOME_HUMAN = 4
+SEED_DONOR_HUMAN = 41
+SEED_READS_HUMAN = 42
+SEED_ARRIVALS = 51
+SEED_READS_SERVE = 52
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def to_acgt_bytes(codes: np.ndarray) -> bytes:
+    """Base codes 0..3 -> ASCII 'ACGT' bytes (the library's genome input)."""
+    return ACGT[np.asarray(codes, dtype=np.uint8)].tobytes()
+
+
+def opposite_strand(codes: np.ndarray) -> np.ndarray:
+    """The other strand of a DNA segment, read 5'->3' (used to draw reads
+    from the minus strand and to copy repeats in reverse orientation)."""
+    return (3 - np.asarray(codes, dtype=np.uint8))[::-1].copy()
+
+
+def substitute(codes: np.ndarray, where: np.ndarray, rng: np.random.Generator) -> None:
+    """In place: replace the bases at ``where`` by one of the three other bases,
+    uniformly."""
+    if len(where) == 0:
+        return
+    shift = rng.integers(1, 4, size=len(where), dtype=np.uint8)
+    codes[where] = (codes[where] + shift) & 3
+
+
+# --------------------------------------------------------------------------
+# Genomes
+# --------------------------------------------------------------------------
+
+@dataclass
+class Genome:
+    codes: np.ndarray                      # uint8 base codes, length N
+    regions: list = field(default_factory=list)  # (start, end, kind) of planted repeats
+
+    @property
+    def n(self) -> int:
+        return int(self.codes.shape[0])
+
+
+def uniform_genome(n: int, seed: int) -> Genome:
+    """i.i.d. uniform A/C/G/T genome of length ``n``."""
+    return Genome(_rng(seed).integers(0, 4, size=n, dtype=np.uint8))
+
+
+def repeat_genome(n: int, seed: int, *, copy_frac: float = 0.05,
+                  copy_len=(1_000, 10_000), copy_div: float = 0.01,
+                  tandem_frac: float = 0.01, unit_len=(2, 50),
+                  array_len=(100, 5_000), tandem_div: float = 0.0) -> Genome:
+    """Genome with interspersed copies and tandem arrays.
+
+    1. i.i.d. uniform base sequence;
+    2. segments of length uniform in ``copy_len`` copied from a random source
+       position to a random destination, in random orientation, each copied
+       base substituted with probability ``copy_div``, until ``copy_frac`` of
+       the length has been overwritten;
+    3. tandem arrays: a random unit of length uniform in ``unit_len`` repeated
+       to an array length uniform in ``array_len`` (each base substituted with
+       probability ``tandem_div``), until ``tandem_frac`` of the length is
+       covered.
+    """
+    rng = _rng(seed)
+    g = rng.integers(0, 4, size=n, dtype=np.uint8)
+    regions = []
+    budget = int(copy_frac * n)
+    while budget > 0:
+        ln = int(rng.integers(copy_len[0], copy_len[1] + 1))
+        ln = min(ln, n // 4)
+        src = int(rng.integers(0, n - ln + 1))
+        dst = int(rng.integers(0, n - ln + 1))
+        seg = g[src:src + ln].copy()
+        if rng.integers(0, 2):
+            seg = opposite_strand(seg)
+        hit = np.flatnonzero(rng.random(ln) < copy_div)
+        substitute(seg, hit, rng)
+        g[dst:dst + ln] = seg
+        regions.append((dst, dst + ln, "copy"))
+        budget -= ln
+    budget = int(tandem_frac * n)
+    while budget > 0:
+        u = int(rng.integers(unit_len[0], unit_len[1] + 1))
+        ln = int(rng.integers(array_len[0], array_len[1] + 1))
+        ln = min(ln, n // 4)
+        unit = rng.integers(0, 4, size=u, dtype=np.uint8)
+        arr = np.resize(unit, ln)
+        if tandem_div > 0:
+            hit = np.flatnonzero(rng.random(ln) < tandem_div)
+            substitute(arr, hit, rng)
+        dst = int(rng.integers(0, n - ln + 1))
+        g[dst:dst + ln] = arr
+        regions.append((dst, dst + ln, "tandem"))
+        budget -= ln
+    return Genome(g, regions)
+
+
+# --------------------------------------------------------------------------
+# Reads
+# --------------------------------------------------------------------------
+
+@dataclass
+class ReadBatch:
+    """A batch of reads in the library's packed layout, with ground truth."""
+    words: np.ndarray        # uint32 packed bases
+    word_off: np.ndarray     # uint64, n+1 word offsets
+    lengths: np.ndarray      # uint16 read lengths
+    k: np.ndarray            # uint8 per-read mismatch budget
+    origin: np.ndarray       # int64 sampled origin (leftmost forward coordinate)
+    strand: np.ndarray       # uint8 0 = forward, 1 = reverse complement
+    n_subs: np.ndarray       # int32 substitutions applied to the read
+
+    @property
+    def n(self) -> int:
+        return int(self.lengths.shape[0])
+
+    def read(self, i: int) -> np.ndarray:
+        """Unpacked base codes of read ``i``."""
+        m = int(self.lengths[i])
+        w = self.words[int(self.word_off[i]):int(self.word_off[i + 1])]
+        return unpack_words(w, m)
+
+    def subset(self, idx) -> "ReadBatch":
+        idx = np.asarray(idx, dtype=np.int64)
+        reads = [self.read(int(i)) for i in idx]
+        words, off, lens = pack_reads(reads)
+        return ReadBatch(words, off, lens, self.k[idx].copy(), self.origin[idx].copy(),
+                         self.strand[idx].copy(), self.n_subs[idx].copy())
+
+
+def unpack_words(words: np.ndarray, m: int) -> np.ndarray:
+    w = np.asarray(words, dtype=np.uint32)
+    shifts = (2 * np.arange(16, dtype=np.uint32))
+    bases = ((w[:, None] >> shifts[None, :]) & 3).astype(np.uint8).reshape(-1)
+    return bases[:m].copy()
+
+
+def pack_reads(reads) -> tuple:
+    """List of uint8 code arrays -> (words uint32, word_off uint64[n+1], lengths uint16)."""
+    n = len(reads)
+    lens = np.fromiter((len(r) for r in reads), dtype=np.int64, count=n)
+    nw = (lens + 15) // 16
+    off = np.zeros(n + 1, dtype=np.uint64)
+    np.cumsum(nw, out=off[1:])
+    words = np.zeros(int(off[-1]), dtype=np.uint32)
+    # group reads of equal length and pack each group with array operations
+    for m in np.unique(lens):
+        idx = np.flatnonzero(lens == m)
+        mat = np.stack([reads[i] for i in idx]).astype(np.uint32)
+        _pack_group(words, off, idx, mat)
+    return words, off, lens.astype(np.uint16)
+
+
+def _pack_group(words, off, idx, mat):
+    m = mat.shape[1]
+    w = (m + 15) // 16
+    pad = np.zeros((mat.shape[0], w * 16), dtype=np.uint32)
+    pad[:, :m] = mat
+    pad = pad.reshape(mat.shape[0], w, 16) << (2 * np.arange(16, dtype=np.uint32))
+    packed = np.bitwise_or.reduce(pad, axis=2)
+    dst = off[idx].astype(np.int64)[:, None] + np.arange(w)[None, :]
+    words[dst] = packed
+
+
+def sample_reads(genome: Genome, lengths: np.ndarray, k: np.ndarray, rng: np.random.Generator, *,
+                 subs: str, sub_rate: float = 0.01, max_subs: int = 2,
+                 repeat_frac: float = 0.0, origin_limit: int | None = None) -> ReadBatch:
+    """Draw reads from ``genome``.
+
+    Origin uniform in [0, N-m] (or, for a fraction ``repeat_frac`` of reads,
+    uniform inside a planted repeat region chosen with probability proportional
+    to its length); strand a fair coin; then substitutions:
+    ``subs == "count"``: a number uniform in {0..max_subs} at distinct uniform
+    positions; ``subs == "rate"``: each base i.i.d. with probability ``sub_rate``.
+    The replacement base is uniform among the three others.
+    """
+    g = genome.codes
+    n_total = genome.n if origin_limit is None else origin_limit
+    n = len(lengths)
+    lengths = np.asarray(lengths, dtype=np.int64)
+    origin = (rng.random(n) * (n_total - lengths + 1)).astype(np.int64)
+    if repeat_frac > 0 and genome.regions:
+        reg = np.array([(a, b) for a, b, _ in genome.regions], dtype=np.int64)
+        w = (reg[:, 1] - reg[:, 0]).astype(np.float64)
+        pick = rng.random(n) < repeat_frac
+        ridx = rng.choice(len(reg), size=int(pick.sum()), p=w / w.sum())
+        a = reg[ridx, 0]
+        b = np.maximum(reg[ridx, 1] - lengths[pick], a)
+        o = a + (rng.random(len(ridx)) * (b - a + 1)).astype(np.int64)
+        origin[pick] = np.minimum(o, n_total - lengths[pick])
+    strand = rng.integers(0, 2, size=n, dtype=np.uint8)
+    reads = []
+    n_subs = np.zeros(n, dtype=np.int32)
+    for m in np.unique(lengths):
+        idx = np.flatnonzero(lengths == m)
+        mat = g[origin[idx][:, None] + np.arange(m)[None, :]]
+        rev = strand[idx] == 1
+        mat[rev] = (3 - mat[rev])[:, ::-1]
+        if subs == "count":
+            cnt = rng.integers(0, max_subs + 1, size=len(idx))
+            for j, c in enumerate(cnt):
+                if c:
+                    pos = rng.choice(m, size=int(c), replace=False)
+                    substitute(mat[j], pos, rng)
+            n_subs[idx] = cnt
+        elif subs == "rate":
+            hit = rng.random(mat.shape) < sub_rate
+            flat = mat.reshape(-1)
+            substitute(flat, np.flatnonzero(hit.reshape(-1)), rng)
+            mat = flat.reshape(mat.shape)
+            n_subs[idx] = hit.sum(axis=1)
+        else:
+            raise ValueError(subs)
+        for j, i in enumerate(idx):
+            reads.append((int(i), mat[j]))
+    reads.sort(key=lambda t: t[0])
+    words, off, lens = pack_reads([r for _, r in reads])
+    return ReadBatch(words, off, lens, np.asarray(k, dtype=np.uint8), origin, strand, n_subs)
+
+
+# --------------------------------------------------------------------------
+# The workloads
+# --------------------------------------------------------------------------
+
+def genome_1m() -> Genome:
+    """Small case: i.i.d. uniform genome of 1 Mbp."""
+    return uniform_genome(1_000_000, SEED_GENOME_1M)
+
+
+def reads_1m(genome: Genome, n: int = 10_000) -> ReadBatch:
+    """10,000 reads of 100 bp, 0-2 substitutions at distinct uniform positions, k = 2."""
+    rng = _rng(SEED_READS_1M)
+    return sample_reads(genome, np.full(n, 100), np.full(n, 2), rng, subs="count", max_subs=2)
+
+
+def slice_10k(genome: Genome, n: int = 1_000, m: int = 100) -> tuple:
+    """Brute-force slice: the first 10,000 bp of the 1 Mbp genome as a genome of
+    its own, and 1,000 reads drawn from it with 0-2 substitutions."""
+    g = Genome(genome.codes[:10_000].copy())
+    rng = _rng(SEED_SLICE_10K)
+    return g, sample_reads(g, np.full(n, m), np.full(n, 2), rng, subs="count", max_subs=2)
+
+
+def genome_64m(n: int = 1 << 26) -> Genome:
+    """Repeat genome of 64 Mbp: 5% copies of 1-10 kbp at 1% divergence, 1% tandem
+    arrays (unit 2-50 bp, array 100-5,000 bp, exact copies)."""
+    return repeat_genome(n, SEED_GENOME_64M)
+
+
+def reads_64m(genome: Genome, n: int = 1_000_000, m: int = 150) -> ReadBatch:
+    """1M reads of 150 bp with 1% i.i.d. substitution error, k = 2."""
+    rng = _rng(SEED_READS_64M)
+    return sample_reads(genome, np.full(n, m), np.full(n, 2), rng, subs="rate", sub_rate=0.01)
+
+
+UNEVEN_LENGTHS = (50, 100, 150, 250)
+
+
+def reads_uneven(genome: Genome, n: int = 1_000_000) -> ReadBatch:
+    """1M reads, length uniform over {50, 100, 150, 250}, k uniform over {0..3},
+    30% drawn from inside planted repeats, 1% substitution error."""
+    rng = _rng(SEED_READS_UNEVEN)
+    lengths = np.asarray(UNEVEN_LENGTHS)[rng.integers(0, 4, size=n)]
+    k = rng.integers(0, 4, size=n).astype(np.uint8)
+    return sample_reads(genome, lengths, k, rng, subs="rate", sub_rate=0.01, repeat_frac=0.30)
