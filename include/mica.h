@@ -1,0 +1,194 @@
+/*
+ * mica.h -- C ABI of the GB300 k-mismatch FM-index read search.
+ *
+ * The operation (MICA, Section 2): every read is first placed on the reference
+ * genome by searching a BWT (FM) index with few mismatches; reads that fail
+ * go on to a dynamic-programming phase for indels, which this library does not
+ * implement.  Here "few mismatches" is a per-read budget k in 0..3 of base
+ * substitutions, and the search is exhaustive on both strands:
+ *
+ *   H(R) = {(p,+,d): d = Ham(R,     G[p,p+m)) <= k}
+ *        u {(p,-,d): d = Ham(rc(R), G[p,p+m)) <= k},     0 <= p <= N-m
+ *
+ * A hit on the - strand reports the leftmost forward-strand coordinate p of
+ * the matched window.  A read equal to its own reverse complement reports both
+ * (p,+,d) and (p,-,d).  Per read, `total` is the exact size of H(R); at most
+ * `hit_cap` hits are listed: when total > hit_cap the listed ones are the first
+ * hit_cap in the order (d ascending, + before -, suffix-array row ascending).
+ * Listed hits are sorted by (position, strand, d).
+ *
+ * The index (Section 2: a BWT index of the genome resident in the
+ * accelerator's global memory, laid out to cut memory transactions) is built
+ * and kept in GPU memory: the 2-bit BWT interleaved with occurrence counts in
+ * 64-byte blocks of 192 rows, a q-mer table of suffix-array interval bounds,
+ * and a text-sampled suffix array with a row-marking bit vector.
+ *
+ * Conventions.  Every function returning int returns MICA_OK (0) or a negative
+ * MICA_E* code; mica_strerror names it.  Input buffers are owned by the caller
+ * and only read during the call.  Objects returned through `out` pointers are
+ * owned by the library until the matching *_free call.  A mica_index is used
+ * by one host thread at a time.  Device pointers are CUDA device addresses on
+ * the index's device.  Base codes: A=0, C=1, G=2, T=3.
+ */
+#ifndef MICA_H
+#define MICA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    MICA_OK = 0,
+    MICA_EINVAL = -1,     /* bad argument: k > 3, read length 0 or > N or > MICA_MAX_READ_LEN,
+                             non-ACGT genome byte, bad parameter */
+    MICA_ENOMEM = -2,     /* host or device allocation failed */
+    MICA_EIO = -3,        /* index file cannot be read or written, or is malformed */
+    MICA_ECUDA = -4,      /* a CUDA runtime call failed */
+    MICA_ETIMEOUT = -5,   /* a bounded device or host wait expired */
+    MICA_EINTERNAL = -6,  /* an internal capacity retry did not converge (should not happen) */
+    MICA_EBUSY = -7,      /* serving: the request is not finished yet */
+    MICA_ENOTFOUND = -8   /* serving: unknown request id */
+};
+
+#define MICA_MAX_READ_LEN 256   /* bases per read */
+#define MICA_MAX_K 3            /* substitutions per read */
+
+typedef struct mica_index mica_index;
+
+/* Index layout parameters (defaults: 12, 16). */
+typedef struct {
+    uint32_t kmer_q;     /* q-mer seed table length, 1..12: table of 4^q + 1 uint32 bounds */
+    uint32_t sa_sample;  /* text sampling rate s, 1..256: SA[j] kept when SA[j] % s == 0 */
+} mica_index_params;
+
+enum { MICA_KERNEL_PERSISTENT = 0, MICA_KERNEL_PLAIN = 1 };
+
+typedef struct {
+    uint32_t hit_cap;    /* listed hits per read; 0 = no cap (every hit listed) */
+    int32_t kernel;      /* MICA_KERNEL_PERSISTENT (warp-cooperative work pool) or
+                            MICA_KERNEL_PLAIN (one (read, strand) task per thread) */
+    void *cuda_stream;   /* cudaStream_t to run on; NULL = the legacy default stream */
+} mica_align_params;
+
+typedef struct {
+    uint32_t pos;        /* leftmost forward coordinate of the matched window */
+    uint8_t strand;      /* 0 = +, 1 = - */
+    uint8_t mm;          /* substitutions d */
+    uint16_t pad;
+} mica_hit;
+
+/* Host-side result, owned by the library until mica_result_free. */
+typedef struct {
+    uint64_t n_reads;
+    uint64_t *total;     /* n_reads: exact |H(R)| */
+    uint64_t *offsets;   /* n_reads + 1: read i's hits are hits[offsets[i], offsets[i+1]) */
+    mica_hit *hits;
+} mica_result;
+
+/* Device-side result: pointers into the index's workspace on its device,
+   valid until the next align call on the same index. */
+typedef struct {
+    uint64_t n_reads;
+    uint64_t n_hits;
+    const uint64_t *total;
+    const uint64_t *offsets;
+    const mica_hit *hits;
+} mica_device_result;
+
+/* Work counters of the last align call on an index. */
+typedef struct {
+    uint64_t tasks;          /* (read, strand) search tasks = 2 * n_reads */
+    uint64_t seeds;          /* q-mer table lookups */
+    uint64_t nodes;          /* backtracking nodes expanded (one interval extension each) */
+    uint64_t rank_blocks;    /* 64-byte occurrence blocks read by the search */
+    uint64_t intervals;      /* leaf SA intervals found */
+    uint64_t located;        /* SA rows resolved to positions */
+    uint64_t lf_steps;       /* LF-mapping steps taken by the resolution */
+    uint64_t spills;         /* work items moved to the device queue (persistent kernel)
+                                or re-queued after the per-thread budget (plain kernel) */
+    uint64_t retries;        /* internal buffer-growth retries */
+    float search_ms;         /* device time of the search phase */
+    float total_ms;          /* device time of the whole call */
+} mica_stats;
+
+typedef struct {
+    uint64_t n;              /* genome length N */
+    uint64_t rows;           /* N + 1 */
+    uint32_t kmer_q, sa_sample;
+    uint64_t dollar_row;     /* BWT row holding $ */
+    uint64_t C[5];           /* C[c] = symbols of G$ smaller than c; C[4] = N + 1 */
+    uint64_t occ_bytes, mark_bytes, sample_bytes, table_bytes;
+    int32_t device;
+} mica_index_info;
+
+const char *mica_strerror(int code);
+
+/* Fill *p with the defaults (kmer_q 12, sa_sample 16). */
+void mica_index_params_default(mica_index_params *p);
+/* Fill *p with the defaults (hit_cap 1000, persistent kernel, default stream). */
+void mica_align_params_default(mica_align_params *p);
+
+/*
+ * Build the index of genome_acgt[0, len) (ASCII A/C/G/T, either case; anything
+ * else is MICA_EINVAL) on the current CUDA device and keep it there.  The
+ * suffix array of G$ is built on the GPU by prefix doubling.  params may be
+ * NULL (defaults).  *out owns device memory until mica_index_free.
+ */
+int mica_index_build_resident(const uint8_t *genome_acgt, uint64_t len,
+                              const mica_index_params *params, int device, mica_index **out);
+
+/* Build as above on the current device, write it to out_path, free it. */
+int mica_index_build(const uint8_t *genome_acgt, uint64_t len,
+                     const mica_index_params *params, const char *out_path);
+
+int mica_index_save(const mica_index *idx, const char *path);
+/* Read an index file and upload it to `device`, where it stays until freed. */
+int mica_index_load(const char *path, int device, mica_index **out);
+void mica_index_free(mica_index *idx);
+int mica_index_get_info(const mica_index *idx, mica_index_info *info);
+
+/*
+ * Align a batch given in HOST memory: packed_reads holds 2-bit bases, 16 per
+ * uint32 word, least-significant bits first; read i (length lengths[i], budget
+ * k[i]) starts at word word_offsets[i] (n_reads + 1 offsets, non-decreasing).
+ * Copies the batch to the device, runs the search, copies the result back.
+ * params may be NULL (defaults).  On success *out is a new mica_result.
+ */
+int mica_align_batch(mica_index *idx, const uint32_t *packed_reads, const uint64_t *word_offsets,
+                     const uint16_t *lengths, const uint8_t *k, uint64_t n_reads,
+                     const mica_align_params *params, mica_result **out);
+void mica_result_free(mica_result *res);
+
+/*
+ * Align a batch already in DEVICE memory (same layout as mica_align_batch).
+ * The result stays on the device (see mica_device_result).  The call returns
+ * after the result is complete on the given stream.
+ */
+int mica_align_device(mica_index *idx, const uint32_t *d_packed_reads, const uint64_t *d_word_offsets,
+                      const uint16_t *d_lengths, const uint8_t *d_k, uint64_t n_reads,
+                      const mica_align_params *params, mica_device_result *out);
+
+int mica_get_stats(const mica_index *idx, mica_stats *out);
+
+/* ---- parity probes: each exposes one step of the path on the GPU ---- */
+
+/* Suffix array of G$ (len + 1 entries, host output) built on the GPU by the
+   same prefix-doubling code the index builder uses. */
+int mica_debug_suffix_array(const uint8_t *genome_acgt, uint64_t len, int device, uint32_t *sa_out);
+
+/* occ_out[4*i + c] = Occ(c, rows[i]) from the interleaved blocks (host in/out). */
+int mica_debug_occ(const mica_index *idx, const uint64_t *rows, uint64_t n, uint32_t *occ_out);
+
+/* pos_out[i] = SA[rows[i]] resolved by LF walks to the sampled rows (host in/out). */
+int mica_debug_locate(const mica_index *idx, const uint64_t *rows, uint64_t n, uint32_t *pos_out);
+
+/* bounds_out[i] = q-mer table entry codes[i] (host in/out), codes < 4^q + 1. */
+int mica_debug_table(const mica_index *idx, const uint32_t *codes, uint64_t n, uint32_t *bounds_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MICA_H */

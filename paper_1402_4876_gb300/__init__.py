@@ -1,0 +1,309 @@
+"""GB300 k-mismatch FM-index read search (the BWT phase of MICA, Section 2).
+
+Thin ctypes binding over ``libmica_gb300.so`` (C ABI in ``include/mica.h``).
+Every step of the search runs in the library's CUDA kernels; this module only
+marshals arguments.  There is no CPU fallback: if the library is missing or
+cannot be loaded, importing the binding raises.
+
+    import paper_1402_4876_gb300 as mica
+    idx = mica.Index.build(genome_acgt_bytes)            # resident on cuda:0
+    res = idx.align(words, word_off, lengths, k, hit_cap=1000)
+    res.hits_of(i)  # [(pos, strand, mismatches), ...]
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmica_gb300.so")
+
+MICA_OK = 0
+MICA_EINVAL = -1
+MICA_ENOMEM = -2
+MICA_EIO = -3
+MICA_ECUDA = -4
+MICA_ETIMEOUT = -5
+MICA_EINTERNAL = -6
+MICA_EBUSY = -7
+MICA_ENOTFOUND = -8
+MAX_READ_LEN = 256
+KERNELS = {"persistent": 0, "plain": 1}
+
+HIT_DTYPE = np.dtype([("pos", "<u4"), ("strand", "u1"), ("mm", "u1"), ("pad", "<u2")])
+
+
+class MicaError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {_lib.mica_strerror(code).decode()} ({code})")
+
+
+class IndexParams(ctypes.Structure):
+    _fields_ = [("kmer_q", ctypes.c_uint32), ("sa_sample", ctypes.c_uint32)]
+
+
+class AlignParams(ctypes.Structure):
+    _fields_ = [("hit_cap", ctypes.c_uint32), ("kernel", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("n_reads", ctypes.c_uint64), ("total", ctypes.POINTER(ctypes.c_uint64)),
+                ("offsets", ctypes.POINTER(ctypes.c_uint64)), ("hits", ctypes.c_void_p)]
+
+
+class _DeviceResult(ctypes.Structure):
+    _fields_ = [("n_reads", ctypes.c_uint64), ("n_hits", ctypes.c_uint64), ("total", ctypes.c_void_p),
+                ("offsets", ctypes.c_void_p), ("hits", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_uint64) for name in
+                ("tasks", "seeds", "nodes", "rank_blocks", "intervals", "located", "lf_steps",
+                 "spills", "retries")] + [("search_ms", ctypes.c_float), ("total_ms", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class IndexInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("rows", ctypes.c_uint64), ("kmer_q", ctypes.c_uint32),
+                ("sa_sample", ctypes.c_uint32), ("dollar_row", ctypes.c_uint64),
+                ("C", ctypes.c_uint64 * 5), ("occ_bytes", ctypes.c_uint64), ("mark_bytes", ctypes.c_uint64),
+                ("sample_bytes", ctypes.c_uint64), ("table_bytes", ctypes.c_uint64), ("device", ctypes.c_int32)]
+
+
+# exported symbol -> (restype, argtypes); the C ABI's full surface
+P = ctypes.c_void_p
+_u64, _u32, _i32 = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+SIGNATURES = {
+    "mica_strerror": (ctypes.c_char_p, [_i32]),
+    "mica_index_params_default": (None, [P]),
+    "mica_align_params_default": (None, [P]),
+    "mica_index_build_resident": (_i32, [P, _u64, P, _i32, P]),
+    "mica_index_build": (_i32, [P, _u64, P, ctypes.c_char_p]),
+    "mica_index_save": (_i32, [P, ctypes.c_char_p]),
+    "mica_index_load": (_i32, [ctypes.c_char_p, _i32, P]),
+    "mica_index_free": (None, [P]),
+    "mica_index_get_info": (_i32, [P, P]),
+    "mica_align_batch": (_i32, [P, P, P, P, P, _u64, P, P]),
+    "mica_result_free": (None, [P]),
+    "mica_align_device": (_i32, [P, P, P, P, P, _u64, P, P]),
+    "mica_get_stats": (_i32, [P, P]),
+    "mica_debug_suffix_array": (_i32, [P, _u64, _i32, P]),
+    "mica_debug_occ": (_i32, [P, P, _u64, P]),
+    "mica_debug_locate": (_i32, [P, P, _u64, P]),
+    "mica_debug_table": (_i32, [P, P, _u64, P]),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_1402_4876_gb300/_build.py` "
+                          "or __graft_entry__.build() (nvcc, sm_103a); there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name, None)
+        if fn is None:
+            continue
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != MICA_OK:
+        raise MicaError(rc, what)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _acgt(genome) -> np.ndarray:
+    if isinstance(genome, (bytes, bytearray)):
+        return np.frombuffer(bytes(genome), dtype=np.uint8)
+    return np.ascontiguousarray(genome, dtype=np.uint8)
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)   # torch.cuda.Stream
+
+
+class Result:
+    """Host-side hit lists in CSR form."""
+
+    def __init__(self, total, offsets, hits):
+        self.total = total
+        self.offsets = offsets
+        self.hits = hits
+
+    def read_hits(self, i: int) -> np.ndarray:
+        return self.hits[int(self.offsets[i]):int(self.offsets[i + 1])]
+
+    def hits_of(self, i: int) -> list:
+        h = self.read_hits(i)
+        return [(int(p), int(s), int(d)) for p, s, d in zip(h["pos"], h["strand"], h["mm"])]
+
+
+class _CudaArray:
+    """Zero-copy view of a device array for torch.as_tensor (CUDA array interface)."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr or 0), True), "version": 3, "strides": None}
+
+
+class DeviceResult:
+    """Result left on the device; valid until the next align call on the index."""
+
+    def __init__(self, r: _DeviceResult):
+        self.n_reads = int(r.n_reads)
+        self.n_hits = int(r.n_hits)
+        self._r = r
+
+    def tensors(self):
+        """(total[u64 n], offsets[u64 n+1], hits[u8 8*n_hits]) as torch CUDA tensors (views)."""
+        import torch
+        t = torch.as_tensor(_CudaArray(self._r.total, (self.n_reads,), "<u8"), device="cuda")
+        o = torch.as_tensor(_CudaArray(self._r.offsets, (self.n_reads + 1,), "<u8"), device="cuda")
+        h = torch.as_tensor(_CudaArray(self._r.hits, (8 * self.n_hits,), "|u1"), device="cuda")
+        return t, o, h
+
+
+class Index:
+    """A resident FM index on one GPU (mica_index)."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+
+    @classmethod
+    def build(cls, genome_acgt, kmer_q: int = 12, sa_sample: int = 16, device: int = 0) -> "Index":
+        g = _acgt(genome_acgt)
+        p = IndexParams(kmer_q, sa_sample)
+        h = ctypes.c_void_p()
+        _check(_lib.mica_index_build_resident(_ptr(g) if g.size else None, g.size, ctypes.byref(p), device,
+                                             ctypes.byref(h)), "mica_index_build_resident")
+        return cls(h.value)
+
+    @classmethod
+    def load(cls, path: str, device: int = 0) -> "Index":
+        h = ctypes.c_void_p()
+        _check(_lib.mica_index_load(os.fsencode(path), device, ctypes.byref(h)), "mica_index_load")
+        return cls(h.value)
+
+    def save(self, path: str):
+        _check(_lib.mica_index_save(self._h, os.fsencode(path)), "mica_index_save")
+
+    def free(self):
+        if self._h:
+            _lib.mica_index_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        i = IndexInfo()
+        _check(_lib.mica_index_get_info(self._h, ctypes.byref(i)), "mica_index_get_info")
+        d = {name: getattr(i, name) for name, _ in IndexInfo._fields_}
+        d["C"] = list(i.C)
+        return d
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(_lib.mica_get_stats(self._h, ctypes.byref(s)), "mica_get_stats")
+        return s.as_dict()
+
+    @staticmethod
+    def _params(hit_cap, kernel, stream):
+        return AlignParams(hit_cap, KERNELS[kernel] if isinstance(kernel, str) else int(kernel),
+                           _stream_handle(stream))
+
+    def align(self, words, word_off, lengths, k, hit_cap: int = 1000, kernel="persistent",
+              stream=None) -> Result:
+        """mica_align_batch on host arrays (copies in, searches, copies out)."""
+        words = np.ascontiguousarray(words, dtype=np.uint32)
+        word_off = np.ascontiguousarray(word_off, dtype=np.uint64)
+        lengths = np.ascontiguousarray(lengths, dtype=np.uint16)
+        k = np.ascontiguousarray(k, dtype=np.uint8)
+        n = lengths.size
+        p = self._params(hit_cap, kernel, stream)
+        out = ctypes.POINTER(_Result)()
+        _check(_lib.mica_align_batch(self._h, _ptr(words) if words.size else None, _ptr(word_off),
+                                     _ptr(lengths) if n else None, _ptr(k) if n else None, n,
+                                     ctypes.byref(p), ctypes.byref(out)), "mica_align_batch")
+        try:
+            r = out.contents
+            total = np.ctypeslib.as_array(r.total, shape=(max(n, 1),))[:n].copy()
+            offsets = np.ctypeslib.as_array(r.offsets, shape=(n + 1,)).copy()
+            nh = int(offsets[-1])
+            hits = np.empty(nh, dtype=HIT_DTYPE)
+            if nh:
+                ctypes.memmove(hits.ctypes.data, r.hits, nh * HIT_DTYPE.itemsize)
+        finally:
+            _lib.mica_result_free(out)
+        return Result(total, offsets, hits)
+
+    def align_batch(self, batch, **kw) -> Result:
+        """align() on any object with words/word_off/lengths/k arrays."""
+        return self.align(batch.words, batch.word_off, batch.lengths, batch.k, **kw)
+
+    def align_device(self, d_words, d_word_off, d_lengths, d_k, n_reads: int, hit_cap: int = 1000,
+                     kernel="persistent", stream=None) -> DeviceResult:
+        """mica_align_device on device pointers (ints) or torch CUDA tensors."""
+        ptr = lambda x: x if isinstance(x, int) else x.data_ptr()
+        p = self._params(hit_cap, kernel, stream)
+        r = _DeviceResult()
+        _check(_lib.mica_align_device(self._h, ctypes.c_void_p(ptr(d_words)), ctypes.c_void_p(ptr(d_word_off)),
+                                      ctypes.c_void_p(ptr(d_lengths)), ctypes.c_void_p(ptr(d_k)), n_reads,
+                                      ctypes.byref(p), ctypes.byref(r)), "mica_align_device")
+        return DeviceResult(r)
+
+    # ---- parity probes ----
+    def debug_occ(self, rows) -> np.ndarray:
+        rows = np.ascontiguousarray(rows, dtype=np.uint64)
+        out = np.empty((rows.size, 4), dtype=np.uint32)
+        _check(_lib.mica_debug_occ(self._h, _ptr(rows), rows.size, _ptr(out)), "mica_debug_occ")
+        return out
+
+    def debug_locate(self, rows) -> np.ndarray:
+        rows = np.ascontiguousarray(rows, dtype=np.uint64)
+        out = np.empty(rows.size, dtype=np.uint32)
+        _check(_lib.mica_debug_locate(self._h, _ptr(rows), rows.size, _ptr(out)), "mica_debug_locate")
+        return out
+
+    def debug_table(self, codes) -> np.ndarray:
+        codes = np.ascontiguousarray(codes, dtype=np.uint32)
+        out = np.empty(codes.size, dtype=np.uint32)
+        _check(_lib.mica_debug_table(self._h, _ptr(codes), codes.size, _ptr(out)), "mica_debug_table")
+        return out
+
+
+def debug_suffix_array(genome_acgt, device: int = 0) -> np.ndarray:
+    """Suffix array of G$ built on the GPU (mica_debug_suffix_array)."""
+    g = _acgt(genome_acgt)
+    sa = np.empty(g.size + 1, dtype=np.uint32)
+    _check(_lib.mica_debug_suffix_array(_ptr(g) if g.size else None, g.size, device, _ptr(sa)),
+           "mica_debug_suffix_array")
+    return sa
+
+
+def exported_symbols() -> list:
+    return sorted(SIGNATURES)

@@ -1,0 +1,543 @@
+// The extern "C" boundary of libmica_gb300 (declared in include/mica.h).
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "mica_internal.cuh"
+
+namespace mica {
+
+static thread_local char g_last_error[512];
+
+void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line)
+{
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s:%d)", cudaGetErrorString(e), what, file, line);
+}
+
+int dev_reserve(DevBuf &b, size_t bytes)
+{
+    if (bytes <= b.bytes && b.p) return 0;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    size_t want = std::max<size_t>(bytes, 256);
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_last_cuda_error(e, "cudaMalloc", __FILE__, __LINE__);
+        b.p = nullptr;
+        return MICA_ENOMEM;
+    }
+    b.bytes = want;
+    return 0;
+}
+
+void dev_release(DevBuf &b)
+{
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+static void free_workspace(Workspace &w)
+{
+    DevBuf *all[] = {&w.ctl, &w.iv, &w.iv_sorted, &w.iv_cnt, &w.iv_off, &w.total, &w.keep, &w.hit_off,
+                     &w.hits, &w.spill, &w.big, &w.scan_tmp, &w.reads_words, &w.reads_off, &w.reads_len,
+                     &w.reads_k, &w.spill2};
+    for (DevBuf *b : all) dev_release(*b);
+    for (auto &e : w.ev)
+        if (e) { cudaEventDestroy(e); e = nullptr; }
+}
+
+static int validate_params(const mica_index_params &p)
+{
+    if (p.kmer_q < 1 || p.kmer_q > MAX_Q) return MICA_EINVAL;
+    if (p.sa_sample < 1 || p.sa_sample > 256) return MICA_EINVAL;
+    return 0;
+}
+
+// ASCII genome -> base codes (host), rejecting anything but A/C/G/T.
+static int encode_genome(const uint8_t *acgt, uint64_t len, std::vector<uint8_t> &codes)
+{
+    static uint8_t lut[256];
+    static std::once_flag once;
+    std::call_once(once, [] {
+        memset(lut, 0xff, sizeof(lut));
+        lut['A'] = lut['a'] = 0; lut['C'] = lut['c'] = 1;
+        lut['G'] = lut['g'] = 2; lut['T'] = lut['t'] = 3;
+    });
+    codes.resize(len);
+    for (uint64_t i = 0; i < len; i++) {
+        uint8_t c = lut[acgt[i]];
+        if (c > 3) return MICA_EINVAL;
+        codes[i] = c;
+    }
+    return 0;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) { if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev); else prev = -1; }
+    ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
+// ---- index file ----
+
+static const char MAGIC[8] = {'M', 'I', 'C', 'A', 'I', 'D', 'X', '1'};
+
+struct FileHeader {
+    char magic[8];
+    uint32_t version, kmer_q, sa_sample, reserved;
+    uint64_t n, dollar_row;
+    uint64_t C[5];
+    uint64_t n_occ_blocks, n_mark_blocks, n_samples, table_len;
+};
+
+static int write_array(FILE *f, const DevBuf &b, uint64_t bytes)
+{
+    std::vector<char> h(std::min<uint64_t>(bytes, 1ull << 26));
+    for (uint64_t off = 0; off < bytes; off += h.size()) {
+        uint64_t c = std::min<uint64_t>(h.size(), bytes - off);
+        MICA_CUDA_TRY(cudaMemcpy(h.data(), (const char *)b.p + off, c, cudaMemcpyDeviceToHost));
+        if (fwrite(h.data(), 1, c, f) != c) return MICA_EIO;
+    }
+    return 0;
+}
+
+static int read_array(FILE *f, DevBuf &b, uint64_t bytes)
+{
+    if (int rc = dev_reserve(b, std::max<uint64_t>(bytes, 4))) return rc;
+    std::vector<char> h(std::min<uint64_t>(std::max<uint64_t>(bytes, 1), 1ull << 26));
+    for (uint64_t off = 0; off < bytes; off += h.size()) {
+        uint64_t c = std::min<uint64_t>(h.size(), bytes - off);
+        if (fread(h.data(), 1, c, f) != c) return MICA_EIO;
+        MICA_CUDA_TRY(cudaMemcpy((char *)b.p + off, h.data(), c, cudaMemcpyHostToDevice));
+    }
+    return 0;
+}
+
+// ---- align orchestration ----
+
+static int align_on_device(mica_index *idx, const ReadsView &rd, const mica_align_params &p, cudaStream_t s,
+                           uint64_t *nh)
+{
+    Workspace &w = idx->ws;
+    for (auto &e : w.ev)
+        if (!e) MICA_CUDA_TRY(cudaEventCreate(&e));
+    idx->stats = mica_stats{};
+    MICA_CUDA_TRY(cudaEventRecord(w.ev[0], s));
+    SearchConfig cfg{};
+    cfg.kernel = p.kernel;
+    cfg.plain_block = 128;
+    cfg.plain_budget = 1u << 16;
+    int rc = run_search(idx, rd, cfg, s);
+    if (rc) return rc;
+    MICA_CUDA_TRY(cudaEventRecord(w.ev[1], s));
+    if ((rc = run_post(idx, rd, p.hit_cap, s, nh))) return rc;
+    MICA_CUDA_TRY(cudaEventRecord(w.ev[2], s));
+    MICA_CUDA_TRY(cudaEventSynchronize(w.ev[2]));
+    cudaEventElapsedTime(&idx->stats.search_ms, w.ev[0], w.ev[1]);
+    cudaEventElapsedTime(&idx->stats.total_ms, w.ev[0], w.ev[2]);
+    return 0;
+}
+
+}  // namespace mica
+
+using namespace mica;
+
+extern "C" {
+
+const char *mica_strerror(int code)
+{
+    switch (code) {
+    case MICA_OK: return "ok";
+    case MICA_EINVAL: return "invalid argument";
+    case MICA_ENOMEM: return "out of memory";
+    case MICA_EIO: return "index file I/O error or malformed file";
+    case MICA_ECUDA: return g_last_error[0] ? g_last_error : "CUDA error";
+    case MICA_ETIMEOUT: return "bounded wait expired";
+    case MICA_EINTERNAL: return "internal capacity retry did not converge";
+    case MICA_EBUSY: return "request not finished";
+    case MICA_ENOTFOUND: return "unknown request";
+    default: return "unknown error";
+    }
+}
+
+void mica_index_params_default(mica_index_params *p)
+{
+    p->kmer_q = 12;
+    p->sa_sample = 16;
+}
+
+void mica_align_params_default(mica_align_params *p)
+{
+    p->hit_cap = 1000;
+    p->kernel = MICA_KERNEL_PERSISTENT;
+    p->cuda_stream = nullptr;
+}
+
+int mica_index_build_resident(const uint8_t *genome_acgt, uint64_t len, const mica_index_params *params,
+                              int device, mica_index **out)
+{
+    if (!out || (!genome_acgt && len)) return MICA_EINVAL;
+    *out = nullptr;
+    mica_index_params p;
+    mica_index_params_default(&p);
+    if (params) p = *params;
+    if (int rc = validate_params(p)) return rc;
+    if (len + 1 >= (1ull << 32)) return MICA_EINVAL;
+    std::vector<uint8_t> codes;
+    if (int rc = encode_genome(genome_acgt, len, codes)) return rc;
+    DeviceGuard g(device);
+    MICA_CUDA_TRY(cudaSetDevice(device));
+    mica_index *idx = new mica_index();
+    idx->device = device;
+    DevBuf dcodes;
+    int rc = dev_reserve(dcodes, std::max<uint64_t>(len, 1));
+    if (!rc && len) {
+        cudaError_t e = cudaMemcpy(dcodes.p, codes.data(), len, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { set_last_cuda_error(e, "cudaMemcpy genome", __FILE__, __LINE__); rc = MICA_ECUDA; }
+    }
+    if (!rc) rc = build_index_from_codes((const uint8_t *)dcodes.p, len, p, idx, 0);
+    dev_release(dcodes);
+    if (rc) { mica_index_free(idx); return rc; }
+    *out = idx;
+    return 0;
+}
+
+int mica_index_build(const uint8_t *genome_acgt, uint64_t len, const mica_index_params *params,
+                     const char *out_path)
+{
+    if (!out_path) return MICA_EINVAL;
+    int dev = 0;
+    MICA_CUDA_TRY(cudaGetDevice(&dev));
+    mica_index *idx = nullptr;
+    int rc = mica_index_build_resident(genome_acgt, len, params, dev, &idx);
+    if (rc) return rc;
+    rc = mica_index_save(idx, out_path);
+    mica_index_free(idx);
+    return rc;
+}
+
+int mica_index_save(const mica_index *idx, const char *path)
+{
+    if (!idx || !path) return MICA_EINVAL;
+    DeviceGuard g(idx->device);
+    FILE *f = fopen(path, "wb");
+    if (!f) return MICA_EIO;
+    FileHeader h{};
+    memcpy(h.magic, MAGIC, 8);
+    h.version = 1;
+    h.kmer_q = idx->params.kmer_q;
+    h.sa_sample = idx->params.sa_sample;
+    h.n = idx->n;
+    h.dollar_row = idx->view.dollar_row;
+    for (int c = 0; c < 5; c++) h.C[c] = idx->view.C[c];
+    h.n_occ_blocks = idx->n_occ_blocks;
+    h.n_mark_blocks = idx->n_mark_blocks;
+    h.n_samples = idx->n_samples;
+    h.table_len = idx->table_len;
+    int rc = fwrite(&h, sizeof(h), 1, f) == 1 ? 0 : MICA_EIO;
+    if (!rc) rc = write_array(f, idx->occ, h.n_occ_blocks * 64);
+    if (!rc) rc = write_array(f, idx->marks, h.n_mark_blocks * 64);
+    if (!rc) rc = write_array(f, idx->samples, h.n_samples * 4);
+    if (!rc) rc = write_array(f, idx->table, h.table_len * 4);
+    if (fclose(f) != 0 && !rc) rc = MICA_EIO;
+    return rc;
+}
+
+int mica_index_load(const char *path, int device, mica_index **out)
+{
+    if (!path || !out) return MICA_EINVAL;
+    *out = nullptr;
+    FILE *f = fopen(path, "rb");
+    if (!f) return MICA_EIO;
+    FileHeader h{};
+    if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, MAGIC, 8) != 0 || h.version != 1 ||
+        h.kmer_q < 1 || h.kmer_q > MAX_Q || h.sa_sample < 1 || h.n + 1 >= (1ull << 32) ||
+        h.n_occ_blocks != (h.n + 1) / OCC_ROWS + 1 || h.n_mark_blocks != (h.n + 1) / MARK_ROWS + 1 ||
+        h.table_len != (1ull << (2 * h.kmer_q)) + 1 || h.n_samples > h.n + 1) {
+        fclose(f);
+        return MICA_EIO;
+    }
+    DeviceGuard g(device);
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) { fclose(f); set_last_cuda_error(e, "cudaSetDevice", __FILE__, __LINE__); return MICA_ECUDA; }
+    mica_index *idx = new mica_index();
+    idx->device = device;
+    idx->params.kmer_q = h.kmer_q;
+    idx->params.sa_sample = h.sa_sample;
+    idx->n = h.n;
+    idx->n_occ_blocks = h.n_occ_blocks;
+    idx->n_mark_blocks = h.n_mark_blocks;
+    idx->n_samples = h.n_samples;
+    idx->table_len = h.table_len;
+    int rc = read_array(f, idx->occ, h.n_occ_blocks * 64);
+    if (!rc) rc = read_array(f, idx->marks, h.n_mark_blocks * 64);
+    if (!rc) rc = read_array(f, idx->samples, h.n_samples * 4);
+    if (!rc) rc = read_array(f, idx->table, h.table_len * 4);
+    fclose(f);
+    if (!rc) {
+        IndexView &v = idx->view;
+        v.occ = (const uint4 *)idx->occ.p;
+        v.marks = (const uint4 *)idx->marks.p;
+        v.samples = (const uint32_t *)idx->samples.p;
+        v.table = (const uint32_t *)idx->table.p;
+        v.n = h.n;
+        v.rows = (uint32_t)(h.n + 1);
+        v.dollar_row = (uint32_t)h.dollar_row;
+        for (int c = 0; c < 5; c++) v.C[c] = (uint32_t)h.C[c];
+        v.q = h.kmer_q;
+        v.sa_sample = h.sa_sample;
+        rc = upload_variants(idx);
+    }
+    if (rc) { mica_index_free(idx); return rc; }
+    *out = idx;
+    return 0;
+}
+
+void mica_index_free(mica_index *idx)
+{
+    if (!idx) return;
+    DeviceGuard g(idx->device);
+    cudaSetDevice(idx->device);
+    dev_release(idx->occ);
+    dev_release(idx->marks);
+    dev_release(idx->samples);
+    dev_release(idx->table);
+    dev_release(idx->variants);
+    free_workspace(idx->ws);
+    delete idx;
+}
+
+int mica_index_get_info(const mica_index *idx, mica_index_info *info)
+{
+    if (!idx || !info) return MICA_EINVAL;
+    info->n = idx->n;
+    info->rows = idx->n + 1;
+    info->kmer_q = idx->params.kmer_q;
+    info->sa_sample = idx->params.sa_sample;
+    info->dollar_row = idx->view.dollar_row;
+    for (int c = 0; c < 5; c++) info->C[c] = idx->view.C[c];
+    info->occ_bytes = idx->n_occ_blocks * 64;
+    info->mark_bytes = idx->n_mark_blocks * 64;
+    info->sample_bytes = idx->n_samples * 4;
+    info->table_bytes = idx->table_len * 4;
+    info->device = idx->device;
+    return 0;
+}
+
+int mica_get_stats(const mica_index *idx, mica_stats *out)
+{
+    if (!idx || !out) return MICA_EINVAL;
+    *out = idx->stats;
+    return 0;
+}
+
+}  // extern "C"
+
+namespace mica {
+namespace {
+
+__global__ void k_validate(ReadsView rd, uint64_t genome_len, unsigned int *bad)
+{
+    uint64_t total_words = rd.word_off[rd.n];
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < rd.n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t m = rd.len[i];
+        uint64_t off = rd.word_off[i];
+        if (m == 0 || m > MICA_MAX_READ_LEN || m > genome_len || rd.k[i] > MICA_MAX_K ||
+            off > total_words || total_words - off < (m + 15) / 16)
+            atomicOr(bad, 1u);
+    }
+}
+
+int validate_device_batch(mica_index *idx, const ReadsView &rd, cudaStream_t s)
+{
+    if (rd.n == 0) return 0;
+    if (int rc = dev_reserve(idx->ws.ctl, sizeof(SearchCtl) + 64)) return rc;
+    unsigned int *bad = (unsigned int *)((char *)idx->ws.ctl.p + sizeof(SearchCtl));
+    MICA_CUDA_TRY(cudaMemsetAsync(bad, 0, 4, s));
+    unsigned g = (unsigned)std::min<uint64_t>((rd.n + 255) / 256, 152 * 32);
+    k_validate<<<g, 256, 0, s>>>(rd, idx->n, bad);
+    unsigned int hb = 0;
+    MICA_CUDA_TRY(cudaMemcpyAsync(&hb, bad, 4, cudaMemcpyDeviceToHost, s));
+    MICA_CUDA_TRY(cudaStreamSynchronize(s));
+    return hb ? MICA_EINVAL : 0;
+}
+
+int validate_host_batch(const mica_index *idx, const uint64_t *off, const uint16_t *len, const uint8_t *k,
+                        uint64_t n)
+{
+    uint64_t total = off[n];
+    for (uint64_t i = 0; i < n; i++) {
+        uint32_t m = len[i];
+        if (m == 0 || m > MICA_MAX_READ_LEN || m > idx->n || k[i] > MICA_MAX_K || off[i] > total ||
+            total - off[i] < (m + 15) / 16)
+            return MICA_EINVAL;
+    }
+    return 0;
+}
+
+}  // namespace
+}  // namespace mica
+
+extern "C" {
+
+int mica_align_device(mica_index *idx, const uint32_t *d_packed_reads, const uint64_t *d_word_offsets,
+                      const uint16_t *d_lengths, const uint8_t *d_k, uint64_t n_reads,
+                      const mica_align_params *params, mica_device_result *out)
+{
+    if (!idx || !out || (n_reads && (!d_packed_reads || !d_word_offsets || !d_lengths || !d_k)))
+        return MICA_EINVAL;
+    if (n_reads >= (1ull << 31)) return MICA_EINVAL;
+    mica_align_params p;
+    mica_align_params_default(&p);
+    if (params) p = *params;
+    if (p.kernel != MICA_KERNEL_PERSISTENT && p.kernel != MICA_KERNEL_PLAIN) return MICA_EINVAL;
+    DeviceGuard g(idx->device);
+    MICA_CUDA_TRY(cudaSetDevice(idx->device));
+    cudaStream_t s = (cudaStream_t)p.cuda_stream;
+    ReadsView rd{d_packed_reads, d_word_offsets, d_lengths, d_k, n_reads};
+    if (int rc = validate_device_batch(idx, rd, s)) return rc;
+    uint64_t nh = 0;
+    if (int rc = align_on_device(idx, rd, p, s, &nh)) return rc;
+    out->n_reads = n_reads;
+    out->n_hits = nh;
+    out->total = (const uint64_t *)idx->ws.total.p;
+    out->offsets = (const uint64_t *)idx->ws.hit_off.p;
+    out->hits = (const mica_hit *)idx->ws.hits.p;
+    return 0;
+}
+
+int mica_align_batch(mica_index *idx, const uint32_t *packed_reads, const uint64_t *word_offsets,
+                     const uint16_t *lengths, const uint8_t *k, uint64_t n_reads,
+                     const mica_align_params *params, mica_result **out)
+{
+    if (!idx || !out || !word_offsets || (n_reads && (!packed_reads || !lengths || !k))) return MICA_EINVAL;
+    *out = nullptr;
+    if (n_reads >= (1ull << 31)) return MICA_EINVAL;
+    if (int rc = validate_host_batch(idx, word_offsets, lengths, k, n_reads)) return rc;
+    mica_align_params p;
+    mica_align_params_default(&p);
+    if (params) p = *params;
+    DeviceGuard g(idx->device);
+    MICA_CUDA_TRY(cudaSetDevice(idx->device));
+    cudaStream_t s = (cudaStream_t)p.cuda_stream;
+    Workspace &w = idx->ws;
+    uint64_t nw = word_offsets[n_reads];
+    int rc;
+    if ((rc = dev_reserve(w.reads_words, std::max<uint64_t>(nw, 1) * 4)) ||
+        (rc = dev_reserve(w.reads_off, (n_reads + 1) * 8)) ||
+        (rc = dev_reserve(w.reads_len, std::max<uint64_t>(n_reads, 1) * 2)) ||
+        (rc = dev_reserve(w.reads_k, std::max<uint64_t>(n_reads, 1))))
+        return rc;
+    if (nw) MICA_CUDA_TRY(cudaMemcpyAsync(w.reads_words.p, packed_reads, nw * 4, cudaMemcpyHostToDevice, s));
+    MICA_CUDA_TRY(cudaMemcpyAsync(w.reads_off.p, word_offsets, (n_reads + 1) * 8, cudaMemcpyHostToDevice, s));
+    if (n_reads) {
+        MICA_CUDA_TRY(cudaMemcpyAsync(w.reads_len.p, lengths, n_reads * 2, cudaMemcpyHostToDevice, s));
+        MICA_CUDA_TRY(cudaMemcpyAsync(w.reads_k.p, k, n_reads, cudaMemcpyHostToDevice, s));
+    }
+    ReadsView rd{(const uint32_t *)w.reads_words.p, (const uint64_t *)w.reads_off.p,
+                 (const uint16_t *)w.reads_len.p, (const uint8_t *)w.reads_k.p, n_reads};
+    uint64_t nh = 0;
+    if ((rc = align_on_device(idx, rd, p, s, &nh))) return rc;
+    mica_result *r = (mica_result *)calloc(1, sizeof(mica_result));
+    if (!r) return MICA_ENOMEM;
+    r->n_reads = n_reads;
+    r->total = (uint64_t *)malloc(std::max<uint64_t>(n_reads, 1) * 8);
+    r->offsets = (uint64_t *)malloc((n_reads + 1) * 8);
+    r->hits = (mica_hit *)malloc(std::max<uint64_t>(nh, 1) * sizeof(mica_hit));
+    if (!r->total || !r->offsets || !r->hits) { mica_result_free(r); return MICA_ENOMEM; }
+    cudaError_t e = cudaSuccess;
+    if (n_reads) e = cudaMemcpyAsync(r->total, w.total.p, n_reads * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(r->offsets, w.hit_off.p, (n_reads + 1) * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && nh) e = cudaMemcpyAsync(r->hits, w.hits.p, nh * sizeof(mica_hit), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e, "result copy", __FILE__, __LINE__);
+        mica_result_free(r);
+        return MICA_ECUDA;
+    }
+    *out = r;
+    return 0;
+}
+
+void mica_result_free(mica_result *res)
+{
+    if (!res) return;
+    free(res->total);
+    free(res->offsets);
+    free(res->hits);
+    free(res);
+}
+
+int mica_debug_suffix_array(const uint8_t *genome_acgt, uint64_t len, int device, uint32_t *sa_out)
+{
+    if ((!genome_acgt && len) || !sa_out || len + 1 >= (1ull << 32)) return MICA_EINVAL;
+    std::vector<uint8_t> codes;
+    if (int rc = encode_genome(genome_acgt, len, codes)) return rc;
+    DeviceGuard g(device);
+    MICA_CUDA_TRY(cudaSetDevice(device));
+    DevBuf dc, dsa;
+    int rc = dev_reserve(dc, std::max<uint64_t>(len, 1));
+    if (!rc) rc = dev_reserve(dsa, (len + 1) * 4);
+    if (!rc && len && cudaMemcpy(dc.p, codes.data(), len, cudaMemcpyHostToDevice) != cudaSuccess) rc = MICA_ECUDA;
+    if (!rc) rc = build_suffix_array((const uint8_t *)dc.p, len, (uint32_t *)dsa.p, 0);
+    if (!rc && cudaMemcpy(sa_out, dsa.p, (len + 1) * 4, cudaMemcpyDeviceToHost) != cudaSuccess) rc = MICA_ECUDA;
+    dev_release(dc);
+    dev_release(dsa);
+    return rc;
+}
+
+static int debug_rows_call(const mica_index *idx, const uint64_t *rows, uint64_t n, uint32_t *out, int per_row,
+                           int which)
+{
+    if (!idx || (n && (!rows || !out))) return MICA_EINVAL;
+    // Occ is defined for rows 0..N+1, SA for rows 0..N
+    uint64_t limit = which == 0 ? idx->n + 1 : idx->n;
+    for (uint64_t i = 0; i < n; i++)
+        if (rows[i] > limit) return MICA_EINVAL;
+    if (n == 0) return 0;
+    DeviceGuard g(idx->device);
+    MICA_CUDA_TRY(cudaSetDevice(idx->device));
+    DevBuf dr, dout;
+    int rc = dev_reserve(dr, n * 8);
+    if (!rc) rc = dev_reserve(dout, n * 4 * per_row);
+    if (!rc && cudaMemcpy(dr.p, rows, n * 8, cudaMemcpyHostToDevice) != cudaSuccess) rc = MICA_ECUDA;
+    if (!rc) rc = which == 0 ? debug_occ(idx, (const uint64_t *)dr.p, n, (uint32_t *)dout.p, 0)
+                             : debug_locate(idx, (const uint64_t *)dr.p, n, (uint32_t *)dout.p, 0);
+    if (!rc && cudaMemcpy(out, dout.p, n * 4 * per_row, cudaMemcpyDeviceToHost) != cudaSuccess) rc = MICA_ECUDA;
+    dev_release(dr);
+    dev_release(dout);
+    return rc;
+}
+
+int mica_debug_occ(const mica_index *idx, const uint64_t *rows, uint64_t n, uint32_t *occ_out)
+{
+    return debug_rows_call(idx, rows, n, occ_out, 4, 0);
+}
+
+int mica_debug_locate(const mica_index *idx, const uint64_t *rows, uint64_t n, uint32_t *pos_out)
+{
+    return debug_rows_call(idx, rows, n, pos_out, 1, 1);
+}
+
+int mica_debug_table(const mica_index *idx, const uint32_t *codes, uint64_t n, uint32_t *bounds_out)
+{
+    if (!idx || (n && (!codes || !bounds_out))) return MICA_EINVAL;
+    std::vector<uint32_t> tab(idx->table_len);
+    for (uint64_t i = 0; i < n; i++)
+        if (codes[i] >= idx->table_len) return MICA_EINVAL;
+    DeviceGuard g(idx->device);
+    MICA_CUDA_TRY(cudaSetDevice(idx->device));
+    MICA_CUDA_TRY(cudaMemcpy(tab.data(), idx->table.p, idx->table_len * 4, cudaMemcpyDeviceToHost));
+    for (uint64_t i = 0; i < n; i++) bounds_out[i] = tab[codes[i]];
+    return 0;
+}
+
+}  // extern "C"

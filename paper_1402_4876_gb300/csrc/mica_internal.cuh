@@ -1,0 +1,178 @@
+// Internal definitions shared by the CUDA translation units of libmica_gb300.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "mica.h"
+
+namespace mica {
+
+// ---------------------------------------------------------------------------
+// Index layout constants
+// ---------------------------------------------------------------------------
+// Occurrence block: 64 bytes = 4 x uint32 counts Occ(A..T, block start)
+// followed by 12 x uint32 words holding 192 BWT symbols, 2 bits each,
+// least-significant first ($ is stored as A and corrected with dollar_row).
+constexpr uint32_t OCC_ROWS = 192;
+constexpr uint32_t OCC_WORDS = 16;        // uint32 per block
+// Mark block: 64 bytes = uint32 rank of marked rows before the block + 15
+// words of mark bits (480 rows).
+constexpr uint32_t MARK_ROWS = 480;
+constexpr uint32_t MAX_Q = 12;
+constexpr uint32_t MAX_WORDS = MICA_MAX_READ_LEN / 16;   // packed words per read
+
+// Seed variants: for budget k, every way to substitute <= k of the last q
+// bases; ordered so the first V(q', k) entries touch only the last q' bases.
+constexpr uint32_t VAR_OFF[5] = {0, 1, 38, 669, 7240};
+constexpr uint32_t N_VARIANTS = 7240;
+__host__ __device__ __forceinline__ uint32_t var_off(uint32_t k)
+{
+    return k == 0 ? 0u : k == 1 ? 1u : k == 2 ? 38u : 669u;
+}
+
+// Device view of a resident index, passed to kernels by value.
+struct IndexView {
+    const uint4 *occ;          // blocks * 4 uint4
+    const uint4 *marks;        // mark blocks * 4 uint4
+    const uint32_t *samples;   // SA values of marked rows, in row order
+    const uint32_t *table;     // 4^q + 1 bounds
+    const uint32_t *variants;  // N_VARIANTS seed variants: bits 0..23 xor mask, 24..25 d
+    uint64_t n;                // genome length
+    uint32_t rows;             // n + 1
+    uint32_t dollar_row;
+    uint32_t C[5];
+    uint32_t q;
+    uint32_t sa_sample;
+};
+
+// Read batch in device memory.
+struct ReadsView {
+    const uint32_t *words;
+    const uint64_t *word_off;
+    const uint16_t *len;
+    const uint8_t *k;
+    uint64_t n;
+};
+
+// Leaf interval found by the search.
+struct Interval {
+    uint32_t read;
+    uint32_t meta;   // bit 0..1 d, bit 2 strand
+    uint32_t l, r;
+};
+
+// Work item in the device queues: a seed range of a (read, strand) task or a
+// continuation node.  meta: bit 31 valid flag (spill queue), bit 30 kind
+// (1 = node), bit 29 strand, bits 0..1 d, bits 8..16 i (node).
+struct WorkItem {
+    uint32_t read;
+    uint32_t meta;
+    uint32_t a, b;   // node: l, r; seeds: first, end variant
+};
+constexpr uint32_t WI_VALID = 1u << 31;
+constexpr uint32_t WI_NODE = 1u << 30;
+constexpr uint32_t WI_MINUS = 1u << 29;
+
+// Hit as written to the output (matches mica_hit).
+struct Hit {
+    uint32_t pos;
+    uint8_t strand, mm;
+    uint16_t pad;
+};
+
+// Device-global control block of one search launch.
+struct SearchCtl {
+    unsigned long long task_head;     // next fresh task
+    unsigned long long ntasks;
+    unsigned int spill_reserve;       // spill queue: reserved slots
+    unsigned int spill_head;          // spill queue: consumed slots
+    unsigned int spill_cap;
+    int busy;                         // warps holding work
+    unsigned int iv_count;            // intervals written
+    unsigned int iv_cap;
+    unsigned int error;               // bit 0 interval overflow, bit 1 spill overflow, bit 2 timeout
+    unsigned int pad_;
+    unsigned long long seeds, nodes, rank_blocks, spills;
+};
+
+constexpr unsigned ERR_IV_OVERFLOW = 1u;
+constexpr unsigned ERR_SPILL_OVERFLOW = 2u;
+constexpr unsigned ERR_TIMEOUT = 4u;
+constexpr unsigned ERR_HIT_OVERFLOW = 8u;
+
+// ---------------------------------------------------------------------------
+// Host-side helpers
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+int dev_reserve(DevBuf &b, size_t bytes);   // grow-only device buffer
+void dev_release(DevBuf &b);
+
+// Per-index workspace reused across align calls.
+struct Workspace {
+    DevBuf ctl, iv, iv_sorted, iv_cnt, iv_off, total, keep, hit_off, hits, spill, big, scan_tmp;
+    DevBuf reads_words, reads_off, reads_len, reads_k;   // staging for host batches
+    DevBuf spill2;                                        // plain kernel re-queue ping-pong
+    uint32_t iv_cap = 0, spill_cap = 0;
+    uint64_t hit_cap_total = 0;
+    bool spill_dirty = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+}  // namespace mica
+
+struct mica_index {
+    int device = 0;
+    mica_index_params params{};
+    mica::IndexView view{};
+    uint64_t n = 0;
+    uint64_t n_occ_blocks = 0, n_mark_blocks = 0, n_samples = 0, table_len = 0;
+    mica::DevBuf occ, marks, samples, table, variants;
+    mica::Workspace ws;
+    mica_stats stats{};
+};
+
+namespace mica {
+
+#define MICA_CUDA_TRY(call)                                   \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) {                              \
+            mica::set_last_cuda_error(e_, #call, __FILE__, __LINE__); \
+            return e_ == cudaErrorMemoryAllocation ? MICA_ENOMEM : MICA_ECUDA; \
+        }                                                     \
+    } while (0)
+
+void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
+// index_build.cu
+int build_suffix_array(const uint8_t *d_codes, uint64_t n, uint32_t *d_sa, cudaStream_t s);
+int build_index_from_codes(const uint8_t *d_codes, uint64_t n, const mica_index_params &p,
+                           mica_index *idx, cudaStream_t s);
+int upload_variants(mica_index *idx);
+void host_variant_table(uint32_t *out);   // N_VARIANTS entries
+uint32_t variant_count(uint32_t q, uint32_t k);
+
+// search.cu
+struct SearchConfig {
+    int kernel;                 // MICA_KERNEL_*
+    int block_threads;          // persistent: threads per block
+    int blocks_per_sm;
+    int plain_block;
+    uint32_t plain_budget;      // plain: node expansions per task before re-queueing
+};
+int run_search(mica_index *idx, const ReadsView &rd, const SearchConfig &cfg, cudaStream_t s);
+
+// post.cu
+int run_post(mica_index *idx, const ReadsView &rd, uint32_t hit_cap, cudaStream_t s,
+             uint64_t *n_hits_out);
+int debug_occ(const mica_index *idx, const uint64_t *d_rows, uint64_t n, uint32_t *d_out, cudaStream_t s);
+int debug_locate(const mica_index *idx, const uint64_t *d_rows, uint64_t n, uint32_t *d_out, cudaStream_t s);
+
+}  // namespace mica

@@ -1,0 +1,419 @@
+// From leaf SA intervals to per-read hit lists:
+//   1. group the intervals by read (prefix sum of per-read counts + scatter);
+//   2. per read: order the intervals by (d, strand, first row), total = sum of
+//      interval sizes (exact), keep = min(total, cap) rows in that order;
+//   3. prefix sum of keep -> CSR offsets; expand the kept rows;
+//   4. resolve each row to a text position by LF walks to the nearest marked
+//      row (SA[j] % s == 0), whose SA value is stored:
+//          SA[j] = SA[LF^t(j)] + t,   LF(j) = C[BWT[j]] + Occ(BWT[j], j);
+//   5. sort each read's hits by (position, strand).
+#include <algorithm>
+#include <vector>
+
+#include "search_common.cuh"
+
+namespace mica {
+
+namespace {
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+constexpr uint32_t SMALL_SORT = 32;
+constexpr uint32_t SMEM_SORT = 4096;
+
+// ---- exclusive scan (n values -> n + 1 offsets) ----
+
+template <typename T>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const T *__restrict__ in, uint64_t n,
+                                                             uint64_t *__restrict__ out,
+                                                             uint64_t *__restrict__ tile_sums)
+{
+    __shared__ uint64_t warp_sums[SCAN_THREADS / 32];
+    uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    uint64_t v[SCAN_ITEMS];
+    uint64_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; j++) {
+        v[j] = (base + j < n) ? (uint64_t)in[base + j] : 0ull;
+        sum += v[j];
+    }
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    uint64_t woff = 0, total = 0;
+    for (int w = 0; w < SCAN_THREADS / 32; w++) {
+        if (w < warp) woff += warp_sums[w];
+        total += warp_sums[w];
+    }
+    uint64_t run = woff + incl - sum;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; j++) {
+        if (base + j < n) out[base + j] = run;
+        run += v[j];
+    }
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+// one block: exclusive scan of the tile sums, grand total at [ntiles]
+__global__ void __launch_bounds__(1024) k_scan_sums(uint64_t *__restrict__ s, uint64_t ntiles)
+{
+    __shared__ uint64_t warp_sums[32];
+    __shared__ uint64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint64_t b0 = 0; b0 < ntiles; b0 += 1024) {
+        uint64_t i = b0 + threadIdx.x;
+        uint64_t x = i < ntiles ? s[i] : 0;
+        uint64_t incl = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) warp_sums[warp] = incl;
+        __syncthreads();
+        uint64_t woff = 0, tot = 0;
+        for (int w = 0; w < 32; w++) {
+            if (w < warp) woff += warp_sums[w];
+            tot += warp_sums[w];
+        }
+        uint64_t c = carry;
+        if (i < ntiles) s[i] = c + woff + incl - x;
+        __syncthreads();
+        if (threadIdx.x == 0) carry = c + tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) s[ntiles] = carry;
+}
+
+__global__ void k_scan_add(uint64_t *__restrict__ out, uint64_t n, const uint64_t *__restrict__ tile_sums)
+{
+    uint64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] += tile_sums[i / SCAN_TILE];
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = tile_sums[ntiles];
+}
+
+template <typename T>
+int exclusive_scan(DevBuf &tmp, const T *in, uint64_t n, uint64_t *out, cudaStream_t s)
+{
+    uint64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (int rc = dev_reserve(tmp, (ntiles + 1) * 8)) return rc;
+    uint64_t *ts = (uint64_t *)tmp.p;
+    if (ntiles) k_scan_tiles<T><<<(unsigned)ntiles, SCAN_THREADS, 0, s>>>(in, n, out, ts);
+    k_scan_sums<<<1, 1024, 0, s>>>(ts, ntiles);
+    unsigned g = (unsigned)std::min<uint64_t>(std::max<uint64_t>((n + 255) / 256, 1), 152 * 32);
+    k_scan_add<<<g, 256, 0, s>>>(out, n, ts);
+    MICA_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+// ---- intervals grouped by read ----
+
+__global__ void k_iv_scatter(const Interval *__restrict__ iv, uint32_t count,
+                             const uint64_t *__restrict__ iv_off, uint32_t *__restrict__ cursor,
+                             Interval *__restrict__ out)
+{
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
+        Interval x = iv[e];
+        uint32_t at = atomicSub(&cursor[x.read], 1u) - 1u;
+        out[iv_off[x.read] + at] = x;
+    }
+}
+
+__device__ __forceinline__ uint64_t iv_key(const Interval &x)
+{
+    return ((uint64_t)(x.meta & 3u) << 33) | ((uint64_t)((x.meta >> 2) & 1u) << 32) | x.l;
+}
+
+__global__ void k_summarize(Interval *__restrict__ ivs, const uint64_t *__restrict__ iv_off, uint64_t n,
+                            uint32_t cap, uint64_t *__restrict__ total, uint64_t *__restrict__ keep)
+{
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n;
+         r += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t b = iv_off[r], e = iv_off[r + 1];
+        uint64_t t = 0;
+        for (uint64_t i = b; i < e; i++) {
+            Interval x = ivs[i];
+            uint64_t kx = iv_key(x);
+            uint64_t j = i;
+            while (j > b && iv_key(ivs[j - 1]) > kx) { ivs[j] = ivs[j - 1]; j--; }
+            ivs[j] = x;
+            t += x.r - x.l;
+        }
+        total[r] = t;
+        keep[r] = (cap && t > cap) ? cap : t;
+    }
+}
+
+__global__ void k_expand(const Interval *__restrict__ ivs, const uint64_t *__restrict__ iv_off,
+                         const uint64_t *__restrict__ hit_off, uint64_t n, Hit *__restrict__ hits)
+{
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n;
+         r += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t q = hit_off[r], qe = hit_off[r + 1];
+        for (uint64_t i = iv_off[r]; i < iv_off[r + 1] && q < qe; i++) {
+            Interval x = ivs[i];
+            for (uint32_t row = x.l; row < x.r && q < qe; row++, q++) {
+                Hit h;
+                h.pos = row;   // resolved to a position by k_locate
+                h.strand = (uint8_t)((x.meta >> 2) & 1u);
+                h.mm = (uint8_t)(x.meta & 3u);
+                h.pad = 0;
+                hits[q] = h;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+// ---- locate: SA[j] by LF walks to a marked row ----
+
+__device__ __forceinline__ uint32_t locate_row(const IndexView &ix, uint32_t j, uint32_t &steps)
+{
+    uint32_t t = 0;
+    for (;;) {
+        uint32_t mb = j / MARK_ROWS, mo = j - mb * MARK_ROWS;
+        const uint4 *mp = ix.marks + (size_t)mb * 4;
+        uint4 q0 = __ldg(mp), q1 = __ldg(mp + 1), q2 = __ldg(mp + 2), q3 = __ldg(mp + 3);
+        uint32_t w[16] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w,
+                          q2.x, q2.y, q2.z, q2.w, q3.x, q3.y, q3.z, q3.w};
+        uint32_t wi = mo >> 5, bi = mo & 31;
+        uint32_t word = 0, before = 0;
+#pragma unroll
+        for (int x = 0; x < 15; x++) {
+            if ((uint32_t)x < wi) before += __popc(w[1 + x]);
+            if ((uint32_t)x == wi) word = w[1 + x];
+        }
+        if ((word >> bi) & 1u) {
+            uint32_t rank = w[0] + before + __popc(word & ((1u << bi) - 1u));
+            steps += t;
+            return __ldg(ix.samples + rank) + t;
+        }
+        // LF step: c = BWT[j] (never $: the $ row has SA = 0, which is marked)
+        uint32_t b = j / OCC_ROWS, o = j - b * OCC_ROWS;
+        const uint4 *blk = ix.occ + (size_t)b * 4;
+        uint4 h = __ldg(blk);
+        uint32_t a[12];
+        load_block_words(blk, o + 1, a);
+        uint32_t c = 0;
+#pragma unroll
+        for (int x = 0; x < 12; x++)
+            if ((uint32_t)x == (o >> 4)) c = (a[x] >> (2 * (o & 15))) & 3u;
+        uint32_t occ[4];
+        occ_from(ix, b, o, h, a, occ);
+        uint32_t oc = c == 0 ? occ[0] : c == 1 ? occ[1] : c == 2 ? occ[2] : occ[3];
+        uint32_t Cc = c == 0 ? ix.C[0] : c == 1 ? ix.C[1] : c == 2 ? ix.C[2] : ix.C[3];
+        j = Cc + oc;
+        t++;
+    }
+}
+
+namespace {
+
+__global__ void k_locate(const IndexView ix, Hit *__restrict__ hits, uint64_t nh,
+                         unsigned long long *__restrict__ steps_out)
+{
+    uint32_t steps = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nh;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        hits[i].pos = locate_row(ix, hits[i].pos, steps);
+    }
+    unsigned mask = __activemask();
+    unsigned s = __reduce_add_sync(mask, steps);
+    if ((threadIdx.x & 31) == (unsigned)(__ffs(mask) - 1) && s) atomicAdd(steps_out, (unsigned long long)s);
+}
+
+__device__ __forceinline__ uint64_t hit_key(uint64_t raw)
+{
+    return ((raw & 0xffffffffull) << 1) | ((raw >> 32) & 1ull);   // (pos, strand)
+}
+
+__global__ void k_sort_small(uint64_t *__restrict__ hits, const uint64_t *__restrict__ hit_off, uint64_t n,
+                             uint32_t *__restrict__ big, unsigned int *__restrict__ nbig)
+{
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n;
+         r += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t b = hit_off[r], e = hit_off[r + 1];
+        if (e - b <= 1) continue;
+        if (e - b > SMALL_SORT) {
+            big[atomicAdd(nbig, 1u)] = (uint32_t)r;
+            continue;
+        }
+        for (uint64_t i = b + 1; i < e; i++) {
+            uint64_t x = hits[i], kx = hit_key(x);
+            uint64_t j = i;
+            while (j > b && hit_key(hits[j - 1]) > kx) { hits[j] = hits[j - 1]; j--; }
+            hits[j] = x;
+        }
+    }
+}
+
+// bitonic sort of one read's hits in shared memory (<= SMEM_SORT)
+__global__ void __launch_bounds__(512) k_sort_big(uint64_t *__restrict__ hits, const uint64_t *__restrict__ hit_off,
+                                                  const uint32_t *__restrict__ big, unsigned int nbig)
+{
+    __shared__ uint64_t sh[SMEM_SORT];
+    for (unsigned bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
+        uint32_t r = big[bi];
+        uint64_t b = hit_off[r], cnt = hit_off[r + 1] - b;
+        if (cnt > SMEM_SORT) continue;   // handled by k_sort_global
+        uint32_t P = 1;
+        while (P < cnt) P <<= 1;
+        for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) sh[i] = i < cnt ? hits[b + i] : ~0ull;
+        __syncthreads();
+        for (uint32_t kk = 2; kk <= P; kk <<= 1)
+            for (uint32_t jj = kk >> 1; jj > 0; jj >>= 1) {
+                for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+                    uint32_t p = i ^ jj;
+                    if (p > i) {
+                        uint64_t x = sh[i], y = sh[p];
+                        bool up = (i & kk) == 0;
+                        uint64_t kx = x == ~0ull ? ~0ull : hit_key(x), ky = y == ~0ull ? ~0ull : hit_key(y);
+                        if ((kx > ky) == up) { sh[i] = y; sh[p] = x; }
+                    }
+                }
+                __syncthreads();
+            }
+        for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) hits[b + i] = sh[i];
+        __syncthreads();
+    }
+}
+
+// one read with more than SMEM_SORT hits: bitonic network over a global scratch
+__global__ void __launch_bounds__(1024) k_sort_global(uint64_t *__restrict__ hits, uint64_t cnt,
+                                                      uint64_t *__restrict__ scratch, uint64_t P)
+{
+    for (uint64_t i = threadIdx.x; i < P; i += blockDim.x) scratch[i] = i < cnt ? hits[i] : ~0ull;
+    __syncthreads();
+    for (uint64_t kk = 2; kk <= P; kk <<= 1)
+        for (uint64_t jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (uint64_t i = threadIdx.x; i < P; i += blockDim.x) {
+                uint64_t p = i ^ jj;
+                if (p > i) {
+                    uint64_t x = scratch[i], y = scratch[p];
+                    bool up = (i & kk) == 0;
+                    uint64_t kx = x == ~0ull ? ~0ull : hit_key(x), ky = y == ~0ull ? ~0ull : hit_key(y);
+                    if ((kx > ky) == up) { scratch[i] = y; scratch[p] = x; }
+                }
+            }
+            __syncthreads();
+        }
+    for (uint64_t i = threadIdx.x; i < cnt; i += blockDim.x) hits[i] = scratch[i];
+}
+
+__global__ void k_debug_occ(const IndexView ix, const uint64_t *__restrict__ rows, uint64_t n,
+                            uint32_t *__restrict__ out)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t j = (uint32_t)rows[i];
+        uint32_t ol[4], orr[4];
+        occ_pair(ix, j, j, ol, orr);
+        for (int c = 0; c < 4; c++) out[4 * i + c] = ol[c];
+    }
+}
+
+__global__ void k_debug_locate(const IndexView ix, const uint64_t *__restrict__ rows, uint64_t n,
+                               uint32_t *__restrict__ out)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t steps = 0;
+        out[i] = locate_row(ix, (uint32_t)rows[i], steps);
+    }
+}
+
+unsigned grid1(uint64_t n, int block = 256)
+{
+    return (unsigned)std::min<uint64_t>(std::max<uint64_t>((n + block - 1) / block, 1), 152ull * 64);
+}
+
+}  // namespace
+
+int run_post(mica_index *idx, const ReadsView &rd, uint32_t hit_cap, cudaStream_t s, uint64_t *n_hits_out)
+{
+    Workspace &w = idx->ws;
+    uint64_t n = rd.n;
+    uint32_t niv = (uint32_t)idx->stats.intervals;
+    int rc;
+    if ((rc = dev_reserve(w.iv_sorted, std::max<uint64_t>(niv, 1) * sizeof(Interval))) ||
+        (rc = dev_reserve(w.iv_off, (n + 1) * 8)) || (rc = dev_reserve(w.total, std::max<uint64_t>(n, 1) * 8)) ||
+        (rc = dev_reserve(w.keep, std::max<uint64_t>(n, 1) * 8)) || (rc = dev_reserve(w.hit_off, (n + 1) * 8)) ||
+        (rc = dev_reserve(w.big, std::max<uint64_t>(n, 1) * 4 + 64)))
+        return rc;
+    uint64_t *iv_off = (uint64_t *)w.iv_off.p, *hit_off = (uint64_t *)w.hit_off.p;
+    if ((rc = exclusive_scan<uint32_t>(w.scan_tmp, (const uint32_t *)w.iv_cnt.p, n, iv_off, s))) return rc;
+    if (niv) k_iv_scatter<<<grid1(niv), 256, 0, s>>>((const Interval *)w.iv.p, niv, iv_off,
+                                                     (uint32_t *)w.iv_cnt.p, (Interval *)w.iv_sorted.p);
+    if (n) k_summarize<<<grid1(n, 128), 128, 0, s>>>((Interval *)w.iv_sorted.p, iv_off, n, hit_cap,
+                                                    (uint64_t *)w.total.p, (uint64_t *)w.keep.p);
+    if ((rc = exclusive_scan<uint64_t>(w.scan_tmp, (const uint64_t *)w.keep.p, n, hit_off, s))) return rc;
+    uint64_t nh = 0;
+    MICA_CUDA_TRY(cudaMemcpyAsync(&nh, hit_off + n, 8, cudaMemcpyDeviceToHost, s));
+    MICA_CUDA_TRY(cudaStreamSynchronize(s));
+    if ((rc = dev_reserve(w.hits, std::max<uint64_t>(nh, 1) * sizeof(Hit) + 64))) return rc;
+    unsigned long long *steps = (unsigned long long *)((char *)w.big.p + std::max<uint64_t>(n, 1) * 4);
+    unsigned int *nbig = (unsigned int *)(steps + 1);
+    MICA_CUDA_TRY(cudaMemsetAsync(steps, 0, 16, s));
+    if (n) k_expand<<<grid1(n, 128), 128, 0, s>>>((const Interval *)w.iv_sorted.p, iv_off, hit_off, n,
+                                                 (Hit *)w.hits.p);
+    if (nh) k_locate<<<grid1(nh), 256, 0, s>>>(idx->view, (Hit *)w.hits.p, nh, steps);
+    if (n) k_sort_small<<<grid1(n, 128), 128, 0, s>>>((uint64_t *)w.hits.p, hit_off, n, (uint32_t *)w.big.p, nbig);
+    unsigned int hb[4] = {0, 0, 0, 0};
+    unsigned long long st = 0;
+    MICA_CUDA_TRY(cudaMemcpyAsync(&st, steps, 8, cudaMemcpyDeviceToHost, s));
+    MICA_CUDA_TRY(cudaMemcpyAsync(hb, nbig, 4, cudaMemcpyDeviceToHost, s));
+    MICA_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hb[0]) {
+        k_sort_big<<<std::min(hb[0], 152u * 4), 512, 0, s>>>((uint64_t *)w.hits.p, hit_off,
+                                                           (const uint32_t *)w.big.p, hb[0]);
+        // reads above the shared-memory size: one global bitonic sort each
+        std::vector<uint32_t> bigr(hb[0]);
+        MICA_CUDA_TRY(cudaMemcpyAsync(bigr.data(), w.big.p, 4ull * hb[0], cudaMemcpyDeviceToHost, s));
+        MICA_CUDA_TRY(cudaStreamSynchronize(s));
+        for (uint32_t r : bigr) {
+            uint64_t ob[2];
+            MICA_CUDA_TRY(cudaMemcpy(ob, hit_off + r, 16, cudaMemcpyDeviceToHost));
+            uint64_t cnt = ob[1] - ob[0];
+            if (cnt <= SMEM_SORT) continue;
+            uint64_t P = 1;
+            while (P < cnt) P <<= 1;
+            DevBuf scratch;
+            if ((rc = dev_reserve(scratch, P * 8))) return rc;
+            k_sort_global<<<1, 1024, 0, s>>>((uint64_t *)w.hits.p + ob[0], cnt, (uint64_t *)scratch.p, P);
+            MICA_CUDA_TRY(cudaStreamSynchronize(s));
+            dev_release(scratch);
+        }
+    }
+    MICA_CUDA_TRY(cudaGetLastError());
+    idx->stats.located = nh;
+    idx->stats.lf_steps = st;
+    *n_hits_out = nh;
+    return 0;
+}
+
+int debug_occ(const mica_index *idx, const uint64_t *d_rows, uint64_t n, uint32_t *d_out, cudaStream_t s)
+{
+    if (n) k_debug_occ<<<grid1(n), 256, 0, s>>>(idx->view, d_rows, n, d_out);
+    MICA_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+int debug_locate(const mica_index *idx, const uint64_t *d_rows, uint64_t n, uint32_t *d_out, cudaStream_t s)
+{
+    if (n) k_debug_locate<<<grid1(n), 256, 0, s>>>(idx->view, d_rows, n, d_out);
+    MICA_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+}  // namespace mica

@@ -1,0 +1,181 @@
+"""GPU k-mismatch search against the oracle, both kernels, bit-exact:
+totals, CSR offsets and every (position, strand, mismatches)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import golden_cases, refcheck
+from tests import gpu_common as gc
+
+pytestmark = pytest.mark.gpu
+KERNELS = ["persistent", "plain"]
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_handworked(kernel):
+    m = gc.mica()
+    for case in golden_cases.cases():
+        g = golden_cases.codes(case["genome"])
+        idx = m.Index.build(case["genome"].encode(), kmer_q=2, sa_sample=2)
+        b = golden_cases.batch_of(case["read"], case["k"])
+        res = idx.align_batch(b, hit_cap=case["cap"], kernel=kernel)
+        assert int(res.total[0]) == case["total"], case
+        assert res.hits_of(0) == case["hits"], case
+        idx.free()
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("q", [5, 10, 12])
+def test_slice_against_bruteforce(kernel, q):
+    g, b = synth.slice_10k(gc.genome("1m"))
+    idx = gc.mica().Index.build(synth.to_acgt_bytes(g.codes), kmer_q=q, sa_sample=8)
+    for k in range(4):
+        b.k[:] = k
+        bf = oracle.bruteforce(g.codes, b)
+        got = idx.align_batch(b, hit_cap=0, kernel=kernel)
+        gc.assert_same(got, bf, f"k={k}")
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_random_1m_10k_reads(kernel):
+    g = gc.genome("1m")
+    b = synth.reads_1m(g)
+    want = gc.oracle_index("1m").align(b, cap=0)
+    got = gc.gpu_index("1m").align_batch(b, hit_cap=0, kernel=kernel)
+    gc.assert_same(got, want)
+    # the closed form: every read hits exactly its origin
+    assert np.array_equal(got.total, np.ones(b.n, np.uint64))
+    assert np.array_equal(got.hits["pos"], b.origin.astype(np.uint32))
+
+
+def _edge_batch(g, rng):
+    n = g.size
+    reads, ks = [], []
+    for m in [1, 2, 3, 11, 12, 13, 15, 16, 17, 31, 32, 33, 63, 64, 65, 100, 150, 250, 255, 256]:
+        for k in range(4):
+            p = int(rng.integers(0, n - m + 1))
+            r = g[p:p + m].copy()
+            if rng.random() < 0.5:
+                r = refcheck.rc(r)
+            for q in rng.choice(m, size=min(m, k), replace=False):
+                r[q] = (r[q] + rng.integers(1, 4)) & 3
+            reads.append(r)
+            ks.append(k)
+    # palindromes (read == its reverse complement)
+    for half in (2, 5, 8):
+        h = rng.integers(0, 4, half).astype(np.uint8)
+        reads.append(np.concatenate([h, refcheck.rc(h)]))
+        ks.append(1)
+    return gc.batch_from_reads(reads, ks)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_edge_lengths_and_budgets(kernel):
+    rng = np.random.default_rng(21)
+    g = synth.repeat_genome(30_000, 3, copy_frac=0.2, copy_len=(300, 2000), tandem_frac=0.1,
+                            array_len=(100, 1500)).codes
+    b = _edge_batch(g, rng)
+    fm = oracle.FMIndex(g)
+    for q, cap in ((12, 0), (8, 3), (4, 40)):
+        idx = gc.mica().Index.build(synth.to_acgt_bytes(g), kmer_q=q, sa_sample=4)
+        got = idx.align_batch(b, hit_cap=cap, kernel=kernel)
+        gc.assert_same(got, fm.align(b, cap=cap), f"q={q} cap={cap}")
+        idx.free()
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_whole_genome_read(kernel):
+    g = np.random.default_rng(4).integers(0, 4, 256).astype(np.uint8)
+    reads = [g.copy(), refcheck.rc(g)]
+    b = gc.batch_from_reads(reads, [3, 0])
+    idx = gc.mica().Index.build(synth.to_acgt_bytes(g), kmer_q=12, sa_sample=16)
+    got = idx.align_batch(b, hit_cap=0, kernel=kernel)
+    gc.assert_same(got, oracle.FMIndex(g).align(b))
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_many_hits_sort_paths(kernel):
+    """Reads in tandem arrays: more than 32 hits (block sort) and, uncapped,
+    more than 4096 hits (global sort)."""
+    g = np.resize(np.array([0, 3, 3], np.uint8), 30_000)       # (ATT)^n
+    g[::997] = 2
+    fm = oracle.FMIndex(g)
+    reads = [g[100:130].copy(), g[5:25].copy(), refcheck.rc(g[40:70])]
+    b = gc.batch_from_reads(reads, [0, 1, 2])
+    idx = gc.mica().Index.build(synth.to_acgt_bytes(g), kmer_q=12, sa_sample=16)
+    for cap in (0, 100, 1000, 5000):
+        got = idx.align_batch(b, hit_cap=cap, kernel=kernel)
+        gc.assert_same(got, fm.align(b, cap=cap), f"cap={cap}")
+    assert int(got.total.max()) > 4096
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_empty_batch(kernel):
+    idx = gc.gpu_index("1m")
+    b = gc.batch_from_reads([], [])
+    res = idx.align(np.zeros(0, np.uint32), np.zeros(1, np.uint64), np.zeros(0, np.uint16),
+                    np.zeros(0, np.uint8), kernel=kernel)
+    assert res.total.size == 0 and res.hits.size == 0 and list(res.offsets) == [0]
+
+
+def test_rejects_invalid_reads():
+    m = gc.mica()
+    idx = gc.gpu_index("1m")
+    for m_len, k in ((0, 0), (257, 0), (10, 4)):
+        words = np.zeros(32, np.uint32)
+        off = np.array([0, 17], np.uint64)
+        with pytest.raises(m.MicaError) as e:
+            idx.align(words, off, np.array([m_len], np.uint16), np.array([k], np.uint8))
+        assert e.value.code == m.MICA_EINVAL
+    # word offsets pointing past the packed words
+    with pytest.raises(m.MicaError):
+        idx.align(np.zeros(2, np.uint32), np.array([0, 2], np.uint64), np.array([100], np.uint16),
+                  np.array([1], np.uint8))
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_repeats_64m_sample(kernel):
+    g = gc.genome("64m")
+    b = synth.reads_64m(g, n=1_000_000).subset(np.arange(0, 1_000_000, 250))   # 4,000 reads
+    want = gc.oracle_index("64m").align(b, cap=1000)
+    got = gc.gpu_index("64m").align_batch(b, hit_cap=1000, kernel=kernel)
+    gc.assert_same(got, want)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_uneven_64m_sample(kernel):
+    g = gc.genome("64m")
+    full = synth.reads_uneven(g, n=200_000)
+    b = full.subset(np.arange(0, full.n, 100))                                     # 2,000 reads
+    want = gc.oracle_index("64m").align(b, cap=1000)
+    got = gc.gpu_index("64m").align_batch(b, hit_cap=1000, kernel=kernel)
+    gc.assert_same(got, want)
+
+
+def test_full_1m_reads_64m():
+    """Full 1M x 150 bp batch on the 64 Mbp repeat genome in the launch shape
+    the benchmark times: both kernels agree exactly; 2,000 sampled reads equal
+    the oracle; every hit's mismatch count is recomputed from the genome."""
+    g = gc.genome("64m")
+    b = synth.reads_64m(g)
+    idx = gc.gpu_index("64m")
+    a = idx.align_batch(b, hit_cap=1000, kernel="persistent")
+    p = idx.align_batch(b, hit_cap=1000, kernel="plain")
+    gc.assert_same(a, p, "persistent vs plain")
+    rng = np.random.default_rng(99)
+    sample = np.sort(rng.choice(b.n, 2000, replace=False))
+    want = gc.oracle_index("64m").align(b.subset(sample), cap=1000)
+    for j, i in enumerate(sample):
+        assert a.hits_of(int(i)) == want.as_tuples(j)
+        assert int(a.total[i]) == int(want.total[j])
+    # invariants on every read
+    cnt = np.diff(a.offsets.astype(np.int64))
+    assert np.all(cnt == np.minimum(a.total.astype(np.int64), 1000))
+    assert np.all(a.hits["mm"] <= 2)
+    assert np.all(a.hits["pos"].astype(np.int64) <= g.n - 150)
+    for i in rng.choice(b.n, 300, replace=False):
+        r = b.read(int(i))
+        for pos, s, d in a.hits_of(int(i)):
+            w = g.codes[pos:pos + 150]
+            assert int(((refcheck.rc(r) if s else r) != w).sum()) == d
