@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark of the k-mismatch FM-index search (the BWT phase of MICA, Section 2).
+
+Workload: the 64 Mbp synthetic repeat genome (i.i.d. base, 5% copies of
+1-10 kbp at 1% divergence, 1% tandem arrays) and 1,000,000 reads of 150 bp
+with 1% substitution error, k <= 2 on both strands, at most 1000 listed hits
+per read (exact totals).  One step = one batch of 1M reads through the whole
+path (seed lookups, backtracking, counting and capping, LF-walk location,
+per-read sort) with the reads already in HBM; the index is built once.
+
+  python bench.py [--gpus N --steps K --warmup W]       our CUDA path (N replicas)
+  python bench.py --impl reference [...]                the CPU oracle, timed
+
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "150bp reads/s aligned (k<=2 FM search) batched vs plain kernel; p99 latency"
+WORKLOAD = "64 Mbp repeat genome, 1M x 150 bp reads (1% substitutions), k<=2 both strands, cap 1000"
+HIT_CAP = 1000
+L2_FLUSH_BYTES = 512 << 20
+PROFILE = os.path.join(ROOT, "profiles", "k_persistent_64m_1m150.txt")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--reads", type=int, default=1_000_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def cpu_info():
+    model = ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    if not model:
+        try:
+            model = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+            model = next((l.split(":", 1)[1].strip() for l in model.splitlines() if "Model name" in l), "")
+        except Exception:
+            model = ""
+    return os.cpu_count() or 1, model
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = os.path.join("/tmp", f"mica_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                      "sw_power_cap"), f[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def profile_traffic(kernel_src: str):
+    """dram bytes per launch of the search kernel from the committed ncu
+    summary, or None when the kernel source changed since the capture."""
+    try:
+        vals = {}
+        for line in open(PROFILE):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+        sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+        if vals.get("search_cu_sha256_16") != sha:
+            return None
+        return float(vals["dram_bytes_per_launch_scaled"])
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def make_workload(n_reads: int, rank: int):
+    g = synth.genome_64m()
+    reads = synth.reads_64m(g, n=n_reads, seed=synth.SEED_READS_64M + rank)
+    return g, reads
+
+
+def run_ours(args):
+    import torch
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    import paper_1402_4876_gb300 as mica
+
+    g, b = make_workload(args.reads, rank)
+    t0 = time.perf_counter()
+    idx = mica.Index.build(synth.to_acgt_bytes(g.codes), kmer_q=12, sa_sample=16, device=local)
+    build_s = time.perf_counter() - t0
+
+    dev = torch.device("cuda", local)
+    d_words = torch.from_numpy(b.words.view(np.int32)).to(dev)
+    d_off = torch.from_numpy(b.word_off.view(np.int64)).to(dev)
+    d_len = torch.from_numpy(b.lengths.view(np.int16)).to(dev)
+    d_k = torch.from_numpy(b.k).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def device_steps(kernel: str, steps: int, warmup: int):
+        for _ in range(warmup):
+            idx.align_device(d_words, d_off, d_len, d_k, b.n, hit_cap=HIT_CAP, kernel=kernel, stream=stream)
+        ms, kms, stats = [], [], []
+        barrier()
+        torch.cuda.synchronize(dev)
+        for _ in range(steps):
+            flush.fill_(rank + len(ms))                      # evict L2 between timed steps
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = idx.align_device(d_words, d_off, d_len, d_k, b.n, hit_cap=HIT_CAP, kernel=kernel,
+                                 stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            st = idx.stats()
+            kms.append(st["kernel_ms"])
+            stats.append(st)
+        torch.cuda.synchronize(dev)
+        barrier()
+        return ms, kms, stats, r
+
+    with ClockSampler(local) as clk:
+        ms, kms, stats, dres = device_steps("persistent", args.steps, args.warmup)
+    clocks = clk.summary()
+    total_ms = max_over_ranks(sum(ms))
+    value = world * b.n * args.steps / (total_ms / 1e3)
+    n_hits = dres.n_hits
+
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": "reads/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (seeded generator; the paper's YH/1000 Genomes data are not available)",
+        "config": {"workload": WORKLOAD, "genome_bp": g.n, "reads_per_gpu": b.n, "read_len": 150, "k": 2,
+                   "hit_cap": HIT_CAP, "kernel": "persistent warp-pool", "index": "q=12 table, 64 B occ blocks, SA 1/16",
+                   "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                   "parallelism": f"replicas x{world} (index per GPU, reads sharded, no collective)"},
+        "latency_ms": {"p50": round(float(np.percentile(ms, 50)), 3), "p99": round(float(np.percentile(ms, 99)), 3),
+                       "what": "per-batch (1M reads) device latency over the timed steps"},
+        "index_build_s": round(build_s, 3),
+        "hits_per_step": int(n_hits),
+    }
+    st = stats[-1]
+    out["work_per_step"] = {k: int(st[k]) for k in ("seeds", "nodes", "rank_blocks", "intervals", "located",
+                                                    "lf_steps", "spills")}
+    out["gpu_launches"] = int(sum(s["launches"] for s in stats))
+
+    # roofline of the dominant kernel (the persistent search)
+    peaks, src = measured_peaks()
+    kernel_s = statistics.mean(kms) / 1e3
+    read_bytes = 2 * 4 * int(np.sum((b.lengths.astype(np.int64) + 15) // 16))
+    alg_bytes = 64 * st["rank_blocks"] + 8 * st["seeds"] + read_bytes + 16 * st["intervals"]
+    achieved = alg_bytes / kernel_s / 1e9
+    traffic = profile_traffic(os.path.join(ROOT, "paper_1402_4876_gb300", "csrc", "search.cu"))
+    out["roofline"] = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                       "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
+                       "kernel": "k_persistent", "kernel_ms": round(kernel_s * 1e3, 3),
+                       "alg_bytes_per_launch": int(alg_bytes),
+                       "peak_source": f"{src} hbm_gbs (copy bandwidth)"}
+    out["clocks"] = clocks
+
+    if not args.no_plain:
+        pms, pkms, pstats, _ = device_steps("plain", max(1, min(args.steps, 3)), 1)
+        ptotal = max_over_ranks(sum(pms))
+        pval = world * b.n * len(pms) / (ptotal / 1e3)
+        out["plain"] = {"value": round(pval, 1), "unit": "reads/s", "ms_per_step": round(ptotal / len(pms), 3),
+                        "kernel_ms": round(statistics.mean(pkms), 3),
+                        "persistent_over_plain": round(value / pval, 3)}
+
+    if not args.no_e2e:
+        # end to end through the public host-buffer call: pinned inputs in, hits out
+        pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+        hw, ho, hl, hk = pin(b.words), pin(b.word_off), pin(b.lengths), pin(b.k)
+        idx.align(hw, ho, hl, hk, hit_cap=HIT_CAP, stream=stream)
+        barrier()
+        t = time.perf_counter()
+        e2e_steps = max(1, min(args.steps, 3))
+        for _ in range(e2e_steps):
+            res = idx.align(hw, ho, hl, hk, hit_cap=HIT_CAP, stream=stream)
+        torch.cuda.synchronize(dev)
+        el = max_over_ranks(time.perf_counter() - t)
+        h2d = hw.nbytes + ho.nbytes + hl.nbytes + hk.nbytes
+        d2h = res.total.nbytes + res.offsets.nbytes + res.hits.nbytes
+        out["e2e"] = {"value": round(world * b.n * e2e_steps / el, 1), "unit": "reads/s",
+                      "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                      "api": "mica_align_batch (host buffers)"}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(g, b)
+
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def cpu_baseline(g, b, stride: int = 20):
+    import oracle
+    cores, model = cpu_info()
+    fm = oracle.FMIndex(g.codes, "sais")                 # index build: not timed
+    sub = b.subset(np.arange(0, b.n, stride))
+    t = time.perf_counter()
+    fm.align(sub, cap=HIT_CAP, threads=cores)
+    dt = time.perf_counter() - t
+    return {"value": round(sub.n / dt, 1), "unit": "reads/s", "cores": cores, "kind": "oracle",
+            "sample": f"{sub.n} of the {b.n} reads (every {stride}th), same genome; oracle index build "
+                      f"(SA-IS) excluded; {dt:.1f} s wall", "cpu": model}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    cores, model = cpu_info()
+    g, b = make_workload(args.reads, 0)
+    fm = oracle.FMIndex(g.codes, "sais")
+    stride = 50
+    sub = b.subset(np.arange(0, b.n, stride))
+    for _ in range(args.warmup):
+        fm.align(sub.subset(np.arange(min(sub.n, 2000))), cap=HIT_CAP, threads=cores)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        fm.align(sub, cap=HIT_CAP, threads=cores)
+        times.append(time.perf_counter() - t)
+    value = sub.n / statistics.mean(times)
+    sample = (f"each step: {sub.n} of the {b.n} reads (every {stride}th); oracle index build excluded; "
+              f"warm-up steps on 2,000 reads")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "reads/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.mean(times), 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "genome_bp": g.n, "reads": b.n, "hit_cap": HIT_CAP},
+        "cpu_baseline": {"value": round(value, 1), "unit": "reads/s", "cores": cores, "kind": "oracle",
+                         "sample": sample, "cpu": model},
+        "e2e": {"value": round(value, 1), "unit": "reads/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -110,7 +110,11 @@ typedef struct {
     uint64_t spills;         /* work items moved to the device queue (persistent kernel)
                                 or re-queued after the per-thread budget (plain kernel) */
     uint64_t retries;        /* internal buffer-growth retries */
-    float search_ms;         /* device time of the search phase */
+    uint64_t launches;       /* CUDA kernels this library launched for the call */
+    uint64_t warp_rounds;    /* persistent kernel: work-pool rounds over all warps */
+    uint64_t lane_ops;       /* persistent kernel: node extensions + seed lookups done by lanes */
+    float search_ms;         /* device time of the search phase (kernel + its control copies) */
+    float kernel_ms;         /* device time of the search kernel launch(es) alone */
     float total_ms;          /* device time of the whole call */
 } mica_stats;
 
@@ -173,6 +177,64 @@ int mica_align_device(mica_index *idx, const uint32_t *d_packed_reads, const uin
 
 int mica_get_stats(const mica_index *idx, mica_stats *out);
 
+/* ---- serving: continuous batching over a resident index ----
+ *
+ * The paper's host keeps the accelerator busy with batches of about a million
+ * reads while it handles the waiting (Section 2, "Pipelining & load
+ * balancing").  Here a server owns worker threads (each with its own CUDA
+ * stream and workspace) that keep admitting queued requests, FIFO, while the
+ * reads fit the tick size and the requests' device-memory estimates fit the
+ * budget; the admitted requests of one tick share one search launch, so their
+ * work interleaves on the device, and with two or more workers one tick's
+ * search overlaps another's hit assembly and copies.  A request's result is
+ * identical to aligning it alone with mica_align_batch.  The index must stay
+ * alive until mica_server_stop returns; it may still be used by the caller's
+ * own align calls (those use the index's workspace, the server uses its own).
+ */
+typedef struct mica_server mica_server;
+
+typedef struct {
+    uint64_t max_device_bytes;  /* device memory for admitted requests; 0 = half the free memory at start */
+    uint64_t max_tick_reads;    /* reads per search launch (a larger single request runs alone); 0 = 2^20 */
+    uint32_t hit_cap;           /* as mica_align_params.hit_cap, for every request */
+    int32_t kernel;             /* MICA_KERNEL_* */
+    int32_t workers;            /* concurrent ticks, 1..8; 0 = 2 */
+    int32_t start_paused;       /* nonzero: queue requests but admit none until mica_server_resume */
+} mica_server_params;
+
+typedef struct {
+    uint64_t submitted, completed, failed, cancelled;
+    uint64_t ticks;             /* search launches run */
+    uint64_t reads;             /* reads of completed requests */
+    uint64_t pending;           /* queued, not yet admitted */
+    uint64_t device_bytes_in_use, device_budget;
+    double busy_s;              /* summed wall time of ticks over all workers */
+} mica_server_stats;
+
+void mica_server_params_default(mica_server_params *p);
+/* Start the worker threads on idx's device.  params may be NULL (defaults). */
+int mica_server_start(mica_index *idx, const mica_server_params *params, mica_server **out);
+/* Queue a host batch (same layout as mica_align_batch; copied before return).
+   MICA_EINVAL for a bad batch, MICA_ENOMEM if its estimate exceeds the whole
+   budget (it could never be admitted), MICA_EBUSY after stop. */
+int mica_server_submit(mica_server *srv, const uint32_t *packed_reads, const uint64_t *word_offsets,
+                       const uint16_t *lengths, const uint8_t *k, uint64_t n_reads, uint64_t *req_id);
+/* MICA_EBUSY while queued or running.  Once done, returns the request's status
+   and hands *out (a mica_result to free with mica_result_free; NULL if out is
+   NULL or the request failed) and *latency_ms (submit to completion, host
+   clock; may be NULL) to the caller; the id is then forgotten. */
+int mica_server_poll(mica_server *srv, uint64_t req_id, mica_result **out, double *latency_ms);
+/* As poll, waiting up to timeout_ms; MICA_ETIMEOUT if still not done. */
+int mica_server_wait(mica_server *srv, uint64_t req_id, uint32_t timeout_ms, mica_result **out,
+                     double *latency_ms);
+/* Drop a queued request (MICA_EBUSY once a tick has taken it). */
+int mica_server_cancel(mica_server *srv, uint64_t req_id);
+void mica_server_resume(mica_server *srv);
+int mica_server_get_stats(mica_server *srv, mica_server_stats *out);
+/* Finish the ticks in flight, drop queued requests, join the workers, free
+   uncollected results. */
+void mica_server_stop(mica_server *srv);
+
 /* ---- parity probes: each exposes one step of the path on the GPU ---- */
 
 /* Suffix array of G$ (len + 1 entries, host output) built on the GPU by the
@@ -185,8 +247,12 @@ int mica_debug_occ(const mica_index *idx, const uint64_t *rows, uint64_t n, uint
 /* pos_out[i] = SA[rows[i]] resolved by LF walks to the sampled rows (host in/out). */
 int mica_debug_locate(const mica_index *idx, const uint64_t *rows, uint64_t n, uint32_t *pos_out);
 
-/* bounds_out[i] = q-mer table entry codes[i] (host in/out), codes < 4^q + 1. */
-int mica_debug_table(const mica_index *idx, const uint32_t *codes, uint64_t n, uint32_t *bounds_out);
+/* SA interval of each len-mer (len <= kmer_q) given by its code (first base
+   most significant, codes[i] < 4^len), looked up in the q-mer table on the
+   GPU as the search's seed step does: lr_out[2i] = l, lr_out[2i+1] = r
+   (host in/out; l == r when the len-mer does not occur). */
+int mica_debug_seed_interval(const mica_index *idx, const uint32_t *codes, uint32_t len, uint64_t n,
+                             uint32_t *lr_out);
 
 #ifdef __cplusplus
 }

@@ -62,10 +62,23 @@ class _DeviceResult(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_uint64) for name in
                 ("tasks", "seeds", "nodes", "rank_blocks", "intervals", "located", "lf_steps",
-                 "spills", "retries")] + [("search_ms", ctypes.c_float), ("total_ms", ctypes.c_float)]
+                 "spills", "retries", "launches", "warp_rounds", "lane_ops")] + [("search_ms", ctypes.c_float), ("kernel_ms", ctypes.c_float),
+                                                      ("total_ms", ctypes.c_float)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class ServerParams(ctypes.Structure):
+    _fields_ = [("max_device_bytes", ctypes.c_uint64), ("max_tick_reads", ctypes.c_uint64),
+                ("hit_cap", ctypes.c_uint32), ("kernel", ctypes.c_int32), ("workers", ctypes.c_int32),
+                ("start_paused", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_uint64) for name in
+                ("submitted", "completed", "failed", "cancelled", "ticks", "reads", "pending",
+                 "device_bytes_in_use", "device_budget")] + [("busy_s", ctypes.c_double)]
 
 
 class IndexInfo(ctypes.Structure):
@@ -95,7 +108,16 @@ SIGNATURES = {
     "mica_debug_suffix_array": (_i32, [P, _u64, _i32, P]),
     "mica_debug_occ": (_i32, [P, P, _u64, P]),
     "mica_debug_locate": (_i32, [P, P, _u64, P]),
-    "mica_debug_table": (_i32, [P, P, _u64, P]),
+    "mica_debug_seed_interval": (_i32, [P, P, _u32, _u64, P]),
+    "mica_server_params_default": (None, [P]),
+    "mica_server_start": (_i32, [P, P, P]),
+    "mica_server_submit": (_i32, [P, P, P, P, P, _u64, P]),
+    "mica_server_poll": (_i32, [P, _u64, P, P]),
+    "mica_server_wait": (_i32, [P, _u64, _u32, P, P]),
+    "mica_server_cancel": (_i32, [P, _u64]),
+    "mica_server_resume": (None, [P]),
+    "mica_server_get_stats": (_i32, [P, P]),
+    "mica_server_stop": (None, [P]),
 }
 
 
@@ -157,6 +179,22 @@ class Result:
     def hits_of(self, i: int) -> list:
         h = self.read_hits(i)
         return [(int(p), int(s), int(d)) for p, s, d in zip(h["pos"], h["strand"], h["mm"])]
+
+
+def _take_result(out) -> Result:
+    """Copy a library-owned mica_result into numpy arrays and free it."""
+    try:
+        r = out.contents
+        n = int(r.n_reads)
+        total = np.ctypeslib.as_array(r.total, shape=(max(n, 1),))[:n].copy()
+        offsets = np.ctypeslib.as_array(r.offsets, shape=(n + 1,)).copy()
+        nh = int(offsets[-1])
+        hits = np.empty(nh, dtype=HIT_DTYPE)
+        if nh:
+            ctypes.memmove(hits.ctypes.data, r.hits, nh * HIT_DTYPE.itemsize)
+    finally:
+        _lib.mica_result_free(out)
+    return Result(total, offsets, hits)
 
 
 class _CudaArray:
@@ -249,17 +287,7 @@ class Index:
         _check(_lib.mica_align_batch(self._h, _ptr(words) if words.size else None, _ptr(word_off),
                                      _ptr(lengths) if n else None, _ptr(k) if n else None, n,
                                      ctypes.byref(p), ctypes.byref(out)), "mica_align_batch")
-        try:
-            r = out.contents
-            total = np.ctypeslib.as_array(r.total, shape=(max(n, 1),))[:n].copy()
-            offsets = np.ctypeslib.as_array(r.offsets, shape=(n + 1,)).copy()
-            nh = int(offsets[-1])
-            hits = np.empty(nh, dtype=HIT_DTYPE)
-            if nh:
-                ctypes.memmove(hits.ctypes.data, r.hits, nh * HIT_DTYPE.itemsize)
-        finally:
-            _lib.mica_result_free(out)
-        return Result(total, offsets, hits)
+        return _take_result(out)
 
     def align_batch(self, batch, **kw) -> Result:
         """align() on any object with words/word_off/lengths/k arrays."""
@@ -289,11 +317,86 @@ class Index:
         _check(_lib.mica_debug_locate(self._h, _ptr(rows), rows.size, _ptr(out)), "mica_debug_locate")
         return out
 
-    def debug_table(self, codes) -> np.ndarray:
+    def debug_seed_interval(self, codes, length: int) -> np.ndarray:
+        """[l, r) of each length-mer code from the q-mer table (GPU seed step)."""
         codes = np.ascontiguousarray(codes, dtype=np.uint32)
-        out = np.empty(codes.size, dtype=np.uint32)
-        _check(_lib.mica_debug_table(self._h, _ptr(codes), codes.size, _ptr(out)), "mica_debug_table")
+        out = np.empty((codes.size, 2), dtype=np.uint32)
+        _check(_lib.mica_debug_seed_interval(self._h, _ptr(codes), length, codes.size, _ptr(out)),
+               "mica_debug_seed_interval")
         return out
+
+
+class Server:
+    """Continuous-batching request loop over a resident index (mica_server_*)."""
+
+    def __init__(self, index: Index, max_device_bytes: int = 0, max_tick_reads: int = 0, hit_cap: int = 1000,
+                 kernel="persistent", workers: int = 2, start_paused: bool = False):
+        p = ServerParams()
+        _lib.mica_server_params_default(ctypes.byref(p))
+        p.max_device_bytes = max_device_bytes
+        p.max_tick_reads = max_tick_reads
+        p.hit_cap = hit_cap
+        p.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+        p.workers = workers
+        p.start_paused = int(start_paused)
+        self.index = index
+        h = ctypes.c_void_p()
+        _check(_lib.mica_server_start(index._h, ctypes.byref(p), ctypes.byref(h)), "mica_server_start")
+        self._h = h
+
+    def submit(self, words, word_off, lengths, k) -> int:
+        words = np.ascontiguousarray(words, dtype=np.uint32)
+        word_off = np.ascontiguousarray(word_off, dtype=np.uint64)
+        lengths = np.ascontiguousarray(lengths, dtype=np.uint16)
+        k = np.ascontiguousarray(k, dtype=np.uint8)
+        rid = ctypes.c_uint64()
+        n = lengths.size
+        _check(_lib.mica_server_submit(self._h, _ptr(words) if words.size else None, _ptr(word_off),
+                                       _ptr(lengths) if n else None, _ptr(k) if n else None, n,
+                                       ctypes.byref(rid)), "mica_server_submit")
+        return int(rid.value)
+
+    def submit_batch(self, batch) -> int:
+        return self.submit(batch.words, batch.word_off, batch.lengths, batch.k)
+
+    def poll(self, rid: int):
+        """(Result, latency_ms) once done, None while queued or running."""
+        out = ctypes.POINTER(_Result)()
+        lat = ctypes.c_double()
+        rc = _lib.mica_server_poll(self._h, rid, ctypes.byref(out), ctypes.byref(lat))
+        if rc == MICA_EBUSY:
+            return None
+        _check(rc, "mica_server_poll")
+        return _take_result(out), lat.value
+
+    def wait(self, rid: int, timeout_ms: int = 600_000):
+        out = ctypes.POINTER(_Result)()
+        lat = ctypes.c_double()
+        _check(_lib.mica_server_wait(self._h, rid, timeout_ms, ctypes.byref(out), ctypes.byref(lat)),
+               "mica_server_wait")
+        return _take_result(out), lat.value
+
+    def cancel(self, rid: int) -> int:
+        return int(_lib.mica_server_cancel(self._h, rid))
+
+    def resume(self):
+        _lib.mica_server_resume(self._h)
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(_lib.mica_server_get_stats(self._h, ctypes.byref(st)), "mica_server_get_stats")
+        return {name: getattr(st, name) for name, _ in ServerStats._fields_}
+
+    def stop(self):
+        if self._h:
+            _lib.mica_server_stop(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.stop()
 
 
 def debug_suffix_array(genome_acgt, device: int = 0) -> np.ndarray:

@@ -43,13 +43,15 @@ void dev_release(DevBuf &b)
     b.bytes = 0;
 }
 
-static void free_workspace(Workspace &w)
+void free_workspace(Workspace &w)
 {
     DevBuf *all[] = {&w.ctl, &w.iv, &w.iv_sorted, &w.iv_cnt, &w.iv_off, &w.total, &w.keep, &w.hit_off,
                      &w.hits, &w.spill, &w.big, &w.scan_tmp, &w.reads_words, &w.reads_off, &w.reads_len,
                      &w.reads_k, &w.spill2};
     for (DevBuf *b : all) dev_release(*b);
     for (auto &e : w.ev)
+        if (e) { cudaEventDestroy(e); e = nullptr; }
+    for (auto &e : w.kev)
         if (e) { cudaEventDestroy(e); e = nullptr; }
 }
 
@@ -95,6 +97,7 @@ struct FileHeader {
     uint64_t n, dollar_row;
     uint64_t C[5];
     uint64_t n_occ_blocks, n_mark_blocks, n_samples, table_len;
+    uint32_t nshort, short_pad[MAX_Q], short_len[MAX_Q];
 };
 
 static int write_array(FILE *f, const DevBuf &b, uint64_t bytes)
@@ -122,26 +125,30 @@ static int read_array(FILE *f, DevBuf &b, uint64_t bytes)
 
 // ---- align orchestration ----
 
-static int align_on_device(mica_index *idx, const ReadsView &rd, const mica_align_params &p, cudaStream_t s,
-                           uint64_t *nh)
+int align_on_device(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd,
+                    const mica_align_params &p, cudaStream_t s, uint64_t *nh)
 {
-    Workspace &w = idx->ws;
     for (auto &e : w.ev)
         if (!e) MICA_CUDA_TRY(cudaEventCreate(&e));
-    idx->stats = mica_stats{};
+    for (auto &e : w.kev)
+        if (!e) MICA_CUDA_TRY(cudaEventCreate(&e));
+    uint64_t launches = st.launches;   // the batch check already counted
+    st = mica_stats{};
+    st.launches = launches;
     MICA_CUDA_TRY(cudaEventRecord(w.ev[0], s));
     SearchConfig cfg{};
     cfg.kernel = p.kernel;
     cfg.plain_block = 128;
     cfg.plain_budget = 1u << 16;
-    int rc = run_search(idx, rd, cfg, s);
+    int rc = run_search(idx, w, st, rd, cfg, s);
     if (rc) return rc;
     MICA_CUDA_TRY(cudaEventRecord(w.ev[1], s));
-    if ((rc = run_post(idx, rd, p.hit_cap, s, nh))) return rc;
+    if ((rc = run_post(idx, w, st, rd, p.hit_cap, s, nh))) return rc;
     MICA_CUDA_TRY(cudaEventRecord(w.ev[2], s));
     MICA_CUDA_TRY(cudaEventSynchronize(w.ev[2]));
-    cudaEventElapsedTime(&idx->stats.search_ms, w.ev[0], w.ev[1]);
-    cudaEventElapsedTime(&idx->stats.total_ms, w.ev[0], w.ev[2]);
+    cudaEventElapsedTime(&st.search_ms, w.ev[0], w.ev[1]);
+    cudaEventElapsedTime(&st.kernel_ms, w.kev[0], w.kev[1]);
+    cudaEventElapsedTime(&st.total_ms, w.ev[0], w.ev[2]);
     return 0;
 }
 
@@ -241,6 +248,11 @@ int mica_index_save(const mica_index *idx, const char *path)
     h.n_mark_blocks = idx->n_mark_blocks;
     h.n_samples = idx->n_samples;
     h.table_len = idx->table_len;
+    h.nshort = idx->view.nshort;
+    for (uint32_t t = 0; t < MAX_Q; t++) {
+        h.short_pad[t] = idx->view.short_pad[t];
+        h.short_len[t] = idx->view.short_len[t];
+    }
     int rc = fwrite(&h, sizeof(h), 1, f) == 1 ? 0 : MICA_EIO;
     if (!rc) rc = write_array(f, idx->occ, h.n_occ_blocks * 64);
     if (!rc) rc = write_array(f, idx->marks, h.n_mark_blocks * 64);
@@ -260,7 +272,8 @@ int mica_index_load(const char *path, int device, mica_index **out)
     if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, MAGIC, 8) != 0 || h.version != 1 ||
         h.kmer_q < 1 || h.kmer_q > MAX_Q || h.sa_sample < 1 || h.n + 1 >= (1ull << 32) ||
         h.n_occ_blocks != (h.n + 1) / OCC_ROWS + 1 || h.n_mark_blocks != (h.n + 1) / MARK_ROWS + 1 ||
-        h.table_len != (1ull << (2 * h.kmer_q)) + 1 || h.n_samples > h.n + 1) {
+        h.table_len != (1ull << (2 * h.kmer_q)) + 1 || h.n_samples > h.n + 1 ||
+        h.nshort != std::min<uint64_t>(h.kmer_q, h.n + 1)) {
         fclose(f);
         return MICA_EIO;
     }
@@ -293,6 +306,11 @@ int mica_index_load(const char *path, int device, mica_index **out)
         for (int c = 0; c < 5; c++) v.C[c] = (uint32_t)h.C[c];
         v.q = h.kmer_q;
         v.sa_sample = h.sa_sample;
+        v.nshort = h.nshort;
+        for (uint32_t t = 0; t < MAX_Q; t++) {
+            v.short_pad[t] = h.short_pad[t];
+            v.short_len[t] = h.short_len[t];
+        }
         rc = upload_variants(idx);
     }
     if (rc) { mica_index_free(idx); return rc; }
@@ -356,14 +374,18 @@ __global__ void k_validate(ReadsView rd, uint64_t genome_len, unsigned int *bad)
     }
 }
 
-int validate_device_batch(mica_index *idx, const ReadsView &rd, cudaStream_t s)
+}  // namespace
+
+int validate_device_batch(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd,
+                          cudaStream_t s)
 {
     if (rd.n == 0) return 0;
-    if (int rc = dev_reserve(idx->ws.ctl, sizeof(SearchCtl) + 64)) return rc;
-    unsigned int *bad = (unsigned int *)((char *)idx->ws.ctl.p + sizeof(SearchCtl));
+    if (int rc = dev_reserve(w.ctl, sizeof(SearchCtl) + 64)) return rc;
+    unsigned int *bad = (unsigned int *)((char *)w.ctl.p + sizeof(SearchCtl));
     MICA_CUDA_TRY(cudaMemsetAsync(bad, 0, 4, s));
     unsigned g = (unsigned)std::min<uint64_t>((rd.n + 255) / 256, 152 * 32);
     k_validate<<<g, 256, 0, s>>>(rd, idx->n, bad);
+    st.launches = 1;
     unsigned int hb = 0;
     MICA_CUDA_TRY(cudaMemcpyAsync(&hb, bad, 4, cudaMemcpyDeviceToHost, s));
     MICA_CUDA_TRY(cudaStreamSynchronize(s));
@@ -383,7 +405,6 @@ int validate_host_batch(const mica_index *idx, const uint64_t *off, const uint16
     return 0;
 }
 
-}  // namespace
 }  // namespace mica
 
 extern "C" {
@@ -403,9 +424,10 @@ int mica_align_device(mica_index *idx, const uint32_t *d_packed_reads, const uin
     MICA_CUDA_TRY(cudaSetDevice(idx->device));
     cudaStream_t s = (cudaStream_t)p.cuda_stream;
     ReadsView rd{d_packed_reads, d_word_offsets, d_lengths, d_k, n_reads};
-    if (int rc = validate_device_batch(idx, rd, s)) return rc;
+    idx->stats.launches = 0;
+    if (int rc = validate_device_batch(idx, idx->ws, idx->stats, rd, s)) return rc;
     uint64_t nh = 0;
-    if (int rc = align_on_device(idx, rd, p, s, &nh)) return rc;
+    if (int rc = align_on_device(idx, idx->ws, idx->stats, rd, p, s, &nh)) return rc;
     out->n_reads = n_reads;
     out->n_hits = nh;
     out->total = (const uint64_t *)idx->ws.total.p;
@@ -444,8 +466,9 @@ int mica_align_batch(mica_index *idx, const uint32_t *packed_reads, const uint64
     }
     ReadsView rd{(const uint32_t *)w.reads_words.p, (const uint64_t *)w.reads_off.p,
                  (const uint16_t *)w.reads_len.p, (const uint8_t *)w.reads_k.p, n_reads};
+    idx->stats.launches = 0;
     uint64_t nh = 0;
-    if ((rc = align_on_device(idx, rd, p, s, &nh))) return rc;
+    if ((rc = align_on_device(idx, idx->ws, idx->stats, rd, p, s, &nh))) return rc;
     mica_result *r = (mica_result *)calloc(1, sizeof(mica_result));
     if (!r) return MICA_ENOMEM;
     r->n_reads = n_reads;
@@ -527,17 +550,24 @@ int mica_debug_locate(const mica_index *idx, const uint64_t *rows, uint64_t n, u
     return debug_rows_call(idx, rows, n, pos_out, 1, 1);
 }
 
-int mica_debug_table(const mica_index *idx, const uint32_t *codes, uint64_t n, uint32_t *bounds_out)
+int mica_debug_seed_interval(const mica_index *idx, const uint32_t *codes, uint32_t len, uint64_t n,
+                             uint32_t *lr_out)
 {
-    if (!idx || (n && (!codes || !bounds_out))) return MICA_EINVAL;
-    std::vector<uint32_t> tab(idx->table_len);
+    if (!idx || (n && (!codes || !lr_out)) || len < 1 || len > idx->params.kmer_q) return MICA_EINVAL;
     for (uint64_t i = 0; i < n; i++)
-        if (codes[i] >= idx->table_len) return MICA_EINVAL;
+        if ((uint64_t)codes[i] >= (1ull << (2 * len))) return MICA_EINVAL;
+    if (n == 0) return 0;
     DeviceGuard g(idx->device);
     MICA_CUDA_TRY(cudaSetDevice(idx->device));
-    MICA_CUDA_TRY(cudaMemcpy(tab.data(), idx->table.p, idx->table_len * 4, cudaMemcpyDeviceToHost));
-    for (uint64_t i = 0; i < n; i++) bounds_out[i] = tab[codes[i]];
-    return 0;
+    DevBuf dc, dout;
+    int rc = dev_reserve(dc, n * 4);
+    if (!rc) rc = dev_reserve(dout, n * 8);
+    if (!rc && cudaMemcpy(dc.p, codes, n * 4, cudaMemcpyHostToDevice) != cudaSuccess) rc = MICA_ECUDA;
+    if (!rc) rc = debug_seed(idx, (const uint32_t *)dc.p, len, n, (uint32_t *)dout.p, 0);
+    if (!rc && cudaMemcpy(lr_out, dout.p, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess) rc = MICA_ECUDA;
+    dev_release(dc);
+    dev_release(dout);
+    return rc;
 }
 
 }  // extern "C"

@@ -11,7 +11,10 @@
 //      start with the number of marked rows before them) and the sampled SA
 //      values in row order;
 //   4. the q-mer table: bound[x] = number of suffixes of T smaller than the
-//      q-mer x, so [bound[x], bound[x+1]) is the SA interval of x.
+//      q-mer x.  The SA interval of x is [bound[x], bound[x+1]) less the
+//      suffixes u$ (|u| < q, at most q of them, at the end of G) whose
+//      A-padded code is x+1: they sort after every suffix starting with x
+//      (and, for shorter seeds, see seed_interval).
 //
 // The sorts and scans of this one-time build use CUB; the search path uses
 // only this library's own kernels.
@@ -411,6 +414,21 @@ int build_index_from_codes(const uint8_t *d_codes, uint64_t n, const mica_index_
 
     // q-mer table
     uint64_t tl = (1ull << (2 * p.kmer_q)) + 1;
+    {
+        // A-padded codes of the short suffixes (positions max(0, n-q+1) .. n)
+        uint32_t q = p.kmer_q;
+        uint64_t first = n >= q ? n - q + 1 : 0;
+        std::vector<uint8_t> tail(n - first);
+        if (!tail.empty())
+            MICA_CUDA_TRY(cudaMemcpy(tail.data(), d_codes + first, tail.size(), cudaMemcpyDeviceToHost));
+        idx->view.nshort = 0;
+        for (uint64_t i = first; i <= n; i++) {
+            uint32_t code = 0;
+            for (uint32_t t = 0; t < q; t++) code = (code << 2) | (i + t < n ? tail[i + t - first] : 0u);
+            idx->view.short_len[idx->view.nshort] = (uint32_t)(n - i);
+            idx->view.short_pad[idx->view.nshort++] = code;
+        }
+    }
     DevBuf tcnt;
     if ((rc = dev_reserve(tcnt, tl * 4)) || (rc = dev_reserve(idx->table, tl * 4))) {
         cleanup(); dev_release(tcnt); return rc;

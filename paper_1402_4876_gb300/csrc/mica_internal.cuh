@@ -46,6 +46,14 @@ struct IndexView {
     uint32_t C[5];
     uint32_t q;
     uint32_t sa_sample;
+    // Suffixes of T shorter than q + 1 symbols (u$ with |u| < q, at most q of
+    // them) sort below u padded with A to a q-mer, so the table bound at that
+    // padded code counts them.  An interval ending at that code must drop
+    // them (they sort after it); an interval of a j-mer starting there must
+    // drop those with |u| >= j (they start with the j-mer).
+    uint32_t nshort;
+    uint32_t short_pad[MAX_Q];
+    uint32_t short_len[MAX_Q];
 };
 
 // Read batch in device memory.
@@ -96,6 +104,7 @@ struct SearchCtl {
     unsigned int error;               // bit 0 interval overflow, bit 1 spill overflow, bit 2 timeout
     unsigned int pad_;
     unsigned long long seeds, nodes, rank_blocks, spills;
+    unsigned long long rounds, lane_ops;
 };
 
 constexpr unsigned ERR_IV_OVERFLOW = 1u;
@@ -122,7 +131,8 @@ struct Workspace {
     uint32_t iv_cap = 0, spill_cap = 0;
     uint64_t hit_cap_total = 0;
     bool spill_dirty = false;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // call timing
+    cudaEvent_t kev[2] = {nullptr, nullptr};                      // search kernel timing
 };
 
 }  // namespace mica
@@ -167,12 +177,23 @@ struct SearchConfig {
     int plain_block;
     uint32_t plain_budget;      // plain: node expansions per task before re-queueing
 };
-int run_search(mica_index *idx, const ReadsView &rd, const SearchConfig &cfg, cudaStream_t s);
+int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd,
+               const SearchConfig &cfg, cudaStream_t s);
 
 // post.cu
-int run_post(mica_index *idx, const ReadsView &rd, uint32_t hit_cap, cudaStream_t s,
-             uint64_t *n_hits_out);
+int run_post(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd, uint32_t hit_cap,
+             cudaStream_t s, uint64_t *n_hits_out);
+// capi.cu: the whole path on one workspace (validation of device batches included)
+int align_on_device(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd,
+                    const mica_align_params &p, cudaStream_t s, uint64_t *nh);
+int validate_device_batch(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd,
+                          cudaStream_t s);
+int validate_host_batch(const mica_index *idx, const uint64_t *off, const uint16_t *len, const uint8_t *k,
+                        uint64_t n);
+void free_workspace(Workspace &w);
 int debug_occ(const mica_index *idx, const uint64_t *d_rows, uint64_t n, uint32_t *d_out, cudaStream_t s);
 int debug_locate(const mica_index *idx, const uint64_t *d_rows, uint64_t n, uint32_t *d_out, cudaStream_t s);
+int debug_seed(const mica_index *idx, const uint32_t *d_codes, uint32_t len, uint64_t n, uint32_t *d_out,
+               cudaStream_t s);
 
 }  // namespace mica

@@ -103,15 +103,16 @@ __global__ void k_scan_add(uint64_t *__restrict__ out, uint64_t n, const uint64_
 }
 
 template <typename T>
-int exclusive_scan(DevBuf &tmp, const T *in, uint64_t n, uint64_t *out, cudaStream_t s)
+int exclusive_scan(DevBuf &tmp, const T *in, uint64_t n, uint64_t *out, cudaStream_t s, uint64_t &launches)
 {
     uint64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (int rc = dev_reserve(tmp, (ntiles + 1) * 8)) return rc;
     uint64_t *ts = (uint64_t *)tmp.p;
-    if (ntiles) k_scan_tiles<T><<<(unsigned)ntiles, SCAN_THREADS, 0, s>>>(in, n, out, ts);
+    if (ntiles) { k_scan_tiles<T><<<(unsigned)ntiles, SCAN_THREADS, 0, s>>>(in, n, out, ts); launches++; }
     k_scan_sums<<<1, 1024, 0, s>>>(ts, ntiles);
     unsigned g = (unsigned)std::min<uint64_t>(std::max<uint64_t>((n + 255) / 256, 1), 152 * 32);
     k_scan_add<<<g, 256, 0, s>>>(out, n, ts);
+    launches += 2;
     MICA_CUDA_TRY(cudaGetLastError());
     return 0;
 }
@@ -333,6 +334,18 @@ __global__ void k_debug_locate(const IndexView ix, const uint64_t *__restrict__ 
     }
 }
 
+__global__ void k_debug_seed(const IndexView ix, const uint32_t *__restrict__ codes, uint32_t len, uint64_t n,
+                             uint32_t *__restrict__ out)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t l, r;
+        seed_interval(ix, codes[i], len, l, r);
+        out[2 * i] = l;
+        out[2 * i + 1] = r < l ? l : r;
+    }
+}
+
 unsigned grid1(uint64_t n, int block = 256)
 {
     return (unsigned)std::min<uint64_t>(std::max<uint64_t>((n + block - 1) / block, 1), 152ull * 64);
@@ -340,35 +353,43 @@ unsigned grid1(uint64_t n, int block = 256)
 
 }  // namespace
 
-int run_post(mica_index *idx, const ReadsView &rd, uint32_t hit_cap, cudaStream_t s, uint64_t *n_hits_out)
+static uint64_t big_list_bytes(uint64_t n)
 {
-    Workspace &w = idx->ws;
+    return (std::max<uint64_t>(n, 1) * 4 + 15) & ~15ull;
+}
+
+int run_post(const mica_index *idx, Workspace &w, mica_stats &stt, const ReadsView &rd, uint32_t hit_cap,
+             cudaStream_t s, uint64_t *n_hits_out)
+{
     uint64_t n = rd.n;
-    uint32_t niv = (uint32_t)idx->stats.intervals;
+    uint32_t niv = (uint32_t)stt.intervals;
     int rc;
     if ((rc = dev_reserve(w.iv_sorted, std::max<uint64_t>(niv, 1) * sizeof(Interval))) ||
         (rc = dev_reserve(w.iv_off, (n + 1) * 8)) || (rc = dev_reserve(w.total, std::max<uint64_t>(n, 1) * 8)) ||
         (rc = dev_reserve(w.keep, std::max<uint64_t>(n, 1) * 8)) || (rc = dev_reserve(w.hit_off, (n + 1) * 8)) ||
-        (rc = dev_reserve(w.big, std::max<uint64_t>(n, 1) * 4 + 64)))
+        (rc = dev_reserve(w.big, big_list_bytes(n) + 64)))
         return rc;
     uint64_t *iv_off = (uint64_t *)w.iv_off.p, *hit_off = (uint64_t *)w.hit_off.p;
-    if ((rc = exclusive_scan<uint32_t>(w.scan_tmp, (const uint32_t *)w.iv_cnt.p, n, iv_off, s))) return rc;
-    if (niv) k_iv_scatter<<<grid1(niv), 256, 0, s>>>((const Interval *)w.iv.p, niv, iv_off,
-                                                     (uint32_t *)w.iv_cnt.p, (Interval *)w.iv_sorted.p);
-    if (n) k_summarize<<<grid1(n, 128), 128, 0, s>>>((Interval *)w.iv_sorted.p, iv_off, n, hit_cap,
-                                                    (uint64_t *)w.total.p, (uint64_t *)w.keep.p);
-    if ((rc = exclusive_scan<uint64_t>(w.scan_tmp, (const uint64_t *)w.keep.p, n, hit_off, s))) return rc;
+    uint64_t &L = stt.launches;
+    if ((rc = exclusive_scan<uint32_t>(w.scan_tmp, (const uint32_t *)w.iv_cnt.p, n, iv_off, s, L))) return rc;
+    if (niv) { k_iv_scatter<<<grid1(niv), 256, 0, s>>>((const Interval *)w.iv.p, niv, iv_off,
+                                                       (uint32_t *)w.iv_cnt.p, (Interval *)w.iv_sorted.p); L++; }
+    if (n) { k_summarize<<<grid1(n, 128), 128, 0, s>>>((Interval *)w.iv_sorted.p, iv_off, n, hit_cap,
+                                                      (uint64_t *)w.total.p, (uint64_t *)w.keep.p); L++; }
+    if ((rc = exclusive_scan<uint64_t>(w.scan_tmp, (const uint64_t *)w.keep.p, n, hit_off, s, L))) return rc;
     uint64_t nh = 0;
     MICA_CUDA_TRY(cudaMemcpyAsync(&nh, hit_off + n, 8, cudaMemcpyDeviceToHost, s));
     MICA_CUDA_TRY(cudaStreamSynchronize(s));
     if ((rc = dev_reserve(w.hits, std::max<uint64_t>(nh, 1) * sizeof(Hit) + 64))) return rc;
-    unsigned long long *steps = (unsigned long long *)((char *)w.big.p + std::max<uint64_t>(n, 1) * 4);
+    // counters after the big-read list, on a 16-byte boundary
+    unsigned long long *steps = (unsigned long long *)((char *)w.big.p + big_list_bytes(n));
     unsigned int *nbig = (unsigned int *)(steps + 1);
     MICA_CUDA_TRY(cudaMemsetAsync(steps, 0, 16, s));
-    if (n) k_expand<<<grid1(n, 128), 128, 0, s>>>((const Interval *)w.iv_sorted.p, iv_off, hit_off, n,
-                                                 (Hit *)w.hits.p);
-    if (nh) k_locate<<<grid1(nh), 256, 0, s>>>(idx->view, (Hit *)w.hits.p, nh, steps);
-    if (n) k_sort_small<<<grid1(n, 128), 128, 0, s>>>((uint64_t *)w.hits.p, hit_off, n, (uint32_t *)w.big.p, nbig);
+    if (n) { k_expand<<<grid1(n, 128), 128, 0, s>>>((const Interval *)w.iv_sorted.p, iv_off, hit_off, n,
+                                                   (Hit *)w.hits.p); L++; }
+    if (nh) { k_locate<<<grid1(nh), 256, 0, s>>>(idx->view, (Hit *)w.hits.p, nh, steps); L++; }
+    if (n) { k_sort_small<<<grid1(n, 128), 128, 0, s>>>((uint64_t *)w.hits.p, hit_off, n, (uint32_t *)w.big.p,
+                                                       nbig); L++; }
     unsigned int hb[4] = {0, 0, 0, 0};
     unsigned long long st = 0;
     MICA_CUDA_TRY(cudaMemcpyAsync(&st, steps, 8, cudaMemcpyDeviceToHost, s));
@@ -377,6 +398,7 @@ int run_post(mica_index *idx, const ReadsView &rd, uint32_t hit_cap, cudaStream_
     if (hb[0]) {
         k_sort_big<<<std::min(hb[0], 152u * 4), 512, 0, s>>>((uint64_t *)w.hits.p, hit_off,
                                                            (const uint32_t *)w.big.p, hb[0]);
+        L++;
         // reads above the shared-memory size: one global bitonic sort each
         std::vector<uint32_t> bigr(hb[0]);
         MICA_CUDA_TRY(cudaMemcpyAsync(bigr.data(), w.big.p, 4ull * hb[0], cudaMemcpyDeviceToHost, s));
@@ -391,13 +413,14 @@ int run_post(mica_index *idx, const ReadsView &rd, uint32_t hit_cap, cudaStream_
             DevBuf scratch;
             if ((rc = dev_reserve(scratch, P * 8))) return rc;
             k_sort_global<<<1, 1024, 0, s>>>((uint64_t *)w.hits.p + ob[0], cnt, (uint64_t *)scratch.p, P);
+            L++;
             MICA_CUDA_TRY(cudaStreamSynchronize(s));
             dev_release(scratch);
         }
     }
     MICA_CUDA_TRY(cudaGetLastError());
-    idx->stats.located = nh;
-    idx->stats.lf_steps = st;
+    stt.located = nh;
+    stt.lf_steps = st;
     *n_hits_out = nh;
     return 0;
 }
@@ -405,6 +428,14 @@ int run_post(mica_index *idx, const ReadsView &rd, uint32_t hit_cap, cudaStream_
 int debug_occ(const mica_index *idx, const uint64_t *d_rows, uint64_t n, uint32_t *d_out, cudaStream_t s)
 {
     if (n) k_debug_occ<<<grid1(n), 256, 0, s>>>(idx->view, d_rows, n, d_out);
+    MICA_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+int debug_seed(const mica_index *idx, const uint32_t *d_codes, uint32_t len, uint64_t n, uint32_t *d_out,
+               cudaStream_t s)
+{
+    if (n) k_debug_seed<<<grid1(n), 256, 0, s>>>(idx->view, d_codes, len, n, d_out);
     MICA_CUDA_TRY(cudaGetLastError());
     return 0;
 }

@@ -22,6 +22,7 @@
 //                   children back with ballot/shuffle prefix sums.  Excess
 //                   nodes spill to a device queue that idle warps drain.
 #include <algorithm>
+#include <mutex>
 
 #include "search_common.cuh"
 
@@ -336,7 +337,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_persistent(PersistArgs a)
     uint32_t bot = 0, top = 0;
     bool busy = false;
     uint32_t idle_rounds = 0, backoff = 256;
-    unsigned long long c_seeds = 0, c_nodes = 0, c_blocks = 0, c_spills = 0;
+    unsigned long long c_seeds = 0, c_nodes = 0, c_blocks = 0, c_spills = 0, c_rounds = 0;
     __syncwarp();
 
     for (uint32_t iter = 0;; iter++) {
@@ -537,6 +538,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_persistent(PersistArgs a)
         }
 
         // ---- extend
+        if (lane == 0) c_rounds++;
         uint32_t slot = has_node ? (x_m & 31u) : sslot;
         uint32_t info = __shfl_sync(FULL, s_info, slot);
         uint32_t rid = __shfl_sync(FULL, s_read, slot);
@@ -651,6 +653,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_persistent(PersistArgs a)
     if (lane == 0 && v) atomicAdd(&ctl->rank_blocks, v);
     v = c_spills; for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     if (lane == 0 && v) atomicAdd(&ctl->spills, v);
+    v = c_rounds; for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if (lane == 0 && v) atomicAdd(&ctl->rounds, v);
+    v = c_seeds + c_nodes; for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if (lane == 0 && v) atomicAdd(&ctl->lane_ops, v);
 }
 
 }  // namespace
@@ -663,9 +669,11 @@ constexpr int P_SCAP = 256;
 constexpr int P_WARPS = 8;
 
 static int g_num_sms = 0, g_persist_blocks = 0;
+static std::mutex g_grid_mu;
 
 static int persistent_grid(int device, int &blocks_per_sm, size_t smem)
 {
+    std::lock_guard<std::mutex> lk(g_grid_mu);
     if (g_num_sms == 0) {
         MICA_CUDA_TRY(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, device));
         MICA_CUDA_TRY(cudaFuncSetAttribute(k_persistent<P_SCAP, P_WARPS>,
@@ -678,9 +686,9 @@ static int persistent_grid(int device, int &blocks_per_sm, size_t smem)
     return 0;
 }
 
-int run_search(mica_index *idx, const ReadsView &rd, const SearchConfig &cfg, cudaStream_t s)
+int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd,
+               const SearchConfig &cfg, cudaStream_t s)
 {
-    Workspace &w = idx->ws;
     uint64_t n = rd.n;
     int rc;
     if ((rc = dev_reserve(w.ctl, sizeof(SearchCtl) + 64))) return rc;
@@ -712,8 +720,11 @@ int run_search(mica_index *idx, const ReadsView &rd, const SearchConfig &cfg, cu
                 pa.spill = (WorkItem *)w.spill.p;
                 int grid = g_num_sms * bps;
                 pa.total_warps = grid * P_WARPS;
+                MICA_CUDA_TRY(cudaEventRecord(w.kev[0], s));
                 k_persistent<P_SCAP, P_WARPS><<<grid, P_WARPS * 32, smem, s>>>(pa);
                 MICA_CUDA_TRY(cudaGetLastError());
+                MICA_CUDA_TRY(cudaEventRecord(w.kev[1], s));
+                st.launches++;
             } else {
                 // plain: one task per thread, then drain the re-queue in rounds
                 if ((rc = dev_reserve(w.spill2, (size_t)w.spill_cap * sizeof(WorkItem)))) return rc;
@@ -726,8 +737,11 @@ int run_search(mica_index *idx, const ReadsView &rd, const SearchConfig &cfg, cu
                 pa.requeue_cap = w.spill_cap;
                 pa.budget = cfg.plain_budget;
                 int blk = cfg.plain_block > 0 ? cfg.plain_block : 128;
+                MICA_CUDA_TRY(cudaEventRecord(w.kev[0], s));
                 k_plain<<<(unsigned)((pa.ntasks + blk - 1) / blk), blk, 0, s>>>(pa);
                 MICA_CUDA_TRY(cudaGetLastError());
+                MICA_CUDA_TRY(cudaEventRecord(w.kev[1], s));
+                st.launches++;
                 WorkItem *bufs[2] = {(WorkItem *)w.spill.p, (WorkItem *)w.spill2.p};
                 for (int round = 0; round < 64; round++) {
                     unsigned int cnt = 0, err = 0;
@@ -743,6 +757,8 @@ int run_search(mica_index *idx, const ReadsView &rd, const SearchConfig &cfg, cu
                     MICA_CUDA_TRY(cudaMemsetAsync(&d_ctl->spill_reserve, 0, 4, s));
                     k_plain<<<(cnt + blk - 1) / blk, blk, 0, s>>>(pa);
                     MICA_CUDA_TRY(cudaGetLastError());
+                    MICA_CUDA_TRY(cudaEventRecord(w.kev[1], s));
+                    st.launches++;
                 }
             }
         }
@@ -751,7 +767,7 @@ int run_search(mica_index *idx, const ReadsView &rd, const SearchConfig &cfg, cu
         MICA_CUDA_TRY(cudaStreamSynchronize(s));
         if (out.error & ERR_TIMEOUT) { w.spill_dirty = true; return MICA_ETIMEOUT; }
         if (out.error & (ERR_IV_OVERFLOW | ERR_SPILL_OVERFLOW)) {
-            idx->stats.retries++;
+            st.retries++;
             if (out.error & ERR_IV_OVERFLOW)
                 w.iv_cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(2ull * out.iv_count, 2ull * w.iv_cap), 0xfffffff0ull);
             if (out.error & ERR_SPILL_OVERFLOW)
@@ -759,12 +775,14 @@ int run_search(mica_index *idx, const ReadsView &rd, const SearchConfig &cfg, cu
             w.spill_dirty = true;
             continue;
         }
-        idx->stats.tasks = 2 * n;
-        idx->stats.seeds = out.seeds;
-        idx->stats.nodes = out.nodes;
-        idx->stats.rank_blocks = out.rank_blocks;
-        idx->stats.intervals = out.iv_count;
-        idx->stats.spills = out.spills;
+        st.tasks = 2 * n;
+        st.seeds = out.seeds;
+        st.nodes = out.nodes;
+        st.rank_blocks = out.rank_blocks;
+        st.intervals = out.iv_count;
+        st.spills = out.spills;
+        st.warp_rounds = out.rounds;
+        st.lane_ops = out.lane_ops;
         return 0;
     }
     return MICA_EINTERNAL;

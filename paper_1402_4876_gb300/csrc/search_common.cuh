@@ -129,14 +129,21 @@ __device__ __forceinline__ uint32_t window_code(const uint32_t *pat, uint32_t m,
     return code;
 }
 
-// SA interval of a (qe)-mer code from the q-mer table: [bound[x*4^(q-qe)],
-// bound[(x+1)*4^(q-qe)]).
+// SA interval of a (qe)-mer code x from the q-mer table, whose entry at a
+// q-mer y is the number of suffixes smaller than y:
+//   l = bound[x * 4^(q-qe)]     - #{short u$ padded to that start, |u| >= qe},
+//   r = bound[(x+1) * 4^(q-qe)] - #{short u$ padded to that end}.
 __device__ __forceinline__ void seed_interval(const IndexView &ix, uint32_t code, uint32_t qe,
                                               uint32_t &l, uint32_t &r)
 {
     uint32_t sh = 2 * (ix.q - qe);
-    l = __ldg(ix.table + ((size_t)code << sh));
-    r = __ldg(ix.table + ((size_t)(code + 1) << sh));
+    uint32_t start = code << sh, end = (code + 1) << sh;
+    l = __ldg(ix.table + (size_t)start);
+    r = __ldg(ix.table + (size_t)end);
+    for (uint32_t t = 0; t < ix.nshort; t++) {
+        l -= (ix.short_pad[t] == start && ix.short_len[t] >= qe);
+        r -= (ix.short_pad[t] == end);
+    }
 }
 
 }  // namespace mica

@@ -223,8 +223,11 @@ def sample_reads(genome: Genome, lengths: np.ndarray, k: np.ndarray, rng: np.ran
         o = a + (rng.random(len(ridx)) * (b - a + 1)).astype(np.int64)
         origin[pick] = np.minimum(o, n_total - lengths[pick])
     strand = rng.integers(0, 2, size=n, dtype=np.uint8)
-    reads = []
     n_subs = np.zeros(n, dtype=np.int32)
+    nw = (lengths + 15) // 16
+    off = np.zeros(n + 1, dtype=np.uint64)
+    np.cumsum(nw, out=off[1:])
+    words = np.zeros(int(off[-1]), dtype=np.uint32)
     for m in np.unique(lengths):
         idx = np.flatnonzero(lengths == m)
         mat = g[origin[idx][:, None] + np.arange(m)[None, :]]
@@ -245,10 +248,8 @@ def sample_reads(genome: Genome, lengths: np.ndarray, k: np.ndarray, rng: np.ran
             n_subs[idx] = hit.sum(axis=1)
         else:
             raise ValueError(subs)
-        for j, i in enumerate(idx):
-            reads.append((int(i), mat[j]))
-    reads.sort(key=lambda t: t[0])
-    words, off, lens = pack_reads([r for _, r in reads])
+        _pack_group(words, off, idx, mat.astype(np.uint32))
+    lens = lengths.astype(np.uint16)
     return ReadBatch(words, off, lens, np.asarray(k, dtype=np.uint8), origin, strand, n_subs)
 
 
@@ -281,9 +282,9 @@ def genome_64m(n: int = 1 << 26) -> Genome:
     return repeat_genome(n, SEED_GENOME_64M)
 
 
-def reads_64m(genome: Genome, n: int = 1_000_000, m: int = 150) -> ReadBatch:
+def reads_64m(genome: Genome, n: int = 1_000_000, m: int = 150, seed: int = SEED_READS_64M) -> ReadBatch:
     """1M reads of 150 bp with 1% i.i.d. substitution error, k = 2."""
-    rng = _rng(SEED_READS_64M)
+    rng = _rng(seed)
     return sample_reads(genome, np.full(n, m), np.full(n, 2), rng, subs="rate", sub_rate=0.01)
 
 

@@ -62,23 +62,26 @@ def test_locate_every_row_small(sa_sample):
 
 
 @pytest.mark.parametrize("q", [1, 4, 8, 12])
-def test_qmer_table_bounds_are_sa_intervals(q):
+def test_seed_intervals_are_sa_intervals(q):
+    """Every length <= q: the table lookup equals exact backward search,
+    including the codes next to the genome's last bases (short suffixes)."""
     g = synth.repeat_genome(20_000, 2, copy_frac=0.1, copy_len=(200, 1000), tandem_frac=0.05).codes
     idx = gc.mica().Index.build(synth.to_acgt_bytes(g), kmer_q=q, sa_sample=16)
     fm = oracle.FMIndex(g)
     rng = np.random.default_rng(q)
-    ncode = 4 ** q
-    codes = np.unique(np.concatenate([rng.integers(0, ncode, 500), [0, ncode - 1]]))
-    lo = idx.debug_table(codes)
-    hi = idx.debug_table(codes + 1)
-    for x, l, r in zip(codes, lo, hi):
-        p = np.array([(int(x) >> (2 * (q - 1 - t))) & 3 for t in range(q)], np.uint8)
-        el, er = fm.exact_interval(p)
-        if el == er:
-            assert l == r
-        else:
-            assert (l, r) == (el, er)
-    assert int(idx.debug_table([ncode])[0]) == g.size + 1
+    for length in sorted({1, max(1, q // 2), q}):
+        ncode = 4 ** length
+        tail = [int("".join(str(int(c)) for c in g[len(g) - j:][:length]).ljust(length, "0"), 4)
+                for j in range(1, length + 1)]
+        near = [min(ncode - 1, c + d) for c in tail for d in (-1, 0, 1) if c + d >= 0]
+        codes = np.unique(np.concatenate([rng.integers(0, ncode, 400), [0, ncode - 1], near])).astype(np.uint32)
+        got = idx.debug_seed_interval(codes, length)
+        for x, (l, r) in zip(codes, got):
+            p = np.array([(int(x) >> (2 * (length - 1 - t))) & 3 for t in range(length)], np.uint8)
+            el, er = fm.exact_interval(p)
+            assert (r - l) == (er - el) == refcheck.count_occurrences(g, p)
+            if el < er:
+                assert (int(l), int(r)) == (el, er)
 
 
 def test_save_load_roundtrip(tmp_path):
