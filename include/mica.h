@@ -64,12 +64,16 @@ typedef struct {
     uint32_t sa_sample;  /* text sampling rate s, 1..256: SA[j] kept when SA[j] % s == 0 */
 } mica_index_params;
 
-enum { MICA_KERNEL_PERSISTENT = 0, MICA_KERNEL_PLAIN = 1 };
+enum {
+    MICA_KERNEL_PERSISTENT = 0,      /* one launch of the warp-cooperative work-pool kernel */
+    MICA_KERNEL_PLAIN = 1,           /* one launch of the one-task-per-thread kernel over the batch */
+    MICA_KERNEL_PLAIN_BY_LENGTH = 2  /* one plain launch per read-length class (1-64, 65-128,
+                                        129-192, 193-256 bases), each with its own block size */
+};
 
 typedef struct {
     uint32_t hit_cap;    /* listed hits per read; 0 = no cap (every hit listed) */
-    int32_t kernel;      /* MICA_KERNEL_PERSISTENT (warp-cooperative work pool) or
-                            MICA_KERNEL_PLAIN (one (read, strand) task per thread) */
+    int32_t kernel;      /* MICA_KERNEL_* */
     void *cuda_stream;   /* cudaStream_t to run on; NULL = the legacy default stream */
 } mica_align_params;
 
@@ -113,6 +117,7 @@ typedef struct {
     uint64_t launches;       /* CUDA kernels this library launched for the call */
     uint64_t warp_rounds;    /* persistent kernel: work-pool rounds over all warps */
     uint64_t lane_ops;       /* persistent kernel: node extensions + seed lookups done by lanes */
+    uint64_t rounds_multi, rounds_single, rounds_seed;   /* persistent kernel rounds by kind of work */
     float search_ms;         /* device time of the search phase (kernel + its control copies) */
     float kernel_ms;         /* device time of the search kernel launch(es) alone */
     float total_ms;          /* device time of the whole call */
@@ -176,6 +181,39 @@ int mica_align_device(mica_index *idx, const uint32_t *d_packed_reads, const uin
                       const mica_align_params *params, mica_device_result *out);
 
 int mica_get_stats(const mica_index *idx, mica_stats *out);
+
+/* ---- tuning of the search launch (no effect on results) ---- */
+typedef struct {
+    int32_t shape;          /* persistent kernel shape, 0 .. mica_tuning_shapes()-1; -1 = default */
+    uint32_t plain_block;   /* plain kernel threads per block (32..512, multiple of 32); 0 = 128 */
+    uint32_t plain_budget;  /* plain kernel node expansions per task before its rest is re-queued
+                               on the device; 0 = 65536 */
+    uint32_t plain_block_len[4];  /* MICA_KERNEL_PLAIN_BY_LENGTH: block size per length class;
+                                     0 = plain_block */
+} mica_tuning;
+
+/* Number of compiled persistent kernel shapes; mica_tuning_shape_info
+   describes one: shared-memory node stack per warp, warps per CTA, minimum
+   resident CTAs per SM the registers were limited for. */
+int mica_tuning_shapes(void);
+int mica_tuning_shape_info(int shape, int *stack_nodes, int *warps_per_cta, int *min_ctas_per_sm);
+int mica_set_tuning(mica_index *idx, const mica_tuning *t);
+int mica_get_tuning(const mica_index *idx, mica_tuning *t);
+
+/* Autotuner: time every persistent kernel shape and the plain kernel's block
+   size (over the batch and per read-length class, on that class's reads) on
+   a host sample batch, `repeats` timed runs after one warm-up each, and keep
+   the fastest in the index's tuning (also copied to *out unless NULL). */
+int mica_autotune(mica_index *idx, const uint32_t *packed_reads, const uint64_t *word_offsets,
+                  const uint16_t *lengths, const uint8_t *k, uint64_t n_reads, uint32_t hit_cap, uint32_t repeats,
+                  mica_tuning *out);
+/* Tuning cache file (text, one line per key).  The key is the GPU name, the
+   genome length, kmer_q, a bit mask of the read-length classes present and the
+   largest k.  lookup returns MICA_ENOTFOUND when the key is absent. */
+int mica_tuning_cache_store(const char *path, const mica_index *idx, uint32_t length_classes, uint32_t kmax,
+                            const mica_tuning *t);
+int mica_tuning_cache_lookup(const char *path, const mica_index *idx, uint32_t length_classes, uint32_t kmax,
+                             mica_tuning *t);
 
 /* ---- serving: continuous batching over a resident index ----
  *

@@ -30,7 +30,7 @@ MICA_EINTERNAL = -6
 MICA_EBUSY = -7
 MICA_ENOTFOUND = -8
 MAX_READ_LEN = 256
-KERNELS = {"persistent": 0, "plain": 1}
+KERNELS = {"persistent": 0, "plain": 1, "plain_by_length": 2}
 
 HIT_DTYPE = np.dtype([("pos", "<u4"), ("strand", "u1"), ("mm", "u1"), ("pad", "<u2")])
 
@@ -62,11 +62,28 @@ class _DeviceResult(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_uint64) for name in
                 ("tasks", "seeds", "nodes", "rank_blocks", "intervals", "located", "lf_steps",
-                 "spills", "retries", "launches", "warp_rounds", "lane_ops")] + [("search_ms", ctypes.c_float), ("kernel_ms", ctypes.c_float),
+                 "spills", "retries", "launches", "warp_rounds", "lane_ops", "rounds_multi", "rounds_single",
+                 "rounds_seed")] + [("search_ms", ctypes.c_float), ("kernel_ms", ctypes.c_float),
                                                       ("total_ms", ctypes.c_float)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("shape", ctypes.c_int32), ("plain_block", ctypes.c_uint32), ("plain_budget", ctypes.c_uint32),
+                ("plain_block_len", ctypes.c_uint32 * 4)]
+
+
+def tuning_shapes() -> list:
+    """[(stack_nodes, warps_per_cta, min_ctas_per_sm)] of the compiled persistent kernel shapes."""
+    out = []
+    for i in range(_lib.mica_tuning_shapes()):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(_lib.mica_tuning_shape_info(i, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+               "mica_tuning_shape_info")
+        out.append((a.value, b.value, c.value))
+    return out
 
 
 class ServerParams(ctypes.Structure):
@@ -109,6 +126,13 @@ SIGNATURES = {
     "mica_debug_occ": (_i32, [P, P, _u64, P]),
     "mica_debug_locate": (_i32, [P, P, _u64, P]),
     "mica_debug_seed_interval": (_i32, [P, P, _u32, _u64, P]),
+    "mica_tuning_shapes": (_i32, []),
+    "mica_tuning_shape_info": (_i32, [_i32, P, P, P]),
+    "mica_set_tuning": (_i32, [P, P]),
+    "mica_get_tuning": (_i32, [P, P]),
+    "mica_autotune": (_i32, [P, P, P, P, P, _u64, _u32, _u32, P]),
+    "mica_tuning_cache_store": (_i32, [ctypes.c_char_p, P, _u32, _u32, P]),
+    "mica_tuning_cache_lookup": (_i32, [ctypes.c_char_p, P, _u32, _u32, P]),
     "mica_server_params_default": (None, [P]),
     "mica_server_start": (_i32, [P, P, P]),
     "mica_server_submit": (_i32, [P, P, P, P, P, _u64, P]),
@@ -263,6 +287,38 @@ class Index:
         d = {name: getattr(i, name) for name, _ in IndexInfo._fields_}
         d["C"] = list(i.C)
         return d
+
+    def set_tuning(self, shape: int = -1, plain_block: int = 0, plain_budget: int = 0, plain_block_len=(0, 0, 0, 0)):
+        t = Tuning(shape, plain_block, plain_budget, (ctypes.c_uint32 * 4)(*plain_block_len))
+        _check(_lib.mica_set_tuning(self._h, ctypes.byref(t)), "mica_set_tuning")
+
+    def autotune(self, batch, hit_cap: int = 1000, repeats: int = 2, cache: str | None = None) -> dict:
+        """Pick the fastest launch shapes on `batch` (or reuse a cached choice)."""
+        words = np.ascontiguousarray(batch.words, dtype=np.uint32)
+        off = np.ascontiguousarray(batch.word_off, dtype=np.uint64)
+        lens = np.ascontiguousarray(batch.lengths, dtype=np.uint16)
+        k = np.ascontiguousarray(batch.k, dtype=np.uint8)
+        classes = 0
+        for c, (lo, hi) in enumerate(((1, 64), (65, 128), (129, 192), (193, 256))):
+            if np.any((lens >= lo) & (lens <= hi)):
+                classes |= 1 << c
+        kmax = int(k.max()) if k.size else 0
+        t = Tuning()
+        if cache and _lib.mica_tuning_cache_lookup(os.fsencode(cache), self._h, classes, kmax, ctypes.byref(t)) == 0:
+            _check(_lib.mica_set_tuning(self._h, ctypes.byref(t)), "mica_set_tuning")
+            return self.tuning()
+        _check(_lib.mica_autotune(self._h, _ptr(words), _ptr(off), _ptr(lens), _ptr(k), lens.size, hit_cap, repeats,
+                                  ctypes.byref(t)), "mica_autotune")
+        if cache:
+            _check(_lib.mica_tuning_cache_store(os.fsencode(cache), self._h, classes, kmax, ctypes.byref(t)),
+                   "mica_tuning_cache_store")
+        return self.tuning()
+
+    def tuning(self) -> dict:
+        t = Tuning()
+        _check(_lib.mica_get_tuning(self._h, ctypes.byref(t)), "mica_get_tuning")
+        return {"shape": t.shape, "plain_block": t.plain_block, "plain_budget": t.plain_budget,
+                "plain_block_len": list(t.plain_block_len)}
 
     def stats(self) -> dict:
         s = Stats()

@@ -47,7 +47,7 @@ void free_workspace(Workspace &w)
 {
     DevBuf *all[] = {&w.ctl, &w.iv, &w.iv_sorted, &w.iv_cnt, &w.iv_off, &w.total, &w.keep, &w.hit_off,
                      &w.hits, &w.spill, &w.big, &w.scan_tmp, &w.reads_words, &w.reads_off, &w.reads_len,
-                     &w.reads_k, &w.spill2};
+                     &w.reads_k, &w.spill2, &w.lenlist};
     for (DevBuf *b : all) dev_release(*b);
     for (auto &e : w.ev)
         if (e) { cudaEventDestroy(e); e = nullptr; }
@@ -96,7 +96,7 @@ struct FileHeader {
     uint32_t version, kmer_q, sa_sample, reserved;
     uint64_t n, dollar_row;
     uint64_t C[5];
-    uint64_t n_occ_blocks, n_mark_blocks, n_samples, table_len;
+    uint64_t n_occ_blocks, n_super, n_mark_blocks, n_samples, table_len;
     uint32_t nshort, short_pad[MAX_Q], short_len[MAX_Q];
 };
 
@@ -138,8 +138,11 @@ int align_on_device(const mica_index *idx, Workspace &w, mica_stats &st, const R
     MICA_CUDA_TRY(cudaEventRecord(w.ev[0], s));
     SearchConfig cfg{};
     cfg.kernel = p.kernel;
-    cfg.plain_block = 128;
-    cfg.plain_budget = 1u << 16;
+    cfg.shape = idx->tuning.shape;
+    cfg.plain_block = idx->tuning.plain_block ? (int)idx->tuning.plain_block : 128;
+    cfg.plain_budget = idx->tuning.plain_budget ? idx->tuning.plain_budget : (1u << 16);
+    for (uint32_t c = 0; c < LEN_CLASSES; c++)
+        cfg.plain_block_len[c] = idx->tuning.plain_block_len[c] ? (int)idx->tuning.plain_block_len[c] : cfg.plain_block;
     int rc = run_search(idx, w, st, rd, cfg, s);
     if (rc) return rc;
     MICA_CUDA_TRY(cudaEventRecord(w.ev[1], s));
@@ -238,13 +241,14 @@ int mica_index_save(const mica_index *idx, const char *path)
     if (!f) return MICA_EIO;
     FileHeader h{};
     memcpy(h.magic, MAGIC, 8);
-    h.version = 1;
+    h.version = 2;
     h.kmer_q = idx->params.kmer_q;
     h.sa_sample = idx->params.sa_sample;
     h.n = idx->n;
     h.dollar_row = idx->view.dollar_row;
     for (int c = 0; c < 5; c++) h.C[c] = idx->view.C[c];
     h.n_occ_blocks = idx->n_occ_blocks;
+    h.n_super = idx->n_super;
     h.n_mark_blocks = idx->n_mark_blocks;
     h.n_samples = idx->n_samples;
     h.table_len = idx->table_len;
@@ -254,7 +258,8 @@ int mica_index_save(const mica_index *idx, const char *path)
         h.short_len[t] = idx->view.short_len[t];
     }
     int rc = fwrite(&h, sizeof(h), 1, f) == 1 ? 0 : MICA_EIO;
-    if (!rc) rc = write_array(f, idx->occ, h.n_occ_blocks * 64);
+    if (!rc) rc = write_array(f, idx->occ, h.n_occ_blocks * 32);
+    if (!rc) rc = write_array(f, idx->super, h.n_super * 16);
     if (!rc) rc = write_array(f, idx->marks, h.n_mark_blocks * 64);
     if (!rc) rc = write_array(f, idx->samples, h.n_samples * 4);
     if (!rc) rc = write_array(f, idx->table, h.table_len * 4);
@@ -269,9 +274,10 @@ int mica_index_load(const char *path, int device, mica_index **out)
     FILE *f = fopen(path, "rb");
     if (!f) return MICA_EIO;
     FileHeader h{};
-    if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, MAGIC, 8) != 0 || h.version != 1 ||
+    if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, MAGIC, 8) != 0 || h.version != 2 ||
         h.kmer_q < 1 || h.kmer_q > MAX_Q || h.sa_sample < 1 || h.n + 1 >= (1ull << 32) ||
-        h.n_occ_blocks != (h.n + 1) / OCC_ROWS + 1 || h.n_mark_blocks != (h.n + 1) / MARK_ROWS + 1 ||
+        h.n_occ_blocks != (h.n + 1) / OCC_ROWS + 1 ||
+        h.n_super != (h.n_occ_blocks + SB_BLOCKS - 1) / SB_BLOCKS || h.n_mark_blocks != (h.n + 1) / MARK_ROWS + 1 ||
         h.table_len != (1ull << (2 * h.kmer_q)) + 1 || h.n_samples > h.n + 1 ||
         h.nshort != std::min<uint64_t>(h.kmer_q, h.n + 1)) {
         fclose(f);
@@ -286,10 +292,12 @@ int mica_index_load(const char *path, int device, mica_index **out)
     idx->params.sa_sample = h.sa_sample;
     idx->n = h.n;
     idx->n_occ_blocks = h.n_occ_blocks;
+    idx->n_super = h.n_super;
     idx->n_mark_blocks = h.n_mark_blocks;
     idx->n_samples = h.n_samples;
     idx->table_len = h.table_len;
-    int rc = read_array(f, idx->occ, h.n_occ_blocks * 64);
+    int rc = read_array(f, idx->occ, h.n_occ_blocks * 32);
+    if (!rc) rc = read_array(f, idx->super, h.n_super * 16);
     if (!rc) rc = read_array(f, idx->marks, h.n_mark_blocks * 64);
     if (!rc) rc = read_array(f, idx->samples, h.n_samples * 4);
     if (!rc) rc = read_array(f, idx->table, h.table_len * 4);
@@ -297,6 +305,7 @@ int mica_index_load(const char *path, int device, mica_index **out)
     if (!rc) {
         IndexView &v = idx->view;
         v.occ = (const uint4 *)idx->occ.p;
+        v.super = (const uint4 *)idx->super.p;
         v.marks = (const uint4 *)idx->marks.p;
         v.samples = (const uint32_t *)idx->samples.p;
         v.table = (const uint32_t *)idx->table.p;
@@ -311,6 +320,8 @@ int mica_index_load(const char *path, int device, mica_index **out)
             v.short_pad[t] = h.short_pad[t];
             v.short_len[t] = h.short_len[t];
         }
+        v.short_bloom = 0;
+        for (uint32_t t = 0; t < v.nshort; t++) v.short_bloom |= 1ull << (v.short_pad[t] & 63);
         rc = upload_variants(idx);
     }
     if (rc) { mica_index_free(idx); return rc; }
@@ -324,6 +335,7 @@ void mica_index_free(mica_index *idx)
     DeviceGuard g(idx->device);
     cudaSetDevice(idx->device);
     dev_release(idx->occ);
+    dev_release(idx->super);
     dev_release(idx->marks);
     dev_release(idx->samples);
     dev_release(idx->table);
@@ -341,7 +353,7 @@ int mica_index_get_info(const mica_index *idx, mica_index_info *info)
     info->sa_sample = idx->params.sa_sample;
     info->dollar_row = idx->view.dollar_row;
     for (int c = 0; c < 5; c++) info->C[c] = idx->view.C[c];
-    info->occ_bytes = idx->n_occ_blocks * 64;
+    info->occ_bytes = idx->n_occ_blocks * 32 + idx->n_super * 16;
     info->mark_bytes = idx->n_mark_blocks * 64;
     info->sample_bytes = idx->n_samples * 4;
     info->table_bytes = idx->table_len * 4;
@@ -353,6 +365,33 @@ int mica_get_stats(const mica_index *idx, mica_stats *out)
 {
     if (!idx || !out) return MICA_EINVAL;
     *out = idx->stats;
+    return 0;
+}
+
+int mica_tuning_shapes(void) { return search_shape_count(); }
+
+int mica_tuning_shape_info(int shape, int *stack_nodes, int *warps_per_cta, int *min_ctas_per_sm)
+{
+    return search_shape_info(shape, stack_nodes, warps_per_cta, min_ctas_per_sm);
+}
+
+int mica_set_tuning(mica_index *idx, const mica_tuning *t)
+{
+    if (!idx || !t) return MICA_EINVAL;
+    if (t->shape < -1 || t->shape >= search_shape_count()) return MICA_EINVAL;
+    if (t->plain_block && (t->plain_block < 32 || t->plain_block > 512 || t->plain_block % 32)) return MICA_EINVAL;
+    for (uint32_t c = 0; c < LEN_CLASSES; c++)
+        if (t->plain_block_len[c] &&
+            (t->plain_block_len[c] < 32 || t->plain_block_len[c] > 512 || t->plain_block_len[c] % 32))
+            return MICA_EINVAL;
+    idx->tuning = *t;
+    return 0;
+}
+
+int mica_get_tuning(const mica_index *idx, mica_tuning *t)
+{
+    if (!idx || !t) return MICA_EINVAL;
+    *t = idx->tuning;
     return 0;
 }
 
@@ -419,7 +458,7 @@ int mica_align_device(mica_index *idx, const uint32_t *d_packed_reads, const uin
     mica_align_params p;
     mica_align_params_default(&p);
     if (params) p = *params;
-    if (p.kernel != MICA_KERNEL_PERSISTENT && p.kernel != MICA_KERNEL_PLAIN) return MICA_EINVAL;
+    if (p.kernel < MICA_KERNEL_PERSISTENT || p.kernel > MICA_KERNEL_PLAIN_BY_LENGTH) return MICA_EINVAL;
     DeviceGuard g(idx->device);
     MICA_CUDA_TRY(cudaSetDevice(idx->device));
     cudaStream_t s = (cudaStream_t)p.cuda_stream;
@@ -447,6 +486,7 @@ int mica_align_batch(mica_index *idx, const uint32_t *packed_reads, const uint64
     mica_align_params p;
     mica_align_params_default(&p);
     if (params) p = *params;
+    if (p.kernel < MICA_KERNEL_PERSISTENT || p.kernel > MICA_KERNEL_PLAIN_BY_LENGTH) return MICA_EINVAL;
     DeviceGuard g(idx->device);
     MICA_CUDA_TRY(cudaSetDevice(idx->device));
     cudaStream_t s = (cudaStream_t)p.cuda_stream;

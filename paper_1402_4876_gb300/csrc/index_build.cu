@@ -5,8 +5,9 @@
 //   1. suffix array of T = G$ by prefix doubling: sort positions by their
 //      first 21 symbols (3 bits each), then repeatedly by (rank[i], rank[i+h])
 //      with h doubling, until all ranks are distinct;
-//   2. BWT[j] = T[SA[j]-1], packed 2 bits/row into 64-byte blocks of 192 rows
-//      that start with the absolute counts Occ(A..T, block start);
+//   2. BWT[j] = T[SA[j]-1] as two bit planes in 32-byte blocks of 96 rows
+//      that start with Occ(A..T, block start) relative to a superblock of
+//      682 blocks, whose absolute counts sit in a small separate table;
 //   3. mark bits for rows with SA[j] % s == 0 (64-byte blocks of 480 rows that
 //      start with the number of marked rows before them) and the sampled SA
 //      values in row order;
@@ -183,28 +184,39 @@ __global__ void k_occ_counts(const uint32_t *__restrict__ sa, const uint8_t *__r
     }
 }
 
+__global__ void k_occ_super(const uint4 *__restrict__ base, uint64_t nblocks, uint64_t nsuper,
+                            uint4 *__restrict__ super)
+{
+    for (uint64_t sb = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; sb < nsuper;
+         sb += (uint64_t)gridDim.x * blockDim.x)
+        super[sb] = base[sb * SB_BLOCKS];
+}
+
 __global__ void k_occ_blocks(const uint32_t *__restrict__ sa, const uint8_t *__restrict__ codes,
                              uint64_t rows, uint64_t nblocks, const uint4 *__restrict__ base,
-                             uint32_t *__restrict__ occ)
+                             const uint4 *__restrict__ super, uint32_t *__restrict__ occ)
 {
     for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < nblocks;
          b += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t *blk = occ + b * OCC_WORDS;
-        uint4 c = base[b];
-        blk[0] = c.x; blk[1] = c.y; blk[2] = c.z; blk[3] = c.w;
+        uint4 c = base[b], sp = super[b / SB_BLOCKS];
+        blk[0] = (c.x - sp.x) | ((c.y - sp.y) << 16);
+        blk[1] = (c.z - sp.z) | ((c.w - sp.w) << 16);
         uint64_t j0 = b * OCC_ROWS;
-        for (int w = 0; w < 12; w++) {
-            uint32_t word = 0;
-            for (int t = 0; t < 16; t++) {
-                uint64_t j = j0 + w * 16 + t;
+        for (int w = 0; w < 3; w++) {
+            uint32_t lo = 0, hi = 0;
+            for (int t = 0; t < 32; t++) {
+                uint64_t j = j0 + w * 32 + t;
                 uint32_t sym = 0;
                 if (j < rows) {
                     uint32_t i = sa[j];
                     sym = i == 0 ? 0u : codes[i - 1];     // $ stored as A
                 }
-                word |= sym << (2 * t);
+                lo |= (sym & 1u) << t;
+                hi |= (sym >> 1) << t;
             }
-            blk[4 + w] = word;
+            blk[2 + 2 * w] = lo;
+            blk[3 + 2 * w] = hi;
         }
     }
 }
@@ -361,10 +373,12 @@ int build_index_from_codes(const uint8_t *d_codes, uint64_t n, const mica_index_
     if ((rc = build_suffix_array(d_codes, n, (uint32_t *)sa.p, s))) { cleanup(); return rc; }
     const uint32_t *d_sa = (const uint32_t *)sa.p;
 
-    // occurrence blocks
+    // occurrence blocks and superblocks
     uint64_t nb = rows / OCC_ROWS + 1;
+    uint64_t nsb = (nb + SB_BLOCKS - 1) / SB_BLOCKS;
     if ((rc = dev_reserve(cnt, nb * 16)) || (rc = dev_reserve(base, nb * 16)) ||
-        (rc = dev_reserve(dr, 16)) || (rc = dev_reserve(idx->occ, nb * 64))) { cleanup(); return rc; }
+        (rc = dev_reserve(dr, 16)) || (rc = dev_reserve(idx->occ, nb * 32)) ||
+        (rc = dev_reserve(idx->super, nsb * 16))) { cleanup(); return rc; }
     int g = grid_for(nb);
     k_occ_counts<<<g, 256, 0, s>>>(d_sa, d_codes, rows, nb, (uint4 *)cnt.p, (uint32_t *)dr.p);
     {
@@ -375,7 +389,9 @@ int build_index_from_codes(const uint8_t *d_codes, uint64_t n, const mica_index_
         MICA_CUDA_TRY(cub::DeviceScan::ExclusiveScan(tmp.p, need, (const uint4 *)cnt.p, (uint4 *)base.p,
                                                      Sum4(), make_uint4(0, 0, 0, 0), (int64_t)nb, s));
     }
-    k_occ_blocks<<<g, 256, 0, s>>>(d_sa, d_codes, rows, nb, (const uint4 *)base.p, (uint32_t *)idx->occ.p);
+    k_occ_super<<<grid_for(nsb), 256, 0, s>>>((const uint4 *)base.p, nb, nsb, (uint4 *)idx->super.p);
+    k_occ_blocks<<<g, 256, 0, s>>>(d_sa, d_codes, rows, nb, (const uint4 *)base.p, (const uint4 *)idx->super.p,
+                                   (uint32_t *)idx->occ.p);
     uint32_t dollar = 0;
     MICA_CUDA_TRY(cudaMemcpyAsync(&dollar, dr.p, 4, cudaMemcpyDeviceToHost, s));
     // totals for C[]: base of the last block holds Occ(c, rows) since rows < nb*192
@@ -422,11 +438,13 @@ int build_index_from_codes(const uint8_t *d_codes, uint64_t n, const mica_index_
         if (!tail.empty())
             MICA_CUDA_TRY(cudaMemcpy(tail.data(), d_codes + first, tail.size(), cudaMemcpyDeviceToHost));
         idx->view.nshort = 0;
+        idx->view.short_bloom = 0;
         for (uint64_t i = first; i <= n; i++) {
             uint32_t code = 0;
             for (uint32_t t = 0; t < q; t++) code = (code << 2) | (i + t < n ? tail[i + t - first] : 0u);
             idx->view.short_len[idx->view.nshort] = (uint32_t)(n - i);
             idx->view.short_pad[idx->view.nshort++] = code;
+            idx->view.short_bloom |= 1ull << (code & 63);
         }
     }
     DevBuf tcnt;
@@ -448,11 +466,13 @@ int build_index_from_codes(const uint8_t *d_codes, uint64_t n, const mica_index_
     idx->n = n;
     idx->params = p;
     idx->n_occ_blocks = nb;
+    idx->n_super = nsb;
     idx->n_mark_blocks = nm;
     idx->n_samples = nsamp;
     idx->table_len = tl;
     IndexView &v = idx->view;
     v.occ = (const uint4 *)idx->occ.p;
+    v.super = (const uint4 *)idx->super.p;
     v.marks = (const uint4 *)idx->marks.p;
     v.samples = (const uint32_t *)idx->samples.p;
     v.table = (const uint32_t *)idx->table.p;

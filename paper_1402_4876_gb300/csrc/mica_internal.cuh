@@ -13,11 +13,17 @@ namespace mica {
 // ---------------------------------------------------------------------------
 // Index layout constants
 // ---------------------------------------------------------------------------
-// Occurrence block: 64 bytes = 4 x uint32 counts Occ(A..T, block start)
-// followed by 12 x uint32 words holding 192 BWT symbols, 2 bits each,
-// least-significant first ($ is stored as A and corrected with dollar_row).
-constexpr uint32_t OCC_ROWS = 192;
-constexpr uint32_t OCC_WORDS = 16;        // uint32 per block
+// Occurrence block: 32 bytes (one sector) for 96 BWT rows =
+//   u32 [A | C << 16], u32 [G | T << 16]: Occ(c, block start) minus the
+//        counts at the start of the block's superblock (16 bits each);
+//   then for rows 0-31, 32-63, 64-95 in turn a low-bit word and a high-bit
+//   word (row t at bit t % 32; symbol code = low | high << 1; $ is stored as
+//   A and corrected with dollar_row).
+// Superblock: SB_BLOCKS consecutive blocks (65,472 rows, so the 16-bit
+// relative counts cannot overflow); its 16-byte entry holds Occ(A..T, start).
+constexpr uint32_t OCC_ROWS = 96;
+constexpr uint32_t OCC_WORDS = 8;         // uint32 per block
+constexpr uint32_t SB_BLOCKS = 682;
 // Mark block: 64 bytes = uint32 rank of marked rows before the block + 15
 // words of mark bits (480 rows).
 constexpr uint32_t MARK_ROWS = 480;
@@ -35,7 +41,8 @@ __host__ __device__ __forceinline__ uint32_t var_off(uint32_t k)
 
 // Device view of a resident index, passed to kernels by value.
 struct IndexView {
-    const uint4 *occ;          // blocks * 4 uint4
+    const uint4 *occ;          // blocks * 2 uint4
+    const uint4 *super;        // superblocks: Occ(A..T, superblock start)
     const uint4 *marks;        // mark blocks * 4 uint4
     const uint32_t *samples;   // SA values of marked rows, in row order
     const uint32_t *table;     // 4^q + 1 bounds
@@ -54,6 +61,7 @@ struct IndexView {
     uint32_t nshort;
     uint32_t short_pad[MAX_Q];
     uint32_t short_len[MAX_Q];
+    unsigned long long short_bloom;   // bit (pad & 63) of every short pad: a cheap pre-check
 };
 
 // Read batch in device memory.
@@ -105,6 +113,7 @@ struct SearchCtl {
     unsigned int pad_;
     unsigned long long seeds, nodes, rank_blocks, spills;
     unsigned long long rounds, lane_ops;
+    unsigned long long rounds_kind[3];   // multi-row, single-row, seed rounds
 };
 
 constexpr unsigned ERR_IV_OVERFLOW = 1u;
@@ -128,6 +137,7 @@ struct Workspace {
     DevBuf ctl, iv, iv_sorted, iv_cnt, iv_off, total, keep, hit_off, hits, spill, big, scan_tmp;
     DevBuf reads_words, reads_off, reads_len, reads_k;   // staging for host batches
     DevBuf spill2;                                        // plain kernel re-queue ping-pong
+    DevBuf lenlist;                                       // plain kernel: reads by length class
     uint32_t iv_cap = 0, spill_cap = 0;
     uint64_t hit_cap_total = 0;
     bool spill_dirty = false;
@@ -142,10 +152,11 @@ struct mica_index {
     mica_index_params params{};
     mica::IndexView view{};
     uint64_t n = 0;
-    uint64_t n_occ_blocks = 0, n_mark_blocks = 0, n_samples = 0, table_len = 0;
-    mica::DevBuf occ, marks, samples, table, variants;
+    uint64_t n_occ_blocks = 0, n_super = 0, n_mark_blocks = 0, n_samples = 0, table_len = 0;
+    mica::DevBuf occ, super, marks, samples, table, variants;
     mica::Workspace ws;
     mica_stats stats{};
+    mica_tuning tuning{-1, 0, 0, {0, 0, 0, 0}};
 };
 
 namespace mica {
@@ -172,13 +183,18 @@ uint32_t variant_count(uint32_t q, uint32_t k);
 // search.cu
 struct SearchConfig {
     int kernel;                 // MICA_KERNEL_*
+    int shape = -1;             // persistent kernel shape (index into the compiled shapes), -1 = default
     int block_threads;          // persistent: threads per block
     int blocks_per_sm;
     int plain_block;
     uint32_t plain_budget;      // plain: node expansions per task before re-queueing
+    int plain_block_len[4] = {0, 0, 0, 0};   // plain by length: block size per class
 };
+constexpr uint32_t LEN_CLASSES = 4;   // 1-64, 65-128, 129-192, 193-256 bases
 int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd,
                const SearchConfig &cfg, cudaStream_t s);
+int search_shape_count();
+int search_shape_info(int shape, int *scap, int *warps, int *minb);
 
 // post.cu
 int run_post(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd, uint32_t hit_cap,

@@ -202,16 +202,12 @@ __device__ __forceinline__ uint32_t locate_row(const IndexView &ix, uint32_t j, 
         }
         // LF step: c = BWT[j] (never $: the $ row has SA = 0, which is marked)
         uint32_t b = j / OCC_ROWS, o = j - b * OCC_ROWS;
-        const uint4 *blk = ix.occ + (size_t)b * 4;
-        uint4 h = __ldg(blk);
-        uint32_t a[12];
-        load_block_words(blk, o + 1, a);
-        uint32_t c = 0;
-#pragma unroll
-        for (int x = 0; x < 12; x++)
-            if ((uint32_t)x == (o >> 4)) c = (a[x] >> (2 * (o & 15))) & 3u;
+        uint4 sup = __ldg(ix.super + b / SB_BLOCKS);
+        OccBlock k;
+        load_block(ix, b, o + 1, k);
+        uint32_t c = block_symbol(k, o);
         uint32_t occ[4];
-        occ_from(ix, b, o, h, a, occ);
+        occ_from(ix, b, o, sup, k, occ);
         uint32_t oc = c == 0 ? occ[0] : c == 1 ? occ[1] : c == 2 ? occ[2] : occ[3];
         uint32_t Cc = c == 0 ? ix.C[0] : c == 1 ? ix.C[1] : c == 2 ? ix.C[2] : ix.C[3];
         j = Cc + oc;
@@ -239,15 +235,21 @@ __device__ __forceinline__ uint64_t hit_key(uint64_t raw)
     return ((raw & 0xffffffffull) << 1) | ((raw >> 32) & 1ull);   // (pos, strand)
 }
 
+// per read: sort <= SMALL_SORT hits in place; list larger reads for the
+// block sort (from the front of `lists`) or the global sort (from the back)
 __global__ void k_sort_small(uint64_t *__restrict__ hits, const uint64_t *__restrict__ hit_off, uint64_t n,
-                             uint32_t *__restrict__ big, unsigned int *__restrict__ nbig)
+                             uint32_t *__restrict__ lists, unsigned int *__restrict__ counts)
 {
     for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n;
          r += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t b = hit_off[r], e = hit_off[r + 1];
         if (e - b <= 1) continue;
+        if (e - b > SMEM_SORT) {
+            lists[n - 1 - atomicAdd(&counts[1], 1u)] = (uint32_t)r;
+            continue;
+        }
         if (e - b > SMALL_SORT) {
-            big[atomicAdd(nbig, 1u)] = (uint32_t)r;
+            lists[atomicAdd(&counts[0], 1u)] = (uint32_t)r;
             continue;
         }
         for (uint64_t i = b + 1; i < e; i++) {
@@ -267,7 +269,6 @@ __global__ void __launch_bounds__(512) k_sort_big(uint64_t *__restrict__ hits, c
     for (unsigned bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
         uint32_t r = big[bi];
         uint64_t b = hit_off[r], cnt = hit_off[r + 1] - b;
-        if (cnt > SMEM_SORT) continue;   // handled by k_sort_global
         uint32_t P = 1;
         while (P < cnt) P <<= 1;
         for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) sh[i] = i < cnt ? hits[b + i] : ~0ull;
@@ -390,24 +391,26 @@ int run_post(const mica_index *idx, Workspace &w, mica_stats &stt, const ReadsVi
     if (nh) { k_locate<<<grid1(nh), 256, 0, s>>>(idx->view, (Hit *)w.hits.p, nh, steps); L++; }
     if (n) { k_sort_small<<<grid1(n, 128), 128, 0, s>>>((uint64_t *)w.hits.p, hit_off, n, (uint32_t *)w.big.p,
                                                        nbig); L++; }
-    unsigned int hb[4] = {0, 0, 0, 0};
+    unsigned int hb[2] = {0, 0};
     unsigned long long st = 0;
     MICA_CUDA_TRY(cudaMemcpyAsync(&st, steps, 8, cudaMemcpyDeviceToHost, s));
-    MICA_CUDA_TRY(cudaMemcpyAsync(hb, nbig, 4, cudaMemcpyDeviceToHost, s));
+    MICA_CUDA_TRY(cudaMemcpyAsync(hb, nbig, 8, cudaMemcpyDeviceToHost, s));
     MICA_CUDA_TRY(cudaStreamSynchronize(s));
     if (hb[0]) {
         k_sort_big<<<std::min(hb[0], 152u * 4), 512, 0, s>>>((uint64_t *)w.hits.p, hit_off,
                                                            (const uint32_t *)w.big.p, hb[0]);
         L++;
-        // reads above the shared-memory size: one global bitonic sort each
-        std::vector<uint32_t> bigr(hb[0]);
-        MICA_CUDA_TRY(cudaMemcpyAsync(bigr.data(), w.big.p, 4ull * hb[0], cudaMemcpyDeviceToHost, s));
+    }
+    if (hb[1]) {
+        // reads above the shared-memory size (only without a cap or with a cap above it)
+        std::vector<uint32_t> huge(hb[1]);
+        MICA_CUDA_TRY(cudaMemcpyAsync(huge.data(), (const uint32_t *)w.big.p + (n - hb[1]), 4ull * hb[1],
+                                      cudaMemcpyDeviceToHost, s));
         MICA_CUDA_TRY(cudaStreamSynchronize(s));
-        for (uint32_t r : bigr) {
+        for (uint32_t r : huge) {
             uint64_t ob[2];
             MICA_CUDA_TRY(cudaMemcpy(ob, hit_off + r, 16, cudaMemcpyDeviceToHost));
             uint64_t cnt = ob[1] - ob[0];
-            if (cnt <= SMEM_SORT) continue;
             uint64_t P = 1;
             while (P < cnt) P <<= 1;
             DevBuf scratch;

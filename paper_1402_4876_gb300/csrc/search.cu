@@ -100,7 +100,7 @@ __device__ __forceinline__ void requeue_push(const PlainArgs &a, uint32_t read, 
     if (at < a.requeue_cap) {
         WorkItem it;
         it.read = read;
-        it.meta = meta | WI_VALID;
+        it.meta = meta;   // no ready flag: only the persistent kernel's queue uses it
         it.a = x;
         it.b = y;
         a.requeue[at] = it;
@@ -109,7 +109,7 @@ __device__ __forceinline__ void requeue_push(const PlainArgs &a, uint32_t read, 
     }
 }
 
-__global__ void __launch_bounds__(128) k_plain(PlainArgs a)
+__global__ void __launch_bounds__(512) k_plain(PlainArgs a)
 {
     uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     if (t >= a.ntasks) return;
@@ -231,6 +231,28 @@ __global__ void __launch_bounds__(128) k_plain(PlainArgs a)
     }
 }
 
+// reads grouped by length class for per-length plain launches
+__device__ __forceinline__ uint32_t len_class(uint32_t m) { return m <= 64 ? 0u : m <= 128 ? 1u : m <= 192 ? 2u : 3u; }
+
+__global__ void k_len_count(ReadsView rd, unsigned int *counts)
+{
+    __shared__ unsigned int c[LEN_CLASSES];
+    if (threadIdx.x < LEN_CLASSES) c[threadIdx.x] = 0;
+    __syncthreads();
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < rd.n; i += (uint64_t)gridDim.x * blockDim.x)
+        atomicAdd(&c[len_class(rd.len[i])], 1u);
+    __syncthreads();
+    if (threadIdx.x < LEN_CLASSES && c[threadIdx.x]) atomicAdd(&counts[threadIdx.x], c[threadIdx.x]);
+}
+
+__global__ void k_len_scatter(ReadsView rd, const unsigned int *base, unsigned int *cursor, uint32_t *list)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < rd.n; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t c = len_class(rd.len[i]);
+        list[base[c] + atomicAdd(&cursor[c], 1u)] = (uint32_t)i;
+    }
+}
+
 // --------------------------------------------------------------------------
 // Persistent warp-pool kernel
 // --------------------------------------------------------------------------
@@ -240,6 +262,7 @@ constexpr uint32_t IDLE_LIMIT = 1u << 22;    // idle rounds (>= 1 us each) befor
 constexpr uint32_t SPIN_LIMIT = 1u << 22;    // waits for a reserved queue entry
 constexpr uint32_t DONATE_MIN = 96;          // stack depth that makes a warp share work
 constexpr uint32_t DONATE_N = 64;
+constexpr int DEFAULT_SHAPE = 1;
 
 struct PersistArgs {
     IndexView ix;
@@ -255,11 +278,13 @@ struct PersistArgs {
 
 template <int SCAP>
 struct WarpSmem {
-    uint32_t nl[SCAP];
-    uint32_t nr[SCAP];
-    uint16_t nm[SCAP];                    // slot | i << 5 | d << 14
+    uint32_t ml[SCAP];                    // multi-row nodes [l, r), r - l > 1
+    uint32_t mr[SCAP];
+    uint16_t mm[SCAP];                    // slot | i << 5 | d << 14
+    uint32_t sl[SCAP];                    // single-row nodes [l, l + 1)
+    uint16_t sm[SCAP];
     uint32_t pat[32][MAX_WORDS + 1];      // pattern of each task slot
-    int live[32];                         // nodes of each slot in the stack
+    int live[32];                         // nodes of each slot in the two stacks
 };
 
 __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t x, int lane)
@@ -279,8 +304,14 @@ __device__ __forceinline__ unsigned long long vload64(const unsigned long long *
     return *(const volatile unsigned long long *)p;
 }
 
-template <int SCAP>
-__device__ __forceinline__ void spill_bottom(WarpSmem<SCAP> &sm, const PersistArgs &a, uint32_t &bot,
+__device__ __forceinline__ uint16_t node_meta(uint32_t slot, uint32_t i, uint32_t d)
+{
+    return (uint16_t)(slot | (i << 5) | (d << 14));
+}
+
+// Move the `nsp` oldest nodes of one stack to the device spill queue.
+template <int SCAP, bool SINGLE>
+__device__ __forceinline__ void spill_bottom(WarpSmem<SCAP> &W, const PersistArgs &a, uint32_t &bot,
                                              uint32_t nsp, uint32_t s_read, uint32_t s_info, int lane,
                                              unsigned long long &c_spills)
 {
@@ -294,7 +325,11 @@ __device__ __forceinline__ void spill_bottom(WarpSmem<SCAP> &sm, const PersistAr
         uint32_t j = r0 + lane;
         bool act = j < nsp;
         uint32_t p = (bot + j) & (SCAP - 1);
-        uint32_t l = act ? sm.nl[p] : 0u, r = act ? sm.nr[p] : 0u, mm = act ? (uint32_t)sm.nm[p] : 0u;
+        uint32_t l = 0, r = 0, mm = 0;
+        if (act) {
+            if (SINGLE) { l = W.sl[p]; r = l + 1; mm = W.sm[p]; }
+            else { l = W.ml[p]; r = W.mr[p]; mm = W.mm[p]; }
+        }
         uint32_t sl = mm & 31u;
         uint32_t rid = __shfl_sync(FULL, s_read, sl);
         uint32_t info = __shfl_sync(FULL, s_info, sl);
@@ -309,7 +344,7 @@ __device__ __forceinline__ void spill_bottom(WarpSmem<SCAP> &sm, const PersistAr
                                 (((mm >> 5) & 511u) << 8) | (mm >> 14);
                 *(volatile uint32_t *)&it->meta = meta;
             }
-            atomicAdd(&sm.live[sl], -1);
+            atomicAdd(&W.live[sl], -1);
         }
     }
     bot += nsp;
@@ -317,35 +352,92 @@ __device__ __forceinline__ void spill_bottom(WarpSmem<SCAP> &sm, const PersistAr
     __syncwarp();
 }
 
-template <int SCAP, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) k_persistent(PersistArgs a)
+// Make room for `add` more nodes on a stack, spilling its oldest ones.
+template <int SCAP, bool SINGLE>
+__device__ __forceinline__ void make_room(WarpSmem<SCAP> &W, const PersistArgs &a, uint32_t &bot, uint32_t top,
+                                          uint32_t add, uint32_t s_read, uint32_t s_info, int lane,
+                                          unsigned long long &c_spills)
+{
+    if ((top - bot) + add > (uint32_t)SCAP) {
+        uint32_t nsp = (top - bot) + add - SCAP + SCAP / 4;
+        nsp = min((nsp + 31) & ~31u, top - bot);
+        spill_bottom<SCAP, SINGLE>(W, a, bot, nsp, s_read, s_info, lane, c_spills);
+    }
+}
+
+// Write at most one leaf interval per lane with one warp-wide atomic.
+__device__ __forceinline__ void emit_one(const PersistArgs &a, bool leaf, uint32_t rid, uint32_t d, uint32_t minus,
+                                         uint32_t l, uint32_t r, int lane, unsigned lt)
+{
+    unsigned bl = __ballot_sync(FULL, leaf);
+    if (!bl) return;
+    uint32_t at0 = 0;
+    if (lane == 0) at0 = atomicAdd(&a.ctl->iv_count, (unsigned)__popc(bl));
+    at0 = __shfl_sync(FULL, at0, 0);
+    if (leaf) {
+        atomicAdd(&a.iv_cnt[rid], 1u);
+        uint32_t q = at0 + __popc(bl & lt);
+        if (q < a.ctl->iv_cap) {
+            Interval x;
+            x.read = rid; x.meta = d | (minus << 2); x.l = l; x.r = r;
+            a.iv[q] = x;
+        } else {
+            atomicOr(&a.ctl->error, ERR_IV_OVERFLOW);
+        }
+    }
+}
+
+// Push at most one node per lane onto the stack its size selects.  Callers
+// guarantee room: admission runs with fewer than 64 nodes held and seed
+// rounds with fewer than 32 on each stack, so 32 more always fit.
+template <int SCAP>
+__device__ __forceinline__ void push_one(WarpSmem<SCAP> &W, bool push, uint32_t l, uint32_t r, uint16_t meta,
+                                         uint32_t &mtop, uint32_t &stop, unsigned lt)
+{
+    bool single = r - l == 1;
+    unsigned bm = __ballot_sync(FULL, push && !single), bs = __ballot_sync(FULL, push && single);
+    if (push && !single) {
+        uint32_t p = (mtop + __popc(bm & lt)) & (SCAP - 1);
+        W.ml[p] = l; W.mr[p] = r; W.mm[p] = meta;
+    }
+    if (push && single) {
+        uint32_t p = (stop + __popc(bs & lt)) & (SCAP - 1);
+        W.sl[p] = l; W.sm[p] = meta;
+    }
+    mtop += __popc(bm);
+    stop += __popc(bs);
+}
+
+template <int SCAP, int WARPS, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
 {
     extern __shared__ uint4 smem_raw[];
     WarpSmem<SCAP> *all = reinterpret_cast<WarpSmem<SCAP> *>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpSmem<SCAP> &sm = all[warp];
+    WarpSmem<SCAP> &W = all[warp];
     const IndexView &ix = a.ix;
     SearchCtl *ctl = a.ctl;
     const unsigned lt = (1u << lane) - 1u;
     const uint32_t spill_cap = ctl->spill_cap;
 
-    sm.live[lane] = 0;
+    W.live[lane] = 0;
     // task slot `lane`: read id, info = m | k << 9 | minus << 11 | qe << 12,
     // window code, next and end seed variant
     uint32_t s_read = 0, s_info = 0, s_code = 0, s_vnext = 0, s_vend = 0;
     bool s_used = false;
-    uint32_t bot = 0, top = 0;
+    uint32_t mbot = 0, mtop = 0, sbot = 0, stop = 0;
     bool busy = false;
     uint32_t idle_rounds = 0, backoff = 256;
-    unsigned long long c_seeds = 0, c_nodes = 0, c_blocks = 0, c_spills = 0, c_rounds = 0;
+    unsigned long long c_seeds = 0, c_nodes = 0, c_blocks = 0, c_spills = 0;
+    uint32_t c_km = 0, c_ks = 0, c_kq = 0;   // rounds by kind (warp-uniform)
     __syncwarp();
 
     for (uint32_t iter = 0;; iter++) {
         if ((iter & 15) == 0 && vload(&ctl->error) != 0) break;
 
-        if (s_used && sm.live[lane] == 0 && s_vnext >= s_vend) s_used = false;
+        if (s_used && W.live[lane] == 0 && s_vnext >= s_vend) s_used = false;
         unsigned used = __ballot_sync(FULL, s_used);
-        uint32_t cnt = top - bot;
+        uint32_t mc = mtop - mbot, sc = stop - sbot, cnt = mc + sc;
         uint32_t avail = s_used ? s_vend - s_vnext : 0u;
         uint32_t seeds_total = __reduce_add_sync(FULL, avail);
         unsigned freem = ~used;
@@ -354,7 +446,6 @@ __global__ void __launch_bounds__(WARPS * 32) k_persistent(PersistArgs a)
         if (freem != 0 && cnt + seeds_total < ADMIT_LOW) {
             bool idle = (cnt + seeds_total == 0) && used == 0;
             // an idle warp first peeks without atomics
-            int peek_work = 1;
             if (idle && !busy) {
                 int pw = 0;
                 if (lane == 0) {
@@ -371,9 +462,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_persistent(PersistArgs a)
                         }
                     }
                 }
-                peek_work = __shfl_sync(FULL, pw, 0);
-                if (peek_work < 0) break;
-                if (peek_work == 0) {
+                pw = __shfl_sync(FULL, pw, 0);
+                if (pw < 0) break;
+                if (pw == 0) {
                     if (++idle_rounds > IDLE_LIMIT) {
                         if (lane == 0) atomicOr(&ctl->error, ERR_TIMEOUT);
                         break;
@@ -409,7 +500,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_persistent(PersistArgs a)
                 uint32_t j = __popc(freem & lt);
                 bool mine = ((freem >> lane) & 1u) && j < take + got;
                 bool is_node = false;
-                uint32_t nd_l = 0, nd_r = 0, nd_m = 0;
+                uint32_t nd_l = 0, nd_r = 0, nd_i = 0, nd_d = 0;
                 if (mine) {
                     uint32_t rid, minus, vb, ve;
                     if (j < take) {
@@ -431,7 +522,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_persistent(PersistArgs a)
                         if (meta & WI_NODE) {
                             is_node = xa < xb;
                             nd_l = xa; nd_r = xb;
-                            nd_m = (uint32_t)lane | (((meta >> 8) & 511u) << 5) | ((meta & 3u) << 14);
+                            nd_i = (meta >> 8) & 511u;
+                            nd_d = meta & 3u;
                             vb = ve = 0;
                         } else {
                             vb = xa; ve = xb;
@@ -449,33 +541,27 @@ __global__ void __launch_bounds__(WARPS * 32) k_persistent(PersistArgs a)
                     s_vnext = vb;
                     s_vend = min(ve, n_variants(qe, k));
                     s_used = true;
-                    sm.live[lane] = is_node ? 1 : 0;
+                    W.live[lane] = is_node ? 1 : 0;
                 }
                 // stage the new tasks' patterns: one coalesced word per lane
-                unsigned newm = __ballot_sync(FULL, mine);
-                unsigned todo = newm;
+                unsigned todo = __ballot_sync(FULL, mine);
                 while (todo) {
                     int s = __ffs(todo) - 1;
                     todo &= todo - 1;
                     uint32_t rid = __shfl_sync(FULL, s_read, s), info = __shfl_sync(FULL, s_info, s);
                     uint32_t m = info & 511u, minus = (info >> 11) & 1u;
-                    uint32_t W = (m + 15) >> 4;
+                    uint32_t Wn = (m + 15) >> 4;
                     unsigned long long off = a.rd.word_off[rid];
-                    uint32_t raw = (uint32_t)lane < W ? a.rd.words[off + lane] : 0u;
-                    uint32_t hi = __shfl_sync(FULL, raw, (int)((W - 1 - lane) & 31u));
-                    uint32_t lo = __shfl_sync(FULL, raw, (int)((W - 2 - lane) & 31u));
-                    if ((uint32_t)lane + 1 >= W) lo = 0u;
+                    uint32_t raw = (uint32_t)lane < Wn ? a.rd.words[off + lane] : 0u;
+                    uint32_t hi = __shfl_sync(FULL, raw, (int)((Wn - 1 - lane) & 31u));
+                    uint32_t lo = __shfl_sync(FULL, raw, (int)((Wn - 2 - lane) & 31u));
+                    if ((uint32_t)lane + 1 >= Wn) lo = 0u;
                     uint32_t out = minus ? rc_word(hi, lo, m) : raw;
-                    if ((uint32_t)lane < W) sm.pat[s][lane] = out;
+                    if ((uint32_t)lane < Wn) W.pat[s][lane] = out;
                 }
                 __syncwarp();
-                if (mine) s_code = window_code(sm.pat[lane], s_info & 511u, (s_info >> 12) & 15u);
-                unsigned nodem = __ballot_sync(FULL, is_node);
-                if (is_node) {
-                    uint32_t p = (top + __popc(nodem & lt)) & (SCAP - 1);
-                    sm.nl[p] = nd_l; sm.nr[p] = nd_r; sm.nm[p] = (uint16_t)nd_m;
-                }
-                top += __popc(nodem);
+                if (mine) s_code = window_code(W.pat[lane], s_info & 511u, (s_info >> 12) & 15u);
+                push_one<SCAP>(W, is_node, nd_l, nd_r, node_meta((uint32_t)lane, nd_i, nd_d), mtop, stop, lt);
                 __syncwarp();
                 idle_rounds = 0;
                 backoff = 256;
@@ -504,134 +590,203 @@ __global__ void __launch_bounds__(WARPS * 32) k_persistent(PersistArgs a)
                 continue;
             }
         }
-
-        // ---- lanes take the newest nodes, the rest take seed variants
-        uint32_t npop = min(cnt, 32u);
-        bool has_node = (uint32_t)lane < npop;
-        uint32_t x_l = 0, x_r = 0, x_m = 0;
-        if (has_node) {
-            uint32_t p = (top - 1 - lane) & (SCAP - 1);
-            x_l = sm.nl[p]; x_r = sm.nr[p]; x_m = sm.nm[p];
-        }
-        top -= npop;
-        __syncwarp();
-        bool has_seed = false;
-        uint32_t sslot = 0, sv = 0;
-        if (seeds_total > 0 && npop < 32) {
-            uint32_t lanes_free = 32 - npop;
-            uint32_t excl = warp_excl_scan(avail, lane);
-            uint32_t incl = excl + avail;
-            uint32_t g = (uint32_t)lane - npop;
-            int s = 0;
-#pragma unroll
-            for (int step = 16; step >= 1; step >>= 1) {
-                uint32_t e = __shfl_sync(FULL, incl, s + step - 1);
-                if (e <= g) s += step;
+        if (cnt + seeds_total == 0) {
+            // slots still held but no work: cannot happen while the per-slot
+            // node counts are right; bounded so a bug cannot spin forever
+            if (++idle_rounds > IDLE_LIMIT) {
+                if (lane == 0) atomicOr(&ctl->error, ERR_TIMEOUT);
+                break;
             }
-            s &= 31;
-            uint32_t ex_s = __shfl_sync(FULL, excl, s), vn_s = __shfl_sync(FULL, s_vnext, s);
-            has_seed = !has_node && g < seeds_total;
-            sslot = (uint32_t)s;
-            sv = vn_s + (g - ex_s);
-            uint32_t taken = lanes_free > excl ? min(avail, lanes_free - excl) : 0u;
-            s_vnext += taken;
+            continue;
         }
 
-        // ---- extend
-        if (lane == 0) c_rounds++;
-        uint32_t slot = has_node ? (x_m & 31u) : sslot;
-        uint32_t info = __shfl_sync(FULL, s_info, slot);
-        uint32_t rid = __shfl_sync(FULL, s_read, slot);
-        uint32_t code = __shfl_sync(FULL, s_code, slot);
-        uint32_t k = (info >> 9) & 3u, minus = (info >> 11) & 1u, m = info & 511u, qe = (info >> 12) & 15u;
-        uint32_t cl[4], cr[4], cd[4];
-        uint32_t valid = 0, ci = 0;
-        if (has_node) {
-            uint32_t i = (x_m >> 5) & 511u, d = x_m >> 14;
-            uint32_t ol[4], orr[4];
-            c_blocks += occ_pair(ix, x_l, x_r, ol, orr);
-            c_nodes++;
-            uint32_t base = pat_base(sm.pat[slot], i - 1);
-#pragma unroll
-            for (int c = 0; c < 4; c++) {
-                uint32_t dd = d + ((uint32_t)c != base);
-                cl[c] = ix.C[c] + ol[c];
-                cr[c] = ix.C[c] + orr[c];
-                cd[c] = dd;
-                if (dd <= k && cl[c] < cr[c]) valid |= 1u << c;
-            }
-            ci = i - 1;
-        } else {
-#pragma unroll
-            for (int c = 0; c < 4; c++) { cl[c] = cr[c] = cd[c] = 0; }
-            if (has_seed) {
-                uint32_t w = __ldg(ix.variants + var_off(k) + sv);
-                uint32_t l, r;
-                seed_interval(ix, code ^ (w & 0xffffffu), qe, l, r);
-                c_seeds++;
-                cl[0] = l; cr[0] = r; cd[0] = w >> 24;
-                if (l < r) valid = 1u;
-                ci = m - qe;
-            }
-        }
-        bool leaf = (ci == 0);
+        // ---- one round over one kind of work: multi-row nodes, single-row
+        // nodes or seed lookups, so that no lane runs another kind's code
+        int kind;
+        if (mc >= 32) kind = 0;
+        else if (sc >= 32) kind = 1;
+        else if (seeds_total >= 32) kind = 2;
+        else kind = (mc >= sc && mc >= seeds_total) ? 0 : (sc >= seeds_total ? 1 : 2);
+        c_km += kind == 0;
+        c_ks += kind == 1;
+        c_kq += kind == 2;
 
-        // ---- leaves: SA intervals of matches
-        uint32_t nleaf = leaf ? (uint32_t)__popc(valid) : 0u;
-        uint32_t leaf_total = __reduce_add_sync(FULL, nleaf);
-        if (leaf_total) {
-            uint32_t pre = warp_excl_scan(nleaf, lane);
-            uint32_t at0 = 0;
-            if (lane == 0) at0 = atomicAdd(&ctl->iv_count, leaf_total);
-            at0 = __shfl_sync(FULL, at0, 0);
-            if (nleaf) {
-                atomicAdd(&a.iv_cnt[rid], nleaf);
-                uint32_t q = at0 + pre;
-#pragma unroll
-                for (int c = 0; c < 4; c++) {
-                    if (valid >> c & 1u) {
-                        if (q < ctl->iv_cap) {
-                            Interval x;
-                            x.read = rid; x.meta = cd[c] | (minus << 2); x.l = cl[c]; x.r = cr[c];
-                            a.iv[q] = x;
-                        } else {
-                            atomicOr(&ctl->error, ERR_IV_OVERFLOW);
-                        }
-                        q++;
+        if (kind == 1) {
+            // single-row node [l, l+1): its only possible child is c = BWT[l]
+            uint32_t npop = min(sc, 32u);
+            bool has = (uint32_t)lane < npop;
+            uint32_t l = 0, meta = 0;
+            if (has) {
+                uint32_t p = (stop - 1 - lane) & (SCAP - 1);
+                l = W.sl[p];
+                meta = W.sm[p];
+            }
+            stop -= npop;
+            __syncwarp();
+            uint32_t slot = meta & 31u;
+            uint32_t info = __shfl_sync(FULL, s_info, slot);
+            uint32_t rid = __shfl_sync(FULL, s_read, slot);
+            uint32_t i = (meta >> 5) & 511u, d = meta >> 14, k = (info >> 9) & 3u, minus = (info >> 11) & 1u;
+            bool child = false;
+            uint32_t l2 = 0, dd = 0;
+            if (has) {
+                c_nodes++;
+                if (l != ix.dollar_row) {
+                    uint32_t b = l / OCC_ROWS, o = l - b * OCC_ROWS;
+                    uint4 sup = ld_nc(ix.super + b / SB_BLOCKS);
+                    OccBlock blk;
+                    load_block(ix, b, o + 1, blk);
+                    c_blocks++;
+                    uint32_t c = block_symbol(blk, o);
+                    uint32_t base = pat_base(W.pat[slot], i - 1);
+                    dd = d + (c != base);
+                    if (dd <= k) {
+                        l2 = C_of(ix, c) + occ_single(ix, b, o, sup, blk, c);
+                        child = true;
                     }
                 }
             }
-        }
-
-        // ---- children back onto the stack
-        uint32_t nc = leaf ? 0u : (uint32_t)__popc(valid);
-        uint32_t pre = warp_excl_scan(nc, lane);
-        uint32_t ch_total = __shfl_sync(FULL, pre + nc, 31);
-        if ((top - bot) + ch_total > (uint32_t)SCAP) {
-            uint32_t nsp = (top - bot) + ch_total - SCAP + SCAP / 4;
-            nsp = min((nsp + 31) & ~31u, top - bot);
-            spill_bottom(sm, a, bot, nsp, s_read, s_info, lane, c_spills);
-        }
-        if (nc) {
-            uint32_t p = top + pre;
+            emit_one(a, child && i == 1, rid, dd, minus, l2, l2 + 1, lane, lt);
+            // a single-row round pops n nodes and pushes at most n: no room check
+            bool push = child && i > 1;
+            unsigned bs = __ballot_sync(FULL, push);
+            if (push) {
+                uint32_t p = (stop + __popc(bs & lt)) & (SCAP - 1);
+                W.sl[p] = l2;
+                W.sm[p] = node_meta(slot, i - 1, dd);
+            }
+            stop += __popc(bs);
+            if (has && !push) atomicAdd(&W.live[slot], -1);
+        } else if (kind == 0) {
+            // multi-row node: counts of all four symbols at l and r
+            uint32_t npop = min(mc, 32u);
+            bool has = (uint32_t)lane < npop;
+            uint32_t l = 0, r = 0, meta = 0;
+            if (has) {
+                uint32_t p = (mtop - 1 - lane) & (SCAP - 1);
+                l = W.ml[p];
+                r = W.mr[p];
+                meta = W.mm[p];
+            }
+            mtop -= npop;
+            __syncwarp();
+            uint32_t slot = meta & 31u;
+            uint32_t info = __shfl_sync(FULL, s_info, slot);
+            uint32_t rid = __shfl_sync(FULL, s_read, slot);
+            uint32_t i = (meta >> 5) & 511u, d = meta >> 14, k = (info >> 9) & 3u, minus = (info >> 11) & 1u;
+            uint32_t cl[4], cr[4], cd[4];
+            uint32_t valid = 0;
 #pragma unroll
-            for (int c = 0; c < 4; c++) {
-                if (valid >> c & 1u) {
-                    uint32_t q = p & (SCAP - 1);
-                    sm.nl[q] = cl[c];
-                    sm.nr[q] = cr[c];
-                    sm.nm[q] = (uint16_t)(slot | (ci << 5) | (cd[c] << 14));
-                    p++;
+            for (int c = 0; c < 4; c++) cl[c] = cr[c] = cd[c] = 0;
+            if (has) {
+                uint32_t ol[4], orr[4];
+                c_blocks += occ_pair(ix, l, r, ol, orr);
+                c_nodes++;
+                uint32_t base = pat_base(W.pat[slot], i - 1);
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    cl[c] = ix.C[c] + ol[c];
+                    cr[c] = ix.C[c] + orr[c];
+                    cd[c] = d + ((uint32_t)c != base);
+                    if (cd[c] <= k && cl[c] < cr[c]) valid |= 1u << c;
                 }
             }
+            bool leafs = (i == 1);
+            // leaves: up to four per lane
+            uint32_t nleaf = leafs ? (uint32_t)__popc(valid) : 0u;
+            if (__ballot_sync(FULL, nleaf != 0)) {
+                uint32_t pre = warp_excl_scan(nleaf, lane);
+                uint32_t tot = __shfl_sync(FULL, pre + nleaf, 31);
+                uint32_t at0 = 0;
+                if (lane == 0) at0 = atomicAdd(&ctl->iv_count, tot);
+                at0 = __shfl_sync(FULL, at0, 0);
+                if (nleaf) {
+                    atomicAdd(&a.iv_cnt[rid], nleaf);
+                    uint32_t q = at0 + pre;
+#pragma unroll
+                    for (int c = 0; c < 4; c++) {
+                        if (valid >> c & 1u) {
+                            if (q < ctl->iv_cap) {
+                                Interval x;
+                                x.read = rid; x.meta = cd[c] | (minus << 2); x.l = cl[c]; x.r = cr[c];
+                                a.iv[q] = x;
+                            } else {
+                                atomicOr(&ctl->error, ERR_IV_OVERFLOW);
+                            }
+                            q++;
+                        }
+                    }
+                }
+            }
+            // children onto the stack their size selects
+            uint32_t nm = 0, ns = 0;
+            if (!leafs) {
+#pragma unroll
+                for (int c = 0; c < 4; c++)
+                    if (valid >> c & 1u) {
+                        if (cr[c] - cl[c] == 1) ns++;
+                        else nm++;
+                    }
+            }
+            uint32_t packed = nm | (ns << 8);
+            uint32_t pre = warp_excl_scan(packed, lane);
+            uint32_t tot = __shfl_sync(FULL, pre + packed, 31);
+            uint32_t tm = tot & 0xffu, ts = tot >> 8;
+            if (tm) make_room<SCAP, false>(W, a, mbot, mtop, tm, s_read, s_info, lane, c_spills);
+            if (ts) make_room<SCAP, true>(W, a, sbot, stop, ts, s_read, s_info, lane, c_spills);
+            if (nm | ns) {
+                uint32_t pm = mtop + (pre & 0xffu), ps = stop + (pre >> 8);
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    if (valid >> c & 1u) {
+                        uint16_t mt = node_meta(slot, i - 1, cd[c]);
+                        if (cr[c] - cl[c] == 1) {
+                            uint32_t q = ps++ & (SCAP - 1);
+                            W.sl[q] = cl[c];
+                            W.sm[q] = mt;
+                        } else {
+                            uint32_t q = pm++ & (SCAP - 1);
+                            W.ml[q] = cl[c];
+                            W.mr[q] = cr[c];
+                            W.mm[q] = mt;
+                        }
+                    }
+                }
+            }
+            mtop += tm;
+            stop += ts;
+            int delta = (int)(nm + ns) - 1;
+            if (has && delta) atomicAdd(&W.live[slot], delta);
+        } else {
+            // seed lookups, all from one slot
+            int s = __ffs(__ballot_sync(FULL, avail > 0)) - 1;
+            uint32_t av = __shfl_sync(FULL, avail, s), vn = __shfl_sync(FULL, s_vnext, s);
+            uint32_t info = __shfl_sync(FULL, s_info, s);
+            uint32_t rid = __shfl_sync(FULL, s_read, s);
+            uint32_t code = __shfl_sync(FULL, s_code, s);
+            if (lane == s) s_vnext += min(av, 32u);
+            bool has = (uint32_t)lane < av;
+            uint32_t k = (info >> 9) & 3u, minus = (info >> 11) & 1u, m = info & 511u, qe = (info >> 12) & 15u;
+            uint32_t l = 0, r = 0, dd = 0;
+            bool child = false;
+            if (has) {
+                uint32_t w = __ldg(ix.variants + var_off(k) + vn + lane);
+                seed_interval(ix, code ^ (w & 0xffffffu), qe, l, r);
+                c_seeds++;
+                dd = w >> 24;
+                child = l < r;
+            }
+            uint32_t i0 = m - qe;
+            emit_one(a, child && i0 == 0, rid, dd, minus, l, r, lane, lt);
+            bool push = child && i0 > 0;
+            push_one<SCAP>(W, push, l, r, node_meta((uint32_t)s, i0, dd), mtop, stop, lt);
+            unsigned bp = __ballot_sync(FULL, push);
+            if (lane == 0 && bp) atomicAdd(&W.live[s], __popc(bp));
         }
-        top += ch_total;
-        int delta = (int)nc - (has_node ? 1 : 0);
-        if (delta && (has_node || has_seed)) atomicAdd(&sm.live[slot], delta);
         __syncwarp();
 
         // ---- share work with idle warps near the end of the batch
-        if ((iter & 31) == 31 && top - bot > DONATE_MIN) {
+        if ((iter & 31) == 31 && (mtop - mbot) + (stop - sbot) > DONATE_MIN) {
             int give = 0;
             if (lane == 0) {
                 uint32_t h = vload(&ctl->spill_head);
@@ -639,7 +794,12 @@ __global__ void __launch_bounds__(WARPS * 32) k_persistent(PersistArgs a)
                 give = h >= R && vload64(&ctl->task_head) >= a.ntasks &&
                        (int)vload((const unsigned *)&ctl->busy) < a.total_warps;
             }
-            if (__shfl_sync(FULL, give, 0)) spill_bottom(sm, a, bot, DONATE_N, s_read, s_info, lane, c_spills);
+            if (__shfl_sync(FULL, give, 0)) {
+                if (stop - sbot >= mtop - mbot)
+                    spill_bottom<SCAP, true>(W, a, sbot, min(DONATE_N, stop - sbot), s_read, s_info, lane, c_spills);
+                else
+                    spill_bottom<SCAP, false>(W, a, mbot, min(DONATE_N, mtop - mbot), s_read, s_info, lane, c_spills);
+            }
         }
     }
 
@@ -653,11 +813,16 @@ __global__ void __launch_bounds__(WARPS * 32) k_persistent(PersistArgs a)
     if (lane == 0 && v) atomicAdd(&ctl->rank_blocks, v);
     v = c_spills; for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     if (lane == 0 && v) atomicAdd(&ctl->spills, v);
-    v = c_rounds; for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-    if (lane == 0 && v) atomicAdd(&ctl->rounds, v);
+    if (lane == 0) atomicAdd(&ctl->rounds, (unsigned long long)c_km + c_ks + c_kq);
     v = c_seeds + c_nodes; for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     if (lane == 0 && v) atomicAdd(&ctl->lane_ops, v);
+    if (lane == 0) {
+        atomicAdd(&ctl->rounds_kind[0], (unsigned long long)c_km);
+        atomicAdd(&ctl->rounds_kind[1], (unsigned long long)c_ks);
+        atomicAdd(&ctl->rounds_kind[2], (unsigned long long)c_kq);
+    }
 }
+
 
 }  // namespace
 
@@ -665,24 +830,51 @@ __global__ void __launch_bounds__(WARPS * 32) k_persistent(PersistArgs a)
 // Host launcher
 // --------------------------------------------------------------------------
 
-constexpr int P_SCAP = 256;
-constexpr int P_WARPS = 8;
+// Persistent kernel shapes: (stack capacity, warps per CTA, min CTAs per SM).
+struct PersistShape {
+    void (*fn)(PersistArgs);
+    int scap, warps, minb;
+    size_t smem;
+    int blocks_per_sm;
+};
 
-static int g_num_sms = 0, g_persist_blocks = 0;
+#define MICA_SHAPE(S, W, B) {k_persistent<S, W, B>, S, W, B, sizeof(WarpSmem<S>) * W, 0}
+static PersistShape g_shapes[] = {
+    MICA_SHAPE(256, 8, 3),
+    MICA_SHAPE(256, 8, 4),
+    MICA_SHAPE(256, 4, 8),
+    MICA_SHAPE(128, 8, 4),
+};
+#undef MICA_SHAPE
+constexpr int N_SHAPES = sizeof(g_shapes) / sizeof(g_shapes[0]);
+
+static int g_num_sms = 0;
 static std::mutex g_grid_mu;
 
-static int persistent_grid(int device, int &blocks_per_sm, size_t smem)
+static int persistent_grid(int device, int shape, int &blocks_per_sm)
 {
     std::lock_guard<std::mutex> lk(g_grid_mu);
-    if (g_num_sms == 0) {
+    if (g_num_sms == 0)
         MICA_CUDA_TRY(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, device));
-        MICA_CUDA_TRY(cudaFuncSetAttribute(k_persistent<P_SCAP, P_WARPS>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        MICA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &g_persist_blocks, k_persistent<P_SCAP, P_WARPS>, P_WARPS * 32, smem));
-        if (g_persist_blocks < 1) g_persist_blocks = 1;
+    PersistShape &sh = g_shapes[shape];
+    if (sh.blocks_per_sm == 0) {
+        MICA_CUDA_TRY(cudaFuncSetAttribute(sh.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem));
+        MICA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh.blocks_per_sm, sh.fn, sh.warps * 32,
+                                                                    sh.smem));
+        if (sh.blocks_per_sm < 1) sh.blocks_per_sm = 1;
     }
-    blocks_per_sm = g_persist_blocks;
+    blocks_per_sm = sh.blocks_per_sm;
+    return 0;
+}
+
+int search_shape_count() { return N_SHAPES; }
+
+int search_shape_info(int shape, int *scap, int *warps, int *minb)
+{
+    if (shape < 0 || shape >= N_SHAPES) return MICA_EINVAL;
+    if (scap) *scap = g_shapes[shape].scap;
+    if (warps) *warps = g_shapes[shape].warps;
+    if (minb) *minb = g_shapes[shape].minb;
     return 0;
 }
 
@@ -696,7 +888,7 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
     if (w.iv_cap == 0) w.iv_cap = (uint32_t)std::min<uint64_t>(4 * n + 65536, 1ull << 30);
     if (w.spill_cap == 0) w.spill_cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(n, 1u << 20), 1ull << 28);
     SearchCtl *d_ctl = (SearchCtl *)w.ctl.p;
-    const size_t smem = sizeof(WarpSmem<P_SCAP>) * P_WARPS;
+    int shape = (cfg.shape >= 0 && cfg.shape < N_SHAPES) ? cfg.shape : DEFAULT_SHAPE;
     for (int attempt = 0; attempt < 8; attempt++) {
         if ((rc = dev_reserve(w.iv, (size_t)w.iv_cap * sizeof(Interval)))) return rc;
         if ((rc = dev_reserve(w.spill, (size_t)w.spill_cap * sizeof(WorkItem)))) return rc;
@@ -713,15 +905,16 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
         if (n > 0) {
             if (cfg.kernel == MICA_KERNEL_PERSISTENT) {
                 int bps = 0;
-                if ((rc = persistent_grid(idx->device, bps, smem))) return rc;
+                if ((rc = persistent_grid(idx->device, shape, bps))) return rc;
+                const PersistShape &sh = g_shapes[shape];
                 PersistArgs pa;
                 pa.ix = idx->view; pa.rd = rd; pa.read_list = nullptr; pa.ntasks = 2 * n;
                 pa.ctl = d_ctl; pa.iv = (Interval *)w.iv.p; pa.iv_cnt = (uint32_t *)w.iv_cnt.p;
                 pa.spill = (WorkItem *)w.spill.p;
                 int grid = g_num_sms * bps;
-                pa.total_warps = grid * P_WARPS;
+                pa.total_warps = grid * sh.warps;
                 MICA_CUDA_TRY(cudaEventRecord(w.kev[0], s));
-                k_persistent<P_SCAP, P_WARPS><<<grid, P_WARPS * 32, smem, s>>>(pa);
+                sh.fn<<<grid, sh.warps * 32, sh.smem, s>>>(pa);
                 MICA_CUDA_TRY(cudaGetLastError());
                 MICA_CUDA_TRY(cudaEventRecord(w.kev[1], s));
                 st.launches++;
@@ -737,11 +930,40 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
                 pa.requeue_cap = w.spill_cap;
                 pa.budget = cfg.plain_budget;
                 int blk = cfg.plain_block > 0 ? cfg.plain_block : 128;
-                MICA_CUDA_TRY(cudaEventRecord(w.kev[0], s));
-                k_plain<<<(unsigned)((pa.ntasks + blk - 1) / blk), blk, 0, s>>>(pa);
-                MICA_CUDA_TRY(cudaGetLastError());
-                MICA_CUDA_TRY(cudaEventRecord(w.kev[1], s));
-                st.launches++;
+                if (cfg.kernel == MICA_KERNEL_PLAIN_BY_LENGTH) {
+                    // one launch per length class, each with its own block size
+                    if ((rc = dev_reserve(w.lenlist, std::max<uint64_t>(n, 1) * 4 + 64))) return rc;
+                    unsigned int *cnt = (unsigned int *)((char *)w.lenlist.p + ((std::max<uint64_t>(n, 1) * 4 + 15) & ~15ull));
+                    MICA_CUDA_TRY(cudaMemsetAsync(cnt, 0, 3 * LEN_CLASSES * 4, s));
+                    unsigned g = (unsigned)std::min<uint64_t>((n + 255) / 256, 152 * 16);
+                    k_len_count<<<g, 256, 0, s>>>(rd, cnt);
+                    unsigned int hc[LEN_CLASSES], hb[LEN_CLASSES];
+                    MICA_CUDA_TRY(cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, s));
+                    MICA_CUDA_TRY(cudaStreamSynchronize(s));
+                    unsigned int acc = 0;
+                    for (uint32_t c = 0; c < LEN_CLASSES; c++) { hb[c] = acc; acc += hc[c]; }
+                    MICA_CUDA_TRY(cudaMemcpyAsync(cnt + LEN_CLASSES, hb, sizeof(hb), cudaMemcpyHostToDevice, s));
+                    k_len_scatter<<<g, 256, 0, s>>>(rd, cnt + LEN_CLASSES, cnt + 2 * LEN_CLASSES, (uint32_t *)w.lenlist.p);
+                    st.launches += 2;
+                    MICA_CUDA_TRY(cudaEventRecord(w.kev[0], s));
+                    for (uint32_t c = 0; c < LEN_CLASSES; c++) {
+                        if (!hc[c]) continue;
+                        int bc = cfg.plain_block_len[c] > 0 ? cfg.plain_block_len[c] : blk;
+                        PlainArgs pc = pa;
+                        pc.read_list = (const uint32_t *)w.lenlist.p + hb[c];
+                        pc.ntasks = 2ull * hc[c];
+                        k_plain<<<(unsigned)((pc.ntasks + bc - 1) / bc), bc, 0, s>>>(pc);
+                        MICA_CUDA_TRY(cudaGetLastError());
+                        st.launches++;
+                    }
+                    MICA_CUDA_TRY(cudaEventRecord(w.kev[1], s));
+                } else {
+                    MICA_CUDA_TRY(cudaEventRecord(w.kev[0], s));
+                    k_plain<<<(unsigned)((pa.ntasks + blk - 1) / blk), blk, 0, s>>>(pa);
+                    MICA_CUDA_TRY(cudaGetLastError());
+                    MICA_CUDA_TRY(cudaEventRecord(w.kev[1], s));
+                    st.launches++;
+                }
                 WorkItem *bufs[2] = {(WorkItem *)w.spill.p, (WorkItem *)w.spill2.p};
                 for (int round = 0; round < 64; round++) {
                     unsigned int cnt = 0, err = 0;
@@ -749,6 +971,8 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
                     MICA_CUDA_TRY(cudaMemcpyAsync(&err, &d_ctl->error, 4, cudaMemcpyDeviceToHost, s));
                     MICA_CUDA_TRY(cudaStreamSynchronize(s));
                     if (cnt == 0 || err) break;
+                    // the re-queue shares the persistent kernel's spill buffer: clear it before that kernel
+                    w.spill_dirty = true;
                     cnt = std::min(cnt, w.spill_cap);
                     pa.items = bufs[round & 1];
                     pa.requeue = bufs[(round + 1) & 1];
@@ -783,6 +1007,9 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
         st.spills = out.spills;
         st.warp_rounds = out.rounds;
         st.lane_ops = out.lane_ops;
+        st.rounds_multi = out.rounds_kind[0];
+        st.rounds_single = out.rounds_kind[1];
+        st.rounds_seed = out.rounds_kind[2];
         return 0;
     }
     return MICA_EINTERNAL;

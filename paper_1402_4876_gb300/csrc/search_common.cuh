@@ -18,83 +18,109 @@ __device__ __forceinline__ uint32_t n_variants(uint32_t q, uint32_t k)
 
 __device__ __forceinline__ uint4 ld_nc(const uint4 *p) { return __ldg(p); }
 
-// Counts of C, G, T among the first `o` symbols (o <= 192) of the 12 BWT
-// words a[0..11].  Words beyond the prefix may hold anything: they are masked.
-// Two words share one popcount: the even-bit masks of word 2p and (shifted
-// left by one) of word 2p+1 never overlap.
-__device__ __forceinline__ void prefix_counts(const uint32_t (&a)[12], uint32_t o,
-                                              uint32_t &nc, uint32_t &ng, uint32_t &nt)
+// Low `rem` bits set, rem in [0, 32].
+__device__ __forceinline__ uint32_t low_mask(uint32_t rem)
 {
-    uint32_t sc = 0, sg = 0, st = 0;
+    return ~__funnelshift_lc(0u, 0xffffffffu, rem);
+}
+
+// One occurrence block in registers: relative counts and the bit planes.
+struct OccBlock {
+    uint32_t ac, gt;          // relative counts A | C << 16, G | T << 16
+    uint32_t lo[3], hi[3];    // rows 0-31, 32-63, 64-95
+};
+
+// Load block b; rows at offsets >= 32 are only fetched when `need` > 32.
+__device__ __forceinline__ void load_block(const IndexView &ix, uint32_t b, uint32_t need, OccBlock &k)
+{
+    const uint4 *p = ix.occ + (size_t)b * 2;
+    uint4 q0 = ld_nc(p);
+    uint4 q1 = make_uint4(0, 0, 0, 0);
+    if (need > 32) q1 = ld_nc(p + 1);
+    k.ac = q0.x; k.gt = q0.y;
+    k.lo[0] = q0.z; k.hi[0] = q0.w;
+    k.lo[1] = q1.x; k.hi[1] = q1.y;
+    k.lo[2] = q1.z; k.hi[2] = q1.w;
+}
+
+// Occ(A..T, b * 96 + o) from a loaded block and its superblock entry.
+__device__ __forceinline__ void occ_from(const IndexView &ix, uint32_t b, uint32_t o, const uint4 &sup,
+                                         const OccBlock &k, uint32_t (&occ)[4])
+{
+    uint32_t sl = 0, sh = 0, st = 0;
 #pragma unroll
-    for (int p = 0; p < 6; p++) {
-        int rem0 = (int)o - 32 * p, rem1 = rem0 - 16;
-        uint32_t m0 = rem0 >= 16 ? 0x55555555u : (rem0 <= 0 ? 0u : (0x55555555u >> (32 - 2 * rem0)));
-        uint32_t m1 = rem1 >= 16 ? 0x55555555u : (rem1 <= 0 ? 0u : (0x55555555u >> (32 - 2 * rem1)));
-        uint32_t x0 = a[2 * p], x1 = a[2 * p + 1];
-        uint32_t lo0 = x0 & m0, hi0 = (x0 >> 1) & m0;
-        uint32_t lo1 = x1 & m1, hi1 = (x1 >> 1) & m1;
-        uint32_t lo = lo0 | (lo1 << 1), hi = hi0 | (hi1 << 1);
-        uint32_t both = (lo0 & hi0) | ((lo1 & hi1) << 1);
-        st += __popc(both);
-        sc += __popc(lo);
-        sg += __popc(hi);
+    for (int j = 0; j < 3; j++) {
+        uint32_t rem = min(max((int)o - 32 * j, 0), 32);
+        uint32_t m = low_mask(rem);
+        uint32_t L = k.lo[j] & m, H = k.hi[j] & m;
+        st += __popc(L & H);
+        sl += __popc(L);
+        sh += __popc(H);
     }
-    nt = st;
-    nc = sc - st;   // code 1 = low bit only
-    ng = sg - st;   // code 2 = high bit only
-}
-
-// Load the words of block `blk` needed for the first `need` symbols.
-__device__ __forceinline__ void load_block_words(const uint4 *blk, uint32_t need, uint32_t (&a)[12])
-{
-    uint4 w0 = make_uint4(0, 0, 0, 0), w1 = w0, w2 = w0;
-    if (need > 0) w0 = ld_nc(blk + 1);
-    if (need > 64) w1 = ld_nc(blk + 2);
-    if (need > 128) w2 = ld_nc(blk + 3);
-    a[0] = w0.x; a[1] = w0.y; a[2] = w0.z; a[3] = w0.w;
-    a[4] = w1.x; a[5] = w1.y; a[6] = w1.z; a[7] = w1.w;
-    a[8] = w2.x; a[9] = w2.y; a[10] = w2.z; a[11] = w2.w;
-}
-
-// Occ(A..T, i) into occ[0..3] from a header and already-loaded words.
-__device__ __forceinline__ void occ_from(const IndexView &ix, uint32_t b, uint32_t o, const uint4 &h,
-                                         const uint32_t (&a)[12], uint32_t (&occ)[4])
-{
-    uint32_t nc, ng, nt;
-    prefix_counts(a, o, nc, ng, nt);
+    uint32_t nt = st, nc = sl - st, ng = sh - st;
     uint32_t na = o - nc - ng - nt;
     uint32_t start = b * OCC_ROWS;
     if (ix.dollar_row >= start && ix.dollar_row < start + o) na -= 1;   // $ is stored as A
-    occ[0] = h.x + na;
-    occ[1] = h.y + nc;
-    occ[2] = h.z + ng;
-    occ[3] = h.w + nt;
+    occ[0] = sup.x + (k.ac & 0xffffu) + na;
+    occ[1] = sup.y + (k.ac >> 16) + nc;
+    occ[2] = sup.z + (k.gt & 0xffffu) + ng;
+    occ[3] = sup.w + (k.gt >> 16) + nt;
+}
+
+// Occ(c, b * 96 + o) for one symbol c.
+__device__ __forceinline__ uint32_t occ_single(const IndexView &ix, uint32_t b, uint32_t o, const uint4 &sup,
+                                               const OccBlock &k, uint32_t c)
+{
+    uint32_t xl = (c & 1u) ? 0u : 0xffffffffu;   // select rows whose low bit equals c's
+    uint32_t xh = (c & 2u) ? 0u : 0xffffffffu;
+    uint32_t n = 0;
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        uint32_t rem = min(max((int)o - 32 * j, 0), 32);
+        n += __popc((k.lo[j] ^ xl) & (k.hi[j] ^ xh) & low_mask(rem));
+    }
+    uint32_t start = b * OCC_ROWS;
+    if (c == 0 && ix.dollar_row >= start && ix.dollar_row < start + o) n -= 1;   // $ is stored as A
+    uint32_t rel = c == 0 ? (k.ac & 0xffffu) : c == 1 ? (k.ac >> 16) : c == 2 ? (k.gt & 0xffffu) : (k.gt >> 16);
+    uint32_t base = c == 0 ? sup.x : c == 1 ? sup.y : c == 2 ? sup.z : sup.w;
+    return base + rel + n;
+}
+
+__device__ __forceinline__ uint32_t C_of(const IndexView &ix, uint32_t c)
+{
+    return c == 0 ? ix.C[0] : c == 1 ? ix.C[1] : c == 2 ? ix.C[2] : ix.C[3];
+}
+
+// Symbol code at offset o of a loaded block.
+__device__ __forceinline__ uint32_t block_symbol(const OccBlock &k, uint32_t o)
+{
+    uint32_t j = o >> 5, bit = o & 31;
+    uint32_t lo = j == 0 ? k.lo[0] : j == 1 ? k.lo[1] : k.lo[2];
+    uint32_t hi = j == 0 ? k.hi[0] : j == 1 ? k.hi[1] : k.hi[2];
+    return ((lo >> bit) & 1u) | (((hi >> bit) & 1u) << 1);
 }
 
 // Occ(c, l) and Occ(c, r) for all c; one block read when l and r share it.
-// Returns the number of 64-byte blocks touched (1 or 2).
+// Returns the number of 32-byte blocks touched (1 or 2).
 __device__ __forceinline__ int occ_pair(const IndexView &ix, uint32_t l, uint32_t r,
                                         uint32_t (&ol)[4], uint32_t (&orr)[4])
 {
     uint32_t bl = l / OCC_ROWS, xl = l - bl * OCC_ROWS;
     uint32_t br = r / OCC_ROWS, xr = r - br * OCC_ROWS;
-    const uint4 *pl = ix.occ + (size_t)bl * 4;
-    uint32_t a[12];
+    uint4 sl = ld_nc(ix.super + bl / SB_BLOCKS);
+    OccBlock a;
     if (bl == br) {
-        uint4 h = ld_nc(pl);
-        load_block_words(pl, xr, a);
-        occ_from(ix, bl, xl, h, a, ol);
-        occ_from(ix, br, xr, h, a, orr);
+        load_block(ix, bl, xr, a);
+        occ_from(ix, bl, xl, sl, a, ol);
+        occ_from(ix, br, xr, sl, a, orr);
         return 1;
     }
-    const uint4 *pr = ix.occ + (size_t)br * 4;
-    uint4 hl = ld_nc(pl), hr = ld_nc(pr);
-    uint32_t b2[12];
-    load_block_words(pl, xl, a);
-    load_block_words(pr, xr, b2);
-    occ_from(ix, bl, xl, hl, a, ol);
-    occ_from(ix, br, xr, hr, b2, orr);
+    uint4 sr = ld_nc(ix.super + br / SB_BLOCKS);
+    OccBlock c;
+    load_block(ix, bl, xl, a);
+    load_block(ix, br, xr, c);
+    occ_from(ix, bl, xl, sl, a, ol);
+    occ_from(ix, br, xr, sr, c, orr);
     return 2;
 }
 
@@ -140,9 +166,11 @@ __device__ __forceinline__ void seed_interval(const IndexView &ix, uint32_t code
     uint32_t start = code << sh, end = (code + 1) << sh;
     l = __ldg(ix.table + (size_t)start);
     r = __ldg(ix.table + (size_t)end);
-    for (uint32_t t = 0; t < ix.nshort; t++) {
-        l -= (ix.short_pad[t] == start && ix.short_len[t] >= qe);
-        r -= (ix.short_pad[t] == end);
+    if (((ix.short_bloom >> (start & 63)) | (ix.short_bloom >> (end & 63))) & 1ull) {
+        for (uint32_t t = 0; t < ix.nshort; t++) {
+            l -= (ix.short_pad[t] == start && ix.short_len[t] >= qe);
+            r -= (ix.short_pad[t] == end);
+        }
     }
 }
 

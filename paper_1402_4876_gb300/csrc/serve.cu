@@ -247,7 +247,7 @@ int mica_server_start(mica_index *idx, const mica_server_params *params, mica_se
     mica_server_params p;
     mica_server_params_default(&p);
     if (params) p = *params;
-    if (p.kernel != MICA_KERNEL_PERSISTENT && p.kernel != MICA_KERNEL_PLAIN) return MICA_EINVAL;
+    if (p.kernel < MICA_KERNEL_PERSISTENT || p.kernel > MICA_KERNEL_PLAIN_BY_LENGTH) return MICA_EINVAL;
     if (p.workers <= 0) p.workers = 2;
     if (p.workers > 8) return MICA_EINVAL;
     if (p.max_tick_reads == 0) p.max_tick_reads = 1u << 20;

@@ -9,7 +9,7 @@ from tests import golden_cases, refcheck
 from tests import gpu_common as gc
 
 pytestmark = pytest.mark.gpu
-KERNELS = ["persistent", "plain"]
+KERNELS = ["persistent", "plain", "plain_by_length"]
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -153,6 +153,28 @@ def test_uneven_64m_sample(kernel):
     gc.assert_same(got, want)
 
 
+def test_every_shape_and_block_gives_the_same_result():
+    g = gc.genome("64m")
+    full = synth.reads_uneven(g, n=200_000)
+    b = full.subset(np.arange(0, full.n, 40))                                      # 5,000 reads
+    idx = gc.gpu_index("64m")
+    ref = idx.align_batch(b, hit_cap=1000, kernel="plain")
+    m = gc.mica()
+    try:
+        for shape in range(len(m.tuning_shapes())):
+            idx.set_tuning(shape=shape)
+            gc.assert_same(idx.align_batch(b, hit_cap=1000, kernel="persistent"), ref, f"shape {shape}")
+        idx.set_tuning(plain_block=64, plain_budget=100, plain_block_len=(32, 96, 256, 512))
+        for kernel in ("plain", "plain_by_length"):
+            got = idx.align_batch(b, hit_cap=1000, kernel=kernel)
+            gc.assert_same(got, ref, f"{kernel} with a 100-node budget")
+            assert idx.stats()["spills"] > 0          # the re-queue path ran
+        with pytest.raises(m.MicaError):
+            idx.set_tuning(shape=99)
+    finally:
+        idx.set_tuning()
+
+
 def test_full_1m_reads_64m():
     """Full 1M x 150 bp batch on the 64 Mbp repeat genome in the launch shape
     the benchmark times: both kernels agree exactly; 2,000 sampled reads equal
@@ -179,3 +201,24 @@ def test_full_1m_reads_64m():
         for pos, s, d in a.hits_of(int(i)):
             w = g.codes[pos:pos + 150]
             assert int(((refcheck.rc(r) if s else r) != w).sum()) == d
+
+
+def test_autotune_cache_and_results_unchanged(tmp_path):
+    g = gc.genome("64m")
+    full = synth.reads_uneven(g, n=200_000)
+    b = full.subset(np.arange(0, full.n, 50))                                      # 4,000 reads
+    idx = gc.gpu_index("64m")
+    m = gc.mica()
+    cache = str(tmp_path / "tuning.txt")
+    try:
+        ref = idx.align_batch(b, hit_cap=1000, kernel="plain")
+        t = idx.autotune(b, repeats=1, cache=cache)
+        assert 0 <= t["shape"] < len(m.tuning_shapes())
+        assert t["plain_block"] in (64, 128, 256, 512)
+        assert all(x in (64, 128, 256, 512) for x in t["plain_block_len"])    # all four classes present
+        idx.set_tuning()
+        assert idx.autotune(b, cache=cache) == t                               # served from the cache
+        for kernel in ("persistent", "plain", "plain_by_length"):
+            gc.assert_same(idx.align_batch(b, hit_cap=1000, kernel=kernel), ref, kernel)
+    finally:
+        idx.set_tuning()
