@@ -313,7 +313,7 @@ __device__ __forceinline__ uint16_t node_meta(uint32_t slot, uint32_t i, uint32_
 template <int SCAP, bool SINGLE>
 __device__ __forceinline__ void spill_bottom(WarpSmem<SCAP> &W, const PersistArgs &a, uint32_t &bot,
                                              uint32_t nsp, uint32_t s_read, uint32_t s_info, int lane,
-                                             unsigned long long &c_spills)
+                                             uint32_t &c_spills)
 {
     SearchCtl *ctl = a.ctl;
     uint32_t at0 = 0;
@@ -356,7 +356,7 @@ __device__ __forceinline__ void spill_bottom(WarpSmem<SCAP> &W, const PersistArg
 template <int SCAP, bool SINGLE>
 __device__ __forceinline__ void make_room(WarpSmem<SCAP> &W, const PersistArgs &a, uint32_t &bot, uint32_t top,
                                           uint32_t add, uint32_t s_read, uint32_t s_info, int lane,
-                                          unsigned long long &c_spills)
+                                          uint32_t &c_spills)
 {
     if ((top - bot) + add > (uint32_t)SCAP) {
         uint32_t nsp = (top - bot) + add - SCAP + SCAP / 4;
@@ -427,9 +427,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
     bool s_used = false;
     uint32_t mbot = 0, mtop = 0, sbot = 0, stop = 0;
     bool busy = false;
-    uint32_t idle_rounds = 0, backoff = 256;
-    unsigned long long c_seeds = 0, c_nodes = 0, c_blocks = 0, c_spills = 0;
-    uint32_t c_km = 0, c_ks = 0, c_kq = 0;   // rounds by kind (warp-uniform)
+    uint32_t idle_rounds = 0;   // consecutive rounds without work; the sleep grows with it
+    uint32_t c_seeds = 0, c_nodes = 0, c_blocks = 0, c_spills = 0;   // per lane
+    uint32_t c_km = 0, c_ks = 0, c_kq = 0;                           // rounds by kind (warp-uniform)
     __syncwarp();
 
     for (uint32_t iter = 0;; iter++) {
@@ -469,8 +469,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
                         if (lane == 0) atomicOr(&ctl->error, ERR_TIMEOUT);
                         break;
                     }
-                    __nanosleep(backoff);
-                    backoff = min(backoff * 2, 8192u);
+                    __nanosleep(256u << min(idle_rounds, 5u));
                     continue;
                 }
             }
@@ -564,7 +563,6 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
                 push_one<SCAP>(W, is_node, nd_l, nd_r, node_meta((uint32_t)lane, nd_i, nd_d), mtop, stop, lt);
                 __syncwarp();
                 idle_rounds = 0;
-                backoff = 256;
                 continue;
             }
             if (idle) {
@@ -585,8 +583,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
                     if (lane == 0) atomicOr(&ctl->error, ERR_TIMEOUT);
                     break;
                 }
-                __nanosleep(backoff);
-                backoff = min(backoff * 2, 8192u);
+                __nanosleep(256u << min(idle_rounds, 5u));
                 continue;
             }
         }
@@ -814,7 +811,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
     v = c_spills; for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     if (lane == 0 && v) atomicAdd(&ctl->spills, v);
     if (lane == 0) atomicAdd(&ctl->rounds, (unsigned long long)c_km + c_ks + c_kq);
-    v = c_seeds + c_nodes; for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    v = (unsigned long long)c_seeds + c_nodes; for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     if (lane == 0 && v) atomicAdd(&ctl->lane_ops, v);
     if (lane == 0) {
         atomicAdd(&ctl->rounds_kind[0], (unsigned long long)c_km);
@@ -844,6 +841,7 @@ static PersistShape g_shapes[] = {
     MICA_SHAPE(256, 8, 4),
     MICA_SHAPE(256, 4, 8),
     MICA_SHAPE(128, 8, 4),
+    MICA_SHAPE(128, 8, 5),
 };
 #undef MICA_SHAPE
 constexpr int N_SHAPES = sizeof(g_shapes) / sizeof(g_shapes[0]);

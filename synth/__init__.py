@@ -298,3 +298,141 @@ def reads_uneven(genome: Genome, n: int = 1_000_000) -> ReadBatch:
     lengths = np.asarray(UNEVEN_LENGTHS)[rng.integers(0, 4, size=n)]
     k = rng.integers(0, 4, size=n).astype(np.uint8)
     return sample_reads(genome, lengths, k, rng, subs="rate", sub_rate=0.01, repeat_frac=0.30)
+
+
+# --------------------------------------------------------------------------
+# Human-scale genome and paired reads
+# --------------------------------------------------------------------------
+
+HUMAN_LEN = 3_100_000_000
+
+
+def _plant(g, seg, dst, rev):
+    if rev:
+        seg = opposite_strand(seg)
+    g[dst:dst + len(seg)] = seg
+
+
+def human_genome(n: int = HUMAN_LEN, seed: int = SEED_GENOME_HUMAN) -> Genome:
+    """About 45% repeats over an i.i.d. base:
+
+    * 300 bp families: 50 consensus sequences; copies with per-copy
+      divergence uniform in 10-15%, random orientation, covering 15%;
+    * 6 kbp families: 20 consensus sequences; copies at 5% divergence,
+      full length or 5'-truncated (half each; truncated length uniform in
+      300-6,000 bp, the 3' end kept), covering 25%;
+    * tandem arrays: unit 2-50 bp, array 100-20,000 bp, per-array divergence
+      uniform in 1-5%, covering 5%.
+    Later plantings overwrite earlier ones where they overlap.
+    """
+    rng = _rng(seed)
+    g = rng.integers(0, 4, size=n, dtype=np.uint8)
+    regions = []
+    # 300 bp families
+    fam = rng.integers(0, 4, size=(50, 300), dtype=np.uint8)
+    total = int(0.15 * n)
+    done = 0
+    while done < total:
+        c = min(100_000, (total - done) // 300 + 1)
+        f = rng.integers(0, 50, size=c)
+        div = rng.uniform(0.10, 0.15, size=c)
+        mat = fam[f].copy()
+        hit = rng.random(mat.shape) < div[:, None]
+        shift = rng.integers(1, 4, size=mat.shape, dtype=np.uint8)
+        mat = np.where(hit, (mat + shift) & 3, mat).astype(np.uint8)
+        rev = rng.integers(0, 2, size=c)
+        dst = rng.integers(0, n - 300, size=c)
+        for j in range(c):
+            _plant(g, mat[j], int(dst[j]), rev[j])
+            regions.append((int(dst[j]), int(dst[j]) + 300, "fam300"))
+        done += 300 * c
+    # 6 kbp families
+    fam = rng.integers(0, 4, size=(20, 6000), dtype=np.uint8)
+    total = int(0.25 * n)
+    done = 0
+    while done < total:
+        f = int(rng.integers(0, 20))
+        ln = 6000 if rng.random() < 0.5 else int(rng.integers(300, 6001))
+        seg = fam[f, 6000 - ln:].copy()
+        substitute(seg, np.flatnonzero(rng.random(ln) < 0.05), rng)
+        dst = int(rng.integers(0, n - ln))
+        _plant(g, seg, dst, rng.integers(0, 2))
+        regions.append((dst, dst + ln, "fam6k"))
+        done += ln
+    # tandem arrays
+    total = int(0.05 * n)
+    done = 0
+    while done < total:
+        u = int(rng.integers(2, 51))
+        ln = int(rng.integers(100, 20_001))
+        arr = np.resize(rng.integers(0, 4, size=u, dtype=np.uint8), ln)
+        substitute(arr, np.flatnonzero(rng.random(ln) < rng.uniform(0.01, 0.05)), rng)
+        dst = int(rng.integers(0, n - ln))
+        g[dst:dst + ln] = arr
+        regions.append((dst, dst + ln, "tandem"))
+        done += ln
+    return Genome(g, regions)
+
+
+def donor_of(genome: Genome, seed: int = SEED_DONOR_HUMAN, snv_rate: float = 0.001) -> np.ndarray:
+    """The sequenced individual: the reference with i.i.d. single-base
+    substitutions at `snv_rate` (no indels: the search is substitution-only)."""
+    rng = _rng(seed)
+    d = genome.codes.copy()
+    where = np.unique(rng.integers(0, genome.n, size=int(snv_rate * genome.n)))
+    substitute(d, where, rng)
+    return d
+
+
+def paired_reads(donor: np.ndarray, n_pairs: int, seed: int = SEED_READS_HUMAN, m: int = 150,
+                 insert_mean: float = 500.0, insert_sd: float = 50.0, err: float = 0.01,
+                 chunk: int = 500_000) -> ReadBatch:
+    """Paired-end reads, mates interleaved (read 2i = mate 1, 2i + 1 = mate 2).
+
+    Fragment length round(Normal(500, 50)) clipped to [300, 700], start
+    uniform; on a + fragment mate 1 is its first m bases and mate 2 the
+    reverse complement of its last m bases; a - fragment swaps the roles.
+    Each base then carries an i.i.d. sequencing substitution with
+    probability `err`.  origin/strand record each mate's true placement on
+    the reference coordinates (the donor has the same coordinates).
+    """
+    rng = _rng(seed)
+    N = len(donor)
+    n = 2 * n_pairs
+    nw = (m + 15) // 16
+    off = (np.arange(n + 1, dtype=np.uint64) * nw).astype(np.uint64)
+    words = np.zeros(n * nw, dtype=np.uint32)
+    origin = np.zeros(n, dtype=np.int64)
+    strand = np.zeros(n, dtype=np.uint8)
+    n_subs = np.zeros(n, dtype=np.int32)
+    for p0 in range(0, n_pairs, chunk):
+        c = min(chunk, n_pairs - p0)
+        L = np.clip(np.rint(rng.normal(insert_mean, insert_sd, size=c)), 300, 700).astype(np.int64)
+        s = (rng.random(c) * (N - L + 1)).astype(np.int64)
+        fwd = rng.integers(0, 2, size=c) == 0
+        left = donor[s[:, None] + np.arange(m)[None, :]]
+        right = donor[(s + L - m)[:, None] + np.arange(m)[None, :]]
+        right_rc = (3 - right)[:, ::-1]
+        left_rc = (3 - left)[:, ::-1]
+        m1 = np.where(fwd[:, None], left, right_rc)
+        m2 = np.where(fwd[:, None], right_rc, left)
+        mates = np.empty((2 * c, m), dtype=np.uint8)
+        mates[0::2] = m1
+        mates[1::2] = m2
+        hit = rng.random(mates.shape) < err
+        shift = rng.integers(1, 4, size=mates.shape, dtype=np.uint8)
+        mates = np.where(hit, (mates + shift) & 3, mates).astype(np.uint32)
+        r0 = 2 * p0
+        idx = np.arange(r0, r0 + 2 * c)
+        _pack_group(words, off, idx, mates)
+        o = np.empty(2 * c, dtype=np.int64)
+        o[0::2] = np.where(fwd, s, s + L - m)
+        o[1::2] = np.where(fwd, s + L - m, s)
+        st = np.empty(2 * c, dtype=np.uint8)
+        st[0::2] = np.where(fwd, 0, 1)
+        st[1::2] = np.where(fwd, 1, 0)
+        origin[r0:r0 + 2 * c] = o
+        strand[r0:r0 + 2 * c] = st
+        n_subs[r0:r0 + 2 * c] = hit.sum(axis=1)
+    return ReadBatch(words, off, np.full(n, m, dtype=np.uint16), np.full(n, 2, dtype=np.uint8),
+                     origin, strand, n_subs)
