@@ -273,6 +273,27 @@ int mica_server_get_stats(mica_server *srv, mica_server_stats *out);
    uncollected results. */
 void mica_server_stop(mica_server *srv);
 
+/* ---- hit-list offsets for callers that cannot allocate device memory ----
+ *
+ * The paper has no counterpart: this serves callers that may not call
+ * cudaMalloc (code running during CUDA graph capture, services whose device
+ * memory belongs to another allocator or pool, processes that must keep a
+ * fixed footprint after start-up).  mica_offsets_noalloc turns n per-read hit
+ * counts (device, uint64) into the n + 1 CSR offsets (device, uint64):
+ * d_offsets[0] = 0, d_offsets[i+1] = d_offsets[i] + d_counts[i] -- the
+ * offsets a mica_device_result holds for its listed hits.  It allocates
+ * nothing: its scratch is a fixed 64 KiB array that every GPU loading the
+ * library holds until exit.  n may be at most MICA_NOALLOC_MAX_COUNTS; larger
+ * n returns MICA_EINVAL before any work.  It runs on cuda_stream (NULL = the
+ * legacy default stream) on the current device and returns without waiting.
+ * The first call on a device looks the scratch up on that device; make that
+ * first call before any stream capture.  All calls share the one scratch
+ * array, so calls whose work overlaps on the GPU (other streams, other host
+ * threads) race: serialise them.
+ */
+#define MICA_NOALLOC_MAX_COUNTS (1ull << 24)
+int mica_offsets_noalloc(const uint64_t *d_counts, uint64_t n, uint64_t *d_offsets, void *cuda_stream);
+
 /* ---- parity probes: each exposes one step of the path on the GPU ---- */
 
 /* Suffix array of G$ (len + 1 entries, host output) built on the GPU by the

@@ -133,6 +133,7 @@ SIGNATURES = {
     "mica_autotune": (_i32, [P, P, P, P, P, _u64, _u32, _u32, P]),
     "mica_tuning_cache_store": (_i32, [ctypes.c_char_p, P, _u32, _u32, P]),
     "mica_tuning_cache_lookup": (_i32, [ctypes.c_char_p, P, _u32, _u32, P]),
+    "mica_offsets_noalloc": (_i32, [P, _u64, P, P]),
     "mica_server_params_default": (None, [P]),
     "mica_server_start": (_i32, [P, P, P]),
     "mica_server_submit": (_i32, [P, P, P, P, P, _u64, P]),
@@ -226,7 +227,7 @@ class _CudaArray:
 
     def __init__(self, ptr: int, shape, typestr: str):
         self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
-                                         "data": (int(ptr or 0), True), "version": 3, "strides": None}
+                                         "data": (int(ptr or 0), False), "version": 3, "strides": None}
 
 
 class DeviceResult:
@@ -453,6 +454,17 @@ class Server:
 
     def __exit__(self, *a):
         self.stop()
+
+
+NOALLOC_MAX_COUNTS = 1 << 24
+
+
+def offsets_noalloc(d_counts, n: int, d_offsets, stream=None) -> None:
+    """mica_offsets_noalloc: CSR offsets from per-read counts (device
+    pointers or torch CUDA tensors), without allocating device memory."""
+    ptr = lambda x: x if isinstance(x, int) else x.data_ptr()
+    _check(_lib.mica_offsets_noalloc(ctypes.c_void_p(ptr(d_counts)), n, ctypes.c_void_p(ptr(d_offsets)),
+                                     _stream_handle(stream)), "mica_offsets_noalloc")
 
 
 def debug_suffix_array(genome_acgt, device: int = 0) -> np.ndarray:

@@ -207,6 +207,8 @@ int validate_device_batch(const mica_index *idx, Workspace &w, mica_stats &st, c
 int validate_host_batch(const mica_index *idx, const uint64_t *off, const uint16_t *len, const uint8_t *k,
                         uint64_t n);
 void free_workspace(Workspace &w);
+int exclusive_scan_u64_scratch(const uint64_t *in, uint64_t n, uint64_t *out, unsigned long long *scratch,
+                               cudaStream_t s);
 int debug_occ(const mica_index *idx, const uint64_t *d_rows, uint64_t n, uint32_t *d_out, cudaStream_t s);
 int debug_locate(const mica_index *idx, const uint64_t *d_rows, uint64_t n, uint32_t *d_out, cudaStream_t s);
 int debug_seed(const mica_index *idx, const uint32_t *d_codes, uint32_t len, uint64_t n, uint32_t *d_out,

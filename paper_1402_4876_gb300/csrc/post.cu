@@ -354,6 +354,21 @@ unsigned grid1(uint64_t n, int block = 256)
 
 }  // namespace
 
+// Exclusive scan of n uint64 counts into n + 1 offsets with caller-provided
+// tile scratch of at least n / 2048 + 2 entries (no allocation).
+int exclusive_scan_u64_scratch(const uint64_t *in, uint64_t n, uint64_t *out, unsigned long long *scratch,
+                               cudaStream_t s)
+{
+    uint64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    uint64_t *ts = (uint64_t *)scratch;
+    if (ntiles) k_scan_tiles<uint64_t><<<(unsigned)ntiles, SCAN_THREADS, 0, s>>>(in, n, out, ts);
+    k_scan_sums<<<1, 1024, 0, s>>>(ts, ntiles);
+    unsigned g = (unsigned)std::min<uint64_t>(std::max<uint64_t>((n + 255) / 256, 1), 152 * 32);
+    k_scan_add<<<g, 256, 0, s>>>(out, n, ts);
+    MICA_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
 static uint64_t big_list_bytes(uint64_t n)
 {
     return (std::max<uint64_t>(n, 1) * 4 + 15) & ~15ull;
