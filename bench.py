@@ -48,6 +48,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="repeats64m", choices=["repeats64m", "uneven", "human", "serve"],
+                    help="repeats64m: the headline; uneven: mixed lengths and budgets; human: 3.1 Gbp genome, "
+                         "10M read pairs; serve: Poisson requests on a resident index")
+    ap.add_argument("--pairs", type=int, default=10_000_000, help="human: read pairs")
+    ap.add_argument("--genome-bp", type=int, default=synth.HUMAN_LEN, help="human/serve: genome length")
+    ap.add_argument("--serve-requests", type=int, default=60, help="serve: requests per load level")
     return ap.parse_args()
 
 
@@ -236,7 +242,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (seeded generator; the paper's YH/1000 Genomes data are not available)",
         "config": {"workload": WORKLOAD, "genome_bp": g.n, "reads_per_gpu": b.n, "read_len": 150, "k": 2,
-                   "hit_cap": HIT_CAP, "kernel": "persistent warp-pool", "index": "q=12 table, 64 B occ blocks, SA 1/16",
+                   "hit_cap": HIT_CAP, "kernel": "persistent warp-pool", "index": "q=12 table, 32 B bit-plane occurrence blocks, SA 1/16",
                    "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                    "parallelism": f"replicas x{world} (index per GPU, reads sharded, no collective)"},
         "latency_ms": {"p50": round(float(np.percentile(ms, 50)), 3), "p99": round(float(np.percentile(ms, 99)), 3),
@@ -253,7 +259,7 @@ def run_ours(args):
     peaks, src = measured_peaks()
     kernel_s = statistics.mean(kms) / 1e3
     read_bytes = 2 * 4 * int(np.sum((b.lengths.astype(np.int64) + 15) // 16))
-    alg_bytes = 64 * st["rank_blocks"] + 8 * st["seeds"] + read_bytes + 16 * st["intervals"]
+    alg_bytes = 32 * st["rank_blocks"] + 8 * st["seeds"] + read_bytes + 16 * st["intervals"]
     achieved = alg_bytes / kernel_s / 1e9
     traffic = profile_traffic(os.path.join(ROOT, "paper_1402_4876_gb300", "csrc", "search.cu"))
     out["roofline"] = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -297,6 +303,193 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# other workloads (one GPU; printed as one JSON line each)
+# ---------------------------------------------------------------------------
+
+def _device_batch(b, dev):
+    import torch
+    return (torch.from_numpy(b.words.view(np.int32)).to(dev), torch.from_numpy(b.word_off.view(np.int64)).to(dev),
+            torch.from_numpy(b.lengths.view(np.int16)).to(dev), torch.from_numpy(b.k).to(dev))
+
+
+def _time_kernel(idx, d, n, kernel, steps, warmup, stream, flush=None):
+    import torch
+    for _ in range(warmup):
+        idx.align_device(*d, n, hit_cap=HIT_CAP, kernel=kernel, stream=stream)
+    ms, kms, st = [], [], None
+    for _ in range(steps):
+        if flush is not None:
+            flush.fill_(len(ms))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = idx.align_device(*d, n, hit_cap=HIT_CAP, kernel=kernel, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        st = idx.stats()
+        kms.append(st["kernel_ms"])
+    return ms, kms, st, r
+
+
+def run_uneven(args):
+    """Batched uneven: 1M reads of 50/100/150/250 bp with k in 0..3 on the
+    64 Mbp repeat genome; one persistent launch vs one plain launch per
+    length class (and a single plain launch)."""
+    import torch
+    import paper_1402_4876_gb300 as mica
+    dev = torch.device("cuda", 0)
+    g = synth.genome_64m()
+    b = synth.reads_uneven(g, n=args.reads)
+    idx = mica.Index.build(synth.to_acgt_bytes(g.codes), kmer_q=12, sa_sample=16)
+    tune = idx.autotune(b.subset(np.arange(0, b.n, max(1, b.n // 20000))), hit_cap=HIT_CAP, repeats=1)
+    d = _device_batch(b, dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    out = {"metric": "reads/s aligned, uneven batch (lengths 50/100/150/250, k 0-3)", "unit": "reads/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "u32",
+           "data": "synthetic", "config": {"workload": "64 Mbp repeat genome, 1M reads, lengths uniform in "
+                                           "{50,100,150,250}, k uniform in 0..3, 30% from repeats, cap 1000",
+                                           "tuning": tune, "l2": "flushed between timed steps"}}
+    for kernel in ("persistent", "plain_by_length", "plain"):
+        ms, kms, st, r = _time_kernel(idx, d, b.n, kernel, args.steps, args.warmup, stream, flush)
+        out[kernel] = {"value": round(b.n * len(ms) / (sum(ms) / 1e3), 1), "ms_per_step": round(statistics.mean(ms), 3),
+                       "kernel_ms": round(statistics.mean(kms), 3), "launches": int(st["launches"]),
+                       "nodes": int(st["nodes"]), "seeds": int(st["seeds"]), "hits": int(r.n_hits)}
+    out["value"] = out["persistent"]["value"]
+    out["persistent_over_plain_by_length"] = round(out["persistent"]["value"] / out["plain_by_length"]["value"], 3)
+    print(json.dumps(out), flush=True)
+
+
+def run_human(args):
+    """Human-scale: a 3.1 Gbp synthetic genome (about 45% repeats) resident
+    in HBM and 10M read pairs (20M mates of 150 bp, 0.1% variants + 1%
+    sequencing error), each mate searched with k <= 2, cap 1000."""
+    import torch
+    import paper_1402_4876_gb300 as mica
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    g = synth.human_genome(args.genome_bp)
+    donor = synth.donor_of(g)
+    b = synth.paired_reads(donor, args.pairs)
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    idx = mica.Index.build(synth.to_acgt_bytes(g.codes), kmer_q=12, sa_sample=16)
+    build_s = time.perf_counter() - t0
+    info = idx.info()
+    stream = torch.cuda.current_stream(dev)
+    batch = 2_000_000
+    res = {}
+    for kernel in ("persistent", "plain"):
+        tot_ms, tot_kms, nodes, blocks, seeds, hits = 0.0, 0.0, 0, 0, 0, 0
+        for warm in range(1):
+            sub = b.subset(np.arange(0, min(b.n, 200_000)))
+            idx.align_device(*_device_batch(sub, dev), sub.n, hit_cap=HIT_CAP, kernel=kernel, stream=stream)
+        for r0 in range(0, b.n, batch):
+            sub = b.subset(np.arange(r0, min(b.n, r0 + batch))) if b.n > batch else b
+            d = _device_batch(sub, dev)
+            ms, kms, st, r = _time_kernel(idx, d, sub.n, kernel, 1, 0, stream)
+            tot_ms += ms[0]
+            tot_kms += kms[0]
+            nodes += st["nodes"]
+            blocks += st["rank_blocks"]
+            seeds += st["seeds"]
+            hits += r.n_hits
+        res[kernel] = {"value": round(b.n / (tot_ms / 1e3), 1), "pairs_per_s": round(b.n / 2 / (tot_ms / 1e3), 1),
+                       "ms_total": round(tot_ms, 1), "kernel_ms_total": round(tot_kms, 1), "nodes": int(nodes),
+                       "rank_blocks": int(blocks), "seeds": int(seeds), "hits": int(hits)}
+    peaks, src = measured_peaks()
+    p = res["persistent"]
+    alg = 32 * p["rank_blocks"] + 8 * p["seeds"]
+    achieved = alg / (p["kernel_ms_total"] / 1e3) / 1e9
+    out = {"metric": "150bp mates/s aligned (k<=2 FM search), human-scale genome", "value": p["value"],
+           "unit": "reads/s", "n_gpus": 1, "higher_is_better": True, "dtype": "u32", "data": "synthetic",
+           "config": {"workload": f"{g.n / 1e9:.2f} Gbp synthetic genome (~45% repeats), {args.pairs} pairs "
+                                  f"(2x150 bp), k<=2 per mate, cap 1000", "batch_reads": batch,
+                      "index_bytes": int(info["occ_bytes"] + info["mark_bytes"] + info["sample_bytes"] + info["table_bytes"])},
+           "persistent": res["persistent"], "plain": res["plain"],
+           "persistent_over_plain": round(res["persistent"]["value"] / res["plain"]["value"], 3),
+           "generate_s": round(gen_s, 1), "index_build_s": round(build_s, 1),
+           "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": round(achieved / peaks["hbm_gbs"], 4), "kernel": "k_persistent",
+                        "alg_bytes": int(alg), "peak_source": f"{src} hbm_gbs (copy bandwidth)"}}
+    print(json.dumps(out), flush=True)
+
+
+def run_serve(args):
+    """Serving: requests of log-uniform size (1e3..1e6 reads; lengths
+    100/150/250, k 0..2) arrive as a Poisson process at 50/70/90% of the
+    sustained rate into the continuous-batching server; p50/p99 latency is
+    submit to completion on the host clock."""
+    import threading
+
+    import torch
+    import paper_1402_4876_gb300 as mica
+    dev = torch.device("cuda", 0)
+    g = synth.human_genome(args.genome_bp)
+    donor = synth.donor_of(g)
+    idx = mica.Index.build(synth.to_acgt_bytes(g.codes), kmer_q=12, sa_sample=16)
+    rng = np.random.default_rng(synth.SEED_ARRIVALS)
+    pool = synth.paired_reads(donor, 1_000_000, seed=synth.SEED_READS_SERVE)
+    # mixed lengths: trim the 150 bp mates to 100 or extend budget classes; k 0..2
+    lens_choice = np.array([100, 150, 250])
+
+    def request(size):
+        ids = rng.integers(0, pool.n, size=size)
+        m = int(lens_choice[rng.integers(0, 3)])
+        reads = []
+        for i in ids:
+            r = pool.read(int(i))
+            if m <= 150:
+                reads.append(r[:m])
+            else:
+                o = int(pool.origin[i])
+                o = min(o, g.n - m)
+                reads.append(donor[o:o + m].copy())
+        words, off, lens = synth.pack_reads(reads)
+        return synth.ReadBatch(words, off, lens, rng.integers(0, 3, size=size).astype(np.uint8),
+                               np.zeros(size, np.int64), np.zeros(size, np.uint8), np.zeros(size, np.int32))
+
+    sizes = np.exp(rng.uniform(np.log(1e3), np.log(1e6), size=3 * args.serve_requests + 8)).astype(np.int64)
+    reqs = [request(int(min(s, 200_000))) for s in sizes[:8]]
+    # sustained rate: back-to-back requests
+    with mica.Server(idx, hit_cap=HIT_CAP, workers=2) as srv:
+        t = time.perf_counter()
+        ids = [srv.submit_batch(r) for r in reqs]
+        for i in ids:
+            srv.wait(i)
+        sustained = sum(r.n for r in reqs) / (time.perf_counter() - t)
+    levels = {}
+    for frac in (0.5, 0.7, 0.9):
+        batch = [request(int(min(s, 200_000))) for s in sizes[8:8 + args.serve_requests]]
+        mean_reads = np.mean([r.n for r in batch])
+        rate = frac * sustained / mean_reads                     # requests per second
+        gaps = rng.exponential(1.0 / rate, size=len(batch))
+        lat = []
+        with mica.Server(idx, hit_cap=HIT_CAP, workers=2) as srv:
+            t0 = time.perf_counter()
+            ids = []
+            for gap, r in zip(gaps, batch):
+                time.sleep(gap)
+                ids.append(srv.submit_batch(r))
+            for i in ids:
+                _, l = srv.wait(i)
+                lat.append(l)
+            el = time.perf_counter() - t0
+            st = srv.stats()
+        levels[f"{int(frac * 100)}%"] = {"p50_ms": round(float(np.percentile(lat, 50)), 2),
+                                         "p99_ms": round(float(np.percentile(lat, 99)), 2),
+                                         "reads_per_s": round(sum(r.n for r in batch) / el, 1),
+                                         "requests": len(batch), "ticks": int(st["ticks"])}
+    out = {"metric": "serving: p50/p99 request latency and sustained reads/s", "value": round(sustained, 1),
+           "unit": "reads/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+           "config": {"workload": f"{g.n / 1e9:.2f} Gbp genome resident; Poisson requests of log-uniform "
+                                  f"1e3..2e5 reads (100/150/250 bp, k 0..2)", "workers": 2},
+           "levels": levels}
+    print(json.dumps(out), flush=True)
 
 
 # ---------------------------------------------------------------------------
@@ -351,8 +544,14 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    else:
+    elif args.workload == "repeats64m":
         run_ours(args)
+    elif args.workload == "uneven":
+        run_uneven(args)
+    elif args.workload == "human":
+        run_human(args)
+    else:
+        run_serve(args)
 
 
 if __name__ == "__main__":

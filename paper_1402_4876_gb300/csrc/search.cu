@@ -262,7 +262,7 @@ constexpr uint32_t IDLE_LIMIT = 1u << 22;    // idle rounds (>= 1 us each) befor
 constexpr uint32_t SPIN_LIMIT = 1u << 22;    // waits for a reserved queue entry
 constexpr uint32_t DONATE_MIN = 96;          // stack depth that makes a warp share work
 constexpr uint32_t DONATE_N = 64;
-constexpr int DEFAULT_SHAPE = 1;
+constexpr int DEFAULT_SHAPE = 3;   // 128-node stacks, 8 warps, 4 CTAs per SM: fastest measured
 
 struct PersistArgs {
     IndexView ix;
@@ -841,7 +841,6 @@ static PersistShape g_shapes[] = {
     MICA_SHAPE(256, 8, 4),
     MICA_SHAPE(256, 4, 8),
     MICA_SHAPE(128, 8, 4),
-    MICA_SHAPE(128, 8, 5),
 };
 #undef MICA_SHAPE
 constexpr int N_SHAPES = sizeof(g_shapes) / sizeof(g_shapes[0]);

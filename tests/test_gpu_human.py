@@ -1,0 +1,68 @@
+"""Human-scale parity: the 3.1 Gbp synthetic genome (about 45% repeats)
+resident in HBM, paired 150 bp mates with k <= 2 and cap 1000, in the
+launch shape the human-scale benchmark uses.
+
+The oracle cannot build its index for 3.1 Gbp within a test, so sampled
+reads are checked one by one against its brute-force Hamming scan of both
+strands (exact totals; exact hit lists where the total is within the cap;
+listed hits a subset otherwise), and every read against properties that
+hold at any size."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import gpu_common as gc
+from tests import refcheck
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def human():
+    g = synth.human_genome()
+    donor = synth.donor_of(g)
+    b = synth.paired_reads(donor, 250_000)                      # 500,000 mates
+    idx = gc.mica().Index.build(synth.to_acgt_bytes(g.codes), kmer_q=12, sa_sample=16)
+    yield g, b, idx
+    idx.free()
+
+
+def test_human_sampled_reads_equal_bruteforce(human):
+    g, b, idx = human
+    res = idx.align_batch(b, hit_cap=1000, kernel="persistent")
+    rng = np.random.default_rng(44)
+    sample = np.sort(rng.choice(b.n, 32, replace=False))
+    sub = b.subset(sample)
+    bf = oracle.bruteforce(g.codes, sub)
+    for j, i in enumerate(sample):
+        got = res.hits_of(int(i))
+        want = bf.as_tuples(j)
+        assert int(res.total[i]) == len(want)
+        if len(want) <= 1000:
+            assert got == want
+        else:
+            assert len(got) == 1000 and set(got) <= set(want)
+
+
+def test_human_properties_and_kernels_agree(human):
+    g, b, idx = human
+    res = idx.align_batch(b, hit_cap=1000, kernel="persistent")
+    cnt = np.diff(res.offsets.astype(np.int64))
+    assert np.all(cnt == np.minimum(res.total.astype(np.int64), 1000))
+    assert np.all(res.hits["mm"] <= 2)
+    assert np.all(res.hits["pos"].astype(np.int64) <= g.n - 150)
+    # most mates carry at most two differences from the reference
+    assert np.mean(res.total > 0) > 0.75
+    rng = np.random.default_rng(45)
+    for i in rng.choice(b.n, 200, replace=False):
+        r = b.read(int(i))
+        hits = res.hits_of(int(i))
+        key = [(p, s) for p, s, _ in hits]
+        assert key == sorted(key)
+        for p, s, d in hits[:20]:
+            w = g.codes[p:p + 150]
+            assert int(((refcheck.rc(r) if s else r) != w).sum()) == d
+    sub = b.subset(np.arange(0, 50_000))
+    gc.assert_same(idx.align_batch(sub, hit_cap=1000, kernel="plain"),
+                   idx.align_batch(sub, hit_cap=1000, kernel="persistent"), "plain vs persistent")
