@@ -54,12 +54,42 @@ def parse():
     ap.add_argument("--pairs", type=int, default=10_000_000, help="human: read pairs")
     ap.add_argument("--genome-bp", type=int, default=synth.HUMAN_LEN, help="human/serve: genome length")
     ap.add_argument("--serve-requests", type=int, default=60, help="serve: requests per load level")
+    ap.add_argument("--serve-max-size", type=int, default=200_000, help="serve: largest request (reads)")
     return ap.parse_args()
 
 
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
             int(os.environ.get("WORLD_SIZE", 1)))
+
+
+# ---- replicas: every GPU holds its own index and aligns its own batch; the
+# ranks meet only for a barrier and the max-over-ranks time (gloo, host) ----
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seed(rank: int) -> int:
+    """Each replica aligns its own batch: reads drawn with a per-rank seed."""
+    return synth.SEED_READS_64M + rank
+
+
+def whole_job_rate(reads_per_rank: int, world: int, steps: int, max_ms: float) -> float:
+    """Units all ranks processed divided by the slowest rank's time."""
+    return world * reads_per_rank * steps / (max_ms / 1e3)
 
 
 def cpu_info():
@@ -167,8 +197,22 @@ def profile_traffic(kernel_src: str):
 
 def make_workload(n_reads: int, rank: int):
     g = synth.genome_64m()
-    reads = synth.reads_64m(g, n=n_reads, seed=synth.SEED_READS_64M + rank)
+    reads = synth.reads_64m(g, n=n_reads, seed=replica_seed(rank))
     return g, reads
+
+
+def gather_ceilings(mica, idx, device: int) -> dict:
+    """Random 32-byte gather ceilings measured after the timed region: one
+    over a buffer the size of the search's hot index arrays (occurrence
+    blocks + q-mer table: the same L2/HBM mix as the search), one over
+    1.5 GiB (HBM)."""
+    info = idx.info()
+    hot = max(1 << 20, (info["occ_bytes"] + info["table_bytes"] + 31) // 32 * 32)
+    a = mica.gather_ceiling(hot, 32, loads=1 << 27, repeats=3, device=device)
+    b = mica.gather_ceiling(3 << 29, 32, loads=1 << 27, repeats=3, device=device)
+    return {"load_bytes": 32, "index_sized_bytes": hot, "index_sized_gbs": round(a["gbs"], 1),
+            "hbm_bytes": 3 << 29, "hbm_gbs": round(b["gbs"], 1),
+            "what": "mica_gather_ceiling: independent random 32 B loads, full occupancy"}
 
 
 def run_ours(args):
@@ -193,24 +237,12 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
 
     def device_steps(kernel: str, steps: int, warmup: int):
         for _ in range(warmup):
             idx.align_device(d_words, d_off, d_len, d_k, b.n, hit_cap=HIT_CAP, kernel=kernel, stream=stream)
         ms, kms, stats = [], [], []
-        barrier()
+        barrier(world)
         torch.cuda.synchronize(dev)
         for _ in range(steps):
             flush.fill_(rank + len(ms))                      # evict L2 between timed steps
@@ -226,14 +258,14 @@ def run_ours(args):
             kms.append(st["kernel_ms"])
             stats.append(st)
         torch.cuda.synchronize(dev)
-        barrier()
+        barrier(world)
         return ms, kms, stats, r
 
     with ClockSampler(local) as clk:
         ms, kms, stats, dres = device_steps("persistent", args.steps, args.warmup)
     clocks = clk.summary()
-    total_ms = max_over_ranks(sum(ms))
-    value = world * b.n * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(ms), world)
+    value = whole_job_rate(b.n, world, args.steps, total_ms)
     n_hits = dres.n_hits
 
     out = {
@@ -254,6 +286,7 @@ def run_ours(args):
     out["work_per_step"] = {k: int(st[k]) for k in ("seeds", "nodes", "rank_blocks", "intervals", "located",
                                                     "lf_steps", "spills")}
     out["gpu_launches"] = int(sum(s["launches"] for s in stats))
+    out["graph_replays"] = int(sum(s["graph_replays"] for s in stats))
 
     # roofline of the dominant kernel (the persistent search)
     peaks, src = measured_peaks()
@@ -268,11 +301,15 @@ def run_ours(args):
                        "alg_bytes_per_launch": int(alg_bytes),
                        "peak_source": f"{src} hbm_gbs (copy bandwidth)"}
     out["clocks"] = clocks
+    out["roofline"]["gather_ceiling"] = gather_ceilings(mica, idx, local)
+    gc_idx = out["roofline"]["gather_ceiling"]["index_sized_gbs"]
+    out["roofline"]["frac_of_gather_ceiling"] = round(achieved / gc_idx, 4) if gc_idx else None
+    out["rank_blocks_per_s"] = round(st["rank_blocks"] / kernel_s, 1)
 
     if not args.no_plain:
         pms, pkms, pstats, _ = device_steps("plain", max(1, min(args.steps, 3)), 1)
-        ptotal = max_over_ranks(sum(pms))
-        pval = world * b.n * len(pms) / (ptotal / 1e3)
+        ptotal = max_over_ranks(sum(pms), world)
+        pval = whole_job_rate(b.n, world, len(pms), ptotal)
         out["plain"] = {"value": round(pval, 1), "unit": "reads/s", "ms_per_step": round(ptotal / len(pms), 3),
                         "kernel_ms": round(statistics.mean(pkms), 3),
                         "persistent_over_plain": round(value / pval, 3)}
@@ -282,13 +319,13 @@ def run_ours(args):
         pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
         hw, ho, hl, hk = pin(b.words), pin(b.word_off), pin(b.lengths), pin(b.k)
         idx.align(hw, ho, hl, hk, hit_cap=HIT_CAP, stream=stream)
-        barrier()
+        barrier(world)
         t = time.perf_counter()
         e2e_steps = max(1, min(args.steps, 3))
         for _ in range(e2e_steps):
             res = idx.align(hw, ho, hl, hk, hit_cap=HIT_CAP, stream=stream)
         torch.cuda.synchronize(dev)
-        el = max_over_ranks(time.perf_counter() - t)
+        el = max_over_ranks(time.perf_counter() - t, world)
         h2d = hw.nbytes + ho.nbytes + hl.nbytes + hk.nbytes
         d2h = res.total.nbytes + res.offsets.nbytes + res.hits.nbytes
         out["e2e"] = {"value": round(world * b.n * e2e_steps / el, 1), "unit": "reads/s",
@@ -433,28 +470,9 @@ def run_serve(args):
     donor = synth.donor_of(g)
     idx = mica.Index.build(synth.to_acgt_bytes(g.codes), kmer_q=12, sa_sample=16)
     rng = np.random.default_rng(synth.SEED_ARRIVALS)
-    pool = synth.paired_reads(donor, 1_000_000, seed=synth.SEED_READS_SERVE)
-    # mixed lengths: trim the 150 bp mates to 100 or extend budget classes; k 0..2
-    lens_choice = np.array([100, 150, 250])
-
-    def request(size):
-        ids = rng.integers(0, pool.n, size=size)
-        m = int(lens_choice[rng.integers(0, 3)])
-        reads = []
-        for i in ids:
-            r = pool.read(int(i))
-            if m <= 150:
-                reads.append(r[:m])
-            else:
-                o = int(pool.origin[i])
-                o = min(o, g.n - m)
-                reads.append(donor[o:o + m].copy())
-        words, off, lens = synth.pack_reads(reads)
-        return synth.ReadBatch(words, off, lens, rng.integers(0, 3, size=size).astype(np.uint8),
-                               np.zeros(size, np.int64), np.zeros(size, np.uint8), np.zeros(size, np.int32))
-
-    sizes = np.exp(rng.uniform(np.log(1e3), np.log(1e6), size=3 * args.serve_requests + 8)).astype(np.int64)
-    reqs = [request(int(min(s, 200_000))) for s in sizes[:8]]
+    n_req = args.serve_requests
+    allreq = synth.serve_requests(donor, 8 + 3 * n_req, max_size=args.serve_max_size)
+    reqs = allreq[:8]
     # sustained rate: back-to-back requests
     with mica.Server(idx, hit_cap=HIT_CAP, workers=2) as srv:
         t = time.perf_counter()
@@ -463,8 +481,8 @@ def run_serve(args):
             srv.wait(i)
         sustained = sum(r.n for r in reqs) / (time.perf_counter() - t)
     levels = {}
-    for frac in (0.5, 0.7, 0.9):
-        batch = [request(int(min(s, 200_000))) for s in sizes[8:8 + args.serve_requests]]
+    for li, frac in enumerate((0.5, 0.7, 0.9)):
+        batch = allreq[8 + li * n_req: 8 + (li + 1) * n_req]
         mean_reads = np.mean([r.n for r in batch])
         rate = frac * sustained / mean_reads                     # requests per second
         gaps = rng.exponential(1.0 / rate, size=len(batch))
@@ -487,7 +505,8 @@ def run_serve(args):
     out = {"metric": "serving: p50/p99 request latency and sustained reads/s", "value": round(sustained, 1),
            "unit": "reads/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
            "config": {"workload": f"{g.n / 1e9:.2f} Gbp genome resident; Poisson requests of log-uniform "
-                                  f"1e3..2e5 reads (100/150/250 bp, k 0..2)", "workers": 2},
+                                  f"1e3..{args.serve_max_size} reads (100/150/250 bp, k 0..2)",
+                      "workers": 2, "requests_per_level": n_req},
            "levels": levels}
     print(json.dumps(out), flush=True)
 

@@ -118,6 +118,9 @@ typedef struct {
     uint64_t warp_rounds;    /* persistent kernel: work-pool rounds over all warps */
     uint64_t lane_ops;       /* persistent kernel: node extensions + seed lookups done by lanes */
     uint64_t rounds_multi, rounds_single, rounds_seed;   /* persistent kernel rounds by kind of work */
+    uint64_t graph_captures;  /* the call captured its pipeline as a CUDA graph (new batch shape) */
+    uint64_t graph_replays;   /* the call ran as one replay of a captured graph */
+    uint64_t graph_fallbacks; /* a replay overflowed a buffer; the regular path recomputed the call */
     float search_ms;         /* device time of the search phase (kernel + its control copies) */
     float kernel_ms;         /* device time of the search kernel launch(es) alone */
     float total_ms;          /* device time of the whole call */
@@ -293,6 +296,25 @@ void mica_server_stop(mica_server *srv);
  */
 #define MICA_NOALLOC_MAX_COUNTS (1ull << 24)
 int mica_offsets_noalloc(const uint64_t *d_counts, uint64_t n, uint64_t *d_offsets, void *cuda_stream);
+
+/* ---- random-gather ceiling (measurement) ----
+ *
+ * The paper locates the BWT phase's bottleneck in access to the index in
+ * memory (Section 3); the search reads one 32-byte occurrence block per
+ * dependent step at a random row.  mica_gather_ceiling measures what this GPU
+ * sustains for that pattern: every thread of a full-occupancy grid makes
+ * independent loads of load_bytes (16, 32, 64 or 128) at uniformly random
+ * load_bytes-aligned offsets of a fresh device buffer of buffer_bytes (a
+ * multiple of load_bytes, >= 4096), about `loads` loads per launch.  *gbs
+ * (required) = bytes loaded / best launch time over `repeats` timed launches
+ * (0 = 1) after one warm-up, in 1e9 bytes/s; *ms (optional) = that time.
+ * A buffer well above L2 gives the HBM random-sector ceiling, one the size
+ * of a small index the L2 one.  The buffer is allocated and freed inside the
+ * call on `device`; MICA_ENOMEM if it does not fit, MICA_EINVAL on bad sizes.
+ * Synchronous on the legacy default stream.
+ */
+int mica_gather_ceiling(int device, uint64_t buffer_bytes, uint32_t load_bytes, uint64_t loads, uint32_t repeats,
+                        double *gbs, double *ms);
 
 /* ---- parity probes: each exposes one step of the path on the GPU ---- */
 

@@ -63,7 +63,7 @@ class Stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_uint64) for name in
                 ("tasks", "seeds", "nodes", "rank_blocks", "intervals", "located", "lf_steps",
                  "spills", "retries", "launches", "warp_rounds", "lane_ops", "rounds_multi", "rounds_single",
-                 "rounds_seed")] + [("search_ms", ctypes.c_float), ("kernel_ms", ctypes.c_float),
+                 "rounds_seed", "graph_captures", "graph_replays", "graph_fallbacks")] + [("search_ms", ctypes.c_float), ("kernel_ms", ctypes.c_float),
                                                       ("total_ms", ctypes.c_float)]
 
     def as_dict(self) -> dict:
@@ -134,6 +134,7 @@ SIGNATURES = {
     "mica_tuning_cache_store": (_i32, [ctypes.c_char_p, P, _u32, _u32, P]),
     "mica_tuning_cache_lookup": (_i32, [ctypes.c_char_p, P, _u32, _u32, P]),
     "mica_offsets_noalloc": (_i32, [P, _u64, P, P]),
+    "mica_gather_ceiling": (_i32, [ctypes.c_int, _u64, _u32, _u64, _u32, P, P]),
     "mica_server_params_default": (None, [P]),
     "mica_server_start": (_i32, [P, P, P]),
     "mica_server_submit": (_i32, [P, P, P, P, P, _u64, P]),
@@ -465,6 +466,16 @@ def offsets_noalloc(d_counts, n: int, d_offsets, stream=None) -> None:
     ptr = lambda x: x if isinstance(x, int) else x.data_ptr()
     _check(_lib.mica_offsets_noalloc(ctypes.c_void_p(ptr(d_counts)), n, ctypes.c_void_p(ptr(d_offsets)),
                                      _stream_handle(stream)), "mica_offsets_noalloc")
+
+
+def gather_ceiling(buffer_bytes: int, load_bytes: int = 32, loads: int = 1 << 28, repeats: int = 3,
+                   device: int = 0) -> dict:
+    """mica_gather_ceiling: GB/s of independent random `load_bytes` loads
+    from a device buffer of `buffer_bytes` (the search's access pattern)."""
+    gbs, ms = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.mica_gather_ceiling(device, buffer_bytes, load_bytes, loads, repeats, ctypes.byref(gbs),
+                                    ctypes.byref(ms)), "mica_gather_ceiling")
+    return {"gbs": gbs.value, "ms": ms.value, "buffer_bytes": buffer_bytes, "load_bytes": load_bytes}
 
 
 def debug_suffix_array(genome_acgt, device: int = 0) -> np.ndarray:

@@ -53,6 +53,10 @@ void free_workspace(Workspace &w)
         if (e) { cudaEventDestroy(e); e = nullptr; }
     for (auto &e : w.kev)
         if (e) { cudaEventDestroy(e); e = nullptr; }
+    if (w.gexec) { cudaGraphExecDestroy(w.gexec); w.gexec = nullptr; }
+    if (w.gstream) { cudaStreamDestroy(w.gstream); w.gstream = nullptr; }
+    if (w.pin_tmpl) { cudaFreeHost(w.pin_tmpl); w.pin_tmpl = nullptr; }
+    if (w.pin_status) { cudaFreeHost(w.pin_status); w.pin_status = nullptr; }
 }
 
 static int validate_params(const mica_index_params &p)
@@ -81,11 +85,6 @@ static int encode_genome(const uint8_t *acgt, uint64_t len, std::vector<uint8_t>
     return 0;
 }
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) { if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev); else prev = -1; }
-    ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
-};
 
 // ---- index file ----
 
@@ -125,8 +124,101 @@ static int read_array(FILE *f, DevBuf &b, uint64_t bytes)
 
 // ---- align orchestration ----
 
+// The persistent pipeline as one CUDA graph per batch shape: captured the
+// first time a shape (input addresses, read count, cap, kernel shape, buffer
+// addresses) is seen, then replayed with a single host synchronisation.  Any
+// overflow, error or read with more than 4096 listed hits sets done = false
+// and the caller runs the regular path, which recomputes the batch.
+static int align_graph(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd,
+                       const mica_align_params &p, cudaStream_t s, uint64_t *nh, bool &done)
+{
+    done = false;
+    uint64_t n = rd.n;
+    if (!w.pin_tmpl) {
+        MICA_CUDA_TRY(cudaMallocHost(&w.pin_tmpl, 256));
+        MICA_CUDA_TRY(cudaMallocHost(&w.pin_status, 256));
+    }
+    if (!w.gstream) MICA_CUDA_TRY(cudaStreamCreateWithFlags(&w.gstream, cudaStreamNonBlocking));
+    SearchCtl tmpl;
+    int grid = 0, shape = 0, rc;
+    if ((rc = prepare_persistent(idx, w, n, idx->tuning.shape, tmpl, grid, shape))) return rc;
+    w.hit_capacity = std::max<uint64_t>(w.hit_capacity, 4 * n + 65536);
+    if ((rc = reserve_post(w, n, w.iv_cap, w.hit_capacity))) return rc;
+    if (w.spill_dirty) {
+        MICA_CUDA_TRY(cudaMemsetAsync(w.spill.p, 0, (size_t)w.spill_cap * sizeof(WorkItem), s));
+        w.spill_dirty = false;
+    }
+    memcpy(w.pin_tmpl, &tmpl, sizeof(tmpl));
+    uint64_t key[16] = {(uint64_t)rd.words, (uint64_t)rd.word_off, (uint64_t)rd.len, (uint64_t)rd.k, n,
+                        p.hit_cap, (uint64_t)shape, (uint64_t)grid, (uint64_t)w.ctl.p, (uint64_t)w.iv.p,
+                        (uint64_t)w.spill.p, (uint64_t)w.iv_sorted.p, (uint64_t)w.hits.p, (uint64_t)w.big.p,
+                        (uint64_t)w.scan_tmp.p, w.hit_capacity ^ ((uint64_t)w.iv_cap << 40) ^ ((uint64_t)w.spill_cap << 20)};
+    if (!w.gexec || memcmp(key, w.gkey, sizeof(key)) != 0) {
+        if (w.gexec) { cudaGraphExecDestroy(w.gexec); w.gexec = nullptr; }
+        uint64_t L = 0;
+        MICA_CUDA_TRY(cudaStreamBeginCapture(w.gstream, cudaStreamCaptureModeThreadLocal));
+        int crc = enqueue_persistent(idx, w, rd, shape, grid, (const SearchCtl *)w.pin_tmpl, w.gstream);
+        if (!crc) crc = enqueue_post_device(idx, w, rd, p.hit_cap, w.hit_capacity, w.gstream, w.pin_status, L);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(w.gstream, &g);
+        if (crc || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return 0;   // capture not possible: the regular path runs
+        }
+        e = cudaGraphInstantiate(&w.gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { w.gexec = nullptr; cudaGetLastError(); return 0; }
+        memcpy(w.gkey, key, sizeof(key));
+        w.gkey[15] = key[15];
+        st.graph_captures++;
+        w.glaunches = L + 1;
+    }
+    MICA_CUDA_TRY(cudaEventRecord(w.ev[0], s));
+    MICA_CUDA_TRY(cudaGraphLaunch(w.gexec, s));
+    MICA_CUDA_TRY(cudaEventRecord(w.ev[2], s));
+    MICA_CUDA_TRY(cudaEventSynchronize(w.ev[2]));
+    SearchCtl out;
+    memcpy(&out, w.pin_status, sizeof(out));
+    const char *stp = (const char *)w.pin_status + sizeof(SearchCtl);
+    uint64_t nhits, steps;
+    unsigned int cnts[2];
+    memcpy(&nhits, stp, 8);
+    memcpy(&steps, stp + 8, 8);
+    memcpy(cnts, stp + 16, 8);
+    if (out.error & ERR_TIMEOUT) { w.spill_dirty = true; return MICA_ETIMEOUT; }
+    if (out.error) {
+        // let the regular path grow the buffers and recompute
+        w.spill_dirty = true;
+        return 0;
+    }
+    if (nhits > w.hit_capacity) { w.hit_capacity = 2 * nhits; return 0; }
+    if (cnts[1]) return 0;   // a read above the shared-memory sort size
+    st.tasks = 2 * n;
+    st.seeds = out.seeds;
+    st.nodes = out.nodes;
+    st.rank_blocks = out.rank_blocks;
+    st.intervals = out.iv_count;
+    st.spills = out.spills;
+    st.warp_rounds = out.rounds;
+    st.lane_ops = out.lane_ops;
+    st.rounds_multi = out.rounds_kind[0];
+    st.rounds_single = out.rounds_kind[1];
+    st.rounds_seed = out.rounds_kind[2];
+    st.located = nhits;
+    st.lf_steps = steps;
+    st.launches += w.glaunches;
+    st.graph_replays++;
+    st.kernel_ms = elapsed_ms(w.kev[0], w.kev[1]);
+    st.search_ms = st.kernel_ms;
+    st.total_ms = elapsed_ms(w.ev[0], w.ev[2]);
+    *nh = nhits;
+    done = true;
+    return 0;
+}
+
 int align_on_device(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd,
-                    const mica_align_params &p, cudaStream_t s, uint64_t *nh)
+                    const mica_align_params &p, cudaStream_t s, uint64_t *nh, bool allow_graph)
 {
     for (auto &e : w.ev)
         if (!e) MICA_CUDA_TRY(cudaEventCreate(&e));
@@ -135,6 +227,12 @@ int align_on_device(const mica_index *idx, Workspace &w, mica_stats &st, const R
     uint64_t launches = st.launches;   // the batch check already counted
     st = mica_stats{};
     st.launches = launches;
+    if (allow_graph && p.kernel == MICA_KERNEL_PERSISTENT && rd.n > 0) {
+        bool done = false;
+        if (int rc = align_graph(idx, w, st, rd, p, s, nh, done)) return rc;
+        if (done) return 0;
+        st.graph_fallbacks++;
+    }
     MICA_CUDA_TRY(cudaEventRecord(w.ev[0], s));
     SearchConfig cfg{};
     cfg.kernel = p.kernel;
@@ -149,9 +247,9 @@ int align_on_device(const mica_index *idx, Workspace &w, mica_stats &st, const R
     if ((rc = run_post(idx, w, st, rd, p.hit_cap, s, nh))) return rc;
     MICA_CUDA_TRY(cudaEventRecord(w.ev[2], s));
     MICA_CUDA_TRY(cudaEventSynchronize(w.ev[2]));
-    cudaEventElapsedTime(&st.search_ms, w.ev[0], w.ev[1]);
-    cudaEventElapsedTime(&st.kernel_ms, w.kev[0], w.kev[1]);
-    cudaEventElapsedTime(&st.total_ms, w.ev[0], w.ev[2]);
+    st.search_ms = elapsed_ms(w.ev[0], w.ev[1]);
+    st.kernel_ms = elapsed_ms(w.kev[0], w.kev[1]);
+    st.total_ms = elapsed_ms(w.ev[0], w.ev[2]);
     return 0;
 }
 

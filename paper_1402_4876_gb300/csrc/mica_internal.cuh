@@ -132,6 +132,13 @@ struct DevBuf {
 int dev_reserve(DevBuf &b, size_t bytes);   // grow-only device buffer
 void dev_release(DevBuf &b);
 
+// Makes `dev` current for a scope and restores the caller's device after.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) { if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev); else prev = -1; }
+    ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
 // Per-index workspace reused across align calls.
 struct Workspace {
     DevBuf ctl, iv, iv_sorted, iv_cnt, iv_off, total, keep, hit_off, hits, spill, big, scan_tmp;
@@ -143,6 +150,13 @@ struct Workspace {
     bool spill_dirty = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // call timing
     cudaEvent_t kev[2] = {nullptr, nullptr};                      // search kernel timing
+    // captured pipeline for a repeated batch shape (persistent kernel)
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t gstream = nullptr;
+    void *pin_tmpl = nullptr, *pin_status = nullptr;              // pinned host blocks
+    uint64_t gkey[16] = {};
+    uint64_t hit_capacity = 0;
+    uint64_t glaunches = 0;   // kernels in the captured graph
 };
 
 }  // namespace mica
@@ -172,6 +186,30 @@ namespace mica {
 
 void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line);
 
+// Records a timing event on s.  While s is being captured into a graph a
+// plain record is only a dependency marker, so the event becomes an external
+// event-record node, recorded on every replay.
+inline cudaError_t record_event(cudaEvent_t e, cudaStream_t s)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t r = cudaStreamIsCapturing(s, &cs);
+    if (r != cudaSuccess) return r;
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                                               : cudaEventRecord(e, s);
+}
+
+// Milliseconds between two recorded events; 0 (and the error cleared) when
+// the pair cannot be timed.
+inline float elapsed_ms(cudaEvent_t a, cudaEvent_t b)
+{
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+        (void)cudaGetLastError();
+        ms = 0.f;
+    }
+    return ms;
+}
+
 // index_build.cu
 int build_suffix_array(const uint8_t *d_codes, uint64_t n, uint32_t *d_sa, cudaStream_t s);
 int build_index_from_codes(const uint8_t *d_codes, uint64_t n, const mica_index_params &p,
@@ -194,6 +232,10 @@ constexpr uint32_t LEN_CLASSES = 4;   // 1-64, 65-128, 129-192, 193-256 bases
 int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd,
                const SearchConfig &cfg, cudaStream_t s);
 int search_shape_count();
+int prepare_persistent(const mica_index *idx, Workspace &w, uint64_t n, int shape_in, SearchCtl &tmpl,
+                       int &grid, int &shape);
+int enqueue_persistent(const mica_index *idx, Workspace &w, const ReadsView &rd, int shape, int grid,
+                       const SearchCtl *pinned_tmpl, cudaStream_t s);
 int search_shape_info(int shape, int *scap, int *warps, int *minb);
 
 // post.cu
@@ -201,12 +243,15 @@ int run_post(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsVie
              cudaStream_t s, uint64_t *n_hits_out);
 // capi.cu: the whole path on one workspace (validation of device batches included)
 int align_on_device(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd,
-                    const mica_align_params &p, cudaStream_t s, uint64_t *nh);
+                    const mica_align_params &p, cudaStream_t s, uint64_t *nh, bool allow_graph = true);
 int validate_device_batch(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd,
                           cudaStream_t s);
 int validate_host_batch(const mica_index *idx, const uint64_t *off, const uint16_t *len, const uint8_t *k,
                         uint64_t n);
 void free_workspace(Workspace &w);
+int enqueue_post_device(const mica_index *idx, Workspace &w, const ReadsView &rd, uint32_t hit_cap,
+                        uint64_t hit_capacity, cudaStream_t s, void *status, uint64_t &launches);
+int reserve_post(Workspace &w, uint64_t n, uint32_t iv_cap, uint64_t hit_capacity);
 int exclusive_scan_u64_scratch(const uint64_t *in, uint64_t n, uint64_t *out, unsigned long long *scratch,
                                cudaStream_t s);
 int debug_occ(const mica_index *idx, const uint64_t *d_rows, uint64_t n, uint32_t *d_out, cudaStream_t s);

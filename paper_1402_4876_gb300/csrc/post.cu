@@ -20,6 +20,7 @@ constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_ITEMS = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 constexpr uint32_t SMALL_SORT = 32;
+constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t SMEM_SORT = 4096;
 
 // ---- exclusive scan (n values -> n + 1 offsets) ----
@@ -119,10 +120,13 @@ int exclusive_scan(DevBuf &tmp, const T *in, uint64_t n, uint64_t *out, cudaStre
 
 // ---- intervals grouped by read ----
 
-__global__ void k_iv_scatter(const Interval *__restrict__ iv, uint32_t count,
-                             const uint64_t *__restrict__ iv_off, uint32_t *__restrict__ cursor,
+// count: the search's interval counter on the device, read here (capped at
+// the buffer's capacity) so the launch needs no host round trip
+__global__ void k_iv_scatter(const Interval *__restrict__ iv, const unsigned int *__restrict__ count_p,
+                             uint32_t cap, const uint64_t *__restrict__ iv_off, uint32_t *__restrict__ cursor,
                              Interval *__restrict__ out)
 {
+    uint32_t count = min(*count_p, cap);
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
         Interval x = iv[e];
         uint32_t at = atomicSub(&cursor[x.read], 1u) - 1u;
@@ -135,32 +139,137 @@ __device__ __forceinline__ uint64_t iv_key(const Interval &x)
     return ((uint64_t)(x.meta & 3u) << 33) | ((uint64_t)((x.meta >> 2) & 1u) << 32) | x.l;
 }
 
+// Per read: total = the sum of its interval sizes (exact) and keep = the
+// rows it lists, min(total, cap).  When total > cap the listed rows are the
+// first cap in the order (d, strand, SA row); k_expand takes rows from the
+// front of the read's interval list until it has `keep`, so that list must
+// start with the kept rows.  A read with at most SUMMARY_SMALL intervals is
+// done here by one thread (insertion sort into key order when over the cap);
+// a longer list goes to `many` for k_summarize_many.
+constexpr uint32_t SUMMARY_SMALL = 32;
+
 __global__ void k_summarize(Interval *__restrict__ ivs, const uint64_t *__restrict__ iv_off, uint64_t n,
-                            uint32_t cap, uint64_t *__restrict__ total, uint64_t *__restrict__ keep)
+                            uint32_t cap, uint64_t *__restrict__ total, uint64_t *__restrict__ keep,
+                            uint32_t *__restrict__ many, unsigned int *__restrict__ n_many)
 {
     for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n;
          r += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t b = iv_off[r], e = iv_off[r + 1];
+        if (e - b > SUMMARY_SMALL) {
+            many[atomicAdd(n_many, 1u)] = (uint32_t)r;
+            continue;
+        }
         uint64_t t = 0;
-        for (uint64_t i = b; i < e; i++) {
-            Interval x = ivs[i];
-            uint64_t kx = iv_key(x);
-            uint64_t j = i;
-            while (j > b && iv_key(ivs[j - 1]) > kx) { ivs[j] = ivs[j - 1]; j--; }
-            ivs[j] = x;
-            t += x.r - x.l;
+        for (uint64_t i = b; i < e; i++) t += ivs[i].r - ivs[i].l;
+        if (cap && t > cap) {
+            for (uint64_t i = b + 1; i < e; i++) {
+                Interval x = ivs[i];
+                uint64_t kx = iv_key(x);
+                uint64_t j = i;
+                while (j > b && iv_key(ivs[j - 1]) > kx) { ivs[j] = ivs[j - 1]; j--; }
+                ivs[j] = x;
+            }
         }
         total[r] = t;
         keep[r] = (cap && t > cap) ? cap : t;
     }
 }
 
+// Block-wide sum of one value per thread (blockDim.x = MANY_THREADS).
+constexpr int MANY_THREADS = 256;
+
+__device__ __forceinline__ uint64_t block_sum(uint64_t v, uint64_t *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+    __syncthreads();                       // red[] free from the previous use
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    uint64_t s = 0;
+    for (int w = 0; w < MANY_THREADS / 32; w++) s += red[w];
+    return s;
+}
+
+// One block per read with more than SUMMARY_SMALL intervals.  The rows a
+// capped read lists are found without sorting: interval keys (d, strand, l)
+// are distinct, so a bitwise search from the top key bit finds the key K at
+// which the running row count in key order first reaches cap (35 passes,
+// each a block-wide sum of the sizes below the candidate prefix).  Intervals
+// with key < K are kept whole, K's interval keeps its first cap - before
+// rows, and the kept ones are compacted to the front of the read's list in
+// chunks of the block size (each chunk read before any of it is overwritten;
+// writes never pass the chunk being read).
+__global__ void __launch_bounds__(MANY_THREADS) k_summarize_many(Interval *__restrict__ ivs,
+                                                                 const uint64_t *__restrict__ iv_off,
+                                                                 uint32_t cap, uint64_t *__restrict__ total,
+                                                                 uint64_t *__restrict__ keep,
+                                                                 const uint32_t *__restrict__ many,
+                                                                 const unsigned int *__restrict__ n_many_p)
+{
+    __shared__ uint64_t red[MANY_THREADS / 32];
+    __shared__ uint32_t wsum[MANY_THREADS / 32];
+    const unsigned n_many = *n_many_p;
+    for (unsigned mi = blockIdx.x; mi < n_many; mi += gridDim.x) {
+        const uint32_t r = many[mi];
+        const uint64_t b = iv_off[r], e = iv_off[r + 1];
+        uint64_t part = 0;
+        for (uint64_t i = b + threadIdx.x; i < e; i += MANY_THREADS) part += ivs[i].r - ivs[i].l;
+        const uint64_t t = block_sum(part, red);
+        if (threadIdx.x == 0) {
+            total[r] = t;
+            keep[r] = (cap && t > cap) ? cap : t;
+        }
+        if (!(cap && t > cap)) continue;
+        // bitwise search for K over the 35-bit keys
+        uint64_t prefix = 0, before = 0;
+        for (int bit = 34; bit >= 0; bit--) {
+            const uint64_t hi = prefix >> (bit + 1);
+            uint64_t z = 0;
+            for (uint64_t i = b + threadIdx.x; i < e; i += MANY_THREADS) {
+                Interval x = ivs[i];
+                uint64_t k = iv_key(x);
+                if ((k >> (bit + 1)) == hi && !((k >> bit) & 1u)) z += x.r - x.l;
+            }
+            z = block_sum(z, red);
+            if (before + z < cap) { before += z; prefix |= 1ull << bit; }
+        }
+        const uint64_t K = prefix;
+        const uint32_t take = (uint32_t)(cap - before);   // rows of K's interval, 1 .. its size
+        // compact the kept intervals to the front
+        uint64_t out = b;
+        for (uint64_t c0 = b; c0 < e; c0 += MANY_THREADS) {
+            uint64_t i = c0 + threadIdx.x;
+            Interval x{};
+            bool kept = false;
+            if (i < e) {
+                x = ivs[i];
+                uint64_t k = iv_key(x);
+                kept = k <= K;
+                if (k == K) x.r = x.l + take;
+            }
+            unsigned bal = __ballot_sync(FULL, kept);
+            __syncthreads();                 // every read of this chunk is done
+            if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = __popc(bal);
+            __syncthreads();
+            uint32_t pre = 0, all = 0;
+            for (int w = 0; w < MANY_THREADS / 32; w++) {
+                if (w < (int)(threadIdx.x >> 5)) pre += wsum[w];
+                all += wsum[w];
+            }
+            pre += __popc(bal & ((1u << (threadIdx.x & 31)) - 1u));
+            if (kept) ivs[out + pre] = x;
+            out += all;
+            __syncthreads();                 // writes done before the next chunk is read
+        }
+    }
+}
+
 __global__ void k_expand(const Interval *__restrict__ ivs, const uint64_t *__restrict__ iv_off,
-                         const uint64_t *__restrict__ hit_off, uint64_t n, Hit *__restrict__ hits)
+                         const uint64_t *__restrict__ hit_off, uint64_t n, Hit *__restrict__ hits,
+                         uint64_t capacity)
 {
     for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n;
          r += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t q = hit_off[r], qe = hit_off[r + 1];
+        uint64_t q = hit_off[r], qe = min(hit_off[r + 1], capacity);
         for (uint64_t i = iv_off[r]; i < iv_off[r + 1] && q < qe; i++) {
             Interval x = ivs[i];
             for (uint32_t row = x.l; row < x.r && q < qe; row++, q++) {
@@ -217,9 +326,10 @@ __device__ __forceinline__ uint32_t locate_row(const IndexView &ix, uint32_t j, 
 
 namespace {
 
-__global__ void k_locate(const IndexView ix, Hit *__restrict__ hits, uint64_t nh,
-                         unsigned long long *__restrict__ steps_out)
+__global__ void k_locate(const IndexView ix, Hit *__restrict__ hits, const uint64_t *__restrict__ nh_p,
+                         uint64_t capacity, unsigned long long *__restrict__ steps_out)
 {
+    uint64_t nh = min(*nh_p, capacity);
     uint32_t steps = 0;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nh;
          i += (uint64_t)gridDim.x * blockDim.x) {
@@ -238,12 +348,12 @@ __device__ __forceinline__ uint64_t hit_key(uint64_t raw)
 // per read: sort <= SMALL_SORT hits in place; list larger reads for the
 // block sort (from the front of `lists`) or the global sort (from the back)
 __global__ void k_sort_small(uint64_t *__restrict__ hits, const uint64_t *__restrict__ hit_off, uint64_t n,
-                             uint32_t *__restrict__ lists, unsigned int *__restrict__ counts)
+                             uint64_t capacity, uint32_t *__restrict__ lists, unsigned int *__restrict__ counts)
 {
     for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n;
          r += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t b = hit_off[r], e = hit_off[r + 1];
-        if (e - b <= 1) continue;
+        if (e - b <= 1 || e > capacity) continue;
         if (e - b > SMEM_SORT) {
             lists[n - 1 - atomicAdd(&counts[1], 1u)] = (uint32_t)r;
             continue;
@@ -263,9 +373,10 @@ __global__ void k_sort_small(uint64_t *__restrict__ hits, const uint64_t *__rest
 
 // bitonic sort of one read's hits in shared memory (<= SMEM_SORT)
 __global__ void __launch_bounds__(512) k_sort_big(uint64_t *__restrict__ hits, const uint64_t *__restrict__ hit_off,
-                                                  const uint32_t *__restrict__ big, unsigned int nbig)
+                                                  const uint32_t *__restrict__ big, const unsigned int *__restrict__ nbig_p)
 {
     __shared__ uint64_t sh[SMEM_SORT];
+    unsigned nbig = *nbig_p;
     for (unsigned bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
         uint32_t r = big[bi];
         uint64_t b = hit_off[r], cnt = hit_off[r + 1] - b;
@@ -374,6 +485,87 @@ static uint64_t big_list_bytes(uint64_t n)
     return (std::max<uint64_t>(n, 1) * 4 + 15) & ~15ull;
 }
 
+// w.big holds: the sort lists (n u32), 64 bytes of counters (locate steps
+// u64, sort-list counts u32[2], many-interval count u32), then the list of
+// reads with many intervals (n u32).
+struct PostLists {
+    uint32_t *sort_lists;
+    unsigned long long *steps;
+    unsigned int *nbig;       // [0] reads for the shared-memory sort, [1] above it
+    unsigned int *n_many;
+    uint32_t *many;
+};
+
+static uint64_t post_list_bytes(uint64_t n) { return 2 * big_list_bytes(n) + 64; }
+
+static PostLists post_lists(Workspace &w, uint64_t n)
+{
+    PostLists p;
+    char *base = (char *)w.big.p;
+    p.sort_lists = (uint32_t *)base;
+    p.steps = (unsigned long long *)(base + big_list_bytes(n));
+    p.nbig = (unsigned int *)(p.steps + 1);
+    p.n_many = p.nbig + 2;
+    p.many = (uint32_t *)(base + big_list_bytes(n) + 64);
+    return p;
+}
+
+// The whole post-search pipeline for one batch, enqueued with every count
+// read on the device (fixed grids, capacity-guarded writes) so it can be
+// captured in a CUDA graph.  Buffers must already hold `hit_capacity` hits.
+// Ends with a copy of the status (search control block, hit total, locate
+// steps and sort-list counts) into pinned host memory `status`.
+int enqueue_post_device(const mica_index *idx, Workspace &w, const ReadsView &rd, uint32_t hit_cap,
+                        uint64_t hit_capacity, cudaStream_t s, void *status, uint64_t &L)
+{
+    uint64_t n = rd.n;
+    uint64_t *iv_off = (uint64_t *)w.iv_off.p, *hit_off = (uint64_t *)w.hit_off.p;
+    PostLists pl = post_lists(w, n);
+    unsigned long long *steps = pl.steps;
+    unsigned int *nbig = pl.nbig;
+    SearchCtl *ctl = (SearchCtl *)w.ctl.p;
+    const unsigned G = 152 * 16;
+    int rc;
+    MICA_CUDA_TRY(cudaMemsetAsync(steps, 0, 64, s));
+    if ((rc = exclusive_scan<uint32_t>(w.scan_tmp, (const uint32_t *)w.iv_cnt.p, n, iv_off, s, L))) return rc;
+    k_iv_scatter<<<G, 256, 0, s>>>((const Interval *)w.iv.p, &ctl->iv_count, w.iv_cap, iv_off,
+                                   (uint32_t *)w.iv_cnt.p, (Interval *)w.iv_sorted.p);
+    k_summarize<<<grid1(n, 128), 128, 0, s>>>((Interval *)w.iv_sorted.p, iv_off, n, hit_cap, (uint64_t *)w.total.p,
+                                              (uint64_t *)w.keep.p, pl.many, pl.n_many);
+    k_summarize_many<<<152 * 2, MANY_THREADS, 0, s>>>((Interval *)w.iv_sorted.p, iv_off, hit_cap,
+                                                      (uint64_t *)w.total.p, (uint64_t *)w.keep.p, pl.many,
+                                                      pl.n_many);
+    L += 3;
+    if ((rc = exclusive_scan<uint64_t>(w.scan_tmp, (const uint64_t *)w.keep.p, n, hit_off, s, L))) return rc;
+    k_expand<<<grid1(n, 128), 128, 0, s>>>((const Interval *)w.iv_sorted.p, iv_off, hit_off, n, (Hit *)w.hits.p,
+                                           hit_capacity);
+    k_locate<<<G, 256, 0, s>>>(idx->view, (Hit *)w.hits.p, hit_off + n, hit_capacity, steps);
+    k_sort_small<<<grid1(n, 128), 128, 0, s>>>((uint64_t *)w.hits.p, hit_off, n, hit_capacity, (uint32_t *)w.big.p,
+                                               nbig);
+    k_sort_big<<<152 * 4, 512, 0, s>>>((uint64_t *)w.hits.p, hit_off, (const uint32_t *)w.big.p, nbig);
+    L += 4;
+    char *st = (char *)status;
+    MICA_CUDA_TRY(cudaMemcpyAsync(st, ctl, sizeof(SearchCtl), cudaMemcpyDeviceToHost, s));
+    MICA_CUDA_TRY(cudaMemcpyAsync(st + sizeof(SearchCtl), hit_off + n, 8, cudaMemcpyDeviceToHost, s));
+    MICA_CUDA_TRY(cudaMemcpyAsync(st + sizeof(SearchCtl) + 8, steps, 16, cudaMemcpyDeviceToHost, s));
+    MICA_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+// Reserve every post-search buffer for n reads and hit_capacity hits.
+int reserve_post(Workspace &w, uint64_t n, uint32_t iv_cap, uint64_t hit_capacity)
+{
+    int rc;
+    uint64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if ((rc = dev_reserve(w.iv_sorted, std::max<uint64_t>(iv_cap, 1) * sizeof(Interval))) ||
+        (rc = dev_reserve(w.iv_off, (n + 1) * 8)) || (rc = dev_reserve(w.total, std::max<uint64_t>(n, 1) * 8)) ||
+        (rc = dev_reserve(w.keep, std::max<uint64_t>(n, 1) * 8)) || (rc = dev_reserve(w.hit_off, (n + 1) * 8)) ||
+        (rc = dev_reserve(w.big, post_list_bytes(n))) || (rc = dev_reserve(w.scan_tmp, (ntiles + 1) * 8)) ||
+        (rc = dev_reserve(w.hits, std::max<uint64_t>(hit_capacity, 1) * sizeof(Hit) + 64)))
+        return rc;
+    return 0;
+}
+
 int run_post(const mica_index *idx, Workspace &w, mica_stats &stt, const ReadsView &rd, uint32_t hit_cap,
              cudaStream_t s, uint64_t *n_hits_out)
 {
@@ -383,28 +575,35 @@ int run_post(const mica_index *idx, Workspace &w, mica_stats &stt, const ReadsVi
     if ((rc = dev_reserve(w.iv_sorted, std::max<uint64_t>(niv, 1) * sizeof(Interval))) ||
         (rc = dev_reserve(w.iv_off, (n + 1) * 8)) || (rc = dev_reserve(w.total, std::max<uint64_t>(n, 1) * 8)) ||
         (rc = dev_reserve(w.keep, std::max<uint64_t>(n, 1) * 8)) || (rc = dev_reserve(w.hit_off, (n + 1) * 8)) ||
-        (rc = dev_reserve(w.big, big_list_bytes(n) + 64)))
+        (rc = dev_reserve(w.big, post_list_bytes(n))))
         return rc;
     uint64_t *iv_off = (uint64_t *)w.iv_off.p, *hit_off = (uint64_t *)w.hit_off.p;
     uint64_t &L = stt.launches;
+    PostLists pl = post_lists(w, n);
+    unsigned long long *steps = pl.steps;
+    unsigned int *nbig = pl.nbig;
+    MICA_CUDA_TRY(cudaMemsetAsync(steps, 0, 64, s));
     if ((rc = exclusive_scan<uint32_t>(w.scan_tmp, (const uint32_t *)w.iv_cnt.p, n, iv_off, s, L))) return rc;
-    if (niv) { k_iv_scatter<<<grid1(niv), 256, 0, s>>>((const Interval *)w.iv.p, niv, iv_off,
-                                                       (uint32_t *)w.iv_cnt.p, (Interval *)w.iv_sorted.p); L++; }
-    if (n) { k_summarize<<<grid1(n, 128), 128, 0, s>>>((Interval *)w.iv_sorted.p, iv_off, n, hit_cap,
-                                                      (uint64_t *)w.total.p, (uint64_t *)w.keep.p); L++; }
+    if (niv) { k_iv_scatter<<<grid1(niv), 256, 0, s>>>((const Interval *)w.iv.p, &((SearchCtl *)w.ctl.p)->iv_count,
+                                                       w.iv_cap, iv_off, (uint32_t *)w.iv_cnt.p,
+                                                       (Interval *)w.iv_sorted.p); L++; }
+    if (n) {
+        k_summarize<<<grid1(n, 128), 128, 0, s>>>((Interval *)w.iv_sorted.p, iv_off, n, hit_cap,
+                                                  (uint64_t *)w.total.p, (uint64_t *)w.keep.p, pl.many, pl.n_many);
+        k_summarize_many<<<152 * 2, MANY_THREADS, 0, s>>>((Interval *)w.iv_sorted.p, iv_off, hit_cap,
+                                                          (uint64_t *)w.total.p, (uint64_t *)w.keep.p, pl.many,
+                                                          pl.n_many);
+        L += 2;
+    }
     if ((rc = exclusive_scan<uint64_t>(w.scan_tmp, (const uint64_t *)w.keep.p, n, hit_off, s, L))) return rc;
     uint64_t nh = 0;
     MICA_CUDA_TRY(cudaMemcpyAsync(&nh, hit_off + n, 8, cudaMemcpyDeviceToHost, s));
     MICA_CUDA_TRY(cudaStreamSynchronize(s));
     if ((rc = dev_reserve(w.hits, std::max<uint64_t>(nh, 1) * sizeof(Hit) + 64))) return rc;
-    // counters after the big-read list, on a 16-byte boundary
-    unsigned long long *steps = (unsigned long long *)((char *)w.big.p + big_list_bytes(n));
-    unsigned int *nbig = (unsigned int *)(steps + 1);
-    MICA_CUDA_TRY(cudaMemsetAsync(steps, 0, 16, s));
     if (n) { k_expand<<<grid1(n, 128), 128, 0, s>>>((const Interval *)w.iv_sorted.p, iv_off, hit_off, n,
-                                                   (Hit *)w.hits.p); L++; }
-    if (nh) { k_locate<<<grid1(nh), 256, 0, s>>>(idx->view, (Hit *)w.hits.p, nh, steps); L++; }
-    if (n) { k_sort_small<<<grid1(n, 128), 128, 0, s>>>((uint64_t *)w.hits.p, hit_off, n, (uint32_t *)w.big.p,
+                                                   (Hit *)w.hits.p, nh); L++; }
+    if (nh) { k_locate<<<grid1(nh), 256, 0, s>>>(idx->view, (Hit *)w.hits.p, hit_off + n, nh, steps); L++; }
+    if (n) { k_sort_small<<<grid1(n, 128), 128, 0, s>>>((uint64_t *)w.hits.p, hit_off, n, nh, (uint32_t *)w.big.p,
                                                        nbig); L++; }
     unsigned int hb[2] = {0, 0};
     unsigned long long st = 0;
@@ -413,7 +612,7 @@ int run_post(const mica_index *idx, Workspace &w, mica_stats &stt, const ReadsVi
     MICA_CUDA_TRY(cudaStreamSynchronize(s));
     if (hb[0]) {
         k_sort_big<<<std::min(hb[0], 152u * 4), 512, 0, s>>>((uint64_t *)w.hits.p, hit_off,
-                                                           (const uint32_t *)w.big.p, hb[0]);
+                                                           (const uint32_t *)w.big.p, nbig);
         L++;
     }
     if (hb[1]) {

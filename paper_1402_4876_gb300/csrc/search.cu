@@ -875,6 +875,51 @@ int search_shape_info(int shape, int *scap, int *warps, int *minb)
     return 0;
 }
 
+// Reserve the search buffers for n reads and prepare the persistent launch;
+// fills the control-block template (to be copied to the device) and the grid.
+int prepare_persistent(const mica_index *idx, Workspace &w, uint64_t n, int shape_in, SearchCtl &tmpl,
+                       int &grid, int &shape)
+{
+    int rc;
+    if ((rc = dev_reserve(w.ctl, sizeof(SearchCtl) + 64))) return rc;
+    if ((rc = dev_reserve(w.iv_cnt, std::max<uint64_t>(n, 1) * 4))) return rc;
+    if (w.iv_cap == 0) w.iv_cap = (uint32_t)std::min<uint64_t>(4 * n + 65536, 1ull << 30);
+    if (w.spill_cap == 0) w.spill_cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(n, 1u << 20), 1ull << 28);
+    if ((rc = dev_reserve(w.iv, (size_t)w.iv_cap * sizeof(Interval)))) return rc;
+    if ((rc = dev_reserve(w.spill, (size_t)w.spill_cap * sizeof(WorkItem)))) return rc;
+    shape = (shape_in >= 0 && shape_in < N_SHAPES) ? shape_in : DEFAULT_SHAPE;
+    int bps = 0;
+    if ((rc = persistent_grid(idx->device, shape, bps))) return rc;
+    grid = g_num_sms * bps;
+    tmpl = SearchCtl{};
+    tmpl.ntasks = 2 * n;
+    tmpl.spill_cap = w.spill_cap;
+    tmpl.iv_cap = w.iv_cap;
+    return 0;
+}
+
+// Enqueue one persistent search (control-block reset from the pinned
+// template, zeroed per-read counters, the kernel between timing events);
+// no host reads, so it can be captured in a CUDA graph.
+int enqueue_persistent(const mica_index *idx, Workspace &w, const ReadsView &rd, int shape, int grid,
+                       const SearchCtl *pinned_tmpl, cudaStream_t s)
+{
+    SearchCtl *d_ctl = (SearchCtl *)w.ctl.p;
+    const PersistShape &sh = g_shapes[shape];
+    MICA_CUDA_TRY(cudaMemcpyAsync(d_ctl, pinned_tmpl, sizeof(SearchCtl), cudaMemcpyHostToDevice, s));
+    MICA_CUDA_TRY(cudaMemsetAsync(w.iv_cnt.p, 0, std::max<uint64_t>(rd.n, 1) * 4, s));
+    PersistArgs pa;
+    pa.ix = idx->view; pa.rd = rd; pa.read_list = nullptr; pa.ntasks = 2 * rd.n;
+    pa.ctl = d_ctl; pa.iv = (Interval *)w.iv.p; pa.iv_cnt = (uint32_t *)w.iv_cnt.p;
+    pa.spill = (WorkItem *)w.spill.p;
+    pa.total_warps = grid * sh.warps;
+    MICA_CUDA_TRY(record_event(w.kev[0], s));
+    if (rd.n) sh.fn<<<grid, sh.warps * 32, sh.smem, s>>>(pa);
+    MICA_CUDA_TRY(cudaGetLastError());
+    MICA_CUDA_TRY(record_event(w.kev[1], s));
+    return 0;
+}
+
 int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd,
                const SearchConfig &cfg, cudaStream_t s)
 {
@@ -910,10 +955,10 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
                 pa.spill = (WorkItem *)w.spill.p;
                 int grid = g_num_sms * bps;
                 pa.total_warps = grid * sh.warps;
-                MICA_CUDA_TRY(cudaEventRecord(w.kev[0], s));
+                MICA_CUDA_TRY(record_event(w.kev[0], s));
                 sh.fn<<<grid, sh.warps * 32, sh.smem, s>>>(pa);
                 MICA_CUDA_TRY(cudaGetLastError());
-                MICA_CUDA_TRY(cudaEventRecord(w.kev[1], s));
+                MICA_CUDA_TRY(record_event(w.kev[1], s));
                 st.launches++;
             } else {
                 // plain: one task per thread, then drain the re-queue in rounds
@@ -942,7 +987,7 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
                     MICA_CUDA_TRY(cudaMemcpyAsync(cnt + LEN_CLASSES, hb, sizeof(hb), cudaMemcpyHostToDevice, s));
                     k_len_scatter<<<g, 256, 0, s>>>(rd, cnt + LEN_CLASSES, cnt + 2 * LEN_CLASSES, (uint32_t *)w.lenlist.p);
                     st.launches += 2;
-                    MICA_CUDA_TRY(cudaEventRecord(w.kev[0], s));
+                    MICA_CUDA_TRY(record_event(w.kev[0], s));
                     for (uint32_t c = 0; c < LEN_CLASSES; c++) {
                         if (!hc[c]) continue;
                         int bc = cfg.plain_block_len[c] > 0 ? cfg.plain_block_len[c] : blk;
@@ -953,12 +998,12 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
                         MICA_CUDA_TRY(cudaGetLastError());
                         st.launches++;
                     }
-                    MICA_CUDA_TRY(cudaEventRecord(w.kev[1], s));
+                    MICA_CUDA_TRY(record_event(w.kev[1], s));
                 } else {
-                    MICA_CUDA_TRY(cudaEventRecord(w.kev[0], s));
+                    MICA_CUDA_TRY(record_event(w.kev[0], s));
                     k_plain<<<(unsigned)((pa.ntasks + blk - 1) / blk), blk, 0, s>>>(pa);
                     MICA_CUDA_TRY(cudaGetLastError());
-                    MICA_CUDA_TRY(cudaEventRecord(w.kev[1], s));
+                    MICA_CUDA_TRY(record_event(w.kev[1], s));
                     st.launches++;
                 }
                 WorkItem *bufs[2] = {(WorkItem *)w.spill.p, (WorkItem *)w.spill2.p};
@@ -978,7 +1023,7 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
                     MICA_CUDA_TRY(cudaMemsetAsync(&d_ctl->spill_reserve, 0, 4, s));
                     k_plain<<<(cnt + blk - 1) / blk, blk, 0, s>>>(pa);
                     MICA_CUDA_TRY(cudaGetLastError());
-                    MICA_CUDA_TRY(cudaEventRecord(w.kev[1], s));
+                    MICA_CUDA_TRY(record_event(w.kev[1], s));
                     st.launches++;
                 }
             }

@@ -135,7 +135,8 @@ int run_tick(mica_server *srv, std::vector<Request *> &tick, Workspace &ws, mica
     ap.cuda_stream = s;
     uint64_t nh = 0;
     st.launches = 0;
-    if ((rc = align_on_device(srv->idx, ws, st, rd, ap, s, &nh))) return rc;
+    // ticks change shape every time: no graph capture
+    if ((rc = align_on_device(srv->idx, ws, st, rd, ap, s, &nh, false))) return rc;
     // results back, split per request
     std::vector<uint64_t> total(std::max<uint64_t>(n, 1)), offs(n + 1);
     std::vector<mica_hit> hits(std::max<uint64_t>(nh, 1));

@@ -52,7 +52,7 @@ int time_search(mica_index *idx, Workspace &ws, const ReadsView &rd, int kernel,
     for (uint32_t r = 0; r <= repeats; r++) {
         mica_stats st{};
         uint64_t nh = 0;
-        if (int rc = align_on_device(idx, ws, st, rd, p, 0, &nh)) return rc;
+        if (int rc = align_on_device(idx, ws, st, rd, p, 0, &nh, false)) return rc;
         if (r > 0) *best = std::min(*best, st.kernel_ms);
     }
     return 0;

@@ -155,11 +155,16 @@ class ReadBatch:
         return unpack_words(w, m)
 
     def subset(self, idx) -> "ReadBatch":
+        """The reads `idx` (in that order) as a batch of their own."""
         idx = np.asarray(idx, dtype=np.int64)
-        reads = [self.read(int(i)) for i in idx]
-        words, off, lens = pack_reads(reads)
-        return ReadBatch(words, off, lens, self.k[idx].copy(), self.origin[idx].copy(),
-                         self.strand[idx].copy(), self.n_subs[idx].copy())
+        off = self.word_off.astype(np.int64)
+        starts, counts = off[idx], off[idx + 1] - off[idx]
+        new_off = np.zeros(len(idx) + 1, dtype=np.uint64)
+        np.cumsum(counts, out=new_off[1:])
+        total = int(new_off[-1])
+        src = np.repeat(starts - new_off[:-1].astype(np.int64), counts) + np.arange(total, dtype=np.int64)
+        return ReadBatch(self.words[src].copy(), new_off, self.lengths[idx].copy(), self.k[idx].copy(),
+                         self.origin[idx].copy(), self.strand[idx].copy(), self.n_subs[idx].copy())
 
 
 def unpack_words(words: np.ndarray, m: int) -> np.ndarray:
@@ -436,3 +441,24 @@ def paired_reads(donor: np.ndarray, n_pairs: int, seed: int = SEED_READS_HUMAN, 
         n_subs[r0:r0 + 2 * c] = hit.sum(axis=1)
     return ReadBatch(words, off, np.full(n, m, dtype=np.uint16), np.full(n, 2, dtype=np.uint8),
                      origin, strand, n_subs)
+
+
+def serve_requests(donor: np.ndarray, n_requests: int, seed: int = SEED_READS_SERVE,
+                   size_range=(1_000, 1_000_000), max_size: int | None = None) -> list:
+    """Serving requests: sizes log-uniform in `size_range` (clipped to
+    `max_size` when given); every read's length uniform over {100, 150, 250}
+    bp and its k uniform in {0, 1, 2}; reads drawn from the donor as the
+    human-scale mates are (uniform origin, fair strand, 1% i.i.d.
+    substitutions)."""
+    rng = _rng(seed)
+    lo, hi = size_range
+    sizes = np.exp(rng.uniform(np.log(lo), np.log(hi), size=n_requests)).astype(np.int64)
+    if max_size is not None:
+        sizes = np.minimum(sizes, max_size)
+    g = Genome(donor)
+    out = []
+    for s in sizes:
+        lengths = rng.choice(np.array([100, 150, 250]), size=int(s))
+        k = rng.integers(0, 3, size=int(s)).astype(np.uint8)
+        out.append(sample_reads(g, lengths, k, rng, subs="rate", sub_rate=0.01))
+    return out

@@ -61,3 +61,8 @@ def test_host_side_rejections_need_no_gpu():
     ok = mica.IndexParams(8, 16)
     assert lib.mica_index_build_resident(g, 5, ctypes.byref(ok), 0, ctypes.byref(out)) == mica.MICA_EINVAL
     assert lib.mica_index_load(b"/nonexistent/index", 0, ctypes.byref(out)) == mica.MICA_EIO
+    # the gather ceiling checks its sizes before touching a device
+    gbs = ctypes.c_double()
+    assert lib.mica_gather_ceiling(0, 1 << 20, 24, 1 << 20, 1, ctypes.byref(gbs), None) == mica.MICA_EINVAL
+    assert lib.mica_gather_ceiling(0, 1000, 32, 1 << 20, 1, ctypes.byref(gbs), None) == mica.MICA_EINVAL
+    assert lib.mica_gather_ceiling(0, 1 << 20, 32, 1 << 20, 1, None, None) == mica.MICA_EINVAL

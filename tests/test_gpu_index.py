@@ -95,3 +95,14 @@ def test_save_load_roundtrip(tmp_path):
     rows = np.arange(0, g.size + 1, 7, dtype=np.uint64)
     assert np.array_equal(idx.debug_locate(rows), idx2.debug_locate(rows))
     assert np.array_equal(idx.debug_occ(rows), idx2.debug_occ(rows))
+
+
+def test_gather_ceiling_orders_l2_above_hbm():
+    """The random-gather ceiling: a buffer that fits L2 serves 32-byte random
+    loads faster than one twelve times L2's size, and both stay below a
+    plausible bound for one GB300 (L2 random reads well under 100 TB/s)."""
+    m = gc.mica()
+    l2 = m.gather_ceiling(64 << 20, 32, loads=1 << 26)
+    hbm = m.gather_ceiling(3 << 29, 32, loads=1 << 26)
+    assert 0 < hbm["gbs"] < l2["gbs"] < 100_000
+    assert hbm["gbs"] < 10_000

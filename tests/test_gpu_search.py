@@ -111,6 +111,33 @@ def test_many_hits_sort_paths(kernel):
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
+def test_many_intervals_and_the_cap(kernel):
+    """Reads in a diverged (AC)^n array (4% substitutions) match thousands
+    of distinct substrings within k: per read 4 to 6,588 SA intervals and
+    4 to 18,580 hits.  Caps 1..5000 take every selection case: a short
+    interval list over the cap, a long one over the cap (threshold found
+    without sorting), a long one within the cap, and uncapped lists above
+    the shared-memory sort size."""
+    rng = np.random.default_rng(7)
+    core = np.resize(np.array([0, 1], np.uint8), 40_000)
+    mut = rng.random(core.size) < 0.04
+    core[mut] = (core[mut] + rng.integers(1, 4, size=int(mut.sum()))) & 3
+    g = np.concatenate([rng.integers(0, 4, 20_000).astype(np.uint8), core,
+                        rng.integers(0, 4, 20_000).astype(np.uint8)])
+    m = 40
+    reads = [g[20_000 + i * 1_999: 20_000 + i * 1_999 + m].copy() for i in range(20)]
+    reads += [refcheck.rc(r) for r in reads[:5]]
+    b = gc.batch_from_reads(reads, [2] * 20 + [3] * 5)
+    fm = oracle.FMIndex(g)
+    idx = gc.mica().Index.build(synth.to_acgt_bytes(g), kmer_q=10, sa_sample=8)
+    for cap in (0, 1, 7, 100, 1000, 5000):
+        got = idx.align_batch(b, hit_cap=cap, kernel=kernel)
+        gc.assert_same(got, fm.align(b, cap=cap), f"cap={cap}")
+    assert int(got.total.max()) > 18_000
+    idx.free()
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
 def test_empty_batch(kernel):
     idx = gc.gpu_index("1m")
     b = gc.batch_from_reads([], [])
@@ -222,3 +249,42 @@ def test_autotune_cache_and_results_unchanged(tmp_path):
             gc.assert_same(idx.align_batch(b, hit_cap=1000, kernel=kernel), ref, kernel)
     finally:
         idx.set_tuning()
+
+
+def test_graph_replay_and_fallback():
+    """Repeated batch shapes replay one captured CUDA graph with the same
+    results; a batch whose hits overflow the graph's buffers falls back to
+    the regular path and is still exact."""
+    import torch
+    m = gc.mica()
+    g = gc.genome("64m")
+    b = synth.reads_64m(g, n=20_000)
+    idx = gc.gpu_index("64m")
+    dev = torch.device("cuda", 0)
+    d = (torch.from_numpy(b.words.view(np.int32)).to(dev), torch.from_numpy(b.word_off.view(np.int64)).to(dev),
+         torch.from_numpy(b.lengths.view(np.int16)).to(dev), torch.from_numpy(b.k).to(dev))
+    want = gc.oracle_index("64m").align(b, cap=1000)
+    seen = []
+    for call in range(3):
+        r = idx.align_device(*d, b.n, hit_cap=1000)
+        st = idx.stats()
+        seen.append((st["graph_captures"], st["graph_replays"]))
+        t, o, h = r.tensors()
+        got = gc.mica().Result(t.cpu().numpy().view(np.uint64), o.cpu().numpy().view(np.uint64),
+                               h.cpu().numpy().view(m.HIT_DTYPE))
+        gc.assert_same(got, want, f"call {call}")
+    assert seen[0] == (1, 1) and seen[1] == (0, 1) and seen[2] == (0, 1)
+    # many hits per read: (AT)-rich genome, uncapped -> more hits than the graph's buffer holds
+    tg = np.resize(np.array([0, 3], np.uint8), 200_000)
+    tg[::1001] = 1
+    tidx = m.Index.build(synth.to_acgt_bytes(tg), kmer_q=10, sa_sample=8)
+    reads = gc.batch_from_reads([tg[10:40].copy() for _ in range(12)], [1] * 12)
+    tw = (torch.from_numpy(reads.words.view(np.int32)).to(dev), torch.from_numpy(reads.word_off.view(np.int64)).to(dev),
+          torch.from_numpy(reads.lengths.view(np.int16)).to(dev), torch.from_numpy(reads.k).to(dev))
+    r = tidx.align_device(*tw, reads.n, hit_cap=0)
+    assert tidx.stats()["graph_fallbacks"] == 1
+    t, o, h = r.tensors()
+    got = gc.mica().Result(t.cpu().numpy().view(np.uint64), o.cpu().numpy().view(np.uint64),
+                           h.cpu().numpy().view(m.HIT_DTYPE))
+    gc.assert_same(got, oracle.FMIndex(tg).align(reads, cap=0), "fallback")
+    tidx.free()
