@@ -19,9 +19,13 @@
  *
  * The index (Section 2: a BWT index of the genome resident in the
  * accelerator's global memory, laid out to cut memory transactions) is built
- * and kept in GPU memory: the 2-bit BWT interleaved with occurrence counts in
- * 64-byte blocks of 192 rows, a q-mer table of suffix-array interval bounds,
- * and a text-sampled suffix array with a row-marking bit vector.
+ * and kept in GPU memory: the BWT as two bit planes interleaved with
+ * occurrence counts in 32-byte blocks of 96 rows, a q-mer table of
+ * suffix-array interval bounds, a text-sampled suffix array with a
+ * row-marking bit vector and, optionally, the occurrence blocks of the
+ * reversed genome, from which the search takes a lower bound on the
+ * mismatches each pattern prefix needs (Li and Durbin's D array) to prune
+ * branches that cannot reach a hit; pruning never changes the result.
  *
  * Conventions.  Every function returning int returns MICA_OK (0) or a negative
  * MICA_E* code; mica_strerror names it.  Input buffers are owned by the caller
@@ -58,10 +62,13 @@ enum {
 
 typedef struct mica_index mica_index;
 
-/* Index layout parameters (defaults: 12, 16). */
+/* Index layout parameters (defaults: 12, 16, 1). */
 typedef struct {
     uint32_t kmer_q;     /* q-mer seed table length, 1..12: table of 4^q + 1 uint32 bounds */
     uint32_t sa_sample;  /* text sampling rate s, 1..256: SA[j] kept when SA[j] % s == 0 */
+    uint32_t lower_bounds; /* 1: also build the reversed genome's occurrence blocks (one more
+                              suffix array at build time, +1/3 device memory) so searches can
+                              prune by mismatch lower bounds; 0: not */
 } mica_index_params;
 
 enum {
@@ -75,6 +82,8 @@ typedef struct {
     uint32_t hit_cap;    /* listed hits per read; 0 = no cap (every hit listed) */
     int32_t kernel;      /* MICA_KERNEL_* */
     void *cuda_stream;   /* cudaStream_t to run on; NULL = the legacy default stream */
+    uint32_t prune;      /* 1 (default): prune by mismatch lower bounds when the index has
+                            them; 0: plain exhaustive backtracking.  Same result either way. */
 } mica_align_params;
 
 typedef struct {
@@ -107,7 +116,7 @@ typedef struct {
     uint64_t tasks;          /* (read, strand) search tasks = 2 * n_reads */
     uint64_t seeds;          /* q-mer table lookups */
     uint64_t nodes;          /* backtracking nodes expanded (one interval extension each) */
-    uint64_t rank_blocks;    /* 64-byte occurrence blocks read by the search */
+    uint64_t rank_blocks;    /* 32-byte occurrence blocks read by the search (incl. lower bounds) */
     uint64_t intervals;      /* leaf SA intervals found */
     uint64_t located;        /* SA rows resolved to positions */
     uint64_t lf_steps;       /* LF-mapping steps taken by the resolution */
@@ -121,8 +130,11 @@ typedef struct {
     uint64_t graph_captures;  /* the call captured its pipeline as a CUDA graph (new batch shape) */
     uint64_t graph_replays;   /* the call ran as one replay of a captured graph */
     uint64_t graph_fallbacks; /* a replay overflowed a buffer; the regular path recomputed the call */
+    uint64_t lb_steps;       /* lower-bound pass: interval extensions on the reversed genome */
+    uint64_t lb_dead_tasks;  /* tasks whose lower bound already exceeds k before any seed */
     float search_ms;         /* device time of the search phase (kernel + its control copies) */
-    float kernel_ms;         /* device time of the search kernel launch(es) alone */
+    float kernel_ms;         /* device time of the search kernel launch(es) alone, with the
+                                lower-bound pass when pruning */
     float total_ms;          /* device time of the whole call */
 } mica_stats;
 
@@ -134,13 +146,15 @@ typedef struct {
     uint64_t C[5];           /* C[c] = symbols of G$ smaller than c; C[4] = N + 1 */
     uint64_t occ_bytes, mark_bytes, sample_bytes, table_bytes;
     int32_t device;
+    uint32_t lower_bounds;   /* 1 if the reversed genome's occurrence blocks are resident */
+    uint64_t rev_occ_bytes;  /* their size (0 without them) */
 } mica_index_info;
 
 const char *mica_strerror(int code);
 
-/* Fill *p with the defaults (kmer_q 12, sa_sample 16). */
+/* Fill *p with the defaults (kmer_q 12, sa_sample 16, lower_bounds 1). */
 void mica_index_params_default(mica_index_params *p);
-/* Fill *p with the defaults (hit_cap 1000, persistent kernel, default stream). */
+/* Fill *p with the defaults (hit_cap 1000, persistent kernel, default stream, prune 1). */
 void mica_align_params_default(mica_align_params *p);
 
 /*
@@ -156,6 +170,8 @@ int mica_index_build_resident(const uint8_t *genome_acgt, uint64_t len,
 int mica_index_build(const uint8_t *genome_acgt, uint64_t len,
                      const mica_index_params *params, const char *out_path);
 
+/* Index files (format version 3) hold the reversed genome's blocks when the
+   index has them; version 2 files (without them) still load. */
 int mica_index_save(const mica_index *idx, const char *path);
 /* Read an index file and upload it to `device`, where it stays until freed. */
 int mica_index_load(const char *path, int device, mica_index **out);
@@ -334,6 +350,18 @@ int mica_debug_locate(const mica_index *idx, const uint64_t *rows, uint64_t n, u
    (host in/out; l == r when the len-mer does not occur). */
 int mica_debug_seed_interval(const mica_index *idx, const uint32_t *codes, uint32_t len, uint64_t n,
                              uint32_t *lr_out);
+
+/* Mismatch lower bounds of every (read, strand) task as the pruned search
+   computes them (host in/out; the index must have lower_bounds).  Task
+   2i + s is read i on strand s (0 = the read, 1 = its reverse complement):
+   P = that strand's pattern, m = |P|, q' = min(m, kmer_q).  Scanning
+   P[0, m - q') left to right, a piece P[s, j] that does not occur in the
+   genome ends at j and the next piece starts at j + 1; 9-bit field t of
+   lb_out[task] (t = 0..3) is j + 1 for the (t+1)-th such piece, 511 where
+   there is none, and the scan stops after k + 1 pieces.  D(i), the number of
+   fields <= i, bounds from below the substitutions P[0, i) needs. */
+int mica_debug_lower_bounds(mica_index *idx, const uint32_t *packed_reads, const uint64_t *word_offsets,
+                            const uint16_t *lengths, const uint8_t *k, uint64_t n_reads, uint64_t *lb_out);
 
 #ifdef __cplusplus
 }

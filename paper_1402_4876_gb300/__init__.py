@@ -42,11 +42,12 @@ class MicaError(RuntimeError):
 
 
 class IndexParams(ctypes.Structure):
-    _fields_ = [("kmer_q", ctypes.c_uint32), ("sa_sample", ctypes.c_uint32)]
+    _fields_ = [("kmer_q", ctypes.c_uint32), ("sa_sample", ctypes.c_uint32), ("lower_bounds", ctypes.c_uint32)]
 
 
 class AlignParams(ctypes.Structure):
-    _fields_ = [("hit_cap", ctypes.c_uint32), ("kernel", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
+    _fields_ = [("hit_cap", ctypes.c_uint32), ("kernel", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
+                ("prune", ctypes.c_uint32)]
 
 
 class _Result(ctypes.Structure):
@@ -63,7 +64,8 @@ class Stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_uint64) for name in
                 ("tasks", "seeds", "nodes", "rank_blocks", "intervals", "located", "lf_steps",
                  "spills", "retries", "launches", "warp_rounds", "lane_ops", "rounds_multi", "rounds_single",
-                 "rounds_seed", "graph_captures", "graph_replays", "graph_fallbacks")] + [("search_ms", ctypes.c_float), ("kernel_ms", ctypes.c_float),
+                 "rounds_seed", "graph_captures", "graph_replays", "graph_fallbacks", "lb_steps",
+                 "lb_dead_tasks")] + [("search_ms", ctypes.c_float), ("kernel_ms", ctypes.c_float),
                                                       ("total_ms", ctypes.c_float)]
 
     def as_dict(self) -> dict:
@@ -102,7 +104,8 @@ class IndexInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint64), ("rows", ctypes.c_uint64), ("kmer_q", ctypes.c_uint32),
                 ("sa_sample", ctypes.c_uint32), ("dollar_row", ctypes.c_uint64),
                 ("C", ctypes.c_uint64 * 5), ("occ_bytes", ctypes.c_uint64), ("mark_bytes", ctypes.c_uint64),
-                ("sample_bytes", ctypes.c_uint64), ("table_bytes", ctypes.c_uint64), ("device", ctypes.c_int32)]
+                ("sample_bytes", ctypes.c_uint64), ("table_bytes", ctypes.c_uint64), ("device", ctypes.c_int32),
+                ("lower_bounds", ctypes.c_uint32), ("rev_occ_bytes", ctypes.c_uint64)]
 
 
 # exported symbol -> (restype, argtypes); the C ABI's full surface
@@ -135,6 +138,7 @@ SIGNATURES = {
     "mica_tuning_cache_lookup": (_i32, [ctypes.c_char_p, P, _u32, _u32, P]),
     "mica_offsets_noalloc": (_i32, [P, _u64, P, P]),
     "mica_gather_ceiling": (_i32, [ctypes.c_int, _u64, _u32, _u64, _u32, P, P]),
+    "mica_debug_lower_bounds": (_i32, [P, P, P, P, P, _u64, P]),
     "mica_server_params_default": (None, [P]),
     "mica_server_start": (_i32, [P, P, P]),
     "mica_server_submit": (_i32, [P, P, P, P, P, _u64, P]),
@@ -255,9 +259,10 @@ class Index:
         self._h = ctypes.c_void_p(handle)
 
     @classmethod
-    def build(cls, genome_acgt, kmer_q: int = 12, sa_sample: int = 16, device: int = 0) -> "Index":
+    def build(cls, genome_acgt, kmer_q: int = 12, sa_sample: int = 16, device: int = 0,
+              lower_bounds: bool = True) -> "Index":
         g = _acgt(genome_acgt)
-        p = IndexParams(kmer_q, sa_sample)
+        p = IndexParams(kmer_q, sa_sample, int(bool(lower_bounds)))
         h = ctypes.c_void_p()
         _check(_lib.mica_index_build_resident(_ptr(g) if g.size else None, g.size, ctypes.byref(p), device,
                                              ctypes.byref(h)), "mica_index_build_resident")
@@ -328,19 +333,19 @@ class Index:
         return s.as_dict()
 
     @staticmethod
-    def _params(hit_cap, kernel, stream):
+    def _params(hit_cap, kernel, stream, prune=True):
         return AlignParams(hit_cap, KERNELS[kernel] if isinstance(kernel, str) else int(kernel),
-                           _stream_handle(stream))
+                           _stream_handle(stream), int(bool(prune)))
 
     def align(self, words, word_off, lengths, k, hit_cap: int = 1000, kernel="persistent",
-              stream=None) -> Result:
+              stream=None, prune: bool = True) -> Result:
         """mica_align_batch on host arrays (copies in, searches, copies out)."""
         words = np.ascontiguousarray(words, dtype=np.uint32)
         word_off = np.ascontiguousarray(word_off, dtype=np.uint64)
         lengths = np.ascontiguousarray(lengths, dtype=np.uint16)
         k = np.ascontiguousarray(k, dtype=np.uint8)
         n = lengths.size
-        p = self._params(hit_cap, kernel, stream)
+        p = self._params(hit_cap, kernel, stream, prune)
         out = ctypes.POINTER(_Result)()
         _check(_lib.mica_align_batch(self._h, _ptr(words) if words.size else None, _ptr(word_off),
                                      _ptr(lengths) if n else None, _ptr(k) if n else None, n,
@@ -352,10 +357,10 @@ class Index:
         return self.align(batch.words, batch.word_off, batch.lengths, batch.k, **kw)
 
     def align_device(self, d_words, d_word_off, d_lengths, d_k, n_reads: int, hit_cap: int = 1000,
-                     kernel="persistent", stream=None) -> DeviceResult:
+                     kernel="persistent", stream=None, prune: bool = True) -> DeviceResult:
         """mica_align_device on device pointers (ints) or torch CUDA tensors."""
         ptr = lambda x: x if isinstance(x, int) else x.data_ptr()
-        p = self._params(hit_cap, kernel, stream)
+        p = self._params(hit_cap, kernel, stream, prune)
         r = _DeviceResult()
         _check(_lib.mica_align_device(self._h, ctypes.c_void_p(ptr(d_words)), ctypes.c_void_p(ptr(d_word_off)),
                                       ctypes.c_void_p(ptr(d_lengths)), ctypes.c_void_p(ptr(d_k)), n_reads,
@@ -373,6 +378,18 @@ class Index:
         rows = np.ascontiguousarray(rows, dtype=np.uint64)
         out = np.empty(rows.size, dtype=np.uint32)
         _check(_lib.mica_debug_locate(self._h, _ptr(rows), rows.size, _ptr(out)), "mica_debug_locate")
+        return out
+
+    def debug_lower_bounds(self, batch) -> np.ndarray:
+        """Lower-bound words of the 2n (read, strand) tasks (mica_debug_lower_bounds)."""
+        words = np.ascontiguousarray(batch.words, dtype=np.uint32)
+        off = np.ascontiguousarray(batch.word_off, dtype=np.uint64)
+        lens = np.ascontiguousarray(batch.lengths, dtype=np.uint16)
+        k = np.ascontiguousarray(batch.k, dtype=np.uint8)
+        out = np.empty(2 * lens.size, dtype=np.uint64)
+        _check(_lib.mica_debug_lower_bounds(self._h, _ptr(words) if words.size else None, _ptr(off),
+                                            _ptr(lens) if lens.size else None, _ptr(k) if k.size else None,
+                                            lens.size, _ptr(out) if out.size else None), "mica_debug_lower_bounds")
         return out
 
     def debug_seed_interval(self, codes, length: int) -> np.ndarray:

@@ -47,7 +47,7 @@ void free_workspace(Workspace &w)
 {
     DevBuf *all[] = {&w.ctl, &w.iv, &w.iv_sorted, &w.iv_cnt, &w.iv_off, &w.total, &w.keep, &w.hit_off,
                      &w.hits, &w.spill, &w.big, &w.scan_tmp, &w.reads_words, &w.reads_off, &w.reads_len,
-                     &w.reads_k, &w.spill2, &w.lenlist};
+                     &w.reads_k, &w.spill2, &w.lenlist, &w.lb};
     for (DevBuf *b : all) dev_release(*b);
     for (auto &e : w.ev)
         if (e) { cudaEventDestroy(e); e = nullptr; }
@@ -63,6 +63,7 @@ static int validate_params(const mica_index_params &p)
 {
     if (p.kmer_q < 1 || p.kmer_q > MAX_Q) return MICA_EINVAL;
     if (p.sa_sample < 1 || p.sa_sample > 256) return MICA_EINVAL;
+    if (p.lower_bounds > 1) return MICA_EINVAL;
     return 0;
 }
 
@@ -97,6 +98,14 @@ struct FileHeader {
     uint64_t C[5];
     uint64_t n_occ_blocks, n_super, n_mark_blocks, n_samples, table_len;
     uint32_t nshort, short_pad[MAX_Q], short_len[MAX_Q];
+};
+
+// Version 3 follows the header with this block; the reversed genome's
+// occurrence blocks and superblocks (same counts as the genome's) follow the
+// genome's arrays when has_rev is 1.
+struct FileHeaderRev {
+    uint32_t has_rev, rev_dollar_row;
+    uint64_t rev_C[5];
 };
 
 static int write_array(FILE *f, const DevBuf &b, uint64_t bytes)
@@ -149,15 +158,21 @@ static int align_graph(const mica_index *idx, Workspace &w, mica_stats &st, cons
         w.spill_dirty = false;
     }
     memcpy(w.pin_tmpl, &tmpl, sizeof(tmpl));
-    uint64_t key[16] = {(uint64_t)rd.words, (uint64_t)rd.word_off, (uint64_t)rd.len, (uint64_t)rd.k, n,
-                        p.hit_cap, (uint64_t)shape, (uint64_t)grid, (uint64_t)w.ctl.p, (uint64_t)w.iv.p,
-                        (uint64_t)w.spill.p, (uint64_t)w.iv_sorted.p, (uint64_t)w.hits.p, (uint64_t)w.big.p,
-                        (uint64_t)w.scan_tmp.p, w.hit_capacity ^ ((uint64_t)w.iv_cap << 40) ^ ((uint64_t)w.spill_cap << 20)};
+    const bool prune = p.prune && idx->has_rev;
+    // every input, size and workspace buffer the captured kernels use: a
+    // buffer grown by any other call since the capture forces a new capture
+    uint64_t key[GRAPH_KEY] = {(uint64_t)rd.words, (uint64_t)rd.word_off, (uint64_t)rd.len, (uint64_t)rd.k, n,
+                               p.hit_cap, (uint64_t)shape | ((uint64_t)prune << 32), (uint64_t)grid,
+                               (uint64_t)w.ctl.p, (uint64_t)w.iv.p, (uint64_t)w.iv_cnt.p, (uint64_t)w.spill.p,
+                               (uint64_t)w.lb.p, (uint64_t)w.iv_sorted.p, (uint64_t)w.iv_off.p,
+                               (uint64_t)w.total.p, (uint64_t)w.keep.p, (uint64_t)w.hit_off.p, (uint64_t)w.hits.p,
+                               (uint64_t)w.big.p, (uint64_t)w.scan_tmp.p, w.hit_capacity, (uint64_t)w.iv_cap,
+                               (uint64_t)w.spill_cap};
     if (!w.gexec || memcmp(key, w.gkey, sizeof(key)) != 0) {
         if (w.gexec) { cudaGraphExecDestroy(w.gexec); w.gexec = nullptr; }
         uint64_t L = 0;
         MICA_CUDA_TRY(cudaStreamBeginCapture(w.gstream, cudaStreamCaptureModeThreadLocal));
-        int crc = enqueue_persistent(idx, w, rd, shape, grid, (const SearchCtl *)w.pin_tmpl, w.gstream);
+        int crc = enqueue_persistent(idx, w, rd, shape, grid, (const SearchCtl *)w.pin_tmpl, prune, w.gstream, L);
         if (!crc) crc = enqueue_post_device(idx, w, rd, p.hit_cap, w.hit_capacity, w.gstream, w.pin_status, L);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(w.gstream, &g);
@@ -170,9 +185,8 @@ static int align_graph(const mica_index *idx, Workspace &w, mica_stats &st, cons
         cudaGraphDestroy(g);
         if (e != cudaSuccess) { w.gexec = nullptr; cudaGetLastError(); return 0; }
         memcpy(w.gkey, key, sizeof(key));
-        w.gkey[15] = key[15];
         st.graph_captures++;
-        w.glaunches = L + 1;
+        w.glaunches = L;
     }
     MICA_CUDA_TRY(cudaEventRecord(w.ev[0], s));
     MICA_CUDA_TRY(cudaGraphLaunch(w.gexec, s));
@@ -205,6 +219,8 @@ static int align_graph(const mica_index *idx, Workspace &w, mica_stats &st, cons
     st.rounds_multi = out.rounds_kind[0];
     st.rounds_single = out.rounds_kind[1];
     st.rounds_seed = out.rounds_kind[2];
+    st.lb_steps = out.lb_steps;
+    st.lb_dead_tasks = out.lb_dead;
     st.located = nhits;
     st.lf_steps = steps;
     st.launches += w.glaunches;
@@ -239,6 +255,7 @@ int align_on_device(const mica_index *idx, Workspace &w, mica_stats &st, const R
     cfg.shape = idx->tuning.shape;
     cfg.plain_block = idx->tuning.plain_block ? (int)idx->tuning.plain_block : 128;
     cfg.plain_budget = idx->tuning.plain_budget ? idx->tuning.plain_budget : (1u << 16);
+    cfg.prune = p.prune && idx->has_rev;
     for (uint32_t c = 0; c < LEN_CLASSES; c++)
         cfg.plain_block_len[c] = idx->tuning.plain_block_len[c] ? (int)idx->tuning.plain_block_len[c] : cfg.plain_block;
     int rc = run_search(idx, w, st, rd, cfg, s);
@@ -279,6 +296,7 @@ void mica_index_params_default(mica_index_params *p)
 {
     p->kmer_q = 12;
     p->sa_sample = 16;
+    p->lower_bounds = 1;
 }
 
 void mica_align_params_default(mica_align_params *p)
@@ -286,6 +304,7 @@ void mica_align_params_default(mica_align_params *p)
     p->hit_cap = 1000;
     p->kernel = MICA_KERNEL_PERSISTENT;
     p->cuda_stream = nullptr;
+    p->prune = 1;
 }
 
 int mica_index_build_resident(const uint8_t *genome_acgt, uint64_t len, const mica_index_params *params,
@@ -339,7 +358,7 @@ int mica_index_save(const mica_index *idx, const char *path)
     if (!f) return MICA_EIO;
     FileHeader h{};
     memcpy(h.magic, MAGIC, 8);
-    h.version = 2;
+    h.version = 3;
     h.kmer_q = idx->params.kmer_q;
     h.sa_sample = idx->params.sa_sample;
     h.n = idx->n;
@@ -355,12 +374,19 @@ int mica_index_save(const mica_index *idx, const char *path)
         h.short_pad[t] = idx->view.short_pad[t];
         h.short_len[t] = idx->view.short_len[t];
     }
+    FileHeaderRev hr{};
+    hr.has_rev = idx->has_rev ? 1u : 0u;
+    hr.rev_dollar_row = idx->view.rev.dollar_row;
+    for (int c = 0; c < 5; c++) hr.rev_C[c] = idx->view.rev.C[c];
     int rc = fwrite(&h, sizeof(h), 1, f) == 1 ? 0 : MICA_EIO;
+    if (!rc && fwrite(&hr, sizeof(hr), 1, f) != 1) rc = MICA_EIO;
     if (!rc) rc = write_array(f, idx->occ, h.n_occ_blocks * 32);
     if (!rc) rc = write_array(f, idx->super, h.n_super * 16);
     if (!rc) rc = write_array(f, idx->marks, h.n_mark_blocks * 64);
     if (!rc) rc = write_array(f, idx->samples, h.n_samples * 4);
     if (!rc) rc = write_array(f, idx->table, h.table_len * 4);
+    if (!rc && idx->has_rev) rc = write_array(f, idx->rocc, h.n_occ_blocks * 32);
+    if (!rc && idx->has_rev) rc = write_array(f, idx->rsuper, h.n_super * 16);
     if (fclose(f) != 0 && !rc) rc = MICA_EIO;
     return rc;
 }
@@ -372,7 +398,9 @@ int mica_index_load(const char *path, int device, mica_index **out)
     FILE *f = fopen(path, "rb");
     if (!f) return MICA_EIO;
     FileHeader h{};
-    if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, MAGIC, 8) != 0 || h.version != 2 ||
+    FileHeaderRev hr{};
+    if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, MAGIC, 8) != 0 || (h.version != 2 && h.version != 3) ||
+        (h.version == 3 && (fread(&hr, sizeof(hr), 1, f) != 1 || hr.has_rev > 1)) ||
         h.kmer_q < 1 || h.kmer_q > MAX_Q || h.sa_sample < 1 || h.n + 1 >= (1ull << 32) ||
         h.n_occ_blocks != (h.n + 1) / OCC_ROWS + 1 ||
         h.n_super != (h.n_occ_blocks + SB_BLOCKS - 1) / SB_BLOCKS || h.n_mark_blocks != (h.n + 1) / MARK_ROWS + 1 ||
@@ -399,7 +427,11 @@ int mica_index_load(const char *path, int device, mica_index **out)
     if (!rc) rc = read_array(f, idx->marks, h.n_mark_blocks * 64);
     if (!rc) rc = read_array(f, idx->samples, h.n_samples * 4);
     if (!rc) rc = read_array(f, idx->table, h.table_len * 4);
+    if (!rc && hr.has_rev) rc = read_array(f, idx->rocc, h.n_occ_blocks * 32);
+    if (!rc && hr.has_rev) rc = read_array(f, idx->rsuper, h.n_super * 16);
     fclose(f);
+    idx->has_rev = hr.has_rev != 0;
+    idx->params.lower_bounds = hr.has_rev;
     if (!rc) {
         IndexView &v = idx->view;
         v.occ = (const uint4 *)idx->occ.p;
@@ -420,6 +452,10 @@ int mica_index_load(const char *path, int device, mica_index **out)
         }
         v.short_bloom = 0;
         for (uint32_t t = 0; t < v.nshort; t++) v.short_bloom |= 1ull << (v.short_pad[t] & 63);
+        v.rev.occ = idx->has_rev ? (const uint4 *)idx->rocc.p : nullptr;
+        v.rev.super = idx->has_rev ? (const uint4 *)idx->rsuper.p : nullptr;
+        v.rev.dollar_row = hr.rev_dollar_row;
+        for (int c = 0; c < 5; c++) v.rev.C[c] = (uint32_t)hr.rev_C[c];
         rc = upload_variants(idx);
     }
     if (rc) { mica_index_free(idx); return rc; }
@@ -438,6 +474,8 @@ void mica_index_free(mica_index *idx)
     dev_release(idx->samples);
     dev_release(idx->table);
     dev_release(idx->variants);
+    dev_release(idx->rocc);
+    dev_release(idx->rsuper);
     free_workspace(idx->ws);
     delete idx;
 }
@@ -456,6 +494,8 @@ int mica_index_get_info(const mica_index *idx, mica_index_info *info)
     info->sample_bytes = idx->n_samples * 4;
     info->table_bytes = idx->table_len * 4;
     info->device = idx->device;
+    info->lower_bounds = idx->has_rev ? 1u : 0u;
+    info->rev_occ_bytes = idx->has_rev ? idx->n_occ_blocks * 32 + idx->n_super * 16 : 0;
     return 0;
 }
 
@@ -686,6 +726,35 @@ int mica_debug_occ(const mica_index *idx, const uint64_t *rows, uint64_t n, uint
 int mica_debug_locate(const mica_index *idx, const uint64_t *rows, uint64_t n, uint32_t *pos_out)
 {
     return debug_rows_call(idx, rows, n, pos_out, 1, 1);
+}
+
+int mica_debug_lower_bounds(mica_index *idx, const uint32_t *packed_reads, const uint64_t *word_offsets,
+                            const uint16_t *lengths, const uint8_t *k, uint64_t n_reads, uint64_t *lb_out)
+{
+    if (!idx || !word_offsets || (n_reads && (!packed_reads || !lengths || !k || !lb_out))) return MICA_EINVAL;
+    if (!idx->has_rev || n_reads >= (1ull << 31)) return MICA_EINVAL;
+    if (int rc = validate_host_batch(idx, word_offsets, lengths, k, n_reads)) return rc;
+    if (n_reads == 0) return 0;
+    DeviceGuard g(idx->device);
+    MICA_CUDA_TRY(cudaSetDevice(idx->device));
+    Workspace &w = idx->ws;
+    uint64_t nw = word_offsets[n_reads];
+    DevBuf dout;
+    int rc;
+    if ((rc = dev_reserve(w.reads_words, std::max<uint64_t>(nw, 1) * 4)) ||
+        (rc = dev_reserve(w.reads_off, (n_reads + 1) * 8)) || (rc = dev_reserve(w.reads_len, n_reads * 2)) ||
+        (rc = dev_reserve(w.reads_k, n_reads)) || (rc = dev_reserve(dout, 2 * n_reads * 8)))
+        return rc;
+    MICA_CUDA_TRY(cudaMemcpy(w.reads_words.p, packed_reads, std::max<uint64_t>(nw, 1) * 4, cudaMemcpyHostToDevice));
+    MICA_CUDA_TRY(cudaMemcpy(w.reads_off.p, word_offsets, (n_reads + 1) * 8, cudaMemcpyHostToDevice));
+    MICA_CUDA_TRY(cudaMemcpy(w.reads_len.p, lengths, n_reads * 2, cudaMemcpyHostToDevice));
+    MICA_CUDA_TRY(cudaMemcpy(w.reads_k.p, k, n_reads, cudaMemcpyHostToDevice));
+    ReadsView rd{(const uint32_t *)w.reads_words.p, (const uint64_t *)w.reads_off.p,
+                 (const uint16_t *)w.reads_len.p, (const uint8_t *)w.reads_k.p, n_reads};
+    rc = debug_lower_bounds(idx, w, rd, (unsigned long long *)dout.p, 0);
+    if (!rc && cudaMemcpy(lb_out, dout.p, 2 * n_reads * 8, cudaMemcpyDeviceToHost) != cudaSuccess) rc = MICA_ECUDA;
+    dev_release(dout);
+    return rc;
 }
 
 int mica_debug_seed_interval(const mica_index *idx, const uint32_t *codes, uint32_t len, uint64_t n,

@@ -362,12 +362,66 @@ int upload_variants(mica_index *idx)
     return 0;
 }
 
+// Occurrence blocks and superblocks of T = text$ from its suffix array: the
+// block layout of the search (counts relative to the superblock, two bit
+// planes), the $ row and C[].  Used for the genome and for its reversal.
+static int build_occ(const uint8_t *d_codes, uint64_t n, const uint32_t *d_sa, DevBuf &occ, DevBuf &super,
+                     uint32_t &dollar, uint32_t (&C)[5], cudaStream_t s)
+{
+    uint64_t rows = n + 1;
+    uint64_t nb = rows / OCC_ROWS + 1;
+    uint64_t nsb = (nb + SB_BLOCKS - 1) / SB_BLOCKS;
+    DevBuf tmp, cnt, base, dr;
+    auto cleanup = [&]() { dev_release(tmp); dev_release(cnt); dev_release(base); dev_release(dr); };
+    int rc;
+    if ((rc = dev_reserve(cnt, nb * 16)) || (rc = dev_reserve(base, nb * 16)) ||
+        (rc = dev_reserve(dr, 16)) || (rc = dev_reserve(occ, nb * 32)) ||
+        (rc = dev_reserve(super, nsb * 16))) { cleanup(); return rc; }
+    int g = grid_for(nb);
+    k_occ_counts<<<g, 256, 0, s>>>(d_sa, d_codes, rows, nb, (uint4 *)cnt.p, (uint32_t *)dr.p);
+    {
+        size_t need = 0;
+        cudaError_t e = cub::DeviceScan::ExclusiveScan(nullptr, need, (const uint4 *)cnt.p, (uint4 *)base.p,
+                                                       Sum4(), make_uint4(0, 0, 0, 0), (int64_t)nb, s);
+        if (e == cudaSuccess && (rc = dev_reserve(tmp, need))) { cleanup(); return rc; }
+        if (e == cudaSuccess)
+            e = cub::DeviceScan::ExclusiveScan(tmp.p, need, (const uint4 *)cnt.p, (uint4 *)base.p, Sum4(),
+                                               make_uint4(0, 0, 0, 0), (int64_t)nb, s);
+        if (e != cudaSuccess) { cleanup(); set_last_cuda_error(e, "occ scan", __FILE__, __LINE__); return MICA_ECUDA; }
+    }
+    k_occ_super<<<grid_for(nsb), 256, 0, s>>>((const uint4 *)base.p, nb, nsb, (uint4 *)super.p);
+    k_occ_blocks<<<g, 256, 0, s>>>(d_sa, d_codes, rows, nb, (const uint4 *)base.p, (const uint4 *)super.p,
+                                   (uint32_t *)occ.p);
+    // totals for C[]: the last block's base plus the rows inside it
+    uint4 tot{}, last{};
+    cudaError_t e = cudaMemcpyAsync(&dollar, dr.p, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&tot, (const uint4 *)base.p + (nb - 1), 16, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&last, (const uint4 *)cnt.p + (nb - 1), 16, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cleanup();
+    if (e != cudaSuccess) { set_last_cuda_error(e, "occ totals", __FILE__, __LINE__); return MICA_ECUDA; }
+    uint64_t cA = (uint64_t)tot.x + last.x, cC = (uint64_t)tot.y + last.y,
+             cG = (uint64_t)tot.z + last.z, cT = (uint64_t)tot.w + last.w;
+    C[0] = 1;
+    C[1] = (uint32_t)(1 + cA);
+    C[2] = (uint32_t)(1 + cA + cC);
+    C[3] = (uint32_t)(1 + cA + cC + cG);
+    C[4] = (uint32_t)(1 + cA + cC + cG + cT);
+    return 0;
+}
+
+__global__ void k_reverse_codes(const uint8_t *__restrict__ in, uint64_t n, uint8_t *__restrict__ out)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        out[n - 1 - i] = in[i];
+}
+
 int build_index_from_codes(const uint8_t *d_codes, uint64_t n, const mica_index_params &p,
                            mica_index *idx, cudaStream_t s)
 {
     uint64_t rows = n + 1;
-    DevBuf sa, tmp, cnt, base, dr;
-    auto cleanup = [&]() { dev_release(sa); dev_release(tmp); dev_release(cnt); dev_release(base); dev_release(dr); };
+    DevBuf sa, tmp;
+    auto cleanup = [&]() { dev_release(sa); dev_release(tmp); };
     int rc;
     if ((rc = dev_reserve(sa, rows * 4))) return rc;
     if ((rc = build_suffix_array(d_codes, n, (uint32_t *)sa.p, s))) { cleanup(); return rc; }
@@ -376,33 +430,8 @@ int build_index_from_codes(const uint8_t *d_codes, uint64_t n, const mica_index_
     // occurrence blocks and superblocks
     uint64_t nb = rows / OCC_ROWS + 1;
     uint64_t nsb = (nb + SB_BLOCKS - 1) / SB_BLOCKS;
-    if ((rc = dev_reserve(cnt, nb * 16)) || (rc = dev_reserve(base, nb * 16)) ||
-        (rc = dev_reserve(dr, 16)) || (rc = dev_reserve(idx->occ, nb * 32)) ||
-        (rc = dev_reserve(idx->super, nsb * 16))) { cleanup(); return rc; }
-    int g = grid_for(nb);
-    k_occ_counts<<<g, 256, 0, s>>>(d_sa, d_codes, rows, nb, (uint4 *)cnt.p, (uint32_t *)dr.p);
-    {
-        size_t need = 0;
-        MICA_CUDA_TRY(cub::DeviceScan::ExclusiveScan(nullptr, need, (const uint4 *)cnt.p, (uint4 *)base.p,
-                                                     Sum4(), make_uint4(0, 0, 0, 0), (int64_t)nb, s));
-        if ((rc = dev_reserve(tmp, need))) { cleanup(); return rc; }
-        MICA_CUDA_TRY(cub::DeviceScan::ExclusiveScan(tmp.p, need, (const uint4 *)cnt.p, (uint4 *)base.p,
-                                                     Sum4(), make_uint4(0, 0, 0, 0), (int64_t)nb, s));
-    }
-    k_occ_super<<<grid_for(nsb), 256, 0, s>>>((const uint4 *)base.p, nb, nsb, (uint4 *)idx->super.p);
-    k_occ_blocks<<<g, 256, 0, s>>>(d_sa, d_codes, rows, nb, (const uint4 *)base.p, (const uint4 *)idx->super.p,
-                                   (uint32_t *)idx->occ.p);
-    uint32_t dollar = 0;
-    MICA_CUDA_TRY(cudaMemcpyAsync(&dollar, dr.p, 4, cudaMemcpyDeviceToHost, s));
-    // totals for C[]: base of the last block holds Occ(c, rows) since rows < nb*192
-    uint4 tot;
-    MICA_CUDA_TRY(cudaMemcpyAsync(&tot, (const uint4 *)base.p + (nb - 1), 16, cudaMemcpyDeviceToHost, s));
-    MICA_CUDA_TRY(cudaStreamSynchronize(s));
-    // the last block's base excludes rows inside it; add them from its counts
-    uint4 last;
-    MICA_CUDA_TRY(cudaMemcpy(&last, (const uint4 *)cnt.p + (nb - 1), 16, cudaMemcpyDeviceToHost));
-    uint64_t cA = (uint64_t)tot.x + last.x, cC = (uint64_t)tot.y + last.y,
-             cG = (uint64_t)tot.z + last.z, cT = (uint64_t)tot.w + last.w;
+    uint32_t dollar = 0, Cf[5];
+    if ((rc = build_occ(d_codes, n, d_sa, idx->occ, idx->super, dollar, Cf, s))) { cleanup(); return rc; }
 
     // marks and samples
     uint32_t sr = p.sa_sample;
@@ -461,6 +490,20 @@ int build_index_from_codes(const uint8_t *d_codes, uint64_t n, const mica_index_
     MICA_CUDA_TRY(cudaStreamSynchronize(s));
     MICA_CUDA_TRY(cudaGetLastError());
     dev_release(tcnt);
+
+    // the reversed genome's occurrence blocks, for mismatch lower bounds
+    uint32_t rdollar = 0, rC[5] = {0, 0, 0, 0, 0};
+    if (p.lower_bounds) {
+        DevBuf rcodes;
+        if ((rc = dev_reserve(rcodes, std::max<uint64_t>(n, 1)))) { cleanup(); return rc; }
+        if (n) k_reverse_codes<<<grid_for(n), 256, 0, s>>>(d_codes, n, (uint8_t *)rcodes.p);
+        rc = build_suffix_array((const uint8_t *)rcodes.p, n, (uint32_t *)sa.p, s);
+        if (!rc) rc = build_occ((const uint8_t *)rcodes.p, n, (const uint32_t *)sa.p, idx->rocc, idx->rsuper,
+                                rdollar, rC, s);
+        dev_release(rcodes);
+        if (rc) { cleanup(); return rc; }
+    }
+    idx->has_rev = p.lower_bounds != 0;
     cleanup();
 
     idx->n = n;
@@ -479,11 +522,11 @@ int build_index_from_codes(const uint8_t *d_codes, uint64_t n, const mica_index_
     v.n = n;
     v.rows = (uint32_t)rows;
     v.dollar_row = dollar;
-    v.C[0] = 1;
-    v.C[1] = (uint32_t)(1 + cA);
-    v.C[2] = (uint32_t)(1 + cA + cC);
-    v.C[3] = (uint32_t)(1 + cA + cC + cG);
-    v.C[4] = (uint32_t)(1 + cA + cC + cG + cT);
+    for (int c = 0; c < 5; c++) v.C[c] = Cf[c];
+    v.rev.occ = idx->has_rev ? (const uint4 *)idx->rocc.p : nullptr;
+    v.rev.super = idx->has_rev ? (const uint4 *)idx->rsuper.p : nullptr;
+    v.rev.dollar_row = rdollar;
+    for (int c = 0; c < 5; c++) v.rev.C[c] = rC[c];
     v.q = p.kmer_q;
     v.sa_sample = p.sa_sample;
     return upload_variants(idx);

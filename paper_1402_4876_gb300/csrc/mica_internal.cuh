@@ -62,6 +62,15 @@ struct IndexView {
     uint32_t short_pad[MAX_Q];
     uint32_t short_len[MAX_Q];
     unsigned long long short_bloom;   // bit (pad & 63) of every short pad: a cheap pre-check
+    // Occurrence blocks of the reversed genome G~$ (same block layout; occ is
+    // null when the index was built without them).  Backward search of a
+    // pattern read left to right on G~ finds whether a substring of G occurs.
+    struct {
+        const uint4 *occ;
+        const uint4 *super;
+        uint32_t dollar_row;
+        uint32_t C[5];
+    } rev;
 };
 
 // Read batch in device memory.
@@ -114,6 +123,7 @@ struct SearchCtl {
     unsigned long long seeds, nodes, rank_blocks, spills;
     unsigned long long rounds, lane_ops;
     unsigned long long rounds_kind[3];   // multi-row, single-row, seed rounds
+    unsigned long long lb_steps, lb_dead; // lower-bound pass: extensions, tasks with no budget left
 };
 
 constexpr unsigned ERR_IV_OVERFLOW = 1u;
@@ -139,9 +149,12 @@ struct DeviceGuard {
     ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
 };
 
+constexpr int GRAPH_KEY = 24;   // words identifying a captured batch shape
+
 // Per-index workspace reused across align calls.
 struct Workspace {
     DevBuf ctl, iv, iv_sorted, iv_cnt, iv_off, total, keep, hit_off, hits, spill, big, scan_tmp;
+    DevBuf lb;   // per (read, strand) task: mismatch lower-bound breakpoints (uint64)
     DevBuf reads_words, reads_off, reads_len, reads_k;   // staging for host batches
     DevBuf spill2;                                        // plain kernel re-queue ping-pong
     DevBuf lenlist;                                       // plain kernel: reads by length class
@@ -154,7 +167,7 @@ struct Workspace {
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t gstream = nullptr;
     void *pin_tmpl = nullptr, *pin_status = nullptr;              // pinned host blocks
-    uint64_t gkey[16] = {};
+    uint64_t gkey[GRAPH_KEY] = {};
     uint64_t hit_capacity = 0;
     uint64_t glaunches = 0;   // kernels in the captured graph
 };
@@ -168,6 +181,8 @@ struct mica_index {
     uint64_t n = 0;
     uint64_t n_occ_blocks = 0, n_super = 0, n_mark_blocks = 0, n_samples = 0, table_len = 0;
     mica::DevBuf occ, super, marks, samples, table, variants;
+    mica::DevBuf rocc, rsuper;   // reversed genome's occurrence blocks (lower bounds)
+    bool has_rev = false;
     mica::Workspace ws;
     mica_stats stats{};
     mica_tuning tuning{-1, 0, 0, {0, 0, 0, 0}};
@@ -227,6 +242,7 @@ struct SearchConfig {
     int plain_block;
     uint32_t plain_budget;      // plain: node expansions per task before re-queueing
     int plain_block_len[4] = {0, 0, 0, 0};   // plain by length: block size per class
+    bool prune = false;         // compute and use mismatch lower bounds (index has them)
 };
 constexpr uint32_t LEN_CLASSES = 4;   // 1-64, 65-128, 129-192, 193-256 bases
 int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd,
@@ -234,8 +250,10 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
 int search_shape_count();
 int prepare_persistent(const mica_index *idx, Workspace &w, uint64_t n, int shape_in, SearchCtl &tmpl,
                        int &grid, int &shape);
+int debug_lower_bounds(const mica_index *idx, Workspace &w, const ReadsView &rd, unsigned long long *d_out,
+                       cudaStream_t s);
 int enqueue_persistent(const mica_index *idx, Workspace &w, const ReadsView &rd, int shape, int grid,
-                       const SearchCtl *pinned_tmpl, cudaStream_t s);
+                       const SearchCtl *pinned_tmpl, bool prune, cudaStream_t s, uint64_t &launches);
 int search_shape_info(int shape, int *scap, int *warps, int *minb);
 
 // post.cu

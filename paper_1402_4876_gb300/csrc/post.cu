@@ -120,12 +120,17 @@ int exclusive_scan(DevBuf &tmp, const T *in, uint64_t n, uint64_t *out, cudaStre
 
 // ---- intervals grouped by read ----
 
+// Every post kernel that indexes by the search's per-read counts first reads
+// the search's error word: after an overflow the counts exceed what was
+// stored, so these kernels do nothing and the caller recomputes the batch.
+//
 // count: the search's interval counter on the device, read here (capped at
 // the buffer's capacity) so the launch needs no host round trip
 __global__ void k_iv_scatter(const Interval *__restrict__ iv, const unsigned int *__restrict__ count_p,
                              uint32_t cap, const uint64_t *__restrict__ iv_off, uint32_t *__restrict__ cursor,
-                             Interval *__restrict__ out)
+                             Interval *__restrict__ out, const unsigned int *__restrict__ err)
 {
+    if (*err) return;
     uint32_t count = min(*count_p, cap);
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
         Interval x = iv[e];
@@ -150,8 +155,10 @@ constexpr uint32_t SUMMARY_SMALL = 32;
 
 __global__ void k_summarize(Interval *__restrict__ ivs, const uint64_t *__restrict__ iv_off, uint64_t n,
                             uint32_t cap, uint64_t *__restrict__ total, uint64_t *__restrict__ keep,
-                            uint32_t *__restrict__ many, unsigned int *__restrict__ n_many)
+                            uint32_t *__restrict__ many, unsigned int *__restrict__ n_many,
+                            const unsigned int *__restrict__ err)
 {
+    if (*err) return;
     for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n;
          r += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t b = iv_off[r], e = iv_off[r + 1];
@@ -203,8 +210,10 @@ __global__ void __launch_bounds__(MANY_THREADS) k_summarize_many(Interval *__res
                                                                  uint32_t cap, uint64_t *__restrict__ total,
                                                                  uint64_t *__restrict__ keep,
                                                                  const uint32_t *__restrict__ many,
-                                                                 const unsigned int *__restrict__ n_many_p)
+                                                                 const unsigned int *__restrict__ n_many_p,
+                                                                 const unsigned int *__restrict__ err)
 {
+    if (*err) return;
     __shared__ uint64_t red[MANY_THREADS / 32];
     __shared__ uint32_t wsum[MANY_THREADS / 32];
     const unsigned n_many = *n_many_p;
@@ -265,8 +274,9 @@ __global__ void __launch_bounds__(MANY_THREADS) k_summarize_many(Interval *__res
 
 __global__ void k_expand(const Interval *__restrict__ ivs, const uint64_t *__restrict__ iv_off,
                          const uint64_t *__restrict__ hit_off, uint64_t n, Hit *__restrict__ hits,
-                         uint64_t capacity)
+                         uint64_t capacity, const unsigned int *__restrict__ err)
 {
+    if (*err) return;
     for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n;
          r += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t q = hit_off[r], qe = min(hit_off[r + 1], capacity);
@@ -327,8 +337,10 @@ __device__ __forceinline__ uint32_t locate_row(const IndexView &ix, uint32_t j, 
 namespace {
 
 __global__ void k_locate(const IndexView ix, Hit *__restrict__ hits, const uint64_t *__restrict__ nh_p,
-                         uint64_t capacity, unsigned long long *__restrict__ steps_out)
+                         uint64_t capacity, unsigned long long *__restrict__ steps_out,
+                         const unsigned int *__restrict__ err)
 {
+    if (*err) return;   // hits not expanded: rows would be stale
     uint64_t nh = min(*nh_p, capacity);
     uint32_t steps = 0;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nh;
@@ -529,17 +541,17 @@ int enqueue_post_device(const mica_index *idx, Workspace &w, const ReadsView &rd
     MICA_CUDA_TRY(cudaMemsetAsync(steps, 0, 64, s));
     if ((rc = exclusive_scan<uint32_t>(w.scan_tmp, (const uint32_t *)w.iv_cnt.p, n, iv_off, s, L))) return rc;
     k_iv_scatter<<<G, 256, 0, s>>>((const Interval *)w.iv.p, &ctl->iv_count, w.iv_cap, iv_off,
-                                   (uint32_t *)w.iv_cnt.p, (Interval *)w.iv_sorted.p);
+                                   (uint32_t *)w.iv_cnt.p, (Interval *)w.iv_sorted.p, &ctl->error);
     k_summarize<<<grid1(n, 128), 128, 0, s>>>((Interval *)w.iv_sorted.p, iv_off, n, hit_cap, (uint64_t *)w.total.p,
-                                              (uint64_t *)w.keep.p, pl.many, pl.n_many);
+                                              (uint64_t *)w.keep.p, pl.many, pl.n_many, &ctl->error);
     k_summarize_many<<<152 * 2, MANY_THREADS, 0, s>>>((Interval *)w.iv_sorted.p, iv_off, hit_cap,
                                                       (uint64_t *)w.total.p, (uint64_t *)w.keep.p, pl.many,
-                                                      pl.n_many);
+                                                      pl.n_many, &ctl->error);
     L += 3;
     if ((rc = exclusive_scan<uint64_t>(w.scan_tmp, (const uint64_t *)w.keep.p, n, hit_off, s, L))) return rc;
     k_expand<<<grid1(n, 128), 128, 0, s>>>((const Interval *)w.iv_sorted.p, iv_off, hit_off, n, (Hit *)w.hits.p,
-                                           hit_capacity);
-    k_locate<<<G, 256, 0, s>>>(idx->view, (Hit *)w.hits.p, hit_off + n, hit_capacity, steps);
+                                           hit_capacity, &ctl->error);
+    k_locate<<<G, 256, 0, s>>>(idx->view, (Hit *)w.hits.p, hit_off + n, hit_capacity, steps, &ctl->error);
     k_sort_small<<<grid1(n, 128), 128, 0, s>>>((uint64_t *)w.hits.p, hit_off, n, hit_capacity, (uint32_t *)w.big.p,
                                                nbig);
     k_sort_big<<<152 * 4, 512, 0, s>>>((uint64_t *)w.hits.p, hit_off, (const uint32_t *)w.big.p, nbig);
@@ -584,15 +596,17 @@ int run_post(const mica_index *idx, Workspace &w, mica_stats &stt, const ReadsVi
     unsigned int *nbig = pl.nbig;
     MICA_CUDA_TRY(cudaMemsetAsync(steps, 0, 64, s));
     if ((rc = exclusive_scan<uint32_t>(w.scan_tmp, (const uint32_t *)w.iv_cnt.p, n, iv_off, s, L))) return rc;
+    const unsigned int *err = &((SearchCtl *)w.ctl.p)->error;
     if (niv) { k_iv_scatter<<<grid1(niv), 256, 0, s>>>((const Interval *)w.iv.p, &((SearchCtl *)w.ctl.p)->iv_count,
                                                        w.iv_cap, iv_off, (uint32_t *)w.iv_cnt.p,
-                                                       (Interval *)w.iv_sorted.p); L++; }
+                                                       (Interval *)w.iv_sorted.p, err); L++; }
     if (n) {
         k_summarize<<<grid1(n, 128), 128, 0, s>>>((Interval *)w.iv_sorted.p, iv_off, n, hit_cap,
-                                                  (uint64_t *)w.total.p, (uint64_t *)w.keep.p, pl.many, pl.n_many);
+                                                  (uint64_t *)w.total.p, (uint64_t *)w.keep.p, pl.many, pl.n_many,
+                                                  err);
         k_summarize_many<<<152 * 2, MANY_THREADS, 0, s>>>((Interval *)w.iv_sorted.p, iv_off, hit_cap,
                                                           (uint64_t *)w.total.p, (uint64_t *)w.keep.p, pl.many,
-                                                          pl.n_many);
+                                                          pl.n_many, err);
         L += 2;
     }
     if ((rc = exclusive_scan<uint64_t>(w.scan_tmp, (const uint64_t *)w.keep.p, n, hit_off, s, L))) return rc;
@@ -601,8 +615,8 @@ int run_post(const mica_index *idx, Workspace &w, mica_stats &stt, const ReadsVi
     MICA_CUDA_TRY(cudaStreamSynchronize(s));
     if ((rc = dev_reserve(w.hits, std::max<uint64_t>(nh, 1) * sizeof(Hit) + 64))) return rc;
     if (n) { k_expand<<<grid1(n, 128), 128, 0, s>>>((const Interval *)w.iv_sorted.p, iv_off, hit_off, n,
-                                                   (Hit *)w.hits.p, nh); L++; }
-    if (nh) { k_locate<<<grid1(nh), 256, 0, s>>>(idx->view, (Hit *)w.hits.p, hit_off + n, nh, steps); L++; }
+                                                   (Hit *)w.hits.p, nh, err); L++; }
+    if (nh) { k_locate<<<grid1(nh), 256, 0, s>>>(idx->view, (Hit *)w.hits.p, hit_off + n, nh, steps, err); L++; }
     if (n) { k_sort_small<<<grid1(n, 128), 128, 0, s>>>((uint64_t *)w.hits.p, hit_off, n, nh, (uint32_t *)w.big.p,
                                                        nbig); L++; }
     unsigned int hb[2] = {0, 0};

@@ -73,6 +73,91 @@ __device__ __forceinline__ void thread_pattern(const ReadsView &rd, uint32_t rea
 }
 
 // --------------------------------------------------------------------------
+// Mismatch lower bounds (Li and Durbin's D array, from the reversed genome)
+// --------------------------------------------------------------------------
+//
+// The search consumes a task's pattern P from its last base; a node at depth
+// i has P[0, i) still to match with at most k - d mismatches.  Cutting P[0, i)
+// left to right into maximal pieces that occur in G, every piece that does
+// not occur forces one mismatch in any placement, so the number D(i) of such
+// failed pieces bounds the mismatches P[0, i) needs from below, and a node
+// with d + D(i) > k cannot reach a hit.  Whether P[s, j] occurs in G is one
+// backward-search step per base on the reversed genome, P read left to right.
+// The bound is kept as its breakpoints: field t (9 bits) of a task's word is
+// the prefix length at which D reaches t + 1 (511 = never), so
+// D(i) = #{t : field t <= i}; at most k + 1 fields are set.
+
+constexpr unsigned long long LB_NONE = ~0ull;   // every field 511: D = 0
+
+__device__ __forceinline__ uint32_t lb_at(unsigned long long v, uint32_t i)
+{
+    return ((uint32_t)(v & 511u) <= i) + ((uint32_t)((v >> 9) & 511u) <= i) +
+           ((uint32_t)((v >> 18) & 511u) <= i) + ((uint32_t)((v >> 27) & 511u) <= i);
+}
+
+// Budget left for P[0, i) at d mismatches used: k - D(i), negative = dead.
+__device__ __forceinline__ int lb_budget(unsigned long long v, uint32_t k, uint32_t i)
+{
+    return (int)k - (int)lb_at(v, i);
+}
+
+__global__ void __launch_bounds__(256) k_lower_bounds(const IndexView ix, const ReadsView rd,
+                                                      unsigned long long *__restrict__ lb, SearchCtl *ctl)
+{
+    IndexView rv = ix;            // the reversed genome's blocks through the same helpers
+    rv.occ = ix.rev.occ;
+    rv.super = ix.rev.super;
+    rv.dollar_row = ix.rev.dollar_row;
+#pragma unroll
+    for (int c = 0; c < 5; c++) rv.C[c] = ix.rev.C[c];
+    const uint64_t ntasks = 2 * rd.n;
+    uint32_t steps = 0, blocks = 0, dead = 0;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < ntasks;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t rid = (uint32_t)(t >> 1), minus = (uint32_t)(t & 1);
+        const uint32_t m = rd.len[rid], k = rd.k[rid];
+        const uint32_t qe = m < ix.q ? m : ix.q, lim = m - qe;
+        const uint32_t *w = rd.words + rd.word_off[rid];
+        unsigned long long v = LB_NONE;
+        uint32_t z = 0, l = 0, r = 0;
+        bool fresh = true;
+        for (uint32_t j = 0; j < lim; j++) {
+            uint32_t jj = minus ? m - 1 - j : j;
+            uint32_t c = (__ldg(w + (jj >> 4)) >> (2 * (jj & 15))) & 3u;
+            if (minus) c = 3u - c;
+            const uint32_t cbase = C_of(rv, c);
+            if (fresh) {
+                l = cbase;
+                r = c == 0 ? rv.C[1] : c == 1 ? rv.C[2] : c == 2 ? rv.C[3] : rv.C[4];
+                fresh = false;
+            } else {
+                uint32_t ol[4], orr[4];
+                blocks += occ_pair(rv, l, r, ol, orr);
+                steps++;
+                l = cbase + sel4(ol, c);
+                r = cbase + sel4(orr, c);
+            }
+            if (l >= r) {
+                // P[s, j] does not occur: one more forced mismatch from prefix j + 1 on
+                v = (v & ~(511ull << (9 * z))) | ((unsigned long long)(j + 1) << (9 * z));
+                fresh = true;
+                if (++z > k) break;
+            }
+        }
+        lb[t] = v;
+        dead += z > k;
+    }
+    unsigned mask = __activemask();
+    unsigned s1 = __reduce_add_sync(mask, steps), s2 = __reduce_add_sync(mask, blocks),
+             s3 = __reduce_add_sync(mask, dead);
+    if ((threadIdx.x & 31) == (unsigned)(__ffs(mask) - 1)) {
+        if (s1) atomicAdd(&ctl->lb_steps, (unsigned long long)s1);
+        if (s2) atomicAdd(&ctl->rank_blocks, (unsigned long long)s2);
+        if (s3) atomicAdd(&ctl->lb_dead, (unsigned long long)s3);
+    }
+}
+
+// --------------------------------------------------------------------------
 // Plain kernel: one work item per thread
 // --------------------------------------------------------------------------
 
@@ -91,6 +176,7 @@ struct PlainArgs {
     unsigned int *requeue_count;
     uint32_t requeue_cap;
     uint32_t budget;             // node expansions before re-queueing the rest
+    const unsigned long long *lb;   // optional: lower-bound breakpoints per (read, strand)
 };
 
 __device__ __forceinline__ void requeue_push(const PlainArgs &a, uint32_t read, uint32_t meta,
@@ -134,12 +220,15 @@ __global__ void __launch_bounds__(512) k_plain(PlainArgs a)
     }
     uint32_t m = a.rd.len[read], k = a.rd.k[read];
     uint32_t qe = m < ix.q ? m : ix.q;
-    uint32_t V = n_variants(qe, k);
+    const unsigned long long lbv = a.lb ? a.lb[2ull * read + minus] : LB_NONE;
+    // seeds: the window's substitutions may use only what the rest cannot need
+    const int keff = lb_budget(lbv, k, m - qe);
+    uint32_t V = keff < 0 ? 0u : n_variants(qe, (uint32_t)keff);
     if (vend > V) vend = V;
     uint32_t pat[MAX_WORDS];
     thread_pattern(a.rd, read, minus, m, pat);
     uint32_t code = window_code(pat, m, qe);
-    const uint32_t *var = ix.variants + var_off(k);
+    const uint32_t *var = ix.variants + var_off(keff < 0 ? 0u : (uint32_t)keff);
 
     uint32_t st_l[PLAIN_STACK], st_r[PLAIN_STACK], st_m[PLAIN_STACK];
     int sp = 0;
@@ -188,11 +277,12 @@ __global__ void __launch_bounds__(512) k_plain(PlainArgs a)
         nodes++;
         spent++;
         uint32_t base = pat_base(pat, i - 1);
+        const int kb = lb_budget(lbv, k, i - 1);   // mismatches children may hold
         // mismatching children first, the matching child last (popped next)
 #pragma unroll
         for (int c = 0; c < 4; c++) {
             uint32_t cc = (uint32_t)c;
-            if (cc == base || d + 1 > k) continue;
+            if (cc == base || (int)d + 1 > kb) continue;
             uint32_t l2 = ix.C[c] + ol[c], r2 = ix.C[c] + orr[c];
             if (l2 >= r2) continue;
             if (i == 1) { emit_interval(a.ctl, a.iv, a.iv_cnt, read, minus, d + 1, l2, r2); continue; }
@@ -203,7 +293,7 @@ __global__ void __launch_bounds__(512) k_plain(PlainArgs a)
                 spills++;
             }
         }
-        {
+        if ((int)d <= kb) {
             uint32_t l2 = ix.C[base] + sel4(ol, base), r2 = ix.C[base] + sel4(orr, base);
             if (l2 < r2) {
                 if (i == 1) {
@@ -274,6 +364,7 @@ struct PersistArgs {
     uint32_t *iv_cnt;
     WorkItem *spill;
     int total_warps;
+    const unsigned long long *lb;   // optional: lower-bound breakpoints per (read, strand)
 };
 
 template <int SCAP>
@@ -284,6 +375,7 @@ struct WarpSmem {
     uint32_t sl[SCAP];                    // single-row nodes [l, l + 1)
     uint16_t sm[SCAP];
     uint32_t pat[32][MAX_WORDS + 1];      // pattern of each task slot
+    unsigned long long lb[32];            // lower-bound breakpoints of each slot
     int live[32];                         // nodes of each slot in the two stacks
 };
 
@@ -535,12 +627,16 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
                     }
                     uint32_t m = a.rd.len[rid], k = a.rd.k[rid];
                     uint32_t qe = min(m, ix.q);
+                    unsigned long long lbv = a.lb ? a.lb[2ull * rid + minus] : LB_NONE;
+                    // the seed window may hold only the mismatches the rest cannot need
+                    int keff = lb_budget(lbv, k, m - qe);
                     s_read = rid;
-                    s_info = m | (k << 9) | (minus << 11) | (qe << 12);
+                    s_info = m | (k << 9) | (minus << 11) | (qe << 12) | ((uint32_t)max(keff, 0) << 16);
                     s_vnext = vb;
-                    s_vend = min(ve, n_variants(qe, k));
+                    s_vend = keff < 0 ? 0u : min(ve, n_variants(qe, (uint32_t)keff));
                     s_used = true;
                     W.live[lane] = is_node ? 1 : 0;
+                    W.lb[lane] = lbv;
                 }
                 // stage the new tasks' patterns: one coalesced word per lane
                 unsigned todo = __ballot_sync(FULL, mine);
@@ -637,7 +733,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
                     uint32_t c = block_symbol(blk, o);
                     uint32_t base = pat_base(W.pat[slot], i - 1);
                     dd = d + (c != base);
-                    if (dd <= k) {
+                    if ((int)dd <= lb_budget(W.lb[slot], k, i - 1)) {
                         l2 = C_of(ix, c) + occ_single(ix, b, o, sup, blk, c);
                         child = true;
                     }
@@ -680,12 +776,13 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
                 c_blocks += occ_pair(ix, l, r, ol, orr);
                 c_nodes++;
                 uint32_t base = pat_base(W.pat[slot], i - 1);
+                const int kb = lb_budget(W.lb[slot], k, i - 1);   // mismatches children may hold
 #pragma unroll
                 for (int c = 0; c < 4; c++) {
                     cl[c] = ix.C[c] + ol[c];
                     cr[c] = ix.C[c] + orr[c];
                     cd[c] = d + ((uint32_t)c != base);
-                    if (cd[c] <= k && cl[c] < cr[c]) valid |= 1u << c;
+                    if ((int)cd[c] <= kb && cl[c] < cr[c]) valid |= 1u << c;
                 }
             }
             bool leafs = (i == 1);
@@ -763,11 +860,11 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
             uint32_t code = __shfl_sync(FULL, s_code, s);
             if (lane == s) s_vnext += min(av, 32u);
             bool has = (uint32_t)lane < av;
-            uint32_t k = (info >> 9) & 3u, minus = (info >> 11) & 1u, m = info & 511u, qe = (info >> 12) & 15u;
+            uint32_t minus = (info >> 11) & 1u, m = info & 511u, qe = (info >> 12) & 15u;
             uint32_t l = 0, r = 0, dd = 0;
             bool child = false;
             if (has) {
-                uint32_t w = __ldg(ix.variants + var_off(k) + vn + lane);
+                uint32_t w = __ldg(ix.variants + var_off((info >> 16) & 3u) + vn + lane);
                 seed_interval(ix, code ^ (w & 0xffffffu), qe, l, r);
                 c_seeds++;
                 dd = w >> 24;
@@ -875,6 +972,34 @@ int search_shape_info(int shape, int *scap, int *warps, int *minb)
     return 0;
 }
 
+// The lower-bound pass over all 2n tasks into w.lb (reserved by the caller).
+static int launch_lower_bounds(const mica_index *idx, Workspace &w, const ReadsView &rd, SearchCtl *d_ctl,
+                               cudaStream_t s)
+{
+    if (rd.n == 0) return 0;
+    unsigned g = (unsigned)std::min<uint64_t>((2 * rd.n + 255) / 256, 152ull * 64);
+    k_lower_bounds<<<g, 256, 0, s>>>(idx->view, rd, (unsigned long long *)w.lb.p, d_ctl);
+    MICA_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+// Parity probe: the lower-bound words of all 2n tasks into d_out.
+int debug_lower_bounds(const mica_index *idx, Workspace &w, const ReadsView &rd, unsigned long long *d_out,
+                       cudaStream_t s)
+{
+    if (!idx->has_rev) return MICA_EINVAL;
+    int rc;
+    if ((rc = dev_reserve(w.ctl, sizeof(SearchCtl) + 64))) return rc;
+    MICA_CUDA_TRY(cudaMemsetAsync(w.ctl.p, 0, sizeof(SearchCtl), s));
+    if (rd.n) {
+        unsigned g = (unsigned)std::min<uint64_t>((2 * rd.n + 255) / 256, 152ull * 64);
+        k_lower_bounds<<<g, 256, 0, s>>>(idx->view, rd, d_out, (SearchCtl *)w.ctl.p);
+        MICA_CUDA_TRY(cudaGetLastError());
+    }
+    MICA_CUDA_TRY(cudaStreamSynchronize(s));
+    return 0;
+}
+
 // Reserve the search buffers for n reads and prepare the persistent launch;
 // fills the control-block template (to be copied to the device) and the grid.
 int prepare_persistent(const mica_index *idx, Workspace &w, uint64_t n, int shape_in, SearchCtl &tmpl,
@@ -883,10 +1008,12 @@ int prepare_persistent(const mica_index *idx, Workspace &w, uint64_t n, int shap
     int rc;
     if ((rc = dev_reserve(w.ctl, sizeof(SearchCtl) + 64))) return rc;
     if ((rc = dev_reserve(w.iv_cnt, std::max<uint64_t>(n, 1) * 4))) return rc;
-    if (w.iv_cap == 0) w.iv_cap = (uint32_t)std::min<uint64_t>(4 * n + 65536, 1ull << 30);
+    // room for 4 leaf intervals per read, kept when a smaller batch follows
+    w.iv_cap = (uint32_t)std::max<uint64_t>(w.iv_cap, std::min<uint64_t>(4 * n + 65536, 1ull << 30));
     if (w.spill_cap == 0) w.spill_cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(n, 1u << 20), 1ull << 28);
     if ((rc = dev_reserve(w.iv, (size_t)w.iv_cap * sizeof(Interval)))) return rc;
     if ((rc = dev_reserve(w.spill, (size_t)w.spill_cap * sizeof(WorkItem)))) return rc;
+    if ((rc = dev_reserve(w.lb, std::max<uint64_t>(2 * n, 1) * 8))) return rc;
     shape = (shape_in >= 0 && shape_in < N_SHAPES) ? shape_in : DEFAULT_SHAPE;
     int bps = 0;
     if ((rc = persistent_grid(idx->device, shape, bps))) return rc;
@@ -902,7 +1029,7 @@ int prepare_persistent(const mica_index *idx, Workspace &w, uint64_t n, int shap
 // template, zeroed per-read counters, the kernel between timing events);
 // no host reads, so it can be captured in a CUDA graph.
 int enqueue_persistent(const mica_index *idx, Workspace &w, const ReadsView &rd, int shape, int grid,
-                       const SearchCtl *pinned_tmpl, cudaStream_t s)
+                       const SearchCtl *pinned_tmpl, bool prune, cudaStream_t s, uint64_t &launches)
 {
     SearchCtl *d_ctl = (SearchCtl *)w.ctl.p;
     const PersistShape &sh = g_shapes[shape];
@@ -913,8 +1040,13 @@ int enqueue_persistent(const mica_index *idx, Workspace &w, const ReadsView &rd,
     pa.ctl = d_ctl; pa.iv = (Interval *)w.iv.p; pa.iv_cnt = (uint32_t *)w.iv_cnt.p;
     pa.spill = (WorkItem *)w.spill.p;
     pa.total_warps = grid * sh.warps;
+    pa.lb = prune ? (const unsigned long long *)w.lb.p : nullptr;
     MICA_CUDA_TRY(record_event(w.kev[0], s));
-    if (rd.n) sh.fn<<<grid, sh.warps * 32, sh.smem, s>>>(pa);
+    if (prune && rd.n) {
+        if (int rc = launch_lower_bounds(idx, w, rd, d_ctl, s)) return rc;
+        launches++;
+    }
+    if (rd.n) { sh.fn<<<grid, sh.warps * 32, sh.smem, s>>>(pa); launches++; }
     MICA_CUDA_TRY(cudaGetLastError());
     MICA_CUDA_TRY(record_event(w.kev[1], s));
     return 0;
@@ -927,10 +1059,13 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
     int rc;
     if ((rc = dev_reserve(w.ctl, sizeof(SearchCtl) + 64))) return rc;
     if ((rc = dev_reserve(w.iv_cnt, std::max<uint64_t>(n, 1) * 4))) return rc;
-    if (w.iv_cap == 0) w.iv_cap = (uint32_t)std::min<uint64_t>(4 * n + 65536, 1ull << 30);
+    // room for 4 leaf intervals per read, kept when a smaller batch follows
+    w.iv_cap = (uint32_t)std::max<uint64_t>(w.iv_cap, std::min<uint64_t>(4 * n + 65536, 1ull << 30));
     if (w.spill_cap == 0) w.spill_cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(n, 1u << 20), 1ull << 28);
     SearchCtl *d_ctl = (SearchCtl *)w.ctl.p;
     int shape = (cfg.shape >= 0 && cfg.shape < N_SHAPES) ? cfg.shape : DEFAULT_SHAPE;
+    if (cfg.prune && (rc = dev_reserve(w.lb, std::max<uint64_t>(2 * n, 1) * 8))) return rc;
+    const unsigned long long *d_lb = cfg.prune ? (const unsigned long long *)w.lb.p : nullptr;
     for (int attempt = 0; attempt < 8; attempt++) {
         if ((rc = dev_reserve(w.iv, (size_t)w.iv_cap * sizeof(Interval)))) return rc;
         if ((rc = dev_reserve(w.spill, (size_t)w.spill_cap * sizeof(WorkItem)))) return rc;
@@ -955,7 +1090,12 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
                 pa.spill = (WorkItem *)w.spill.p;
                 int grid = g_num_sms * bps;
                 pa.total_warps = grid * sh.warps;
+                pa.lb = d_lb;
                 MICA_CUDA_TRY(record_event(w.kev[0], s));
+                if (cfg.prune) {
+                    if ((rc = launch_lower_bounds(idx, w, rd, d_ctl, s))) return rc;
+                    st.launches++;
+                }
                 sh.fn<<<grid, sh.warps * 32, sh.smem, s>>>(pa);
                 MICA_CUDA_TRY(cudaGetLastError());
                 MICA_CUDA_TRY(record_event(w.kev[1], s));
@@ -971,6 +1111,7 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
                 pa.requeue_count = &d_ctl->spill_reserve;
                 pa.requeue_cap = w.spill_cap;
                 pa.budget = cfg.plain_budget;
+                pa.lb = d_lb;
                 int blk = cfg.plain_block > 0 ? cfg.plain_block : 128;
                 if (cfg.kernel == MICA_KERNEL_PLAIN_BY_LENGTH) {
                     // one launch per length class, each with its own block size
@@ -988,6 +1129,10 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
                     k_len_scatter<<<g, 256, 0, s>>>(rd, cnt + LEN_CLASSES, cnt + 2 * LEN_CLASSES, (uint32_t *)w.lenlist.p);
                     st.launches += 2;
                     MICA_CUDA_TRY(record_event(w.kev[0], s));
+                    if (cfg.prune) {
+                        if ((rc = launch_lower_bounds(idx, w, rd, d_ctl, s))) return rc;
+                        st.launches++;
+                    }
                     for (uint32_t c = 0; c < LEN_CLASSES; c++) {
                         if (!hc[c]) continue;
                         int bc = cfg.plain_block_len[c] > 0 ? cfg.plain_block_len[c] : blk;
@@ -1001,6 +1146,10 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
                     MICA_CUDA_TRY(record_event(w.kev[1], s));
                 } else {
                     MICA_CUDA_TRY(record_event(w.kev[0], s));
+                    if (cfg.prune) {
+                        if ((rc = launch_lower_bounds(idx, w, rd, d_ctl, s))) return rc;
+                        st.launches++;
+                    }
                     k_plain<<<(unsigned)((pa.ntasks + blk - 1) / blk), blk, 0, s>>>(pa);
                     MICA_CUDA_TRY(cudaGetLastError());
                     MICA_CUDA_TRY(record_event(w.kev[1], s));
@@ -1052,6 +1201,8 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
         st.rounds_multi = out.rounds_kind[0];
         st.rounds_single = out.rounds_kind[1];
         st.rounds_seed = out.rounds_kind[2];
+        st.lb_steps = out.lb_steps;
+        st.lb_dead_tasks = out.lb_dead;
         return 0;
     }
     return MICA_EINTERNAL;

@@ -41,3 +41,39 @@ def hamming_hits(g: np.ndarray, read: np.ndarray, k: int) -> list:
         for pos in np.flatnonzero(d <= k):
             out.append((int(pos), strand, int(d[pos])))
     return sorted(out)
+
+
+def lower_bound_breakpoints(g: np.ndarray, pattern: np.ndarray, k: int, q: int) -> list:
+    """The mismatch lower bound of the pruned search, from its definition:
+    scan P[0, m - q') left to right (q' = min(m, q)), cutting it into maximal
+    pieces that occur in G; each piece P[s, j] that does not occur ends at j
+    (the next starts at j + 1) and gives the breakpoint j + 1.  Stops after
+    k + 1 breakpoints.  Substring occurrence is plain `bytes in bytes`."""
+    text = np.asarray(g, dtype=np.uint8).tobytes()
+    p = np.asarray(pattern, dtype=np.uint8)
+    lim = len(p) - min(len(p), q)
+    out, s = [], 0
+    for j in range(lim):
+        if p[s:j + 1].tobytes() not in text:
+            out.append(j + 1)
+            s = j + 1
+            if len(out) > k:
+                break
+    return out
+
+
+def lb_word(breakpoints: list) -> int:
+    """Pack breakpoints as the GPU does: 9-bit field t = t-th breakpoint, 511 unused."""
+    v = (1 << 64) - 1
+    for t, b in enumerate(breakpoints):
+        v &= ~(511 << (9 * t))
+        v |= b << (9 * t)
+    return v
+
+
+def min_prefix_mismatches(g: np.ndarray, pattern: np.ndarray, i: int) -> int:
+    """min over placements of Ham(P[0, i), G[p, p+i)) by brute force (0 for i = 0)."""
+    if i == 0:
+        return 0
+    w = windows(g, i)
+    return int((w != np.asarray(pattern[:i], dtype=np.uint8)[None, :]).sum(axis=1).min())

@@ -137,6 +137,28 @@ def test_many_intervals_and_the_cap(kernel):
     idx.free()
 
 
+def test_graph_path_interval_overflow_falls_back():
+    """A captured batch whose search overflows the interval buffer (64 reads
+    with thousands of leaf intervals each, far above the 4 per read plus
+    65,536 it is sized for) leaves the post kernels idle and falls back to
+    the regular path, which grows the buffer: the result is the oracle's."""
+    rng = np.random.default_rng(8)
+    core = np.resize(np.array([0, 1], np.uint8), 40_000)
+    mut = rng.random(core.size) < 0.04
+    core[mut] = (core[mut] + rng.integers(1, 4, size=int(mut.sum()))) & 3
+    g = np.concatenate([rng.integers(0, 4, 10_000).astype(np.uint8), core])
+    reads = [g[10_000 + i * 600: 10_000 + i * 600 + 40].copy() for i in range(64)]
+    b = gc.batch_from_reads(reads, [3] * 64)
+    idx = gc.mica().Index.build(synth.to_acgt_bytes(g), kmer_q=10, sa_sample=8)
+    want = oracle.FMIndex(g).align(b, cap=1000)
+    for call in range(2):
+        got = idx.align_batch(b, hit_cap=1000, kernel="persistent")
+        st = idx.stats()
+        gc.assert_same(got, want, f"call {call}")
+        assert st["intervals"] > 4 * 64 + 65_536
+    idx.free()
+
+
 @pytest.mark.parametrize("kernel", KERNELS)
 def test_empty_batch(kernel):
     idx = gc.gpu_index("1m")
