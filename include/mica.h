@@ -132,6 +132,10 @@ typedef struct {
     uint64_t graph_fallbacks; /* a replay overflowed a buffer; the regular path recomputed the call */
     uint64_t lb_steps;       /* lower-bound pass: interval extensions on the reversed genome */
     uint64_t lb_dead_tasks;  /* tasks whose lower bound already exceeds k before any seed */
+    uint64_t queue_wait_ns;  /* persistent kernel: nanoseconds slept by warps waiting on the spill ring
+                                (summed over warps; compare with kernel_ms x warps) */
+    uint64_t idle_wait_ns;   /* persistent kernel: nanoseconds slept by warps with no work */
+    uint64_t overflow_moves; /* persistent kernel: nodes moved to a warp's private overflow stack */
     float search_ms;         /* device time of the search phase (kernel + its control copies) */
     float kernel_ms;         /* device time of the search kernel launch(es) alone, with the
                                 lower-bound pass when pruning */

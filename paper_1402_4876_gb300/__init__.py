@@ -65,7 +65,7 @@ class Stats(ctypes.Structure):
                 ("tasks", "seeds", "nodes", "rank_blocks", "intervals", "located", "lf_steps",
                  "spills", "retries", "launches", "warp_rounds", "lane_ops", "rounds_multi", "rounds_single",
                  "rounds_seed", "graph_captures", "graph_replays", "graph_fallbacks", "lb_steps",
-                 "lb_dead_tasks")] + [("search_ms", ctypes.c_float), ("kernel_ms", ctypes.c_float),
+                 "lb_dead_tasks", "queue_wait_ns", "idle_wait_ns", "overflow_moves")] + [("search_ms", ctypes.c_float), ("kernel_ms", ctypes.c_float),
                                                       ("total_ms", ctypes.c_float)]
 
     def as_dict(self) -> dict:

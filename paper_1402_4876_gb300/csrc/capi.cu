@@ -18,6 +18,13 @@ void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int 
     snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s:%d)", cudaGetErrorString(e), what, file, line);
 }
 
+static thread_local char g_last_internal[256];
+
+void set_last_internal(const char *msg)
+{
+    snprintf(g_last_internal, sizeof(g_last_internal), "%s", msg);
+}
+
 int dev_reserve(DevBuf &b, size_t bytes)
 {
     if (bytes <= b.bytes && b.p) return 0;
@@ -47,7 +54,7 @@ void free_workspace(Workspace &w)
 {
     DevBuf *all[] = {&w.ctl, &w.iv, &w.iv_sorted, &w.iv_cnt, &w.iv_off, &w.total, &w.keep, &w.hit_off,
                      &w.hits, &w.spill, &w.big, &w.scan_tmp, &w.reads_words, &w.reads_off, &w.reads_len,
-                     &w.reads_k, &w.spill2, &w.lenlist, &w.lb};
+                     &w.reads_k, &w.spill2, &w.lenlist, &w.lb, &w.spill_seq, &w.deep};
     for (DevBuf *b : all) dev_release(*b);
     for (auto &e : w.ev)
         if (e) { cudaEventDestroy(e); e = nullptr; }
@@ -167,7 +174,7 @@ static int align_graph(const mica_index *idx, Workspace &w, mica_stats &st, cons
                                (uint64_t)w.lb.p, (uint64_t)w.iv_sorted.p, (uint64_t)w.iv_off.p,
                                (uint64_t)w.total.p, (uint64_t)w.keep.p, (uint64_t)w.hit_off.p, (uint64_t)w.hits.p,
                                (uint64_t)w.big.p, (uint64_t)w.scan_tmp.p, w.hit_capacity, (uint64_t)w.iv_cap,
-                               (uint64_t)w.spill_cap};
+                               (uint64_t)w.spill_cap, (uint64_t)w.spill_seq.p, (uint64_t)w.deep.p};
     if (!w.gexec || memcmp(key, w.gkey, sizeof(key)) != 0) {
         if (w.gexec) { cudaGraphExecDestroy(w.gexec); w.gexec = nullptr; }
         uint64_t L = 0;
@@ -221,6 +228,9 @@ static int align_graph(const mica_index *idx, Workspace &w, mica_stats &st, cons
     st.rounds_seed = out.rounds_kind[2];
     st.lb_steps = out.lb_steps;
     st.lb_dead_tasks = out.lb_dead;
+    st.queue_wait_ns = out.wait_queue_ns;
+    st.idle_wait_ns = out.wait_idle_ns;
+    st.overflow_moves = out.deep_moves;
     st.located = nhits;
     st.lf_steps = steps;
     st.launches += w.glaunches;
@@ -285,7 +295,7 @@ const char *mica_strerror(int code)
     case MICA_EIO: return "index file I/O error or malformed file";
     case MICA_ECUDA: return g_last_error[0] ? g_last_error : "CUDA error";
     case MICA_ETIMEOUT: return "bounded wait expired";
-    case MICA_EINTERNAL: return "internal capacity retry did not converge";
+    case MICA_EINTERNAL: return g_last_internal[0] ? g_last_internal : "internal capacity retry did not converge";
     case MICA_EBUSY: return "request not finished";
     case MICA_ENOTFOUND: return "unknown request";
     default: return "unknown error";

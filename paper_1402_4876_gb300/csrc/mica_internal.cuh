@@ -90,14 +90,14 @@ struct Interval {
 };
 
 // Work item in the device queues: a seed range of a (read, strand) task or a
-// continuation node.  meta: bit 31 valid flag (spill queue), bit 30 kind
-// (1 = node), bit 29 strand, bits 0..1 d, bits 8..16 i (node).
+// continuation node.  meta: bit 30 kind (1 = node), bit 29 strand, bits 0..1
+// d, bits 8..16 i (node).  The persistent kernel's spill ring publishes items
+// through a separate sequence word per slot.
 struct WorkItem {
     uint32_t read;
     uint32_t meta;
     uint32_t a, b;   // node: l, r; seeds: first, end variant
 };
-constexpr uint32_t WI_VALID = 1u << 31;
 constexpr uint32_t WI_NODE = 1u << 30;
 constexpr uint32_t WI_MINUS = 1u << 29;
 
@@ -124,6 +124,8 @@ struct SearchCtl {
     unsigned long long rounds, lane_ops;
     unsigned long long rounds_kind[3];   // multi-row, single-row, seed rounds
     unsigned long long lb_steps, lb_dead; // lower-bound pass: extensions, tasks with no budget left
+    unsigned long long wait_queue_ns, wait_idle_ns;   // sleeps in queue waits / by idle warps (summed)
+    unsigned long long deep_moves;                    // nodes moved to per-warp overflow stacks
 };
 
 constexpr unsigned ERR_IV_OVERFLOW = 1u;
@@ -149,12 +151,14 @@ struct DeviceGuard {
     ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
 };
 
-constexpr int GRAPH_KEY = 24;   // words identifying a captured batch shape
+constexpr int GRAPH_KEY = 26;   // words identifying a captured batch shape
 
 // Per-index workspace reused across align calls.
 struct Workspace {
     DevBuf ctl, iv, iv_sorted, iv_cnt, iv_off, total, keep, hit_off, hits, spill, big, scan_tmp;
     DevBuf lb;   // per (read, strand) task: mismatch lower-bound breakpoints (uint64)
+    DevBuf spill_seq;   // spill ring: one sequence word per slot
+    DevBuf deep;        // per-warp overflow stacks of the persistent kernel
     DevBuf reads_words, reads_off, reads_len, reads_k;   // staging for host batches
     DevBuf spill2;                                        // plain kernel re-queue ping-pong
     DevBuf lenlist;                                       // plain kernel: reads by length class
@@ -200,6 +204,7 @@ namespace mica {
     } while (0)
 
 void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+void set_last_internal(const char *msg);   // detail returned by mica_strerror(MICA_EINTERNAL)
 
 // Records a timing event on s.  While s is being captured into a graph a
 // plain record is only a dependency marker, so the event becomes an external

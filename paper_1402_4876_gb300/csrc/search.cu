@@ -343,6 +343,13 @@ __global__ void k_len_scatter(ReadsView rd, const unsigned int *base, unsigned i
     }
 }
 
+// The spill ring's sequence words for a fresh launch: slot i expects
+// position i.
+__global__ void k_ring_init(uint32_t *seq, uint32_t cap)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x) seq[i] = i;
+}
+
 // --------------------------------------------------------------------------
 // Persistent warp-pool kernel
 // --------------------------------------------------------------------------
@@ -350,9 +357,14 @@ __global__ void k_len_scatter(ReadsView rd, const unsigned int *base, unsigned i
 constexpr uint32_t ADMIT_LOW = 64;          // admit tasks when pending work < this
 constexpr uint32_t IDLE_LIMIT = 1u << 22;    // idle rounds (>= 1 us each) before timing out
 constexpr uint32_t SPIN_LIMIT = 1u << 22;    // waits for a reserved queue entry
+constexpr uint32_t RESERVE_LIMIT = 1u << 20; // spill reservation attempts (lost races back off)
+constexpr uint32_t FULL_WAITS = 1024;        // waits on a full ring before a room spill gives up
+constexpr uint32_t DONATE_TRIES = 8;         // reservation attempts of a donation under contention
+constexpr uint32_t DEEP_CAP = 2048;          // entries of each per-warp overflow stack
 constexpr uint32_t DONATE_MIN = 96;          // stack depth that makes a warp share work
 constexpr uint32_t DONATE_N = 64;
-constexpr int DEFAULT_SHAPE = 3;   // 128-node stacks, 8 warps, 4 CTAs per SM: fastest measured
+constexpr int DEFAULT_SHAPE = 0;   // 256-node stacks, 8 warps, 3 CTAs per SM: fastest measured
+                                   // on both the 64 Mbp and the 3.1 Gbp genome
 
 struct PersistArgs {
     IndexView ix;
@@ -363,6 +375,9 @@ struct PersistArgs {
     Interval *iv;
     uint32_t *iv_cnt;
     WorkItem *spill;
+    uint32_t *seq;                  // spill ring: one sequence word per slot
+    uint4 *deep_m;                  // per-warp overflow stacks in global memory: multi-row nodes
+    uint2 *deep_s;                  //   and single-row nodes, DEEP_CAP entries per warp each
     int total_warps;
     const unsigned long long *lb;   // optional: lower-bound breakpoints per (read, strand)
 };
@@ -401,18 +416,52 @@ __device__ __forceinline__ uint16_t node_meta(uint32_t slot, uint32_t i, uint32_
     return (uint16_t)(slot | (i << 5) | (d << 14));
 }
 
-// Move the `nsp` oldest nodes of one stack to the device spill queue.
+// Move the `nsp` oldest nodes of one stack to the device spill queue, a
+// bounded ring of spill_cap (a power of two) work items with one sequence
+// word per slot (Vyukov's bounded multi-producer multi-consumer queue):
+// slot p % cap may be written for position p when its sequence is p, is
+// readable when it is p + 1, and is released for position p + cap after the
+// read.  Slots are reserved only while the items reserved and not yet
+// claimed fit in the ring, so a producer waits (bounded) only for a consumer
+// that has already claimed the previous item and is reading it.  A full ring refuses a donation (returns false, stack unchanged);
+// when the nodes must go to make room, they are dropped and the overflow flag
+// makes the host rerun the batch with a larger ring.
 template <int SCAP, bool SINGLE>
-__device__ __forceinline__ void spill_bottom(WarpSmem<SCAP> &W, const PersistArgs &a, uint32_t &bot,
+__device__ __forceinline__ bool spill_bottom(WarpSmem<SCAP> &W, const PersistArgs &a, uint32_t &bot,
                                              uint32_t nsp, uint32_t s_read, uint32_t s_info, int lane,
-                                             uint32_t &c_spills)
+                                             uint32_t &c_spills, bool donation)
 {
     SearchCtl *ctl = a.ctl;
+    const uint32_t cap = ctl->spill_cap;
     uint32_t at0 = 0;
-    if (lane == 0) at0 = atomicAdd(&ctl->spill_reserve, nsp);
+    int ok = 0;
+    if (lane == 0) {
+        uint32_t full_waits = 0;
+        unsigned long long waited = 0;
+        for (uint32_t tries = 0; tries < RESERVE_LIMIT; tries++) {
+            // claims never pass reservations, so reading the claim counter
+            // first gives R - H >= 0 (an over-estimate of the backlog)
+            uint32_t H = atomicAdd(&ctl->spill_head, 0u);
+            __threadfence();
+            uint32_t R = atomicAdd(&ctl->spill_reserve, 0u);
+            if ((int)(R - H) < 0 || (R - H) + nsp > cap) {
+                // full: a donation gives up, room waits a little for readers
+                if (donation || ++full_waits > FULL_WAITS) break;
+                __nanosleep(256);
+                waited += 256;
+                continue;
+            }
+            if (atomicCAS(&ctl->spill_reserve, R, R + nsp) == R) { at0 = R; ok = 1; break; }
+            if (donation && tries + 1 >= DONATE_TRIES) break;   // contended: the donor keeps its nodes
+            __nanosleep(32 + 8 * (tries & 31));     // lost the race to another producer: back off
+            waited += 32 + 8 * (tries & 31);
+        }
+        if (waited) atomicAdd(&ctl->wait_queue_ns, waited);
+        if (!ok && !donation) atomicOr(&ctl->error, ERR_SPILL_OVERFLOW);
+    }
+    ok = __shfl_sync(FULL, ok, 0);
     at0 = __shfl_sync(FULL, at0, 0);
-    uint32_t cap = ctl->spill_cap;
-    if (at0 + nsp > cap && lane == 0) atomicOr(&ctl->error, ERR_SPILL_OVERFLOW);
+    if (!ok && donation) return false;
     for (uint32_t r0 = 0; r0 < nsp; r0 += 32) {
         uint32_t j = r0 + lane;
         bool act = j < nsp;
@@ -426,15 +475,27 @@ __device__ __forceinline__ void spill_bottom(WarpSmem<SCAP> &W, const PersistArg
         uint32_t rid = __shfl_sync(FULL, s_read, sl);
         uint32_t info = __shfl_sync(FULL, s_info, sl);
         if (act) {
-            if (at0 + j < cap) {
-                WorkItem *it = a.spill + at0 + j;
-                it->read = rid;
-                it->a = l;
-                it->b = r;
-                __threadfence();
-                uint32_t meta = WI_VALID | WI_NODE | (((info >> 11) & 1u) ? WI_MINUS : 0u) |
-                                (((mm >> 5) & 511u) << 8) | (mm >> 14);
-                *(volatile uint32_t *)&it->meta = meta;
+            if (ok) {
+                const uint32_t pos = at0 + j, slot_i = pos & (cap - 1);
+                WorkItem *it = a.spill + slot_i;
+                volatile uint32_t *sq = a.seq + slot_i;
+                uint32_t spin = 0;
+                bool free_ = true;
+                while (*sq != pos) {               // previous lap's item not read yet
+                    if (++spin > SPIN_LIMIT) { atomicOr(&ctl->error, ERR_TIMEOUT); free_ = false; break; }
+                    __nanosleep(64);
+                }
+                if (spin) atomicAdd(&ctl->wait_queue_ns, 64ull * spin);
+                if (free_) {
+                    __threadfence();
+                    it->read = rid;
+                    it->a = l;
+                    it->b = r;
+                    it->meta = WI_NODE | (((info >> 11) & 1u) ? WI_MINUS : 0u) | (((mm >> 5) & 511u) << 8) |
+                               (mm >> 14);
+                    __threadfence();
+                    *sq = pos + 1;                 // published
+                }
             }
             atomicAdd(&W.live[sl], -1);
         }
@@ -442,18 +503,82 @@ __device__ __forceinline__ void spill_bottom(WarpSmem<SCAP> &W, const PersistArg
     bot += nsp;
     if (lane == 0) c_spills += nsp;
     __syncwarp();
+    return true;
 }
 
-// Make room for `add` more nodes on a stack, spilling its oldest ones.
+// The warp's private overflow stacks: when a shared-memory stack is full its
+// oldest nodes move to global memory (coalesced, no atomics, no other warp
+// involved) and come back under the stack's bottom when it runs low, so the
+// order stays depth-first and the nodes keep their task slots.
+__device__ __forceinline__ uint4 *deep_m_of(const PersistArgs &a, int warp_global)
+{
+    return a.deep_m + (size_t)warp_global * DEEP_CAP;
+}
+__device__ __forceinline__ uint2 *deep_s_of(const PersistArgs &a, int warp_global)
+{
+    return a.deep_s + (size_t)warp_global * DEEP_CAP;
+}
+
+// Move the `n` oldest nodes of a stack to its overflow stack (n fits).
 template <int SCAP, bool SINGLE>
-__device__ __forceinline__ void make_room(WarpSmem<SCAP> &W, const PersistArgs &a, uint32_t &bot, uint32_t top,
-                                          uint32_t add, uint32_t s_read, uint32_t s_info, int lane,
-                                          uint32_t &c_spills)
+__device__ __forceinline__ void deep_push(WarpSmem<SCAP> &W, const PersistArgs &a, int wg, uint32_t &dtop,
+                                          uint32_t &bot, uint32_t n, int lane)
+{
+    for (uint32_t r0 = 0; r0 < n; r0 += 32) {
+        uint32_t j = r0 + (uint32_t)lane;
+        if (j < n) {
+            uint32_t p = (bot + j) & (SCAP - 1);
+            if (SINGLE) deep_s_of(a, wg)[dtop + j] = make_uint2(W.sl[p], W.sm[p]);
+            else deep_m_of(a, wg)[dtop + j] = make_uint4(W.ml[p], W.mr[p], W.mm[p], 0u);
+        }
+    }
+    dtop += n;
+    bot += n;
+    __syncwarp();
+}
+
+// Bring the `n` most recently moved nodes back under the stack's bottom.
+template <int SCAP, bool SINGLE>
+__device__ __forceinline__ void deep_pop(WarpSmem<SCAP> &W, const PersistArgs &a, int wg, uint32_t &dtop,
+                                         uint32_t &bot, uint32_t n, int lane)
+{
+    for (uint32_t r0 = 0; r0 < n; r0 += 32) {
+        uint32_t j = r0 + (uint32_t)lane;
+        if (j < n) {
+            uint32_t p = (bot - n + j) & (SCAP - 1);
+            if (SINGLE) {
+                uint2 v = deep_s_of(a, wg)[dtop - n + j];
+                W.sl[p] = v.x;
+                W.sm[p] = (uint16_t)v.y;
+            } else {
+                uint4 v = deep_m_of(a, wg)[dtop - n + j];
+                W.ml[p] = v.x;
+                W.mr[p] = v.y;
+                W.mm[p] = (uint16_t)v.z;
+            }
+        }
+    }
+    dtop -= n;
+    bot -= n;
+    __syncwarp();
+}
+
+// Make room for `add` more nodes on a stack: its oldest nodes go to the
+// warp's overflow stack, or to the shared spill ring when that is full.
+template <int SCAP, bool SINGLE>
+__device__ __forceinline__ void make_room(WarpSmem<SCAP> &W, const PersistArgs &a, int wg, uint32_t &dtop,
+                                          uint32_t &bot, uint32_t top, uint32_t add, uint32_t s_read,
+                                          uint32_t s_info, int lane, uint32_t &c_spills, uint32_t &c_deep)
 {
     if ((top - bot) + add > (uint32_t)SCAP) {
         uint32_t nsp = (top - bot) + add - SCAP + SCAP / 4;
         nsp = min((nsp + 31) & ~31u, top - bot);
-        spill_bottom<SCAP, SINGLE>(W, a, bot, nsp, s_read, s_info, lane, c_spills);
+        if (dtop + nsp <= DEEP_CAP) {
+            deep_push<SCAP, SINGLE>(W, a, wg, dtop, bot, nsp, lane);
+            c_deep += nsp;
+        } else {
+            spill_bottom<SCAP, SINGLE>(W, a, bot, nsp, s_read, s_info, lane, c_spills, false);
+        }
     }
 }
 
@@ -518,9 +643,13 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
     uint32_t s_read = 0, s_info = 0, s_code = 0, s_vnext = 0, s_vend = 0;
     bool s_used = false;
     uint32_t mbot = 0, mtop = 0, sbot = 0, stop = 0;
+    uint32_t dmt = 0, dst = 0;    // entries in the warp's overflow stacks (multi-row, single-row)
+    const int wg = (int)blockIdx.x * WARPS + warp;
     bool busy = false;
     uint32_t idle_rounds = 0;   // consecutive rounds without work; the sleep grows with it
     uint32_t c_seeds = 0, c_nodes = 0, c_blocks = 0, c_spills = 0;   // per lane
+    unsigned long long c_idle_ns = 0;                                 // warp-uniform
+    uint32_t c_deep = 0;                                              // warp-uniform
     uint32_t c_km = 0, c_ks = 0, c_kq = 0;                           // rounds by kind (warp-uniform)
     __syncwarp();
 
@@ -529,28 +658,40 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
 
         if (s_used && W.live[lane] == 0 && s_vnext >= s_vend) s_used = false;
         unsigned used = __ballot_sync(FULL, s_used);
-        uint32_t mc = mtop - mbot, sc = stop - sbot, cnt = mc + sc;
+        uint32_t mc = mtop - mbot, sc = stop - sbot;
+        // refill a low stack from the warp's overflow stack (mc, sc < 32: room for 64)
+        if (mc < 32 && dmt > 0) {
+            uint32_t k = min(dmt, 64u);
+            deep_pop<SCAP, false>(W, a, wg, dmt, mbot, k, lane);
+            mc += k;
+        }
+        if (sc < 32 && dst > 0) {
+            uint32_t k = min(dst, 64u);
+            deep_pop<SCAP, true>(W, a, wg, dst, sbot, k, lane);
+            sc += k;
+        }
+        uint32_t cnt = mc + sc;
         uint32_t avail = s_used ? s_vend - s_vnext : 0u;
         uint32_t seeds_total = __reduce_add_sync(FULL, avail);
         unsigned freem = ~used;
 
-        // ---- admission of new work into free slots
-        if (freem != 0 && cnt + seeds_total < ADMIT_LOW) {
+        // ---- admission of new work into free slots (not while the overflow stacks hold work)
+        if (freem != 0 && cnt + seeds_total + dmt + dst < ADMIT_LOW) {
             bool idle = (cnt + seeds_total == 0) && used == 0;
             // an idle warp first peeks without atomics
             if (idle && !busy) {
                 int pw = 0;
                 if (lane == 0) {
                     uint32_t h = vload(&ctl->spill_head);
-                    uint32_t R = min(vload(&ctl->spill_reserve), spill_cap);
-                    pw = (h < R) || (vload64(&ctl->task_head) < a.ntasks);
+                    uint32_t R = vload(&ctl->spill_reserve);
+                    pw = (R != h) || (vload64(&ctl->task_head) < a.ntasks);
                     if (!pw) {
                         // nothing queued: finished once no warp holds work
                         if (vload((const unsigned *)&ctl->busy) == 0) {
                             __threadfence();
                             h = vload(&ctl->spill_head);
-                            R = min(vload(&ctl->spill_reserve), spill_cap);
-                            if (h >= R && vload64(&ctl->task_head) >= a.ntasks) pw = -1;
+                            R = vload(&ctl->spill_reserve);
+                            if (R == h && vload64(&ctl->task_head) >= a.ntasks) pw = -1;
                         }
                     }
                 }
@@ -562,6 +703,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
                         break;
                     }
                     __nanosleep(256u << min(idle_rounds, 5u));
+                    c_idle_ns += 256u << min(idle_rounds, 5u);
                     continue;
                 }
             }
@@ -572,8 +714,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
                 if (!busy) atomicAdd(&ctl->busy, 1);
                 for (int tries = 0; tries < 32; tries++) {
                     uint32_t h = atomicAdd(&ctl->spill_head, 0u);
-                    uint32_t R = min(atomicAdd(&ctl->spill_reserve, 0u), spill_cap);
-                    if (h >= R) break;
+                    __threadfence();
+                    uint32_t R = atomicAdd(&ctl->spill_reserve, 0u);   // read after h: R - h is the backlog
+                    if ((int)(R - h) <= 0) break;
                     uint32_t n = min(R - h, want);
                     if (atomicCAS(&ctl->spill_head, h, h + n) == h) { h0 = h; take = n; break; }
                 }
@@ -595,20 +738,23 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
                 if (mine) {
                     uint32_t rid, minus, vb, ve;
                     if (j < take) {
-                        WorkItem *it = a.spill + h0 + j;
-                        volatile uint32_t *vm = &it->meta;
-                        uint32_t meta = *vm;
+                        const uint32_t pos = h0 + j, slot_i = pos & (spill_cap - 1);
+                        WorkItem *it = a.spill + slot_i;
+                        volatile uint32_t *sq = a.seq + slot_i;
                         uint32_t spin = 0;
-                        while (!(meta & WI_VALID)) {
-                            if (++spin > SPIN_LIMIT) { atomicOr(&ctl->error, ERR_TIMEOUT); break; }
+                        bool ready = true;
+                        while (*sq != pos + 1) {          // written by its producer?
+                            if (++spin > SPIN_LIMIT) { atomicOr(&ctl->error, ERR_TIMEOUT); ready = false; break; }
                             __nanosleep(128);
-                            meta = *vm;
                         }
+                        if (spin) atomicAdd(&ctl->wait_queue_ns, 128ull * spin);
                         __threadfence();
                         rid = *(volatile uint32_t *)&it->read;
+                        uint32_t meta = *(volatile uint32_t *)&it->meta;
                         uint32_t xa = *(volatile uint32_t *)&it->a, xb = *(volatile uint32_t *)&it->b;
-                        *vm = 0u;
-                        if (!(meta & WI_VALID)) { rid = 0; meta = WI_NODE; xa = xb = 0; }   // timed out
+                        __threadfence();
+                        if (ready) *sq = pos + spill_cap;   // the slot is free for the next lap
+                        else { rid = 0; meta = WI_NODE; xa = xb = 0; }   // timed out
                         minus = (meta & WI_MINUS) ? 1u : 0u;
                         if (meta & WI_NODE) {
                             is_node = xa < xb;
@@ -669,8 +815,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
                     int old = atomicSub(&ctl->busy, 1);
                     if (old == 1) {
                         uint32_t h = atomicAdd(&ctl->spill_head, 0u);
-                        uint32_t R = min(atomicAdd(&ctl->spill_reserve, 0u), spill_cap);
-                        if (h >= R && vload64(&ctl->task_head) >= a.ntasks) done = 1;
+                        uint32_t R = atomicAdd(&ctl->spill_reserve, 0u);
+                        if (R == h && vload64(&ctl->task_head) >= a.ntasks) done = 1;
                     }
                 }
                 busy = false;
@@ -680,6 +826,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
                     break;
                 }
                 __nanosleep(256u << min(idle_rounds, 5u));
+                c_idle_ns += 256u << min(idle_rounds, 5u);
                 continue;
             }
         }
@@ -826,8 +973,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
             uint32_t pre = warp_excl_scan(packed, lane);
             uint32_t tot = __shfl_sync(FULL, pre + packed, 31);
             uint32_t tm = tot & 0xffu, ts = tot >> 8;
-            if (tm) make_room<SCAP, false>(W, a, mbot, mtop, tm, s_read, s_info, lane, c_spills);
-            if (ts) make_room<SCAP, true>(W, a, sbot, stop, ts, s_read, s_info, lane, c_spills);
+            if (tm) make_room<SCAP, false>(W, a, wg, dmt, mbot, mtop, tm, s_read, s_info, lane, c_spills, c_deep);
+            if (ts) make_room<SCAP, true>(W, a, wg, dst, sbot, stop, ts, s_read, s_info, lane, c_spills, c_deep);
             if (nm | ns) {
                 uint32_t pm = mtop + (pre & 0xffu), ps = stop + (pre >> 8);
 #pragma unroll
@@ -880,19 +1027,21 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
         __syncwarp();
 
         // ---- share work with idle warps near the end of the batch
-        if ((iter & 31) == 31 && (mtop - mbot) + (stop - sbot) > DONATE_MIN) {
+        if ((iter & 31) == 31 && (mtop - mbot) + (stop - sbot) + dmt + dst > DONATE_MIN) {
             int give = 0;
             if (lane == 0) {
                 uint32_t h = vload(&ctl->spill_head);
-                uint32_t R = min(vload(&ctl->spill_reserve), spill_cap);
-                give = h >= R && vload64(&ctl->task_head) >= a.ntasks &&
+                uint32_t R = vload(&ctl->spill_reserve);
+                give = R == h && vload64(&ctl->task_head) >= a.ntasks &&
                        (int)vload((const unsigned *)&ctl->busy) < a.total_warps;
             }
             if (__shfl_sync(FULL, give, 0)) {
                 if (stop - sbot >= mtop - mbot)
-                    spill_bottom<SCAP, true>(W, a, sbot, min(DONATE_N, stop - sbot), s_read, s_info, lane, c_spills);
+                    spill_bottom<SCAP, true>(W, a, sbot, min(DONATE_N, stop - sbot), s_read, s_info, lane, c_spills,
+                                             true);
                 else
-                    spill_bottom<SCAP, false>(W, a, mbot, min(DONATE_N, mtop - mbot), s_read, s_info, lane, c_spills);
+                    spill_bottom<SCAP, false>(W, a, mbot, min(DONATE_N, mtop - mbot), s_read, s_info, lane, c_spills,
+                                              true);
             }
         }
     }
@@ -907,6 +1056,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
     if (lane == 0 && v) atomicAdd(&ctl->rank_blocks, v);
     v = c_spills; for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     if (lane == 0 && v) atomicAdd(&ctl->spills, v);
+    if (lane == 0 && c_idle_ns) atomicAdd(&ctl->wait_idle_ns, c_idle_ns);
+    if (lane == 0 && c_deep) atomicAdd(&ctl->deep_moves, (unsigned long long)c_deep);
     if (lane == 0) atomicAdd(&ctl->rounds, (unsigned long long)c_km + c_ks + c_kq);
     v = (unsigned long long)c_seeds + c_nodes; for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     if (lane == 0 && v) atomicAdd(&ctl->lane_ops, v);
@@ -972,6 +1123,36 @@ int search_shape_info(int shape, int *scap, int *warps, int *minb)
     return 0;
 }
 
+// Spill ring capacity for a batch of n reads: a power of two >= max(n, 2^20).
+static uint32_t ring_capacity(uint64_t n)
+{
+    uint64_t c = 1u << 20;
+    while (c < n && c < (1ull << 28)) c <<= 1;
+    return (uint32_t)c;
+}
+
+// Per-warp overflow stacks for a grid of `total_warps` warps: DEEP_CAP multi-row
+// entries (16 B) then DEEP_CAP single-row entries (8 B) per warp.
+static int reserve_deep(Workspace &w, int total_warps)
+{
+    return dev_reserve(w.deep, (size_t)total_warps * DEEP_CAP * 24);
+}
+
+static void deep_ptrs(const Workspace &w, int total_warps, uint4 *&dm, uint2 *&ds)
+{
+    dm = (uint4 *)w.deep.p;
+    ds = (uint2 *)((char *)w.deep.p + (size_t)total_warps * DEEP_CAP * 16);
+}
+
+// Fresh sequence words for the spill ring (w.spill_seq, spill_cap entries).
+static int launch_ring_init(Workspace &w, cudaStream_t s)
+{
+    unsigned g = (unsigned)std::min<uint64_t>((w.spill_cap + 255) / 256, 152ull * 8);
+    k_ring_init<<<g, 256, 0, s>>>((uint32_t *)w.spill_seq.p, w.spill_cap);
+    MICA_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
 // The lower-bound pass over all 2n tasks into w.lb (reserved by the caller).
 static int launch_lower_bounds(const mica_index *idx, Workspace &w, const ReadsView &rd, SearchCtl *d_ctl,
                                cudaStream_t s)
@@ -1010,14 +1191,16 @@ int prepare_persistent(const mica_index *idx, Workspace &w, uint64_t n, int shap
     if ((rc = dev_reserve(w.iv_cnt, std::max<uint64_t>(n, 1) * 4))) return rc;
     // room for 4 leaf intervals per read, kept when a smaller batch follows
     w.iv_cap = (uint32_t)std::max<uint64_t>(w.iv_cap, std::min<uint64_t>(4 * n + 65536, 1ull << 30));
-    if (w.spill_cap == 0) w.spill_cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(n, 1u << 20), 1ull << 28);
+    if (w.spill_cap == 0) w.spill_cap = ring_capacity(n);
     if ((rc = dev_reserve(w.iv, (size_t)w.iv_cap * sizeof(Interval)))) return rc;
     if ((rc = dev_reserve(w.spill, (size_t)w.spill_cap * sizeof(WorkItem)))) return rc;
     if ((rc = dev_reserve(w.lb, std::max<uint64_t>(2 * n, 1) * 8))) return rc;
+    if ((rc = dev_reserve(w.spill_seq, (size_t)w.spill_cap * 4))) return rc;
     shape = (shape_in >= 0 && shape_in < N_SHAPES) ? shape_in : DEFAULT_SHAPE;
     int bps = 0;
     if ((rc = persistent_grid(idx->device, shape, bps))) return rc;
     grid = g_num_sms * bps;
+    if ((rc = reserve_deep(w, grid * g_shapes[shape].warps))) return rc;
     tmpl = SearchCtl{};
     tmpl.ntasks = 2 * n;
     tmpl.spill_cap = w.spill_cap;
@@ -1041,6 +1224,12 @@ int enqueue_persistent(const mica_index *idx, Workspace &w, const ReadsView &rd,
     pa.spill = (WorkItem *)w.spill.p;
     pa.total_warps = grid * sh.warps;
     pa.lb = prune ? (const unsigned long long *)w.lb.p : nullptr;
+    pa.seq = (uint32_t *)w.spill_seq.p;
+    deep_ptrs(w, pa.total_warps, pa.deep_m, pa.deep_s);
+    if (rd.n) {
+        if (int rc = launch_ring_init(w, s)) return rc;
+        launches++;
+    }
     MICA_CUDA_TRY(record_event(w.kev[0], s));
     if (prune && rd.n) {
         if (int rc = launch_lower_bounds(idx, w, rd, d_ctl, s)) return rc;
@@ -1061,7 +1250,7 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
     if ((rc = dev_reserve(w.iv_cnt, std::max<uint64_t>(n, 1) * 4))) return rc;
     // room for 4 leaf intervals per read, kept when a smaller batch follows
     w.iv_cap = (uint32_t)std::max<uint64_t>(w.iv_cap, std::min<uint64_t>(4 * n + 65536, 1ull << 30));
-    if (w.spill_cap == 0) w.spill_cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(n, 1u << 20), 1ull << 28);
+    if (w.spill_cap == 0) w.spill_cap = ring_capacity(n);
     SearchCtl *d_ctl = (SearchCtl *)w.ctl.p;
     int shape = (cfg.shape >= 0 && cfg.shape < N_SHAPES) ? cfg.shape : DEFAULT_SHAPE;
     if (cfg.prune && (rc = dev_reserve(w.lb, std::max<uint64_t>(2 * n, 1) * 8))) return rc;
@@ -1090,7 +1279,13 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
                 pa.spill = (WorkItem *)w.spill.p;
                 int grid = g_num_sms * bps;
                 pa.total_warps = grid * sh.warps;
+                if ((rc = reserve_deep(w, pa.total_warps))) return rc;
+                deep_ptrs(w, pa.total_warps, pa.deep_m, pa.deep_s);
                 pa.lb = d_lb;
+                if ((rc = dev_reserve(w.spill_seq, (size_t)w.spill_cap * 4))) return rc;
+                pa.seq = (uint32_t *)w.spill_seq.p;
+                if ((rc = launch_ring_init(w, s))) return rc;
+                st.launches++;
                 MICA_CUDA_TRY(record_event(w.kev[0], s));
                 if (cfg.prune) {
                     if ((rc = launch_lower_bounds(idx, w, rd, d_ctl, s))) return rc;
@@ -1183,6 +1378,11 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
         if (out.error & ERR_TIMEOUT) { w.spill_dirty = true; return MICA_ETIMEOUT; }
         if (out.error & (ERR_IV_OVERFLOW | ERR_SPILL_OVERFLOW)) {
             st.retries++;
+            char msg[256];
+            snprintf(msg, sizeof(msg),
+                     "internal capacity retry did not converge (last error bits 0x%x, %u intervals for %u, "
+                     "%llu spills, ring %u)", out.error, out.iv_count, w.iv_cap, out.spills, w.spill_cap);
+            set_last_internal(msg);
             if (out.error & ERR_IV_OVERFLOW)
                 w.iv_cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(2ull * out.iv_count, 2ull * w.iv_cap), 0xfffffff0ull);
             if (out.error & ERR_SPILL_OVERFLOW)
@@ -1203,6 +1403,9 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
         st.rounds_seed = out.rounds_kind[2];
         st.lb_steps = out.lb_steps;
         st.lb_dead_tasks = out.lb_dead;
+        st.queue_wait_ns = out.wait_queue_ns;
+        st.idle_wait_ns = out.wait_idle_ns;
+        st.overflow_moves = out.deep_moves;
         return 0;
     }
     return MICA_EINTERNAL;
