@@ -213,6 +213,10 @@ typedef struct {
                                on the device; 0 = 65536 */
     uint32_t plain_block_len[4];  /* MICA_KERNEL_PLAIN_BY_LENGTH: block size per length class;
                                      0 = plain_block */
+    int32_t prefetch;       /* persistent kernel: at the end of a round, prefetch into L2 the
+                               occurrence blocks of the next round's nodes.  -1 = automatic (on
+                               when the occurrence blocks exceed 96 MiB and so do not stay in
+                               L2), 0 = off, 1 = on */
 } mica_tuning;
 
 /* Number of compiled persistent kernel shapes; mica_tuning_shape_info

@@ -74,7 +74,7 @@ class Stats(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("shape", ctypes.c_int32), ("plain_block", ctypes.c_uint32), ("plain_budget", ctypes.c_uint32),
-                ("plain_block_len", ctypes.c_uint32 * 4)]
+                ("plain_block_len", ctypes.c_uint32 * 4), ("prefetch", ctypes.c_int32)]
 
 
 def tuning_shapes() -> list:
@@ -295,8 +295,9 @@ class Index:
         d["C"] = list(i.C)
         return d
 
-    def set_tuning(self, shape: int = -1, plain_block: int = 0, plain_budget: int = 0, plain_block_len=(0, 0, 0, 0)):
-        t = Tuning(shape, plain_block, plain_budget, (ctypes.c_uint32 * 4)(*plain_block_len))
+    def set_tuning(self, shape: int = -1, plain_block: int = 0, plain_budget: int = 0, plain_block_len=(0, 0, 0, 0),
+                   prefetch: int = -1):
+        t = Tuning(shape, plain_block, plain_budget, (ctypes.c_uint32 * 4)(*plain_block_len), prefetch)
         _check(_lib.mica_set_tuning(self._h, ctypes.byref(t)), "mica_set_tuning")
 
     def autotune(self, batch, hit_cap: int = 1000, repeats: int = 2, cache: str | None = None) -> dict:
@@ -325,7 +326,7 @@ class Index:
         t = Tuning()
         _check(_lib.mica_get_tuning(self._h, ctypes.byref(t)), "mica_get_tuning")
         return {"shape": t.shape, "plain_block": t.plain_block, "plain_budget": t.plain_budget,
-                "plain_block_len": list(t.plain_block_len)}
+                "plain_block_len": list(t.plain_block_len), "prefetch": t.prefetch}
 
     def stats(self) -> dict:
         s = Stats()

@@ -140,6 +140,13 @@ static int read_array(FILE *f, DevBuf &b, uint64_t bytes)
 
 // ---- align orchestration ----
 
+// Prefetching the next round's blocks pays when they are not L2 hits.
+static bool use_prefetch(const mica_index *idx)
+{
+    if (idx->tuning.prefetch >= 0) return idx->tuning.prefetch == 1;
+    return idx->n_occ_blocks * 32 > (96ull << 20);
+}
+
 // The persistent pipeline as one CUDA graph per batch shape: captured the
 // first time a shape (input addresses, read count, cap, kernel shape, buffer
 // addresses) is seen, then replayed with a single host synchronisation.  Any
@@ -166,10 +173,12 @@ static int align_graph(const mica_index *idx, Workspace &w, mica_stats &st, cons
     }
     memcpy(w.pin_tmpl, &tmpl, sizeof(tmpl));
     const bool prune = p.prune && idx->has_rev;
+    const bool prefetch = use_prefetch(idx);
     // every input, size and workspace buffer the captured kernels use: a
     // buffer grown by any other call since the capture forces a new capture
     uint64_t key[GRAPH_KEY] = {(uint64_t)rd.words, (uint64_t)rd.word_off, (uint64_t)rd.len, (uint64_t)rd.k, n,
-                               p.hit_cap, (uint64_t)shape | ((uint64_t)prune << 32), (uint64_t)grid,
+                               p.hit_cap, (uint64_t)shape | ((uint64_t)prune << 32) | ((uint64_t)prefetch << 33),
+                               (uint64_t)grid,
                                (uint64_t)w.ctl.p, (uint64_t)w.iv.p, (uint64_t)w.iv_cnt.p, (uint64_t)w.spill.p,
                                (uint64_t)w.lb.p, (uint64_t)w.iv_sorted.p, (uint64_t)w.iv_off.p,
                                (uint64_t)w.total.p, (uint64_t)w.keep.p, (uint64_t)w.hit_off.p, (uint64_t)w.hits.p,
@@ -179,7 +188,8 @@ static int align_graph(const mica_index *idx, Workspace &w, mica_stats &st, cons
         if (w.gexec) { cudaGraphExecDestroy(w.gexec); w.gexec = nullptr; }
         uint64_t L = 0;
         MICA_CUDA_TRY(cudaStreamBeginCapture(w.gstream, cudaStreamCaptureModeThreadLocal));
-        int crc = enqueue_persistent(idx, w, rd, shape, grid, (const SearchCtl *)w.pin_tmpl, prune, w.gstream, L);
+        int crc = enqueue_persistent(idx, w, rd, shape, grid, (const SearchCtl *)w.pin_tmpl, prune, prefetch,
+                                     w.gstream, L);
         if (!crc) crc = enqueue_post_device(idx, w, rd, p.hit_cap, w.hit_capacity, w.gstream, w.pin_status, L);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(w.gstream, &g);
@@ -266,6 +276,7 @@ int align_on_device(const mica_index *idx, Workspace &w, mica_stats &st, const R
     cfg.plain_block = idx->tuning.plain_block ? (int)idx->tuning.plain_block : 128;
     cfg.plain_budget = idx->tuning.plain_budget ? idx->tuning.plain_budget : (1u << 16);
     cfg.prune = p.prune && idx->has_rev;
+    cfg.prefetch = use_prefetch(idx);
     for (uint32_t c = 0; c < LEN_CLASSES; c++)
         cfg.plain_block_len[c] = idx->tuning.plain_block_len[c] ? (int)idx->tuning.plain_block_len[c] : cfg.plain_block;
     int rc = run_search(idx, w, st, rd, cfg, s);
@@ -532,6 +543,7 @@ int mica_set_tuning(mica_index *idx, const mica_tuning *t)
         if (t->plain_block_len[c] &&
             (t->plain_block_len[c] < 32 || t->plain_block_len[c] > 512 || t->plain_block_len[c] % 32))
             return MICA_EINVAL;
+    if (t->prefetch < -1 || t->prefetch > 1) return MICA_EINVAL;
     idx->tuning = *t;
     return 0;
 }

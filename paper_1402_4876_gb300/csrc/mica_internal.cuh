@@ -189,7 +189,7 @@ struct mica_index {
     bool has_rev = false;
     mica::Workspace ws;
     mica_stats stats{};
-    mica_tuning tuning{-1, 0, 0, {0, 0, 0, 0}};
+    mica_tuning tuning{-1, 0, 0, {0, 0, 0, 0}, -1};
 };
 
 namespace mica {
@@ -248,6 +248,7 @@ struct SearchConfig {
     uint32_t plain_budget;      // plain: node expansions per task before re-queueing
     int plain_block_len[4] = {0, 0, 0, 0};   // plain by length: block size per class
     bool prune = false;         // compute and use mismatch lower bounds (index has them)
+    bool prefetch = false;      // persistent: prefetch the next round's occurrence blocks into L2
 };
 constexpr uint32_t LEN_CLASSES = 4;   // 1-64, 65-128, 129-192, 193-256 bases
 int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd,
@@ -258,7 +259,8 @@ int prepare_persistent(const mica_index *idx, Workspace &w, uint64_t n, int shap
 int debug_lower_bounds(const mica_index *idx, Workspace &w, const ReadsView &rd, unsigned long long *d_out,
                        cudaStream_t s);
 int enqueue_persistent(const mica_index *idx, Workspace &w, const ReadsView &rd, int shape, int grid,
-                       const SearchCtl *pinned_tmpl, bool prune, cudaStream_t s, uint64_t &launches);
+                       const SearchCtl *pinned_tmpl, bool prune, bool prefetch, cudaStream_t s,
+                       uint64_t &launches);
 int search_shape_info(int shape, int *scap, int *warps, int *minb);
 
 // post.cu

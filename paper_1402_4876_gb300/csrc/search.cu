@@ -101,6 +101,30 @@ __device__ __forceinline__ int lb_budget(unsigned long long v, uint32_t k, uint3
     return (int)k - (int)lb_at(v, i);
 }
 
+// Occ(c, l) and Occ(c, r) for one symbol c (one block read when l and r share
+// it); returns the 32-byte blocks touched.
+__device__ __forceinline__ uint32_t occ_single_pair(const IndexView &ix, uint32_t l, uint32_t r, uint32_t c,
+                                                    uint32_t &ol, uint32_t &orr)
+{
+    uint32_t bl = l / OCC_ROWS, xl = l - bl * OCC_ROWS;
+    uint32_t br = r / OCC_ROWS, xr = r - br * OCC_ROWS;
+    uint4 sl = ld_nc(ix.super + bl / SB_BLOCKS);
+    OccBlock a;
+    if (bl == br) {
+        load_block(ix, bl, xr, a);
+        ol = occ_single(ix, bl, xl, sl, a, c);
+        orr = occ_single(ix, br, xr, sl, a, c);
+        return 1;
+    }
+    uint4 sr = ld_nc(ix.super + br / SB_BLOCKS);
+    OccBlock b;
+    load_block(ix, bl, xl, a);
+    load_block(ix, br, xr, b);
+    ol = occ_single(ix, bl, xl, sl, a, c);
+    orr = occ_single(ix, br, xr, sr, b, c);
+    return 2;
+}
+
 __global__ void __launch_bounds__(256) k_lower_bounds(const IndexView ix, const ReadsView rd,
                                                       unsigned long long *__restrict__ lb, SearchCtl *ctl)
 {
@@ -131,11 +155,11 @@ __global__ void __launch_bounds__(256) k_lower_bounds(const IndexView ix, const 
                 r = c == 0 ? rv.C[1] : c == 1 ? rv.C[2] : c == 2 ? rv.C[3] : rv.C[4];
                 fresh = false;
             } else {
-                uint32_t ol[4], orr[4];
-                blocks += occ_pair(rv, l, r, ol, orr);
+                uint32_t ol, orr;
+                blocks += occ_single_pair(rv, l, r, c, ol, orr);
                 steps++;
-                l = cbase + sel4(ol, c);
-                r = cbase + sel4(orr, c);
+                l = cbase + ol;
+                r = cbase + orr;
             }
             if (l >= r) {
                 // P[s, j] does not occur: one more forced mismatch from prefix j + 1 on
@@ -379,6 +403,7 @@ struct PersistArgs {
     uint4 *deep_m;                  // per-warp overflow stacks in global memory: multi-row nodes
     uint2 *deep_s;                  //   and single-row nodes, DEEP_CAP entries per warp each
     int total_warps;
+    bool prefetch;                  // warm the next round's occurrence blocks in L2
     const unsigned long long *lb;   // optional: lower-bound breakpoints per (read, strand)
 };
 
@@ -439,10 +464,10 @@ __device__ __forceinline__ bool spill_bottom(WarpSmem<SCAP> &W, const PersistArg
         uint32_t full_waits = 0;
         unsigned long long waited = 0;
         for (uint32_t tries = 0; tries < RESERVE_LIMIT; tries++) {
-            // claims never pass reservations, so reading the claim counter
-            // first gives R - H >= 0 (an over-estimate of the backlog)
+            // both counters only grow and claims never pass reservations: with
+            // H read first R - H >= 0 over-estimates the backlog at the CAS
+            // below (a negative difference is a stale read, treated as full)
             uint32_t H = atomicAdd(&ctl->spill_head, 0u);
-            __threadfence();
             uint32_t R = atomicAdd(&ctl->spill_reserve, 0u);
             if ((int)(R - H) < 0 || (R - H) + nsp > cap) {
                 // full: a donation gives up, room waits a little for readers
@@ -582,6 +607,30 @@ __device__ __forceinline__ void make_room(WarpSmem<SCAP> &W, const PersistArgs &
     }
 }
 
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// Ask L2 for the occurrence blocks of the nodes the next round will take
+// (the top 32 of each stack), so that round's dependent loads find them
+// there instead of in HBM.  No register waits on a prefetch.
+template <int SCAP>
+__device__ __forceinline__ void prefetch_next(const WarpSmem<SCAP> &W, const IndexView &ix, uint32_t mbot,
+                                              uint32_t mtop, uint32_t sbot, uint32_t stop, int lane)
+{
+    if ((uint32_t)lane < mtop - mbot) {
+        uint32_t p = (mtop - 1 - (uint32_t)lane) & (SCAP - 1);
+        uint32_t bl = W.ml[p] / OCC_ROWS, br = W.mr[p] / OCC_ROWS;
+        prefetch_l2(ix.occ + (size_t)bl * 2);
+        if (br != bl) prefetch_l2(ix.occ + (size_t)br * 2);
+    }
+    if ((uint32_t)lane < stop - sbot) {
+        uint32_t p = (stop - 1 - (uint32_t)lane) & (SCAP - 1);
+        prefetch_l2(ix.occ + (size_t)(W.sl[p] / OCC_ROWS) * 2);
+    }
+}
+
 // Write at most one leaf interval per lane with one warp-wide atomic.
 __device__ __forceinline__ void emit_one(const PersistArgs &a, bool leaf, uint32_t rid, uint32_t d, uint32_t minus,
                                          uint32_t l, uint32_t r, int lane, unsigned lt)
@@ -712,10 +761,12 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
             unsigned long long t0 = 0;
             if (lane == 0) {
                 if (!busy) atomicAdd(&ctl->busy, 1);
-                for (int tries = 0; tries < 32; tries++) {
+                // a plain read first: the ring is usually empty, and then no atomic is spent
+                bool ring = vload(&ctl->spill_reserve) != vload(&ctl->spill_head);
+                for (int tries = 0; ring && tries < 32; tries++) {
+                    // claims up to R, both counters only grow: R - h <= 0 is a stale read
                     uint32_t h = atomicAdd(&ctl->spill_head, 0u);
-                    __threadfence();
-                    uint32_t R = atomicAdd(&ctl->spill_reserve, 0u);   // read after h: R - h is the backlog
+                    uint32_t R = atomicAdd(&ctl->spill_reserve, 0u);
                     if ((int)(R - h) <= 0) break;
                     uint32_t n = min(R - h, want);
                     if (atomicCAS(&ctl->spill_head, h, h + n) == h) { h0 = h; take = n; break; }
@@ -1025,6 +1076,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
             if (lane == 0 && bp) atomicAdd(&W.live[s], __popc(bp));
         }
         __syncwarp();
+        if (a.prefetch) prefetch_next<SCAP>(W, ix, mbot, mtop, sbot, stop, lane);
 
         // ---- share work with idle warps near the end of the batch
         if ((iter & 31) == 31 && (mtop - mbot) + (stop - sbot) + dmt + dst > DONATE_MIN) {
@@ -1212,7 +1264,8 @@ int prepare_persistent(const mica_index *idx, Workspace &w, uint64_t n, int shap
 // template, zeroed per-read counters, the kernel between timing events);
 // no host reads, so it can be captured in a CUDA graph.
 int enqueue_persistent(const mica_index *idx, Workspace &w, const ReadsView &rd, int shape, int grid,
-                       const SearchCtl *pinned_tmpl, bool prune, cudaStream_t s, uint64_t &launches)
+                       const SearchCtl *pinned_tmpl, bool prune, bool prefetch, cudaStream_t s,
+                       uint64_t &launches)
 {
     SearchCtl *d_ctl = (SearchCtl *)w.ctl.p;
     const PersistShape &sh = g_shapes[shape];
@@ -1225,6 +1278,7 @@ int enqueue_persistent(const mica_index *idx, Workspace &w, const ReadsView &rd,
     pa.total_warps = grid * sh.warps;
     pa.lb = prune ? (const unsigned long long *)w.lb.p : nullptr;
     pa.seq = (uint32_t *)w.spill_seq.p;
+    pa.prefetch = prefetch;
     deep_ptrs(w, pa.total_warps, pa.deep_m, pa.deep_s);
     if (rd.n) {
         if (int rc = launch_ring_init(w, s)) return rc;
@@ -1281,6 +1335,7 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
                 pa.total_warps = grid * sh.warps;
                 if ((rc = reserve_deep(w, pa.total_warps))) return rc;
                 deep_ptrs(w, pa.total_warps, pa.deep_m, pa.deep_s);
+                pa.prefetch = cfg.prefetch;
                 pa.lb = d_lb;
                 if ((rc = dev_reserve(w.spill_seq, (size_t)w.spill_cap * 4))) return rc;
                 pa.seq = (uint32_t *)w.spill_seq.p;
