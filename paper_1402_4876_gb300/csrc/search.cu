@@ -384,7 +384,7 @@ constexpr uint32_t SPIN_LIMIT = 1u << 22;    // waits for a reserved queue entry
 constexpr uint32_t RESERVE_LIMIT = 1u << 20; // spill reservation attempts (lost races back off)
 constexpr uint32_t FULL_WAITS = 1024;        // waits on a full ring before a room spill gives up
 constexpr uint32_t DONATE_TRIES = 8;         // reservation attempts of a donation under contention
-constexpr uint32_t DEEP_CAP = 2048;          // entries of each per-warp overflow stack
+constexpr uint32_t DEEP_CAP = 8192;          // entries of each per-warp overflow stack
 constexpr uint32_t DONATE_MIN = 96;          // stack depth that makes a warp share work
 constexpr uint32_t DONATE_N = 64;
 constexpr int DEFAULT_SHAPE = 0;   // 256-node stacks, 8 warps, 3 CTAs per SM: fastest measured
@@ -724,8 +724,11 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
         uint32_t seeds_total = __reduce_add_sync(FULL, avail);
         unsigned freem = ~used;
 
-        // ---- admission of new work into free slots (not while the overflow stacks hold work)
-        if (freem != 0 && cnt + seeds_total + dmt + dst < ADMIT_LOW) {
+        // ---- admission of new work into free slots (not while the overflow stacks hold
+        // work; a warp that still has work tries only every fourth iteration, so
+        // the queue counters are not hammered by warps that can keep busy)
+        if (freem != 0 && cnt + seeds_total + dmt + dst < ADMIT_LOW &&
+            (cnt + seeds_total == 0 || (iter & 3) == 0)) {
             bool idle = (cnt + seeds_total == 0) && used == 0;
             // an idle warp first peeks without atomics
             if (idle && !busy) {
@@ -763,7 +766,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
                 if (!busy) atomicAdd(&ctl->busy, 1);
                 // a plain read first: the ring is usually empty, and then no atomic is spent
                 bool ring = vload(&ctl->spill_reserve) != vload(&ctl->spill_head);
-                for (int tries = 0; ring && tries < 32; tries++) {
+                for (int tries = 0; ring && tries < 4; tries++) {   // contended: try again later
                     // claims up to R, both counters only grow: R - h <= 0 is a stale read
                     uint32_t h = atomicAdd(&ctl->spill_head, 0u);
                     uint32_t R = atomicAdd(&ctl->spill_reserve, 0u);
@@ -835,21 +838,32 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
                     W.live[lane] = is_node ? 1 : 0;
                     W.lb[lane] = lbv;
                 }
-                // stage the new tasks' patterns: one coalesced word per lane
-                unsigned todo = __ballot_sync(FULL, mine);
-                while (todo) {
-                    int s = __ffs(todo) - 1;
-                    todo &= todo - 1;
-                    uint32_t rid = __shfl_sync(FULL, s_read, s), info = __shfl_sync(FULL, s_info, s);
-                    uint32_t m = info & 511u, minus = (info >> 11) & 1u;
-                    uint32_t Wn = (m + 15) >> 4;
-                    unsigned long long off = a.rd.word_off[rid];
-                    uint32_t raw = (uint32_t)lane < Wn ? a.rd.words[off + lane] : 0u;
-                    uint32_t hi = __shfl_sync(FULL, raw, (int)((Wn - 1 - lane) & 31u));
-                    uint32_t lo = __shfl_sync(FULL, raw, (int)((Wn - 2 - lane) & 31u));
-                    if ((uint32_t)lane + 1 >= Wn) lo = 0u;
-                    uint32_t out = minus ? rc_word(hi, lo, m) : raw;
-                    if ((uint32_t)lane < Wn) W.pat[s][lane] = out;
+                // stage the new tasks' patterns, each lane its own slot's read:
+                // the loads of all new slots are independent, so an admission
+                // waits for a couple of memory round trips instead of two per
+                // new task.  A minus-strand pattern is first stored word-reversed
+                // and then turned into the reverse complement in place (word j
+                // needs stored words j and j + 1, and only word j is overwritten).
+                if (mine) {
+                    const uint32_t m = s_info & 511u, minus = (s_info >> 11) & 1u;
+                    const uint32_t Wn = (m + 15) >> 4;
+                    const uint32_t *src = a.rd.words + a.rd.word_off[s_read];
+                    uint32_t *row = W.pat[lane];
+#pragma unroll
+                    for (uint32_t c0 = 0; c0 < MAX_WORDS; c0 += 8) {
+                        uint32_t v[8];
+#pragma unroll
+                        for (uint32_t j = 0; j < 8; j++) v[j] = c0 + j < Wn ? __ldg(src + c0 + j) : 0u;
+#pragma unroll
+                        for (uint32_t j = 0; j < 8; j++)
+                            if (c0 + j < Wn) row[minus ? Wn - 1 - (c0 + j) : c0 + j] = v[j];
+                    }
+                    if (minus) {
+                        for (uint32_t j = 0; j < Wn; j++) {
+                            uint32_t hi = row[j], lo = j + 1 < Wn ? row[j + 1] : 0u;
+                            row[j] = rc_word(hi, lo, m);
+                        }
+                    }
                 }
                 __syncwarp();
                 if (mine) s_code = window_code(W.pat[lane], s_info & 511u, (s_info >> 12) & 15u);
