@@ -380,7 +380,7 @@ __global__ void k_ring_init(uint32_t *seq, uint32_t cap)
 
 constexpr uint32_t ADMIT_LOW = 64;          // admit tasks when pending work < this
 constexpr uint32_t IDLE_LIMIT = 1u << 22;    // idle rounds (>= 1 us each) before timing out
-constexpr uint32_t SPIN_LIMIT = 1u << 22;    // waits for a reserved queue entry
+constexpr uint32_t SPIN_LIMIT = 1u << 24;    // waits on one ring slot (64-128 ns each: ~1-2 s)
 constexpr uint32_t RESERVE_LIMIT = 1u << 20; // spill reservation attempts (lost races back off)
 constexpr uint32_t FULL_WAITS = 1024;        // waits on a full ring before a room spill gives up
 constexpr uint32_t DONATE_TRIES = 8;         // reservation attempts of a donation under contention
