@@ -379,6 +379,9 @@ __global__ void k_ring_init(uint32_t *seq, uint32_t cap)
 // --------------------------------------------------------------------------
 
 constexpr uint32_t ADMIT_LOW = 64;          // admit tasks when pending work < this
+constexpr int ADMIT_MIN_FREE = 8;            // ... and, while holding work, >= this many slots are free
+                                             // (an admission costs a few memory round trips whatever
+                                             // it takes, so it should fill several slots)
 constexpr uint32_t IDLE_LIMIT = 1u << 22;    // idle rounds (>= 1 us each) before timing out
 constexpr uint32_t SPIN_LIMIT = 1u << 24;    // waits on one ring slot (64-128 ns each: ~1-2 s)
 constexpr uint32_t RESERVE_LIMIT = 1u << 20; // spill reservation attempts (lost races back off)
@@ -725,10 +728,12 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
         unsigned freem = ~used;
 
         // ---- admission of new work into free slots (not while the overflow stacks hold
-        // work; a warp that still has work tries only every fourth iteration, so
-        // the queue counters are not hammered by warps that can keep busy)
+        // work; a warp that still has work tries only every fourth iteration and
+        // once several slots are free or its work runs low, so the queue counters
+        // are not hammered and each admission fills several slots)
         if (freem != 0 && cnt + seeds_total + dmt + dst < ADMIT_LOW &&
-            (cnt + seeds_total == 0 || (iter & 3) == 0)) {
+            (cnt + seeds_total == 0 ||
+             ((iter & 3) == 0 && (__popc(freem) >= ADMIT_MIN_FREE || cnt + seeds_total < ADMIT_LOW / 4)))) {
             bool idle = (cnt + seeds_total == 0) && used == 0;
             // an idle warp first peeks without atomics
             if (idle && !busy) {
