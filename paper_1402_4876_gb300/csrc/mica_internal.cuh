@@ -112,8 +112,9 @@ struct Hit {
 struct SearchCtl {
     unsigned long long task_head;     // next fresh task
     unsigned long long ntasks;
-    unsigned int spill_reserve;       // spill queue: reserved slots
-    unsigned int spill_head;          // spill queue: consumed slots
+    unsigned int spill_reserve;       // spill ring: positions reserved by producers (plain kernel:
+                                      //   items in its re-queue array)
+    unsigned int spill_head;          // spill ring: positions claimed by consumers
     unsigned int spill_cap;
     int busy;                         // warps holding work
     unsigned int iv_count;            // intervals written

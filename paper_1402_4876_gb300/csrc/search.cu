@@ -8,7 +8,11 @@
 // every way of substituting at most k of them (the "seed variants"); each
 // non-empty interval continues base by base: a node (i, [l, r), d) has a
 // child for every symbol c with l' = C[c] + Occ(c, l) < r' = C[c] + Occ(c, r)
-// and d + [c != P[i-1]] <= k; nodes with i = 0 are leaf intervals.
+// and d + [c != P[i-1]] <= k; nodes with i = 0 are leaf intervals.  With
+// lower bounds (k_lower_bounds, from the reversed genome) a child at depth i
+// must also satisfy d + D(i) <= k, and the seed window takes at most
+// k - D(m - qe) substitutions: branches that cannot reach a hit are dropped,
+// the leaf set is unchanged.
 //
 // Two kernels produce the same leaf set:
 //   * k_plain:      one task per thread, depth-first with a stack in local
@@ -16,11 +20,13 @@
 //                   nodes (and untried seeds) to a re-queue that the next
 //                   launch drains.
 //   * k_persistent: one CTA per SM slot, each warp a work pool of up to 32
-//                   tasks.  Every round the 32 lanes take the 32 newest nodes
-//                   of the warp's shared-memory stack (topped up with seed
-//                   lookups), extend them in parallel, and compact the
-//                   children back with ballot/shuffle prefix sums.  Excess
-//                   nodes spill to a device queue that idle warps drain.
+//                   tasks.  Every round the 32 lanes take the newest nodes
+//                   of one kind from the warp's shared-memory stacks (or
+//                   seed lookups of one task), extend them in parallel, and
+//                   compact the children back with ballot/shuffle prefix
+//                   sums.  Full stacks move their oldest nodes to the warp's
+//                   overflow stacks in global memory; near the end of a batch
+//                   warps donate nodes through a bounded ring to idle warps.
 #include <algorithm>
 #include <mutex>
 
@@ -210,7 +216,7 @@ __device__ __forceinline__ void requeue_push(const PlainArgs &a, uint32_t read, 
     if (at < a.requeue_cap) {
         WorkItem it;
         it.read = read;
-        it.meta = meta;   // no ready flag: only the persistent kernel's queue uses it
+        it.meta = meta;   // a plain array: the persistent kernel's ring publishes through sequence words
         it.a = x;
         it.b = y;
         a.requeue[at] = it;

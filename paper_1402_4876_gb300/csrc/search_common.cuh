@@ -1,5 +1,5 @@
 // Device helpers shared by the search and locate kernels: occurrence counts
-// from one 64-byte block, interval extension, read patterns and seed lookups.
+// from one 32-byte block, interval extension, read patterns and seed lookups.
 #pragma once
 
 #include "mica_internal.cuh"
