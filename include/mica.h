@@ -300,6 +300,46 @@ int mica_server_get_stats(mica_server *srv, mica_server_stats *out);
    uncollected results. */
 void mica_server_stop(mica_server *srv);
 
+/* ---- mate pairing (after the search; no effect on its result) ----
+ *
+ * The paper benchmarks paired-end reads and reports the share of properly
+ * paired ones (Section 3, Table 1).  Reads 2i and 2i + 1 of a batch are the
+ * two mates of pair i.  A concordant placement of pair i is a listed hit a of
+ * one mate on the + strand and a listed hit b of the other mate on the -
+ * strand with fragment length L = b.pos + m_b - a.pos (m_b the length of b's
+ * mate) in [insert_min, insert_max] -- the forward/reverse orientation of
+ * paired-end sequencing.  Only listed hits are paired: a mate whose total
+ * exceeds the cap contributes its listed hits alone.
+ *
+ * Per pair: n_concordant = number of such (a, b) combinations; mm = the
+ * smallest a.mm + b.mm among them and n_best = how many reach it (1 = a
+ * unique best placement); pos_plus / pos_minus / plus_mate describe the best
+ * one, ties broken by smallest pos_plus, then mate 1 before mate 2 on the +
+ * strand, then smallest pos_minus.  With no concordant placement n_concordant
+ * = n_best = 0 and the other fields are 0.
+ */
+typedef struct {
+    uint32_t n_concordant;
+    uint32_t n_best;
+    uint32_t pos_plus;    /* + strand hit of the best placement (fragment start) */
+    uint32_t pos_minus;   /* - strand hit of the best placement */
+    uint8_t plus_mate;    /* 0: mate 1 is on the + strand, 1: mate 2 */
+    uint8_t mm;           /* substitutions of both mates together */
+    uint16_t pad;
+} mica_pair;
+
+/* Pair the device result of a batch of 2 * n_pairs reads (d_offsets: 2 *
+   n_pairs + 1 CSR offsets, d_hits: hits sorted by (pos, strand) per read as
+   mica_align_device returns them, d_lengths: read lengths) into d_out[n_pairs]
+   on cuda_stream (NULL = legacy default stream) of the current device;
+   returns without waiting.  MICA_EINVAL if insert_min > insert_max. */
+int mica_pair_device(const uint64_t *d_offsets, const mica_hit *d_hits, const uint16_t *d_lengths,
+                     uint64_t n_pairs, uint32_t insert_min, uint32_t insert_max, mica_pair *d_out,
+                     void *cuda_stream);
+/* The same on host arrays (copied to `device` and back; synchronous). */
+int mica_pair_batch(int device, const uint64_t *offsets, const mica_hit *hits, const uint16_t *lengths,
+                    uint64_t n_pairs, uint32_t insert_min, uint32_t insert_max, mica_pair *out);
+
 /* ---- hit-list offsets for callers that cannot allocate device memory ----
  *
  * The paper has no counterpart: this serves callers that may not call

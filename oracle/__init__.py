@@ -19,6 +19,11 @@ Functions and what pins them (tests/test_oracle_*.py):
   genome (chance hits are vanishingly rare there), reverse-complement symmetry,
   and for the hit cap by the properties that define it.
 * :func:`bruteforce` -- pinned against the numpy scan in the tests.
+* :func:`pair` -- mate pairing of a result (the paper's properly paired
+  reads, Section 3, Table 1), plain Python loops over every combination of
+  listed hits; pinned by the generator's true fragments on a random genome
+  (every pair found concordant at its true fragment, with its true
+  substitutions) and by hand-worked cases.
 """
 from __future__ import annotations
 
@@ -224,3 +229,38 @@ def bruteforce(g, batch, threads: int = 0) -> Result:
     h = lib.oracle_bruteforce(_ptr(g), len(g), _ptr(words), _ptr(off), _ptr(lens), _ptr(k),
                               len(lens), threads)
     return _take_result(lib, h)
+
+
+def pair(result: Result, lengths, insert_min: int, insert_max: int) -> list:
+    """For each pair i (reads 2i, 2i+1): every listed + strand hit a of one
+    mate with every listed - strand hit b of the other, concordant when
+    L = b.pos + m_b - a.pos is in [insert_min, insert_max] (m_b: the length
+    of b's read).  Returns per pair (n_concordant, n_best, pos_plus,
+    pos_minus, plus_mate, mm): the count, the smallest a.mm + b.mm, how many
+    combinations reach it, and the best one by (mm, pos_plus, plus_mate,
+    pos_minus); zeros when there is none."""
+    lengths = np.asarray(lengths)
+    out = []
+    for p in range((len(result.offsets) - 1) // 2):
+        mates = [result.as_tuples(2 * p), result.as_tuples(2 * p + 1)]
+        combos = []
+        for amate in (0, 1):
+            bmate = 1 - amate
+            mb = int(lengths[2 * p + bmate])
+            for (apos, astr, ad) in mates[amate]:
+                if astr != 0:
+                    continue
+                for (bpos, bstr, bd) in mates[bmate]:
+                    if bstr != 1:
+                        continue
+                    frag = bpos + mb - apos
+                    if insert_min <= frag <= insert_max:
+                        combos.append((ad + bd, apos, amate, bpos))
+        if not combos:
+            out.append((0, 0, 0, 0, 0, 0))
+            continue
+        best = min(combos)
+        n_best = sum(1 for c in combos if c[0] == best[0])
+        out.append((len(combos), n_best, best[1], best[3], best[2], best[0]))
+    return out
+

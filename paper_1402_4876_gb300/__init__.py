@@ -139,6 +139,8 @@ SIGNATURES = {
     "mica_offsets_noalloc": (_i32, [P, _u64, P, P]),
     "mica_gather_ceiling": (_i32, [ctypes.c_int, _u64, _u32, _u64, _u32, P, P]),
     "mica_debug_lower_bounds": (_i32, [P, P, P, P, P, _u64, P]),
+    "mica_pair_device": (_i32, [P, P, P, _u64, _u32, _u32, P, P]),
+    "mica_pair_batch": (_i32, [ctypes.c_int, P, P, P, _u64, _u32, _u32, P]),
     "mica_server_params_default": (None, [P]),
     "mica_server_start": (_i32, [P, P, P]),
     "mica_server_submit": (_i32, [P, P, P, P, P, _u64, P]),
@@ -484,6 +486,32 @@ def offsets_noalloc(d_counts, n: int, d_offsets, stream=None) -> None:
     ptr = lambda x: x if isinstance(x, int) else x.data_ptr()
     _check(_lib.mica_offsets_noalloc(ctypes.c_void_p(ptr(d_counts)), n, ctypes.c_void_p(ptr(d_offsets)),
                                      _stream_handle(stream)), "mica_offsets_noalloc")
+
+
+PAIR_DTYPE = np.dtype([("n_concordant", np.uint32), ("n_best", np.uint32), ("pos_plus", np.uint32),
+                       ("pos_minus", np.uint32), ("plus_mate", np.uint8), ("mm", np.uint8), ("pad", np.uint16)])
+
+
+def pair_batch(result, lengths, insert_min: int, insert_max: int, device: int = 0) -> np.ndarray:
+    """mica_pair_batch: mate pairing of a host Result whose reads 2i, 2i+1 are
+    the mates of pair i; returns a PAIR_DTYPE array, one row per pair."""
+    off = np.ascontiguousarray(result.offsets, dtype=np.uint64)
+    hits = np.ascontiguousarray(result.hits)
+    lens = np.ascontiguousarray(lengths, dtype=np.uint16)
+    n_pairs = (off.size - 1) // 2
+    out = np.zeros(n_pairs, dtype=PAIR_DTYPE)
+    _check(_lib.mica_pair_batch(device, _ptr(off), _ptr(hits) if hits.size else None, _ptr(lens) if lens.size else None,
+                                n_pairs, insert_min, insert_max, _ptr(out) if n_pairs else None), "mica_pair_batch")
+    return out
+
+
+def pair_device(d_offsets, d_hits, d_lengths, n_pairs: int, insert_min: int, insert_max: int, d_out,
+                stream=None) -> None:
+    """mica_pair_device on device pointers (ints) or torch CUDA tensors."""
+    ptr = lambda x: x if isinstance(x, int) else x.data_ptr()
+    _check(_lib.mica_pair_device(ctypes.c_void_p(ptr(d_offsets)), ctypes.c_void_p(ptr(d_hits)),
+                                 ctypes.c_void_p(ptr(d_lengths)), n_pairs, insert_min, insert_max,
+                                 ctypes.c_void_p(ptr(d_out)), _stream_handle(stream)), "mica_pair_device")
 
 
 def gather_ceiling(buffer_bytes: int, load_bytes: int = 32, loads: int = 1 << 28, repeats: int = 3,

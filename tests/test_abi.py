@@ -66,3 +66,6 @@ def test_host_side_rejections_need_no_gpu():
     assert lib.mica_gather_ceiling(0, 1 << 20, 24, 1 << 20, 1, ctypes.byref(gbs), None) == mica.MICA_EINVAL
     assert lib.mica_gather_ceiling(0, 1000, 32, 1 << 20, 1, ctypes.byref(gbs), None) == mica.MICA_EINVAL
     assert lib.mica_gather_ceiling(0, 1 << 20, 32, 1 << 20, 1, None, None) == mica.MICA_EINVAL
+    # pairing rejects an inverted insert window before touching a device
+    assert lib.mica_pair_batch(0, None, None, None, 1, 700, 300, None) == mica.MICA_EINVAL
+    assert lib.mica_pair_device(None, None, None, 1, 700, 300, None, None) == mica.MICA_EINVAL
