@@ -84,7 +84,14 @@ typedef struct {
     void *cuda_stream;   /* cudaStream_t to run on; NULL = the legacy default stream */
     uint32_t prune;      /* 1 (default): prune by mismatch lower bounds when the index has
                             them; 0: plain exhaustive backtracking.  Same result either way. */
+    uint32_t report;     /* MICA_REPORT_*: which placements a read's total and list cover */
 } mica_align_params;
+
+enum {
+    MICA_REPORT_ALL = 0,          /* H(R): every placement with d <= k (default) */
+    MICA_REPORT_BEST_STRATUM = 1  /* the placements of H(R) with the read's smallest d; total = their
+                                     number (1 = a unique best placement), cap and order as above */
+};
 
 typedef struct {
     uint32_t pos;        /* leftmost forward coordinate of the matched window */
@@ -158,7 +165,8 @@ const char *mica_strerror(int code);
 
 /* Fill *p with the defaults (kmer_q 12, sa_sample 16, lower_bounds 1). */
 void mica_index_params_default(mica_index_params *p);
-/* Fill *p with the defaults (hit_cap 1000, persistent kernel, default stream, prune 1). */
+/* Fill *p with the defaults (hit_cap 1000, persistent kernel, default stream, prune 1,
+   report MICA_REPORT_ALL). */
 void mica_align_params_default(mica_align_params *p);
 
 /*

@@ -210,6 +210,37 @@ class FMIndex:
                               len(lens), cap, threads)
         return _take_result(_lib, h)
 
+    def align_best_stratum(self, batch, cap: int = 0, threads: int = 0) -> Result:
+        """Best-stratum reporting: of each read's hits (all of them, from
+        :meth:`align` without a cap) only those with the read's smallest d;
+        total = their number; over the cap, the first `cap` in the order
+        (strand, SA row of the window's position), listed by (pos, strand, d)."""
+        full = self.align(batch, cap=0, threads=threads)
+        sa = self.sa().astype(np.int64)
+        isa = np.empty_like(sa)
+        isa[sa] = np.arange(sa.size)
+        n = len(full.total)
+        total = np.zeros(n, dtype=np.uint64)
+        lists = []
+        for i in range(n):
+            h = full.as_tuples(i)
+            if h:
+                dmin = min(d for _, _, d in h)
+                h = [x for x in h if x[2] == dmin]
+            total[i] = len(h)
+            if cap and len(h) > cap:
+                h = sorted(sorted(h, key=lambda x: (x[1], int(isa[x[0]])))[:cap])
+            lists.append(h)
+        offsets = np.zeros(n + 1, dtype=np.uint64)
+        offsets[1:] = np.cumsum([len(x) for x in lists])
+        hits = np.zeros(int(offsets[-1]), dtype=HIT_DTYPE)
+        j = 0
+        for h in lists:
+            for (p, st, d) in h:
+                hits[j] = (p, st, d, 0)
+                j += 1
+        return Result(total, offsets, hits, full.nodes)
+
 
 def _batch_arrays(batch):
     words = np.ascontiguousarray(batch.words, dtype=np.uint32)

@@ -31,6 +31,7 @@ MICA_EBUSY = -7
 MICA_ENOTFOUND = -8
 MAX_READ_LEN = 256
 KERNELS = {"persistent": 0, "plain": 1, "plain_by_length": 2}
+REPORTS = {"all": 0, "best_stratum": 1}
 
 HIT_DTYPE = np.dtype([("pos", "<u4"), ("strand", "u1"), ("mm", "u1"), ("pad", "<u2")])
 
@@ -47,7 +48,7 @@ class IndexParams(ctypes.Structure):
 
 class AlignParams(ctypes.Structure):
     _fields_ = [("hit_cap", ctypes.c_uint32), ("kernel", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
-                ("prune", ctypes.c_uint32)]
+                ("prune", ctypes.c_uint32), ("report", ctypes.c_uint32)]
 
 
 class _Result(ctypes.Structure):
@@ -336,19 +337,20 @@ class Index:
         return s.as_dict()
 
     @staticmethod
-    def _params(hit_cap, kernel, stream, prune=True):
+    def _params(hit_cap, kernel, stream, prune=True, report="all"):
         return AlignParams(hit_cap, KERNELS[kernel] if isinstance(kernel, str) else int(kernel),
-                           _stream_handle(stream), int(bool(prune)))
+                           _stream_handle(stream), int(bool(prune)),
+                           REPORTS[report] if isinstance(report, str) else int(report))
 
     def align(self, words, word_off, lengths, k, hit_cap: int = 1000, kernel="persistent",
-              stream=None, prune: bool = True) -> Result:
+              stream=None, prune: bool = True, report="all") -> Result:
         """mica_align_batch on host arrays (copies in, searches, copies out)."""
         words = np.ascontiguousarray(words, dtype=np.uint32)
         word_off = np.ascontiguousarray(word_off, dtype=np.uint64)
         lengths = np.ascontiguousarray(lengths, dtype=np.uint16)
         k = np.ascontiguousarray(k, dtype=np.uint8)
         n = lengths.size
-        p = self._params(hit_cap, kernel, stream, prune)
+        p = self._params(hit_cap, kernel, stream, prune, report)
         out = ctypes.POINTER(_Result)()
         _check(_lib.mica_align_batch(self._h, _ptr(words) if words.size else None, _ptr(word_off),
                                      _ptr(lengths) if n else None, _ptr(k) if n else None, n,
@@ -360,10 +362,10 @@ class Index:
         return self.align(batch.words, batch.word_off, batch.lengths, batch.k, **kw)
 
     def align_device(self, d_words, d_word_off, d_lengths, d_k, n_reads: int, hit_cap: int = 1000,
-                     kernel="persistent", stream=None, prune: bool = True) -> DeviceResult:
+                     kernel="persistent", stream=None, prune: bool = True, report="all") -> DeviceResult:
         """mica_align_device on device pointers (ints) or torch CUDA tensors."""
         ptr = lambda x: x if isinstance(x, int) else x.data_ptr()
-        p = self._params(hit_cap, kernel, stream, prune)
+        p = self._params(hit_cap, kernel, stream, prune, report)
         r = _DeviceResult()
         _check(_lib.mica_align_device(self._h, ctypes.c_void_p(ptr(d_words)), ctypes.c_void_p(ptr(d_word_off)),
                                       ctypes.c_void_p(ptr(d_lengths)), ctypes.c_void_p(ptr(d_k)), n_reads,

@@ -183,14 +183,16 @@ static int align_graph(const mica_index *idx, Workspace &w, mica_stats &st, cons
                                (uint64_t)w.lb.p, (uint64_t)w.iv_sorted.p, (uint64_t)w.iv_off.p,
                                (uint64_t)w.total.p, (uint64_t)w.keep.p, (uint64_t)w.hit_off.p, (uint64_t)w.hits.p,
                                (uint64_t)w.big.p, (uint64_t)w.scan_tmp.p, w.hit_capacity, (uint64_t)w.iv_cap,
-                               (uint64_t)w.spill_cap, (uint64_t)w.spill_seq.p, (uint64_t)w.deep.p};
+                               (uint64_t)w.spill_cap, (uint64_t)w.spill_seq.p, (uint64_t)w.deep.p,
+                               (uint64_t)p.report};
     if (!w.gexec || memcmp(key, w.gkey, sizeof(key)) != 0) {
         if (w.gexec) { cudaGraphExecDestroy(w.gexec); w.gexec = nullptr; }
         uint64_t L = 0;
         MICA_CUDA_TRY(cudaStreamBeginCapture(w.gstream, cudaStreamCaptureModeThreadLocal));
         int crc = enqueue_persistent(idx, w, rd, shape, grid, (const SearchCtl *)w.pin_tmpl, prune, prefetch,
                                      w.gstream, L);
-        if (!crc) crc = enqueue_post_device(idx, w, rd, p.hit_cap, w.hit_capacity, w.gstream, w.pin_status, L);
+        if (!crc) crc = enqueue_post_device(idx, w, rd, p.hit_cap, p.report, w.hit_capacity, w.gstream,
+                                            w.pin_status, L);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(w.gstream, &g);
         if (crc || e != cudaSuccess) {
@@ -282,7 +284,7 @@ int align_on_device(const mica_index *idx, Workspace &w, mica_stats &st, const R
     int rc = run_search(idx, w, st, rd, cfg, s);
     if (rc) return rc;
     MICA_CUDA_TRY(cudaEventRecord(w.ev[1], s));
-    if ((rc = run_post(idx, w, st, rd, p.hit_cap, s, nh))) return rc;
+    if ((rc = run_post(idx, w, st, rd, p.hit_cap, p.report, s, nh))) return rc;
     MICA_CUDA_TRY(cudaEventRecord(w.ev[2], s));
     MICA_CUDA_TRY(cudaEventSynchronize(w.ev[2]));
     st.search_ms = elapsed_ms(w.ev[0], w.ev[1]);
@@ -326,6 +328,7 @@ void mica_align_params_default(mica_align_params *p)
     p->kernel = MICA_KERNEL_PERSISTENT;
     p->cuda_stream = nullptr;
     p->prune = 1;
+    p->report = MICA_REPORT_ALL;
 }
 
 int mica_index_build_resident(const uint8_t *genome_acgt, uint64_t len, const mica_index_params *params,
@@ -619,6 +622,7 @@ int mica_align_device(mica_index *idx, const uint32_t *d_packed_reads, const uin
     mica_align_params_default(&p);
     if (params) p = *params;
     if (p.kernel < MICA_KERNEL_PERSISTENT || p.kernel > MICA_KERNEL_PLAIN_BY_LENGTH) return MICA_EINVAL;
+    if (p.report > MICA_REPORT_BEST_STRATUM) return MICA_EINVAL;
     DeviceGuard g(idx->device);
     MICA_CUDA_TRY(cudaSetDevice(idx->device));
     cudaStream_t s = (cudaStream_t)p.cuda_stream;
@@ -647,6 +651,7 @@ int mica_align_batch(mica_index *idx, const uint32_t *packed_reads, const uint64
     mica_align_params_default(&p);
     if (params) p = *params;
     if (p.kernel < MICA_KERNEL_PERSISTENT || p.kernel > MICA_KERNEL_PLAIN_BY_LENGTH) return MICA_EINVAL;
+    if (p.report > MICA_REPORT_BEST_STRATUM) return MICA_EINVAL;
     DeviceGuard g(idx->device);
     MICA_CUDA_TRY(cudaSetDevice(idx->device));
     cudaStream_t s = (cudaStream_t)p.cuda_stream;

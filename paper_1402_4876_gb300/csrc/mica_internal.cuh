@@ -152,7 +152,7 @@ struct DeviceGuard {
     ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
 };
 
-constexpr int GRAPH_KEY = 26;   // words identifying a captured batch shape
+constexpr int GRAPH_KEY = 27;   // words identifying a captured batch shape
 
 // Per-index workspace reused across align calls.
 struct Workspace {
@@ -266,7 +266,7 @@ int search_shape_info(int shape, int *scap, int *warps, int *minb);
 
 // post.cu
 int run_post(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd, uint32_t hit_cap,
-             cudaStream_t s, uint64_t *n_hits_out);
+             uint32_t report, cudaStream_t s, uint64_t *n_hits_out);
 // capi.cu: the whole path on one workspace (validation of device batches included)
 int align_on_device(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd,
                     const mica_align_params &p, cudaStream_t s, uint64_t *nh, bool allow_graph = true);
@@ -276,7 +276,8 @@ int validate_host_batch(const mica_index *idx, const uint64_t *off, const uint16
                         uint64_t n);
 void free_workspace(Workspace &w);
 int enqueue_post_device(const mica_index *idx, Workspace &w, const ReadsView &rd, uint32_t hit_cap,
-                        uint64_t hit_capacity, cudaStream_t s, void *status, uint64_t &launches);
+                        uint32_t report, uint64_t hit_capacity, cudaStream_t s, void *status,
+                        uint64_t &launches);
 int reserve_post(Workspace &w, uint64_t n, uint32_t iv_cap, uint64_t hit_capacity);
 int exclusive_scan_u64_scratch(const uint64_t *in, uint64_t n, uint64_t *out, unsigned long long *scratch,
                                cudaStream_t s);

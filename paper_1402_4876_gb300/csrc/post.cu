@@ -144,6 +144,22 @@ __device__ __forceinline__ uint64_t iv_key(const Interval &x)
     return ((uint64_t)(x.meta & 3u) << 33) | ((uint64_t)((x.meta >> 2) & 1u) << 32) | x.l;
 }
 
+// Best-stratum reporting: a read keeps only its intervals with the smallest
+// d; the others become empty (r = l) and so count and list nothing.
+__global__ void k_stratum(Interval *__restrict__ ivs, const uint64_t *__restrict__ iv_off, uint64_t n,
+                          const unsigned int *__restrict__ err)
+{
+    if (*err) return;
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n;
+         r += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t b = iv_off[r], e = iv_off[r + 1];
+        uint32_t dmin = 3;
+        for (uint64_t i = b; i < e; i++) dmin = min(dmin, ivs[i].meta & 3u);
+        for (uint64_t i = b; i < e; i++)
+            if ((ivs[i].meta & 3u) > dmin) ivs[i].r = ivs[i].l;
+    }
+}
+
 // Per read: total = the sum of its interval sizes (exact) and keep = the
 // rows it lists, min(total, cap).  When total > cap the listed rows are the
 // first cap in the order (d, strand, SA row); k_expand takes rows from the
@@ -528,7 +544,7 @@ static PostLists post_lists(Workspace &w, uint64_t n)
 // Ends with a copy of the status (search control block, hit total, locate
 // steps and sort-list counts) into pinned host memory `status`.
 int enqueue_post_device(const mica_index *idx, Workspace &w, const ReadsView &rd, uint32_t hit_cap,
-                        uint64_t hit_capacity, cudaStream_t s, void *status, uint64_t &L)
+                        uint32_t report, uint64_t hit_capacity, cudaStream_t s, void *status, uint64_t &L)
 {
     uint64_t n = rd.n;
     uint64_t *iv_off = (uint64_t *)w.iv_off.p, *hit_off = (uint64_t *)w.hit_off.p;
@@ -542,6 +558,10 @@ int enqueue_post_device(const mica_index *idx, Workspace &w, const ReadsView &rd
     if ((rc = exclusive_scan<uint32_t>(w.scan_tmp, (const uint32_t *)w.iv_cnt.p, n, iv_off, s, L))) return rc;
     k_iv_scatter<<<G, 256, 0, s>>>((const Interval *)w.iv.p, &ctl->iv_count, w.iv_cap, iv_off,
                                    (uint32_t *)w.iv_cnt.p, (Interval *)w.iv_sorted.p, &ctl->error);
+    if (report == MICA_REPORT_BEST_STRATUM) {
+        k_stratum<<<grid1(n, 128), 128, 0, s>>>((Interval *)w.iv_sorted.p, iv_off, n, &ctl->error);
+        L++;
+    }
     k_summarize<<<grid1(n, 128), 128, 0, s>>>((Interval *)w.iv_sorted.p, iv_off, n, hit_cap, (uint64_t *)w.total.p,
                                               (uint64_t *)w.keep.p, pl.many, pl.n_many, &ctl->error);
     k_summarize_many<<<152 * 2, MANY_THREADS, 0, s>>>((Interval *)w.iv_sorted.p, iv_off, hit_cap,
@@ -579,7 +599,7 @@ int reserve_post(Workspace &w, uint64_t n, uint32_t iv_cap, uint64_t hit_capacit
 }
 
 int run_post(const mica_index *idx, Workspace &w, mica_stats &stt, const ReadsView &rd, uint32_t hit_cap,
-             cudaStream_t s, uint64_t *n_hits_out)
+             uint32_t report, cudaStream_t s, uint64_t *n_hits_out)
 {
     uint64_t n = rd.n;
     uint32_t niv = (uint32_t)stt.intervals;
@@ -600,6 +620,10 @@ int run_post(const mica_index *idx, Workspace &w, mica_stats &stt, const ReadsVi
     if (niv) { k_iv_scatter<<<grid1(niv), 256, 0, s>>>((const Interval *)w.iv.p, &((SearchCtl *)w.ctl.p)->iv_count,
                                                        w.iv_cap, iv_off, (uint32_t *)w.iv_cnt.p,
                                                        (Interval *)w.iv_sorted.p, err); L++; }
+    if (n && report == MICA_REPORT_BEST_STRATUM) {
+        k_stratum<<<grid1(n, 128), 128, 0, s>>>((Interval *)w.iv_sorted.p, iv_off, n, err);
+        L++;
+    }
     if (n) {
         k_summarize<<<grid1(n, 128), 128, 0, s>>>((Interval *)w.iv_sorted.p, iv_off, n, hit_cap,
                                                   (uint64_t *)w.total.p, (uint64_t *)w.keep.p, pl.many, pl.n_many,

@@ -69,3 +69,7 @@ def test_host_side_rejections_need_no_gpu():
     # pairing rejects an inverted insert window before touching a device
     assert lib.mica_pair_batch(0, None, None, None, 1, 700, 300, None) == mica.MICA_EINVAL
     assert lib.mica_pair_device(None, None, None, 1, 700, 300, None, None) == mica.MICA_EINVAL
+    # defaults: pruning on, every placement reported
+    p = mica.AlignParams()
+    lib.mica_align_params_default(ctypes.byref(p))
+    assert p.report == 0 and p.prune == 1

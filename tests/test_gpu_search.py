@@ -310,3 +310,30 @@ def test_graph_replay_and_fallback():
                            h.cpu().numpy().view(m.HIT_DTYPE))
     gc.assert_same(got, oracle.FMIndex(tg).align(reads, cap=0), "fallback")
     tidx.free()
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_best_stratum_reporting(kernel):
+    """MICA_REPORT_BEST_STRATUM = the oracle's best-stratum result: on the
+    uneven 64 Mbp sample (k 0..3; caps 1000 and 3) and on the diverged
+    (AC)^n fixture whose reads have thousands of intervals (caps 0, 1, 7)."""
+    g = gc.genome("64m")
+    b = synth.reads_uneven(g, n=200_000).subset(np.arange(0, 200_000, 200))     # 1,000 reads
+    fm = gc.oracle_index("64m")
+    idx = gc.gpu_index("64m")
+    for cap in (1000, 3):
+        got = idx.align_batch(b, hit_cap=cap, kernel=kernel, report="best_stratum")
+        gc.assert_same(got, fm.align_best_stratum(b, cap=cap), f"64m cap={cap}")
+    rng = np.random.default_rng(7)
+    core = np.resize(np.array([0, 1], np.uint8), 40_000)
+    mut = rng.random(core.size) < 0.04
+    core[mut] = (core[mut] + rng.integers(1, 4, size=int(mut.sum()))) & 3
+    tg = np.concatenate([rng.integers(0, 4, 20_000).astype(np.uint8), core])
+    reads = [tg[20_000 + i * 1_999: 20_000 + i * 1_999 + 40].copy() for i in range(12)]
+    tb = gc.batch_from_reads(reads, [2] * 8 + [3] * 4)
+    tfm = oracle.FMIndex(tg)
+    tidx = gc.mica().Index.build(synth.to_acgt_bytes(tg), kmer_q=10, sa_sample=8)
+    for cap in (0, 1, 7):
+        got = tidx.align_batch(tb, hit_cap=cap, kernel=kernel, report="best_stratum")
+        gc.assert_same(got, tfm.align_best_stratum(tb, cap=cap), f"tandem cap={cap}")
+    tidx.free()

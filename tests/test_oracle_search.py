@@ -201,3 +201,58 @@ def test_cap_order_by_suffix_comparison():
     plus = sorted((p for p, s, d in allh if s == 0), key=tail)
     assert sorted(kept) == sorted(plus[:10])
     assert int(res.total[0]) == len(allh)
+
+
+@pytest.mark.parametrize("kind", ["random", "tandem"])
+def test_best_stratum_against_numpy_scan(kind):
+    """Best-stratum reporting = the Hamming hits with the read's smallest d
+    (numpy scan filtered by its definition)."""
+    rng = np.random.default_rng({"random": 21, "tandem": 22}[kind])
+    if kind == "random":
+        g = rng.integers(0, 4, 3000).astype(np.uint8)
+    else:
+        g = np.resize(np.array([0, 3, 3, 1, 0], np.uint8), 1500)
+        g[rng.choice(1500, 20, replace=False)] = rng.integers(0, 4, 20)
+    fm = oracle.FMIndex(g)
+    reads, b = _tiny_batches(g, rng)
+    res = fm.align_best_stratum(b)
+    for i, r in enumerate(reads):
+        allh = refcheck.hamming_hits(g, r, int(b.k[i]))
+        if allh:
+            dmin = min(d for _, _, d in allh)
+            allh = [h for h in allh if h[2] == dmin]
+        assert _set(res, i) == allh
+        assert int(res.total[i]) == len(allh)
+
+
+def test_best_stratum_cap_order_by_suffix_comparison():
+    """Over the cap, best-stratum keeps the first rows by (strand, suffix)."""
+    g = synth.repeat_genome(6_000, 11, copy_frac=0.0, tandem_frac=0.3,
+                            unit_len=(2, 4), array_len=(300, 1000)).codes
+    fm = oracle.FMIndex(g, "sort")
+    rng = np.random.default_rng(13)
+    reads = []
+    for _ in range(40):
+        p = int(rng.integers(0, len(g) - 16))
+        reads.append(g[p:p + 16].copy())
+    words, off, lens = synth.pack_reads(reads)
+    b = synth.ReadBatch(words, off, lens, rng.integers(0, 3, 40).astype(np.uint8),
+                        np.zeros(40, np.int64), np.zeros(40, np.uint8), np.zeros(40, np.int32))
+    cap = 7
+    full, capped = fm.align_best_stratum(b), fm.align_best_stratum(b, cap=cap)
+    t = (g + 1).tobytes() + b"\x00"
+    order = sorted(range(len(t)), key=lambda i: t[i:])
+    suffix_rank = np.empty(len(t), np.int64)
+    suffix_rank[order] = np.arange(len(t))
+    n_capped = 0
+    for i in range(b.n):
+        allh, kept = _set(full, i), _set(capped, i)
+        assert int(capped.total[i]) == int(full.total[i]) == len(allh)
+        assert len({d for _, _, d in allh}) <= 1
+        assert len(kept) == min(cap, len(allh)) and set(kept) <= set(allh)
+        if len(allh) > cap:
+            n_capped += 1
+            key = lambda h: (h[1], suffix_rank[h[0]])
+            dropped = set(allh) - set(kept)
+            assert max(key(h) for h in kept) < min(key(h) for h in dropped)
+    assert n_capped > 5
