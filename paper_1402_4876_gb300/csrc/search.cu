@@ -385,9 +385,10 @@ __global__ void k_ring_init(uint32_t *seq, uint32_t cap)
 // --------------------------------------------------------------------------
 
 constexpr uint32_t ADMIT_LOW = 64;          // admit tasks when pending work < this
-constexpr int ADMIT_MIN_FREE = 8;            // ... and, while holding work, >= this many slots are free
-                                             // (an admission costs a few memory round trips whatever
-                                             // it takes, so it should fill several slots)
+// ... and, while holding work, once at least PersistArgs::admit_min_free slots
+// are free: an admission costs a few memory round trips whatever it takes, so
+// it should fill several slots -- 8, or 16 when the index lives in HBM and
+// the round trips are longer (measured faster on each genome)
 constexpr uint32_t IDLE_LIMIT = 1u << 22;    // idle rounds (>= 1 us each) before timing out
 constexpr uint32_t SPIN_LIMIT = 1u << 24;    // waits on one ring slot (64-128 ns each: ~1-2 s)
 constexpr uint32_t RESERVE_LIMIT = 1u << 20; // spill reservation attempts (lost races back off)
@@ -395,7 +396,7 @@ constexpr uint32_t FULL_WAITS = 1024;        // waits on a full ring before a ro
 constexpr uint32_t DONATE_TRIES = 8;         // reservation attempts of a donation under contention
 constexpr uint32_t DEEP_CAP = 8192;          // entries of each per-warp overflow stack
 constexpr uint32_t DONATE_MIN = 96;          // stack depth that makes a warp share work
-constexpr uint32_t DONATE_N = 64;
+constexpr uint32_t DONATE_N = 128;
 constexpr int DEFAULT_SHAPE = 0;   // 256-node stacks, 8 warps, 3 CTAs per SM: fastest measured
                                    // on both the 64 Mbp and the 3.1 Gbp genome
 
@@ -413,6 +414,7 @@ struct PersistArgs {
     uint2 *deep_s;                  //   and single-row nodes, DEEP_CAP entries per warp each
     int total_warps;
     bool prefetch;                  // warm the next round's occurrence blocks in L2
+    int admit_min_free;             // free slots that make a warp holding work admit more
     const unsigned long long *lb;   // optional: lower-bound breakpoints per (read, strand)
 };
 
@@ -739,7 +741,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
         // are not hammered and each admission fills several slots)
         if (freem != 0 && cnt + seeds_total + dmt + dst < ADMIT_LOW &&
             (cnt + seeds_total == 0 ||
-             ((iter & 3) == 0 && (__popc(freem) >= ADMIT_MIN_FREE || cnt + seeds_total < ADMIT_LOW / 4)))) {
+             ((iter & 3) == 0 && (__popc(freem) >= a.admit_min_free || cnt + seeds_total < ADMIT_LOW / 4)))) {
             bool idle = (cnt + seeds_total == 0) && used == 0;
             // an idle warp first peeks without atomics
             if (idle && !busy) {
@@ -1200,6 +1202,13 @@ int search_shape_info(int shape, int *scap, int *warps, int *minb)
     return 0;
 }
 
+// Admission threshold (see k_persistent): 16 free slots when the occurrence
+// blocks do not stay in L2 (over 96 MiB), else 8.
+static int admit_min_free_for(const mica_index *idx)
+{
+    return idx->n_occ_blocks * 32 > (96ull << 20) ? 16 : 8;
+}
+
 // Spill ring capacity for a batch of n reads: a power of two >= max(n, 2^20).
 static uint32_t ring_capacity(uint64_t n)
 {
@@ -1304,6 +1313,7 @@ int enqueue_persistent(const mica_index *idx, Workspace &w, const ReadsView &rd,
     pa.lb = prune ? (const unsigned long long *)w.lb.p : nullptr;
     pa.seq = (uint32_t *)w.spill_seq.p;
     pa.prefetch = prefetch;
+    pa.admit_min_free = admit_min_free_for(idx);
     deep_ptrs(w, pa.total_warps, pa.deep_m, pa.deep_s);
     if (rd.n) {
         if (int rc = launch_ring_init(w, s)) return rc;
@@ -1361,6 +1371,7 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
                 if ((rc = reserve_deep(w, pa.total_warps))) return rc;
                 deep_ptrs(w, pa.total_warps, pa.deep_m, pa.deep_s);
                 pa.prefetch = cfg.prefetch;
+                pa.admit_min_free = admit_min_free_for(idx);
                 pa.lb = d_lb;
                 if ((rc = dev_reserve(w.spill_seq, (size_t)w.spill_cap * 4))) return rc;
                 pa.seq = (uint32_t *)w.spill_seq.p;
