@@ -66,3 +66,30 @@ def test_human_properties_and_kernels_agree(human):
     sub = b.subset(np.arange(0, 4_000))
     gc.assert_same(idx.align_batch(sub, hit_cap=1000, kernel="plain"),
                    idx.align_batch(sub, hit_cap=1000, kernel="persistent"), "plain vs persistent")
+
+
+def test_human_serving_alone_equals_mix(human):
+    """Serving on the resident 3.1 Gbp index (the serving workload's index):
+    requests of mixed sizes, lengths and budgets submitted concurrently share
+    ticks, and each result is bit-identical to the same request aligned
+    alone; the alone results are pinned above (brute force and properties)."""
+    import threading
+    g, b, idx = human
+    donor = synth.donor_of(g)
+    reqs = synth.serve_requests(donor, 9, seed=47, size_range=(200, 6_000))
+    alone = [idx.align_batch(r, hit_cap=1000) for r in reqs]
+    ids = [None] * len(reqs)
+    with gc.mica().Server(idx, hit_cap=1000, workers=2, max_tick_reads=8_000) as srv:
+        def client(j0):
+            for j in range(j0, len(reqs), 3):
+                ids[j] = srv.submit_batch(reqs[j])
+        th = [threading.Thread(target=client, args=(j,)) for j in range(3)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        for j, rid in enumerate(ids):
+            got, lat = srv.wait(rid)
+            gc.assert_same(got, alone[j], f"request {j}")
+        assert srv.stats()["ticks"] >= 1
+    assert sum(int(r.offsets[-1]) for r in alone) > 0
