@@ -265,7 +265,8 @@ int align_on_device(const mica_index *idx, Workspace &w, mica_stats &st, const R
     uint64_t launches = st.launches;   // the batch check already counted
     st = mica_stats{};
     st.launches = launches;
-    if (allow_graph && p.kernel == MICA_KERNEL_PERSISTENT && rd.n > 0) {
+    const bool deepen = p.report == MICA_REPORT_BEST_STRATUM && p.kernel == MICA_KERNEL_PERSISTENT && rd.n > 0;
+    if (allow_graph && !deepen && p.kernel == MICA_KERNEL_PERSISTENT && rd.n > 0) {
         bool done = false;
         if (int rc = align_graph(idx, w, st, rd, p, s, nh, done)) return rc;
         if (done) return 0;
@@ -281,7 +282,11 @@ int align_on_device(const mica_index *idx, Workspace &w, mica_stats &st, const R
     cfg.prefetch = use_prefetch(idx);
     for (uint32_t c = 0; c < LEN_CLASSES; c++)
         cfg.plain_block_len[c] = idx->tuning.plain_block_len[c] ? (int)idx->tuning.plain_block_len[c] : cfg.plain_block;
-    int rc = run_search(idx, w, st, rd, cfg, s);
+    int rc = deepen ? run_search_stratum(idx, w, st, rd, cfg, s) : run_search(idx, w, st, rd, cfg, s);
+    if (rc == STRATUM_FALLBACK) {
+        w.spill_dirty = true;
+        rc = run_search(idx, w, st, rd, cfg, s);   // exhaustive search, filtered after
+    }
     if (rc) return rc;
     MICA_CUDA_TRY(cudaEventRecord(w.ev[1], s));
     if ((rc = run_post(idx, w, st, rd, p.hit_cap, p.report, s, nh))) return rc;

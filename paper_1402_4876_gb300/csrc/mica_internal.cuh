@@ -259,6 +259,9 @@ int prepare_persistent(const mica_index *idx, Workspace &w, uint64_t n, int shap
                        int &grid, int &shape);
 int debug_lower_bounds(const mica_index *idx, Workspace &w, const ReadsView &rd, unsigned long long *d_out,
                        cudaStream_t s);
+constexpr int STRATUM_FALLBACK = 1;   // run_search_stratum: rerun as an exhaustive search
+int run_search_stratum(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd,
+                       const SearchConfig &cfg, cudaStream_t s);
 int enqueue_persistent(const mica_index *idx, Workspace &w, const ReadsView &rd, int shape, int grid,
                        const SearchCtl *pinned_tmpl, bool prune, bool prefetch, cudaStream_t s,
                        uint64_t &launches);

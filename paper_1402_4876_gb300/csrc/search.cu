@@ -373,6 +373,33 @@ __global__ void k_len_scatter(ReadsView rd, const unsigned int *base, unsigned i
     }
 }
 
+// Best-stratum deepening: pass j searches the reads of `list` with budget
+// min(k, j) (written into k_pass); the reads that found nothing and allow
+// more mismatches form the next pass's list.
+__global__ void k_stratum_pass(const uint32_t *__restrict__ list, uint32_t n_list, const uint8_t *__restrict__ k,
+                               uint32_t j, uint8_t *__restrict__ k_pass)
+{
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n_list; t += gridDim.x * blockDim.x) {
+        uint32_t r = list[t];
+        k_pass[r] = (uint8_t)min((uint32_t)k[r], j);
+    }
+}
+
+__global__ void k_stratum_next(const uint32_t *__restrict__ list, uint32_t n_list,
+                               const uint32_t *__restrict__ iv_cnt, const uint8_t *__restrict__ k, uint32_t j,
+                               uint32_t *__restrict__ next, unsigned int *__restrict__ n_next)
+{
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n_list; t += gridDim.x * blockDim.x) {
+        uint32_t r = list[t];
+        if (iv_cnt[r] == 0 && k[r] > j) next[atomicAdd(n_next, 1u)] = r;
+    }
+}
+
+__global__ void k_iota(uint32_t *list, uint32_t n)
+{
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) list[t] = t;
+}
+
 // The spill ring's sequence words for a fresh launch: slot i expects
 // position i.
 __global__ void k_ring_init(uint32_t *seq, uint32_t cap)
@@ -1500,6 +1527,132 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
         return 0;
     }
     return MICA_EINTERNAL;
+}
+
+// Best-stratum search by iterative deepening (persistent kernel): pass j =
+// 0, 1, ... searches, with budget min(k, j), only the reads that found
+// nothing at a smaller budget; a read's first pass with hits finds exactly
+// its best stratum (every hit of that pass has d = j), so the result equals
+// the exhaustive search filtered to the best stratum, with less work.  The
+// intervals of all passes accumulate in one buffer.  Returns
+// STRATUM_FALLBACK when a pass overflows a buffer: the caller then runs the
+// exhaustive search with the stratum filter.
+int run_search_stratum(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd,
+                       const SearchConfig &cfg, cudaStream_t s)
+{
+    const uint64_t n = rd.n;
+    int rc;
+    if (n == 0 || n >= (1ull << 31)) return STRATUM_FALLBACK;
+    if ((rc = dev_reserve(w.ctl, sizeof(SearchCtl) + 64))) return rc;
+    if ((rc = dev_reserve(w.iv_cnt, n * 4))) return rc;
+    w.iv_cap = (uint32_t)std::max<uint64_t>(w.iv_cap, std::min<uint64_t>(4 * n + 65536, 1ull << 30));
+    if (w.spill_cap == 0) w.spill_cap = ring_capacity(n);
+    if ((rc = dev_reserve(w.iv, (size_t)w.iv_cap * sizeof(Interval))) ||
+        (rc = dev_reserve(w.spill, (size_t)w.spill_cap * sizeof(WorkItem))) ||
+        (rc = dev_reserve(w.spill_seq, (size_t)w.spill_cap * 4)) ||
+        (rc = dev_reserve(w.lb, 2 * n * 8)) ||
+        (rc = dev_reserve(w.lenlist, 2 * n * 4 + n + 64)))
+        return rc;
+    uint32_t *lists[2] = {(uint32_t *)w.lenlist.p, (uint32_t *)w.lenlist.p + n};
+    uint8_t *k_pass = (uint8_t *)((uint32_t *)w.lenlist.p + 2 * n);
+    unsigned int *d_next = (unsigned int *)((char *)w.lenlist.p + ((2 * n * 4 + n + 15) & ~15ull));
+    SearchCtl *d_ctl = (SearchCtl *)w.ctl.p;
+    const int shape = (cfg.shape >= 0 && cfg.shape < N_SHAPES) ? cfg.shape : DEFAULT_SHAPE;
+    int bps = 0;
+    if ((rc = persistent_grid(idx->device, shape, bps))) return rc;
+    const PersistShape &sh = g_shapes[shape];
+    const int grid = g_num_sms * bps;
+    if ((rc = reserve_deep(w, grid * sh.warps))) return rc;
+    const unsigned g1 = (unsigned)std::min<uint64_t>((n + 255) / 256, 152ull * 16);
+
+    MICA_CUDA_TRY(cudaMemsetAsync(w.iv_cnt.p, 0, n * 4, s));
+    k_iota<<<g1, 256, 0, s>>>(lists[0], (uint32_t)n);
+    MICA_CUDA_TRY(record_event(w.kev[0], s));
+    st.launches++;
+    {   // pass 0's control block, then the lower bounds (their counters land in
+        // it) with the reads' own budgets: valid for every smaller budget
+        SearchCtl h{};
+        h.ntasks = 2ull * n;
+        h.spill_cap = w.spill_cap;
+        h.iv_cap = w.iv_cap;
+        MICA_CUDA_TRY(cudaMemcpyAsync(d_ctl, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+        if (cfg.prune) {
+            if ((rc = launch_lower_bounds(idx, w, rd, d_ctl, s))) return rc;
+            st.launches++;
+        }
+    }
+    ReadsView rp = rd;
+    rp.k = k_pass;
+    uint32_t n_list = (uint32_t)n, iv_base = 0, cur = 0;
+    SearchCtl total{};
+    for (uint32_t j = 0; j <= MICA_MAX_K && n_list > 0; j++) {
+        k_stratum_pass<<<g1, 256, 0, s>>>(lists[cur], n_list, rd.k, j, k_pass);
+        if (j > 0) {
+            SearchCtl h{};
+            h.ntasks = 2ull * n_list;
+            h.spill_cap = w.spill_cap;
+            h.iv_cap = w.iv_cap;
+            h.iv_count = iv_base;
+            MICA_CUDA_TRY(cudaMemcpyAsync(d_ctl, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+        }
+        if ((rc = launch_ring_init(w, s))) return rc;
+        PersistArgs pa;
+        pa.ix = idx->view; pa.rd = rp; pa.read_list = lists[cur]; pa.ntasks = 2ull * n_list;
+        pa.ctl = d_ctl; pa.iv = (Interval *)w.iv.p; pa.iv_cnt = (uint32_t *)w.iv_cnt.p;
+        pa.spill = (WorkItem *)w.spill.p;
+        pa.seq = (uint32_t *)w.spill_seq.p;
+        pa.total_warps = grid * sh.warps;
+        deep_ptrs(w, pa.total_warps, pa.deep_m, pa.deep_s);
+        pa.prefetch = cfg.prefetch;
+        pa.admit_min_free = admit_min_free_for(idx);
+        pa.lb = cfg.prune ? (const unsigned long long *)w.lb.p : nullptr;
+        sh.fn<<<grid, sh.warps * 32, sh.smem, s>>>(pa);
+        MICA_CUDA_TRY(cudaGetLastError());
+        MICA_CUDA_TRY(cudaMemsetAsync(d_next, 0, 4, s));
+        k_stratum_next<<<g1, 256, 0, s>>>(lists[cur], n_list, (const uint32_t *)w.iv_cnt.p, rd.k, j,
+                                          lists[cur ^ 1], d_next);
+        st.launches += 4;
+        SearchCtl out;
+        unsigned int nn = 0;
+        MICA_CUDA_TRY(cudaMemcpyAsync(&out, d_ctl, sizeof(out), cudaMemcpyDeviceToHost, s));
+        MICA_CUDA_TRY(cudaMemcpyAsync(&nn, d_next, 4, cudaMemcpyDeviceToHost, s));
+        MICA_CUDA_TRY(cudaStreamSynchronize(s));
+        if (out.error & ERR_TIMEOUT) return MICA_ETIMEOUT;
+        if (out.error) return STRATUM_FALLBACK;
+        iv_base = out.iv_count;
+        total.seeds += out.seeds; total.nodes += out.nodes; total.rank_blocks += out.rank_blocks;
+        total.spills += out.spills; total.rounds += out.rounds; total.lane_ops += out.lane_ops;
+        for (int q = 0; q < 3; q++) total.rounds_kind[q] += out.rounds_kind[q];
+        total.wait_queue_ns += out.wait_queue_ns; total.wait_idle_ns += out.wait_idle_ns;
+        total.deep_moves += out.deep_moves;
+        if (j == 0) { total.lb_steps = out.lb_steps; total.lb_dead = out.lb_dead; }
+        n_list = nn;
+        cur ^= 1;
+    }
+    MICA_CUDA_TRY(record_event(w.kev[1], s));
+    // the post kernels read the interval count from the control block
+    SearchCtl fin{};
+    fin.iv_count = iv_base;
+    fin.iv_cap = w.iv_cap;
+    MICA_CUDA_TRY(cudaMemcpyAsync(d_ctl, &fin, sizeof(fin), cudaMemcpyHostToDevice, s));
+    MICA_CUDA_TRY(cudaStreamSynchronize(s));
+    st.tasks = 2 * n;
+    st.seeds = total.seeds;
+    st.nodes = total.nodes;
+    st.rank_blocks = total.rank_blocks;
+    st.intervals = iv_base;
+    st.spills = total.spills;
+    st.warp_rounds = total.rounds;
+    st.lane_ops = total.lane_ops;
+    st.rounds_multi = total.rounds_kind[0];
+    st.rounds_single = total.rounds_kind[1];
+    st.rounds_seed = total.rounds_kind[2];
+    st.lb_steps = total.lb_steps;
+    st.lb_dead_tasks = total.lb_dead;
+    st.queue_wait_ns = total.wait_queue_ns;
+    st.idle_wait_ns = total.wait_idle_ns;
+    st.overflow_moves = total.deep_moves;
+    return 0;
 }
 
 }  // namespace mica
