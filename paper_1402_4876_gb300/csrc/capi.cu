@@ -167,10 +167,6 @@ static int align_graph(const mica_index *idx, Workspace &w, mica_stats &st, cons
     if ((rc = prepare_persistent(idx, w, n, idx->tuning.shape, tmpl, grid, shape))) return rc;
     w.hit_capacity = std::max<uint64_t>(w.hit_capacity, 4 * n + 65536);
     if ((rc = reserve_post(w, n, w.iv_cap, w.hit_capacity))) return rc;
-    if (w.spill_dirty) {
-        MICA_CUDA_TRY(cudaMemsetAsync(w.spill.p, 0, (size_t)w.spill_cap * sizeof(WorkItem), s));
-        w.spill_dirty = false;
-    }
     memcpy(w.pin_tmpl, &tmpl, sizeof(tmpl));
     const bool prune = p.prune && idx->has_rev;
     const bool prefetch = use_prefetch(idx);
@@ -219,10 +215,9 @@ static int align_graph(const mica_index *idx, Workspace &w, mica_stats &st, cons
     memcpy(&nhits, stp, 8);
     memcpy(&steps, stp + 8, 8);
     memcpy(cnts, stp + 16, 8);
-    if (out.error & ERR_TIMEOUT) { w.spill_dirty = true; return MICA_ETIMEOUT; }
+    if (out.error & ERR_TIMEOUT) return MICA_ETIMEOUT;
     if (out.error) {
         // let the regular path grow the buffers and recompute
-        w.spill_dirty = true;
         return 0;
     }
     if (nhits > w.hit_capacity) { w.hit_capacity = 2 * nhits; return 0; }
@@ -284,7 +279,6 @@ int align_on_device(const mica_index *idx, Workspace &w, mica_stats &st, const R
         cfg.plain_block_len[c] = idx->tuning.plain_block_len[c] ? (int)idx->tuning.plain_block_len[c] : cfg.plain_block;
     int rc = deepen ? run_search_stratum(idx, w, st, rd, cfg, s) : run_search(idx, w, st, rd, cfg, s);
     if (rc == STRATUM_FALLBACK) {
-        w.spill_dirty = true;
         rc = run_search(idx, w, st, rd, cfg, s);   // exhaustive search, filtered after
     }
     if (rc) return rc;

@@ -165,7 +165,6 @@ struct Workspace {
     DevBuf lenlist;                                       // plain kernel: reads by length class
     uint32_t iv_cap = 0, spill_cap = 0;
     uint64_t hit_cap_total = 0;
-    bool spill_dirty = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // call timing
     cudaEvent_t kev[2] = {nullptr, nullptr};                      // search kernel timing
     // captured pipeline for a repeated batch shape (persistent kernel)

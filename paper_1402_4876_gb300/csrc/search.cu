@@ -1374,10 +1374,6 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
     for (int attempt = 0; attempt < 8; attempt++) {
         if ((rc = dev_reserve(w.iv, (size_t)w.iv_cap * sizeof(Interval)))) return rc;
         if ((rc = dev_reserve(w.spill, (size_t)w.spill_cap * sizeof(WorkItem)))) return rc;
-        if (w.spill_dirty) {
-            MICA_CUDA_TRY(cudaMemsetAsync(w.spill.p, 0, (size_t)w.spill_cap * sizeof(WorkItem), s));
-            w.spill_dirty = false;
-        }
         SearchCtl h{};
         h.ntasks = 2 * n;
         h.spill_cap = w.spill_cap;
@@ -1475,8 +1471,6 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
                     MICA_CUDA_TRY(cudaMemcpyAsync(&err, &d_ctl->error, 4, cudaMemcpyDeviceToHost, s));
                     MICA_CUDA_TRY(cudaStreamSynchronize(s));
                     if (cnt == 0 || err) break;
-                    // the re-queue shares the persistent kernel's spill buffer: clear it before that kernel
-                    w.spill_dirty = true;
                     cnt = std::min(cnt, w.spill_cap);
                     pa.items = bufs[round & 1];
                     pa.requeue = bufs[(round + 1) & 1];
@@ -1493,7 +1487,7 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
         SearchCtl out;
         MICA_CUDA_TRY(cudaMemcpyAsync(&out, d_ctl, sizeof(out), cudaMemcpyDeviceToHost, s));
         MICA_CUDA_TRY(cudaStreamSynchronize(s));
-        if (out.error & ERR_TIMEOUT) { w.spill_dirty = true; return MICA_ETIMEOUT; }
+        if (out.error & ERR_TIMEOUT) return MICA_ETIMEOUT;
         if (out.error & (ERR_IV_OVERFLOW | ERR_SPILL_OVERFLOW)) {
             st.retries++;
             char msg[256];
@@ -1505,7 +1499,6 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
                 w.iv_cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(2ull * out.iv_count, 2ull * w.iv_cap), 0xfffffff0ull);
             if (out.error & ERR_SPILL_OVERFLOW)
                 w.spill_cap = (uint32_t)std::min<uint64_t>(4ull * w.spill_cap, 1ull << 30);
-            w.spill_dirty = true;
             continue;
         }
         st.tasks = 2 * n;
