@@ -462,7 +462,9 @@ oracle_result *oracle_bruteforce(const uint8_t *g, uint64_t n, const uint32_t *w
 #ifdef _OPENMP
     if (threads > 0) omp_set_num_threads(threads);
 #endif
-    #pragma omp parallel for schedule(dynamic, 4) reduction(|:fail)
+    /* one read per chunk: a scan of a large genome per read is long enough
+       that even a handful of reads should spread over every thread */
+    #pragma omp parallel for schedule(dynamic, 1) reduction(|:fail)
     for (uint64_t i = 0; i < n_reads; i++) {
         uint32_t m = lengths[i];
         int k = kk[i];
