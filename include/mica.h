@@ -348,6 +348,156 @@ int mica_pair_device(const uint64_t *d_offsets, const mica_hit *d_hits, const ui
 int mica_pair_batch(int device, const uint64_t *offsets, const mica_hit *hits, const uint16_t *lengths,
                     uint64_t n_pairs, uint32_t insert_min, uint32_t insert_max, mica_pair *out);
 
+/* ---- reference sequences: contigs, ambiguous bases (host-side) ----
+ *
+ * The paper aligns reads against a reference genome and hands the BWT
+ * phase's placements on to SAM-producing stages (Section 2); a real
+ * reference is a set of named contigs whose bytes may hold N or other IUPAC
+ * codes.  The index has one text over {A,C,G,T}, so a mica_reference maps the
+ * two onto each other, entirely on the host (no CUDA call):
+ *
+ *   - contig i (in input order) occupies [start_i, start_i + length_i) of the
+ *     concatenated text G, start_0 = 0, start_{i+1} = start_i + length_i;
+ *   - a byte other than A/C/G/T (either case) is ambiguous: in G it becomes
+ *     the base given by the top two bits of SplitMix64 (Steele, Lea and
+ *     Flood, 2014) of its coordinate in G, and it is recorded in a maximal
+ *     run [s, e) of ambiguous coordinates;
+ *   - a placement (p, strand, d) of a read of length m is a placement on the
+ *     reference when [p, p + m) lies inside one contig and holds no ambiguous
+ *     coordinate.  The others (windows across a contig boundary or over a
+ *     replaced base) exist only in G and are dropped by mica_reference_filter
+ *     and by the SAM writer.
+ *
+ * Feed mica_reference_text() to mica_index_build.  The text must stay below
+ * 2^32 - 1 bases (the index's limit); contigs are non-empty; names follow
+ * SAM's reference-name rule (printable, no whitespace, none of "'(),<>[\]`{},
+ * not starting with * or =) and are unique.  A mica_reference is read-only
+ * after creation and may be shared between threads.
+ */
+typedef struct mica_reference mica_reference;
+
+typedef struct {
+    uint64_t length;           /* bases of the concatenated text G */
+    uint64_t n_contigs;
+    uint64_t n_ambiguous_runs; /* maximal runs of ambiguous coordinates */
+    uint64_t ambiguous_bases;  /* their total length */
+} mica_reference_info;
+
+/* From memory: `sequence` holds the contigs' bytes back to back (len bytes),
+   contig i has contig_lengths[i] of them (sum = len).  names[i] is contig i's
+   name (NUL-terminated); names = NULL names them contig1, contig2, ....
+   MICA_EINVAL on a zero-length contig, lengths that do not sum to len, a bad
+   or repeated name, or a text too long for the index. */
+int mica_reference_create(const uint8_t *sequence, uint64_t len, const uint64_t *contig_lengths,
+                          const char *const *names, uint64_t n_contigs, mica_reference **out);
+/* From a FASTA file: each record starts with a '>' line whose first
+   whitespace-delimited word is the contig name; the sequence lines that
+   follow hold letters (any non-ACGT letter is ambiguous) and whitespace,
+   which is skipped; lines starting with ';' are comments.  MICA_EIO when the
+   file cannot be read or is malformed (bytes before the first record, a
+   character other than a letter or whitespace, an empty record, an empty,
+   invalid or repeated name); MICA_EINVAL when the text is too long. */
+int mica_reference_read_fasta(const char *path, mica_reference **out);
+/* Binary copy (contig table, ambiguous runs, G at 2 bits per base). */
+int mica_reference_save(const mica_reference *ref, const char *path);
+int mica_reference_load(const char *path, mica_reference **out);   /* MICA_EIO when malformed */
+void mica_reference_free(mica_reference *ref);
+
+int mica_reference_get_info(const mica_reference *ref, mica_reference_info *info);
+/* *acgt = G as 'A','C','G','T' bytes (owned by ref), *len = its length. */
+int mica_reference_text(const mica_reference *ref, const uint8_t **acgt, uint64_t *len);
+/* Contig i: *name (owned by ref), *start, *length; MICA_EINVAL when i is out
+   of range.  Any output pointer may be NULL. */
+int mica_reference_contig(const mica_reference *ref, uint64_t i, const char **name, uint64_t *start,
+                          uint64_t *length);
+/* Ambiguous run j as [*start, *start + *length) of G; MICA_EINVAL when j is
+   out of range. */
+int mica_reference_ambiguous_run(const mica_reference *ref, uint64_t j, uint64_t *start, uint64_t *length);
+
+/* For each window [pos[i], pos[i] + span[i]) of G: contig[i] = its contig
+   when it is a placement on the reference (inside one contig, no ambiguous
+   coordinate), else -1; local[i] = pos[i] - that contig's start (0 for -1).
+   MICA_EINVAL when a span is 0 or a window ends past G. */
+int mica_reference_locate(const mica_reference *ref, const uint32_t *pos, const uint16_t *span, uint64_t n,
+                          int32_t *contig, uint32_t *local);
+/* In place on a host result of n_reads reads (read i of length lengths[i]):
+   removes the listed hits that are not placements on the reference, keeping
+   the others in order, rewrites offsets[0..n_reads] and lowers total[i] by
+   the number removed from read i.  total[i] is then exact for every read
+   whose hits were all listed (total <= hit cap); for a capped read it is an
+   upper bound, since unlisted hits were never located.  *n_dropped
+   (optional) = hits removed.  MICA_EINVAL when offsets decrease, a listed
+   count exceeds total, or a hit ends past G. */
+int mica_reference_filter(const mica_reference *ref, const uint16_t *lengths, uint64_t n_reads, uint64_t *total,
+                          uint64_t *offsets, mica_hit *hits, uint64_t *n_dropped);
+
+/* ---- SAM output (host-side) ----
+ *
+ * Writes the search's placements as SAM 1.6 text (header @HD, one @SQ per
+ * contig, @PG).  Per read (numbered from 0 across calls; pairs numbered by
+ * pair), of length m, V = its listed hits that are placements on the
+ * reference:
+ *
+ *   - V empty: one unmapped record (FLAG 4, SEQ the read as given);
+ *   - else the primary record is the first hit of V (listed order: position,
+ *     strand) with the fewest substitutions dmin: RNAME/POS its contig and
+ *     1-based contig coordinate, CIGAR mM, FLAG 16 on the - strand with SEQ
+ *     the reverse complement (SAM stores the forward strand), QUAL *, tags
+ *     NM:i (substitutions, recomputed against G and required to equal the
+ *     hit's d), MD:Z (the reference bases at the substitutions), X0:i (hits
+ *     of V with dmin), X1:i (hits of V with dmin + 1) and ZT:i (the read's
+ *     total less the listed hits dropped, as mica_reference_filter gives);
+ *   - MAPQ: 0 unless the best placement is unique (X0 = 1, and the list is
+ *     complete or holds a hit with d > dmin, so the cap cut no dmin hit);
+ *     then 37 when no placement with dmin + 1 exists (X1 = 0 and the list is
+ *     complete or holds a hit with d > dmin + 1), else 25;
+ *   - with `secondary`, every other hit of V follows as FLAG 256, MAPQ 0,
+ *     SEQ *, with NM and MD.
+ *
+ * Pairs (mates 2i and 2i + 1, `pairs` from mica_pair_batch on the same
+ * result): FLAG 1, and 64 / 128 for mate 1 / 2.  When pairs[i] names a best
+ * concordant placement whose two hits are both in V and in the same contig,
+ * those hits are the mates' primaries and FLAG 2 (properly paired) is set,
+ * with MAPQ 0 when n_best > 1, 37 when the placement is the only concordant
+ * one and both mates' lists are complete, else 25.  Otherwise each mate
+ * takes its own primary as above.  Mate fields follow SAM: FLAG 8 / 32 for
+ * an unmapped / reverse-strand mate, RNEXT = or the mate's contig, PNEXT the
+ * mate's POS; an unmapped mate of a mapped read takes that read's RNAME and
+ * POS; TLEN = +-(rightmost end - leftmost start) when both are in one
+ * contig, + on the mate that starts first (mate 1 on a tie), else 0.
+ *
+ * A mica_sam_writer keeps a pointer to `ref`: free the reference only after
+ * mica_sam_close.  One host thread at a time.
+ */
+typedef struct mica_sam_writer mica_sam_writer;
+
+typedef struct {
+    const char *qname_prefix;  /* QNAME = prefix + read (or pair) number; NULL = "r" */
+    uint32_t secondary;        /* 1: also write the other placements of V as secondary records */
+    const char *command_line;  /* written as @PG CL: when not NULL */
+} mica_sam_params;
+
+void mica_sam_params_default(mica_sam_params *p);
+/* Creates or truncates `path` and writes the header.  MICA_EIO when the file
+   cannot be written; MICA_EINVAL on a prefix with whitespace or a command
+   line with a tab or newline. */
+int mica_sam_open(const char *path, const mica_reference *ref, const mica_sam_params *params,
+                  mica_sam_writer **out);
+/* Appends the records of a batch of n_reads reads (host arrays, the layout
+   mica_align_batch takes and returns).  pairs = NULL: single reads;
+   otherwise n_reads is even and pairs holds n_reads / 2 entries.  MICA_EINVAL
+   on inconsistent input (offsets decrease, more listed hits than total, a hit
+   that ends past G, or a hit whose d differs from its substitutions against
+   G, which means the result does not belong to these reads and this
+   reference); nothing of the batch is written then.  MICA_EIO on a write
+   error. */
+int mica_sam_write(mica_sam_writer *w, const uint32_t *packed_reads, const uint64_t *word_offsets,
+                   const uint16_t *lengths, uint64_t n_reads, const uint64_t *total, const uint64_t *offsets,
+                   const mica_hit *hits, const mica_pair *pairs);
+/* Flushes and closes the file and frees the writer (also on error).
+   MICA_EIO when the final write fails. */
+int mica_sam_close(mica_sam_writer *w);
+
 /* ---- hit-list offsets for callers that cannot allocate device memory ----
  *
  * The paper has no counterpart: this serves callers that may not call

@@ -19,6 +19,13 @@ Functions and what pins them (tests/test_oracle_*.py):
   genome (chance hits are vanishingly rare there), reverse-complement symmetry,
   and for the hit cap by the properties that define it.
 * :func:`bruteforce` -- pinned against the numpy scan in the tests.
+* :func:`reference_concat`, :func:`reference_filter` -- references of
+  several contigs with ambiguous bases: the concatenated text and the rule
+  that keeps a hit only when its window lies in one contig and covers no
+  ambiguous byte.  :func:`splitmix64` is pinned by the published outputs of
+  its reference implementation (tests/golden/splitmix64.txt); the filtered
+  search is pinned by a brute-force Hamming scan of each contig's own bytes
+  that skips windows with ambiguous bytes (tests/test_reference.py).
 * :func:`pair` -- mate pairing of a result (the paper's properly paired
   reads, Section 3, Table 1), plain Python loops over every combination of
   listed hits; pinned by the generator's true fragments on a random genome
@@ -295,3 +302,72 @@ def pair(result: Result, lengths, insert_min: int, insert_max: int) -> list:
         out.append((len(combos), n_best, best[1], best[3], best[2], best[0]))
     return out
 
+
+
+# --------------------------------------------------------------------------
+# References of several contigs with ambiguous bases
+# --------------------------------------------------------------------------
+
+_M64 = (1 << 64) - 1
+
+
+def splitmix64(state: int) -> int:
+    """SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): the output when the
+    generator's state before the call is ``state``."""
+    z = (state + 0x9E3779B97F4A7C15) & _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def reference_concat(contigs) -> tuple:
+    """The text G of a reference given as a list of contig byte strings (any
+    case; a byte other than A/C/G/T is ambiguous): the contigs back to back,
+    each ambiguous byte at coordinate j replaced by base splitmix64(j) >> 62.
+    Returns (codes uint8[N], starts [n + 1 contig bounds], runs [(s, e)]
+    maximal runs of ambiguous coordinates).  Plain loops; small inputs."""
+    codes, starts, runs = [], [0], []
+    value = {ord("A"): 0, ord("C"): 1, ord("G"): 2, ord("T"): 3}
+    for seq in contigs:
+        for byte in bytes(seq).upper():
+            j = len(codes)
+            if byte in value:
+                codes.append(value[byte])
+                continue
+            codes.append(splitmix64(j) >> 62)
+            if runs and runs[-1][1] == j:
+                runs[-1] = (runs[-1][0], j + 1)
+            else:
+                runs.append((j, j + 1))
+        starts.append(len(codes))
+    return np.array(codes, dtype=np.uint8), starts, runs
+
+
+def on_reference(pos: int, m: int, starts, runs) -> bool:
+    """Whether the window [pos, pos + m) of G lies inside one contig and
+    covers no ambiguous coordinate (a placement on the reference)."""
+    inside = any(starts[c] <= pos and pos + m <= starts[c + 1] for c in range(len(starts) - 1))
+    clear = not any(s < pos + m and pos < e for s, e in runs)
+    return inside and clear
+
+
+def reference_filter(result: Result, lengths, starts, runs) -> tuple:
+    """Drop the listed hits that are not placements on the reference; each
+    read's total falls by the number dropped from its list.  Returns
+    (Result, number dropped)."""
+    lengths = np.asarray(lengths)
+    n = len(result.offsets) - 1
+    total = np.array(result.total, dtype=np.uint64)
+    offsets = np.zeros(n + 1, dtype=np.uint64)
+    kept, dropped = [], 0
+    for i in range(n):
+        m = int(lengths[i])
+        for h in result.read_hits(i):
+            if on_reference(int(h["pos"]), m, starts, runs):
+                kept.append(h)
+            else:
+                total[i] -= 1
+                dropped += 1
+        offsets[i + 1] = len(kept)
+    hits = np.array(kept, dtype=HIT_DTYPE) if kept else np.zeros(0, dtype=HIT_DTYPE)
+    return Result(total, offsets, hits), dropped

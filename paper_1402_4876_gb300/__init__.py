@@ -142,6 +142,21 @@ SIGNATURES = {
     "mica_debug_lower_bounds": (_i32, [P, P, P, P, P, _u64, P]),
     "mica_pair_device": (_i32, [P, P, P, _u64, _u32, _u32, P, P]),
     "mica_pair_batch": (_i32, [ctypes.c_int, P, P, P, _u64, _u32, _u32, P]),
+    "mica_reference_create": (_i32, [P, _u64, P, P, _u64, P]),
+    "mica_reference_read_fasta": (_i32, [ctypes.c_char_p, P]),
+    "mica_reference_save": (_i32, [P, ctypes.c_char_p]),
+    "mica_reference_load": (_i32, [ctypes.c_char_p, P]),
+    "mica_reference_free": (None, [P]),
+    "mica_reference_get_info": (_i32, [P, P]),
+    "mica_reference_text": (_i32, [P, P, P]),
+    "mica_reference_contig": (_i32, [P, _u64, P, P, P]),
+    "mica_reference_ambiguous_run": (_i32, [P, _u64, P, P]),
+    "mica_reference_locate": (_i32, [P, P, P, _u64, P, P]),
+    "mica_reference_filter": (_i32, [P, P, _u64, P, P, P, P]),
+    "mica_sam_params_default": (None, [P]),
+    "mica_sam_open": (_i32, [ctypes.c_char_p, P, P, P]),
+    "mica_sam_write": (_i32, [P, P, P, P, _u64, P, P, P, P]),
+    "mica_sam_close": (_i32, [P]),
     "mica_server_params_default": (None, [P]),
     "mica_server_start": (_i32, [P, P, P]),
     "mica_server_submit": (_i32, [P, P, P, P, P, _u64, P]),
@@ -514,6 +529,162 @@ def pair_device(d_offsets, d_hits, d_lengths, n_pairs: int, insert_min: int, ins
     _check(_lib.mica_pair_device(ctypes.c_void_p(ptr(d_offsets)), ctypes.c_void_p(ptr(d_hits)),
                                  ctypes.c_void_p(ptr(d_lengths)), n_pairs, insert_min, insert_max,
                                  ctypes.c_void_p(ptr(d_out)), _stream_handle(stream)), "mica_pair_device")
+
+
+class ReferenceInfo(ctypes.Structure):
+    _fields_ = [("length", ctypes.c_uint64), ("n_contigs", ctypes.c_uint64), ("n_ambiguous_runs", ctypes.c_uint64),
+                ("ambiguous_bases", ctypes.c_uint64)]
+
+
+class SamParams(ctypes.Structure):
+    _fields_ = [("qname_prefix", ctypes.c_char_p), ("secondary", ctypes.c_uint32), ("command_line", ctypes.c_char_p)]
+
+
+class Reference:
+    """Named contigs concatenated into the index's text G (mica_reference):
+    ambiguous bytes replaced by a coordinate-derived base and recorded as
+    runs.  Host-only; build the index from :meth:`text`."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+
+    @classmethod
+    def create(cls, sequence, contig_lengths, names=None) -> "Reference":
+        seq = _acgt(sequence)
+        cl = np.ascontiguousarray(contig_lengths, dtype=np.uint64)
+        arr = None
+        if names is not None:
+            arr = (ctypes.c_char_p * len(names))(*[n.encode() for n in names])
+        out = ctypes.c_void_p()
+        _check(_lib.mica_reference_create(_ptr(seq) if seq.size else None, seq.size, _ptr(cl) if cl.size else None,
+                                          arr, cl.size, ctypes.byref(out)), "mica_reference_create")
+        return cls(out.value)
+
+    @classmethod
+    def from_fasta(cls, path: str) -> "Reference":
+        out = ctypes.c_void_p()
+        _check(_lib.mica_reference_read_fasta(path.encode(), ctypes.byref(out)), "mica_reference_read_fasta")
+        return cls(out.value)
+
+    @classmethod
+    def load(cls, path: str) -> "Reference":
+        out = ctypes.c_void_p()
+        _check(_lib.mica_reference_load(path.encode(), ctypes.byref(out)), "mica_reference_load")
+        return cls(out.value)
+
+    def save(self, path: str):
+        _check(_lib.mica_reference_save(self._h, path.encode()), "mica_reference_save")
+
+    def free(self):
+        if self._h:
+            _lib.mica_reference_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        i = ReferenceInfo()
+        _check(_lib.mica_reference_get_info(self._h, ctypes.byref(i)), "mica_reference_get_info")
+        return {f: int(getattr(i, f)) for f, _ in ReferenceInfo._fields_}
+
+    def text(self) -> bytes:
+        """G as 'ACGT' bytes (a copy): the genome to build the index from."""
+        p, n = ctypes.c_void_p(), ctypes.c_uint64()
+        _check(_lib.mica_reference_text(self._h, ctypes.byref(p), ctypes.byref(n)), "mica_reference_text")
+        return ctypes.string_at(p.value, n.value) if n.value else b""
+
+    def contigs(self) -> list:
+        """[(name, start, length)] in order."""
+        out = []
+        for i in range(self.info()["n_contigs"]):
+            name, st, ln = ctypes.c_char_p(), ctypes.c_uint64(), ctypes.c_uint64()
+            _check(_lib.mica_reference_contig(self._h, i, ctypes.byref(name), ctypes.byref(st), ctypes.byref(ln)),
+                   "mica_reference_contig")
+            out.append((name.value.decode(), int(st.value), int(ln.value)))
+        return out
+
+    def ambiguous_runs(self) -> np.ndarray:
+        """(start, length) of every maximal run of ambiguous coordinates of G."""
+        n = self.info()["n_ambiguous_runs"]
+        out = np.zeros((n, 2), dtype=np.uint64)
+        st, ln = ctypes.c_uint64(), ctypes.c_uint64()
+        for j in range(n):
+            _check(_lib.mica_reference_ambiguous_run(self._h, j, ctypes.byref(st), ctypes.byref(ln)),
+                   "mica_reference_ambiguous_run")
+            out[j] = (st.value, ln.value)
+        return out
+
+    def locate(self, pos, span):
+        """(contig int32, local uint32) of windows [pos, pos + span) of G;
+        contig -1 when the window is not a placement on the reference."""
+        pos = np.ascontiguousarray(pos, dtype=np.uint32)
+        span = np.ascontiguousarray(np.broadcast_to(span, pos.shape), dtype=np.uint16)
+        contig = np.empty(pos.size, dtype=np.int32)
+        local = np.empty(pos.size, dtype=np.uint32)
+        if pos.size:
+            _check(_lib.mica_reference_locate(self._h, _ptr(pos), _ptr(span), pos.size, _ptr(contig), _ptr(local)),
+                   "mica_reference_locate")
+        return contig, local
+
+    def filter(self, result, lengths):
+        """A copy of a host Result without the hits that are not placements on
+        the reference (mica_reference_filter); returns (Result, n_dropped)."""
+        total = np.array(result.total, dtype=np.uint64)
+        off = np.array(result.offsets, dtype=np.uint64)
+        hits = np.array(result.hits, dtype=HIT_DTYPE)
+        lens = np.ascontiguousarray(lengths, dtype=np.uint16)
+        dropped = ctypes.c_uint64()
+        n = total.size
+        _check(_lib.mica_reference_filter(self._h, _ptr(lens) if n else None, n, _ptr(total) if n else None,
+                                          _ptr(off), _ptr(hits) if hits.size else None, ctypes.byref(dropped)),
+               "mica_reference_filter")
+        return Result(total, off, hits[:int(off[-1])].copy()), int(dropped.value)
+
+
+class SamWriter:
+    """SAM output of results against a Reference (mica_sam_*).  Keep the
+    Reference alive until close()."""
+
+    def __init__(self, path: str, reference: Reference, qname_prefix: str = "r", secondary: bool = False,
+                 command_line: str | None = None):
+        self._ref = reference
+        p = SamParams(qname_prefix.encode(), int(secondary), command_line.encode() if command_line else None)
+        out = ctypes.c_void_p()
+        _check(_lib.mica_sam_open(path.encode(), reference._h, ctypes.byref(p), ctypes.byref(out)), "mica_sam_open")
+        self._h = ctypes.c_void_p(out.value)
+
+    def write(self, batch, result, pairs=None):
+        """Records of one batch (a ReadBatch-like object with words, word_off,
+        lengths) and its host Result; pairs: PAIR_DTYPE rows from pair_batch
+        when reads 2i, 2i+1 are mates."""
+        words = np.ascontiguousarray(batch.words, dtype=np.uint32)
+        woff = np.ascontiguousarray(batch.word_off, dtype=np.uint64)
+        lens = np.ascontiguousarray(batch.lengths, dtype=np.uint16)
+        total = np.ascontiguousarray(result.total, dtype=np.uint64)
+        off = np.ascontiguousarray(result.offsets, dtype=np.uint64)
+        hits = np.ascontiguousarray(result.hits, dtype=HIT_DTYPE)
+        n = lens.size
+        pr = None if pairs is None else np.ascontiguousarray(pairs, dtype=PAIR_DTYPE)
+        if n == 0:
+            return
+        _check(_lib.mica_sam_write(self._h, _ptr(words) if words.size else None, _ptr(woff), _ptr(lens), n,
+                                   _ptr(total), _ptr(off), _ptr(hits) if hits.size else None,
+                                   _ptr(pr) if pr is not None and pr.size else None), "mica_sam_write")
+
+    def close(self):
+        if self._h:
+            h, self._h = self._h, None
+            _check(_lib.mica_sam_close(h), "mica_sam_close")
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def gather_ceiling(buffer_bytes: int, load_bytes: int = 32, loads: int = 1 << 28, repeats: int = 3,

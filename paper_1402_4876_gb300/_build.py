@@ -1,6 +1,7 @@
 """Compile libmica_gb300.so in-tree with nvcc for sm_103a.
 
-Each translation unit is compiled in parallel to an object file under
+Each translation unit (``.cu`` device code, ``.cpp`` host-only code) is
+compiled in parallel to an object file under
 ``_build/``; the objects are linked into ``libmica_gb300.so`` next to this
 file.  No cmake, no torch extension machinery.
 """
@@ -17,7 +18,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmica_gb300.so")
-SOURCES = ["capi.cu", "index_build.cu", "search.cu", "post.cu", "serve.cu", "tune.cu", "noalloc.cu", "ceiling.cu", "pair.cu"]
+SOURCES = ["capi.cu", "index_build.cu", "search.cu", "post.cu", "serve.cu", "tune.cu", "noalloc.cu", "ceiling.cu",
+           "pair.cu", "reference.cpp", "sam.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -48,7 +50,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
 
     def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
         cmd = [cc] + _flags() + ["-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)

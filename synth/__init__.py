@@ -34,6 +34,8 @@ SEED_DONOR_HUMAN = 41
 SEED_READS_HUMAN = 42
 SEED_ARRIVALS = 51
 SEED_READS_SERVE = 52
+SEED_REFERENCE = 61
+SEED_REFERENCE_READS = 62
 
 
 def _rng(seed: int) -> np.random.Generator:
@@ -462,3 +464,55 @@ def serve_requests(donor: np.ndarray, n_requests: int, seed: int = SEED_READS_SE
         k = rng.integers(0, 3, size=int(s)).astype(np.uint8)
         out.append(sample_reads(g, lengths, k, rng, subs="rate", sub_rate=0.01))
     return out
+
+
+# --------------------------------------------------------------------------
+# A reference of several contigs, as FASTA files hold them
+# --------------------------------------------------------------------------
+
+IUPAC_AMBIGUOUS = b"NRYKMSWBDHV"
+
+
+def multi_contig_reference(lengths=(3000, 1700, 2600, 900), seed: int = SEED_REFERENCE, *,
+                           shared: int = 400) -> list:
+    """Contig byte strings with what real references hold besides A/C/G/T:
+    lower-case stretches (soft-masked repeats, 5% of bases in runs of up to
+    200), runs of N (assembly gaps: two per contig, 1-60 bases), scattered
+    single IUPAC ambiguity codes (0.2% of bases), and a ``shared``-base
+    segment of contig 0 copied into contig 2 and, reverse-complemented and
+    with one substitution per 50 bases, into contig 3 (so that reads land on
+    several contigs, on both strands, at several substitution counts)."""
+    rng = _rng(seed)
+    codes = [rng.integers(0, 4, size=n, dtype=np.uint8) for n in lengths]
+    if len(codes) >= 4 and shared and min(lengths[0], lengths[2], lengths[3]) > shared + 200:
+        seg = codes[0][100:100 + shared].copy()
+        codes[2][150:150 + shared] = seg
+        codes[3][50:50 + shared] = opposite_strand(seg)
+        substitute(codes[3], 50 + np.arange(25, shared, 50), rng)   # a near copy: one change per 50 bases
+    out = []
+    for c in codes:
+        b = bytearray(ACGT[c].tobytes())
+        n = len(b)
+        for _ in range(max(1, n // 4000)):      # soft-masked stretches
+            a = int(rng.integers(0, n))
+            for j in range(a, min(n, a + int(rng.integers(1, 201)))):
+                b[j] |= 0x20
+        for _ in range(2):                      # N gaps
+            ln = int(rng.integers(1, 61))
+            a = int(rng.integers(0, max(1, n - ln)))
+            b[a:a + ln] = b"N" * ln
+        for j in np.flatnonzero(rng.random(n) < 0.002):   # single ambiguity codes
+            b[int(j)] = IUPAC_AMBIGUOUS[int(rng.integers(0, len(IUPAC_AMBIGUOUS)))]
+        out.append(bytes(b))
+    return out
+
+
+def to_fasta(contigs, names, width: int = 60, crlf: bool = False) -> bytes:
+    """FASTA text of the contigs, sequence lines of ``width`` bytes."""
+    nl = b"\r\n" if crlf else b"\n"
+    parts = []
+    for name, seq in zip(names, contigs):
+        parts.append(b">" + name.encode() + b" synthetic contig" + nl)
+        for a in range(0, len(seq), width):
+            parts.append(seq[a:a + width] + nl)
+    return b"".join(parts)

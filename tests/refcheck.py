@@ -77,3 +77,22 @@ def min_prefix_mismatches(g: np.ndarray, pattern: np.ndarray, i: int) -> int:
         return 0
     w = windows(g, i)
     return int((w != np.asarray(pattern[:i], dtype=np.uint8)[None, :]).sum(axis=1).min())
+
+
+def contig_hamming_hits(contigs, read: np.ndarray, k: int) -> list:
+    """Sorted [(pos, strand, d)] over a reference of several contigs, from the
+    definition on each contig's own bytes: a window counts only when it lies
+    inside one contig and holds no byte other than A/C/G/T (either case);
+    pos is the window's start in the contigs laid back to back."""
+    value = np.full(256, 255, dtype=np.uint8)
+    for ch, v in zip(b"ACGT", range(4)):
+        value[ch] = v
+        value[ch + 32] = v
+    out, base = [], 0
+    for seq in contigs:
+        c = value[np.frombuffer(bytes(seq), dtype=np.uint8)]
+        for pos, strand, d in hamming_hits(np.where(c == 255, 0, c), read, k):
+            if not np.any(c[pos:pos + len(read)] == 255):
+                out.append((base + pos, strand, d))
+        base += len(seq)
+    return sorted(out)

@@ -1,0 +1,207 @@
+"""SAM output (host-side, no GPU): the library's mica_sam_* writer against a
+plain-Python restatement of the same rules (tests/samcheck.py), on oracle
+results over a reference of several contigs with ambiguous bases, and
+against what SAM itself fixes, checked on the records alone: SEQ, NM and MD
+reproduce the contig's own bytes at POS, FLAG 16 iff SEQ is the reverse
+complement of the read, one primary record per read, and mate fields that
+point at each other."""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import samcheck
+
+NAMES = ["chr1", "chr2", "chrUn_1", "chrM"]
+WINDOW = (200, 600)
+
+
+@pytest.fixture(scope="module")
+def mica():
+    import paper_1402_4876_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def setup(mica):
+    contigs = synth.multi_contig_reference()
+    g, starts, runs = oracle.reference_concat(contigs)
+    ref = mica.Reference.create(b"".join(contigs), [len(c) for c in contigs], NAMES)
+    return contigs, g, starts, runs, ref, oracle.FMIndex(g)
+
+
+@pytest.fixture(scope="module")
+def single(setup):
+    contigs, g, starts, runs, ref, fm = setup
+    rng = np.random.Generator(np.random.PCG64(synth.SEED_REFERENCE_READS + 1))
+    regions = [(max(0, s - 120), min(len(g), s + 120), "boundary") for s in starts[1:-1]]
+    regions += [(max(0, s - 120), min(len(g), e + 120), "ambiguous") for s, e in runs]
+    regions += [(100, 500, "shared"), (starts[3] + 50, starts[3] + 450, "near copy")]
+    n = 300
+    lengths = rng.choice(np.array([60, 100]), size=n)
+    k = rng.integers(0, 4, size=n, dtype=np.uint8)
+    return synth.sample_reads(synth.Genome(g, regions), lengths, k, rng, subs="count", max_subs=3,
+                              repeat_frac=0.6)
+
+
+@pytest.fixture(scope="module")
+def paired(setup):
+    g = setup[1]
+    return synth.paired_reads(g, 150, seed=synth.SEED_REFERENCE_READS + 2, m=100, insert_mean=350.0,
+                              insert_sd=40.0)
+
+
+def _write(mica, path, ref, batches, **kw):
+    with mica.SamWriter(str(path), ref, **kw) as w:
+        for batch, res, pairs in batches:
+            w.write(batch, res, pairs)
+    return open(path).read()
+
+
+def _expected(setup, batch, res, pairs=None, **kw):
+    contigs, g, starts, runs, ref, fm = setup
+    return samcheck.sam_text(NAMES, starts, runs, synth.to_acgt_bytes(g).decode(), batch, res, pairs, **kw)
+
+
+def _parse(text):
+    return [line.split("\t") for line in text.splitlines() if not line.startswith("@")]
+
+
+RC = str.maketrans("ACGT", "TGCA")
+
+
+def _check_records(setup, batch, text, paired_mode=False):
+    """What SAM fixes, from the records and the input bytes alone."""
+    contigs = setup[0]
+    by_name = dict(zip(NAMES, contigs))
+    recs = _parse(text)
+    primaries = {}
+    for f in recs:
+        qname, flag, rname, pos, mapq, cigar = f[0], int(f[1]), f[2], int(f[3]), int(f[4]), f[5]
+        tags = dict((t[:2], t[5:]) for t in f[11:])
+        i = int(qname[1:])
+        if paired_mode:
+            assert flag & 1
+            read = 2 * i + (0 if flag & 64 else 1)
+            assert bool(flag & 64) != bool(flag & 128)
+        else:
+            read = i
+        seq_read = "".join("ACGT"[c] for c in batch.read(read))
+        if not flag & 256:
+            assert read not in primaries
+            primaries[read] = f
+        if flag & 4:
+            assert f[9] == seq_read and cigar == "*" and mapq == 0
+            continue
+        m = len(seq_read)
+        assert cigar == f"{m}M"
+        window = by_name[rname][pos - 1:pos - 1 + m].upper()
+        assert len(window) == m and set(window) <= set(b"ACGT")
+        window = window.decode()
+        seq = seq_read.translate(RC)[::-1] if flag & 16 else seq_read
+        if not flag & 256:
+            assert f[9] == seq
+        assert int(tags["NM"]) == sum(a != b for a, b in zip(seq, window))
+        # MD spells the reference window from SEQ
+        md, rebuilt, j, num = tags["MD"], [], 0, ""
+        for ch in md + "$":
+            if ch.isdigit():
+                num += ch
+                continue
+            run = int(num or 0)
+            rebuilt.append(seq[j:j + run])
+            j += run
+            num = ""
+            if ch != "$":
+                rebuilt.append(ch)
+                j += 1
+        assert "".join(rebuilt) == window and j == m
+    assert sorted(primaries) == list(range(batch.n))
+    if paired_mode:
+        for p in range(batch.n // 2):
+            a, b = primaries[2 * p], primaries[2 * p + 1]
+            for x, y in ((a, b), (b, a)):
+                ry = y[2]
+                assert x[6] == ("*" if ry == "*" else "=" if ry == x[2] else ry)
+                assert int(x[7]) == int(y[3])
+                assert bool(int(x[1]) & 8) == bool(int(y[1]) & 4)
+                if not int(y[1]) & 4:
+                    assert bool(int(x[1]) & 32) == bool(int(y[1]) & 16)
+            assert int(a[8]) == -int(b[8])
+            if int(a[1]) & 2:
+                assert int(b[1]) & 2 and a[2] == b[2] and (int(a[1]) & 16) != (int(b[1]) & 16)
+                assert WINDOW[0] <= abs(int(a[8])) <= WINDOW[1]
+
+
+@pytest.mark.parametrize("cap,secondary", [(0, False), (0, True), (3, True)])
+def test_single_end(mica, setup, single, tmp_path, cap, secondary):
+    fm, ref = setup[5], setup[4]
+    res = fm.align(single, cap=cap)
+    got = _write(mica, tmp_path / "s.sam", ref, [(single, res, None)], secondary=secondary,
+                 qname_prefix="q", command_line="bench --sam")
+    want = _expected(setup, single, res, prefix="q", secondary=secondary, command_line="bench --sam")
+    assert got == want
+    _check_records(setup, single, got)
+    flags = [int(f[1]) for f in _parse(got)]
+    assert any(f & 4 for f in flags) and any(f & 16 for f in flags) and any(not f & 20 for f in flags)
+    mapqs = {int(f[4]) for f in _parse(got) if not int(f[1]) & 260}
+    assert mapqs == {0, 25, 37}
+
+
+def test_best_stratum_result(mica, setup, single, tmp_path):
+    fm, ref = setup[5], setup[4]
+    res = fm.align_best_stratum(single, cap=2)
+    got = _write(mica, tmp_path / "b.sam", ref, [(single, res, None)], secondary=True)
+    assert got == _expected(setup, single, res, secondary=True)
+    _check_records(setup, single, got)
+
+
+def test_paired(mica, setup, paired, tmp_path):
+    fm, ref = setup[5], setup[4]
+    res = fm.align(paired, cap=0)
+    tuples = oracle.pair(res, paired.lengths, *WINDOW)
+    pairs = samcheck.pairs_array(tuples, mica.PAIR_DTYPE)
+    got = _write(mica, tmp_path / "p.sam", ref, [(paired, res, pairs)], secondary=True, qname_prefix="p")
+    assert got == _expected(setup, paired, res, pairs, prefix="p", secondary=True)
+    _check_records(setup, paired, got, paired_mode=True)
+    flags = [int(f[1]) for f in _parse(got) if not int(f[1]) & 256]
+    assert any(f & 2 for f in flags) and any(not f & 2 for f in flags) and any(f & 8 for f in flags)
+    # concordant in G but across a contig boundary or over an ambiguous base: never properly paired
+    assert sum(1 for t in tuples if t[0]) > sum(1 for f in flags if f & 2) // 2
+
+
+def test_batches_continue_numbering(mica, setup, single, tmp_path):
+    fm, ref = setup[5], setup[4]
+    res = fm.align(single)
+    whole = _write(mica, tmp_path / "w.sam", ref, [(single, res, None)])
+    h = single.n // 2
+    a, b = single.subset(np.arange(h)), single.subset(np.arange(h, single.n))
+    parts = _write(mica, tmp_path / "p.sam", ref, [(a, fm.align(a), None), (b, fm.align(b), None)])
+    assert parts == whole
+
+
+def test_rejects_inconsistent_input(mica, setup, single, paired, tmp_path):
+    fm, ref = setup[5], setup[4]
+    res = fm.align(single)
+    bad = oracle.Result(res.total.copy(), res.offsets.copy(), res.hits.copy())
+    bad.hits["mm"][0] = (int(bad.hits["mm"][0]) + 1) % 4          # not the hit's substitutions
+    path = tmp_path / "r.sam"
+    with mica.SamWriter(str(path), ref) as w:
+        with pytest.raises(mica.MicaError) as e:
+            w.write(single, bad)
+        assert e.value.code == mica.MICA_EINVAL
+    assert all(line.startswith("@") for line in open(path).read().splitlines())
+    pres = fm.align(paired)
+    pairs = samcheck.pairs_array(oracle.pair(pres, paired.lengths, *WINDOW), mica.PAIR_DTYPE)
+    j = int(np.flatnonzero(pairs["n_concordant"] > 0)[0])
+    pairs["pos_plus"][j] += 1                                      # names no listed hit
+    with mica.SamWriter(str(path), ref) as w:
+        with pytest.raises(mica.MicaError):
+            w.write(paired, pres, pairs)
+        odd = paired.subset(np.arange(3))
+        with pytest.raises(mica.MicaError):
+            w.write(odd, fm.align(odd), pairs[:1])
+    for kw in ({"qname_prefix": "a b"}, {"qname_prefix": "@r"}, {"command_line": "x\ty"}):
+        with pytest.raises(mica.MicaError):
+            mica.SamWriter(str(path), ref, **kw)
