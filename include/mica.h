@@ -475,12 +475,14 @@ typedef struct {
     const char *qname_prefix;  /* QNAME = prefix + read (or pair) number; NULL = "r" */
     uint32_t secondary;        /* 1: also write the other placements of V as secondary records */
     const char *command_line;  /* written as @PG CL: when not NULL */
+    uint32_t threads;          /* host threads checking and formatting records, <= 256;
+                                  0 = the hardware's thread count */
 } mica_sam_params;
 
 void mica_sam_params_default(mica_sam_params *p);
 /* Creates or truncates `path` and writes the header.  MICA_EIO when the file
    cannot be written; MICA_EINVAL on a prefix with whitespace or a command
-   line with a tab or newline. */
+   line with a tab or newline, or more than 256 threads. */
 int mica_sam_open(const char *path, const mica_reference *ref, const mica_sam_params *params,
                   mica_sam_writer **out);
 /* Appends the records of a batch of n_reads reads (host arrays, the layout
@@ -490,7 +492,9 @@ int mica_sam_open(const char *path, const mica_reference *ref, const mica_sam_pa
    that ends past G, or a hit whose d differs from its substitutions against
    G, which means the result does not belong to these reads and this
    reference); nothing of the batch is written then.  MICA_EIO on a write
-   error. */
+   error and MICA_ENOMEM when a formatting buffer cannot grow; part of the
+   batch may have been written then.  Records come out in read order
+   whatever the thread count. */
 int mica_sam_write(mica_sam_writer *w, const uint32_t *packed_reads, const uint64_t *word_offsets,
                    const uint16_t *lengths, uint64_t n_reads, const uint64_t *total, const uint64_t *offsets,
                    const mica_hit *hits, const mica_pair *pairs);

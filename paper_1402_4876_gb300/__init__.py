@@ -537,7 +537,8 @@ class ReferenceInfo(ctypes.Structure):
 
 
 class SamParams(ctypes.Structure):
-    _fields_ = [("qname_prefix", ctypes.c_char_p), ("secondary", ctypes.c_uint32), ("command_line", ctypes.c_char_p)]
+    _fields_ = [("qname_prefix", ctypes.c_char_p), ("secondary", ctypes.c_uint32), ("command_line", ctypes.c_char_p),
+                ("threads", ctypes.c_uint32)]
 
 
 class Reference:
@@ -650,9 +651,10 @@ class SamWriter:
     Reference alive until close()."""
 
     def __init__(self, path: str, reference: Reference, qname_prefix: str = "r", secondary: bool = False,
-                 command_line: str | None = None):
+                 command_line: str | None = None, threads: int = 0):
         self._ref = reference
-        p = SamParams(qname_prefix.encode(), int(secondary), command_line.encode() if command_line else None)
+        p = SamParams(qname_prefix.encode(), int(secondary), command_line.encode() if command_line else None,
+                      threads)
         out = ctypes.c_void_p()
         _check(_lib.mica_sam_open(path.encode(), reference._h, ctypes.byref(p), ctypes.byref(out)), "mica_sam_open")
         self._h = ctypes.c_void_p(out.value)

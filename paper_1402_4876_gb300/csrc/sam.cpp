@@ -8,13 +8,18 @@
 // uniqueness MAPQ and, for paired reads, the pairing fields.
 //
 // A batch is checked in full before any of it is formatted, so that bad
-// input leaves the file as it was.
+// input leaves the file as it was.  Records are independent per read (per
+// pair), so both the check and the formatting run on host threads over
+// chunks of 4,096 reads; formatted chunks are written in read order.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <memory>
 #include <new>
 #include <string>
+#include <system_error>
+#include <thread>
 #include <vector>
 
 #include "reference_internal.h"
@@ -24,15 +29,17 @@ struct mica_sam_writer {
     const mica_reference *ref = nullptr;
     std::string prefix;
     uint32_t secondary = 0;
-    uint64_t next_id = 0;   // number of the next read, or of the next pair
-    std::string buf;
+    uint32_t threads = 1;
+    uint64_t next_id = 0;          // number of the next read, or of the next pair
+    std::vector<std::string> bufs; // one per chunk of a formatting window, kept across calls
 };
 
 namespace mica {
 namespace {
 
 constexpr const char *ACGT = "ACGT";
-constexpr size_t FLUSH_BYTES = 8u << 20;
+constexpr uint64_t CHUNK_READS = 4096;   // even: a pair never straddles two chunks
+constexpr uint32_t MAX_THREADS = 256;
 
 struct Placement {
     const mica_hit *h;
@@ -188,50 +195,56 @@ inline Spot spot_of(const Placement *p)
     return s;
 }
 
-struct Writer {
-    mica_sam_writer &w;
+// Formats records into one buffer (one buffer per chunk of reads).
+struct Formatter {
+    std::string &buf;
     const mica_reference &ref;
+    const std::string &prefix;
+    bool secondary;
 
     void qname(uint64_t id)
     {
-        w.buf += w.prefix;
-        put_u64(w.buf, id);
-        w.buf.push_back('\t');
+        buf += prefix;
+        put_u64(buf, id);
+        buf.push_back('\t');
     }
 
     void rname(int32_t contig)
     {
-        if (contig < 0) w.buf.push_back('*');
-        else w.buf += ref.names[contig];
-        w.buf.push_back('\t');
+        if (contig < 0) buf.push_back('*');
+        else buf += ref.names[contig];
+        buf.push_back('\t');
     }
 
     // RNEXT and PNEXT of a record at contig `self` whose mate sits at `mate`.
     void next(int32_t self, const Spot *mate)
     {
         if (!mate || mate->contig < 0) {
-            w.buf += "*\t0\t";
+            buf += "*\t0\t";
             return;
         }
-        if (mate->contig == self) w.buf.push_back('=');
-        else w.buf += ref.names[mate->contig];
-        w.buf.push_back('\t');
-        put_u64(w.buf, mate->pos1);
-        w.buf.push_back('\t');
+        if (mate->contig == self) buf.push_back('=');
+        else buf += ref.names[mate->contig];
+        buf.push_back('\t');
+        put_u64(buf, mate->pos1);
+        buf.push_back('\t');
     }
 
     void seq(const ReadInfo &r, int strand)
     {
-        for (uint32_t j = 0; j < r.m; j++) w.buf.push_back(ACGT[oriented(r, strand, j)]);
-        w.buf += "\t*";   // SEQ, QUAL
+        const size_t o = buf.size();
+        buf.resize(o + r.m);
+        char *d = &buf[o];
+        for (uint32_t j = 0; j < r.m; j++) d[j] = ACGT[oriented(r, strand, j)];
+        buf += "\t*";   // QUAL
     }
 
     void match_tags(const ReadInfo &r, const Placement &p)
     {
-        w.buf += "\tNM:i:";
-        put_u64(w.buf, p.h->mm);
-        w.buf += "\tMD:Z:";
-        put_md(w.buf, ref, r, p.h->pos, p.h->strand);
+        buf += "\tNM:i:";
+        put_u64(buf, p.h->mm);
+        buf += "\tMD:Z:";
+        put_md(buf, ref, r, p.h->pos, p.h->strand);
     }
 
     // One primary record.  flag0: the pairing bits; mate = NULL for single reads.
@@ -240,65 +253,57 @@ struct Writer {
     {
         const uint32_t flag = flag0 | (p ? 0u : 4u) | (p && p->h->strand ? 16u : 0u);
         qname(id);
-        put_u64(w.buf, flag);
-        w.buf.push_back('\t');
+        put_u64(buf, flag);
+        buf.push_back('\t');
         rname(self.contig);
-        put_u64(w.buf, self.pos1);
-        w.buf.push_back('\t');
-        put_u64(w.buf, p ? (uint64_t)mapq : 0u);
-        w.buf.push_back('\t');
+        put_u64(buf, self.pos1);
+        buf.push_back('\t');
+        put_u64(buf, p ? (uint64_t)mapq : 0u);
+        buf.push_back('\t');
         if (p) {
-            put_u64(w.buf, r.m);
-            w.buf += "M\t";
+            put_u64(buf, r.m);
+            buf += "M\t";
         } else {
-            w.buf += "*\t";
+            buf += "*\t";
         }
         next(self.contig, mate);
-        put_i64(w.buf, tlen);
-        w.buf.push_back('\t');
+        put_i64(buf, tlen);
+        buf.push_back('\t');
         seq(r, p ? p->h->strand : 0);
         if (p) {
             match_tags(r, *p);
-            w.buf += "\tX0:i:";
-            put_u64(w.buf, r.c0);
-            w.buf += "\tX1:i:";
-            put_u64(w.buf, r.c1);
-            w.buf += "\tZT:i:";
-            put_u64(w.buf, r.total_ref);
+            buf += "\tX0:i:";
+            put_u64(buf, r.c0);
+            buf += "\tX1:i:";
+            put_u64(buf, r.c1);
+            buf += "\tZT:i:";
+            put_u64(buf, r.total_ref);
         }
-        w.buf.push_back('\n');
+        buf.push_back('\n');
     }
 
     void secondaries(uint64_t id, uint32_t flag0, const ReadInfo &r, const Placement *p, const Spot *mate)
     {
-        if (!w.secondary) return;
+        if (!secondary) return;
         for (const Placement &s : r.V) {
             if (&s == p) continue;
             qname(id);
-            put_u64(w.buf, flag0 | 256u | (s.h->strand ? 16u : 0u));
-            w.buf.push_back('\t');
+            put_u64(buf, flag0 | 256u | (s.h->strand ? 16u : 0u));
+            buf.push_back('\t');
             rname(s.contig);
-            put_u64(w.buf, (uint64_t)s.local + 1);
-            w.buf += "\t0\t";
-            put_u64(w.buf, r.m);
-            w.buf += "M\t";
+            put_u64(buf, (uint64_t)s.local + 1);
+            buf += "\t0\t";
+            put_u64(buf, r.m);
+            buf += "M\t";
             next(s.contig, mate);
-            w.buf += "0\t*\t*";
+            buf += "0\t*\t*";
             match_tags(r, s);
-            w.buf.push_back('\n');
+            buf.push_back('\n');
         }
     }
 };
 
-bool flush(mica_sam_writer &w)
-{
-    if (w.buf.empty()) return true;
-    const bool ok = fwrite(w.buf.data(), 1, w.buf.size(), w.f) == w.buf.size();
-    w.buf.clear();
-    return ok;
-}
-
-// Proper-pair placement of pair i, or false.  Sets the two primaries and MAPQ.
+// Proper-pair placement of a pair: sets the two primaries and their MAPQ.
 int proper_pair(const mica_pair &pr, const ReadInfo &m1, const ReadInfo &m2, const mica_hit *hits,
                 const Placement **p1, const Placement **p2, int *mapq, bool *proper)
 {
@@ -329,6 +334,112 @@ int64_t tlen_of(const Placement &self, uint32_t mself, const Placement &other, u
     return self_is_mate1 ? t : -t;
 }
 
+// A batch as mica_sam_write receives it.
+struct Batch {
+    const uint32_t *words;
+    const uint64_t *word_off;
+    const uint16_t *len;
+    const uint64_t *total;
+    const uint64_t *offsets;
+    const mica_hit *hits;
+    const mica_pair *pairs;
+    uint64_t n;
+};
+
+inline int classify_read(const mica_reference &ref, const Batch &b, uint64_t i, bool check, ReadInfo &r)
+{
+    return classify(ref, b.words, b.word_off, b.len, b.total, b.offsets, b.hits, i, check, r);
+}
+
+// Checks reads [a, e) of the batch (a even when paired).
+int check_range(const mica_reference &ref, const Batch &b, uint64_t a, uint64_t e, ReadInfo &r1, ReadInfo &r2)
+{
+    for (uint64_t i = a; i < e; i++) {
+        ReadInfo &r = ((i - a) & 1) ? r2 : r1;
+        if (int rc = classify_read(ref, b, i, true, r)) return rc;
+        if (b.pairs && ((i - a) & 1)) {
+            const Placement *p1 = nullptr, *p2 = nullptr;
+            int mapq = 0;
+            bool proper = false;
+            if (int rc = proper_pair(b.pairs[i / 2], r1, r2, b.hits, &p1, &p2, &mapq, &proper)) return rc;
+        }
+    }
+    return 0;
+}
+
+// Formats reads [a, e) of a checked batch; first_id = number of read a (of
+// its pair when paired).
+void format_range(Formatter &out, const Batch &b, uint64_t a, uint64_t e, uint64_t first_id, ReadInfo &r1,
+                  ReadInfo &r2)
+{
+    const mica_reference &ref = out.ref;
+    if (!b.pairs) {
+        for (uint64_t i = a; i < e; i++) {
+            classify_read(ref, b, i, false, r1);
+            const uint64_t id = first_id + (i - a);
+            out.primary(id, 0, r1, r1.primary, r1.mapq, spot_of(r1.primary), nullptr, 0);
+            out.secondaries(id, 0, r1, r1.primary, nullptr);
+        }
+        return;
+    }
+    for (uint64_t i = a; i < e; i += 2) {
+        classify_read(ref, b, i, false, r1);
+        classify_read(ref, b, i + 1, false, r2);
+        const Placement *p1 = r1.primary, *p2 = r2.primary;
+        int q1 = r1.mapq, q2 = r2.mapq, qp = 0;
+        bool proper = false;
+        const Placement *x = nullptr, *y = nullptr;
+        proper_pair(b.pairs[i / 2], r1, r2, b.hits, &x, &y, &qp, &proper);
+        if (proper) {
+            p1 = x;
+            p2 = y;
+            q1 = q2 = qp;
+        }
+        // an unmapped mate sits at its mapped mate's place
+        Spot s1 = spot_of(p1), s2 = spot_of(p2);
+        if (!p1) s1 = s2;
+        if (!p2) s2 = s1;
+        int64_t t1 = 0, t2 = 0;
+        if (p1 && p2 && p1->contig == p2->contig) {
+            t1 = tlen_of(*p1, r1.m, *p2, r2.m, true);
+            t2 = tlen_of(*p2, r2.m, *p1, r1.m, false);
+        }
+        const uint32_t base = 1u | (proper ? 2u : 0u);
+        const uint32_t f1 = base | 64u | (p2 ? (p2->h->strand ? 32u : 0u) : 8u);
+        const uint32_t f2 = base | 128u | (p1 ? (p1->h->strand ? 32u : 0u) : 8u);
+        const uint64_t id = first_id + (i - a) / 2;
+        out.primary(id, f1, r1, p1, q1, s1, &s2, t1);
+        out.secondaries(id, f1 & ~2u, r1, p1, &s2);
+        out.primary(id, f2, r2, p2, q2, s2, &s1, t2);
+        out.secondaries(id, f2 & ~2u, r2, p2, &s1);
+    }
+}
+
+// Runs f(c) for c = 0..n-1 on up to `threads` host threads (the caller's
+// among them).  f must not throw.
+template <typename F> void parallel_chunks(uint64_t n, unsigned threads, F f)
+{
+    std::atomic<uint64_t> next{0};
+    auto worker = [&]() {
+        for (uint64_t c; (c = next.fetch_add(1, std::memory_order_relaxed)) < n;) f(c);
+    };
+    const unsigned t = (unsigned)std::min<uint64_t>(threads, n);
+    std::vector<std::thread> pool;
+    try {
+        pool.reserve(t);
+        for (unsigned i = 1; i < t; i++) pool.emplace_back(worker);
+    } catch (...) {   // fewer threads than asked: the started ones and this one finish the work
+    }
+    worker();
+    for (auto &th : pool) th.join();
+}
+
+inline void set_error(std::atomic<int> &err, int rc)
+{
+    int none = 0;
+    err.compare_exchange_strong(none, rc);
+}
+
 }  // namespace
 }  // namespace mica
 
@@ -342,6 +453,7 @@ void mica_sam_params_default(mica_sam_params *p)
     p->qname_prefix = nullptr;
     p->secondary = 0;
     p->command_line = nullptr;
+    p->threads = 0;
 }
 
 int mica_sam_open(const char *path, const mica_reference *ref, const mica_sam_params *params,
@@ -354,7 +466,7 @@ int mica_sam_open(const char *path, const mica_reference *ref, const mica_sam_pa
     mica_sam_params_default(&p);
     if (params) p = *params;
     const std::string prefix = p.qname_prefix ? p.qname_prefix : "r";
-    if (prefix.size() > 200 || p.secondary > 1) return MICA_EINVAL;
+    if (prefix.size() > 200 || p.secondary > 1 || p.threads > MAX_THREADS) return MICA_EINVAL;
     for (char c : prefix)   // QNAME: printable, no '@'
         if ((unsigned char)c < 33 || (unsigned char)c > 126 || c == '@') return MICA_EINVAL;
     if (p.command_line && strpbrk(p.command_line, "\t\n\r")) return MICA_EINVAL;
@@ -363,10 +475,9 @@ int mica_sam_open(const char *path, const mica_reference *ref, const mica_sam_pa
         w->ref = ref;
         w->prefix = prefix;
         w->secondary = p.secondary;
-        w->f = fopen(path, "wb");
-        if (!w->f) return MICA_EIO;
-        std::string &s = w->buf;
-        s += "@HD\tVN:1.6\tSO:unsorted\n";
+        w->threads = p.threads ? p.threads : std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(),
+                                                                              MAX_THREADS));
+        std::string s = "@HD\tVN:1.6\tSO:unsorted\n";
         for (size_t i = 0; i < ref->names.size(); i++) {
             s += "@SQ\tSN:";
             s += ref->names[i];
@@ -380,7 +491,9 @@ int mica_sam_open(const char *path, const mica_reference *ref, const mica_sam_pa
             s += p.command_line;
         }
         s.push_back('\n');
-        if (!flush(*w)) {
+        w->f = fopen(path, "wb");
+        if (!w->f) return MICA_EIO;
+        if (fwrite(s.data(), 1, s.size(), w->f) != s.size()) {
             fclose(w->f);
             return MICA_EIO;
         }
@@ -400,78 +513,75 @@ int mica_sam_write(mica_sam_writer *w, const uint32_t *packed_reads, const uint6
     if (!packed_reads || !word_offsets || !lengths || !total || !offsets) return MICA_EINVAL;
     if (pairs && (n_reads & 1)) return MICA_EINVAL;
     const mica_reference &ref = *w->ref;
+    const Batch b{packed_reads, word_offsets, lengths, total, offsets, hits, pairs, n_reads};
+    const uint64_t n_chunks = (n_reads + CHUNK_READS - 1) / CHUNK_READS;
+    std::atomic<int> err{0};
+    // pass 1: check everything, write nothing
+    parallel_chunks(n_chunks, w->threads, [&](uint64_t c) {
+        try {
+            ReadInfo r1, r2;
+            const uint64_t a = c * CHUNK_READS, e = std::min(n_reads, a + CHUNK_READS);
+            if (int rc = check_range(ref, b, a, e, r1, r2)) set_error(err, rc);
+        } catch (const std::bad_alloc &) {
+            set_error(err, MICA_ENOMEM);
+        }
+    });
+    if (int rc = err.load()) return rc;
+    // pass 2: format windows of chunks in parallel into one half of a double
+    // buffer while a writer thread writes the previous window from the other
     try {
-        ReadInfo r1, r2;
-        // pass 1: check everything, write nothing
-        for (uint64_t i = 0; i < n_reads; i++) {
-            ReadInfo &r = (i & 1) ? r2 : r1;
-            if (int rc = classify(ref, packed_reads, word_offsets, lengths, total, offsets, hits, i, true, r))
-                return rc;
-            if (pairs && (i & 1)) {
-                const Placement *p1 = nullptr, *p2 = nullptr;
-                int mapq = 0;
-                bool proper = false;
-                if (int rc = proper_pair(pairs[i / 2], r1, r2, hits, &p1, &p2, &mapq, &proper)) return rc;
+        const uint64_t window = (uint64_t)w->threads * 4;
+        if (w->bufs.size() < 2 * window) w->bufs.resize(2 * window);
+        std::thread writer;
+        std::atomic<bool> write_ok{true};
+        auto write_window = [&](uint64_t half, uint64_t nw) {
+            for (uint64_t j = 0; j < nw; j++) {
+                const std::string &buf = w->bufs[half * window + j];
+                if (fwrite(buf.data(), 1, buf.size(), w->f) != buf.size()) {
+                    write_ok = false;
+                    return;
+                }
+            }
+        };
+        auto join_writer = [&]() {
+            if (writer.joinable()) writer.join();
+        };
+        for (uint64_t c0 = 0, k = 0; c0 < n_chunks; c0 += window, k++) {
+            const uint64_t nw = std::min(window, n_chunks - c0), half = k & 1;
+            parallel_chunks(nw, w->threads, [&](uint64_t j) {
+                try {
+                    ReadInfo r1, r2;
+                    const uint64_t a = (c0 + j) * CHUNK_READS, e = std::min(n_reads, a + CHUNK_READS);
+                    std::string &buf = w->bufs[half * window + j];
+                    buf.clear();
+                    Formatter out{buf, ref, w->prefix, w->secondary != 0};
+                    format_range(out, b, a, e, w->next_id + (pairs ? a / 2 : a), r1, r2);
+                } catch (const std::bad_alloc &) {
+                    set_error(err, MICA_ENOMEM);
+                }
+            });
+            join_writer();
+            if (!write_ok) return MICA_EIO;
+            if (int rc = err.load()) return rc;
+            try {
+                writer = std::thread(write_window, half, nw);
+            } catch (const std::system_error &) {
+                write_window(half, nw);   // no thread to spare: write here
             }
         }
-        // pass 2: format
-        Writer out{*w, ref};
-        if (!pairs) {
-            for (uint64_t i = 0; i < n_reads; i++) {
-                classify(ref, packed_reads, word_offsets, lengths, total, offsets, hits, i, false, r1);
-                const Spot self = spot_of(r1.primary);
-                out.primary(w->next_id + i, 0, r1, r1.primary, r1.mapq, self, nullptr, 0);
-                out.secondaries(w->next_id + i, 0, r1, r1.primary, nullptr);
-                if (w->buf.size() >= FLUSH_BYTES && !flush(*w)) return MICA_EIO;
-            }
-            w->next_id += n_reads;
-        } else {
-            for (uint64_t i = 0; i < n_reads; i += 2) {
-                classify(ref, packed_reads, word_offsets, lengths, total, offsets, hits, i, false, r1);
-                classify(ref, packed_reads, word_offsets, lengths, total, offsets, hits, i + 1, false, r2);
-                const Placement *p1 = r1.primary, *p2 = r2.primary;
-                int q1 = r1.mapq, q2 = r2.mapq, qp = 0;
-                bool proper = false;
-                const Placement *a = nullptr, *b = nullptr;
-                proper_pair(pairs[i / 2], r1, r2, hits, &a, &b, &qp, &proper);
-                if (proper) {
-                    p1 = a;
-                    p2 = b;
-                    q1 = q2 = qp;
-                }
-                // an unmapped mate sits at its mapped mate's place
-                Spot s1 = spot_of(p1), s2 = spot_of(p2);
-                if (!p1) s1 = s2;
-                if (!p2) s2 = s1;
-                int64_t t1 = 0, t2 = 0;
-                if (p1 && p2 && p1->contig == p2->contig) {
-                    t1 = tlen_of(*p1, r1.m, *p2, r2.m, true);
-                    t2 = tlen_of(*p2, r2.m, *p1, r1.m, false);
-                }
-                const uint32_t base = 1u | (proper ? 2u : 0u);
-                const uint32_t f1 = base | 64u | (p2 ? (p2->h->strand ? 32u : 0u) : 8u);
-                const uint32_t f2 = base | 128u | (p1 ? (p1->h->strand ? 32u : 0u) : 8u);
-                const uint64_t id = w->next_id + i / 2;
-                out.primary(id, f1, r1, p1, q1, s1, &s2, t1);
-                out.secondaries(id, f1 & ~2u, r1, p1, &s2);
-                out.primary(id, f2, r2, p2, q2, s2, &s1, t2);
-                out.secondaries(id, f2 & ~2u, r2, p2, &s1);
-                if (w->buf.size() >= FLUSH_BYTES && !flush(*w)) return MICA_EIO;
-            }
-            w->next_id += n_reads / 2;
-        }
-        return flush(*w) ? 0 : MICA_EIO;
+        join_writer();
+        if (!write_ok) return MICA_EIO;
     } catch (const std::bad_alloc &) {
-        w->buf.clear();
         return MICA_ENOMEM;
     }
+    w->next_id += pairs ? n_reads / 2 : n_reads;
+    return 0;
 }
 
 int mica_sam_close(mica_sam_writer *w)
 {
     if (!w) return MICA_EINVAL;
-    bool ok = flush(*w);
-    ok = fclose(w->f) == 0 && ok;
+    const bool ok = fclose(w->f) == 0;
     delete w;
     return ok ? 0 : MICA_EIO;
 }

@@ -205,3 +205,55 @@ def test_rejects_inconsistent_input(mica, setup, single, paired, tmp_path):
     for kw in ({"qname_prefix": "a b"}, {"qname_prefix": "@r"}, {"command_line": "x\ty"}):
         with pytest.raises(mica.MicaError):
             mica.SamWriter(str(path), ref, **kw)
+
+
+def _tile(batch, res, t):
+    """The batch and its result repeated t times (a batch of many chunks)."""
+    class B:
+        pass
+    b = B()
+    nw = int(batch.word_off[-1])
+    b.words = np.tile(batch.words, t)
+    b.word_off = np.concatenate([batch.word_off[:-1] + i * nw for i in range(t)] + [[t * nw]]).astype(np.uint64)
+    b.lengths = np.tile(batch.lengths, t)
+    nh = int(res.offsets[-1])
+    off = np.concatenate([res.offsets[:-1] + i * nh for i in range(t)] + [[t * nh]]).astype(np.uint64)
+    return b, oracle.Result(np.tile(res.total, t), off, np.tile(res.hits, t))
+
+
+@pytest.mark.parametrize("paired_mode", [False, True])
+def test_threads_keep_read_order(mica, setup, single, paired, tmp_path, paired_mode):
+    """Batches of many 4,096-read chunks: the same text whatever the thread count."""
+    fm, ref = setup[5], setup[4]
+    batch = paired if paired_mode else single
+    res = fm.align(batch, cap=3)
+    pairs = None
+    if paired_mode:
+        pairs = samcheck.pairs_array(oracle.pair(res, batch.lengths, *WINDOW), mica.PAIR_DTYPE)
+    t = -(-20_000 // batch.n)
+    big, bres = _tile(batch, res, t)
+    bpairs = None if pairs is None else np.tile(pairs, t)
+    texts = []
+    for threads in (1, 3, 0):
+        texts.append(_write(mica, tmp_path / f"t{threads}.sam", ref, [(big, bres, bpairs)], secondary=True,
+                            threads=threads))
+    assert texts[0] == texts[1] == texts[2]
+    one = _write(mica, tmp_path / "one.sam", ref, [(batch, res, pairs)], secondary=True)
+    body = [line for line in texts[0].splitlines() if not line.startswith("@")]
+    first = [line for line in one.splitlines() if not line.startswith("@")]
+    assert body[:len(first)] == first                        # the first copy, numbered from 0
+    assert len(body) == t * len(first)
+    with pytest.raises(mica.MicaError):
+        mica.SamWriter(str(tmp_path / "x.sam"), ref, threads=257)
+
+
+def test_bad_read_in_a_late_chunk_writes_nothing(mica, setup, single, tmp_path):
+    fm, ref = setup[5], setup[4]
+    big, bres = _tile(single, fm.align(single), 40)
+    j = int(bres.offsets[-1]) - 1
+    bres.hits["mm"][j] = (int(bres.hits["mm"][j]) + 1) % 4      # the last listed hit
+    path = tmp_path / "late.sam"
+    with mica.SamWriter(str(path), ref, threads=4) as w:
+        with pytest.raises(mica.MicaError):
+            w.write(big, bres)
+    assert all(line.startswith("@") for line in open(path).read().splitlines())
