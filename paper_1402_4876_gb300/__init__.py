@@ -279,11 +279,17 @@ class Index:
     @classmethod
     def build(cls, genome_acgt, kmer_q: int = 12, sa_sample: int = 16, device: int = 0,
               lower_bounds: bool = True) -> "Index":
-        g = _acgt(genome_acgt)
+        """Index of `genome_acgt` (ACGT bytes, a uint8 array of them, or a
+        Reference, whose text is passed without a copy)."""
+        if isinstance(genome_acgt, Reference):
+            ptr, n = genome_acgt._text_ptr()
+        else:
+            g = _acgt(genome_acgt)
+            ptr, n = (_ptr(g) if g.size else None), g.size
         p = IndexParams(kmer_q, sa_sample, int(bool(lower_bounds)))
         h = ctypes.c_void_p()
-        _check(_lib.mica_index_build_resident(_ptr(g) if g.size else None, g.size, ctypes.byref(p), device,
-                                             ctypes.byref(h)), "mica_index_build_resident")
+        _check(_lib.mica_index_build_resident(ptr, n, ctypes.byref(p), device, ctypes.byref(h)),
+               "mica_index_build_resident")
         return cls(h.value)
 
     @classmethod
@@ -592,11 +598,15 @@ class Reference:
         _check(_lib.mica_reference_get_info(self._h, ctypes.byref(i)), "mica_reference_get_info")
         return {f: int(getattr(i, f)) for f, _ in ReferenceInfo._fields_}
 
-    def text(self) -> bytes:
-        """G as 'ACGT' bytes (a copy): the genome to build the index from."""
+    def _text_ptr(self):
         p, n = ctypes.c_void_p(), ctypes.c_uint64()
         _check(_lib.mica_reference_text(self._h, ctypes.byref(p), ctypes.byref(n)), "mica_reference_text")
-        return ctypes.string_at(p.value, n.value) if n.value else b""
+        return p, int(n.value)
+
+    def text(self) -> bytes:
+        """G as 'ACGT' bytes (a copy); Index.build(reference) needs no copy."""
+        p, n = self._text_ptr()
+        return ctypes.string_at(p.value, n) if n else b""
 
     def contigs(self) -> list:
         """[(name, start, length)] in order."""

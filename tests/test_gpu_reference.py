@@ -23,7 +23,7 @@ def setup():
     g, starts, runs = oracle.reference_concat(contigs)
     ref = m.Reference.create(b"".join(contigs), [len(c) for c in contigs], NAMES)
     assert ref.text() == synth.to_acgt_bytes(g)
-    return m, contigs, g, starts, runs, ref, m.Index.build(ref.text()), oracle.FMIndex(g)
+    return m, contigs, g, starts, runs, ref, m.Index.build(ref), oracle.FMIndex(g)
 
 
 def _single(g, starts, runs):

@@ -12,7 +12,7 @@ import pytest
 
 import oracle
 import synth
-from tests import refcheck
+from tests import hostlib, refcheck
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 GOLDEN = os.path.join(ROOT, "tests", "golden", "splitmix64.txt")
@@ -21,8 +21,7 @@ NAMES = ["chr1", "chr2", "chrUn_1", "chrM"]
 
 @pytest.fixture(scope="module")
 def mica():
-    import paper_1402_4876_gb300 as m
-    return m
+    return hostlib.mica()
 
 
 @pytest.fixture(scope="module")
@@ -33,11 +32,6 @@ def contigs():
 @pytest.fixture(scope="module")
 def concat(contigs):
     return oracle.reference_concat(contigs)
-
-
-class Batch:
-    def __init__(self, words, word_off, lengths, k):
-        self.words, self.word_off, self.lengths, self.k = words, word_off, lengths, k
 
 
 @pytest.fixture(scope="module")

@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 import synth
-from tests import samcheck
+from tests import hostlib, samcheck
 
 NAMES = ["chr1", "chr2", "chrUn_1", "chrM"]
 WINDOW = (200, 600)
@@ -19,8 +19,7 @@ WINDOW = (200, 600)
 
 @pytest.fixture(scope="module")
 def mica():
-    import paper_1402_4876_gb300 as m
-    return m
+    return hostlib.mica()
 
 
 @pytest.fixture(scope="module")
