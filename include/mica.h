@@ -431,6 +431,70 @@ int mica_reference_locate(const mica_reference *ref, const uint32_t *pos, const 
 int mica_reference_filter(const mica_reference *ref, const uint16_t *lengths, uint64_t n_reads, uint64_t *total,
                           uint64_t *offsets, mica_hit *hits, uint64_t *n_dropped);
 
+/* ---- reads from FASTQ (host-side) ----
+ *
+ * The paper's input is sequencer reads in FASTQ (Section 3: paired-end
+ * lanes).  A mica_fastq reads one file, or two files of mates, into batches
+ * in the layout mica_align_batch takes, keeping names and qualities for SAM.
+ * Each record is four lines: '@' and the name (its first word is kept; a
+ * trailing "/1" or "/2" is dropped for mates), the bases, a line starting
+ * with '+', and one quality character (33..126) per base; CRLF is accepted
+ * and blank lines between records are skipped.  A base other than A/C/G/T
+ * (either case; N, IUPAC codes, '.') is ambiguous: the packed read holds the
+ * base given by the top two bits of SplitMix64(2^8 * r + j) for read number
+ * r of the file (mates numbered 2i, 2i + 1) and offset j, and its offset is
+ * recorded.
+ *
+ * N in reads.  An ambiguous read base matches no reference base, so a
+ * placement's substitutions d' count it always.  The search over the packed
+ * read never counts it more than that (its stand-in base costs 0 or 1), so
+ * every placement with d' <= k is among the search's hits, and
+ * mica_read_batch_filter_n keeps exactly those, with d' as their mm: the
+ * result is {(p, s, d'): d' <= k}.  For a read listed in full (total <= hit
+ * cap) this is exact; for a capped read the cap chose among the search's d
+ * and total is an upper bound.
+ */
+typedef struct mica_fastq mica_fastq;
+typedef struct mica_read_batch mica_read_batch;
+
+/* path2 = NULL: single reads; else mates of path1 and path2 interleaved as
+   reads 2i and 2i + 1.  MICA_EIO when a file cannot be opened. */
+int mica_fastq_open(const char *path1, const char *path2, mica_fastq **out);
+/* The next batch: up to max_reads reads (rounded down to even when paired,
+   at least 2), each with budget k.  *out = a batch of 0 reads at the end of
+   the file(s).  MICA_EIO on a malformed record, names of mates that differ,
+   or files of mates of different lengths; MICA_EINVAL on a read of length 0
+   or above MICA_MAX_READ_LEN, or k > MICA_MAX_K. */
+int mica_fastq_read(mica_fastq *fq, uint64_t max_reads, uint8_t k, mica_read_batch **out);
+void mica_fastq_close(mica_fastq *fq);
+
+typedef struct {
+    uint64_t n_reads;
+    const uint32_t *packed_reads;  /* the layout mica_align_batch takes, owned by the batch */
+    const uint64_t *word_offsets;
+    const uint16_t *lengths;
+    const uint8_t *k;
+    uint64_t n_ambiguous_reads;    /* reads with at least one ambiguous base */
+    uint32_t paired;               /* 1: reads 2i and 2i + 1 are mates */
+} mica_read_batch_view;
+
+int mica_read_batch_get_view(const mica_read_batch *b, mica_read_batch_view *v);
+/* Read i's name (owned by the batch), qualities (lengths[i] bytes, not
+   NUL-terminated) and ambiguous offsets (ascending).  Any output pointer may
+   be NULL. */
+int mica_read_batch_read(const mica_read_batch *b, uint64_t i, const char **name, const char **qualities,
+                         const uint16_t **ambiguous, uint32_t *n_ambiguous);
+void mica_read_batch_free(mica_read_batch *b);
+
+/* In place on the host result of this batch (as mica_reference_filter):
+   for every read with ambiguous bases, each listed hit's mm becomes d'
+   (mismatches against the reference text plus ambiguous bases) and hits
+   with d' > k are removed, total falling by their number.  Idempotent.
+   MICA_EINVAL on inconsistent input (offsets, totals, a hit past the text,
+   or an mm that is neither the hit's d nor its d'); nothing changes then. */
+int mica_read_batch_filter_n(const mica_read_batch *b, const mica_reference *ref, uint64_t *total,
+                             uint64_t *offsets, mica_hit *hits, uint64_t *n_dropped);
+
 /* ---- SAM output (host-side) ----
  *
  * Writes the search's placements as SAM 1.6 text (header @HD, one @SQ per
@@ -498,6 +562,18 @@ int mica_sam_open(const char *path, const mica_reference *ref, const mica_sam_pa
 int mica_sam_write(mica_sam_writer *w, const uint32_t *packed_reads, const uint64_t *word_offsets,
                    const uint16_t *lengths, uint64_t n_reads, const uint64_t *total, const uint64_t *offsets,
                    const mica_hit *hits, const mica_pair *pairs);
+/* As mica_sam_write for a batch from mica_fastq_read, with its names,
+   qualities and ambiguous bases: QNAME is the read's name (mate 1's for a
+   pair), SEQ shows ambiguous bases as N, QUAL holds the read's qualities
+   (reversed on the - strand), NM and MD count ambiguous bases as
+   substitutions (d'), and hits with d' > k are left out as
+   mica_read_batch_filter_n leaves them out; the hits may be given before or
+   after that filter.  pairs: the pairing of a paired batch's result
+   (mica_pair_batch), or NULL, which writes its mates as pairs with none
+   properly paired; must be NULL for a batch of single reads.  The numbering
+   of mica_sam_write is not used or advanced. */
+int mica_sam_write_batch(mica_sam_writer *w, const mica_read_batch *b, const uint64_t *total,
+                         const uint64_t *offsets, const mica_hit *hits, const mica_pair *pairs);
 /* Flushes and closes the file and frees the writer (also on error).
    MICA_EIO when the final write fails. */
 int mica_sam_close(mica_sam_writer *w);

@@ -26,6 +26,9 @@ Functions and what pins them (tests/test_oracle_*.py):
   its reference implementation (tests/golden/splitmix64.txt); the filtered
   search is pinned by a brute-force Hamming scan of each contig's own bytes
   that skips windows with ambiguous bytes (tests/test_reference.py).
+* :func:`n_filter` -- reads with ambiguous bases (N): each such base costs
+  one substitution wherever it falls; pinned by a brute-force Hamming scan
+  in which the read's ambiguous bases equal no base (tests/test_fastq.py).
 * :func:`pair` -- mate pairing of a result (the paper's properly paired
   reads, Section 3, Table 1), plain Python loops over every combination of
   listed hits; pinned by the generator's true fragments on a random genome
@@ -365,6 +368,50 @@ def reference_filter(result: Result, lengths, starts, runs) -> tuple:
         for h in result.read_hits(i):
             if on_reference(int(h["pos"]), m, starts, runs):
                 kept.append(h)
+            else:
+                total[i] -= 1
+                dropped += 1
+        offsets[i + 1] = len(kept)
+    hits = np.array(kept, dtype=HIT_DTYPE) if kept else np.zeros(0, dtype=HIT_DTYPE)
+    return Result(total, offsets, hits), dropped
+
+
+# --------------------------------------------------------------------------
+# Reads with ambiguous bases
+# --------------------------------------------------------------------------
+
+def n_filter(result: Result, reads, ambiguous, k, g) -> tuple:
+    """Ambiguous read bases count as substitutions wherever they fall.
+
+    reads[i]: read i's base codes as searched (ambiguous offsets hold some
+    stand-in base); ambiguous[i]: its ambiguous offsets; k[i]: its budget;
+    g: the text's base codes.  For every read with ambiguous bases, each
+    listed hit's d becomes d' = the window offsets whose reference base
+    differs from the read's base or whose read base is ambiguous (the read
+    reverse-complemented on the - strand), and hits with d' > k[i] are
+    dropped, total falling by their number.  Returns (Result, dropped)."""
+    g = np.asarray(g)
+    n = len(result.offsets) - 1
+    total = np.array(result.total, dtype=np.uint64)
+    offsets = np.zeros(n + 1, dtype=np.uint64)
+    kept, dropped = [], 0
+    for i in range(n):
+        amb = set(int(j) for j in ambiguous[i])
+        read = [int(c) for c in reads[i]]
+        m = len(read)
+        for h in result.read_hits(i):
+            if not amb:
+                kept.append(h)
+                continue
+            pos, strand = int(h["pos"]), int(h["strand"])
+            d = 0
+            for j in range(m):
+                r = m - 1 - j if strand else j            # read offset at window offset j
+                base = 3 - read[r] if strand else read[r]
+                if r in amb or int(g[pos + j]) != base:
+                    d += 1
+            if d <= int(k[i]):
+                kept.append((pos, strand, d, 0))
             else:
                 total[i] -= 1
                 dropped += 1

@@ -153,6 +153,14 @@ SIGNATURES = {
     "mica_reference_ambiguous_run": (_i32, [P, _u64, P, P]),
     "mica_reference_locate": (_i32, [P, P, P, _u64, P, P]),
     "mica_reference_filter": (_i32, [P, P, _u64, P, P, P, P]),
+    "mica_fastq_open": (_i32, [ctypes.c_char_p, ctypes.c_char_p, P]),
+    "mica_fastq_read": (_i32, [P, _u64, ctypes.c_uint8, P]),
+    "mica_fastq_close": (None, [P]),
+    "mica_read_batch_get_view": (_i32, [P, P]),
+    "mica_read_batch_read": (_i32, [P, _u64, P, P, P, P]),
+    "mica_read_batch_free": (None, [P]),
+    "mica_read_batch_filter_n": (_i32, [P, P, P, P, P, P]),
+    "mica_sam_write_batch": (_i32, [P, P, P, P, P, P]),
     "mica_sam_params_default": (None, [P]),
     "mica_sam_open": (_i32, [ctypes.c_char_p, P, P, P]),
     "mica_sam_write": (_i32, [P, P, P, P, _u64, P, P, P, P]),
@@ -656,6 +664,119 @@ class Reference:
         return Result(total, off, hits[:int(off[-1])].copy()), int(dropped.value)
 
 
+class ReadBatchView(ctypes.Structure):
+    _fields_ = [("n_reads", ctypes.c_uint64), ("packed_reads", ctypes.c_void_p), ("word_offsets", ctypes.c_void_p),
+                ("lengths", ctypes.c_void_p), ("k", ctypes.c_void_p), ("n_ambiguous_reads", ctypes.c_uint64),
+                ("paired", ctypes.c_uint32)]
+
+
+def _copy_array(ptr, n: int, dtype) -> np.ndarray:
+    out = np.empty(n, dtype=dtype)
+    if n:
+        ctypes.memmove(out.ctypes.data, ptr, n * out.itemsize)
+    return out
+
+
+class FastqBatch:
+    """Reads of one mica_fastq_read call (mica_read_batch): words, word_off,
+    lengths and k as numpy copies (so `Index.align_batch(batch)` works), plus
+    names, qualities and the offsets of ambiguous bases."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+        v = ReadBatchView()
+        _check(_lib.mica_read_batch_get_view(self._h, ctypes.byref(v)), "mica_read_batch_get_view")
+        n = int(v.n_reads)
+        self.word_off = _copy_array(v.word_offsets, n + 1, np.uint64)
+        self.words = _copy_array(v.packed_reads, int(self.word_off[-1]), np.uint32)
+        self.lengths = _copy_array(v.lengths, n, np.uint16)
+        self.k = _copy_array(v.k, n, np.uint8)
+        self.n_ambiguous_reads = int(v.n_ambiguous_reads)
+        self.paired = bool(v.paired)
+
+    @property
+    def n(self) -> int:
+        return int(self.lengths.size)
+
+    def read(self, i: int) -> np.ndarray:
+        """Base codes of read i as searched (ambiguous bases hold their stand-ins)."""
+        m = int(self.lengths[i])
+        w = self.words[int(self.word_off[i]):int(self.word_off[i + 1])]
+        return ((w[:, None] >> (2 * np.arange(16, dtype=np.uint32))[None, :]) & 3).astype(np.uint8).reshape(-1)[:m]
+
+    def record(self, i: int):
+        """(name, qualities, ambiguous offsets) of read i."""
+        name, qual, amb, na = ctypes.c_char_p(), ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_uint32()
+        _check(_lib.mica_read_batch_read(self._h, i, ctypes.byref(name), ctypes.byref(qual), ctypes.byref(amb),
+                                         ctypes.byref(na)), "mica_read_batch_read")
+        m = int(self.lengths[i])
+        return (name.value.decode(), ctypes.string_at(qual.value, m).decode(),
+                _copy_array(amb.value, int(na.value), np.uint16))
+
+    def filter_n(self, reference: "Reference", result):
+        """A copy of this batch's host Result with ambiguous read bases counted
+        as substitutions (mica_read_batch_filter_n); returns (Result, n_dropped)."""
+        total = np.array(result.total, dtype=np.uint64)
+        off = np.array(result.offsets, dtype=np.uint64)
+        hits = np.array(result.hits, dtype=HIT_DTYPE)
+        dropped = ctypes.c_uint64()
+        _check(_lib.mica_read_batch_filter_n(self._h, reference._h, _ptr(total) if total.size else None, _ptr(off),
+                                             _ptr(hits) if hits.size else None, ctypes.byref(dropped)),
+               "mica_read_batch_filter_n")
+        return Result(total, off, hits[:int(off[-1])].copy()), int(dropped.value)
+
+    def free(self):
+        if self._h:
+            _lib.mica_read_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class FastqReader:
+    """Batches of reads from one FASTQ file, or two files of mates (mica_fastq)."""
+
+    def __init__(self, path1: str, path2: str | None = None):
+        out = ctypes.c_void_p()
+        _check(_lib.mica_fastq_open(path1.encode(), path2.encode() if path2 else None, ctypes.byref(out)),
+               "mica_fastq_open")
+        self._h = ctypes.c_void_p(out.value)
+
+    def read(self, max_reads: int, k: int = 2) -> FastqBatch:
+        """The next batch (0 reads at the end)."""
+        out = ctypes.c_void_p()
+        _check(_lib.mica_fastq_read(self._h, max_reads, k, ctypes.byref(out)), "mica_fastq_read")
+        return FastqBatch(out.value)
+
+    def batches(self, max_reads: int, k: int = 2):
+        while True:
+            b = self.read(max_reads, k)
+            if b.n == 0:
+                return
+            yield b
+
+    def close(self):
+        if self._h:
+            _lib.mica_fastq_close(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class SamWriter:
     """SAM output of results against a Reference (mica_sam_*).  Keep the
     Reference alive until close()."""
@@ -686,6 +807,17 @@ class SamWriter:
         _check(_lib.mica_sam_write(self._h, _ptr(words) if words.size else None, _ptr(woff), _ptr(lens), n,
                                    _ptr(total), _ptr(off), _ptr(hits) if hits.size else None,
                                    _ptr(pr) if pr is not None and pr.size else None), "mica_sam_write")
+
+    def write_batch(self, batch: FastqBatch, result, pairs=None):
+        """Records of a FastqBatch and its host Result (names, qualities, N)."""
+        if batch.n == 0:
+            return
+        total = np.ascontiguousarray(result.total, dtype=np.uint64)
+        off = np.ascontiguousarray(result.offsets, dtype=np.uint64)
+        hits = np.ascontiguousarray(result.hits, dtype=HIT_DTYPE)
+        pr = None if pairs is None else np.ascontiguousarray(pairs, dtype=PAIR_DTYPE)
+        _check(_lib.mica_sam_write_batch(self._h, batch._h, _ptr(total), _ptr(off), _ptr(hits) if hits.size else None,
+                                         _ptr(pr) if pr is not None and pr.size else None), "mica_sam_write_batch")
 
     def close(self):
         if self._h:

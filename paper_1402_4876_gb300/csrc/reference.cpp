@@ -22,30 +22,8 @@ constexpr uint64_t MAX_TEXT = (1ull << 32) - 2;   // the index keeps |G| + 1 < 2
 constexpr uint64_t MAX_NAME = 1u << 16;
 constexpr char FILE_MAGIC[8] = {'M', 'I', 'C', 'A', 'R', 'E', 'F', '1'};
 
-// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): the value returned when
-// the generator's state before the call is x.
-uint64_t splitmix64(uint64_t x)
-{
-    x += 0x9E3779B97F4A7C15ull;
-    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
-    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
-    return x ^ (x >> 31);
-}
-
 inline uint8_t replacement_base(uint64_t coord) { return "ACGT"[splitmix64(coord) >> 62]; }
 
-inline int base_code(uint8_t c)
-{
-    switch (c | 0x20) {
-    case 'a': return 0;
-    case 'c': return 1;
-    case 'g': return 2;
-    case 't': return 3;
-    default: return -1;
-    }
-}
-
-inline bool is_letter(uint8_t c) { return (c | 0x20) >= 'a' && (c | 0x20) <= 'z'; }
 inline bool is_space(uint8_t c) { return c == ' ' || c == '\t' || c == '\r' || c == '\n' || c == '\v' || c == '\f'; }
 
 // Append one sequence byte to G (the caller checks the length limit).

@@ -29,4 +29,29 @@ int32_t reference_place(const mica_reference &r, uint64_t pos, uint64_t span);
 // SAM's reference-name rule: [0-9A-Za-z!#$%&+./:;?@^_|~-][0-9A-Za-z!#$%&*+./:;=?@^_|~-]*
 bool sam_name_ok(const std::string &s);
 
+// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): the value returned when
+// the generator's state before the call is x.  Picks the stand-in base of an
+// ambiguous byte (top two bits).
+inline uint64_t splitmix64(uint64_t x)
+{
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+// Base code of an A/C/G/T byte (either case), -1 for any other byte.
+inline int base_code(uint8_t c)
+{
+    switch (c | 0x20) {
+    case 'a': return 0;
+    case 'c': return 1;
+    case 'g': return 2;
+    case 't': return 3;
+    default: return -1;
+    }
+}
+
+inline bool is_letter(uint8_t c) { return (c | 0x20) >= 'a' && (c | 0x20) <= 'z'; }
+
 }  // namespace mica

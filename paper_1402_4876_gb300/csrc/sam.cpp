@@ -22,6 +22,7 @@
 #include <thread>
 #include <vector>
 
+#include "read_batch_internal.h"
 #include "reference_internal.h"
 
 struct mica_sam_writer {
@@ -45,12 +46,17 @@ struct Placement {
     const mica_hit *h;
     int32_t contig;
     uint32_t local;   // 0-based coordinate in the contig
+    uint32_t d;       // substitutions, ambiguous read bases included
 };
 
 // One read of the batch as the records need it.
 struct ReadInfo {
     uint32_t m = 0;
     uint8_t codes[MICA_MAX_READ_LEN];
+    uint8_t amb[MICA_MAX_READ_LEN];   // 1: an ambiguous base (a substitution wherever it falls)
+    bool has_amb = false;
+    const char *name = nullptr;       // from a read batch, else NULL
+    const char *qual = nullptr;
     uint64_t b = 0, e = 0;          // listed hits [b, e)
     std::vector<Placement> V;       // listed hits that are placements on the reference
     const Placement *primary = nullptr;
@@ -68,25 +74,64 @@ inline uint8_t oriented(const ReadInfo &r, int strand, uint32_t j)
     return strand == 0 ? r.codes[j] : (uint8_t)(3 - r.codes[r.m - 1 - j]);
 }
 
-uint32_t substitutions(const mica_reference &ref, const ReadInfo &r, uint64_t pos, int strand)
+// The read offset at window offset j (the - strand runs backwards).
+inline uint32_t read_offset(const ReadInfo &r, int strand, uint32_t j) { return strand ? r.m - 1 - j : j; }
+
+// Substitutions of the read on `strand` against G[pos, pos + m): *raw counts
+// the stand-in bases as bases, *dprime counts every ambiguous base.
+void substitutions(const mica_reference &ref, const ReadInfo &r, uint64_t pos, int strand, uint32_t *raw,
+                   uint32_t *dprime)
 {
-    uint32_t d = 0;
-    for (uint32_t j = 0; j < r.m; j++) d += ref.text[pos + j] != (uint8_t)ACGT[oriented(r, strand, j)];
-    return d;
+    uint32_t a = 0, b = 0;
+    for (uint32_t j = 0; j < r.m; j++) {
+        const bool mism = ref.text[pos + j] != (uint8_t)ACGT[oriented(r, strand, j)];
+        a += mism;
+        b += mism || r.amb[read_offset(r, strand, j)];
+    }
+    *raw = a;
+    *dprime = b;
 }
+
+// A batch as the writer receives it; rb (optional) adds names, qualities,
+// ambiguous bases and budgets.
+struct Batch {
+    const uint32_t *words;
+    const uint64_t *word_off;
+    const uint16_t *len;
+    const uint64_t *total;
+    const uint64_t *offsets;
+    const mica_hit *hits;
+    const mica_pair *pairs;   // pairing rows, or NULL
+    uint64_t n;
+    const mica_read_batch *rb;
+    bool paired;              // reads 2i and 2i + 1 are mates
+};
 
 // Decode and classify read i; `check` also recomputes every listed hit's
 // substitutions against G.  Returns MICA_EINVAL on inconsistent input.
-int classify(const mica_reference &ref, const uint32_t *words, const uint64_t *word_off, const uint16_t *len,
-             const uint64_t *total, const uint64_t *offsets, const mica_hit *hits, uint64_t i, bool check,
-             ReadInfo &r)
+int classify(const mica_reference &ref, const Batch &bt, uint64_t i, bool check, ReadInfo &r)
 {
-    r.m = len[i];
+    const uint64_t *word_off = bt.word_off, *total = bt.total, *offsets = bt.offsets;
+    const mica_hit *hits = bt.hits;
+    r.m = bt.len[i];
     if (r.m == 0 || r.m > MICA_MAX_READ_LEN || word_off[i + 1] < word_off[i] ||
         word_off[i + 1] - word_off[i] < (r.m + 15u) / 16u)
         return MICA_EINVAL;
-    const uint32_t *w = words + word_off[i];
-    for (uint32_t j = 0; j < r.m; j++) r.codes[j] = (uint8_t)((w[j >> 4] >> (2 * (j & 15))) & 3);
+    const uint32_t *w = bt.words + word_off[i];
+    for (uint32_t j = 0; j < r.m; j++) {
+        r.codes[j] = (uint8_t)((w[j >> 4] >> (2 * (j & 15))) & 3);
+        r.amb[j] = 0;
+    }
+    r.has_amb = false;
+    uint32_t kmax = MICA_MAX_K;
+    if (bt.rb) {
+        const mica_read_batch &rb = *bt.rb;
+        for (uint64_t a = rb.amb_off[i]; a < rb.amb_off[i + 1]; a++) r.amb[rb.amb[a]] = 1;
+        r.has_amb = rb.amb_off[i + 1] > rb.amb_off[i];
+        r.name = rb.names.c_str() + rb.name_off[i];
+        r.qual = rb.quals.data() + rb.qual_off[i];
+        kmax = rb.k[i];
+    }
     r.b = offsets[i];
     r.e = offsets[i + 1];
     if (r.e < r.b || r.e - r.b > total[i] || (r.e > r.b && !hits)) return MICA_EINVAL;
@@ -98,25 +143,31 @@ int classify(const mica_reference &ref, const uint32_t *words, const uint64_t *w
         const mica_hit &x = hits[h];
         const int32_t c = reference_place(ref, x.pos, r.m);
         if (c == PLACE_OUT_OF_RANGE || x.strand > 1 || x.mm > MICA_MAX_K) return MICA_EINVAL;
-        if (check && substitutions(ref, r, x.pos, x.strand) != x.mm) return MICA_EINVAL;
-        if (c >= 0) {
-            r.V.push_back({&x, c, (uint32_t)(x.pos - ref.start[c])});
-            dmin = std::min<uint32_t>(dmin, x.mm);
+        uint32_t raw = x.mm, d = x.mm;
+        if (check || r.has_amb) {
+            substitutions(ref, r, x.pos, x.strand, &raw, &d);
+            // as the search gave it (raw), or after the N filter (d')
+            if (check && x.mm != raw && !(r.has_amb && x.mm == d)) return MICA_EINVAL;
+            if (!r.has_amb) d = raw;
         }
+        if (c >= 0 && d <= kmax) r.V.push_back({&x, c, (uint32_t)(x.pos - ref.start[c]), d});
+    }
+    for (const Placement &p : r.V) dmin = std::min(dmin, p.d);
+    for (uint64_t h = r.b; h < r.e; h++) {   // the cap cuts the search's highest d first
+        uint32_t raw = hits[h].mm, dd = raw;
+        if (r.has_amb) substitutions(ref, r, hits[h].pos, hits[h].strand, &raw, &dd);
+        deeper0 |= raw > dmin;
+        deeper1 |= raw > dmin + 1;
     }
     r.dmin = dmin;
     r.c0 = r.c1 = 0;
     for (const Placement &p : r.V) {
-        if (p.h->mm == dmin) {
+        if (p.d == dmin) {
             if (!r.primary) r.primary = &p;
             r.c0++;
-        } else if (p.h->mm == dmin + 1) {
+        } else if (p.d == dmin + 1) {
             r.c1++;
         }
-    }
-    for (uint64_t h = r.b; h < r.e; h++) {   // the cap cuts the highest d first
-        deeper0 |= hits[h].mm > dmin;
-        deeper1 |= hits[h].mm > dmin + 1;
     }
     const uint64_t listed = r.e - r.b;
     r.complete = total[i] == listed;
@@ -167,7 +218,7 @@ void put_md(std::string &s, const mica_reference &ref, const ReadInfo &r, uint64
     uint64_t run = 0;
     for (uint32_t j = 0; j < r.m; j++) {
         const uint8_t g = ref.text[pos + j];
-        if (g == (uint8_t)ACGT[oriented(r, strand, j)]) {
+        if (!r.amb[read_offset(r, strand, j)] && g == (uint8_t)ACGT[oriented(r, strand, j)]) {
             run++;
         } else {
             put_u64(s, run);
@@ -202,10 +253,14 @@ struct Formatter {
     const std::string &prefix;
     bool secondary;
 
-    void qname(uint64_t id)
+    void qname(uint64_t id, const ReadInfo &r)
     {
-        buf += prefix;
-        put_u64(buf, id);
+        if (r.name) {
+            buf += r.name;
+        } else {
+            buf += prefix;
+            put_u64(buf, id);
+        }
         buf.push_back('\t');
     }
 
@@ -230,19 +285,29 @@ struct Formatter {
         buf.push_back('\t');
     }
 
+    // SEQ and QUAL on the forward strand of the reference
     void seq(const ReadInfo &r, int strand)
     {
-        const size_t o = buf.size();
+        size_t o = buf.size();
         buf.resize(o + r.m);
         char *d = &buf[o];
-        for (uint32_t j = 0; j < r.m; j++) d[j] = ACGT[oriented(r, strand, j)];
-        buf += "\t*";   // QUAL
+        for (uint32_t j = 0; j < r.m; j++)
+            d[j] = r.amb[read_offset(r, strand, j)] ? 'N' : ACGT[oriented(r, strand, j)];
+        buf.push_back('\t');
+        if (!r.qual) {
+            buf.push_back('*');
+            return;
+        }
+        o = buf.size();
+        buf.resize(o + r.m);
+        d = &buf[o];
+        for (uint32_t j = 0; j < r.m; j++) d[j] = r.qual[read_offset(r, strand, j)];
     }
 
     void match_tags(const ReadInfo &r, const Placement &p)
     {
         buf += "\tNM:i:";
-        put_u64(buf, p.h->mm);
+        put_u64(buf, p.d);
         buf += "\tMD:Z:";
         put_md(buf, ref, r, p.h->pos, p.h->strand);
     }
@@ -252,7 +317,7 @@ struct Formatter {
                  const Spot *mate, int64_t tlen)
     {
         const uint32_t flag = flag0 | (p ? 0u : 4u) | (p && p->h->strand ? 16u : 0u);
-        qname(id);
+        qname(id, r);
         put_u64(buf, flag);
         buf.push_back('\t');
         rname(self.contig);
@@ -287,7 +352,7 @@ struct Formatter {
         if (!secondary) return;
         for (const Placement &s : r.V) {
             if (&s == p) continue;
-            qname(id);
+            qname(id, r);
             put_u64(buf, flag0 | 256u | (s.h->strand ? 16u : 0u));
             buf.push_back('\t');
             rname(s.contig);
@@ -334,21 +399,9 @@ int64_t tlen_of(const Placement &self, uint32_t mself, const Placement &other, u
     return self_is_mate1 ? t : -t;
 }
 
-// A batch as mica_sam_write receives it.
-struct Batch {
-    const uint32_t *words;
-    const uint64_t *word_off;
-    const uint16_t *len;
-    const uint64_t *total;
-    const uint64_t *offsets;
-    const mica_hit *hits;
-    const mica_pair *pairs;
-    uint64_t n;
-};
-
 inline int classify_read(const mica_reference &ref, const Batch &b, uint64_t i, bool check, ReadInfo &r)
 {
-    return classify(ref, b.words, b.word_off, b.len, b.total, b.offsets, b.hits, i, check, r);
+    return classify(ref, b, i, check, r);
 }
 
 // Checks reads [a, e) of the batch (a even when paired).
@@ -373,7 +426,7 @@ void format_range(Formatter &out, const Batch &b, uint64_t a, uint64_t e, uint64
                   ReadInfo &r2)
 {
     const mica_reference &ref = out.ref;
-    if (!b.pairs) {
+    if (!b.paired) {
         for (uint64_t i = a; i < e; i++) {
             classify_read(ref, b, i, false, r1);
             const uint64_t id = first_id + (i - a);
@@ -389,7 +442,7 @@ void format_range(Formatter &out, const Batch &b, uint64_t a, uint64_t e, uint64
         int q1 = r1.mapq, q2 = r2.mapq, qp = 0;
         bool proper = false;
         const Placement *x = nullptr, *y = nullptr;
-        proper_pair(b.pairs[i / 2], r1, r2, b.hits, &x, &y, &qp, &proper);
+        if (b.pairs) proper_pair(b.pairs[i / 2], r1, r2, b.hits, &x, &y, &qp, &proper);
         if (proper) {
             p1 = x;
             p2 = y;
@@ -439,6 +492,77 @@ inline void set_error(std::atomic<int> &err, int rc)
     int none = 0;
     err.compare_exchange_strong(none, rc);
 }
+
+// Checks a whole batch, then formats and writes it (see mica_sam_write).
+int write_records(mica_sam_writer *w, const Batch &b)
+{
+    const mica_reference &ref = *w->ref;
+    const uint64_t n_reads = b.n;
+    const bool pairs = b.paired;
+    const uint64_t n_chunks = (n_reads + CHUNK_READS - 1) / CHUNK_READS;
+    std::atomic<int> err{0};
+    // pass 1: check everything, write nothing
+    parallel_chunks(n_chunks, w->threads, [&](uint64_t c) {
+        try {
+            ReadInfo r1, r2;
+            const uint64_t a = c * CHUNK_READS, e = std::min(n_reads, a + CHUNK_READS);
+            if (int rc = check_range(ref, b, a, e, r1, r2)) set_error(err, rc);
+        } catch (const std::bad_alloc &) {
+            set_error(err, MICA_ENOMEM);
+        }
+    });
+    if (int rc = err.load()) return rc;
+    // pass 2: format windows of chunks in parallel into one half of a double
+    // buffer while a writer thread writes the previous window from the other
+    try {
+        const uint64_t window = (uint64_t)w->threads * 4;
+        if (w->bufs.size() < 2 * window) w->bufs.resize(2 * window);
+        std::thread writer;
+        std::atomic<bool> write_ok{true};
+        auto write_window = [&](uint64_t half, uint64_t nw) {
+            for (uint64_t j = 0; j < nw; j++) {
+                const std::string &buf = w->bufs[half * window + j];
+                if (fwrite(buf.data(), 1, buf.size(), w->f) != buf.size()) {
+                    write_ok = false;
+                    return;
+                }
+            }
+        };
+        auto join_writer = [&]() {
+            if (writer.joinable()) writer.join();
+        };
+        for (uint64_t c0 = 0, k = 0; c0 < n_chunks; c0 += window, k++) {
+            const uint64_t nw = std::min(window, n_chunks - c0), half = k & 1;
+            parallel_chunks(nw, w->threads, [&](uint64_t j) {
+                try {
+                    ReadInfo r1, r2;
+                    const uint64_t a = (c0 + j) * CHUNK_READS, e = std::min(n_reads, a + CHUNK_READS);
+                    std::string &buf = w->bufs[half * window + j];
+                    buf.clear();
+                    Formatter out{buf, ref, w->prefix, w->secondary != 0};
+                    format_range(out, b, a, e, w->next_id + (pairs ? a / 2 : a), r1, r2);
+                } catch (const std::bad_alloc &) {
+                    set_error(err, MICA_ENOMEM);
+                }
+            });
+            join_writer();
+            if (!write_ok) return MICA_EIO;
+            if (int rc = err.load()) return rc;
+            try {
+                writer = std::thread(write_window, half, nw);
+            } catch (const std::system_error &) {
+                write_window(half, nw);   // no thread to spare: write here
+            }
+        }
+        join_writer();
+        if (!write_ok) return MICA_EIO;
+    } catch (const std::bad_alloc &) {
+        return MICA_ENOMEM;
+    }
+    if (!b.rb) w->next_id += pairs ? n_reads / 2 : n_reads;
+    return 0;
+}
+
 
 }  // namespace
 }  // namespace mica
@@ -512,70 +636,19 @@ int mica_sam_write(mica_sam_writer *w, const uint32_t *packed_reads, const uint6
     if (n_reads == 0) return 0;
     if (!packed_reads || !word_offsets || !lengths || !total || !offsets) return MICA_EINVAL;
     if (pairs && (n_reads & 1)) return MICA_EINVAL;
-    const mica_reference &ref = *w->ref;
-    const Batch b{packed_reads, word_offsets, lengths, total, offsets, hits, pairs, n_reads};
-    const uint64_t n_chunks = (n_reads + CHUNK_READS - 1) / CHUNK_READS;
-    std::atomic<int> err{0};
-    // pass 1: check everything, write nothing
-    parallel_chunks(n_chunks, w->threads, [&](uint64_t c) {
-        try {
-            ReadInfo r1, r2;
-            const uint64_t a = c * CHUNK_READS, e = std::min(n_reads, a + CHUNK_READS);
-            if (int rc = check_range(ref, b, a, e, r1, r2)) set_error(err, rc);
-        } catch (const std::bad_alloc &) {
-            set_error(err, MICA_ENOMEM);
-        }
-    });
-    if (int rc = err.load()) return rc;
-    // pass 2: format windows of chunks in parallel into one half of a double
-    // buffer while a writer thread writes the previous window from the other
-    try {
-        const uint64_t window = (uint64_t)w->threads * 4;
-        if (w->bufs.size() < 2 * window) w->bufs.resize(2 * window);
-        std::thread writer;
-        std::atomic<bool> write_ok{true};
-        auto write_window = [&](uint64_t half, uint64_t nw) {
-            for (uint64_t j = 0; j < nw; j++) {
-                const std::string &buf = w->bufs[half * window + j];
-                if (fwrite(buf.data(), 1, buf.size(), w->f) != buf.size()) {
-                    write_ok = false;
-                    return;
-                }
-            }
-        };
-        auto join_writer = [&]() {
-            if (writer.joinable()) writer.join();
-        };
-        for (uint64_t c0 = 0, k = 0; c0 < n_chunks; c0 += window, k++) {
-            const uint64_t nw = std::min(window, n_chunks - c0), half = k & 1;
-            parallel_chunks(nw, w->threads, [&](uint64_t j) {
-                try {
-                    ReadInfo r1, r2;
-                    const uint64_t a = (c0 + j) * CHUNK_READS, e = std::min(n_reads, a + CHUNK_READS);
-                    std::string &buf = w->bufs[half * window + j];
-                    buf.clear();
-                    Formatter out{buf, ref, w->prefix, w->secondary != 0};
-                    format_range(out, b, a, e, w->next_id + (pairs ? a / 2 : a), r1, r2);
-                } catch (const std::bad_alloc &) {
-                    set_error(err, MICA_ENOMEM);
-                }
-            });
-            join_writer();
-            if (!write_ok) return MICA_EIO;
-            if (int rc = err.load()) return rc;
-            try {
-                writer = std::thread(write_window, half, nw);
-            } catch (const std::system_error &) {
-                write_window(half, nw);   // no thread to spare: write here
-            }
-        }
-        join_writer();
-        if (!write_ok) return MICA_EIO;
-    } catch (const std::bad_alloc &) {
-        return MICA_ENOMEM;
-    }
-    w->next_id += pairs ? n_reads / 2 : n_reads;
-    return 0;
+    return write_records(w, Batch{packed_reads, word_offsets, lengths, total, offsets, hits, pairs, n_reads, nullptr,
+                                  pairs != nullptr});
+}
+
+int mica_sam_write_batch(mica_sam_writer *w, const mica_read_batch *b, const uint64_t *total,
+                         const uint64_t *offsets, const mica_hit *hits, const mica_pair *pairs)
+{
+    if (!w || !b) return MICA_EINVAL;
+    const uint64_t n = b->n();
+    if (n == 0) return 0;
+    if (!total || !offsets || (pairs && !b->paired)) return MICA_EINVAL;
+    return write_records(w, Batch{b->words.data(), b->word_off.data(), b->len.data(), total, offsets, hits, pairs, n, b,
+                                  b->paired});
 }
 
 int mica_sam_close(mica_sam_writer *w)

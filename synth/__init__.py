@@ -516,3 +516,45 @@ def to_fasta(contigs, names, width: int = 60, crlf: bool = False) -> bytes:
         for a in range(0, len(seq), width):
             parts.append(seq[a:a + width] + nl)
     return b"".join(parts)
+
+
+# --------------------------------------------------------------------------
+# Reads as FASTQ text
+# --------------------------------------------------------------------------
+
+SEED_FASTQ = 71
+
+
+def to_fastq(batch: ReadBatch, *, n_frac: float = 0.3, max_n: int = 3, lower_frac: float = 0.1,
+             mate_suffix: bool = False, crlf: bool = False, seed: int = SEED_FASTQ) -> tuple:
+    """FASTQ text of a batch as a sequencer writes it: names with a comment
+    after a space, qualities in '!'..'J', a fraction ``n_frac`` of reads with
+    1..``max_n`` bases turned into N (or another IUPAC code), and a fraction
+    ``lower_frac`` of reads in lower case.  With ``mate_suffix``, reads 2i and
+    2i + 1 are written to two texts as "/1" and "/2" mates of one name.
+    Returns (texts, ambiguous offsets per read, qualities per read)."""
+    rng = _rng(seed)
+    nl = b"\r\n" if crlf else b"\n"
+    texts = [[], []] if mate_suffix else [[]]
+    amb, quals = [], []
+    for i in range(batch.n):
+        seq = bytearray(ACGT[batch.read(i)].tobytes())
+        m = len(seq)
+        pos = []
+        if rng.random() < n_frac:
+            pos = sorted(rng.choice(m, size=int(rng.integers(1, max_n + 1)), replace=False).tolist())
+            for j in pos:
+                seq[j] = IUPAC_AMBIGUOUS[int(rng.integers(0, len(IUPAC_AMBIGUOUS)))] if rng.random() < 0.2 else ord("N")
+        if rng.random() < lower_frac:
+            seq = bytearray(bytes(seq).lower())
+        q = bytes(rng.integers(33, 75, size=m, dtype=np.uint8))
+        amb.append(pos)
+        quals.append(q.decode())
+        if mate_suffix:
+            name = f"frag{i // 2}/{i % 2 + 1}".encode()
+            out = texts[i % 2]
+        else:
+            name = f"read{i}".encode()
+            out = texts[0]
+        out.append(b"@" + name + b" lane=1" + nl + bytes(seq) + nl + b"+" + nl + q + nl)
+    return [b"".join(t) for t in texts], amb, quals

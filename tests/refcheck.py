@@ -96,3 +96,20 @@ def contig_hamming_hits(contigs, read: np.ndarray, k: int) -> list:
                 out.append((base + pos, strand, d))
         base += len(seq)
     return sorted(out)
+
+
+def hamming_hits_n(g: np.ndarray, read: np.ndarray, k: int) -> list:
+    """Sorted [(pos, strand, d)] for a read whose ambiguous bases are coded
+    255: such a base equals no genome base on either strand."""
+    p = np.asarray(read, dtype=np.int16)
+    rcp = np.where(p == 255, 255, 3 - p)[::-1]
+    m = len(p)
+    if m > len(g):
+        return []
+    w = windows(g, m).astype(np.int16)
+    out = []
+    for strand, q in ((0, p), (1, rcp)):
+        d = (w != q[None, :]).sum(axis=1)
+        for pos in np.flatnonzero(d <= k):
+            out.append((int(pos), strand, int(d[pos])))
+    return sorted(out)

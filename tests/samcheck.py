@@ -30,15 +30,27 @@ def _oriented(codes: list, strand: int) -> list:
 
 
 class _Read:
-    def __init__(self, batch, result, i, starts, runs):
+    """rec = (name, qualities, ambiguous offsets, k) for a read from FASTQ."""
+
+    def __init__(self, batch, result, i, starts, runs, text, rec=None):
         self.codes = _codes(batch, i)
         self.m = len(self.codes)
+        self.name, self.qual = (rec[0], rec[1]) if rec else (None, None)
+        self.amb = set(rec[2]) if rec else set()
+        kmax = rec[3] if rec else 3
         listed = result.as_tuples(i)
         total = int(result.total[i])
-        self.listed = listed
         self.V = []
-        for pos, strand, d in listed:
-            if oracle.on_reference(pos, self.m, starts, runs):
+        raws = []
+        for pos, strand, mm in listed:
+            raw, d = mm, mm
+            if self.amb:
+                ori = _oriented(self.codes, strand)
+                offs = [self.m - 1 - j if strand else j for j in range(self.m)]
+                raw = sum(1 for j in range(self.m) if text[pos + j] != ACGT[ori[j]])
+                d = sum(1 for j in range(self.m) if text[pos + j] != ACGT[ori[j]] or offs[j] in self.amb)
+            raws.append(raw)
+            if oracle.on_reference(pos, self.m, starts, runs) and d <= kmax:
                 c = max(j for j in range(len(starts) - 1) if starts[j] <= pos)
                 self.V.append((pos, strand, d, c, pos - starts[c]))
         self.primary = None
@@ -52,16 +64,23 @@ class _Read:
         self.primary = next(v for v in self.V if v[2] == dmin)
         self.c0 = sum(1 for v in self.V if v[2] == dmin)
         self.c1 = sum(1 for v in self.V if v[2] == dmin + 1)
-        unique = self.c0 == 1 and (self.complete or any(h[2] > dmin for h in listed))
+        # the cap cut the search's highest d first
+        unique = self.c0 == 1 and (self.complete or any(r > dmin for r in raws))
         if unique:
-            sure = self.c1 == 0 and (self.complete or any(h[2] > dmin + 1 for h in listed))
+            sure = self.c1 == 0 and (self.complete or any(r > dmin + 1 for r in raws))
             self.mapq = 37 if sure else 25
 
+    def seq(self, strand):
+        s = "".join("N" if (self.m - 1 - j if strand else j) in self.amb else ACGT[c]
+                    for j, c in enumerate(_oriented(self.codes, strand)))
+        q = "*" if self.qual is None else (self.qual[::-1] if strand else self.qual)
+        return s, q
 
-def _md(read_codes: list, window: str) -> str:
+
+def _md(seq: str, window: str) -> str:
     out, run = [], 0
-    for c, g in zip(read_codes, window):
-        if ACGT[c] == g:
+    for c, g in zip(seq, window):
+        if c == g:
             run += 1
         else:
             out.append(f"{run}{g}")
@@ -70,19 +89,21 @@ def _md(read_codes: list, window: str) -> str:
 
 
 def sam_text(names, starts, runs, text: str, batch, result, pairs=None, prefix: str = "r",
-             secondary: bool = False, command_line: str | None = None, first_id: int = 0) -> str:
-    """The whole SAM file (header and records) as a string."""
+             secondary: bool = False, command_line: str | None = None, first_id: int = 0,
+             records=None) -> str:
+    """The whole SAM file (header and records) as a string; records: per
+    read (name, qualities, ambiguous offsets, k) for a batch from FASTQ."""
     lines = ["@HD\tVN:1.6\tSO:unsorted"]
     for j, name in enumerate(names):
         lines.append(f"@SQ\tSN:{name}\tLN:{starts[j + 1] - starts[j]}")
     pg = "@PG\tID:mica-gb300\tPN:mica-gb300\tVN:1.0"
     lines.append(pg + (f"\tCL:{command_line}" if command_line else ""))
     n = len(batch.lengths)
-    reads = [_Read(batch, result, i, starts, runs) for i in range(n)]
+    reads = [_Read(batch, result, i, starts, runs, text, records[i] if records else None) for i in range(n)]
 
     def match_tags(r, v):
         pos, strand, d = v[0], v[1], v[2]
-        return [f"NM:i:{d}", "MD:Z:" + _md(_oriented(r.codes, strand), text[pos:pos + r.m])]
+        return [f"NM:i:{d}", "MD:Z:" + _md(r.seq(strand)[0], text[pos:pos + r.m])]
 
     def record(qname, flag, r, v, mapq, here, mate, tlen):
         # here / mate: (contig, pos1) or None
@@ -92,13 +113,13 @@ def sam_text(names, starts, runs, text: str, batch, result, pairs=None, prefix: 
             rnext, pnext = "*", 0
         else:
             rnext, pnext = ("=" if here and mate[0] == here[0] else names[mate[0]]), mate[1]
+        if r.name is not None:
+            qname = r.name
         if v is None:
-            fields = [qname, flag | 4, rname, pos1, 0, "*", rnext, pnext, tlen,
-                      "".join(ACGT[c] for c in r.codes), "*"]
+            fields = [qname, flag | 4, rname, pos1, 0, "*", rnext, pnext, tlen, *r.seq(0)]
             return "\t".join(map(str, fields))
         flag |= 16 if v[1] else 0
-        fields = [qname, flag, rname, pos1, mapq, f"{r.m}M", rnext, pnext, tlen,
-                  "".join(ACGT[c] for c in _oriented(r.codes, v[1])), "*"]
+        fields = [qname, flag, rname, pos1, mapq, f"{r.m}M", rnext, pnext, tlen, *r.seq(v[1])]
         fields += match_tags(r, v) + [f"X0:i:{r.c0}", f"X1:i:{r.c1}", f"ZT:i:{r.zt}"]
         return "\t".join(map(str, fields))
 
@@ -115,7 +136,8 @@ def sam_text(names, starts, runs, text: str, batch, result, pairs=None, prefix: 
             else:
                 rnext, pnext = ("=" if mate[0] == here[0] else names[mate[0]]), mate[1]
             f = flag | 256 | (16 if s[1] else 0)
-            fields = [qname, f, names[s[3]], s[4] + 1, 0, f"{r.m}M", rnext, pnext, 0, "*", "*"]
+            q = r.name if r.name is not None else qname
+            fields = [q, f, names[s[3]], s[4] + 1, 0, f"{r.m}M", rnext, pnext, 0, "*", "*"]
             out.append("\t".join(map(str, fields + match_tags(r, s))))
         return out
 
@@ -172,3 +194,8 @@ def pairs_array(tuples, dtype) -> np.ndarray:
     for i, (nc, nb, pp, pm, mate, mm) in enumerate(tuples):
         out[i] = (nc, nb, pp, pm, mate, mm, 0)
     return out
+
+
+def no_pairs(n_pairs: int, dtype) -> np.ndarray:
+    """Pairing rows with no concordant placement (mates written as pairs)."""
+    return np.zeros(n_pairs, dtype=dtype)
