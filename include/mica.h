@@ -464,7 +464,9 @@ int mica_fastq_open(const char *path1, const char *path2, mica_fastq **out);
    at least 2), each with budget k.  *out = a batch of 0 reads at the end of
    the file(s).  MICA_EIO on a malformed record, names of mates that differ,
    or files of mates of different lengths; MICA_EINVAL on a read of length 0
-   or above MICA_MAX_READ_LEN, or k > MICA_MAX_K. */
+   or above MICA_MAX_READ_LEN, or k > MICA_MAX_K; after an error the
+   reader's position is unspecified (close it).  Records are checked and
+   packed on all host threads. */
 int mica_fastq_read(mica_fastq *fq, uint64_t max_reads, uint8_t k, mica_read_batch **out);
 void mica_fastq_close(mica_fastq *fq);
 

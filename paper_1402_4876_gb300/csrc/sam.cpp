@@ -22,6 +22,7 @@
 #include <thread>
 #include <vector>
 
+#include "host_parallel.h"
 #include "read_batch_internal.h"
 #include "reference_internal.h"
 
@@ -40,7 +41,6 @@ namespace {
 
 constexpr const char *ACGT = "ACGT";
 constexpr uint64_t CHUNK_READS = 4096;   // even: a pair never straddles two chunks
-constexpr uint32_t MAX_THREADS = 256;
 
 struct Placement {
     const mica_hit *h;
@@ -468,25 +468,6 @@ void format_range(Formatter &out, const Batch &b, uint64_t a, uint64_t e, uint64
     }
 }
 
-// Runs f(c) for c = 0..n-1 on up to `threads` host threads (the caller's
-// among them).  f must not throw.
-template <typename F> void parallel_chunks(uint64_t n, unsigned threads, F f)
-{
-    std::atomic<uint64_t> next{0};
-    auto worker = [&]() {
-        for (uint64_t c; (c = next.fetch_add(1, std::memory_order_relaxed)) < n;) f(c);
-    };
-    const unsigned t = (unsigned)std::min<uint64_t>(threads, n);
-    std::vector<std::thread> pool;
-    try {
-        pool.reserve(t);
-        for (unsigned i = 1; i < t; i++) pool.emplace_back(worker);
-    } catch (...) {   // fewer threads than asked: the started ones and this one finish the work
-    }
-    worker();
-    for (auto &th : pool) th.join();
-}
-
 inline void set_error(std::atomic<int> &err, int rc)
 {
     int none = 0;
@@ -590,7 +571,7 @@ int mica_sam_open(const char *path, const mica_reference *ref, const mica_sam_pa
     mica_sam_params_default(&p);
     if (params) p = *params;
     const std::string prefix = p.qname_prefix ? p.qname_prefix : "r";
-    if (prefix.size() > 200 || p.secondary > 1 || p.threads > MAX_THREADS) return MICA_EINVAL;
+    if (prefix.size() > 200 || p.secondary > 1 || p.threads > MAX_HOST_THREADS) return MICA_EINVAL;
     for (char c : prefix)   // QNAME: printable, no '@'
         if ((unsigned char)c < 33 || (unsigned char)c > 126 || c == '@') return MICA_EINVAL;
     if (p.command_line && strpbrk(p.command_line, "\t\n\r")) return MICA_EINVAL;
@@ -599,8 +580,7 @@ int mica_sam_open(const char *path, const mica_reference *ref, const mica_sam_pa
         w->ref = ref;
         w->prefix = prefix;
         w->secondary = p.secondary;
-        w->threads = p.threads ? p.threads : std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(),
-                                                                              MAX_THREADS));
+        w->threads = p.threads ? p.threads : host_threads();
         std::string s = "@HD\tVN:1.6\tSO:unsorted\n";
         for (size_t i = 0; i < ref->names.size(); i++) {
             s += "@SQ\tSN:";
