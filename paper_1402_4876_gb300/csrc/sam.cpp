@@ -26,6 +26,53 @@
 #include "read_batch_internal.h"
 #include "reference_internal.h"
 
+namespace mica {
+
+// Formatted records of one chunk: bytes [0, n) of data.  Room for a whole
+// record is made before it is written (begin), so the writes themselves go
+// through a plain cursor.
+struct Out {
+    std::vector<char> data;
+    size_t n = 0;
+    char *p = nullptr;
+
+    void begin(size_t room)
+    {
+        if (data.size() < n + room) data.resize(std::max(n + room, 2 * data.size()));
+        p = data.data() + n;
+    }
+    void end() { n = (size_t)(p - data.data()); }
+    void put(char c) { *p++ = c; }
+    void put(const char *s, size_t len)
+    {
+        memcpy(p, s, len);
+        p += len;
+    }
+    template <size_t L> void lit(const char (&s)[L]) { put(s, L - 1); }
+    void put(const std::string &s) { put(s.data(), s.size()); }
+    void u64(uint64_t v)
+    {
+        char t[24];
+        int k = 0;
+        do {
+            t[k++] = (char)('0' + v % 10);
+            v /= 10;
+        } while (v);
+        while (k) *p++ = t[--k];
+    }
+    void i64(int64_t v)
+    {
+        if (v < 0) {
+            put('-');
+            u64((uint64_t)(-(v + 1)) + 1);
+        } else {
+            u64((uint64_t)v);
+        }
+    }
+};
+
+}  // namespace mica
+
 struct mica_sam_writer {
     FILE *f = nullptr;
     const mica_reference *ref = nullptr;
@@ -33,7 +80,8 @@ struct mica_sam_writer {
     uint32_t secondary = 0;
     uint32_t threads = 1;
     uint64_t next_id = 0;          // number of the next read, or of the next pair
-    std::vector<std::string> bufs; // one per chunk of a formatting window, kept across calls
+    std::vector<mica::Out> bufs;   // one per chunk of a formatting window, kept across calls
+    size_t name_room = 0;          // the longest contig name
 };
 
 namespace mica {
@@ -52,9 +100,14 @@ struct Placement {
 // One read of the batch as the records need it.
 struct ReadInfo {
     uint32_t m = 0;
-    uint8_t codes[MICA_MAX_READ_LEN];
-    uint8_t amb[MICA_MAX_READ_LEN];   // 1: an ambiguous base (a substitution wherever it falls)
+    // the read as the window of a hit on strand s reads it: bases[s][j] is
+    // the base at window offset j ('A'..'T', stand-ins for ambiguous bases)
+    // and ambo[s][j] = 1 where that base is ambiguous (a substitution
+    // wherever it falls); s = 1 is the reverse complement
+    char bases[2][MICA_MAX_READ_LEN + 16];   // + room for whole-word decoding
+    uint8_t ambo[2][MICA_MAX_READ_LEN];
     bool has_amb = false;
+    bool ambo_clear = false;   // ambo holds zeros for the whole read length
     const char *name = nullptr;       // from a read batch, else NULL
     const char *qual = nullptr;
     uint64_t b = 0, e = 0;          // listed hits [b, e)
@@ -67,12 +120,21 @@ struct ReadInfo {
     uint64_t total_ref = 0;
 };
 
-// The read's base on `strand` at offset j of the matched window (the reverse
-// complement for the - strand).
-inline uint8_t oriented(const ReadInfo &r, int strand, uint32_t j)
-{
-    return strand == 0 ? r.codes[j] : (uint8_t)(3 - r.codes[r.m - 1 - j]);
-}
+// The four bases of one byte of a packed word (least significant first) as
+// ASCII, and their complements in reverse order, four bytes each.
+struct DecodeTable {
+    char fwd[256][4], rc[256][4];
+    DecodeTable()
+    {
+        for (int v = 0; v < 256; v++)
+            for (int t = 0; t < 4; t++) {
+                const int c = (v >> (2 * t)) & 3;
+                fwd[v][t] = ACGT[c];
+                rc[v][3 - t] = ACGT[3 - c];
+            }
+    }
+};
+const DecodeTable DECODE;
 
 // The read offset at window offset j (the - strand runs backwards).
 inline uint32_t read_offset(const ReadInfo &r, int strand, uint32_t j) { return strand ? r.m - 1 - j : j; }
@@ -82,11 +144,14 @@ inline uint32_t read_offset(const ReadInfo &r, int strand, uint32_t j) { return 
 void substitutions(const mica_reference &ref, const ReadInfo &r, uint64_t pos, int strand, uint32_t *raw,
                    uint32_t *dprime)
 {
+    const uint8_t *t = ref.text.data() + pos;
+    const char *s = r.bases[strand];
+    const uint8_t *am = r.ambo[strand];
     uint32_t a = 0, b = 0;
     for (uint32_t j = 0; j < r.m; j++) {
-        const bool mism = ref.text[pos + j] != (uint8_t)ACGT[oriented(r, strand, j)];
+        const uint32_t mism = t[j] != (uint8_t)s[j];
         a += mism;
-        b += mism || r.amb[read_offset(r, strand, j)];
+        b += mism | am[j];
     }
     *raw = a;
     *dprime = b;
@@ -118,16 +183,33 @@ int classify(const mica_reference &ref, const Batch &bt, uint64_t i, bool check,
         word_off[i + 1] - word_off[i] < (r.m + 15u) / 16u)
         return MICA_EINVAL;
     const uint32_t *w = bt.words + word_off[i];
-    for (uint32_t j = 0; j < r.m; j++) {
-        r.codes[j] = (uint8_t)((w[j >> 4] >> (2 * (j & 15))) & 3);
-        r.amb[j] = 0;
+    const uint32_t m = r.m;
+    // forward: 4 bases per byte; reverse complement: the same bytes from
+    // the last base backwards (written right to left into a padded array)
+    const uint32_t nbytes = (m + 3) / 4;
+    char *rc_end = r.bases[1] + 4 * nbytes;   // rc of bases [0, 4 * nbytes), its last 4*nbytes - m are padding
+    for (uint32_t q = 0; q < nbytes; q++) {
+        const uint8_t byte = (uint8_t)(w[q >> 2] >> (8 * (q & 3)));
+        memcpy(r.bases[0] + 4 * q, DECODE.fwd[byte], 4);
+        memcpy(rc_end - 4 * (q + 1), DECODE.rc[byte], 4);
+    }
+    // the rc of the padded read starts with 4 * nbytes - m padding bases
+    if (4 * nbytes != m) memmove(r.bases[1], r.bases[1] + (4 * nbytes - m), m);
+    if (!r.ambo_clear || r.has_amb) {
+        memset(r.ambo[0], 0, MICA_MAX_READ_LEN);
+        memset(r.ambo[1], 0, MICA_MAX_READ_LEN);
+        r.ambo_clear = true;
     }
     r.has_amb = false;
     uint32_t kmax = MICA_MAX_K;
     if (bt.rb) {
         const mica_read_batch &rb = *bt.rb;
-        for (uint64_t a = rb.amb_off[i]; a < rb.amb_off[i + 1]; a++) r.amb[rb.amb[a]] = 1;
+        for (uint64_t a = rb.amb_off[i]; a < rb.amb_off[i + 1]; a++) {
+            r.ambo[0][rb.amb[a]] = 1;
+            r.ambo[1][m - 1 - rb.amb[a]] = 1;
+        }
         r.has_amb = rb.amb_off[i + 1] > rb.amb_off[i];
+        if (r.has_amb) r.ambo_clear = false;
         r.name = rb.names.c_str() + rb.name_off[i];
         r.qual = rb.quals.data() + rb.qual_off[i];
         kmax = rb.k[i];
@@ -203,30 +285,33 @@ inline void put_u64(std::string &s, uint64_t v)
     while (n) s.push_back(t[--n]);
 }
 
-inline void put_i64(std::string &s, int64_t v)
+void put_md(Out &o, const mica_reference &ref, const ReadInfo &r, uint64_t pos, int strand)
 {
-    if (v < 0) {
-        s.push_back('-');
-        put_u64(s, (uint64_t)(-(v + 1)) + 1);
-    } else {
-        put_u64(s, (uint64_t)v);
-    }
-}
-
-void put_md(std::string &s, const mica_reference &ref, const ReadInfo &r, uint64_t pos, int strand)
-{
+    const uint8_t *t = ref.text.data() + pos;
+    const char *s = r.bases[strand];
+    const uint8_t *am = r.ambo[strand];
     uint64_t run = 0;
-    for (uint32_t j = 0; j < r.m; j++) {
-        const uint8_t g = ref.text[pos + j];
-        if (!r.amb[read_offset(r, strand, j)] && g == (uint8_t)ACGT[oriented(r, strand, j)]) {
+    for (uint32_t j = 0; j < r.m;) {
+        if (!r.has_amb && j + 8 <= r.m) {   // eight matching bases at a time
+            uint64_t x, y;
+            memcpy(&x, t + j, 8);
+            memcpy(&y, s + j, 8);
+            if (x == y) {
+                run += 8;
+                j += 8;
+                continue;
+            }
+        }
+        if (!am[j] && t[j] == (uint8_t)s[j]) {
             run++;
         } else {
-            put_u64(s, run);
-            s.push_back((char)g);
+            o.u64(run);
+            o.put((char)t[j]);
             run = 0;
         }
+        j++;
     }
-    put_u64(s, run);
+    o.u64(run);
 }
 
 // Where a read's primary record sits: its own primary placement, or (for an
@@ -246,70 +331,81 @@ inline Spot spot_of(const Placement *p)
     return s;
 }
 
-// Formats records into one buffer (one buffer per chunk of reads).
+// Formats records into one chunk's Out.
 struct Formatter {
-    std::string &buf;
+    Out &out;
     const mica_reference &ref;
     const std::string &prefix;
     bool secondary;
+    size_t name_room;   // the longest contig name
+
+    // An upper bound on one record's bytes: QNAME, two contig names, SEQ,
+    // QUAL, MD (at most 4 bytes per base and a run) and the fixed fields.
+    size_t room(const ReadInfo &r) const
+    {
+        const size_t qn = r.name ? strlen(r.name) : prefix.size() + 20;
+        return qn + 2 * name_room + 6 * (size_t)r.m + 320;
+    }
 
     void qname(uint64_t id, const ReadInfo &r)
     {
         if (r.name) {
-            buf += r.name;
+            out.put(r.name, strlen(r.name));
         } else {
-            buf += prefix;
-            put_u64(buf, id);
+            out.put(prefix);
+            out.u64(id);
         }
-        buf.push_back('\t');
+        out.put('\t');
     }
 
     void rname(int32_t contig)
     {
-        if (contig < 0) buf.push_back('*');
-        else buf += ref.names[contig];
-        buf.push_back('\t');
+        if (contig < 0) out.put('*');
+        else out.put(ref.names[contig]);
+        out.put('\t');
     }
 
     // RNEXT and PNEXT of a record at contig `self` whose mate sits at `mate`.
     void next(int32_t self, const Spot *mate)
     {
         if (!mate || mate->contig < 0) {
-            buf += "*\t0\t";
+            out.lit("*\t0\t");
             return;
         }
-        if (mate->contig == self) buf.push_back('=');
-        else buf += ref.names[mate->contig];
-        buf.push_back('\t');
-        put_u64(buf, mate->pos1);
-        buf.push_back('\t');
+        if (mate->contig == self) out.put('=');
+        else out.put(ref.names[mate->contig]);
+        out.put('\t');
+        out.u64(mate->pos1);
+        out.put('\t');
     }
 
     // SEQ and QUAL on the forward strand of the reference
     void seq(const ReadInfo &r, int strand)
     {
-        size_t o = buf.size();
-        buf.resize(o + r.m);
-        char *d = &buf[o];
-        for (uint32_t j = 0; j < r.m; j++)
-            d[j] = r.amb[read_offset(r, strand, j)] ? 'N' : ACGT[oriented(r, strand, j)];
-        buf.push_back('\t');
+        char *d = out.p;
+        out.put(r.bases[strand], r.m);
+        if (r.has_amb)
+            for (uint32_t j = 0; j < r.m; j++)
+                if (r.ambo[strand][j]) d[j] = 'N';
+        out.put('\t');
         if (!r.qual) {
-            buf.push_back('*');
+            out.put('*');
             return;
         }
-        o = buf.size();
-        buf.resize(o + r.m);
-        d = &buf[o];
-        for (uint32_t j = 0; j < r.m; j++) d[j] = r.qual[read_offset(r, strand, j)];
+        if (strand == 0) {
+            out.put(r.qual, r.m);
+        } else {
+            for (uint32_t j = 0; j < r.m; j++) out.p[j] = r.qual[r.m - 1 - j];
+            out.p += r.m;
+        }
     }
 
     void match_tags(const ReadInfo &r, const Placement &p)
     {
-        buf += "\tNM:i:";
-        put_u64(buf, p.d);
-        buf += "\tMD:Z:";
-        put_md(buf, ref, r, p.h->pos, p.h->strand);
+        out.lit("\tNM:i:");
+        out.u64(p.d);
+        out.lit("\tMD:Z:");
+        put_md(out, ref, r, p.h->pos, p.h->strand);
     }
 
     // One primary record.  flag0: the pairing bits; mate = NULL for single reads.
@@ -317,34 +413,36 @@ struct Formatter {
                  const Spot *mate, int64_t tlen)
     {
         const uint32_t flag = flag0 | (p ? 0u : 4u) | (p && p->h->strand ? 16u : 0u);
+        out.begin(room(r));
         qname(id, r);
-        put_u64(buf, flag);
-        buf.push_back('\t');
+        out.u64(flag);
+        out.put('\t');
         rname(self.contig);
-        put_u64(buf, self.pos1);
-        buf.push_back('\t');
-        put_u64(buf, p ? (uint64_t)mapq : 0u);
-        buf.push_back('\t');
+        out.u64(self.pos1);
+        out.put('\t');
+        out.u64(p ? (uint64_t)mapq : 0u);
+        out.put('\t');
         if (p) {
-            put_u64(buf, r.m);
-            buf += "M\t";
+            out.u64(r.m);
+            out.lit("M\t");
         } else {
-            buf += "*\t";
+            out.lit("*\t");
         }
         next(self.contig, mate);
-        put_i64(buf, tlen);
-        buf.push_back('\t');
+        out.i64(tlen);
+        out.put('\t');
         seq(r, p ? p->h->strand : 0);
         if (p) {
             match_tags(r, *p);
-            buf += "\tX0:i:";
-            put_u64(buf, r.c0);
-            buf += "\tX1:i:";
-            put_u64(buf, r.c1);
-            buf += "\tZT:i:";
-            put_u64(buf, r.total_ref);
+            out.lit("\tX0:i:");
+            out.u64(r.c0);
+            out.lit("\tX1:i:");
+            out.u64(r.c1);
+            out.lit("\tZT:i:");
+            out.u64(r.total_ref);
         }
-        buf.push_back('\n');
+        out.put('\n');
+        out.end();
     }
 
     void secondaries(uint64_t id, uint32_t flag0, const ReadInfo &r, const Placement *p, const Spot *mate)
@@ -352,18 +450,20 @@ struct Formatter {
         if (!secondary) return;
         for (const Placement &s : r.V) {
             if (&s == p) continue;
+            out.begin(room(r));
             qname(id, r);
-            put_u64(buf, flag0 | 256u | (s.h->strand ? 16u : 0u));
-            buf.push_back('\t');
+            out.u64(flag0 | 256u | (s.h->strand ? 16u : 0u));
+            out.put('\t');
             rname(s.contig);
-            put_u64(buf, (uint64_t)s.local + 1);
-            buf += "\t0\t";
-            put_u64(buf, r.m);
-            buf += "M\t";
+            out.u64((uint64_t)s.local + 1);
+            out.lit("\t0\t");
+            out.u64(r.m);
+            out.lit("M\t");
             next(s.contig, mate);
-            buf += "0\t*\t*";
+            out.lit("0\t*\t*");
             match_tags(r, s);
-            buf.push_back('\n');
+            out.put('\n');
+            out.end();
         }
     }
 };
@@ -502,8 +602,8 @@ int write_records(mica_sam_writer *w, const Batch &b)
         std::atomic<bool> write_ok{true};
         auto write_window = [&](uint64_t half, uint64_t nw) {
             for (uint64_t j = 0; j < nw; j++) {
-                const std::string &buf = w->bufs[half * window + j];
-                if (fwrite(buf.data(), 1, buf.size(), w->f) != buf.size()) {
+                const Out &o = w->bufs[half * window + j];
+                if (fwrite(o.data.data(), 1, o.n, w->f) != o.n) {
                     write_ok = false;
                     return;
                 }
@@ -518,9 +618,9 @@ int write_records(mica_sam_writer *w, const Batch &b)
                 try {
                     ReadInfo r1, r2;
                     const uint64_t a = (c0 + j) * CHUNK_READS, e = std::min(n_reads, a + CHUNK_READS);
-                    std::string &buf = w->bufs[half * window + j];
-                    buf.clear();
-                    Formatter out{buf, ref, w->prefix, w->secondary != 0};
+                    Out &o = w->bufs[half * window + j];
+                    o.n = 0;
+                    Formatter out{o, ref, w->prefix, w->secondary != 0, w->name_room};
                     format_range(out, b, a, e, w->next_id + (pairs ? a / 2 : a), r1, r2);
                 } catch (const std::bad_alloc &) {
                     set_error(err, MICA_ENOMEM);
@@ -581,6 +681,7 @@ int mica_sam_open(const char *path, const mica_reference *ref, const mica_sam_pa
         w->prefix = prefix;
         w->secondary = p.secondary;
         w->threads = p.threads ? p.threads : host_threads();
+        for (const std::string &name : ref->names) w->name_room = std::max(w->name_room, name.size());
         std::string s = "@HD\tVN:1.6\tSO:unsorted\n";
         for (size_t i = 0; i < ref->names.size(); i++) {
             s += "@SQ\tSN:";
