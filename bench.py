@@ -310,6 +310,7 @@ def run_ours(args):
     gc_idx = out["roofline"]["gather_ceiling"]["index_sized_gbs"]
     out["roofline"]["frac_of_gather_ceiling"] = round(achieved / gc_idx, 4) if gc_idx else None
     out["rank_blocks_per_s"] = round(st["rank_blocks"] / kernel_s, 1)
+    out["mbp_per_s"] = round(value * float(np.mean(b.lengths)) / 1e6, 1)   # bases of reads aligned
 
     if not args.no_plain:
         # the same exhaustive search without lower-bound pruning (same result, more work)
