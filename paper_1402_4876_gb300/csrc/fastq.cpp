@@ -9,7 +9,9 @@
 // A batch is read in two steps: the file is read in large blocks whose line
 // ends are found on all host threads, and cut into records (one thread,
 // over those offsets); then the records are checked and packed in chunks on
-// all host threads and the chunks joined in file order.
+// all host threads and the chunks joined in file order.  After a full batch
+// a background thread reads and indexes about as many bytes again, so that
+// the reading overlaps whatever the caller does with the batch.
 #include <algorithm>
 #include <cstddef>
 #include <cstdint>
@@ -19,6 +21,8 @@
 #include <memory>
 #include <new>
 #include <string>
+#include <system_error>
+#include <thread>
 #include <vector>
 
 #include "host_parallel.h"
@@ -302,7 +306,35 @@ struct mica_fastq {
     bool paired = false;
     uint64_t next_read = 0;   // number of the next read of the file(s)
     std::vector<mica::Span> spans[2];
+    // reads and indexes the next batch's bytes while the caller works on the
+    // last batch; joined before the inputs are touched again
+    std::thread ahead;
+
+    void join_ahead()
+    {
+        if (ahead.joinable()) ahead.join();
+    }
+    ~mica_fastq() { join_ahead(); }
 };
+
+namespace mica {
+namespace {
+
+// Fills each input until it holds `bytes` unconsumed bytes (or its end).
+void read_ahead(mica_fastq *fq, size_t bytes)
+{
+    try {
+        for (int i = 0; i < (fq->paired ? 2 : 1); i++) {
+            Input &in = fq->in[i];
+            while (in.size - in.base < bytes && in.fill()) {
+            }
+        }
+    } catch (...) {   // the next read meets the same condition itself
+    }
+}
+
+}  // namespace
+}  // namespace mica
 
 using namespace mica;
 
@@ -334,6 +366,7 @@ int mica_fastq_read(mica_fastq *fq, uint64_t max_reads, uint8_t k, mica_read_bat
     if (!fq || k > MICA_MAX_K) return MICA_EINVAL;
     if (fq->paired) max_reads &= ~1ull;
     if (max_reads < (fq->paired ? 2u : 1u)) return MICA_EINVAL;
+    fq->join_ahead();
     try {
         // step 1: cut records (per file: the reads, or the mates, of the batch)
         const int files = fq->paired ? 2 : 1;
@@ -363,8 +396,18 @@ int mica_fastq_read(mica_fastq *fq, uint64_t max_reads, uint8_t k, mica_read_bat
         std::unique_ptr<mica_read_batch> b(new mica_read_batch());
         b->paired = fq->paired;
         join_parts(*b, parts, k);
-        for (int i = 0; i < files; i++) fq->in[i].consume(pos[i]);
+        size_t used = 0;
+        for (int i = 0; i < files; i++) {
+            used = std::max(used, pos[i] - fq->in[i].base);
+            fq->in[i].consume(pos[i]);
+        }
         fq->next_read += b->n();
+        if (b->n() == max_reads) {   // likely more to come: read its bytes ahead
+            try {
+                fq->ahead = std::thread(read_ahead, fq, std::min<size_t>(used, size_t(1) << 30));
+            } catch (const std::system_error &) {
+            }
+        }
         *out = b.release();
         return 0;
     } catch (const std::bad_alloc &) {
