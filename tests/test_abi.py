@@ -73,3 +73,65 @@ def test_host_side_rejections_need_no_gpu():
     p = mica.AlignParams()
     lib.mica_align_params_default(ctypes.byref(p))
     assert p.report == 0 and p.prune == 1
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <stdlib.h>
+#include "mica.h"
+
+/* argv: reference FASTA, reads FASTQ, output SAM.  Host-only calls: every
+   read is written unmapped (an empty result). */
+int main(int argc, char **argv)
+{
+    mica_reference *ref = NULL;
+    mica_fastq *fq = NULL;
+    mica_read_batch *b = NULL;
+    mica_sam_writer *w = NULL;
+    mica_read_batch_view v;
+    mica_sam_params p;
+    uint64_t *total, *offsets;
+    if (argc != 4) return 9;
+    if (mica_reference_read_fasta(argv[1], &ref) != MICA_OK) return 1;
+    if (mica_fastq_open(argv[2], NULL, &fq) != MICA_OK) return 2;
+    if (mica_fastq_read(fq, 1000, 2, &b) != MICA_OK) return 3;
+    if (mica_read_batch_get_view(b, &v) != MICA_OK) return 4;
+    total = calloc(v.n_reads, sizeof(uint64_t));
+    offsets = calloc(v.n_reads + 1, sizeof(uint64_t));
+    mica_sam_params_default(&p);
+    if (mica_sam_open(argv[3], ref, &p, &w) != MICA_OK) return 5;
+    if (mica_sam_write_batch(w, b, total, offsets, NULL, NULL) != MICA_OK) return 6;
+    if (mica_sam_close(w) != MICA_OK) return 7;
+    printf("%llu %s\n", (unsigned long long)v.n_reads, mica_strerror(MICA_EIO));
+    free(total);
+    free(offsets);
+    mica_read_batch_free(b);
+    mica_fastq_close(fq);
+    mica_reference_free(ref);
+    return 0;
+}
+"""
+
+
+def test_c_program_uses_the_host_calls(lib, tmp_path):
+    """A C99 program compiled against include/mica.h and linked with the
+    library runs the host-only calls (FASTA, FASTQ, SAM) without a GPU."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "prog.c"
+    src.write_text(C_PROGRAM)
+    libdir = os.path.join(ROOT, "paper_1402_4876_gb300")
+    exe = tmp_path / "prog"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I" + os.path.join(ROOT, "include"), str(src),
+                    "-L" + libdir, "-lmica_gb300", "-Wl,-rpath," + libdir, "-o", str(exe)], check=True)
+    (tmp_path / "ref.fa").write_bytes(b">chrA\nACGTACGTNNACGT\n>chrB\nTTTTGGGG\n")
+    (tmp_path / "reads.fq").write_bytes(b"@q1 x\nACGTN\n+\nIIIII\n@q2\nGGGG\n+\n!!!!\n")
+    out = subprocess.run([str(exe), str(tmp_path / "ref.fa"), str(tmp_path / "reads.fq"), str(tmp_path / "o.sam")],
+                         capture_output=True, text=True, check=True)
+    assert out.stdout.split()[0] == "2"
+    lines = (tmp_path / "o.sam").read_text().splitlines()
+    assert lines[:3] == ["@HD\tVN:1.6\tSO:unsorted", "@SQ\tSN:chrA\tLN:14", "@SQ\tSN:chrB\tLN:8"]
+    assert lines[-2:] == ["q1\t4\t*\t0\t0\t*\t*\t0\t0\tACGTN\tIIIII", "q2\t4\t*\t0\t0\t*\t*\t0\t0\tGGGG\t!!!!"]
