@@ -136,9 +136,6 @@ struct DecodeTable {
 };
 const DecodeTable DECODE;
 
-// The read offset at window offset j (the - strand runs backwards).
-inline uint32_t read_offset(const ReadInfo &r, int strand, uint32_t j) { return strand ? r.m - 1 - j : j; }
-
 // Substitutions of the read on `strand` against G[pos, pos + m): *raw counts
 // the stand-in bases as bases, *dprime counts every ambiguous base.
 void substitutions(const mica_reference &ref, const ReadInfo &r, uint64_t pos, int strand, uint32_t *raw,
