@@ -135,3 +135,56 @@ def test_c_program_uses_the_host_calls(lib, tmp_path):
     lines = (tmp_path / "o.sam").read_text().splitlines()
     assert lines[:3] == ["@HD\tVN:1.6\tSO:unsorted", "@SQ\tSN:chrA\tLN:14", "@SQ\tSN:chrB\tLN:8"]
     assert lines[-2:] == ["q1\t4\t*\t0\t0\t*\t*\t0\t0\tACGTN\tIIIII", "q2\t4\t*\t0\t0\t*\t*\t0\t0\tGGGG\t!!!!"]
+
+
+class _IndexHeader(ctypes.Structure):
+    """The index file's leading header as the library writes it (version 3):
+    magic, version, q, sampling, the text's sizes and the short-suffix codes."""
+    _fields_ = [("magic", ctypes.c_char * 8), ("version", ctypes.c_uint32), ("kmer_q", ctypes.c_uint32),
+                ("sa_sample", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("n", ctypes.c_uint64),
+                ("dollar_row", ctypes.c_uint64), ("C", ctypes.c_uint64 * 5), ("n_occ_blocks", ctypes.c_uint64),
+                ("n_super", ctypes.c_uint64), ("n_mark_blocks", ctypes.c_uint64), ("n_samples", ctypes.c_uint64),
+                ("table_len", ctypes.c_uint64), ("nshort", ctypes.c_uint32), ("short_pad", ctypes.c_uint32 * 12),
+                ("short_len", ctypes.c_uint32 * 12)]
+
+
+def _consistent_header(n=1000, q=8, s=16):
+    h = _IndexHeader()
+    h.magic, h.version, h.kmer_q, h.sa_sample, h.n = b"MICAIDX1", 3, q, s, n
+    h.n_occ_blocks = (n + 1) // 96 + 1
+    h.n_super = (h.n_occ_blocks + 681) // 682
+    h.n_mark_blocks = (n + 1) // 480 + 1
+    h.n_samples = (n + 1) // s + 1
+    h.table_len = (1 << (2 * q)) + 1
+    h.nshort = min(q, n + 1)
+    return h
+
+
+@pytest.mark.parametrize("field,value", [
+    ("magic", b"MICAIDX9"), ("version", 4), ("kmer_q", 0), ("kmer_q", 13), ("sa_sample", 0),
+    ("n_occ_blocks", 5), ("n_super", 0), ("n_mark_blocks", 0), ("table_len", 17), ("n_samples", 2000),
+    ("nshort", 3), ("n", 1 << 32),
+])
+def test_index_file_header_checked_before_any_device_call(tmp_path, field, value):
+    """A malformed index header is MICA_EIO before the library touches a GPU."""
+    import paper_1402_4876_gb300 as mica
+    lib = mica.lib()
+    h = _consistent_header()
+    setattr(h, field, value)
+    path = tmp_path / "bad.mica"
+    path.write_bytes(bytes(h) + bytes(64))
+    out = ctypes.c_void_p()
+    assert lib.mica_index_load(str(path).encode(), 0, ctypes.byref(out)) == mica.MICA_EIO
+    # the unmodified header passes the checks: without a device the load then
+    # stops at the device call itself
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except Exception:
+        has_gpu = False
+    if not has_gpu:
+        path.write_bytes(bytes(_consistent_header()) + bytes(64))
+        assert lib.mica_index_load(str(path).encode(), 0, ctypes.byref(out)) == mica.MICA_ECUDA
+    for blob in (b"", b"MICAIDX1", bytes(h)[:40]):          # empty and truncated files
+        path.write_bytes(blob)
+        assert lib.mica_index_load(str(path).encode(), 0, ctypes.byref(out)) == mica.MICA_EIO
