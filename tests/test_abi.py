@@ -188,3 +188,23 @@ def test_index_file_header_checked_before_any_device_call(tmp_path, field, value
     for blob in (b"", b"MICAIDX1", bytes(h)[:40]):          # empty and truncated files
         path.write_bytes(blob)
         assert lib.mica_index_load(str(path).encode(), 0, ctypes.byref(out)) == mica.MICA_EIO
+
+
+def test_shape_table_and_defaults_need_no_gpu():
+    import paper_1402_4876_gb300 as mica
+    lib = mica.lib()
+    shapes = mica.tuning_shapes()
+    assert len(shapes) == lib.mica_tuning_shapes() >= 1
+    assert shapes[0] == (256, 8, 3)           # the default persistent shape
+    for stack, warps, min_ctas in shapes:
+        assert stack in (128, 256) and warps in (4, 8) and 1 <= min_ctas <= 8
+    a = ctypes.c_int()
+    assert lib.mica_tuning_shape_info(len(shapes), ctypes.byref(a), ctypes.byref(a), ctypes.byref(a)) \
+        == mica.MICA_EINVAL
+    sp = mica.ServerParams()
+    lib.mica_server_params_default(ctypes.byref(sp))
+    assert (sp.max_device_bytes, sp.max_tick_reads, sp.hit_cap, sp.kernel, sp.workers, sp.start_paused) == \
+        (0, 1 << 20, 1000, 0, 2, 0)
+    wp = mica.SamParams(b"x", 1, b"y", 7)
+    lib.mica_sam_params_default(ctypes.byref(wp))
+    assert (wp.qname_prefix, wp.secondary, wp.command_line, wp.threads) == (None, 0, None, 0)
