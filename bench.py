@@ -560,7 +560,7 @@ def cpu_baseline(g, b, stride: int = 20):
     fm = oracle.FMIndex(g.codes, "sais")                 # index build: not timed
     sub = b.subset(np.arange(0, b.n, stride))
     t = time.perf_counter()
-    fm.align(sub, cap=HIT_CAP, threads=cores)
+    res = fm.align(sub, cap=HIT_CAP, threads=cores)
     dt = time.perf_counter() - t
     one = sub.subset(np.arange(0, sub.n, 8))             # an eighth of the sample on one core
     t = time.perf_counter()
@@ -570,7 +570,9 @@ def cpu_baseline(g, b, stride: int = 20):
             "sample": f"{sub.n} of the {b.n} reads (every {stride}th), same genome; oracle index build "
                       f"(SA-IS) excluded; {dt:.1f} s wall", "cpu": model,
             "one_core": {"value": round(one.n / dt1, 1), "unit": "reads/s",
-                         "sample": f"every 8th read of that sample ({one.n} reads), {dt1:.1f} s wall"}}
+                         "sample": f"every 8th read of that sample ({one.n} reads), {dt1:.1f} s wall"},
+            "nodes_per_read": round(res.nodes / max(sub.n, 1), 1),   # plain backtracking, no table, no pruning
+            }
 
 
 def run_reference(args):
