@@ -33,6 +33,10 @@
  * owned by the library until the matching *_free call.  A mica_index is used
  * by one host thread at a time.  Device pointers are CUDA device addresses on
  * the index's device.  Base codes: A=0, C=1, G=2, T=3.
+ *
+ * Around the search, host-side layers read references (FASTA, several
+ * contigs, ambiguous bases) and reads (FASTQ), and write SAM; they make no
+ * CUDA call and work on machines without a GPU.
  */
 #ifndef MICA_H
 #define MICA_H
