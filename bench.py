@@ -500,8 +500,6 @@ def run_serve(args):
     100/150/250, k 0..2) arrive as a Poisson process at 50/70/90% of the
     sustained rate into the continuous-batching server; p50/p99 latency is
     submit to completion on the host clock."""
-    import threading
-
     import torch
     import paper_1402_4876_gb300 as mica
     dev = torch.device("cuda", 0)
