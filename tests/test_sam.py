@@ -6,6 +6,8 @@ reproduce the contig's own bytes at POS, FLAG 16 iff SEQ is the reverse
 complement of the read, one primary record per read, and mate fields that
 point at each other."""
 
+import os
+
 import numpy as np
 import pytest
 
@@ -256,3 +258,69 @@ def test_bad_read_in_a_late_chunk_writes_nothing(mica, setup, single, tmp_path):
         with pytest.raises(mica.MicaError):
             w.write(big, bres)
     assert all(line.startswith("@") for line in open(path).read().splitlines())
+
+
+def _handworked():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "handworked_sam.txt")
+    g = {"contig": [], "read": [], "sam": [], "pair": [], "psam": []}
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            key, rest = line.split(" ", 1)
+            g[key].append(rest)
+    return g
+
+
+def _result(entries, mica):
+    """(codes list, result) from 'bases total pos,strand,d ...' entries."""
+    codes, total, offsets, hits = [], [], [0], []
+    for e in entries:
+        parts = e.split()
+        codes.append(np.frombuffer(parts[0].encode(), np.uint8).copy())
+        total.append(int(parts[1]))
+        for h in parts[2:]:
+            p, s, d = h.split(",")
+            hits.append((int(p), 0 if s == "+" else 1, int(d), 0))
+        offsets.append(len(hits))
+    for c in codes:
+        c[:] = np.searchsorted(np.frombuffer(b"ACGT", np.uint8), c)
+    res = oracle.Result(np.array(total, np.uint64), np.array(offsets, np.uint64),
+                        np.array(hits, dtype=mica.HIT_DTYPE) if hits else np.zeros(0, mica.HIT_DTYPE))
+    return codes, res
+
+
+def test_handworked_records(mica, tmp_path):
+    """SAM records derived by hand from the SAM specification
+    (tests/golden/handworked_sam.txt): FLAG 99/147 and 73/133 pairs, TLEN,
+    MD with mismatches at the end and inside, a reverse-strand secondary, a
+    hit across a contig boundary left unmapped."""
+    g = _handworked()
+    names = [c.split()[0] for c in g["contig"]]
+    seqs = [c.split()[1].encode() for c in g["contig"]]
+    ref = mica.Reference.create(b"".join(seqs), [len(s) for s in seqs], names)
+    header = ["@HD\tVN:1.6\tSO:unsorted"] + [f"@SQ\tSN:{n}\tLN:{len(s)}" for n, s in zip(names, seqs)] + \
+             ["@PG\tID:mica-gb300\tPN:mica-gb300\tVN:1.0"]
+    codes, res = _result([r.split(" ", 1)[1] for r in g["read"]], mica)
+    words, off, lens = synth.pack_reads(codes)
+    batch = synth.ReadBatch(words, off, lens, np.zeros(len(codes), np.uint8), np.zeros(len(codes), np.int64),
+                            np.zeros(len(codes), np.uint8), np.zeros(len(codes), np.int32))
+    got = _write(mica, tmp_path / "h.sam", ref, [(batch, res, None)], secondary=True, qname_prefix="r")
+    assert got.splitlines() == header + [s.replace("|", "\t") for s in g["sam"]]
+    mates, rows = [], []
+    for p in g["pair"]:
+        m1, m2, row = (x.strip() for x in p.split(" ", 1)[1].split("|"))
+        mates += [m1, m2]
+        rows.append(tuple(int(v) for v in row.split()) + (0,))
+    codes, res = _result(mates, mica)
+    words, off, lens = synth.pack_reads(codes)
+    batch = synth.ReadBatch(words, off, lens, np.zeros(len(codes), np.uint8), np.zeros(len(codes), np.int64),
+                            np.zeros(len(codes), np.uint8), np.zeros(len(codes), np.int32))
+    pairs = np.array(rows, dtype=mica.PAIR_DTYPE)
+    got = _write(mica, tmp_path / "hp.sam", ref, [(batch, res, pairs)], qname_prefix="p")
+    assert got.splitlines() == header + [s.replace("|", "\t") for s in g["psam"]]
+    # the restatement agrees with the hand-worked records too
+    text = ref.text().decode()
+    starts = [0, len(seqs[0]), len(seqs[0]) + len(seqs[1])]
+    runs = [(int(s), int(s + n)) for s, n in ref.ambiguous_runs()]
+    assert samcheck.sam_text(names, starts, runs, text, batch, res, pairs, prefix="p").splitlines() == \
+        header + [s.replace("|", "\t") for s in g["psam"]]
