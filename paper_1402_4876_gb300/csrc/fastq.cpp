@@ -13,6 +13,7 @@
 // a background thread reads and indexes about as many bytes again, so that
 // the reading overlaps whatever the caller does with the batch.
 #include <algorithm>
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <cstdio>
@@ -457,34 +458,42 @@ int mica_read_batch_filter_n(const mica_read_batch *b, const mica_reference *ref
     const uint64_t text_len = ref->text.size();
     try {
         // d' of every hit of a read with ambiguous bases (0xff: unchanged),
-        // decided before anything changes
+        // decided (reads in chunks on host threads) before anything changes
         const uint64_t base0 = offsets[0];
         std::vector<uint8_t> dn(offsets[n] - base0, 0xffu);
-        uint8_t codes[MICA_MAX_READ_LEN], amb[MICA_MAX_READ_LEN];
-        for (uint64_t i = 0; i < n; i++) {
-            if (b->amb_off[i + 1] == b->amb_off[i] || offsets[i + 1] == offsets[i]) continue;
-            const uint32_t m = b->len[i];
-            const uint32_t *w = b->words.data() + b->word_off[i];
-            for (uint32_t j = 0; j < m; j++) {
-                codes[j] = (uint8_t)((w[j >> 4] >> (2 * (j & 15))) & 3);
-                amb[j] = 0;
-            }
-            for (uint64_t a = b->amb_off[i]; a < b->amb_off[i + 1]; a++) amb[b->amb[a]] = 1;
-            for (uint64_t h = offsets[i]; h < offsets[i + 1]; h++) {
-                const mica_hit &x = hits[h];
-                if (x.strand > 1 || x.pos >= text_len || m > text_len - x.pos) return MICA_EINVAL;
-                uint32_t raw = 0, dprime = 0;
+        const uint64_t chunk = 16384, n_chunks = (n + chunk - 1) / chunk;
+        std::atomic<bool> bad{false};
+        parallel_chunks(n_chunks, host_threads(), [&](uint64_t c) {
+            uint8_t codes[MICA_MAX_READ_LEN], amb[MICA_MAX_READ_LEN];
+            for (uint64_t i = c * chunk; i < std::min(n, (c + 1) * chunk); i++) {
+                if (b->amb_off[i + 1] == b->amb_off[i] || offsets[i + 1] == offsets[i]) continue;
+                const uint32_t m = b->len[i];
+                const uint32_t *w = b->words.data() + b->word_off[i];
                 for (uint32_t j = 0; j < m; j++) {
-                    const uint32_t ri = x.strand ? m - 1 - j : j;   // read offset at window offset j
-                    const uint8_t base = x.strand ? (uint8_t)(3 - codes[ri]) : codes[ri];
-                    const bool mism = ref->text[x.pos + j] != (uint8_t)"ACGT"[base];
-                    raw += mism;
-                    dprime += mism || amb[ri];
+                    codes[j] = (uint8_t)((w[j >> 4] >> (2 * (j & 15))) & 3);
+                    amb[j] = 0;
                 }
-                if (x.mm != raw && x.mm != dprime) return MICA_EINVAL;
-                dn[h - base0] = (uint8_t)std::min<uint32_t>(dprime, 0xfeu);
+                for (uint64_t a = b->amb_off[i]; a < b->amb_off[i + 1]; a++) amb[b->amb[a]] = 1;
+                for (uint64_t h = offsets[i]; h < offsets[i + 1]; h++) {
+                    const mica_hit &x = hits[h];
+                    if (x.strand > 1 || x.pos >= text_len || m > text_len - x.pos) {
+                        bad = true;
+                        continue;
+                    }
+                    uint32_t raw = 0, dprime = 0;
+                    for (uint32_t j = 0; j < m; j++) {
+                        const uint32_t ri = x.strand ? m - 1 - j : j;   // read offset at window offset j
+                        const uint8_t base = x.strand ? (uint8_t)(3 - codes[ri]) : codes[ri];
+                        const bool mism = ref->text[x.pos + j] != (uint8_t)"ACGT"[base];
+                        raw += mism;
+                        dprime += mism || amb[ri];
+                    }
+                    if (x.mm != raw && x.mm != dprime) bad = true;
+                    dn[h - base0] = (uint8_t)std::min<uint32_t>(dprime, 0xfeu);
+                }
             }
-        }
+        });
+        if (bad) return MICA_EINVAL;
         uint64_t wpos = base0, dropped = 0;
         for (uint64_t i = 0; i < n; i++) {
             const uint64_t s = offsets[i], e = offsets[i + 1];   // offsets[i + 1] not yet rewritten

@@ -7,12 +7,14 @@
 // the reference, filters hit lists by that rule and keeps a binary copy.
 // No CUDA call is made here.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <memory>
 #include <new>
 #include <unordered_set>
 
+#include "host_parallel.h"
 #include "reference_internal.h"
 
 namespace mica {
@@ -370,15 +372,21 @@ int mica_reference_filter(const mica_reference *ref, const uint16_t *lengths, ui
         if (offsets[i + 1] < offsets[i] || offsets[i + 1] - offsets[i] > total[i]) return MICA_EINVAL;
     if (offsets[n_reads] > offsets[0] && !hits) return MICA_EINVAL;
     try {
-        // decide every hit first, so that bad input changes nothing
-        std::vector<uint8_t> keep(offsets[n_reads] - offsets[0]);
-        for (uint64_t i = 0; i < n_reads; i++)
-            for (uint64_t h = offsets[i]; h < offsets[i + 1]; h++) {
-                const int32_t c = reference_place(*ref, hits[h].pos, lengths[i]);
-                if (c == PLACE_OUT_OF_RANGE) return MICA_EINVAL;
-                keep[h - offsets[0]] = c >= 0;
-            }
+        // decide every hit first (reads in chunks on host threads), so that
+        // bad input changes nothing
         const uint64_t base0 = offsets[0];
+        std::vector<uint8_t> keep(offsets[n_reads] - base0);
+        const uint64_t chunk = 16384, n_chunks = (n_reads + chunk - 1) / chunk;
+        std::atomic<bool> bad{false};
+        parallel_chunks(n_chunks, host_threads(), [&](uint64_t c) {
+            for (uint64_t i = c * chunk; i < std::min(n_reads, (c + 1) * chunk); i++)
+                for (uint64_t h = offsets[i]; h < offsets[i + 1]; h++) {
+                    const int32_t pl = reference_place(*ref, hits[h].pos, lengths[i]);
+                    if (pl == PLACE_OUT_OF_RANGE) bad = true;
+                    keep[h - base0] = pl >= 0;
+                }
+        });
+        if (bad) return MICA_EINVAL;
         uint64_t w = base0, dropped = 0;
         for (uint64_t i = 0; i < n_reads; i++) {
             const uint64_t b = offsets[i], e = offsets[i + 1];   // offsets[i + 1] not yet rewritten
