@@ -830,6 +830,12 @@ class SamWriter:
     def __exit__(self, *a):
         self.close()
 
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
 
 def gather_ceiling(buffer_bytes: int, load_bytes: int = 32, loads: int = 1 << 28, repeats: int = 3,
                    device: int = 0) -> dict:
