@@ -22,26 +22,76 @@ constexpr uint64_t NOALLOC_TILE = 2048;
 constexpr uint64_t NOALLOC_SCRATCH = MICA_NOALLOC_MAX_COUNTS / NOALLOC_TILE + 2;
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[NOALLOC_SCRATCH];
 
-// The array's device address, looked up once per device with that device
-// current (in host code the symbol's name is only a host-side stand-in).
+// The array's device address, looked up once per device and context with
+// that device current (in host code the symbol's name is only a host-side
+// stand-in).  A device reset destroys the context and the module with it; the
+// context that replaces it has a new id, so the address is looked up again.
 constexpr int MAX_DEVICES = 64;
 std::mutex g_noalloc_mu;
-unsigned long long *g_noalloc_ptr[MAX_DEVICES];
+struct ScratchAddr {
+    unsigned long long ctx_id = 0;   // 0: not looked up yet (context ids start at 1)
+    unsigned long long *ptr = nullptr;
+};
+ScratchAddr g_noalloc_addr[MAX_DEVICES];
+
+// Id of the calling thread's current context, through the driver's entry
+// points (the library links only the runtime).
+typedef int (*ctx_get_current_fn)(void **);
+typedef int (*ctx_get_id_fn)(void *, unsigned long long *);
+
+int current_context_id(unsigned long long *id)
+{
+    static ctx_get_current_fn get_current = nullptr;
+    static ctx_get_id_fn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa);
+        if (e == cudaSuccess) e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb);
+        if (e != cudaSuccess || qa != cudaDriverEntryPointSuccess || qb != cudaDriverEntryPointSuccess) {
+            if (e == cudaSuccess) e = cudaErrorNotSupported;
+            set_last_cuda_error(e, "cudaGetDriverEntryPointByVersion(cuCtxGetCurrent, cuCtxGetId)", __FILE__, __LINE__);
+            return MICA_ECUDA;
+        }
+        get_current = (ctx_get_current_fn)a;
+        get_id = (ctx_get_id_fn)b;
+    }
+    void *ctx = nullptr;
+    *id = 0;
+    if (get_current(&ctx) != 0 || (ctx && get_id(ctx, id) != 0)) {
+        set_last_cuda_error(cudaErrorDeviceUninitialized, "cuCtxGetCurrent / cuCtxGetId", __FILE__, __LINE__);
+        return MICA_ECUDA;
+    }
+    return 0;   // *id stays 0 while the thread has no current context yet
+}
 
 int noalloc_scratch(int device, unsigned long long **out)
 {
     if (device < 0 || device >= MAX_DEVICES) return MICA_EINVAL;
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[device]) {
+    unsigned long long ctx = 0;
+    if (int rc = current_context_id(&ctx)) return rc;
+    ScratchAddr &a = g_noalloc_addr[device];
+    if (ctx == 0 || a.ctx_id != ctx || !a.ptr) {
+        // the lookup makes the device's primary context current if no
+        // context was yet, so the id is read after it
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) {
             set_last_cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
             return MICA_ECUDA;
         }
-        g_noalloc_ptr[device] = (unsigned long long *)p;
+        if (ctx == 0) {
+            if (int rc = current_context_id(&ctx)) return rc;
+            if (ctx == 0) {
+                set_last_cuda_error(cudaErrorDeviceUninitialized, "no current context after the lookup", __FILE__, __LINE__);
+                return MICA_ECUDA;
+            }
+        }
+        a.ptr = (unsigned long long *)p;
+        a.ctx_id = ctx;
     }
-    *out = g_noalloc_ptr[device];
+    *out = a.ptr;
     return 0;
 }
 

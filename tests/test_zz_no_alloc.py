@@ -50,4 +50,32 @@ def test_offsets_without_allocation_equal_align_device():
     with pytest.raises(mica.MicaError) as e:
         mica.offsets_noalloc(counts, mica.NOALLOC_MAX_COUNTS + 1, out)
     assert e.value.code == mica.MICA_EINVAL
+    # a counts tensor of the wrong element size or length is refused by the binding
+    with pytest.raises(mica.MicaError) as e:
+        mica.offsets_noalloc(counts.to(torch.int32), n, out)
+    assert e.value.code == mica.MICA_EINVAL
+    with pytest.raises(mica.MicaError) as e:
+        mica.offsets_noalloc(counts[:-1], n, out)
+    assert e.value.code == mica.MICA_EINVAL
     idx.free()
+
+
+@pytest.mark.parametrize("n", [0, 1, 2047, 2048, 2049, 3 * 2048 + 5])
+def test_offsets_without_allocation_at_tile_edges(n):
+    """Empty input, one count, and counts at and around the 2,048-count tile
+    size, against numpy's running sum."""
+    import torch
+
+    import paper_1402_4876_gb300 as mica
+
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(100 + n)
+    c = rng.integers(0, 1 << 20, size=n, dtype=np.int64)
+    want = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(c, out=want[1:])
+    counts = torch.from_numpy(c).to(dev)
+    for call in range(2):
+        out = torch.full((n + 1,), -1, dtype=torch.int64, device=dev)
+        mica.offsets_noalloc(counts, n, out)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), want), f"n={n} call {call}"
