@@ -147,6 +147,7 @@ typedef struct {
                                 (summed over warps; compare with kernel_ms x warps) */
     uint64_t idle_wait_ns;   /* persistent kernel: nanoseconds slept by warps with no work */
     uint64_t overflow_moves; /* persistent kernel: nodes moved to a warp's private overflow stack */
+    uint64_t grid_ctas;      /* persistent kernel: CTAs of the launch (SMs x resident CTAs per SM) */
     float search_ms;         /* device time of the search phase (kernel + its control copies) */
     float kernel_ms;         /* device time of the search kernel launch(es) alone, with the
                                 lower-bound pass when pruning */
@@ -238,6 +239,16 @@ int mica_tuning_shapes(void);
 int mica_tuning_shape_info(int shape, int *stack_nodes, int *warps_per_cta, int *min_ctas_per_sm);
 int mica_set_tuning(mica_index *idx, const mica_tuning *t);
 int mica_get_tuning(const mica_index *idx, mica_tuning *t);
+
+/* Bounds of the persistent kernel's device waits (the paper's thread give-up
+   rule of Section 2 turned into bounded waits: no wait on the device is
+   endless).  idle_rounds: rounds a warp with no work may wait for work before
+   the launch gives up (>= 1 us each; 0 = the default, 2^22); ring_spins:
+   waits on one slot of the device spill queue (64-128 ns each; 0 = the
+   default, 2^24).  A launch that gives up stops every warp, and the align call
+   returns MICA_ETIMEOUT with no result; the index stays usable and the next
+   call starts afresh.  Small values exist to exercise that path. */
+int mica_set_wait_limits(mica_index *idx, uint32_t idle_rounds, uint32_t ring_spins);
 
 /* Autotuner: time every persistent kernel shape and the plain kernel's block
    size (over the batch and per read-length class, on that class's reads) on
@@ -597,8 +608,9 @@ int mica_sam_close(mica_sam_writer *w);
  * library holds until exit.  n may be at most MICA_NOALLOC_MAX_COUNTS; larger
  * n returns MICA_EINVAL before any work.  It runs on cuda_stream (NULL = the
  * legacy default stream) on the current device and returns without waiting.
- * The first call on a device looks the scratch up on that device; make that
- * first call before any stream capture.  All calls share the one scratch
+ * The first call on a device looks the scratch up on that device, and so does
+ * the first call after the device's context was replaced (a device reset);
+ * make such a call before any stream capture.  All calls share the one scratch
  * array, so calls whose work overlaps on the GPU (other streams, other host
  * threads) race: serialise them.
  */

@@ -66,7 +66,7 @@ class Stats(ctypes.Structure):
                 ("tasks", "seeds", "nodes", "rank_blocks", "intervals", "located", "lf_steps",
                  "spills", "retries", "launches", "warp_rounds", "lane_ops", "rounds_multi", "rounds_single",
                  "rounds_seed", "graph_captures", "graph_replays", "graph_fallbacks", "lb_steps",
-                 "lb_dead_tasks", "queue_wait_ns", "idle_wait_ns", "overflow_moves")] + [("search_ms", ctypes.c_float), ("kernel_ms", ctypes.c_float),
+                 "lb_dead_tasks", "queue_wait_ns", "idle_wait_ns", "overflow_moves", "grid_ctas")] + [("search_ms", ctypes.c_float), ("kernel_ms", ctypes.c_float),
                                                       ("total_ms", ctypes.c_float)]
 
     def as_dict(self) -> dict:
@@ -134,6 +134,7 @@ SIGNATURES = {
     "mica_tuning_shape_info": (_i32, [_i32, P, P, P]),
     "mica_set_tuning": (_i32, [P, P]),
     "mica_get_tuning": (_i32, [P, P]),
+    "mica_set_wait_limits": (_i32, [P, _u32, _u32]),
     "mica_autotune": (_i32, [P, P, P, P, P, _u64, _u32, _u32, P]),
     "mica_tuning_cache_store": (_i32, [ctypes.c_char_p, P, _u32, _u32, P]),
     "mica_tuning_cache_lookup": (_i32, [ctypes.c_char_p, P, _u32, _u32, P]),
@@ -237,19 +238,39 @@ class Result:
         return [(int(p), int(s), int(d)) for p, s, d in zip(h["pos"], h["strand"], h["mm"])]
 
 
+class _ResultOwner:
+    """Frees a library-owned mica_result once no numpy view of it is left."""
+
+    def __init__(self, out):
+        self._out = out
+
+    def __del__(self):
+        if self._out is not None and _lib is not None:
+            _lib.mica_result_free(self._out)
+            self._out = None
+
+
+def _view(addr: int, n: int, dtype, owner) -> np.ndarray:
+    dtype = np.dtype(dtype)
+    if n == 0 or not addr:
+        return np.empty(0, dtype=dtype)
+    buf = (ctypes.c_char * (n * dtype.itemsize)).from_address(addr)
+    buf._owner = owner                       # the views keep the result alive
+    return np.frombuffer(buf, dtype=dtype)
+
+
 def _take_result(out) -> Result:
-    """Copy a library-owned mica_result into numpy arrays and free it."""
-    try:
-        r = out.contents
-        n = int(r.n_reads)
-        total = np.ctypeslib.as_array(r.total, shape=(max(n, 1),))[:n].copy()
-        offsets = np.ctypeslib.as_array(r.offsets, shape=(n + 1,)).copy()
-        nh = int(offsets[-1])
-        hits = np.empty(nh, dtype=HIT_DTYPE)
-        if nh:
-            ctypes.memmove(hits.ctypes.data, r.hits, nh * HIT_DTYPE.itemsize)
-    finally:
-        _lib.mica_result_free(out)
+    """Numpy views (no copy) of a library-owned mica_result; the result is
+    freed when the last view is collected."""
+    owner = _ResultOwner(out)
+    r = out.contents
+    n = int(r.n_reads)
+    offsets = _view(ctypes.cast(r.offsets, ctypes.c_void_p).value, n + 1, np.uint64, owner)
+    total = _view(ctypes.cast(r.total, ctypes.c_void_p).value, n, np.uint64, owner)
+    nh = int(offsets[-1]) if n else 0
+    hits = _view(r.hits, nh, HIT_DTYPE, owner)
+    if hits.size == 0:
+        hits = np.empty(0, dtype=HIT_DTYPE)
     return Result(total, offsets, hits)
 
 
@@ -353,6 +374,10 @@ class Index:
             _check(_lib.mica_tuning_cache_store(os.fsencode(cache), self._h, classes, kmax, ctypes.byref(t)),
                    "mica_tuning_cache_store")
         return self.tuning()
+
+    def set_wait_limits(self, idle_rounds: int = 0, ring_spins: int = 0):
+        """Bounds of the persistent kernel's device waits (0 = defaults); see mica_set_wait_limits."""
+        _check(_lib.mica_set_wait_limits(self._h, idle_rounds, ring_spins), "mica_set_wait_limits")
 
     def tuning(self) -> dict:
         t = Tuning()
@@ -513,7 +538,26 @@ NOALLOC_MAX_COUNTS = 1 << 24
 
 def offsets_noalloc(d_counts, n: int, d_offsets, stream=None) -> None:
     """mica_offsets_noalloc: CSR offsets from per-read counts (device
-    pointers or torch CUDA tensors), without allocating device memory."""
+    pointers or torch CUDA tensors), without allocating device memory.
+
+    Tensors must be 8-byte integer CUDA tensors on the current device with at
+    least n (counts) and n + 1 (offsets) elements; anything else raises
+    MicaError(MICA_EINVAL) before the call.  With tensors and no stream, the
+    call runs on torch's current stream, which is where they were produced;
+    with raw pointers and no stream, on the legacy default stream."""
+    tensors = [x for x in (d_counts, d_offsets) if not isinstance(x, int)]
+    if tensors:
+        import torch
+        dev = torch.cuda.current_device()
+        for x, need, what in ((d_counts, n, "counts"), (d_offsets, n + 1, "offsets")):
+            if isinstance(x, int):
+                continue
+            if not (x.is_cuda and x.device.index == dev and x.element_size() == 8 and
+                    not x.dtype.is_floating_point and x.is_contiguous() and x.numel() >= need):
+                raise MicaError(MICA_EINVAL, f"offsets_noalloc: {what} must be a contiguous 8-byte integer "
+                                             f"CUDA tensor on device {dev} with at least {need} elements")
+        if stream is None:
+            stream = torch.cuda.current_stream()
     ptr = lambda x: x if isinstance(x, int) else x.data_ptr()
     _check(_lib.mica_offsets_noalloc(ctypes.c_void_p(ptr(d_counts)), n, ctypes.c_void_p(ptr(d_offsets)),
                                      _stream_handle(stream)), "mica_offsets_noalloc")

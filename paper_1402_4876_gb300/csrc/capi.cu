@@ -43,6 +43,101 @@ int dev_reserve(DevBuf &b, size_t bytes)
     return 0;
 }
 
+// ---- host results in pinned memory ----
+//
+// A host result's arrays live in one page-locked block, so the device writes
+// them by DMA at the link's speed (a copy into pageable memory goes through a
+// staging buffer and runs several times slower).  Blocks come from a
+// process-wide pool of size classes (steps of a quarter of a power of two);
+// a freed result's block returns to the pool, which keeps up to 1 GiB of idle
+// blocks and releases the rest.  When page-locked memory cannot be had, the
+// block is ordinary heap memory.
+namespace {
+
+constexpr uint32_t RESULT_MAGIC = 0x4d525331u;   // "MRS1"
+constexpr size_t PIN_IDLE_MAX = 1ull << 30;
+
+struct ResultBlock {
+    mica_result pub;     // first member: a mica_result * is a ResultBlock *
+    uint32_t magic;
+    int pinned;
+    void *mem;
+    size_t bytes;
+};
+
+std::mutex g_pin_mu;
+std::vector<std::pair<size_t, void *>> g_pin_idle;
+size_t g_pin_idle_bytes = 0;
+
+size_t pin_class(size_t bytes)
+{
+    size_t c = 4096;
+    while (c < bytes) c <<= 1;
+    if (c <= 16384) return c;
+    size_t q = c / 8;                          // quarter steps of the half below c
+    size_t r = c / 2;
+    while (r < bytes) r += q;
+    return r;
+}
+
+void *pin_get(size_t bytes, size_t &got, int &pinned)
+{
+    got = pin_class(bytes);
+    {
+        std::lock_guard<std::mutex> lk(g_pin_mu);
+        for (size_t i = 0; i < g_pin_idle.size(); i++)
+            if (g_pin_idle[i].first == got) {
+                void *p = g_pin_idle[i].second;
+                g_pin_idle[i] = g_pin_idle.back();
+                g_pin_idle.pop_back();
+                g_pin_idle_bytes -= got;
+                pinned = 1;
+                return p;
+            }
+    }
+    void *p = nullptr;
+    if (cudaMallocHost(&p, got) == cudaSuccess) {
+        pinned = 1;
+        return p;
+    }
+    cudaGetLastError();
+    pinned = 0;
+    got = bytes;
+    return malloc(std::max<size_t>(bytes, 1));
+}
+
+void pin_put(void *p, size_t bytes)
+{
+    {
+        std::lock_guard<std::mutex> lk(g_pin_mu);
+        if (g_pin_idle_bytes + bytes <= PIN_IDLE_MAX) {
+            g_pin_idle.emplace_back(bytes, p);
+            g_pin_idle_bytes += bytes;
+            return;
+        }
+    }
+    cudaFreeHost(p);
+}
+
+}  // namespace
+
+mica_result *result_new(uint64_t n_reads, uint64_t n_hits)
+{
+    ResultBlock *b = (ResultBlock *)calloc(1, sizeof(ResultBlock));
+    if (!b) return nullptr;
+    size_t tb = (std::max<uint64_t>(n_reads, 1) * 8 + 63) & ~63ull;
+    size_t ob = ((n_reads + 1) * 8 + 63) & ~63ull;
+    size_t hb = std::max<uint64_t>(n_hits, 1) * sizeof(mica_hit);
+    b->mem = pin_get(tb + ob + hb, b->bytes, b->pinned);
+    if (!b->mem) { free(b); return nullptr; }
+    b->magic = RESULT_MAGIC;
+    b->pub.n_reads = n_reads;
+    b->pub.total = (uint64_t *)b->mem;
+    b->pub.offsets = (uint64_t *)((char *)b->mem + tb);
+    b->pub.hits = (mica_hit *)((char *)b->mem + tb + ob);
+    return &b->pub;
+}
+
 void dev_release(DevBuf &b)
 {
     if (b.p) cudaFree(b.p);
@@ -180,7 +275,7 @@ static int align_graph(const mica_index *idx, Workspace &w, mica_stats &st, cons
                                (uint64_t)w.total.p, (uint64_t)w.keep.p, (uint64_t)w.hit_off.p, (uint64_t)w.hits.p,
                                (uint64_t)w.big.p, (uint64_t)w.scan_tmp.p, w.hit_capacity, (uint64_t)w.iv_cap,
                                (uint64_t)w.spill_cap, (uint64_t)w.spill_seq.p, (uint64_t)w.deep.p,
-                               (uint64_t)p.report};
+                               (uint64_t)p.report, ((uint64_t)idx->idle_limit << 32) | idx->spin_limit};
     if (!w.gexec || memcmp(key, w.gkey, sizeof(key)) != 0) {
         if (w.gexec) { cudaGraphExecDestroy(w.gexec); w.gexec = nullptr; }
         uint64_t L = 0;
@@ -238,6 +333,7 @@ static int align_graph(const mica_index *idx, Workspace &w, mica_stats &st, cons
     st.queue_wait_ns = out.wait_queue_ns;
     st.idle_wait_ns = out.wait_idle_ns;
     st.overflow_moves = out.deep_moves;
+    st.grid_ctas = (uint64_t)grid;
     st.located = nhits;
     st.lf_steps = steps;
     st.launches += w.glaunches;
@@ -557,6 +653,14 @@ int mica_get_tuning(const mica_index *idx, mica_tuning *t)
     return 0;
 }
 
+int mica_set_wait_limits(mica_index *idx, uint32_t idle_rounds, uint32_t ring_spins)
+{
+    if (!idx) return MICA_EINVAL;
+    idx->idle_limit = idle_rounds;
+    idx->spin_limit = ring_spins;
+    return 0;
+}
+
 }  // extern "C"
 
 namespace mica {
@@ -673,13 +777,8 @@ int mica_align_batch(mica_index *idx, const uint32_t *packed_reads, const uint64
     idx->stats.launches = 0;
     uint64_t nh = 0;
     if ((rc = align_on_device(idx, idx->ws, idx->stats, rd, p, s, &nh))) return rc;
-    mica_result *r = (mica_result *)calloc(1, sizeof(mica_result));
+    mica_result *r = result_new(n_reads, nh);
     if (!r) return MICA_ENOMEM;
-    r->n_reads = n_reads;
-    r->total = (uint64_t *)malloc(std::max<uint64_t>(n_reads, 1) * 8);
-    r->offsets = (uint64_t *)malloc((n_reads + 1) * 8);
-    r->hits = (mica_hit *)malloc(std::max<uint64_t>(nh, 1) * sizeof(mica_hit));
-    if (!r->total || !r->offsets || !r->hits) { mica_result_free(r); return MICA_ENOMEM; }
     cudaError_t e = cudaSuccess;
     if (n_reads) e = cudaMemcpyAsync(r->total, w.total.p, n_reads * 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(r->offsets, w.hit_off.p, (n_reads + 1) * 8, cudaMemcpyDeviceToHost, s);
@@ -697,10 +796,12 @@ int mica_align_batch(mica_index *idx, const uint32_t *packed_reads, const uint64
 void mica_result_free(mica_result *res)
 {
     if (!res) return;
-    free(res->total);
-    free(res->offsets);
-    free(res->hits);
-    free(res);
+    ResultBlock *b = (ResultBlock *)res;
+    if (b->magic != RESULT_MAGIC) return;   // not a result of this library (or freed twice)
+    b->magic = 0;
+    if (b->pinned) pin_put(b->mem, b->bytes);
+    else free(b->mem);
+    free(b);
 }
 
 int mica_debug_suffix_array(const uint8_t *genome_acgt, uint64_t len, int device, uint32_t *sa_out)

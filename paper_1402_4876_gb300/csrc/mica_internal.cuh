@@ -144,6 +144,9 @@ struct DevBuf {
 
 int dev_reserve(DevBuf &b, size_t bytes);   // grow-only device buffer
 void dev_release(DevBuf &b);
+// A host result for n_reads reads and n_hits listed hits (arrays in one
+// page-locked block from the library's pool); free with mica_result_free.
+mica_result *result_new(uint64_t n_reads, uint64_t n_hits);
 
 // Makes `dev` current for a scope and restores the caller's device after.
 struct DeviceGuard {
@@ -152,7 +155,7 @@ struct DeviceGuard {
     ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
 };
 
-constexpr int GRAPH_KEY = 27;   // words identifying a captured batch shape
+constexpr int GRAPH_KEY = 28;   // words identifying a captured batch shape
 
 // Per-index workspace reused across align calls.
 struct Workspace {
@@ -190,6 +193,7 @@ struct mica_index {
     mica::Workspace ws;
     mica_stats stats{};
     mica_tuning tuning{-1, 0, 0, {0, 0, 0, 0}, -1};
+    uint32_t idle_limit = 0, spin_limit = 0;   // persistent kernel wait bounds; 0 = built-in defaults
 };
 
 namespace mica {

@@ -416,8 +416,12 @@ constexpr uint32_t ADMIT_LOW = 64;          // admit tasks when pending work < t
 // are free: an admission costs a few memory round trips whatever it takes, so
 // it should fill several slots -- 8, or 16 when the index lives in HBM and
 // the round trips are longer (measured faster on each genome)
-constexpr uint32_t IDLE_LIMIT = 1u << 22;    // idle rounds (>= 1 us each) before timing out
-constexpr uint32_t SPIN_LIMIT = 1u << 24;    // waits on one ring slot (64-128 ns each: ~1-2 s)
+// Bounded waits: the defaults of PersistArgs::idle_limit (idle rounds of
+// >= 1 us each before the kernel gives up with ERR_TIMEOUT) and
+// PersistArgs::spin_limit (waits of 64-128 ns on one ring slot: ~1-2 s);
+// mica_set_wait_limits overrides both.
+constexpr uint32_t IDLE_LIMIT = 1u << 22;
+constexpr uint32_t SPIN_LIMIT = 1u << 24;
 constexpr uint32_t RESERVE_LIMIT = 1u << 20; // spill reservation attempts (lost races back off)
 constexpr uint32_t FULL_WAITS = 1024;        // waits on a full ring before a room spill gives up
 constexpr uint32_t DONATE_TRIES = 8;         // reservation attempts of a donation under contention
@@ -443,6 +447,8 @@ struct PersistArgs {
     bool prefetch;                  // warm the next round's occurrence blocks in L2
     int admit_min_free;             // free slots that make a warp holding work admit more
     const unsigned long long *lb;   // optional: lower-bound breakpoints per (read, strand)
+    uint32_t idle_limit;            // idle rounds before ERR_TIMEOUT
+    uint32_t spin_limit;            // waits on one spill-ring slot before ERR_TIMEOUT
 };
 
 template <int SCAP>
@@ -455,6 +461,7 @@ struct WarpSmem {
     uint32_t pat[32][MAX_WORDS + 1];      // pattern of each task slot
     unsigned long long lb[32];            // lower-bound breakpoints of each slot
     int live[32];                         // nodes of each slot in the two stacks
+    uint8_t rank_lane[32];                // admission: the slot of the j-th new task
 };
 
 __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t x, int lane)
@@ -545,7 +552,7 @@ __device__ __forceinline__ bool spill_bottom(WarpSmem<SCAP> &W, const PersistArg
                 uint32_t spin = 0;
                 bool free_ = true;
                 while (*sq != pos) {               // previous lap's item not read yet
-                    if (++spin > SPIN_LIMIT) { atomicOr(&ctl->error, ERR_TIMEOUT); free_ = false; break; }
+                    if (++spin > a.spin_limit) { atomicOr(&ctl->error, ERR_TIMEOUT); free_ = false; break; }
                     __nanosleep(64);
                 }
                 if (spin) atomicAdd(&ctl->wait_queue_ns, 64ull * spin);
@@ -691,6 +698,49 @@ __device__ __forceinline__ void emit_one(const PersistArgs &a, bool leaf, uint32
     }
 }
 
+// Copy the packed words of `nnew` newly admitted slots into their pattern
+// rows (word-reversed for the minus strand), four lanes per slot: lane g of a
+// quad loads the 16-byte-aligned chunks g and g + 4 of the slot's read.
+// woff / info are read from the slot's own lane by shuffle.
+template <int SCAP>
+__device__ __forceinline__ void stage_patterns(WarpSmem<SCAP> &W, const uint32_t *words, const uint32_t *words_end,
+                                               uint64_t woff, uint32_t info, uint32_t nnew, int lane)
+{
+    const uint32_t quad = (uint32_t)lane >> 2, g = (uint32_t)lane & 3u;
+    for (uint32_t base = 0; base < nnew; base += 8) {
+        const uint32_t r = base + quad;
+        const int src = r < nnew ? W.rank_lane[r] : 0;
+        const uint64_t off = __shfl_sync(FULL, woff, src);
+        const uint32_t inf = __shfl_sync(FULL, info, src);
+        if (r >= nnew) continue;
+        const uint32_t m = inf & 511u, minus = (inf >> 11) & 1u, Wn = (m + 15) >> 4;
+        const uint32_t *p0 = words + off, *pend = p0 + Wn;
+        const uint32_t *a0 = (const uint32_t *)((uintptr_t)p0 & ~(uintptr_t)15);
+        uint32_t *row = W.pat[src];
+#pragma unroll
+        for (uint32_t c = g; c < 8; c += 4) {
+            const uint32_t *cp = a0 + 4 * c;
+            if (cp >= pend) break;
+            uint32_t v[4];
+            if (cp >= words && cp + 4 <= words_end) {
+                uint4 x = __ldg((const uint4 *)cp);
+                v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; e++) v[e] = (cp + e >= p0 && cp + e < pend) ? __ldg(cp + e) : 0u;
+            }
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const uint32_t *wp = cp + e;
+                if (wp >= p0 && wp < pend) {
+                    const uint32_t t = (uint32_t)(wp - p0);
+                    row[minus ? Wn - 1 - t : t] = v[e];
+                }
+            }
+        }
+    }
+}
+
 // Push at most one node per lane onto the stack its size selects.  Callers
 // guarantee room: admission runs with fewer than 64 nodes held and seed
 // rounds with fewer than 32 on each stack, so 32 more always fit.
@@ -728,7 +778,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
     // task slot `lane`: read id, info = m | k << 9 | minus << 11 | qe << 12,
     // window code, next and end seed variant
     uint32_t s_read = 0, s_info = 0, s_code = 0, s_vnext = 0, s_vend = 0;
+    uint64_t s_woff = 0;          // admission only: word offset of the slot's read
     bool s_used = false;
+    const uint32_t *words_end = a.rd.words + a.rd.word_off[a.rd.n];   // end of the batch's packed words
     uint32_t mbot = 0, mtop = 0, sbot = 0, stop = 0;
     uint32_t dmt = 0, dst = 0;    // entries in the warp's overflow stacks (multi-row, single-row)
     const int wg = (int)blockIdx.x * WARPS + warp;
@@ -790,7 +842,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
                 pw = __shfl_sync(FULL, pw, 0);
                 if (pw < 0) break;
                 if (pw == 0) {
-                    if (++idle_rounds > IDLE_LIMIT) {
+                    if (++idle_rounds > a.idle_limit) {
                         if (lane == 0) atomicOr(&ctl->error, ERR_TIMEOUT);
                         break;
                     }
@@ -838,7 +890,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
                         uint32_t spin = 0;
                         bool ready = true;
                         while (*sq != pos + 1) {          // written by its producer?
-                            if (++spin > SPIN_LIMIT) { atomicOr(&ctl->error, ERR_TIMEOUT); ready = false; break; }
+                            if (++spin > a.spin_limit) { atomicOr(&ctl->error, ERR_TIMEOUT); ready = false; break; }
                             __nanosleep(128);
                         }
                         if (spin) atomicAdd(&ctl->wait_queue_ns, 128ull * spin);
@@ -878,31 +930,30 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
                     W.live[lane] = is_node ? 1 : 0;
                     W.lb[lane] = lbv;
                 }
-                // stage the new tasks' patterns, each lane its own slot's read:
-                // the loads of all new slots are independent, so an admission
-                // waits for a couple of memory round trips instead of two per
-                // new task.  A minus-strand pattern is first stored word-reversed
-                // and then turned into the reverse complement in place (word j
-                // needs stored words j and j + 1, and only word j is overwritten).
+                // stage the new tasks' patterns cooperatively: four lanes per
+                // new slot, eight slots per pass, each lane moving 16-byte
+                // vector loads of the slot's packed words (consecutive lanes on
+                // consecutive chunks, so a read costs its two or three sectors
+                // once).  Chunks are aligned down to 16 bytes; the bytes of
+                // neighbouring reads they cover are dropped, and a chunk that
+                // would reach outside the batch's words array (its first or
+                // last read only) is read word by word.  A minus-strand pattern
+                // is stored word-reversed and then turned into the reverse
+                // complement in place by the slot's own lane (word j needs
+                // stored words j and j + 1, and only word j is overwritten).
                 if (mine) {
-                    const uint32_t m = s_info & 511u, minus = (s_info >> 11) & 1u;
-                    const uint32_t Wn = (m + 15) >> 4;
-                    const uint32_t *src = a.rd.words + a.rd.word_off[s_read];
+                    W.rank_lane[j] = (uint8_t)lane;
+                    s_woff = a.rd.word_off[s_read];
+                }
+                __syncwarp();
+                stage_patterns<SCAP>(W, a.rd.words, words_end, s_woff, s_info, take + got, lane);
+                __syncwarp();
+                if (mine && ((s_info >> 11) & 1u)) {
+                    const uint32_t m = s_info & 511u, Wn = (m + 15) >> 4;
                     uint32_t *row = W.pat[lane];
-#pragma unroll
-                    for (uint32_t c0 = 0; c0 < MAX_WORDS; c0 += 8) {
-                        uint32_t v[8];
-#pragma unroll
-                        for (uint32_t j = 0; j < 8; j++) v[j] = c0 + j < Wn ? __ldg(src + c0 + j) : 0u;
-#pragma unroll
-                        for (uint32_t j = 0; j < 8; j++)
-                            if (c0 + j < Wn) row[minus ? Wn - 1 - (c0 + j) : c0 + j] = v[j];
-                    }
-                    if (minus) {
-                        for (uint32_t j = 0; j < Wn; j++) {
-                            uint32_t hi = row[j], lo = j + 1 < Wn ? row[j + 1] : 0u;
-                            row[j] = rc_word(hi, lo, m);
-                        }
+                    for (uint32_t q = 0; q < Wn; q++) {
+                        uint32_t hi = row[q], lo = q + 1 < Wn ? row[q + 1] : 0u;
+                        row[q] = rc_word(hi, lo, m);
                     }
                 }
                 __syncwarp();
@@ -926,7 +977,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
                 }
                 busy = false;
                 if (__shfl_sync(FULL, done, 0)) break;
-                if (++idle_rounds > IDLE_LIMIT) {
+                if (++idle_rounds > a.idle_limit) {
                     if (lane == 0) atomicOr(&ctl->error, ERR_TIMEOUT);
                     break;
                 }
@@ -938,7 +989,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
         if (cnt + seeds_total == 0) {
             // slots still held but no work: cannot happen while the per-slot
             // node counts are right; bounded so a bug cannot spin forever
-            if (++idle_rounds > IDLE_LIMIT) {
+            if (++idle_rounds > a.idle_limit) {
                 if (lane == 0) atomicOr(&ctl->error, ERR_TIMEOUT);
                 break;
             }
@@ -1236,6 +1287,12 @@ static int admit_min_free_for(const mica_index *idx)
     return idx->n_occ_blocks * 32 > (96ull << 20) ? 16 : 8;
 }
 
+static void set_wait_limits(const mica_index *idx, PersistArgs &pa)
+{
+    pa.idle_limit = idx->idle_limit ? idx->idle_limit : IDLE_LIMIT;
+    pa.spin_limit = idx->spin_limit ? idx->spin_limit : SPIN_LIMIT;
+}
+
 // Spill ring capacity for a batch of n reads: a power of two >= max(n, 2^20).
 static uint32_t ring_capacity(uint64_t n)
 {
@@ -1342,6 +1399,7 @@ int enqueue_persistent(const mica_index *idx, Workspace &w, const ReadsView &rd,
     pa.prefetch = prefetch;
     pa.admit_min_free = admit_min_free_for(idx);
     deep_ptrs(w, pa.total_warps, pa.deep_m, pa.deep_s);
+    set_wait_limits(idx, pa);
     if (rd.n) {
         if (int rc = launch_ring_init(w, s)) return rc;
         launches++;
@@ -1396,6 +1454,7 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
                 pa.prefetch = cfg.prefetch;
                 pa.admit_min_free = admit_min_free_for(idx);
                 pa.lb = d_lb;
+                set_wait_limits(idx, pa);
                 if ((rc = dev_reserve(w.spill_seq, (size_t)w.spill_cap * 4))) return rc;
                 pa.seq = (uint32_t *)w.spill_seq.p;
                 if ((rc = launch_ring_init(w, s))) return rc;
@@ -1409,6 +1468,7 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
                 MICA_CUDA_TRY(cudaGetLastError());
                 MICA_CUDA_TRY(record_event(w.kev[1], s));
                 st.launches++;
+                st.grid_ctas = (uint64_t)grid;
             } else {
                 // plain: one task per thread, then drain the re-queue in rounds
                 if ((rc = dev_reserve(w.spill2, (size_t)w.spill_cap * sizeof(WorkItem)))) return rc;
@@ -1599,6 +1659,7 @@ int run_search_stratum(const mica_index *idx, Workspace &w, mica_stats &st, cons
         pa.prefetch = cfg.prefetch;
         pa.admit_min_free = admit_min_free_for(idx);
         pa.lb = cfg.prune ? (const unsigned long long *)w.lb.p : nullptr;
+        set_wait_limits(idx, pa);
         sh.fn<<<grid, sh.warps * 32, sh.smem, s>>>(pa);
         MICA_CUDA_TRY(cudaGetLastError());
         MICA_CUDA_TRY(cudaMemsetAsync(d_next, 0, 4, s));
@@ -1645,6 +1706,7 @@ int run_search_stratum(const mica_index *idx, Workspace &w, mica_stats &st, cons
     st.queue_wait_ns = total.wait_queue_ns;
     st.idle_wait_ns = total.wait_idle_ns;
     st.overflow_moves = total.deep_moves;
+    st.grid_ctas = (uint64_t)grid;
     return 0;
 }
 

@@ -146,16 +146,9 @@ int run_tick(mica_server *srv, std::vector<Request *> &tick, Workspace &ws, mica
     MICA_CUDA_TRY(cudaStreamSynchronize(s));
     rpos = 0;
     for (Request *r : tick) {
-        mica_result *res = (mica_result *)calloc(1, sizeof(mica_result));
         uint64_t h0 = offs[rpos], h1 = offs[rpos + r->n];
-        if (res) {
-            res->n_reads = r->n;
-            res->total = (uint64_t *)malloc(std::max<uint64_t>(r->n, 1) * 8);
-            res->offsets = (uint64_t *)malloc((r->n + 1) * 8);
-            res->hits = (mica_hit *)malloc(std::max<uint64_t>(h1 - h0, 1) * sizeof(mica_hit));
-        }
-        if (!res || !res->total || !res->offsets || !res->hits) {
-            mica_result_free(res);
+        mica_result *res = result_new(r->n, h1 - h0);
+        if (!res) {
             r->rc = MICA_ENOMEM;
         } else {
             if (r->n) memcpy(res->total, total.data() + rpos, r->n * 8);
