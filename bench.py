@@ -8,8 +8,18 @@ per read (exact totals).  One step = one batch of 1M reads through the whole
 path (seed lookups, backtracking, counting and capping, LF-walk location,
 per-read sort) with the reads already in HBM; the index is built once.
 
+At one GPU the line also carries two more workloads, each its own sub-object
+with its own roofline:
+  "uneven": 1M reads of 50/100/150/250 bp with k in 0..3 (30% from repeats)
+            on the same genome: one persistent launch vs one plain launch per
+            length class and one plain launch;
+  "human":  a 3.1 Gbp synthetic genome (about 45% repeats) resident in HBM and
+            one batch of 1M read pairs (2M mates of 150 bp, k <= 2 per mate):
+            persistent vs plain, against the HBM random-gather ceiling.
+
   python bench.py [--gpus N --steps K --warmup W]       our CUDA path (N replicas)
   python bench.py --impl reference [...]                the CPU oracle, timed
+  python bench.py --workload uneven|human|serve         one workload on its own
 
 Prints one JSON line on rank 0.
 """
@@ -37,6 +47,29 @@ HIT_CAP = 1000
 PAIR_WINDOW = (300, 700)   # fragment lengths of the human-scale pairs: Normal(500, 50) clipped to this
 L2_FLUSH_BYTES = 512 << 20
 PROFILE = os.path.join(ROOT, "profiles", "k_persistent_64m_1m150.txt")
+PROFILE_HUMAN = os.path.join(ROOT, "profiles", "k_persistent_3g_human2m.txt")
+SEARCH_CU = os.path.join(ROOT, "paper_1402_4876_gb300", "csrc", "search.cu")
+BIDIR_CU = os.path.join(ROOT, "paper_1402_4876_gb300", "csrc", "bidir.cu")
+PROFILE_BIDIR = os.path.join(ROOT, "profiles", "k_bidir_64m_1m150.txt")
+PROFILE_BIDIR_HUMAN = os.path.join(ROOT, "profiles", "k_bidir_3g_human2m.txt")
+KERNEL_NAMES = {"bidirectional": "k_bidir", "persistent": "k_lower_bounds + k_persistent"}
+KERNEL_LABEL = {"bidirectional": "bidirectional warp-pool (one persistent launch)",
+                "persistent": "one-directional persistent warp-pool"}
+SEARCH_LABEL = {"bidirectional": "k + 1 pieces, one search per leftmost exact piece over the genome's and the "
+                                 "reversed genome's index (same result as exhaustive backtracking)",
+                "persistent": "exhaustive backtracking from the read's end, pruned by mismatch lower bounds "
+                              "(same result as unpruned)"}
+ALG_LABEL = {"bidirectional": "32 B x occurrence blocks read + 16 B x seeds (two table entries in each of two "
+                              "tables) + the packed reads once + 16 B x leaf intervals",
+             "persistent": "32 B x occurrence blocks read (search and lower-bound pass) + 8 B x seeds + the "
+                           "packed reads twice + 16 B x leaf intervals"}
+
+
+def search_alg_bytes(kernel: str, st: dict, read_bytes: int) -> int:
+    """Algorithmic bytes of one search step from the on-device work counters."""
+    if kernel == "bidirectional":
+        return 32 * st["rank_blocks"] + 16 * st["seeds"] + read_bytes + 16 * st["intervals"]
+    return 32 * st["rank_blocks"] + 8 * st["seeds"] + 2 * read_bytes + 16 * st["intervals"]
 
 
 def parse():
@@ -49,13 +82,21 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--kernel", default="bidirectional", choices=["bidirectional", "persistent"],
+                    help="the batched kernel timed for the headline (the other is timed beside it)")
+    ap.add_argument("--no-uneven", action="store_true", help="leave the uneven-batch leg out of the default line")
+    ap.add_argument("--no-human", action="store_true", help="leave the human-scale leg out of the default line")
+    ap.add_argument("--human-pairs", type=int, default=1_000_000, help="default line: pairs of the human-scale leg")
     ap.add_argument("--workload", default="repeats64m", choices=["repeats64m", "uneven", "human", "serve"],
                     help="repeats64m: the headline; uneven: mixed lengths and budgets; human: 3.1 Gbp genome, "
                          "10M read pairs; serve: Poisson requests on a resident index")
     ap.add_argument("--pairs", type=int, default=10_000_000, help="human: read pairs")
     ap.add_argument("--genome-bp", type=int, default=synth.HUMAN_LEN, help="human/serve: genome length")
-    ap.add_argument("--serve-requests", type=int, default=60, help="serve: requests per load level")
-    ap.add_argument("--serve-max-size", type=int, default=200_000, help="serve: largest request (reads)")
+    ap.add_argument("--serve-requests", type=int, default=200, help="serve: requests per load level")
+    ap.add_argument("--serve-max-size", type=int, default=1_000_000, help="serve: largest request (reads)")
+    ap.add_argument("--serve-tick", type=int, default=1 << 20, help="serve: reads per search launch")
+    ap.add_argument("--serve-chunk", type=int, default=1 << 18, help="serve: largest piece of a request per launch")
+    ap.add_argument("--serve-kernel", default="persistent", help="serve: search kernel")
     return ap.parse_args()
 
 
@@ -175,19 +216,19 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
-def profile_traffic(kernel_src: str):
-    """dram bytes per launch of the search kernel from the committed ncu
-    summary, or None when the kernel source changed since the capture."""
+def profile_traffic(kernel_src: str, profile: str = PROFILE, key: str = "dram_bytes_per_launch_scaled"):
+    """dram bytes per launch of the search step from a committed ncu summary,
+    or None when the kernel source changed since the capture."""
     try:
         vals = {}
-        for line in open(PROFILE):
+        for line in open(profile):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
         sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
         if vals.get("search_cu_sha256_16") != sha:
             return None
-        return float(vals["dram_bytes_per_launch_scaled"])
+        return float(vals[key])
     except Exception:
         return None
 
@@ -264,7 +305,7 @@ def run_ours(args):
         return ms, kms, stats, r
 
     with ClockSampler(local) as clk:
-        ms, kms, stats, dres = device_steps("persistent", args.steps, args.warmup)
+        ms, kms, stats, dres = device_steps(args.kernel, args.steps, args.warmup)
     clocks = clk.summary()
     total_ms = max_over_ranks(sum(ms), world)
     value = whole_job_rate(b.n, world, args.steps, total_ms)
@@ -276,8 +317,10 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (seeded generator; the paper's YH/1000 Genomes data are not available)",
         "config": {"workload": WORKLOAD, "genome_bp": g.n, "reads_per_gpu": b.n, "read_len": 150, "k": 2,
-                   "hit_cap": HIT_CAP, "kernel": "persistent warp-pool", "index": "q=12 table, 32 B bit-plane occurrence blocks, SA 1/16, reversed-genome blocks",
-                   "search": "exhaustive backtracking pruned by mismatch lower bounds (same result as unpruned)",
+                   "hit_cap": HIT_CAP, "kernel": KERNEL_LABEL[args.kernel],
+                   "index": "q=12 tables of the genome and its reversal, 32 B bit-plane occurrence blocks of both, "
+                            "SA 1/16",
+                   "search": SEARCH_LABEL[args.kernel],
                    "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                    "parallelism": f"replicas x{world} (index per GPU, reads sharded, no collective)"},
         "latency_ms": {"p50": round(float(np.percentile(ms, 50)), 3), "p99": round(float(np.percentile(ms, 99)), 3),
@@ -291,26 +334,51 @@ def run_ours(args):
     out["gpu_launches"] = int(sum(s["launches"] for s in stats))
     out["graph_replays"] = int(sum(s["graph_replays"] for s in stats))
 
-    # roofline of the dominant kernel (the persistent search)
+    # roofline of the dominant kernel(s) of the search step.  The 64 Mbp index
+    # (occurrence blocks and q-mer tables, under 129 MB) stays in L2, so the
+    # step is bound by dependent random 32-byte gathers from L2, not by HBM:
+    # its ceiling is the measured random-gather rate over a buffer of the
+    # index's size, taken in this run.
     peaks, src = measured_peaks()
     kernel_s = statistics.mean(kms) / 1e3
-    read_bytes = 2 * 4 * int(np.sum((b.lengths.astype(np.int64) + 15) // 16))
-    # the packed reads are read once by the search and once by the lower-bound pass
-    alg_bytes = 32 * st["rank_blocks"] + 8 * st["seeds"] + 2 * read_bytes + 16 * st["intervals"]
+    read_bytes = 4 * int(np.sum((b.lengths.astype(np.int64) + 15) // 16))
+    alg_bytes = search_alg_bytes(args.kernel, st, read_bytes)
     achieved = alg_bytes / kernel_s / 1e9
-    traffic = profile_traffic(os.path.join(ROOT, "paper_1402_4876_gb300", "csrc", "search.cu"))
-    out["roofline"] = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                       "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
-                       "kernel": "k_lower_bounds + k_persistent (one search step)",
+    traffic = profile_traffic(SEARCH_CU if args.kernel == "persistent" else BIDIR_CU,
+                              PROFILE if args.kernel == "persistent" else PROFILE_BIDIR)
+    ceil = gather_ceilings(mica, idx, local)
+    gc_idx = ceil["index_sized_gbs"]
+    out["roofline"] = {"bound": "l2_random_gather", "achieved": round(achieved, 1), "peak": gc_idx, "unit": "GB/s",
+                       "frac": round(achieved / gc_idx, 4) if gc_idx else None, "traffic": traffic,
+                       "kernel": KERNEL_NAMES[args.kernel] + " (one search step)",
                        "kernel_ms": round(kernel_s * 1e3, 3),
                        "alg_bytes_per_launch": int(alg_bytes),
-                       "peak_source": f"{src} hbm_gbs (copy bandwidth)"}
+                       "alg_bytes_what": ALG_LABEL[args.kernel],
+                       "peak_source": "measured in this run: mica_gather_ceiling, independent random 32 B loads "
+                                      "over a buffer of the index's size (L2-resident), full occupancy",
+                       "hbm_copy_peak": peaks["hbm_gbs"],
+                       "frac_of_hbm_copy": round(achieved / peaks["hbm_gbs"], 4),
+                       "hbm_copy_peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json, copy bandwidth)",
+                       "gather_ceiling": ceil,
+                       "note": "traffic (DRAM bytes per step, ncu) is far below the algorithmic bytes: the index "
+                               "stays in L2; the kernel is latency-bound on dependent gathers"}
     out["clocks"] = clocks
-    out["roofline"]["gather_ceiling"] = gather_ceilings(mica, idx, local)
-    gc_idx = out["roofline"]["gather_ceiling"]["index_sized_gbs"]
-    out["roofline"]["frac_of_gather_ceiling"] = round(achieved / gc_idx, 4) if gc_idx else None
     out["rank_blocks_per_s"] = round(st["rank_blocks"] / kernel_s, 1)
     out["mbp_per_s"] = round(value * float(np.mean(b.lengths)) / 1e6, 1)   # bases of reads aligned
+
+    # the other batched kernel on the same batch
+    other = "persistent" if args.kernel == "bidirectional" else "bidirectional"
+    oms, okms, ostats, _ = device_steps(other, max(1, min(args.steps, 5)), 1)
+    ototal = max_over_ranks(sum(oms), world)
+    oval = whole_job_rate(b.n, world, len(oms), ototal)
+    ost = ostats[-1]
+    oalg = search_alg_bytes(other, ost, read_bytes)
+    out[other] = {"value": round(oval, 1), "unit": "reads/s", "ms_per_step": round(ototal / len(oms), 3),
+                  "kernel_ms": round(statistics.mean(okms), 3), "kernel": KERNEL_NAMES[other],
+                  "search": SEARCH_LABEL[other], "nodes": int(ost["nodes"]), "seeds": int(ost["seeds"]),
+                  "rank_blocks": int(ost["rank_blocks"]),
+                  "roofline_frac": round(oalg / (statistics.mean(okms) / 1e3) / 1e9 / gc_idx, 4) if gc_idx else None,
+                  f"{args.kernel}_over_{other}": round(value / oval, 3)}
 
     if not args.no_plain:
         # the same exhaustive search without lower-bound pruning (same result, more work)
@@ -319,7 +387,9 @@ def run_ours(args):
         uval = whole_job_rate(b.n, world, len(ums), utotal)
         out["unpruned"] = {"value": round(uval, 1), "unit": "reads/s", "ms_per_step": round(utotal / len(ums), 3),
                            "kernel_ms": round(statistics.mean(ukms), 3), "nodes": int(ustats[-1]["nodes"]),
-                           "seeds": int(ustats[-1]["seeds"]), "pruned_over_unpruned": round(value / uval, 3)}
+                           "seeds": int(ustats[-1]["seeds"]),
+                           "pruned_over_unpruned": round((value if args.kernel == "persistent" else oval) / uval, 3),
+                           "what": "the one-directional persistent search without lower-bound pruning"}
         # best-stratum reporting (iterative deepening over the mismatch budget)
         bms, bkms, bstats, _ = device_steps("persistent", max(1, min(args.steps, 3)), 1, report="best_stratum")
         btotal = max_over_ranks(sum(bms), world)
@@ -327,13 +397,15 @@ def run_ours(args):
                                "ms_per_step": round(btotal / len(bms), 3),
                                "kernel_ms": round(statistics.mean(bkms), 3), "nodes": int(bstats[-1]["nodes"]),
                                "seeds": int(bstats[-1]["seeds"]),
-                               "what": "report = best stratum: each read's placements with its smallest d"}
+                               "what": "report = best stratum: each read's placements with its smallest d "
+                                       "(one-directional persistent kernel, deepening the budget pass by pass)"}
         pms, pkms, pstats, _ = device_steps("plain", max(1, min(args.steps, 3)), 1)
         ptotal = max_over_ranks(sum(pms), world)
         pval = whole_job_rate(b.n, world, len(pms), ptotal)
         out["plain"] = {"value": round(pval, 1), "unit": "reads/s", "ms_per_step": round(ptotal / len(pms), 3),
                         "kernel_ms": round(statistics.mean(pkms), 3),
-                        "persistent_over_plain": round(value / pval, 3)}
+                        "batched_over_plain": round(value / pval, 3),
+                        "what": "one (read, strand) task per thread, lower-bound pruning, device re-queue"}
 
     if not args.no_e2e:
         # end to end through the public host-buffer call: pinned inputs in, hits out
@@ -355,6 +427,17 @@ def run_ours(args):
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(g, b)
+
+    # the other workloads, one GPU only (replica runs time the headline alone)
+    if world == 1:
+        if not args.no_uneven:
+            out["uneven"] = uneven_leg(mica, idx, g, args.reads, max(1, min(args.steps, 3)), 1, stream, flush,
+                                       headline=args.kernel)
+        idx.free()
+        if not args.no_human:
+            out["human"] = human_leg(mica, dev, stream, args.human_pairs, synth.HUMAN_LEN,
+                                     steps=max(1, min(args.steps, 2)), plain=not args.no_plain,
+                                     headline=args.kernel)
 
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -393,157 +476,261 @@ def _time_kernel(idx, d, n, kernel, steps, warmup, stream, flush=None):
     return ms, kms, st, r
 
 
+def uneven_leg(mica, idx, g, n_reads, steps, warmup, stream, flush, headline="bidirectional") -> dict:
+    """Batched uneven: n_reads reads of 50/100/150/250 bp with k in 0..3 (30%
+    from planted repeats) on the 64 Mbp repeat genome; one launch of each
+    batched kernel (the bidirectional and the one-directional persistent one,
+    autotuned shape) vs one plain launch per length class (autotuned block
+    sizes) and one plain launch."""
+    import torch
+    dev = torch.device("cuda", 0)
+    b = synth.reads_uneven(g, n=n_reads)
+    tune = idx.autotune(b.subset(np.arange(0, b.n, max(1, b.n // 20000))), hit_cap=HIT_CAP, repeats=1)
+    d = _device_batch(b, dev)
+    out = {"workload": f"64 Mbp repeat genome, {b.n} reads, lengths uniform in {{50,100,150,250}}, "
+                       "k uniform in 0..3, 30% from repeats, cap 1000",
+           "unit": "reads/s", "steps": steps, "warmup": warmup, "tuning": tune,
+           "l2": "flushed between timed steps"}
+    for kernel in ("bidirectional", "persistent", "plain_by_length", "plain"):
+        reps = steps if kernel in ("bidirectional", "persistent") else 1
+        ms, kms, st, r = _time_kernel(idx, d, b.n, kernel, reps, warmup, stream, flush)
+        out[kernel] = {"value": round(b.n * len(ms) / (sum(ms) / 1e3), 1), "ms_per_step": round(statistics.mean(ms), 3),
+                       "kernel_ms": round(statistics.mean(kms), 3), "launches": int(st["launches"]),
+                       "nodes": int(st["nodes"]), "seeds": int(st["seeds"]), "rank_blocks": int(st["rank_blocks"]),
+                       "intervals": int(st["intervals"]), "retries": int(st["retries"]), "hits": int(r.n_hits)}
+    h = out[headline]
+    out["value"] = h["value"]
+    out["kernel"] = KERNEL_LABEL[headline]
+    for base in ("plain_by_length", "plain", "persistent", "bidirectional"):
+        if base != headline:
+            out[f"{headline}_over_{base}"] = round(h["value"] / out[base]["value"], 3)
+    read_bytes = 4 * int(np.sum((b.lengths.astype(np.int64) + 15) // 16))
+    alg = search_alg_bytes(headline, h, read_bytes)
+    info = idx.info()
+    ceil = mica.gather_ceiling(max(1 << 20, (info["occ_bytes"] + info["table_bytes"] + 31) // 32 * 32),
+                               32, loads=1 << 27, repeats=3)
+    ach = alg / (h["kernel_ms"] / 1e3) / 1e9
+    out["roofline"] = {"bound": "l2_random_gather", "achieved": round(ach, 1), "peak": round(ceil["gbs"], 1),
+                       "unit": "GB/s", "frac": round(ach / ceil["gbs"], 4), "kernel": KERNEL_NAMES[headline],
+                       "alg_bytes_per_launch": int(alg), "alg_bytes_what": ALG_LABEL[headline],
+                       "peak_source": "measured in this run: random 32 B gathers over an index-sized buffer"}
+    return out
+
+
 def run_uneven(args):
-    """Batched uneven: 1M reads of 50/100/150/250 bp with k in 0..3 on the
-    64 Mbp repeat genome; one persistent launch vs one plain launch per
-    length class (and a single plain launch)."""
     import torch
     import paper_1402_4876_gb300 as mica
     dev = torch.device("cuda", 0)
     g = synth.genome_64m()
-    b = synth.reads_uneven(g, n=args.reads)
     idx = mica.Index.build(synth.to_acgt_bytes(g.codes), kmer_q=12, sa_sample=16)
-    tune = idx.autotune(b.subset(np.arange(0, b.n, max(1, b.n // 20000))), hit_cap=HIT_CAP, repeats=1)
-    d = _device_batch(b, dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
-    stream = torch.cuda.current_stream(dev)
-    out = {"metric": "reads/s aligned, uneven batch (lengths 50/100/150/250, k 0-3)", "unit": "reads/s",
-           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "u32",
-           "data": "synthetic", "config": {"workload": "64 Mbp repeat genome, 1M reads, lengths uniform in "
-                                           "{50,100,150,250}, k uniform in 0..3, 30% from repeats, cap 1000",
-                                           "tuning": tune, "l2": "flushed between timed steps"}}
-    for kernel in ("persistent", "plain_by_length", "plain"):
-        ms, kms, st, r = _time_kernel(idx, d, b.n, kernel, args.steps, args.warmup, stream, flush)
-        out[kernel] = {"value": round(b.n * len(ms) / (sum(ms) / 1e3), 1), "ms_per_step": round(statistics.mean(ms), 3),
-                       "kernel_ms": round(statistics.mean(kms), 3), "launches": int(st["launches"]),
-                       "nodes": int(st["nodes"]), "seeds": int(st["seeds"]), "hits": int(r.n_hits)}
-    out["value"] = out["persistent"]["value"]
-    out["persistent_over_plain_by_length"] = round(out["persistent"]["value"] / out["plain_by_length"]["value"], 3)
+    leg = uneven_leg(mica, idx, g, args.reads, args.steps, args.warmup, torch.cuda.current_stream(dev), flush,
+                     headline=args.kernel)
+    out = {"metric": "reads/s aligned, uneven batch (lengths 50/100/150/250, k 0-3)", "value": leg["value"],
+           "unit": "reads/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+           "dtype": "u32", "data": "synthetic", "config": {"workload": leg["workload"]}, "uneven": leg}
     print(json.dumps(out), flush=True)
 
 
-def run_human(args):
-    """Human-scale: a 3.1 Gbp synthetic genome (about 45% repeats) resident
-    in HBM and 10M read pairs (20M mates of 150 bp, 0.1% variants + 1%
-    sequencing error), each mate searched with k <= 2, cap 1000."""
+def human_leg(mica, dev, stream, pairs: int, genome_bp: int, steps: int = 2, plain: bool = True,
+              batch: int = 2_000_000, pairing: bool = True, headline: str = "bidirectional") -> dict:
+    """Human-scale: a synthetic genome of `genome_bp` (about 45% repeats) with
+    its index resident in HBM, and `pairs` read pairs (2 x 150 bp mates, 0.1%
+    donor variants + 1% sequencing error), each mate searched with k <= 2,
+    cap 1000, in batches of `batch` mates.  Each batched kernel (the headline
+    first) runs every batch `steps` times (the time is the mean), the plain
+    kernel once; the index (3.3 GB) is larger than L2, so no flush is needed
+    between steps."""
     import torch
-    import paper_1402_4876_gb300 as mica
-    dev = torch.device("cuda", 0)
     t0 = time.perf_counter()
-    g = synth.human_genome(args.genome_bp)
+    g = synth.human_genome(genome_bp)
     donor = synth.donor_of(g)
-    b = synth.paired_reads(donor, args.pairs)
+    b = synth.paired_reads(donor, pairs)
     gen_s = time.perf_counter() - t0
     t0 = time.perf_counter()
-    idx = mica.Index.build(synth.to_acgt_bytes(g.codes), kmer_q=12, sa_sample=16)
+    acgt = synth.to_acgt_bytes(g.codes)
+    n_genome = g.n
+    del g, donor
+    idx = mica.Index.build(acgt, kmer_q=12, sa_sample=16)
+    del acgt
     build_s = time.perf_counter() - t0
     info = idx.info()
-    stream = torch.cuda.current_stream(dev)
-    batch = 2_000_000
     res = {}
     paired, pair_ms = 0, 0.0
-    for kernel in ("persistent", "plain"):
-        tot_ms, tot_kms, nodes, blocks, seeds, hits = 0.0, 0.0, 0, 0, 0, 0
-        for warm in range(1):
-            sub = b.subset(np.arange(0, min(b.n, 200_000)))
-            idx.align_device(*_device_batch(sub, dev), sub.n, hit_cap=HIT_CAP, kernel=kernel, stream=stream)
+    other = "persistent" if headline == "bidirectional" else "bidirectional"
+    kernels = (headline, other) + (("plain",) if plain else ())
+    for kernel in kernels:
+        tot_ms, tot_kms, nodes, blocks, seeds, hits, ivs, retries = 0.0, 0.0, 0, 0, 0, 0, 0, 0
+        warm = b.subset(np.arange(0, min(b.n, 200_000)))
+        idx.align_device(*_device_batch(warm, dev), warm.n, hit_cap=HIT_CAP, kernel=kernel, stream=stream)
+        reps = steps if kernel != "plain" else 1
         for r0 in range(0, b.n, batch):
             sub = b.subset(np.arange(r0, min(b.n, r0 + batch))) if b.n > batch else b
             d = _device_batch(sub, dev)
-            ms, kms, st, r = _time_kernel(idx, d, sub.n, kernel, 1, 0, stream)
-            if kernel == "persistent":
+            ms, kms, st, r = _time_kernel(idx, d, sub.n, kernel, reps, 0, stream)
+            if kernel == headline and pairing:
                 # mate pairing of the batch's device result (outside the timed search)
                 _, o, h = r.tensors()
-                out = torch.zeros(sub.n // 2 * mica.PAIR_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+                pout = torch.zeros(sub.n // 2 * mica.PAIR_DTYPE.itemsize, dtype=torch.uint8, device=dev)
                 p0 = torch.cuda.Event(enable_timing=True)
                 p1 = torch.cuda.Event(enable_timing=True)
                 p0.record(stream)
-                mica.pair_device(o, h, d[2], sub.n // 2, PAIR_WINDOW[0], PAIR_WINDOW[1], out, stream=stream)
+                mica.pair_device(o, h, d[2], sub.n // 2, PAIR_WINDOW[0], PAIR_WINDOW[1], pout, stream=stream)
                 p1.record(stream)
                 p1.synchronize()
                 pair_ms += p0.elapsed_time(p1)
-                pr = out.cpu().numpy().view(mica.PAIR_DTYPE)
+                pr = pout.cpu().numpy().view(mica.PAIR_DTYPE)
                 paired += int(np.count_nonzero(pr["n_concordant"]))
-            tot_ms += ms[0]
-            tot_kms += kms[0]
+            tot_ms += statistics.mean(ms)
+            tot_kms += statistics.mean(kms)
             nodes += st["nodes"]
             blocks += st["rank_blocks"]
             seeds += st["seeds"]
+            ivs += st["intervals"]
+            retries += st["retries"]
             hits += r.n_hits
         res[kernel] = {"value": round(b.n / (tot_ms / 1e3), 1), "pairs_per_s": round(b.n / 2 / (tot_ms / 1e3), 1),
                        "ms_total": round(tot_ms, 1), "kernel_ms_total": round(tot_kms, 1), "nodes": int(nodes),
-                       "rank_blocks": int(blocks), "seeds": int(seeds), "hits": int(hits)}
+                       "rank_blocks": int(blocks), "seeds": int(seeds), "intervals": int(ivs),
+                       "retries": int(retries), "hits": int(hits)}
     peaks, src = measured_peaks()
-    p = res["persistent"]
-    alg = 32 * p["rank_blocks"] + 8 * p["seeds"]
+    p = res[headline]
+    read_bytes = 4 * int(np.sum((b.lengths.astype(np.int64) + 15) // 16))
+    alg = search_alg_bytes(headline, p, read_bytes)
     achieved = alg / (p["kernel_ms_total"] / 1e3) / 1e9
-    out = {"metric": "150bp mates/s aligned (k<=2 FM search), human-scale genome", "value": p["value"],
-           "unit": "reads/s", "n_gpus": 1, "higher_is_better": True, "dtype": "u32", "data": "synthetic",
-           "config": {"workload": f"{g.n / 1e9:.2f} Gbp synthetic genome (~45% repeats), {args.pairs} pairs "
-                                  f"(2x150 bp), k<=2 per mate, cap 1000", "batch_reads": batch,
-                      "index_bytes": int(info["occ_bytes"] + info["mark_bytes"] + info["sample_bytes"] + info["table_bytes"])},
-           "persistent": res["persistent"], "plain": res["plain"],
-           "pairing": {"properly_paired": round(paired / (b.n // 2), 4), "window": list(PAIR_WINDOW),
-                       "kernel_ms_total": round(pair_ms, 1),
-                       "what": "pairs with a concordant placement (opposite strands, fragment in the window) "
-                               "among their listed hits; mica_pair_device after each batch"},
-           "persistent_over_plain": round(res["persistent"]["value"] / res["plain"]["value"], 3),
+    hot = int(info["occ_bytes"] + info["rev_occ_bytes"] + info["table_bytes"] + info["rev_table_bytes"])
+    ceil = mica.gather_ceiling((hot + 31) // 32 * 32, 32, loads=1 << 27, repeats=3)
+    traffic = profile_traffic(BIDIR_CU if headline == "bidirectional" else SEARCH_CU,
+                              PROFILE_BIDIR_HUMAN if headline == "bidirectional" else PROFILE_HUMAN,
+                              "dram_bytes_search_step")
+    n_batches = max(1, -(-b.n // batch))
+    out = {"workload": f"{n_genome / 1e9:.2f} Gbp synthetic genome (~45% repeats), index resident in HBM; "
+                       f"{pairs} pairs (2x150 bp), k<=2 per mate, cap 1000",
+           "value": p["value"], "unit": "mates/s", "kernel": KERNEL_LABEL[headline],
+           "batch_mates": min(batch, b.n), "steps": steps,
+           "index_bytes": int(info["occ_bytes"] + info["mark_bytes"] + info["sample_bytes"] + info["table_bytes"]
+                              + info["rev_occ_bytes"] + info["rev_table_bytes"]),
+           headline: res[headline], other: res[other],
+           f"{headline}_over_{other}": round(res[headline]["value"] / res[other]["value"], 3),
            "generate_s": round(gen_s, 1), "index_build_s": round(build_s, 1),
-           "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                        "frac": round(achieved / peaks["hbm_gbs"], 4), "kernel": "k_persistent",
-                        "alg_bytes": int(alg), "peak_source": f"{src} hbm_gbs (copy bandwidth)"}}
+           "roofline": {"bound": "hbm_random_gather", "achieved": round(achieved, 1), "peak": round(ceil["gbs"], 1),
+                        "unit": "GB/s", "frac": round(achieved / ceil["gbs"], 4),
+                        "traffic": traffic, "kernel": KERNEL_NAMES[headline],
+                        "alg_bytes_per_launch": int(alg / n_batches), "alg_bytes_what": ALG_LABEL[headline],
+                        "peak_source": f"measured in this run: random 32 B gathers over {hot >> 20} MiB "
+                                       "(the index's occurrence blocks and q-mer tables of both directions: HBM)",
+                        "hbm_copy_peak": peaks["hbm_gbs"], "frac_of_hbm_copy": round(achieved / peaks["hbm_gbs"], 4),
+                        "hbm_copy_peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)"}}
+    if "plain" in res:
+        out["plain"] = res["plain"]
+        out["batched_over_plain"] = round(res[headline]["value"] / res["plain"]["value"], 3)
+    if pairing:
+        out["pairing"] = {"properly_paired": round(paired / (b.n // 2), 4), "window": list(PAIR_WINDOW),
+                          "kernel_ms_total": round(pair_ms, 1),
+                          "what": "pairs with a concordant placement (opposite strands, fragment in the window) "
+                                  "among their listed hits; mica_pair_device after each batch"}
+    idx.free()
+    return out
+
+
+def run_human(args):
+    """Human-scale workload on its own: all `--pairs` pairs in batches of 2M mates."""
+    import torch
+    import paper_1402_4876_gb300 as mica
+    dev = torch.device("cuda", 0)
+    leg = human_leg(mica, dev, torch.cuda.current_stream(dev), args.pairs, args.genome_bp, steps=1,
+                    headline=args.kernel)
+    out = {"metric": "150bp mates/s aligned (k<=2 FM search), human-scale genome", "value": leg["value"],
+           "unit": "reads/s", "n_gpus": 1, "higher_is_better": True, "dtype": "u32", "data": "synthetic",
+           "config": {"workload": leg["workload"]}, "human": leg}
     print(json.dumps(out), flush=True)
 
 
 def run_serve(args):
     """Serving: requests of log-uniform size (1e3..1e6 reads; lengths
-    100/150/250, k 0..2) arrive as a Poisson process at 50/70/90% of the
-    sustained rate into the continuous-batching server; p50/p99 latency is
-    submit to completion on the host clock."""
+    100/150/250, k 0..2) drawn from the human-scale donor arrive as a Poisson
+    process at 50/70/90% of the sustained rate into the continuous-batching
+    server over the resident 3.1 Gbp index; p50/p99 latency is submit to
+    completion on the host clock.  Arrivals are open-loop: a submitting thread
+    follows the drawn schedule, another thread collects results."""
+    import threading
     import torch
     import paper_1402_4876_gb300 as mica
-    dev = torch.device("cuda", 0)
     g = synth.human_genome(args.genome_bp)
     donor = synth.donor_of(g)
-    idx = mica.Index.build(synth.to_acgt_bytes(g.codes), kmer_q=12, sa_sample=16)
-    rng = np.random.default_rng(synth.SEED_ARRIVALS)
+    acgt = synth.to_acgt_bytes(g.codes)
+    n_genome = g.n
+    del g
+    t0 = time.perf_counter()
+    idx = mica.Index.build(acgt, kmer_q=12, sa_sample=16)
+    build_s = time.perf_counter() - t0
+    del acgt
+    size_range = (1_000, args.serve_max_size)
     n_req = args.serve_requests
-    allreq = synth.serve_requests(donor, 8 + 3 * n_req, max_size=args.serve_max_size)
-    reqs = allreq[:8]
-    # sustained rate: back-to-back requests
-    with mica.Server(idx, hit_cap=HIT_CAP, workers=2) as srv:
-        t = time.perf_counter()
-        ids = [srv.submit_batch(r) for r in reqs]
-        for i in ids:
-            srv.wait(i)
-        sustained = sum(r.n for r in reqs) / (time.perf_counter() - t)
-    levels = {}
-    for li, frac in enumerate((0.5, 0.7, 0.9)):
-        batch = allreq[8 + li * n_req: 8 + (li + 1) * n_req]
-        mean_reads = np.mean([r.n for r in batch])
-        rate = frac * sustained / mean_reads                     # requests per second
-        gaps = rng.exponential(1.0 / rate, size=len(batch))
-        lat = []
-        with mica.Server(idx, hit_cap=HIT_CAP, workers=2) as srv:
-            t0 = time.perf_counter()
-            ids = []
-            for gap, r in zip(gaps, batch):
-                time.sleep(gap)
-                ids.append(srv.submit_batch(r))
-            for i in ids:
-                _, l = srv.wait(i)
-                lat.append(l)
-            el = time.perf_counter() - t0
+    workers, chunk, tick = 2, args.serve_chunk, args.serve_tick
+
+    def run_level(reqs, gaps):
+        lat, done = [None] * len(reqs), [0]
+        with mica.Server(idx, hit_cap=HIT_CAP, workers=workers, chunk_reads=chunk, max_tick_reads=tick,
+                         kernel=args.serve_kernel) as srv:
+            ids = [None] * len(reqs)
+            ready = threading.Semaphore(0)
+
+            def submitter():
+                t_next = time.perf_counter()
+                for j, (gap, r) in enumerate(zip(gaps, reqs)):
+                    t_next += gap
+                    dt = t_next - time.perf_counter()
+                    if dt > 0:
+                        time.sleep(dt)
+                    ids[j] = srv.submit_batch(r)
+                    ready.release()
+
+            th = threading.Thread(target=submitter)
+            t_start = time.perf_counter()
+            th.start()
+            for j in range(len(reqs)):
+                ready.acquire()
+                _, lat[j] = srv.wait(ids[j])
+            el = time.perf_counter() - t_start
+            th.join()
             st = srv.stats()
-        levels[f"{int(frac * 100)}%"] = {"p50_ms": round(float(np.percentile(lat, 50)), 2),
-                                         "p99_ms": round(float(np.percentile(lat, 99)), 2),
-                                         "reads_per_s": round(sum(r.n for r in batch) / el, 1),
-                                         "requests": len(batch), "ticks": int(st["ticks"])}
+        return lat, el, st
+
+    # sustained rate: 16 requests queued back to back
+    base = synth.serve_requests(donor, 16, seed=synth.SEED_READS_SERVE, size_range=size_range)
+    _, el, st = run_level(base, [0.0] * len(base))
+    sustained = sum(r.n for r in base) / el
+    levels = {}
+    clocks = []
+    for li, frac in enumerate((0.5, 0.7, 0.9)):
+        reqs = synth.serve_requests(donor, n_req, seed=synth.SEED_READS_SERVE + 1 + li, size_range=size_range)
+        rng = np.random.default_rng(synth.SEED_ARRIVALS + li)
+        mean_reads = np.mean([r.n for r in reqs])
+        rate = frac * sustained / mean_reads                     # requests per second
+        gaps = rng.exponential(1.0 / rate, size=len(reqs))
+        with ClockSampler(0) as clk:
+            lat, el, st = run_level(reqs, gaps)
+        clocks.append(clk.summary())
+        sizes = np.array([r.n for r in reqs])
+        lat = np.array(lat)
+        small = sizes <= np.percentile(sizes, 50)
+        levels[f"{int(frac * 100)}%"] = {
+            "p50_ms": round(float(np.percentile(lat, 50)), 2), "p99_ms": round(float(np.percentile(lat, 99)), 2),
+            "p50_ms_smaller_half": round(float(np.percentile(lat[small], 50)), 2),
+            "p99_ms_smaller_half": round(float(np.percentile(lat[small], 99)), 2),
+            "offered_reads_per_s": round(frac * sustained, 1),
+            "reads_per_s": round(int(sizes.sum()) / el, 1), "requests": len(reqs), "wall_s": round(el, 2),
+            "ticks": int(st["ticks"]), "device_bytes_in_use": int(st["device_bytes_in_use"]),
+            "clocks": clocks[-1]}
+        del reqs
     out = {"metric": "serving: p50/p99 request latency and sustained reads/s", "value": round(sustained, 1),
-           "unit": "reads/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
-           "config": {"workload": f"{g.n / 1e9:.2f} Gbp genome resident; Poisson requests of log-uniform "
-                                  f"1e3..{args.serve_max_size} reads (100/150/250 bp, k 0..2)",
-                      "workers": 2, "requests_per_level": n_req},
+           "unit": "reads/s", "n_gpus": 1, "higher_is_better": True, "dtype": "u32", "data": "synthetic",
+           "config": {"workload": f"{n_genome / 1e9:.2f} Gbp genome resident; Poisson requests of log-uniform "
+                                  f"{size_range[0]}..{size_range[1]} reads (100/150/250 bp, k 0..2)",
+                      "workers": workers, "chunk_reads": chunk, "max_tick_reads": tick, "kernel": args.serve_kernel,
+                      "requests_per_level": n_req,
+                      "index_build_s": round(build_s, 1)},
            "levels": levels}
     print(json.dumps(out), flush=True)
 

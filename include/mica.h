@@ -70,16 +70,21 @@ typedef struct mica_index mica_index;
 typedef struct {
     uint32_t kmer_q;     /* q-mer seed table length, 1..12: table of 4^q + 1 uint32 bounds */
     uint32_t sa_sample;  /* text sampling rate s, 1..256: SA[j] kept when SA[j] % s == 0 */
-    uint32_t lower_bounds; /* 1: also build the reversed genome's occurrence blocks (one more
-                              suffix array at build time, +1/3 device memory) so searches can
-                              prune by mismatch lower bounds; 0: not */
+    uint32_t lower_bounds; /* 1: also build the reversed genome's occurrence blocks and q-mer
+                              table (one more suffix array at build time, about +1/3 device
+                              memory) so searches can prune by mismatch lower bounds and extend
+                              patterns in both directions; 0: not */
 } mica_index_params;
 
 enum {
     MICA_KERNEL_PERSISTENT = 0,      /* one launch of the warp-cooperative work-pool kernel */
     MICA_KERNEL_PLAIN = 1,           /* one launch of the one-task-per-thread kernel over the batch */
-    MICA_KERNEL_PLAIN_BY_LENGTH = 2  /* one plain launch per read-length class (1-64, 65-128,
+    MICA_KERNEL_PLAIN_BY_LENGTH = 2, /* one plain launch per read-length class (1-64, 65-128,
                                         129-192, 193-256 bases), each with its own block size */
+    MICA_KERNEL_BIDIRECTIONAL = 3    /* one launch of the warp-pool kernel searching both directions: the
+                                        read in k + 1 pieces, one search per leftmost exact piece, over the
+                                        genome's and the reversed genome's index (needs an index built with
+                                        lower_bounds = 1, format 4; MICA_EINVAL otherwise).  Same result */
 };
 
 typedef struct {
@@ -148,6 +153,8 @@ typedef struct {
     uint64_t idle_wait_ns;   /* persistent kernel: nanoseconds slept by warps with no work */
     uint64_t overflow_moves; /* persistent kernel: nodes moved to a warp's private overflow stack */
     uint64_t grid_ctas;      /* persistent kernel: CTAs of the launch (SMs x resident CTAs per SM) */
+    uint64_t fallback_reads; /* bidirectional kernel: reads it gave up on (over the node budget, or on a
+                                warp whose overflow stack filled), searched again by the persistent kernel */
     float search_ms;         /* device time of the search phase (kernel + its control copies) */
     float kernel_ms;         /* device time of the search kernel launch(es) alone, with the
                                 lower-bound pass when pruning */
@@ -164,6 +171,7 @@ typedef struct {
     int32_t device;
     uint32_t lower_bounds;   /* 1 if the reversed genome's occurrence blocks are resident */
     uint64_t rev_occ_bytes;  /* their size (0 without them) */
+    uint64_t rev_table_bytes; /* the reversed genome's q-mer table (bidirectional search; 0 without it) */
 } mica_index_info;
 
 const char *mica_strerror(int code);
@@ -187,8 +195,9 @@ int mica_index_build_resident(const uint8_t *genome_acgt, uint64_t len,
 int mica_index_build(const uint8_t *genome_acgt, uint64_t len,
                      const mica_index_params *params, const char *out_path);
 
-/* Index files (format version 3) hold the reversed genome's blocks when the
-   index has them; version 2 files (without them) still load. */
+/* Index files (format version 4) hold the reversed genome's blocks and q-mer
+   table when the index has them; version 3 files (blocks, no table) and
+   version 2 files (neither) still load. */
 int mica_index_save(const mica_index *idx, const char *path);
 /* Read an index file and upload it to `device`, where it stays until freed. */
 int mica_index_load(const char *path, int device, mica_index **out);
@@ -230,6 +239,10 @@ typedef struct {
                                occurrence blocks of the next round's nodes.  -1 = automatic (on
                                when the occurrence blocks exceed 96 MiB and so do not stay in
                                L2), 0 = off, 1 = on */
+    uint32_t bidir_budget;  /* bidirectional kernel: node expansions a task may take before it hands
+                               its pending nodes to the next launch round, where they are tasks of
+                               their own on every warp (bounds each round's tail; no effect on
+                               results); 0 = 4096 */
 } mica_tuning;
 
 /* Number of compiled persistent kernel shapes; mica_tuning_shape_info
@@ -270,41 +283,56 @@ int mica_tuning_cache_lookup(const char *path, const mica_index *idx, uint32_t l
  * The paper's host keeps the accelerator busy with batches of about a million
  * reads while it handles the waiting (Section 2, "Pipelining & load
  * balancing").  Here a server owns worker threads (each with its own CUDA
- * stream and workspace) that keep admitting queued requests, FIFO, while the
- * reads fit the tick size and the requests' device-memory estimates fit the
- * budget; the admitted requests of one tick share one search launch, so their
- * work interleaves on the device, and with two or more workers one tick's
- * search overlaps another's hit assembly and copies.  A request's result is
- * identical to aligning it alone with mica_align_batch.  The index must stay
- * alive until mica_server_stop returns; it may still be used by the caller's
- * own align calls (those use the index's workspace, the server uses its own).
+ * stream and workspace).  A request is split on submit into chunks of at most
+ * chunk_reads reads.  A worker forms a tick by taking the next chunk of every
+ * queued request in arrival order, then their following chunks, round after
+ * round, while the tick's reads fit max_tick_reads and the device memory its
+ * search needs (mica_server_workspace_bytes) fits the worker's share of
+ * max_device_bytes; the tick is one search launch, so the work of its
+ * requests interleaves on the device, and with two or more workers one tick's
+ * search overlaps another's hit assembly and copies.  A large request so
+ * advances a chunk per tick beside later small ones.  A request completes
+ * when its last chunk does, and its result is identical to aligning it alone
+ * with mica_align_batch.  The index must stay alive until mica_server_stop
+ * returns; it may still be used by the caller's own align calls (those use
+ * the index's workspace, the server uses its own).
  */
 typedef struct mica_server mica_server;
 
 typedef struct {
-    uint64_t max_device_bytes;  /* device memory for admitted requests; 0 = half the free memory at start */
-    uint64_t max_tick_reads;    /* reads per search launch (a larger single request runs alone); 0 = 2^20 */
+    uint64_t max_device_bytes;  /* device memory for the workers' workspaces (each worker may use an equal
+                                   share); 0 = half the free memory at start */
+    uint64_t max_tick_reads;    /* reads per search launch; 0 = 2^20 */
     uint32_t hit_cap;           /* as mica_align_params.hit_cap, for every request */
     int32_t kernel;             /* MICA_KERNEL_* */
     int32_t workers;            /* concurrent ticks, 1..8; 0 = 2 */
     int32_t start_paused;       /* nonzero: queue requests but admit none until mica_server_resume */
+    uint64_t chunk_reads;       /* largest piece of a request in one tick; 0 = 2^18 (smaller when a
+                                   worker's share of the memory cannot hold it) */
 } mica_server_params;
 
 typedef struct {
     uint64_t submitted, completed, failed, cancelled;
     uint64_t ticks;             /* search launches run */
     uint64_t reads;             /* reads of completed requests */
-    uint64_t pending;           /* queued, not yet admitted */
-    uint64_t device_bytes_in_use, device_budget;
+    uint64_t pending;           /* requests with chunks not yet admitted */
+    uint64_t device_bytes_in_use, device_budget;   /* workspace the workers' ticks have needed (each
+                                                      worker's largest; workspaces only grow), budget */
     double busy_s;              /* summed wall time of ticks over all workers */
 } mica_server_stats;
 
 void mica_server_params_default(mica_server_params *p);
 /* Start the worker threads on idx's device.  params may be NULL (defaults). */
 int mica_server_start(mica_index *idx, const mica_server_params *params, mica_server **out);
+/* Device bytes a worker's workspace needs to run one tick of n_reads reads
+   held in n_words packed words (the staged batch, the search's buffers incl.
+   the persistent grid's overflow stacks, and the hit assembly's at 4 hits per
+   read): what admission charges against a worker's share. */
+int mica_server_workspace_bytes(const mica_index *idx, uint64_t n_reads, uint64_t n_words, uint64_t *bytes);
 /* Queue a host batch (same layout as mica_align_batch; copied before return).
-   MICA_EINVAL for a bad batch, MICA_ENOMEM if its estimate exceeds the whole
-   budget (it could never be admitted), MICA_EBUSY after stop. */
+   MICA_EINVAL for a bad batch, MICA_ENOMEM if a worker's share of the budget
+   cannot hold even a one-read tick (nothing could ever be admitted),
+   MICA_EBUSY after stop. */
 int mica_server_submit(mica_server *srv, const uint32_t *packed_reads, const uint64_t *word_offsets,
                        const uint16_t *lengths, const uint8_t *k, uint64_t n_reads, uint64_t *req_id);
 /* MICA_EBUSY while queued or running.  Once done, returns the request's status
@@ -315,12 +343,13 @@ int mica_server_poll(mica_server *srv, uint64_t req_id, mica_result **out, doubl
 /* As poll, waiting up to timeout_ms; MICA_ETIMEOUT if still not done. */
 int mica_server_wait(mica_server *srv, uint64_t req_id, uint32_t timeout_ms, mica_result **out,
                      double *latency_ms);
-/* Drop a queued request (MICA_EBUSY once a tick has taken it). */
+/* Drop a queued request (MICA_EBUSY once a tick has taken one of its chunks). */
 int mica_server_cancel(mica_server *srv, uint64_t req_id);
 void mica_server_resume(mica_server *srv);
 int mica_server_get_stats(mica_server *srv, mica_server_stats *out);
-/* Finish the ticks in flight, drop queued requests, join the workers, free
-   uncollected results. */
+/* Finish the ticks in flight and the requests they have started, drop the
+   queued requests no tick has taken, join the workers, free uncollected
+   results. */
 void mica_server_stop(mica_server *srv);
 
 /* ---- mate pairing (after the search; no effect on its result) ----

@@ -30,7 +30,7 @@ MICA_EINTERNAL = -6
 MICA_EBUSY = -7
 MICA_ENOTFOUND = -8
 MAX_READ_LEN = 256
-KERNELS = {"persistent": 0, "plain": 1, "plain_by_length": 2}
+KERNELS = {"persistent": 0, "plain": 1, "plain_by_length": 2, "bidirectional": 3}
 REPORTS = {"all": 0, "best_stratum": 1}
 
 HIT_DTYPE = np.dtype([("pos", "<u4"), ("strand", "u1"), ("mm", "u1"), ("pad", "<u2")])
@@ -66,7 +66,7 @@ class Stats(ctypes.Structure):
                 ("tasks", "seeds", "nodes", "rank_blocks", "intervals", "located", "lf_steps",
                  "spills", "retries", "launches", "warp_rounds", "lane_ops", "rounds_multi", "rounds_single",
                  "rounds_seed", "graph_captures", "graph_replays", "graph_fallbacks", "lb_steps",
-                 "lb_dead_tasks", "queue_wait_ns", "idle_wait_ns", "overflow_moves", "grid_ctas")] + [("search_ms", ctypes.c_float), ("kernel_ms", ctypes.c_float),
+                 "lb_dead_tasks", "queue_wait_ns", "idle_wait_ns", "overflow_moves", "grid_ctas", "fallback_reads")] + [("search_ms", ctypes.c_float), ("kernel_ms", ctypes.c_float),
                                                       ("total_ms", ctypes.c_float)]
 
     def as_dict(self) -> dict:
@@ -75,7 +75,8 @@ class Stats(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("shape", ctypes.c_int32), ("plain_block", ctypes.c_uint32), ("plain_budget", ctypes.c_uint32),
-                ("plain_block_len", ctypes.c_uint32 * 4), ("prefetch", ctypes.c_int32)]
+                ("plain_block_len", ctypes.c_uint32 * 4), ("prefetch", ctypes.c_int32),
+                ("bidir_budget", ctypes.c_uint32)]
 
 
 def tuning_shapes() -> list:
@@ -92,7 +93,7 @@ def tuning_shapes() -> list:
 class ServerParams(ctypes.Structure):
     _fields_ = [("max_device_bytes", ctypes.c_uint64), ("max_tick_reads", ctypes.c_uint64),
                 ("hit_cap", ctypes.c_uint32), ("kernel", ctypes.c_int32), ("workers", ctypes.c_int32),
-                ("start_paused", ctypes.c_int32)]
+                ("start_paused", ctypes.c_int32), ("chunk_reads", ctypes.c_uint64)]
 
 
 class ServerStats(ctypes.Structure):
@@ -106,7 +107,8 @@ class IndexInfo(ctypes.Structure):
                 ("sa_sample", ctypes.c_uint32), ("dollar_row", ctypes.c_uint64),
                 ("C", ctypes.c_uint64 * 5), ("occ_bytes", ctypes.c_uint64), ("mark_bytes", ctypes.c_uint64),
                 ("sample_bytes", ctypes.c_uint64), ("table_bytes", ctypes.c_uint64), ("device", ctypes.c_int32),
-                ("lower_bounds", ctypes.c_uint32), ("rev_occ_bytes", ctypes.c_uint64)]
+                ("lower_bounds", ctypes.c_uint32), ("rev_occ_bytes", ctypes.c_uint64),
+                ("rev_table_bytes", ctypes.c_uint64)]
 
 
 # exported symbol -> (restype, argtypes); the C ABI's full surface
@@ -168,6 +170,7 @@ SIGNATURES = {
     "mica_sam_close": (_i32, [P]),
     "mica_server_params_default": (None, [P]),
     "mica_server_start": (_i32, [P, P, P]),
+    "mica_server_workspace_bytes": (_i32, [P, _u64, _u64, P]),
     "mica_server_submit": (_i32, [P, P, P, P, P, _u64, P]),
     "mica_server_poll": (_i32, [P, _u64, P, P]),
     "mica_server_wait": (_i32, [P, _u64, _u32, P, P]),
@@ -349,8 +352,8 @@ class Index:
         return d
 
     def set_tuning(self, shape: int = -1, plain_block: int = 0, plain_budget: int = 0, plain_block_len=(0, 0, 0, 0),
-                   prefetch: int = -1):
-        t = Tuning(shape, plain_block, plain_budget, (ctypes.c_uint32 * 4)(*plain_block_len), prefetch)
+                   prefetch: int = -1, bidir_budget: int = 0):
+        t = Tuning(shape, plain_block, plain_budget, (ctypes.c_uint32 * 4)(*plain_block_len), prefetch, bidir_budget)
         _check(_lib.mica_set_tuning(self._h, ctypes.byref(t)), "mica_set_tuning")
 
     def autotune(self, batch, hit_cap: int = 1000, repeats: int = 2, cache: str | None = None) -> dict:
@@ -383,7 +386,7 @@ class Index:
         t = Tuning()
         _check(_lib.mica_get_tuning(self._h, ctypes.byref(t)), "mica_get_tuning")
         return {"shape": t.shape, "plain_block": t.plain_block, "plain_budget": t.plain_budget,
-                "plain_block_len": list(t.plain_block_len), "prefetch": t.prefetch}
+                "plain_block_len": list(t.plain_block_len), "prefetch": t.prefetch, "bidir_budget": t.bidir_budget}
 
     def stats(self) -> dict:
         s = Stats()
@@ -464,11 +467,12 @@ class Server:
     """Continuous-batching request loop over a resident index (mica_server_*)."""
 
     def __init__(self, index: Index, max_device_bytes: int = 0, max_tick_reads: int = 0, hit_cap: int = 1000,
-                 kernel="persistent", workers: int = 2, start_paused: bool = False):
+                 kernel="persistent", workers: int = 2, start_paused: bool = False, chunk_reads: int = 0):
         p = ServerParams()
         _lib.mica_server_params_default(ctypes.byref(p))
         p.max_device_bytes = max_device_bytes
         p.max_tick_reads = max_tick_reads
+        p.chunk_reads = chunk_reads
         p.hit_cap = hit_cap
         p.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
         p.workers = workers
@@ -477,6 +481,14 @@ class Server:
         h = ctypes.c_void_p()
         _check(_lib.mica_server_start(index._h, ctypes.byref(p), ctypes.byref(h)), "mica_server_start")
         self._h = h
+
+    @staticmethod
+    def workspace_bytes(index: Index, n_reads: int, n_words: int) -> int:
+        """Device bytes one worker needs for a tick of n_reads reads (mica_server_workspace_bytes)."""
+        b = ctypes.c_uint64()
+        _check(_lib.mica_server_workspace_bytes(index._h, n_reads, n_words, ctypes.byref(b)),
+               "mica_server_workspace_bytes")
+        return int(b.value)
 
     def submit(self, words, word_off, lengths, k) -> int:
         words = np.ascontiguousarray(words, dtype=np.uint32)

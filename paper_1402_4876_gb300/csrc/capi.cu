@@ -149,7 +149,7 @@ void free_workspace(Workspace &w)
 {
     DevBuf *all[] = {&w.ctl, &w.iv, &w.iv_sorted, &w.iv_cnt, &w.iv_off, &w.total, &w.keep, &w.hit_off,
                      &w.hits, &w.spill, &w.big, &w.scan_tmp, &w.reads_words, &w.reads_off, &w.reads_len,
-                     &w.reads_k, &w.spill2, &w.lenlist, &w.lb, &w.spill_seq, &w.deep};
+                     &w.reads_k, &w.spill2, &w.lenlist, &w.lb, &w.spill_seq, &w.deep, &w.redo, &w.frontier};
     for (DevBuf *b : all) dev_release(*b);
     for (auto &e : w.ev)
         if (e) { cudaEventDestroy(e); e = nullptr; }
@@ -210,6 +210,13 @@ struct FileHeaderRev {
     uint64_t rev_C[5];
 };
 
+// Version 4 adds this block after FileHeaderRev; when has_rev_table is 1 the
+// reversed genome's q-mer table (table_len uint32) follows its superblocks.
+struct FileHeaderRevTable {
+    uint32_t has_rev_table, rev_nshort;
+    uint32_t rev_short_pad[MAX_Q], rev_short_len[MAX_Q];
+};
+
 static int write_array(FILE *f, const DevBuf &b, uint64_t bytes)
 {
     std::vector<char> h(std::min<uint64_t>(bytes, 1ull << 26));
@@ -259,7 +266,13 @@ static int align_graph(const mica_index *idx, Workspace &w, mica_stats &st, cons
     if (!w.gstream) MICA_CUDA_TRY(cudaStreamCreateWithFlags(&w.gstream, cudaStreamNonBlocking));
     SearchCtl tmpl;
     int grid = 0, shape = 0, rc;
-    if ((rc = prepare_persistent(idx, w, n, idx->tuning.shape, tmpl, grid, shape))) return rc;
+    const bool bidir = p.kernel == MICA_KERNEL_BIDIRECTIONAL;
+    if (bidir) {
+        if ((rc = prepare_bidir(idx, w, n, tmpl, grid))) return rc;
+        shape = 1 << 8;   // distinguishes the bidirectional kernel in the key
+    } else if ((rc = prepare_persistent(idx, w, n, idx->tuning.shape, tmpl, grid, shape))) {
+        return rc;
+    }
     w.hit_capacity = std::max<uint64_t>(w.hit_capacity, 4 * n + 65536);
     if ((rc = reserve_post(w, n, w.iv_cap, w.hit_capacity))) return rc;
     memcpy(w.pin_tmpl, &tmpl, sizeof(tmpl));
@@ -275,13 +288,15 @@ static int align_graph(const mica_index *idx, Workspace &w, mica_stats &st, cons
                                (uint64_t)w.total.p, (uint64_t)w.keep.p, (uint64_t)w.hit_off.p, (uint64_t)w.hits.p,
                                (uint64_t)w.big.p, (uint64_t)w.scan_tmp.p, w.hit_capacity, (uint64_t)w.iv_cap,
                                (uint64_t)w.spill_cap, (uint64_t)w.spill_seq.p, (uint64_t)w.deep.p,
-                               (uint64_t)p.report, ((uint64_t)idx->idle_limit << 32) | idx->spin_limit};
+                               (uint64_t)p.report | ((uint64_t)idx->tuning.bidir_budget << 32),
+                               ((uint64_t)idx->idle_limit << 32) | idx->spin_limit};
     if (!w.gexec || memcmp(key, w.gkey, sizeof(key)) != 0) {
         if (w.gexec) { cudaGraphExecDestroy(w.gexec); w.gexec = nullptr; }
         uint64_t L = 0;
         MICA_CUDA_TRY(cudaStreamBeginCapture(w.gstream, cudaStreamCaptureModeThreadLocal));
-        int crc = enqueue_persistent(idx, w, rd, shape, grid, (const SearchCtl *)w.pin_tmpl, prune, prefetch,
-                                     w.gstream, L);
+        int crc = bidir ? enqueue_bidir_graph(idx, w, rd, grid, (const SearchCtl *)w.pin_tmpl, w.gstream, L)
+                        : enqueue_persistent(idx, w, rd, shape, grid, (const SearchCtl *)w.pin_tmpl, prune, prefetch,
+                                             w.gstream, L);
         if (!crc) crc = enqueue_post_device(idx, w, rd, p.hit_cap, p.report, w.hit_capacity, w.gstream,
                                             w.pin_status, L);
         cudaGraph_t g = nullptr;
@@ -313,6 +328,13 @@ static int align_graph(const mica_index *idx, Workspace &w, mica_stats &st, cons
     if (out.error & ERR_TIMEOUT) return MICA_ETIMEOUT;
     if (out.error) {
         // let the regular path grow the buffers and recompute
+        return 0;
+    }
+    if (bidir && (out.redo_reads || out.fr_count)) {
+        // reads given up, or nodes still exported after the captured rounds:
+        // the regular path runs the rounds to the end and searches the given-up
+        // reads again
+        w.bd_redo_seen = true;
         return 0;
     }
     if (nhits > w.hit_capacity) { w.hit_capacity = 2 * nhits; return 0; }
@@ -357,7 +379,12 @@ int align_on_device(const mica_index *idx, Workspace &w, mica_stats &st, const R
     st = mica_stats{};
     st.launches = launches;
     const bool deepen = p.report == MICA_REPORT_BEST_STRATUM && p.kernel == MICA_KERNEL_PERSISTENT && rd.n > 0;
-    if (allow_graph && !deepen && p.kernel == MICA_KERNEL_PERSISTENT && rd.n > 0) {
+    // (the budget that gives reads up is part of the captured kernel's arguments)
+    // a bidirectional batch that gives reads up needs host steps after the
+    // kernel: after one did, this workspace runs bidirectional calls uncaptured
+    const bool graphable = p.kernel == MICA_KERNEL_PERSISTENT ||
+                           (p.kernel == MICA_KERNEL_BIDIRECTIONAL && !w.bd_redo_seen);
+    if (allow_graph && !deepen && graphable && rd.n > 0) {
         bool done = false;
         if (int rc = align_graph(idx, w, st, rd, p, s, nh, done)) return rc;
         if (done) return 0;
@@ -373,9 +400,20 @@ int align_on_device(const mica_index *idx, Workspace &w, mica_stats &st, const R
     cfg.prefetch = use_prefetch(idx);
     for (uint32_t c = 0; c < LEN_CLASSES; c++)
         cfg.plain_block_len[c] = idx->tuning.plain_block_len[c] ? (int)idx->tuning.plain_block_len[c] : cfg.plain_block;
-    int rc = deepen ? run_search_stratum(idx, w, st, rd, cfg, s) : run_search(idx, w, st, rd, cfg, s);
-    if (rc == STRATUM_FALLBACK) {
-        rc = run_search(idx, w, st, rd, cfg, s);   // exhaustive search, filtered after
+    int rc;
+    if (p.kernel == MICA_KERNEL_BIDIRECTIONAL) {
+        rc = run_search_bidir(idx, w, st, rd, s);
+        if (rc == BIDIR_FALLBACK) {
+            // a warp's overflow stack filled: the one-directional search (same result)
+            st.retries++;
+            cfg.kernel = MICA_KERNEL_PERSISTENT;
+            rc = run_search(idx, w, st, rd, cfg, s);
+        }
+    } else {
+        rc = deepen ? run_search_stratum(idx, w, st, rd, cfg, s) : run_search(idx, w, st, rd, cfg, s);
+        if (rc == STRATUM_FALLBACK) {
+            rc = run_search(idx, w, st, rd, cfg, s);   // exhaustive search, filtered after
+        }
     }
     if (rc) return rc;
     MICA_CUDA_TRY(cudaEventRecord(w.ev[1], s));
@@ -477,7 +515,7 @@ int mica_index_save(const mica_index *idx, const char *path)
     if (!f) return MICA_EIO;
     FileHeader h{};
     memcpy(h.magic, MAGIC, 8);
-    h.version = 3;
+    h.version = 4;
     h.kmer_q = idx->params.kmer_q;
     h.sa_sample = idx->params.sa_sample;
     h.n = idx->n;
@@ -497,8 +535,16 @@ int mica_index_save(const mica_index *idx, const char *path)
     hr.has_rev = idx->has_rev ? 1u : 0u;
     hr.rev_dollar_row = idx->view.rev.dollar_row;
     for (int c = 0; c < 5; c++) hr.rev_C[c] = idx->view.rev.C[c];
+    FileHeaderRevTable ht{};
+    ht.has_rev_table = idx->view.rev.table ? 1u : 0u;
+    ht.rev_nshort = idx->view.rev.nshort;
+    for (uint32_t t = 0; t < MAX_Q; t++) {
+        ht.rev_short_pad[t] = idx->view.rev.short_pad[t];
+        ht.rev_short_len[t] = idx->view.rev.short_len[t];
+    }
     int rc = fwrite(&h, sizeof(h), 1, f) == 1 ? 0 : MICA_EIO;
     if (!rc && fwrite(&hr, sizeof(hr), 1, f) != 1) rc = MICA_EIO;
+    if (!rc && fwrite(&ht, sizeof(ht), 1, f) != 1) rc = MICA_EIO;
     if (!rc) rc = write_array(f, idx->occ, h.n_occ_blocks * 32);
     if (!rc) rc = write_array(f, idx->super, h.n_super * 16);
     if (!rc) rc = write_array(f, idx->marks, h.n_mark_blocks * 64);
@@ -506,6 +552,7 @@ int mica_index_save(const mica_index *idx, const char *path)
     if (!rc) rc = write_array(f, idx->table, h.table_len * 4);
     if (!rc && idx->has_rev) rc = write_array(f, idx->rocc, h.n_occ_blocks * 32);
     if (!rc && idx->has_rev) rc = write_array(f, idx->rsuper, h.n_super * 16);
+    if (!rc && ht.has_rev_table) rc = write_array(f, idx->rtable, h.table_len * 4);
     if (fclose(f) != 0 && !rc) rc = MICA_EIO;
     return rc;
 }
@@ -518,8 +565,11 @@ int mica_index_load(const char *path, int device, mica_index **out)
     if (!f) return MICA_EIO;
     FileHeader h{};
     FileHeaderRev hr{};
-    if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, MAGIC, 8) != 0 || (h.version != 2 && h.version != 3) ||
-        (h.version == 3 && (fread(&hr, sizeof(hr), 1, f) != 1 || hr.has_rev > 1)) ||
+    FileHeaderRevTable ht{};
+    if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, MAGIC, 8) != 0 || h.version < 2 || h.version > 4 ||
+        (h.version >= 3 && (fread(&hr, sizeof(hr), 1, f) != 1 || hr.has_rev > 1)) ||
+        (h.version >= 4 && (fread(&ht, sizeof(ht), 1, f) != 1 || ht.has_rev_table > hr.has_rev ||
+                            (ht.has_rev_table && ht.rev_nshort != h.nshort))) ||
         h.kmer_q < 1 || h.kmer_q > MAX_Q || h.sa_sample < 1 || h.n + 1 >= (1ull << 32) ||
         h.n_occ_blocks != (h.n + 1) / OCC_ROWS + 1 ||
         h.n_super != (h.n_occ_blocks + SB_BLOCKS - 1) / SB_BLOCKS || h.n_mark_blocks != (h.n + 1) / MARK_ROWS + 1 ||
@@ -548,6 +598,7 @@ int mica_index_load(const char *path, int device, mica_index **out)
     if (!rc) rc = read_array(f, idx->table, h.table_len * 4);
     if (!rc && hr.has_rev) rc = read_array(f, idx->rocc, h.n_occ_blocks * 32);
     if (!rc && hr.has_rev) rc = read_array(f, idx->rsuper, h.n_super * 16);
+    if (!rc && ht.has_rev_table) rc = read_array(f, idx->rtable, h.table_len * 4);
     fclose(f);
     idx->has_rev = hr.has_rev != 0;
     idx->params.lower_bounds = hr.has_rev;
@@ -575,6 +626,14 @@ int mica_index_load(const char *path, int device, mica_index **out)
         v.rev.super = idx->has_rev ? (const uint4 *)idx->rsuper.p : nullptr;
         v.rev.dollar_row = hr.rev_dollar_row;
         for (int c = 0; c < 5; c++) v.rev.C[c] = (uint32_t)hr.rev_C[c];
+        v.rev.table = ht.has_rev_table ? (const uint32_t *)idx->rtable.p : nullptr;
+        v.rev.nshort = ht.rev_nshort;
+        v.rev.short_bloom = 0;
+        for (uint32_t t = 0; t < MAX_Q; t++) {
+            v.rev.short_pad[t] = ht.rev_short_pad[t];
+            v.rev.short_len[t] = ht.rev_short_len[t];
+        }
+        for (uint32_t t = 0; t < v.rev.nshort; t++) v.rev.short_bloom |= 1ull << (v.rev.short_pad[t] & 63);
         rc = upload_variants(idx);
     }
     if (rc) { mica_index_free(idx); return rc; }
@@ -595,6 +654,7 @@ void mica_index_free(mica_index *idx)
     dev_release(idx->variants);
     dev_release(idx->rocc);
     dev_release(idx->rsuper);
+    dev_release(idx->rtable);
     free_workspace(idx->ws);
     delete idx;
 }
@@ -615,6 +675,7 @@ int mica_index_get_info(const mica_index *idx, mica_index_info *info)
     info->device = idx->device;
     info->lower_bounds = idx->has_rev ? 1u : 0u;
     info->rev_occ_bytes = idx->has_rev ? idx->n_occ_blocks * 32 + idx->n_super * 16 : 0;
+    info->rev_table_bytes = idx->view.rev.table ? idx->table_len * 4 : 0;
     return 0;
 }
 
@@ -724,7 +785,8 @@ int mica_align_device(mica_index *idx, const uint32_t *d_packed_reads, const uin
     mica_align_params p;
     mica_align_params_default(&p);
     if (params) p = *params;
-    if (p.kernel < MICA_KERNEL_PERSISTENT || p.kernel > MICA_KERNEL_PLAIN_BY_LENGTH) return MICA_EINVAL;
+    if (p.kernel < MICA_KERNEL_PERSISTENT || p.kernel > MICA_KERNEL_BIDIRECTIONAL) return MICA_EINVAL;
+    if (p.kernel == MICA_KERNEL_BIDIRECTIONAL && !bidir_available(idx)) return MICA_EINVAL;
     if (p.report > MICA_REPORT_BEST_STRATUM) return MICA_EINVAL;
     DeviceGuard g(idx->device);
     MICA_CUDA_TRY(cudaSetDevice(idx->device));
@@ -753,7 +815,8 @@ int mica_align_batch(mica_index *idx, const uint32_t *packed_reads, const uint64
     mica_align_params p;
     mica_align_params_default(&p);
     if (params) p = *params;
-    if (p.kernel < MICA_KERNEL_PERSISTENT || p.kernel > MICA_KERNEL_PLAIN_BY_LENGTH) return MICA_EINVAL;
+    if (p.kernel < MICA_KERNEL_PERSISTENT || p.kernel > MICA_KERNEL_BIDIRECTIONAL) return MICA_EINVAL;
+    if (p.kernel == MICA_KERNEL_BIDIRECTIONAL && !bidir_available(idx)) return MICA_EINVAL;
     if (p.report > MICA_REPORT_BEST_STRATUM) return MICA_EINVAL;
     DeviceGuard g(idx->device);
     MICA_CUDA_TRY(cudaSetDevice(idx->device));

@@ -416,6 +416,51 @@ __global__ void k_reverse_codes(const uint8_t *__restrict__ in, uint64_t n, uint
         out[n - 1 - i] = in[i];
 }
 
+// The q-mer table of a text T = codes$ (bound[x] = suffixes of T smaller than
+// the q-mer x) and the A-padded codes of its suffixes shorter than q + 1
+// symbols, which seed lookups correct for.
+int build_qmer_table(const uint8_t *d_codes, uint64_t n, uint32_t q, DevBuf &table, QmerShort &sh, DevBuf &tmp,
+                     cudaStream_t s)
+{
+    uint64_t tl = (1ull << (2 * q)) + 1;
+    uint64_t first = n >= q ? n - q + 1 : 0;
+    std::vector<uint8_t> tail(n - first);
+    if (!tail.empty()) MICA_CUDA_TRY(cudaMemcpy(tail.data(), d_codes + first, tail.size(), cudaMemcpyDeviceToHost));
+    sh = QmerShort{};
+    for (uint64_t i = first; i <= n; i++) {
+        uint32_t code = 0;
+        for (uint32_t t = 0; t < q; t++) code = (code << 2) | (i + t < n ? tail[i + t - first] : 0u);
+        sh.len[sh.nshort] = (uint32_t)(n - i);
+        sh.pad[sh.nshort++] = code;
+        sh.bloom |= 1ull << (code & 63);
+    }
+    DevBuf tcnt;
+    int rc;
+    if ((rc = dev_reserve(tcnt, tl * 4)) || (rc = dev_reserve(table, tl * 4))) { dev_release(tcnt); return rc; }
+    MICA_CUDA_TRY(cudaMemsetAsync(tcnt.p, 0, tl * 4, s));
+    k_qmer_hist<<<grid_for(n + 1), 256, 0, s>>>(d_codes, n, q, (uint32_t *)tcnt.p);
+    k_qmer_short<<<1, 32, 0, s>>>(d_codes, n, q, (uint32_t *)tcnt.p, 0);
+    if ((rc = exclusive_sum_u32(tmp, (const uint32_t *)tcnt.p, (uint32_t *)table.p, tl, s))) {
+        dev_release(tcnt);
+        return rc;
+    }
+    k_qmer_short<<<1, 32, 0, s>>>(d_codes, n, q, (uint32_t *)table.p, 1);
+    MICA_CUDA_TRY(cudaStreamSynchronize(s));
+    MICA_CUDA_TRY(cudaGetLastError());
+    dev_release(tcnt);
+    return 0;
+}
+
+void set_rev_short(IndexView &v, const QmerShort &sh)
+{
+    v.rev.nshort = sh.nshort;
+    v.rev.short_bloom = sh.bloom;
+    for (uint32_t t = 0; t < MAX_Q; t++) {
+        v.rev.short_pad[t] = sh.pad[t];
+        v.rev.short_len[t] = sh.len[t];
+    }
+}
+
 int build_index_from_codes(const uint8_t *d_codes, uint64_t n, const mica_index_params &p,
                            mica_index *idx, cudaStream_t s)
 {
@@ -460,36 +505,15 @@ int build_index_from_codes(const uint8_t *d_codes, uint64_t n, const mica_index_
     // q-mer table
     uint64_t tl = (1ull << (2 * p.kmer_q)) + 1;
     {
-        // A-padded codes of the short suffixes (positions max(0, n-q+1) .. n)
-        uint32_t q = p.kmer_q;
-        uint64_t first = n >= q ? n - q + 1 : 0;
-        std::vector<uint8_t> tail(n - first);
-        if (!tail.empty())
-            MICA_CUDA_TRY(cudaMemcpy(tail.data(), d_codes + first, tail.size(), cudaMemcpyDeviceToHost));
-        idx->view.nshort = 0;
-        idx->view.short_bloom = 0;
-        for (uint64_t i = first; i <= n; i++) {
-            uint32_t code = 0;
-            for (uint32_t t = 0; t < q; t++) code = (code << 2) | (i + t < n ? tail[i + t - first] : 0u);
-            idx->view.short_len[idx->view.nshort] = (uint32_t)(n - i);
-            idx->view.short_pad[idx->view.nshort++] = code;
-            idx->view.short_bloom |= 1ull << (code & 63);
+        QmerShort sh;
+        if ((rc = build_qmer_table(d_codes, n, p.kmer_q, idx->table, sh, tmp, s))) { cleanup(); return rc; }
+        idx->view.nshort = sh.nshort;
+        idx->view.short_bloom = sh.bloom;
+        for (uint32_t t = 0; t < MAX_Q; t++) {
+            idx->view.short_pad[t] = sh.pad[t];
+            idx->view.short_len[t] = sh.len[t];
         }
     }
-    DevBuf tcnt;
-    if ((rc = dev_reserve(tcnt, tl * 4)) || (rc = dev_reserve(idx->table, tl * 4))) {
-        cleanup(); dev_release(tcnt); return rc;
-    }
-    MICA_CUDA_TRY(cudaMemsetAsync(tcnt.p, 0, tl * 4, s));
-    k_qmer_hist<<<grid_for(rows), 256, 0, s>>>(d_codes, n, p.kmer_q, (uint32_t *)tcnt.p);
-    k_qmer_short<<<1, 32, 0, s>>>(d_codes, n, p.kmer_q, (uint32_t *)tcnt.p, 0);
-    if ((rc = exclusive_sum_u32(tmp, (const uint32_t *)tcnt.p, (uint32_t *)idx->table.p, tl, s))) {
-        cleanup(); dev_release(tcnt); return rc;
-    }
-    k_qmer_short<<<1, 32, 0, s>>>(d_codes, n, p.kmer_q, (uint32_t *)idx->table.p, 1);
-    MICA_CUDA_TRY(cudaStreamSynchronize(s));
-    MICA_CUDA_TRY(cudaGetLastError());
-    dev_release(tcnt);
 
     // the reversed genome's occurrence blocks, for mismatch lower bounds
     uint32_t rdollar = 0, rC[5] = {0, 0, 0, 0, 0};
@@ -500,8 +524,13 @@ int build_index_from_codes(const uint8_t *d_codes, uint64_t n, const mica_index_
         rc = build_suffix_array((const uint8_t *)rcodes.p, n, (uint32_t *)sa.p, s);
         if (!rc) rc = build_occ((const uint8_t *)rcodes.p, n, (const uint32_t *)sa.p, idx->rocc, idx->rsuper,
                                 rdollar, rC, s);
+        // and its q-mer table: the seed of a bidirectional search needs the
+        // interval of the reversed q-mer too
+        QmerShort rsh;
+        if (!rc) rc = build_qmer_table((const uint8_t *)rcodes.p, n, p.kmer_q, idx->rtable, rsh, tmp, s);
         dev_release(rcodes);
         if (rc) { cleanup(); return rc; }
+        set_rev_short(idx->view, rsh);
     }
     idx->has_rev = p.lower_bounds != 0;
     cleanup();
@@ -527,6 +556,7 @@ int build_index_from_codes(const uint8_t *d_codes, uint64_t n, const mica_index_
     v.rev.super = idx->has_rev ? (const uint4 *)idx->rsuper.p : nullptr;
     v.rev.dollar_row = rdollar;
     for (int c = 0; c < 5; c++) v.rev.C[c] = rC[c];
+    v.rev.table = idx->has_rev ? (const uint32_t *)idx->rtable.p : nullptr;
     v.q = p.kmer_q;
     v.sa_sample = p.sa_sample;
     return upload_variants(idx);

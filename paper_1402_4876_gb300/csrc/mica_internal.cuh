@@ -70,6 +70,13 @@ struct IndexView {
         const uint4 *super;
         uint32_t dollar_row;
         uint32_t C[5];
+        // q-mer table of G~$ and its short-suffix corrections (as above);
+        // table is null when the index has none (index files before version 4)
+        const uint32_t *table;
+        uint32_t nshort;
+        uint32_t short_pad[MAX_Q];
+        uint32_t short_len[MAX_Q];
+        unsigned long long short_bloom;
     } rev;
 };
 
@@ -127,12 +134,15 @@ struct SearchCtl {
     unsigned long long lb_steps, lb_dead; // lower-bound pass: extensions, tasks with no budget left
     unsigned long long wait_queue_ns, wait_idle_ns;   // sleeps in queue waits / by idle warps (summed)
     unsigned long long deep_moves;                    // nodes moved to per-warp overflow stacks
+    unsigned int redo_reads;                          // bidirectional search: reads given up, to be re-searched
+    unsigned int fr_count;                            // bidirectional search: nodes exported this round
 };
 
 constexpr unsigned ERR_IV_OVERFLOW = 1u;
 constexpr unsigned ERR_SPILL_OVERFLOW = 2u;
 constexpr unsigned ERR_TIMEOUT = 4u;
 constexpr unsigned ERR_HIT_OVERFLOW = 8u;
+constexpr uint32_t IV_PURGED = 0xffffffffu;   // Interval::read of a leaf dropped after the search
 
 // ---------------------------------------------------------------------------
 // Host-side helpers
@@ -166,7 +176,11 @@ struct Workspace {
     DevBuf reads_words, reads_off, reads_len, reads_k;   // staging for host batches
     DevBuf spill2;                                        // plain kernel re-queue ping-pong
     DevBuf lenlist;                                       // plain kernel: reads by length class
+    DevBuf redo;                                          // bidirectional search: given-up reads (bits, list)
+    DevBuf frontier;                                      // bidirectional search: exported nodes, two rounds
     uint32_t iv_cap = 0, spill_cap = 0;
+    uint32_t bd_deep_cap = 0;   // bidirectional search: entries of each warp's overflow stacks
+    bool bd_redo_seen = false;  // bidirectional search: the last call gave reads up (no graph replay then)
     uint64_t hit_cap_total = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // call timing
     cudaEvent_t kev[2] = {nullptr, nullptr};                      // search kernel timing
@@ -188,11 +202,12 @@ struct mica_index {
     uint64_t n = 0;
     uint64_t n_occ_blocks = 0, n_super = 0, n_mark_blocks = 0, n_samples = 0, table_len = 0;
     mica::DevBuf occ, super, marks, samples, table, variants;
-    mica::DevBuf rocc, rsuper;   // reversed genome's occurrence blocks (lower bounds)
+    mica::DevBuf rocc, rsuper;   // reversed genome's occurrence blocks (lower bounds, bidirectional search)
+    mica::DevBuf rtable;         // reversed genome's q-mer table (bidirectional search)
     bool has_rev = false;
     mica::Workspace ws;
     mica_stats stats{};
-    mica_tuning tuning{-1, 0, 0, {0, 0, 0, 0}, -1};
+    mica_tuning tuning{-1, 0, 0, {0, 0, 0, 0}, -1, 0};
     uint32_t idle_limit = 0, spin_limit = 0;   // persistent kernel wait bounds; 0 = built-in defaults
 };
 
@@ -239,6 +254,13 @@ int build_suffix_array(const uint8_t *d_codes, uint64_t n, uint32_t *d_sa, cudaS
 int build_index_from_codes(const uint8_t *d_codes, uint64_t n, const mica_index_params &p,
                            mica_index *idx, cudaStream_t s);
 int upload_variants(mica_index *idx);
+struct QmerShort {
+    uint32_t nshort = 0, pad[MAX_Q] = {}, len[MAX_Q] = {};
+    unsigned long long bloom = 0;
+};
+int build_qmer_table(const uint8_t *d_codes, uint64_t n, uint32_t q, DevBuf &table, QmerShort &sh, DevBuf &tmp,
+                     cudaStream_t s);
+void set_rev_short(IndexView &v, const QmerShort &sh);
 void host_variant_table(uint32_t *out);   // N_VARIANTS entries
 uint32_t variant_count(uint32_t q, uint32_t k);
 
@@ -262,6 +284,8 @@ int prepare_persistent(const mica_index *idx, Workspace &w, uint64_t n, int shap
                        int &grid, int &shape);
 int debug_lower_bounds(const mica_index *idx, Workspace &w, const ReadsView &rd, unsigned long long *d_out,
                        cudaStream_t s);
+int run_search_list(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd, const uint32_t *d_list,
+                    uint32_t n_list, uint32_t iv_base, bool prune, cudaStream_t s);
 constexpr int STRATUM_FALLBACK = 1;   // run_search_stratum: rerun as an exhaustive search
 int run_search_stratum(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd,
                        const SearchConfig &cfg, cudaStream_t s);
@@ -269,6 +293,15 @@ int enqueue_persistent(const mica_index *idx, Workspace &w, const ReadsView &rd,
                        const SearchCtl *pinned_tmpl, bool prune, bool prefetch, cudaStream_t s,
                        uint64_t &launches);
 int search_shape_info(int shape, int *scap, int *warps, int *minb);
+int search_workspace_bytes(const mica_index *idx, uint64_t n, uint64_t *bytes);
+
+// bidir.cu
+constexpr int BIDIR_FALLBACK = 2;   // run_search_bidir: an overflow stack filled; run the one-directional search
+bool bidir_available(const mica_index *idx);
+int prepare_bidir(const mica_index *idx, Workspace &w, uint64_t n, SearchCtl &tmpl, int &grid);
+int enqueue_bidir_graph(const mica_index *idx, Workspace &w, const ReadsView &rd, int grid, const SearchCtl *tmpl_src,
+                        cudaStream_t s, uint64_t &launches);
+int run_search_bidir(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd, cudaStream_t s);
 
 // post.cu
 int run_post(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd, uint32_t hit_cap,
@@ -285,6 +318,7 @@ int enqueue_post_device(const mica_index *idx, Workspace &w, const ReadsView &rd
                         uint32_t report, uint64_t hit_capacity, cudaStream_t s, void *status,
                         uint64_t &launches);
 int reserve_post(Workspace &w, uint64_t n, uint32_t iv_cap, uint64_t hit_capacity);
+uint64_t post_workspace_bytes(uint64_t n, uint64_t iv_cap, uint64_t hit_capacity);
 int exclusive_scan_u64_scratch(const uint64_t *in, uint64_t n, uint64_t *out, unsigned long long *scratch,
                                cudaStream_t s);
 int debug_occ(const mica_index *idx, const uint64_t *d_rows, uint64_t n, uint32_t *d_out, cudaStream_t s);

@@ -134,6 +134,7 @@ __global__ void k_iv_scatter(const Interval *__restrict__ iv, const unsigned int
     uint32_t count = min(*count_p, cap);
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
         Interval x = iv[e];
+        if (x.read == IV_PURGED) continue;   // a leaf of a read that was searched again
         uint32_t at = atomicSub(&cursor[x.read], 1u) - 1u;
         out[iv_off[x.read] + at] = x;
     }
@@ -585,6 +586,14 @@ int enqueue_post_device(const mica_index *idx, Workspace &w, const ReadsView &rd
 }
 
 // Reserve every post-search buffer for n reads and hit_capacity hits.
+// Device bytes reserve_post takes for n reads (the sizes below).
+uint64_t post_workspace_bytes(uint64_t n, uint64_t iv_cap, uint64_t hit_capacity)
+{
+    uint64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    return std::max<uint64_t>(iv_cap, 1) * sizeof(Interval) + 2 * (n + 1) * 8 + 2 * std::max<uint64_t>(n, 1) * 8 +
+           post_list_bytes(n) + (ntiles + 1) * 8 + std::max<uint64_t>(hit_capacity, 1) * sizeof(Hit) + 64;
+}
+
 int reserve_post(Workspace &w, uint64_t n, uint32_t iv_cap, uint64_t hit_capacity)
 {
     int rc;

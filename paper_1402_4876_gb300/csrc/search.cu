@@ -132,7 +132,9 @@ __device__ __forceinline__ uint32_t occ_single_pair(const IndexView &ix, uint32_
 }
 
 __global__ void __launch_bounds__(256) k_lower_bounds(const IndexView ix, const ReadsView rd,
-                                                      unsigned long long *__restrict__ lb, SearchCtl *ctl)
+                                                      unsigned long long *__restrict__ lb, SearchCtl *ctl,
+                                                      const uint32_t *__restrict__ read_list = nullptr,
+                                                      uint64_t n_list = 0)
 {
     IndexView rv = ix;            // the reversed genome's blocks through the same helpers
     rv.occ = ix.rev.occ;
@@ -140,11 +142,11 @@ __global__ void __launch_bounds__(256) k_lower_bounds(const IndexView ix, const 
     rv.dollar_row = ix.rev.dollar_row;
 #pragma unroll
     for (int c = 0; c < 5; c++) rv.C[c] = ix.rev.C[c];
-    const uint64_t ntasks = 2 * rd.n;
+    const uint64_t ntasks = 2 * (read_list ? n_list : rd.n);
     uint32_t steps = 0, blocks = 0, dead = 0;
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < ntasks;
          t += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t rid = (uint32_t)(t >> 1), minus = (uint32_t)(t & 1);
+        const uint32_t rid = read_list ? read_list[t >> 1] : (uint32_t)(t >> 1), minus = (uint32_t)(t & 1);
         const uint32_t m = rd.len[rid], k = rd.k[rid];
         const uint32_t qe = m < ix.q ? m : ix.q, lim = m - qe;
         const uint32_t *w = rd.words + rd.word_off[rid];
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(256) k_lower_bounds(const IndexView ix, const 
                 if (++z > k) break;
             }
         }
-        lb[t] = v;
+        lb[2ull * rid + minus] = v;
         dead += z > k;
     }
     unsigned mask = __activemask();
@@ -1232,6 +1234,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_persistent(PersistArgs a)
 // Host launcher
 // --------------------------------------------------------------------------
 
+static uint32_t ring_capacity(uint64_t n);
+
 // Persistent kernel shapes: (stack capacity, warps per CTA, min CTAs per SM).
 struct PersistShape {
     void (*fn)(PersistArgs);
@@ -1270,6 +1274,24 @@ static int persistent_grid(int device, int shape, int &blocks_per_sm)
 }
 
 int search_shape_count() { return N_SHAPES; }
+
+// Device bytes the persistent search reserves for a batch of n reads (grow-
+// only workspace buffers at their first-call sizes): per-read counters, the
+// interval buffer (4 per read + 65,536), lower-bound words, the spill ring
+// (a power of two >= max(n, 2^20) items) and the grid's per-warp overflow
+// stacks, which do not depend on n.
+int search_workspace_bytes(const mica_index *idx, uint64_t n, uint64_t *bytes)
+{
+    int shape = (idx->tuning.shape >= 0 && idx->tuning.shape < N_SHAPES) ? idx->tuning.shape : DEFAULT_SHAPE;
+    int bps = 0;
+    if (int rc = persistent_grid(idx->device, shape, bps)) return rc;
+    uint64_t warps = (uint64_t)g_num_sms * bps * g_shapes[shape].warps;
+    uint64_t iv_cap = std::min<uint64_t>(4 * n + 65536, 1ull << 30);
+    uint64_t ring = ring_capacity(n);
+    *bytes = sizeof(SearchCtl) + 64 + 4 * std::max<uint64_t>(n, 1) + iv_cap * sizeof(Interval) +
+             16 * std::max<uint64_t>(n, 1) + ring * (sizeof(WorkItem) + 4) + warps * DEEP_CAP * 24;
+    return 0;
+}
 
 int search_shape_info(int shape, int *scap, int *warps, int *minb)
 {
@@ -1580,6 +1602,69 @@ int run_search(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsV
         return 0;
     }
     return MICA_EINTERNAL;
+}
+
+// The persistent search of the reads d_list[0, n_list) of a batch (both
+// strands of each), appending to the interval buffer after iv_base leaves
+// already there (their per-read counts must be 0 for the listed reads).  Used
+// for the reads the bidirectional search gave up on.  Returns
+// BIDIR_FALLBACK when a buffer overflows (the caller then searches the whole
+// batch with the persistent kernel).
+int run_search_list(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd, const uint32_t *d_list,
+                    uint32_t n_list, uint32_t iv_base, bool prune, cudaStream_t s)
+{
+    int rc;
+    if (w.spill_cap == 0) w.spill_cap = ring_capacity(rd.n);
+    if ((rc = dev_reserve(w.spill, (size_t)w.spill_cap * sizeof(WorkItem))) ||
+        (rc = dev_reserve(w.spill_seq, (size_t)w.spill_cap * 4)))
+        return rc;
+    if (prune && (rc = dev_reserve(w.lb, std::max<uint64_t>(2 * rd.n, 1) * 8))) return rc;
+    const int shape = (idx->tuning.shape >= 0 && idx->tuning.shape < N_SHAPES) ? idx->tuning.shape : DEFAULT_SHAPE;
+    int bps = 0;
+    if ((rc = persistent_grid(idx->device, shape, bps))) return rc;
+    const PersistShape &sh = g_shapes[shape];
+    const int grid = g_num_sms * bps;
+    if ((rc = reserve_deep(w, grid * sh.warps))) return rc;
+    SearchCtl *d_ctl = (SearchCtl *)w.ctl.p;
+    SearchCtl h{};
+    h.ntasks = 2ull * n_list;
+    h.spill_cap = w.spill_cap;
+    h.iv_cap = w.iv_cap;
+    h.iv_count = iv_base;
+    MICA_CUDA_TRY(cudaMemcpyAsync(d_ctl, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+    if (prune) {
+        unsigned g = (unsigned)std::min<uint64_t>((2ull * n_list + 255) / 256, 152ull * 64);
+        k_lower_bounds<<<g, 256, 0, s>>>(idx->view, rd, (unsigned long long *)w.lb.p, d_ctl, d_list, n_list);
+        st.launches++;
+    }
+    if ((rc = launch_ring_init(w, s))) return rc;
+    st.launches++;
+    PersistArgs pa;
+    pa.ix = idx->view; pa.rd = rd; pa.read_list = d_list; pa.ntasks = 2ull * n_list;
+    pa.ctl = d_ctl; pa.iv = (Interval *)w.iv.p; pa.iv_cnt = (uint32_t *)w.iv_cnt.p;
+    pa.spill = (WorkItem *)w.spill.p;
+    pa.seq = (uint32_t *)w.spill_seq.p;
+    pa.total_warps = grid * sh.warps;
+    deep_ptrs(w, pa.total_warps, pa.deep_m, pa.deep_s);
+    pa.prefetch = idx->n_occ_blocks * 32 > (96ull << 20);
+    pa.admit_min_free = admit_min_free_for(idx);
+    pa.lb = prune ? (const unsigned long long *)w.lb.p : nullptr;
+    set_wait_limits(idx, pa);
+    sh.fn<<<grid, sh.warps * 32, sh.smem, s>>>(pa);
+    MICA_CUDA_TRY(cudaGetLastError());
+    st.launches++;
+    SearchCtl out;
+    MICA_CUDA_TRY(cudaMemcpyAsync(&out, d_ctl, sizeof(out), cudaMemcpyDeviceToHost, s));
+    MICA_CUDA_TRY(cudaStreamSynchronize(s));
+    if (out.error & ERR_TIMEOUT) return MICA_ETIMEOUT;
+    if (out.error) return BIDIR_FALLBACK;
+    st.seeds += out.seeds;
+    st.nodes += out.nodes;
+    st.rank_blocks += out.rank_blocks;
+    st.intervals = out.iv_count;
+    st.spills += out.spills;
+    st.lb_steps += out.lb_steps;
+    return 0;
 }
 
 // Best-stratum search by iterative deepening (persistent kernel): pass j =

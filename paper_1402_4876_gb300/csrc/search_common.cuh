@@ -124,6 +124,74 @@ __device__ __forceinline__ int occ_pair(const IndexView &ix, uint32_t l, uint32_
     return 2;
 }
 
+// One of the two indices of a bidirectional search (the genome's, or the
+// reversed genome's): its occurrence blocks, superblocks, $ row and C[].
+struct OccSide {
+    const uint4 *occ;
+    const uint4 *super;
+    uint32_t dollar_row;
+    uint32_t C[5];
+};
+
+__device__ __forceinline__ void load_block(const OccSide &ix, uint32_t b, uint32_t need, OccBlock &k)
+{
+    const uint4 *p = ix.occ + (size_t)b * 2;
+    uint4 q0 = ld_nc(p);
+    uint4 q1 = make_uint4(0, 0, 0, 0);
+    if (need > 32) q1 = ld_nc(p + 1);
+    k.ac = q0.x; k.gt = q0.y;
+    k.lo[0] = q0.z; k.hi[0] = q0.w;
+    k.lo[1] = q1.x; k.hi[1] = q1.y;
+    k.lo[2] = q1.z; k.hi[2] = q1.w;
+}
+
+// Occ(A..T, b * 96 + o) on one side ($ excluded from A).
+__device__ __forceinline__ void occ_from(const OccSide &ix, uint32_t b, uint32_t o, const uint4 &sup,
+                                         const OccBlock &k, uint32_t (&occ)[4])
+{
+    uint32_t sl = 0, sh = 0, st = 0;
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        uint32_t rem = min(max((int)o - 32 * j, 0), 32);
+        uint32_t m = low_mask(rem);
+        uint32_t L = k.lo[j] & m, H = k.hi[j] & m;
+        st += __popc(L & H);
+        sl += __popc(L);
+        sh += __popc(H);
+    }
+    uint32_t nt = st, nc = sl - st, ng = sh - st;
+    uint32_t na = o - nc - ng - nt;
+    uint32_t start = b * OCC_ROWS;
+    if (ix.dollar_row >= start && ix.dollar_row < start + o) na -= 1;
+    occ[0] = sup.x + (k.ac & 0xffffu) + na;
+    occ[1] = sup.y + (k.ac >> 16) + nc;
+    occ[2] = sup.z + (k.gt & 0xffffu) + ng;
+    occ[3] = sup.w + (k.gt >> 16) + nt;
+}
+
+// Occ(c, l) and Occ(c, r) for all c on one side; returns the blocks read.
+__device__ __forceinline__ int occ_pair(const OccSide &ix, uint32_t l, uint32_t r, uint32_t (&ol)[4],
+                                        uint32_t (&orr)[4])
+{
+    uint32_t bl = l / OCC_ROWS, xl = l - bl * OCC_ROWS;
+    uint32_t br = r / OCC_ROWS, xr = r - br * OCC_ROWS;
+    uint4 sl = ld_nc(ix.super + bl / SB_BLOCKS);
+    OccBlock a;
+    if (bl == br) {
+        load_block(ix, bl, xr, a);
+        occ_from(ix, bl, xl, sl, a, ol);
+        occ_from(ix, br, xr, sl, a, orr);
+        return 1;
+    }
+    uint4 sr = ld_nc(ix.super + br / SB_BLOCKS);
+    OccBlock c;
+    load_block(ix, bl, xl, a);
+    load_block(ix, br, xr, c);
+    occ_from(ix, bl, xl, sl, a, ol);
+    occ_from(ix, br, xr, sr, c, orr);
+    return 2;
+}
+
 // Base t of a packed pattern.
 __device__ __forceinline__ uint32_t pat_base(const uint32_t *pat, uint32_t t)
 {
@@ -153,6 +221,25 @@ __device__ __forceinline__ uint32_t window_code(const uint32_t *pat, uint32_t m,
     uint32_t code = 0;
     for (uint32_t t = m - qe; t < m; t++) code = (code << 2) | pat_base(pat, t);
     return code;
+}
+
+// SA interval of a (qe)-mer code x from a q-mer table (the genome's or the
+// reversed genome's) with its short-suffix corrections.
+__device__ __forceinline__ void seed_interval_in(const uint32_t *table, uint32_t q, uint32_t nshort,
+                                                 const uint32_t *short_pad, const uint32_t *short_len,
+                                                 unsigned long long bloom, uint32_t code, uint32_t qe,
+                                                 uint32_t &l, uint32_t &r)
+{
+    uint32_t sh = 2 * (q - qe);
+    uint32_t start = code << sh, end = (code + 1) << sh;
+    l = __ldg(table + (size_t)start);
+    r = __ldg(table + (size_t)end);
+    if (((bloom >> (start & 63)) | (bloom >> (end & 63))) & 1ull) {
+        for (uint32_t t = 0; t < nshort; t++) {
+            l -= (short_pad[t] == start && short_len[t] >= qe);
+            r -= (short_pad[t] == end);
+        }
+    }
 }
 
 // SA interval of a (qe)-mer code x from the q-mer table, whose entry at a

@@ -138,7 +138,7 @@ def test_c_program_uses_the_host_calls(lib, tmp_path):
 
 
 class _IndexHeader(ctypes.Structure):
-    """The index file's leading header as the library writes it (version 3):
+    """The index file's leading header as the library writes it (version 4):
     magic, version, q, sampling, the text's sizes and the short-suffix codes."""
     _fields_ = [("magic", ctypes.c_char * 8), ("version", ctypes.c_uint32), ("kmer_q", ctypes.c_uint32),
                 ("sa_sample", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("n", ctypes.c_uint64),
@@ -150,7 +150,7 @@ class _IndexHeader(ctypes.Structure):
 
 def _consistent_header(n=1000, q=8, s=16):
     h = _IndexHeader()
-    h.magic, h.version, h.kmer_q, h.sa_sample, h.n = b"MICAIDX1", 3, q, s, n
+    h.magic, h.version, h.kmer_q, h.sa_sample, h.n = b"MICAIDX1", 3, q, s, n   # a version-3 file: no table block
     h.n_occ_blocks = (n + 1) // 96 + 1
     h.n_super = (h.n_occ_blocks + 681) // 682
     h.n_mark_blocks = (n + 1) // 480 + 1
@@ -161,7 +161,7 @@ def _consistent_header(n=1000, q=8, s=16):
 
 
 @pytest.mark.parametrize("field,value", [
-    ("magic", b"MICAIDX9"), ("version", 4), ("kmer_q", 0), ("kmer_q", 13), ("sa_sample", 0),
+    ("magic", b"MICAIDX9"), ("version", 5), ("kmer_q", 0), ("kmer_q", 13), ("sa_sample", 0),
     ("n_occ_blocks", 5), ("n_super", 0), ("n_mark_blocks", 0), ("table_len", 17), ("n_samples", 2000),
     ("nshort", 3), ("n", 1 << 32),
 ])

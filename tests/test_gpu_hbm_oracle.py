@@ -1,0 +1,62 @@
+"""Oracle parity where the index lives in HBM (paper Section 2: reads placed
+on a human-scale genome whose BWT index sits in the accelerator's memory;
+Table 1's genome scale).
+
+A 512 Mbp genome drawn by the human-scale recipe (about 45% repeats: 300 bp
+families at 10-15% divergence, 6 kbp families at 5%, tandem arrays) has
+170 MiB of occurrence blocks and as much again for the reversed genome, so
+its index does not fit the 129 MB L2: every rank query of the search and of
+the lower-bound pass may go to HBM, and the persistent kernel takes its
+HBM admission policy (occurrence blocks above 96 MiB).  The oracle builds
+its own index of the same genome by SA-IS and searches by plain
+backtracking; 20,000 paired 150 bp mates (k <= 2, cap 1000) must give the
+same totals, offsets and hits, bit for bit, for every kernel."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import gpu_common as gc
+
+pytestmark = pytest.mark.gpu
+
+GENOME_BP = 512_000_000
+
+
+@pytest.fixture(scope="module")
+def hbm():
+    g = synth.human_genome(GENOME_BP)
+    donor = synth.donor_of(g)
+    b = synth.paired_reads(donor, 10_000)                       # 20,000 mates
+    idx = gc.mica().Index.build(synth.to_acgt_bytes(g.codes), kmer_q=12, sa_sample=16)
+    fm = oracle.FMIndex(g.codes, "sais")
+    want = fm.align(b, cap=1000)
+    yield g, b, idx, fm, want
+    idx.free()
+
+
+def test_index_does_not_fit_l2(hbm):
+    import torch
+    _, _, idx, _, _ = hbm
+    info = idx.info()
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+    assert info["occ_bytes"] > 96 << 20                         # the HBM admission policy applies
+    assert info["occ_bytes"] + info["rev_occ_bytes"] + info["table_bytes"] > 2 * l2
+
+
+@pytest.mark.parametrize("kernel", ["persistent", "plain", "bidirectional"])
+def test_hbm_20k_mates_equal_oracle(hbm, kernel):
+    _, b, idx, _, want = hbm
+    got = idx.align_batch(b, hit_cap=1000, kernel=kernel)
+    gc.assert_same(got, want, kernel)
+    assert int(want.offsets[-1]) > b.n // 2                     # most mates are placed
+    assert int(want.total.max()) > 1000                         # and the cap is exercised
+
+
+def test_hbm_unpruned_and_best_stratum_equal_oracle(hbm):
+    _, b, idx, fm, want = hbm
+    sub = b.subset(np.arange(0, 6_000))
+    got = idx.align_batch(sub, hit_cap=1000, kernel="persistent", prune=False)
+    gc.assert_same(got, fm.align(sub, cap=1000), "unpruned")
+    got = idx.align_batch(sub, hit_cap=1000, kernel="persistent", report="best_stratum")
+    gc.assert_same(got, fm.align_best_stratum(sub, cap=1000), "best stratum")

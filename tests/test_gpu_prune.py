@@ -79,6 +79,12 @@ def test_index_with_and_without_lower_bounds(tmp_path):
     with pytest.raises(m.MicaError) as e:
         plain.debug_lower_bounds(b)
     assert e.value.code == m.MICA_EINVAL
+    # the bidirectional search needs the reversed genome's index and q-mer table
+    assert lbi.info()["rev_table_bytes"] == lbi.info()["table_bytes"] and plain.info()["rev_table_bytes"] == 0
+    gc.assert_same(lbi.align_batch(b, hit_cap=1000, kernel="bidirectional"), want, "bidirectional")
+    with pytest.raises(m.MicaError) as e:
+        plain.align_batch(b, hit_cap=1000, kernel="bidirectional")
+    assert e.value.code == m.MICA_EINVAL
     # the index file keeps (or omits) the reversed genome's blocks
     for idx, name in ((plain, "plain.mica"), (lbi, "lb.mica")):
         path = str(tmp_path / name)
@@ -88,6 +94,7 @@ def test_index_with_and_without_lower_bounds(tmp_path):
         gc.assert_same(back.align_batch(b, hit_cap=1000), want, name)
         if idx is lbi:
             assert np.array_equal(back.debug_lower_bounds(b), lbi.debug_lower_bounds(b))
+            gc.assert_same(back.align_batch(b, hit_cap=1000, kernel="bidirectional"), want, "loaded, bidirectional")
         back.free()
     plain.free()
     lbi.free()

@@ -9,7 +9,7 @@ from tests import golden_cases, refcheck
 from tests import gpu_common as gc
 
 pytestmark = pytest.mark.gpu
-KERNELS = ["persistent", "plain", "plain_by_length"]
+KERNELS = ["persistent", "plain", "plain_by_length", "bidirectional"]
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -202,6 +202,65 @@ def test_uneven_64m_sample(kernel):
     gc.assert_same(got, want)
 
 
+def test_uneven_64m_100k_reads_equal_oracle():
+    """100,000 reads of the benchmark's uneven 1M-read batch (every tenth:
+    lengths 50-250, k 0..3, 30% from repeats) equal the oracle for the
+    persistent kernel and the per-length plain launches."""
+    g = gc.genome("64m")
+    b = synth.reads_uneven(g, n=1_000_000).subset(np.arange(0, 1_000_000, 10))
+    want = gc.oracle_index("64m").align(b, cap=1000)
+    idx = gc.gpu_index("64m")
+    for kernel in ("persistent", "plain_by_length", "bidirectional"):
+        gc.assert_same(idx.align_batch(b, hit_cap=1000, kernel=kernel), want, kernel)
+    assert int(want.total.max()) > 1000 and np.count_nonzero(b.k == 3) > 20_000
+
+
+def test_bidirectional_frontier_rounds_and_give_up():
+    """The bidirectional kernel's budget: a task over its node budget exports
+    its pending nodes, and further launches continue them as tasks of their
+    own; a read still exporting after the last round is given up, its leaves
+    dropped and the read searched again by the persistent kernel.  Budgets of
+    200 and 8 nodes take many reads through the rounds, a budget of 1 through
+    the give-up path (walks of 100+ steps need more than 64 rounds), on the
+    uneven 64 Mbp sample (k 0..3) and on diverged (AC)^n reads with thousands
+    of leaves; every result equals the oracle, on repeated calls (the
+    captured-graph path steps aside once a batch needed more)."""
+    g = gc.genome("64m")
+    b = synth.reads_uneven(g, n=200_000).subset(np.arange(0, 200_000, 100))   # 2,000 reads
+    want = gc.oracle_index("64m").align(b, cap=1000)
+    idx = gc.gpu_index("64m")
+    try:
+        for budget in (200, 8, 1):
+            idx.set_tuning(bidir_budget=budget)
+            for call in range(2):
+                got = idx.align_batch(b, hit_cap=1000, kernel="bidirectional")
+                gc.assert_same(got, want, f"budget {budget}, call {call}")
+                st = idx.stats()
+                assert st["spills"] > 0                                # nodes exported to later rounds
+                if budget == 1:
+                    assert st["fallback_reads"] > 0                    # and reads given up
+        idx.set_tuning()
+        gc.assert_same(idx.align_batch(b, hit_cap=1000, kernel="bidirectional"), want, "default budget")
+    finally:
+        idx.set_tuning()
+    rng = np.random.default_rng(7)
+    core = np.resize(np.array([0, 1], np.uint8), 40_000)
+    mut = rng.random(core.size) < 0.04
+    core[mut] = (core[mut] + rng.integers(1, 4, size=int(mut.sum()))) & 3
+    tg = np.concatenate([rng.integers(0, 4, 20_000).astype(np.uint8), core])
+    reads = [tg[20_000 + i * 1_999: 20_000 + i * 1_999 + 40].copy() for i in range(16)]
+    tb = gc.batch_from_reads(reads, [2] * 8 + [3] * 8)
+    tfm = oracle.FMIndex(tg)
+    tidx = gc.mica().Index.build(synth.to_acgt_bytes(tg), kmer_q=10, sa_sample=8)
+    for budget in (200, 1):
+        tidx.set_tuning(bidir_budget=budget)
+        for cap in (0, 1000):
+            got = tidx.align_batch(tb, hit_cap=cap, kernel="bidirectional")
+            gc.assert_same(got, tfm.align(tb, cap=cap), f"tandem budget {budget} cap={cap}")
+            assert tidx.stats()["spills"] > 0
+    tidx.free()
+
+
 def test_every_shape_and_block_gives_the_same_result():
     g = gc.genome("64m")
     full = synth.reads_uneven(g, n=200_000)
@@ -226,20 +285,19 @@ def test_every_shape_and_block_gives_the_same_result():
 
 def test_full_1m_reads_64m():
     """Full 1M x 150 bp batch on the 64 Mbp repeat genome in the launch shape
-    the benchmark times: both kernels agree exactly; 2,000 sampled reads equal
-    the oracle; every hit's mismatch count is recomputed from the genome."""
+    the benchmark times: every read's total, offsets and hits equal the
+    oracle's for both kernels; every hit's mismatch count is recomputed from
+    the genome on a sample."""
     g = gc.genome("64m")
     b = synth.reads_64m(g)
     idx = gc.gpu_index("64m")
+    want = gc.oracle_index("64m").align(b, cap=1000)
     a = idx.align_batch(b, hit_cap=1000, kernel="persistent")
+    gc.assert_same(a, want, "persistent vs oracle, 1M reads")
     p = idx.align_batch(b, hit_cap=1000, kernel="plain")
-    gc.assert_same(a, p, "persistent vs plain")
+    gc.assert_same(p, want, "plain vs oracle, 1M reads")
+    gc.assert_same(idx.align_batch(b, hit_cap=1000, kernel="bidirectional"), want, "bidirectional vs oracle, 1M reads")
     rng = np.random.default_rng(99)
-    sample = np.sort(rng.choice(b.n, 2000, replace=False))
-    want = gc.oracle_index("64m").align(b.subset(sample), cap=1000)
-    for j, i in enumerate(sample):
-        assert a.hits_of(int(i)) == want.as_tuples(j)
-        assert int(a.total[i]) == int(want.total[j])
     # invariants on every read
     cnt = np.diff(a.offsets.astype(np.int64))
     assert np.all(cnt == np.minimum(a.total.astype(np.int64), 1000))

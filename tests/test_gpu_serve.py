@@ -32,7 +32,8 @@ def test_alone_equals_mix_equals_oracle():
     reqs = _requests(24, 1)
     alone = [idx.align_batch(r, hit_cap=1000) for r in reqs]
     results = [None] * len(reqs)
-    with gc.mica().Server(idx, hit_cap=1000, workers=2, max_tick_reads=30000) as srv:
+    # chunks of 3,000 reads: the larger requests run over several ticks
+    with gc.mica().Server(idx, hit_cap=1000, workers=2, max_tick_reads=30000, chunk_reads=3000) as srv:
         ids = [None] * len(reqs)
         rng = np.random.default_rng(2)
 
@@ -51,7 +52,8 @@ def test_alone_equals_mix_equals_oracle():
             assert lat >= 0
         st = srv.stats()
         assert st["completed"] == len(reqs) and st["failed"] == 0
-        assert st["ticks"] < len(reqs)            # requests shared launches
+        n_chunks = sum(max(1, -(-r.n // 3000)) for r in reqs)
+        assert st["ticks"] < n_chunks             # chunks of several requests shared launches
     for j, r in enumerate(reqs):
         gc.assert_same(results[j], alone[j], f"request {j}")
     fm = gc.oracle_index("64m")
@@ -81,23 +83,30 @@ def test_paused_admission_cancel_and_timeout():
 
 
 def test_budget_refusal_and_serialised_admission():
+    """Admission charges each tick the workspace its reads need
+    (mica_server_workspace_bytes) against the worker's share of the budget:
+    with a share that holds a tick of 5,000 reads, larger requests run in
+    smaller chunks and still equal their alone results, and the workspace in
+    use never exceeds the budget; a share that cannot hold a one-read tick
+    refuses every request."""
     idx = gc.gpu_index("64m")
     m = gc.mica()
     reqs = _requests(6, 4)
-    big = max(reqs, key=lambda r: r.n)
-    # a budget that one request at a time fits, and the biggest never fits
-    small_budget = (1 << 20) + 160 * 5000 + 4 * 2 * 5000 * 16
-    with m.Server(idx, workers=2, max_device_bytes=small_budget) as srv:
-        if big.n > 5000:
-            with pytest.raises(m.MicaError) as e:
-                srv.submit_batch(big)
-            assert e.value.code == m.MICA_ENOMEM
-        ok = [r for r in reqs if r.n <= 5000]
-        ids = [srv.submit_batch(r) for r in ok]
-        for r, rid in zip(ok, ids):
+    assert max(r.n for r in reqs) > 5000
+    share = m.Server.workspace_bytes(idx, 5000, 5000 * 16)
+    assert share > m.Server.workspace_bytes(idx, 1000, 1000 * 16) > m.Server.workspace_bytes(idx, 1, 16)
+    with m.Server(idx, workers=2, max_device_bytes=2 * share) as srv:
+        ids = [srv.submit_batch(r) for r in reqs]
+        for r, rid in zip(reqs, ids):
             res, _ = srv.wait(rid)
             gc.assert_same(res, idx.align_batch(r, hit_cap=1000))
-            assert srv.stats()["device_bytes_in_use"] <= small_budget
+            assert 0 < srv.stats()["device_bytes_in_use"] <= 2 * share
+        assert srv.stats()["ticks"] >= sum(-(-r.n // 5000) for r in reqs) // 2
+    tiny = m.Server.workspace_bytes(idx, 1, 16) // 2
+    with m.Server(idx, workers=1, max_device_bytes=tiny) as srv:
+        with pytest.raises(m.MicaError) as e:
+            srv.submit_batch(reqs[0])
+        assert e.value.code == m.MICA_ENOMEM
 
 
 def test_invalid_request_and_stop_with_queue():
@@ -111,3 +120,8 @@ def test_invalid_request_and_stop_with_queue():
     for r in _requests(3, 5):
         srv.submit_batch(r)
     srv.stop()          # drops the queued requests, joins the workers
+    # a request with chunks already on the GPU is finished, not dropped, by stop
+    big = _requests(6, 4)
+    srv = m.Server(idx, workers=1, chunk_reads=1000)
+    rid = srv.submit_batch(max(big, key=lambda r: r.n))
+    srv.stop()
