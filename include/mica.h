@@ -81,10 +81,12 @@ enum {
     MICA_KERNEL_PLAIN = 1,           /* one launch of the one-task-per-thread kernel over the batch */
     MICA_KERNEL_PLAIN_BY_LENGTH = 2, /* one plain launch per read-length class (1-64, 65-128,
                                         129-192, 193-256 bases), each with its own block size */
-    MICA_KERNEL_BIDIRECTIONAL = 3    /* one launch of the warp-pool kernel searching both directions: the
+    MICA_KERNEL_BIDIRECTIONAL = 3    /* the default: the warp-pool kernel searching both directions (the
                                         read in k + 1 pieces, one search per leftmost exact piece, over the
-                                        genome's and the reversed genome's index (needs an index built with
-                                        lower_bounds = 1, format 4; MICA_EINVAL otherwise).  Same result */
+                                        genome's and the reversed genome's index), plus further launch
+                                        rounds for the nodes of heavy trees.  Same result.  An index built
+                                        without lower_bounds (or loaded from a file before format 4) runs
+                                        the persistent kernel instead */
 };
 
 typedef struct {
@@ -178,7 +180,7 @@ const char *mica_strerror(int code);
 
 /* Fill *p with the defaults (kmer_q 12, sa_sample 16, lower_bounds 1). */
 void mica_index_params_default(mica_index_params *p);
-/* Fill *p with the defaults (hit_cap 1000, persistent kernel, default stream, prune 1,
+/* Fill *p with the defaults (hit_cap 1000, bidirectional kernel, default stream, prune 1,
    report MICA_REPORT_ALL). */
 void mica_align_params_default(mica_align_params *p);
 
@@ -304,7 +306,7 @@ typedef struct {
                                    share); 0 = half the free memory at start */
     uint64_t max_tick_reads;    /* reads per search launch; 0 = 2^20 */
     uint32_t hit_cap;           /* as mica_align_params.hit_cap, for every request */
-    int32_t kernel;             /* MICA_KERNEL_* */
+    int32_t kernel;             /* MICA_KERNEL_* (default: bidirectional) */
     int32_t workers;            /* concurrent ticks, 1..8; 0 = 2 */
     int32_t start_paused;       /* nonzero: queue requests but admit none until mica_server_resume */
     uint64_t chunk_reads;       /* largest piece of a request in one tick; 0 = 2^18 (smaller when a

@@ -399,7 +399,7 @@ class Index:
                            _stream_handle(stream), int(bool(prune)),
                            REPORTS[report] if isinstance(report, str) else int(report))
 
-    def align(self, words, word_off, lengths, k, hit_cap: int = 1000, kernel="persistent",
+    def align(self, words, word_off, lengths, k, hit_cap: int = 1000, kernel="bidirectional",
               stream=None, prune: bool = True, report="all") -> Result:
         """mica_align_batch on host arrays (copies in, searches, copies out)."""
         words = np.ascontiguousarray(words, dtype=np.uint32)
@@ -419,7 +419,7 @@ class Index:
         return self.align(batch.words, batch.word_off, batch.lengths, batch.k, **kw)
 
     def align_device(self, d_words, d_word_off, d_lengths, d_k, n_reads: int, hit_cap: int = 1000,
-                     kernel="persistent", stream=None, prune: bool = True, report="all") -> DeviceResult:
+                     kernel="bidirectional", stream=None, prune: bool = True, report="all") -> DeviceResult:
         """mica_align_device on device pointers (ints) or torch CUDA tensors."""
         ptr = lambda x: x if isinstance(x, int) else x.data_ptr()
         p = self._params(hit_cap, kernel, stream, prune, report)
@@ -467,7 +467,7 @@ class Server:
     """Continuous-batching request loop over a resident index (mica_server_*)."""
 
     def __init__(self, index: Index, max_device_bytes: int = 0, max_tick_reads: int = 0, hit_cap: int = 1000,
-                 kernel="persistent", workers: int = 2, start_paused: bool = False, chunk_reads: int = 0):
+                 kernel="bidirectional", workers: int = 2, start_paused: bool = False, chunk_reads: int = 0):
         p = ServerParams()
         _lib.mica_server_params_default(ctypes.byref(p))
         p.max_device_bytes = max_device_bytes

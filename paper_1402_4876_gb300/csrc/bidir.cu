@@ -75,9 +75,22 @@ __device__ __forceinline__ uint32_t bm_j(uint32_t x) { return (x >> 27) & 7u; }
 
 // piece boundaries of a pattern of m bases in p pieces
 __device__ __forceinline__ uint32_t bnd(uint32_t i, uint32_t m, uint32_t p) { return i * m / p; }
-__device__ __forceinline__ uint32_t piece_of(uint32_t pos, uint32_t m, uint32_t p)
+
+// The boundaries bnd(0) .. bnd(4) of a task's pieces as 9-bit fields (fields
+// past p hold 511), computed once per task so that a node's scheme check
+// needs no division.
+__device__ __forceinline__ unsigned long long pack_bounds(uint32_t m, uint32_t p)
 {
-    return ((pos + 1) * p - 1) / m;
+    unsigned long long v = 0;
+#pragma unroll
+    for (uint32_t i = 0; i <= 4; i++) v |= (unsigned long long)(i <= p ? bnd(i, m, p) : 511u) << (9 * i);
+    return v;
+}
+__device__ __forceinline__ uint32_t bound_at(unsigned long long v, uint32_t i) { return (uint32_t)(v >> (9 * i)) & 511u; }
+// the piece holding position pos: the boundaries 1..3 at or below it
+__device__ __forceinline__ uint32_t piece_at(unsigned long long v, uint32_t pos)
+{
+    return (pos >= bound_at(v, 1)) + (pos >= bound_at(v, 2)) + (pos >= bound_at(v, 3));
 }
 
 struct BidirArgs {
@@ -110,6 +123,7 @@ struct BdSmem {
     uint32_t pat[32][MAX_WORDS + 1];                     // pattern of each task slot
     int live[32];                                        // nodes of each slot on the stacks
     uint32_t work[32];                                   // node expansions of each slot's task
+    unsigned long long bounds[32];                       // piece boundaries of each slot's pattern
     unsigned long long stage_off[32];                    // admission: word offset of each new slot's read,
     uint32_t stage_m[32];                                //   its length | minus << 15,
     uint8_t rank_lane[32];                               //   and the slot of the j-th new task
@@ -196,19 +210,19 @@ __device__ __forceinline__ void bd_complement_row(uint32_t *row, uint32_t m)
 // May a child that extends P[a, b) by base c at position pos (to the left
 // when a > 0, else to the right) exist under scheme j?  Returns the child's
 // d0 (mismatches before its current left piece) through d0n.
-__device__ __forceinline__ bool bd_allowed(uint32_t j, uint32_t a, uint32_t pos, uint32_t m, uint32_t p, uint32_t k,
-                                           uint32_t d, uint32_t d0, uint32_t cost, uint32_t &d0n)
+__device__ __forceinline__ bool bd_allowed(uint32_t j, uint32_t a, uint32_t pos, unsigned long long bounds,
+                                           uint32_t k, uint32_t d, uint32_t d0, uint32_t cost, uint32_t &d0n)
 {
     const uint32_t dn = d + cost;
     d0n = d0;
     if (dn > k) return false;
     if (j == SCHEME_FREE || a == 0) return true;              // free scheme, or the right phase
-    const uint32_t i = piece_of(pos, m, p);
+    const uint32_t i = piece_at(bounds, pos);
     if (i == j) return cost == 0;                             // the exact piece
     // a piece left of j: it needs a substitution, and so do pieces 0 .. i - 1
-    d0n = (a == bnd(i + 1, m, p)) ? d : d0;                   // entering piece i
+    d0n = (a == bound_at(bounds, i + 1)) ? d : d0;            // entering piece i
     const uint32_t dp = dn - d0n;
-    if (pos == bnd(i, m, p)) return dp >= 1 && dn + i <= k;   // piece i complete
+    if (pos == bound_at(bounds, i)) return dp >= 1 && dn + i <= k;   // piece i complete
     return dn + i + (dp == 0 ? 1u : 0u) <= k;
 }
 
@@ -424,6 +438,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
     bool s_used = false;
     uint32_t mbot = 0, mtop = 0, sbot = 0, stop = 0, dmt = 0, dst = 0;
     bool tasks_left = true;
+    // once the launch's task counter is spent, a task keeps an eighth of its
+    // budget: a warp left holding heavy trees hands them to the next round,
+    // where every warp takes part, instead of working through them alone
+    uint32_t budget = a.budget;
     uint32_t c_seeds = 0, c_nodes = 0, c_blocks = 0, c_deep = 0, c_rounds = 0;
     __syncwarp();
 
@@ -443,13 +461,35 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
             bd_deep_pop<SCAP, true>(W, deep_s, dst, sbot, n, lane);
             sc += n;
         }
-        // ---- slots over their node budget (all schemes seeded) hand their
-        // nodes to the next round: one pass over both stacks
-        const bool over = s_used && s_next >= s_nsch && W.live[lane] > 0 &&
-                          W.work[lane] >= a.budget;
+        if ((iter & 15) == 0 && budget == a.budget) {
+            int spent = 0;
+            if (lane == 0) spent = *(volatile unsigned long long *)&ctl->task_head >= ntasks;
+            if (__shfl_sync(BFULL, spent, 0)) budget = max(a.budget >> 3, 32u);
+        }
+        // ---- slots over their node budget hand their nodes to the next
+        // round (one pass over both stacks), and their schemes not yet seeded
+        // as seed items (size 0, the scheme in the meta word)
+        const bool over = s_used && W.work[lane] >= budget && (W.live[lane] > 0 || s_next < s_nsch);
         const unsigned expm = __ballot_sync(BFULL, over);
         if (expm) {
             const uint32_t task = 2 * s_read + ((s_info >> 11) & 1u);
+            const uint32_t nseed = over ? s_nsch - s_next : 0u;
+            uint32_t pre = nseed;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(BFULL, pre, o);
+                if (lane >= o) pre += y;
+            }
+            const uint32_t tot = __shfl_sync(BFULL, pre, 31);
+            pre -= nseed;
+            if (tot) {
+                uint32_t base = 0;
+                if (lane == 0) base = atomicAdd(&ctl->fr_count, tot);
+                base = __shfl_sync(BFULL, base, 0);
+                for (uint32_t i = 0; i < nseed; i++)
+                    bd_export_one(a, base + pre + i, task, 0, 0, 0, bd_meta(0, 0, 0, 0, 0, s_next + i));
+            }
+            if (over) s_next = s_nsch;
             mtop = mbot + bd_export_stack<SCAP, false, false>(W, a, nullptr, mbot, mtop, expm, task, lane);
             stop = sbot + bd_export_stack<SCAP, true, false>(W, a, nullptr, sbot, stop, expm, task, lane);
             if (dmt) dmt = bd_export_stack<SCAP, false, true>(W, a, deep_m, 0, dmt, expm, task, lane);
@@ -484,19 +524,28 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
                 bool push = false;
                 if (mine) {
                     unsigned long long t = t0 + jr;
-                    if (a.mode == 1) t = a.fr_in[t].x;   // a node exported by the previous round: its task
+                    uint32_t seed_j = 8;                   // 8: not a seed item
+                    if (a.mode == 1) {                     // a node (or a scheme to seed) exported by the last round
+                        const uint4 it = a.fr_in[t];
+                        if (it.w == 0) seed_j = bm_j(a.fr_in_meta[t]);
+                        t = it.x;
+                    }
                     const uint32_t rid = (uint32_t)(t >> 1), minus = (uint32_t)(t & 1);
                     const uint32_t m = a.rd.len[rid], k = a.rd.k[rid];
                     const uint32_t p = m >= k + 1 ? k + 1 : 1u;
                     const uint32_t nsch = m >= k + 1 ? p : 1u;
                     s_read = rid;
-                    s_info = m | (k << 9) | (minus << 11) | (p << 12) | (nsch << 15);
-                    s_next = a.mode == 1 ? nsch : 0;
+                    const bool given_up = a.mode == 1 && ((a.redo[rid >> 5] >> (rid & 31)) & 1u);
+                    // a seed item seeds its one scheme: the slot's scheme range is [j, j + 1)
+                    const uint32_t send = seed_j < 8 ? seed_j + 1 : nsch;
+                    s_info = m | (k << 9) | (minus << 11) | (p << 12) | (send << 15);
+                    s_next = a.mode == 0 ? 0 : (seed_j < 8 && !given_up ? seed_j : send);
                     s_used = true;
                     // the node of a read already given up is not continued
-                    push = a.mode == 1 && !((a.redo[rid >> 5] >> (rid & 31)) & 1u);
+                    push = a.mode == 1 && seed_j == 8 && !given_up;
                     W.live[lane] = push ? 1 : 0;
                     W.work[lane] = 0;
+                    W.bounds[lane] = pack_bounds(m, p);
                     W.rank_lane[jr] = (uint8_t)lane;
                     W.stage_off[lane] = a.rd.word_off[rid];
                     W.stage_m[lane] = m | (minus << 15);
@@ -564,7 +613,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
                     meta = bd_meta((uint32_t)lane, m, m, 0, 0, SCHEME_FREE);
                     push = true;
                 } else {
-                    const uint32_t bj = bnd(j + 1, m, p), aj = bnd(j, m, p);
+                    const uint32_t bj = bound_at(W.bounds[lane], j + 1), aj = bound_at(W.bounds[lane], j);
                     const uint32_t qe = min(ix.q, bj - aj);
                     uint32_t code = 0, rcode = 0;
                     for (uint32_t t = 0; t < qe; t++) {
@@ -620,7 +669,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
             const bool live_node = has;
             if (has) atomicAdd(&W.work[slot], 1u);
             if (live_node) {
-                const uint32_t m = info & 511u, k = (info >> 9) & 3u, p = (info >> 12) & 7u;
+                const uint32_t m = info & 511u, k = (info >> 9) & 3u;
                 const uint32_t A = bm_a(meta), B = bm_b(meta), d = bm_d(meta), d0 = bm_d0(meta), j = bm_j(meta);
                 const bool left = A > 0;
                 const OccSide &sd = left ? a.fwd : a.rev;
@@ -636,7 +685,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
                     const uint32_t pos = left ? A - 1 : B;
                     const uint32_t cost = c != pat_base(W.pat[slot], pos) ? 1u : 0u;
                     uint32_t d0n;
-                    if (bd_allowed(j, A, pos, m, p, k, d, d0, cost, d0n)) {
+                    if (bd_allowed(j, A, pos, W.bounds[slot], k, d, d0, cost, d0n)) {
                         const uint32_t nr = side_C(sd, c) + occ_single_side(sd, bk, o, sup, blk, c);
                         if (left) nl = nr; else nlr = nr;
                         dn = d + cost;
@@ -675,7 +724,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
             const bool live_node = has;
             if (has) atomicAdd(&W.work[slot], 1u);
             if (live_node) {
-                const uint32_t m = info & 511u, k = (info >> 9) & 3u, p = (info >> 12) & 7u;
+                const uint32_t m = info & 511u, k = (info >> 9) & 3u;
                 const uint32_t A = bm_a(meta), B = bm_b(meta), d = bm_d(meta), d0 = bm_d0(meta), j = bm_j(meta);
                 const bool left = A > 0;
                 const OccSide &sd = left ? a.fwd : a.rev;
@@ -693,7 +742,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
                     const uint32_t n_c = orr[c] - ol[c];
                     const uint32_t cost = (uint32_t)c != base ? 1u : 0u;
                     uint32_t d0n;
-                    if (n_c > 0 && bd_allowed(j, A, pos, m, p, k, d, d0, cost, d0n)) {
+                    if (n_c > 0 && bd_allowed(j, A, pos, W.bounds[slot], k, d, d0, cost, d0n)) {
                         const uint32_t start = side_C(sd, c) + ol[c];
                         cl[c] = left ? start : acc;
                         clr[c] = left ? acc : start;

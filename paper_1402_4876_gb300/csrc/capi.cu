@@ -7,6 +7,7 @@
 #include <mutex>
 #include <vector>
 
+#include "host_parallel.h"
 #include "mica_internal.cuh"
 
 namespace mica {
@@ -369,8 +370,11 @@ static int align_graph(const mica_index *idx, Workspace &w, mica_stats &st, cons
 }
 
 int align_on_device(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd,
-                    const mica_align_params &p, cudaStream_t s, uint64_t *nh, bool allow_graph)
+                    const mica_align_params &p_in, cudaStream_t s, uint64_t *nh, bool allow_graph)
 {
+    // an index without the reversed genome's table runs the persistent kernel instead
+    mica_align_params p = p_in;
+    if (p.kernel == MICA_KERNEL_BIDIRECTIONAL && !bidir_available(idx)) p.kernel = MICA_KERNEL_PERSISTENT;
     for (auto &e : w.ev)
         if (!e) MICA_CUDA_TRY(cudaEventCreate(&e));
     for (auto &e : w.kev)
@@ -458,7 +462,7 @@ void mica_index_params_default(mica_index_params *p)
 void mica_align_params_default(mica_align_params *p)
 {
     p->hit_cap = 1000;
-    p->kernel = MICA_KERNEL_PERSISTENT;
+    p->kernel = MICA_KERNEL_BIDIRECTIONAL;
     p->cuda_stream = nullptr;
     p->prune = 1;
     p->report = MICA_REPORT_ALL;
@@ -761,14 +765,25 @@ int validate_device_batch(const mica_index *idx, Workspace &w, mica_stats &st, c
 int validate_host_batch(const mica_index *idx, const uint64_t *off, const uint16_t *len, const uint8_t *k,
                         uint64_t n)
 {
-    uint64_t total = off[n];
-    for (uint64_t i = 0; i < n; i++) {
-        uint32_t m = len[i];
-        if (m == 0 || m > MICA_MAX_READ_LEN || m > idx->n || k[i] > MICA_MAX_K || off[i] > total ||
-            total - off[i] < (m + 15) / 16)
-            return MICA_EINVAL;
-    }
-    return 0;
+    const uint64_t total = off[n];
+    auto bad_in = [&](uint64_t i0, uint64_t i1) {
+        for (uint64_t i = i0; i < i1; i++) {
+            uint32_t m = len[i];
+            if (m == 0 || m > MICA_MAX_READ_LEN || m > idx->n || k[i] > MICA_MAX_K || off[i] > total ||
+                total - off[i] < (m + 15) / 16)
+                return true;
+        }
+        return false;
+    };
+    // a batch of a million reads: chunks on the host threads
+    constexpr uint64_t CHUNK = 1u << 16;
+    if (n <= 2 * CHUNK) return bad_in(0, n) ? MICA_EINVAL : 0;
+    std::atomic<bool> bad{false};
+    parallel_chunks((n + CHUNK - 1) / CHUNK, host_threads(), [&](uint64_t c) {
+        if (!bad.load(std::memory_order_relaxed) && bad_in(c * CHUNK, std::min(n, (c + 1) * CHUNK)))
+            bad.store(true, std::memory_order_relaxed);
+    });
+    return bad.load() ? MICA_EINVAL : 0;
 }
 
 }  // namespace mica
@@ -786,7 +801,6 @@ int mica_align_device(mica_index *idx, const uint32_t *d_packed_reads, const uin
     mica_align_params_default(&p);
     if (params) p = *params;
     if (p.kernel < MICA_KERNEL_PERSISTENT || p.kernel > MICA_KERNEL_BIDIRECTIONAL) return MICA_EINVAL;
-    if (p.kernel == MICA_KERNEL_BIDIRECTIONAL && !bidir_available(idx)) return MICA_EINVAL;
     if (p.report > MICA_REPORT_BEST_STRATUM) return MICA_EINVAL;
     DeviceGuard g(idx->device);
     MICA_CUDA_TRY(cudaSetDevice(idx->device));
@@ -816,7 +830,6 @@ int mica_align_batch(mica_index *idx, const uint32_t *packed_reads, const uint64
     mica_align_params_default(&p);
     if (params) p = *params;
     if (p.kernel < MICA_KERNEL_PERSISTENT || p.kernel > MICA_KERNEL_BIDIRECTIONAL) return MICA_EINVAL;
-    if (p.kernel == MICA_KERNEL_BIDIRECTIONAL && !bidir_available(idx)) return MICA_EINVAL;
     if (p.report > MICA_REPORT_BEST_STRATUM) return MICA_EINVAL;
     DeviceGuard g(idx->device);
     MICA_CUDA_TRY(cudaSetDevice(idx->device));

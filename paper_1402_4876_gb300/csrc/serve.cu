@@ -317,7 +317,7 @@ void mica_server_params_default(mica_server_params *p)
     p->max_device_bytes = 0;
     p->max_tick_reads = 1u << 20;
     p->hit_cap = 1000;
-    p->kernel = MICA_KERNEL_PERSISTENT;
+    p->kernel = MICA_KERNEL_BIDIRECTIONAL;
     p->workers = 2;
     p->start_paused = 0;
     p->chunk_reads = 1u << 18;
@@ -339,7 +339,6 @@ int mica_server_start(mica_index *idx, const mica_server_params *params, mica_se
     mica_server_params_default(&p);
     if (params) p = *params;
     if (p.kernel < MICA_KERNEL_PERSISTENT || p.kernel > MICA_KERNEL_BIDIRECTIONAL) return MICA_EINVAL;
-    if (p.kernel == MICA_KERNEL_BIDIRECTIONAL && !bidir_available(idx)) return MICA_EINVAL;
     if (p.workers <= 0) p.workers = 2;
     if (p.workers > 8) return MICA_EINVAL;
     if (p.max_tick_reads == 0) p.max_tick_reads = 1u << 20;

@@ -44,7 +44,7 @@ def test_strerror_and_defaults(lib):
     assert b"invalid" in lib.mica_strerror(-1)
     p = mica.AlignParams()
     lib.mica_align_params_default(ctypes.byref(p))
-    assert p.hit_cap == 1000 and p.kernel == 0
+    assert p.hit_cap == 1000 and p.kernel == mica.KERNELS["bidirectional"]
     q = mica.IndexParams()
     lib.mica_index_params_default(ctypes.byref(q))
     assert (q.kmer_q, q.sa_sample) == (12, 16)
@@ -203,8 +203,8 @@ def test_shape_table_and_defaults_need_no_gpu():
         == mica.MICA_EINVAL
     sp = mica.ServerParams()
     lib.mica_server_params_default(ctypes.byref(sp))
-    assert (sp.max_device_bytes, sp.max_tick_reads, sp.hit_cap, sp.kernel, sp.workers, sp.start_paused) == \
-        (0, 1 << 20, 1000, 0, 2, 0)
+    assert (sp.max_device_bytes, sp.max_tick_reads, sp.hit_cap, sp.kernel, sp.workers, sp.start_paused,
+            sp.chunk_reads) == (0, 1 << 20, 1000, mica.KERNELS["bidirectional"], 2, 0, 1 << 18)
     wp = mica.SamParams(b"x", 1, b"y", 7)
     lib.mica_sam_params_default(ctypes.byref(wp))
     assert (wp.qname_prefix, wp.secondary, wp.command_line, wp.threads) == (None, 0, None, 0)
