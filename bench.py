@@ -226,7 +226,7 @@ def profile_traffic(kernel_src: str, profile: str = PROFILE, key: str = "dram_by
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
         sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
-        if vals.get("search_cu_sha256_16") != sha:
+        if sha not in (vals.get("kernel_src_sha256_16"), vals.get("search_cu_sha256_16")):
             return None
         return float(vals[key])
     except Exception:

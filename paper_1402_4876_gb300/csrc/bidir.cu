@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
             bd_deep_pop<SCAP, true>(W, deep_s, dst, sbot, n, lane);
             sc += n;
         }
-        if ((iter & 15) == 0 && budget == a.budget) {
+        if ((iter & 63) == 63 && budget == a.budget) {
             int spent = 0;
             if (lane == 0) spent = *(volatile unsigned long long *)&ctl->task_head >= ntasks;
             if (__shfl_sync(BFULL, spent, 0)) budget = max(a.budget >> 3, 32u);
@@ -1080,8 +1080,11 @@ int run_search_bidir(const mica_index *idx, Workspace &w, mica_stats &st, const 
         MICA_CUDA_TRY(cudaStreamSynchronize(s));
         // frontier rounds while the last one exported nodes (and nothing failed)
         int r = 1;
-        for (; r <= BD_MAX_ROUNDS && out.fr_count && !out.error; r++) {
-            if (int rc = launch_round(idx, w, rd, grid, r, s, st.launches)) return rc;
+        // four rounds per host read of the control block (a round with
+        // nothing exported to it returns at once)
+        while (r <= BD_MAX_ROUNDS && out.fr_count && !out.error) {
+            for (int q = 0; q < 4 && r <= BD_MAX_ROUNDS; q++, r++)
+                if (int rc = launch_round(idx, w, rd, grid, r, s, st.launches)) return rc;
             MICA_CUDA_TRY(cudaMemcpyAsync(&out, w.ctl.p, sizeof(out), cudaMemcpyDeviceToHost, s));
             MICA_CUDA_TRY(cudaStreamSynchronize(s));
         }
