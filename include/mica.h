@@ -66,7 +66,7 @@ enum {
 
 typedef struct mica_index mica_index;
 
-/* Index layout parameters (defaults: 12, 16, 1). */
+/* Index layout parameters (defaults: 12, 16, 1, 1). */
 typedef struct {
     uint32_t kmer_q;     /* q-mer seed table length, 1..12: table of 4^q + 1 uint32 bounds */
     uint32_t sa_sample;  /* text sampling rate s, 1..256: SA[j] kept when SA[j] % s == 0 */
@@ -74,6 +74,11 @@ typedef struct {
                               table (one more suffix array at build time, about +1/3 device
                               memory) so searches can prune by mismatch lower bounds and extend
                               patterns in both directions; 0: not */
+    uint32_t full_sa;    /* 1: also keep the whole suffix array, its inverse and the genome at
+                            2 bits per base on the device (4 (N + 1) + 4 (N + 1) + N / 4 bytes):
+                            the bidirectional search then checks an interval of one row
+                            against the genome's text instead of extending it base by base, and
+                            locating a row is one read; 0: not.  Same results either way */
 } mica_index_params;
 
 enum {
@@ -157,6 +162,8 @@ typedef struct {
     uint64_t grid_ctas;      /* persistent kernel: CTAs of the launch (SMs x resident CTAs per SM) */
     uint64_t fallback_reads; /* bidirectional kernel: reads it gave up on (over the node budget, or on a
                                 warp whose overflow stack filled), searched again by the persistent kernel */
+    uint64_t verified;       /* bidirectional kernel: one-row intervals checked against the genome's text */
+    uint64_t verify_bytes;   /* bytes those checks read: suffix array and inverse entries, text words */
     float search_ms;         /* device time of the search phase (kernel + its control copies) */
     float kernel_ms;         /* device time of the search kernel launch(es) alone, with the
                                 lower-bound pass when pruning */
@@ -174,11 +181,13 @@ typedef struct {
     uint32_t lower_bounds;   /* 1 if the reversed genome's occurrence blocks are resident */
     uint64_t rev_occ_bytes;  /* their size (0 without them) */
     uint64_t rev_table_bytes; /* the reversed genome's q-mer table (bidirectional search; 0 without it) */
+    uint32_t full_sa;        /* 1 if the whole suffix array, its inverse and the 2-bit text are resident */
+    uint64_t full_sa_bytes;  /* their size (0 without them) */
 } mica_index_info;
 
 const char *mica_strerror(int code);
 
-/* Fill *p with the defaults (kmer_q 12, sa_sample 16, lower_bounds 1). */
+/* Fill *p with the defaults (kmer_q 12, sa_sample 16, lower_bounds 1, full_sa 1). */
 void mica_index_params_default(mica_index_params *p);
 /* Fill *p with the defaults (hit_cap 1000, bidirectional kernel, default stream, prune 1,
    report MICA_REPORT_ALL). */
@@ -197,9 +206,13 @@ int mica_index_build_resident(const uint8_t *genome_acgt, uint64_t len,
 int mica_index_build(const uint8_t *genome_acgt, uint64_t len,
                      const mica_index_params *params, const char *out_path);
 
-/* Index files (format version 4) hold the reversed genome's blocks and q-mer
-   table when the index has them; version 3 files (blocks, no table) and
-   version 2 files (neither) still load. */
+/* Index files (format version 5) hold the reversed genome's blocks and q-mer
+   table when the index has them.  The whole suffix array, its inverse and the
+   text are not stored: a file records whether the index kept them, and
+   loading rebuilds them on the device from the sampled suffix array by LF
+   steps (N steps in all, s - 1 at most from each sample).  Version 4 files
+   (no such record), version 3 files (blocks, no table) and version 2 files
+   (neither) still load. */
 int mica_index_save(const mica_index *idx, const char *path);
 /* Read an index file and upload it to `device`, where it stays until freed. */
 int mica_index_load(const char *path, int device, mica_index **out);
@@ -211,7 +224,12 @@ int mica_index_get_info(const mica_index *idx, mica_index_info *info);
  * uint32 word, least-significant bits first; read i (length lengths[i], budget
  * k[i]) starts at word word_offsets[i] (n_reads + 1 offsets, non-decreasing).
  * Copies the batch to the device, runs the search, copies the result back.
- * params may be NULL (defaults).  On success *out is a new mica_result.
+ * The host checks the batch (lengths 1..MICA_MAX_READ_LEN and at most the
+ * genome's length, k <= MICA_MAX_K, every read inside packed_reads) while the
+ * copies run; a batch that fails returns MICA_EINVAL with no search launched,
+ * after its copies have finished.  The input buffers are the caller's and are
+ * not used after the call returns.  params may be NULL (defaults).  On
+ * success *out is a new mica_result (pinned host memory from a pool).
  */
 int mica_align_batch(mica_index *idx, const uint32_t *packed_reads, const uint64_t *word_offsets,
                      const uint16_t *lengths, const uint8_t *k, uint64_t n_reads,
@@ -245,6 +263,10 @@ typedef struct {
                                its pending nodes to the next launch round, where they are tasks of
                                their own on every warp (bounds each round's tail; no effect on
                                results); 0 = 4096 */
+    uint32_t bidir_verify;  /* bidirectional kernel with full_sa: an interval of one row whose matched
+                               part is at least this many bases (and which has at least 8 bases
+                               left to match) is checked against the genome's text in one step
+                               instead of being extended base by base; 0 = 20, 256 or more = never */
 } mica_tuning;
 
 /* Number of compiled persistent kernel shapes; mica_tuning_shape_info
@@ -676,8 +698,16 @@ int mica_debug_suffix_array(const uint8_t *genome_acgt, uint64_t len, int device
 /* occ_out[4*i + c] = Occ(c, rows[i]) from the interleaved blocks (host in/out). */
 int mica_debug_occ(const mica_index *idx, const uint64_t *rows, uint64_t n, uint32_t *occ_out);
 
-/* pos_out[i] = SA[rows[i]] resolved by LF walks to the sampled rows (host in/out). */
+/* pos_out[i] = SA[rows[i]] resolved by LF walks to the sampled rows (host in/out),
+   whether or not the index keeps the whole suffix array. */
 int mica_debug_locate(const mica_index *idx, const uint64_t *rows, uint64_t n, uint32_t *pos_out);
+
+/* Copy entries [first, first + n) of one of the full_sa arrays to out (host):
+   which = 0: the suffix array SA[0, N]; 1: its inverse ISA[0, N] (ISA[SA[j]]
+   = j); 2: the genome as 2-bit codes, 16 per uint32 word, least-significant
+   bits first (word w holds G[16 w, 16 w + 16), zero past N).  MICA_EINVAL
+   for an index without them or a range past the array. */
+int mica_debug_full_sa(const mica_index *idx, uint32_t which, uint64_t first, uint64_t n, uint32_t *out);
 
 /* SA interval of each len-mer (len <= kmer_q) given by its code (first base
    most significant, codes[i] < 4^len), looked up in the q-mer table on the

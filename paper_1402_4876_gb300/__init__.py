@@ -43,7 +43,8 @@ class MicaError(RuntimeError):
 
 
 class IndexParams(ctypes.Structure):
-    _fields_ = [("kmer_q", ctypes.c_uint32), ("sa_sample", ctypes.c_uint32), ("lower_bounds", ctypes.c_uint32)]
+    _fields_ = [("kmer_q", ctypes.c_uint32), ("sa_sample", ctypes.c_uint32), ("lower_bounds", ctypes.c_uint32),
+                ("full_sa", ctypes.c_uint32)]
 
 
 class AlignParams(ctypes.Structure):
@@ -66,7 +67,8 @@ class Stats(ctypes.Structure):
                 ("tasks", "seeds", "nodes", "rank_blocks", "intervals", "located", "lf_steps",
                  "spills", "retries", "launches", "warp_rounds", "lane_ops", "rounds_multi", "rounds_single",
                  "rounds_seed", "graph_captures", "graph_replays", "graph_fallbacks", "lb_steps",
-                 "lb_dead_tasks", "queue_wait_ns", "idle_wait_ns", "overflow_moves", "grid_ctas", "fallback_reads")] + [("search_ms", ctypes.c_float), ("kernel_ms", ctypes.c_float),
+                 "lb_dead_tasks", "queue_wait_ns", "idle_wait_ns", "overflow_moves", "grid_ctas", "fallback_reads",
+                 "verified", "verify_bytes")] + [("search_ms", ctypes.c_float), ("kernel_ms", ctypes.c_float),
                                                       ("total_ms", ctypes.c_float)]
 
     def as_dict(self) -> dict:
@@ -76,7 +78,7 @@ class Stats(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("shape", ctypes.c_int32), ("plain_block", ctypes.c_uint32), ("plain_budget", ctypes.c_uint32),
                 ("plain_block_len", ctypes.c_uint32 * 4), ("prefetch", ctypes.c_int32),
-                ("bidir_budget", ctypes.c_uint32)]
+                ("bidir_budget", ctypes.c_uint32), ("bidir_verify", ctypes.c_uint32)]
 
 
 def tuning_shapes() -> list:
@@ -108,7 +110,8 @@ class IndexInfo(ctypes.Structure):
                 ("C", ctypes.c_uint64 * 5), ("occ_bytes", ctypes.c_uint64), ("mark_bytes", ctypes.c_uint64),
                 ("sample_bytes", ctypes.c_uint64), ("table_bytes", ctypes.c_uint64), ("device", ctypes.c_int32),
                 ("lower_bounds", ctypes.c_uint32), ("rev_occ_bytes", ctypes.c_uint64),
-                ("rev_table_bytes", ctypes.c_uint64)]
+                ("rev_table_bytes", ctypes.c_uint64), ("full_sa", ctypes.c_uint32),
+                ("full_sa_bytes", ctypes.c_uint64)]
 
 
 # exported symbol -> (restype, argtypes); the C ABI's full surface
@@ -131,6 +134,7 @@ SIGNATURES = {
     "mica_debug_suffix_array": (_i32, [P, _u64, _i32, P]),
     "mica_debug_occ": (_i32, [P, P, _u64, P]),
     "mica_debug_locate": (_i32, [P, P, _u64, P]),
+    "mica_debug_full_sa": (_i32, [P, ctypes.c_uint32, _u64, _u64, P]),
     "mica_debug_seed_interval": (_i32, [P, P, _u32, _u64, P]),
     "mica_tuning_shapes": (_i32, []),
     "mica_tuning_shape_info": (_i32, [_i32, P, P, P]),
@@ -310,7 +314,7 @@ class Index:
 
     @classmethod
     def build(cls, genome_acgt, kmer_q: int = 12, sa_sample: int = 16, device: int = 0,
-              lower_bounds: bool = True) -> "Index":
+              lower_bounds: bool = True, full_sa: bool = True) -> "Index":
         """Index of `genome_acgt` (ACGT bytes, a uint8 array of them, or a
         Reference, whose text is passed without a copy)."""
         if isinstance(genome_acgt, Reference):
@@ -318,7 +322,7 @@ class Index:
         else:
             g = _acgt(genome_acgt)
             ptr, n = (_ptr(g) if g.size else None), g.size
-        p = IndexParams(kmer_q, sa_sample, int(bool(lower_bounds)))
+        p = IndexParams(kmer_q, sa_sample, int(bool(lower_bounds)), int(bool(full_sa)))
         h = ctypes.c_void_p()
         _check(_lib.mica_index_build_resident(ptr, n, ctypes.byref(p), device, ctypes.byref(h)),
                "mica_index_build_resident")
@@ -352,8 +356,9 @@ class Index:
         return d
 
     def set_tuning(self, shape: int = -1, plain_block: int = 0, plain_budget: int = 0, plain_block_len=(0, 0, 0, 0),
-                   prefetch: int = -1, bidir_budget: int = 0):
-        t = Tuning(shape, plain_block, plain_budget, (ctypes.c_uint32 * 4)(*plain_block_len), prefetch, bidir_budget)
+                   prefetch: int = -1, bidir_budget: int = 0, bidir_verify: int = 0):
+        t = Tuning(shape, plain_block, plain_budget, (ctypes.c_uint32 * 4)(*plain_block_len), prefetch, bidir_budget,
+                   bidir_verify)
         _check(_lib.mica_set_tuning(self._h, ctypes.byref(t)), "mica_set_tuning")
 
     def autotune(self, batch, hit_cap: int = 1000, repeats: int = 2, cache: str | None = None) -> dict:
@@ -386,7 +391,8 @@ class Index:
         t = Tuning()
         _check(_lib.mica_get_tuning(self._h, ctypes.byref(t)), "mica_get_tuning")
         return {"shape": t.shape, "plain_block": t.plain_block, "plain_budget": t.plain_budget,
-                "plain_block_len": list(t.plain_block_len), "prefetch": t.prefetch, "bidir_budget": t.bidir_budget}
+                "plain_block_len": list(t.plain_block_len), "prefetch": t.prefetch, "bidir_budget": t.bidir_budget,
+                "bidir_verify": t.bidir_verify}
 
     def stats(self) -> dict:
         s = Stats()
@@ -407,6 +413,11 @@ class Index:
         lengths = np.ascontiguousarray(lengths, dtype=np.uint16)
         k = np.ascontiguousarray(k, dtype=np.uint8)
         n = lengths.size
+        # the library reads word_off[n] words, n + 1 offsets and n budgets from these buffers
+        if word_off.size != n + 1 or k.size != n or int(word_off[-1]) > words.size:
+            raise MicaError(MICA_EINVAL, f"mica_align_batch: {n} lengths need {n + 1} word offsets (got "
+                                         f"{word_off.size}), {n} budgets (got {k.size}) and the words the "
+                                         f"last offset names (got {words.size})")
         p = self._params(hit_cap, kernel, stream, prune, report)
         out = ctypes.POINTER(_Result)()
         _check(_lib.mica_align_batch(self._h, _ptr(words) if words.size else None, _ptr(word_off),
@@ -440,6 +451,18 @@ class Index:
         rows = np.ascontiguousarray(rows, dtype=np.uint64)
         out = np.empty(rows.size, dtype=np.uint32)
         _check(_lib.mica_debug_locate(self._h, _ptr(rows), rows.size, _ptr(out)), "mica_debug_locate")
+        return out
+
+    def debug_full_sa(self, which: str, first: int = 0, n: int | None = None) -> np.ndarray:
+        """Entries of the resident whole suffix array ("sa"), its inverse ("isa")
+        or the 2-bit text words ("text") (mica_debug_full_sa)."""
+        w = {"sa": 0, "isa": 1, "text": 2}[which]
+        info = self.info()
+        length = info["rows"] if w < 2 else (info["full_sa_bytes"] - 8 * info["rows"]) // 4
+        if n is None:
+            n = length - first
+        out = np.empty(n, dtype=np.uint32)
+        _check(_lib.mica_debug_full_sa(self._h, w, first, n, _ptr(out) if n else None), "mica_debug_full_sa")
         return out
 
     def debug_lower_bounds(self, batch) -> np.ndarray:

@@ -18,7 +18,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmica_gb300.so")
-SOURCES = ["capi.cu", "index_build.cu", "search.cu", "bidir.cu", "post.cu", "serve.cu", "tune.cu", "noalloc.cu",
+SOURCES = ["capi.cu", "index_build.cu", "full_sa.cu", "search.cu", "bidir.cu", "post.cu", "serve.cu", "tune.cu",
+           "noalloc.cu",
            "ceiling.cu", "pair.cu", "reference.cpp", "sam.cpp", "fastq.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -59,6 +59,9 @@ constexpr uint32_t BD_ADMIT_LOW = 64;       // admit new tasks while fewer items
 constexpr uint32_t BD_DEEP_MIN = 8192;      // entries of each per-warp overflow stack, at least
 constexpr uint32_t SCHEME_FREE = 7;         // the single scheme of reads shorter than k + 1
 constexpr uint32_t BD_BUDGET = 1u << 12;    // node expansions a task may take before it exports its nodes
+constexpr uint32_t BD_VERIFY_MIN = 20;      // matched bases of a one-row node before it is checked against the text
+constexpr uint32_t BD_VERIFY_LEFT = 8;      // ... when at least this many bases are left to match
+constexpr int VCAP = 64;                    // one-row nodes waiting for that check (at most 63: see the round choice)
 
 // node meta: slot (5 bits) | a (9) | b (9) | d (2) | d0 (2) | scheme (3)
 __device__ __forceinline__ uint32_t bd_meta(uint32_t slot, uint32_t a, uint32_t b, uint32_t d, uint32_t d0,
@@ -114,12 +117,16 @@ struct BidirArgs {
     uint4 *fr_out;
     uint32_t *fr_out_meta;
     uint32_t fr_cap;
+    // one-row nodes with at least verify_min matched bases are checked
+    // against the text (needs the whole suffix array); 0 = never
+    uint32_t verify_min;
 };
 
 template <int SCAP>
 struct BdSmem {
     uint32_t ml[SCAP], mlr[SCAP], msz[SCAP], mm[SCAP];   // multi-row nodes
     uint32_t sl[SCAP], slr[SCAP], sm[SCAP];              // single-row nodes
+    uint32_t vl[VCAP], vlr[VCAP], vm[VCAP];              // single-row nodes to check against the text
     uint32_t pat[32][MAX_WORDS + 1];                     // pattern of each task slot
     int live[32];                                        // nodes of each slot on the stacks
     uint32_t work[32];                                   // node expansions of each slot's task
@@ -224,6 +231,57 @@ __device__ __forceinline__ bool bd_allowed(uint32_t j, uint32_t a, uint32_t pos,
     const uint32_t dp = dn - d0n;
     if (pos == bound_at(bounds, i)) return dp >= 1 && dn + i <= k;   // piece i complete
     return dn + i + (dp == 0 ? 1u : 0u) <= k;
+}
+
+// The text check of a one-row node: its pattern `pat` (m bases in p pieces
+// with boundaries `bnds`, scheme j, budget k) has P[A, B) matched at text
+// position t = SA[l].  Below a one-row node the tree is a single path, the
+// text around that occurrence (each row has one preceding and, in the
+// reversed genome's index, one following symbol), so the node has a leaf iff
+// the window G[t - A, t - A + m) lies inside G and meets the scheme: at most
+// k mismatches in all, none in piece j, at least one in each piece left of j
+// (the free scheme of short reads: the budget alone).  The window's mismatch
+// count goes to d, the text words read to words.
+__device__ __forceinline__ bool bd_check_window(const uint32_t *__restrict__ text, uint64_t n, const uint32_t *pat,
+                                                uint32_t m, unsigned long long bnds, uint32_t j, uint32_t k,
+                                                uint32_t t, uint32_t A, uint32_t &d, uint32_t &words)
+{
+    words = 0;
+    d = 0;
+    if (t < A || (uint64_t)(t - A) + m > n) return false;
+    const uint32_t s0 = t - A, w0 = s0 >> 4, sh = 2u * (s0 & 15u);
+    const uint32_t Wn = (m + 15) >> 4;
+    const int b1 = (int)bound_at(bnds, 1), b2 = (int)bound_at(bnds, 2), b3 = (int)bound_at(bnds, 3);
+    uint32_t tot = 0, c1 = 0, c2 = 0, c3 = 0;   // mismatches in all and before boundaries 1, 2, 3
+    uint32_t prev = __ldg(text + w0);
+    for (uint32_t q0 = 0; q0 < Wn; q0 += 8) {
+        uint32_t tw[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) tw[i] = (q0 + i < Wn) ? __ldg(text + w0 + q0 + i + 1) : 0u;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const uint32_t q = q0 + (uint32_t)i;
+            if (q < Wn) {
+                const uint32_t g = __funnelshift_r(prev, tw[i], sh);   // G[s0 + 16 q, s0 + 16 q + 16)
+                prev = tw[i];
+                uint32_t x = pat[q] ^ g;
+                x = (x | (x >> 1)) & 0x55555555u;                     // bit 2i: base 16 q + i differs
+                const int base = 16 * (int)q;
+                x &= low_mask(2u * (uint32_t)min(max((int)m - base, 0), 16));
+                tot += __popc(x);
+                c1 += __popc(x & low_mask(2u * (uint32_t)min(max(b1 - base, 0), 16)));
+                c2 += __popc(x & low_mask(2u * (uint32_t)min(max(b2 - base, 0), 16)));
+                c3 += __popc(x & low_mask(2u * (uint32_t)min(max(b3 - base, 0), 16)));
+            }
+        }
+    }
+    words = Wn + 1;
+    d = tot;
+    if (tot > k) return false;
+    if (j == SCHEME_FREE) return true;
+    const uint32_t pc0 = c1, pc1 = c2 - c1, pc2 = c3 - c2, pc3 = tot - c3;
+    const uint32_t pj = j == 0 ? pc0 : j == 1 ? pc1 : j == 2 ? pc2 : pc3;
+    return pj == 0 && (j < 1 || pc0 > 0) && (j < 2 || pc1 > 0) && (j < 3 || pc2 > 0);
 }
 
 // Move the n oldest nodes of a stack to the warp's overflow stack (n fits).
@@ -335,6 +393,41 @@ __device__ __forceinline__ uint32_t bd_export_stack(BdSmem<SCAP> &W, const Bidir
     return kept;
 }
 
+// The same for the stack of nodes waiting for the text check ([0, vtop),
+// no overflow part): they leave as single-row nodes.
+template <int SCAP>
+__device__ __forceinline__ uint32_t bd_export_verify(BdSmem<SCAP> &W, const BidirArgs &a, uint32_t vtop,
+                                                     unsigned expm, uint32_t task_of_lane, int lane)
+{
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t kept = 0;
+    for (uint32_t r0 = 0; r0 < vtop; r0 += 32) {
+        const uint32_t e = r0 + (uint32_t)lane;
+        const bool has = e < vtop;
+        uint32_t l = 0, lr = 0, meta = 0;
+        if (has) { l = W.vl[e]; lr = W.vlr[e]; meta = W.vm[e]; }
+        const uint32_t slot = bm_slot(meta);
+        const uint32_t task = __shfl_sync(BFULL, task_of_lane, slot);
+        const bool ex = has && ((expm >> slot) & 1u);
+        const bool keep = has && !ex;
+        const unsigned em = __ballot_sync(BFULL, ex), km = __ballot_sync(BFULL, keep);
+        uint32_t base = 0;
+        if (em) {
+            if (lane == 0) base = atomicAdd(&a.ctl->fr_count, (unsigned)__popc(em));
+            base = __shfl_sync(BFULL, base, 0);
+        }
+        __syncwarp();   // every lane has read its entry before any is overwritten below
+        if (ex) bd_export_one(a, base + __popc(em & lt), task, l, lr, 1u, meta);
+        if (keep) {
+            const uint32_t o = kept + __popc(km & lt);
+            W.vl[o] = l; W.vlr[o] = lr; W.vm[o] = meta;
+        }
+        kept += __popc(km);
+        __syncwarp();
+    }
+    return kept;
+}
+
 // Room for `add` more nodes on a stack: its oldest nodes go to the warp's
 // overflow stack, or, when that is full, to the frontier buffer as tasks of
 // the next round (task_of_lane: 2 read + strand of the lane's slot).
@@ -437,12 +530,13 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
     uint32_t s_read = 0, s_info = 0, s_next = 0;
     bool s_used = false;
     uint32_t mbot = 0, mtop = 0, sbot = 0, stop = 0, dmt = 0, dst = 0;
+    uint32_t vtop = 0;   // nodes waiting for the text check: W.v*[0, vtop)
     bool tasks_left = true;
     // once the launch's task counter is spent, a task keeps an eighth of its
     // budget: a warp left holding heavy trees hands them to the next round,
     // where every warp takes part, instead of working through them alone
     uint32_t budget = a.budget;
-    uint32_t c_seeds = 0, c_nodes = 0, c_blocks = 0, c_deep = 0, c_rounds = 0;
+    uint32_t c_seeds = 0, c_nodes = 0, c_blocks = 0, c_deep = 0, c_rounds = 0, c_verify = 0, c_vbytes = 0;
     __syncwarp();
 
     for (uint32_t iter = 0;; iter++) {
@@ -494,13 +588,14 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
             stop = sbot + bd_export_stack<SCAP, true, false>(W, a, nullptr, sbot, stop, expm, task, lane);
             if (dmt) dmt = bd_export_stack<SCAP, false, true>(W, a, deep_m, 0, dmt, expm, task, lane);
             if (dst) dst = bd_export_stack<SCAP, true, true>(W, a, deep_s, 0, dst, expm, task, lane);
+            if (vtop) vtop = bd_export_verify<SCAP>(W, a, vtop, expm, task, lane);
             if (over) W.live[lane] = 0;   // its nodes are gone: the slot frees below
             __syncwarp();
             continue;
         }
         const uint32_t avail = (s_used && s_next < s_nsch) ? 1u : 0u;
         const uint32_t seeds_total = __popc(__ballot_sync(BFULL, avail));
-        const uint32_t cnt = mc + sc;
+        const uint32_t cnt = mc + sc + vtop;
 
         // ---- admission of fresh tasks into free slots
         const unsigned freem = ~used;
@@ -590,13 +685,18 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
         }
         c_rounds++;
 
+        // (a single-row round moves at most 32 nodes to the text-check stack
+        // and runs only while it holds fewer than 32: it never holds 64)
         int kind;
         const bool seed_room = mc + 32 <= (uint32_t)SCAP && sc + 32 <= (uint32_t)SCAP;
-        if (mc >= 32) kind = 0;
+        if (vtop >= 32) kind = 3;
+        else if (mc >= 32) kind = 0;
         else if (sc >= 32) kind = 1;
         else if (seeds_total > 0 && seed_room && (seeds_total >= 16 || cnt == 0)) kind = 2;
-        else kind = mc >= sc ? (mc ? 0 : 1) : 1;
-        if (kind != 2 && cnt == 0) kind = 2;
+        else if (mc && mc >= sc && mc >= vtop) kind = 0;
+        else if (sc && sc >= vtop) kind = 1;
+        else if (vtop) kind = 3;
+        else kind = 2;
 
         if (kind == 2) {
             // ---- one scheme's seed per slot: piece j's last bases from both tables
@@ -666,8 +766,18 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
             const uint32_t rid = __shfl_sync(BFULL, s_read, slot);
             bool child = false, leaf = false;
             uint32_t nl = l, nlr = lr, nmeta = 0, dn = 0;
-            const bool live_node = has;
-            if (has) atomicAdd(&W.work[slot], 1u);
+            // a node far enough in (and far enough from the end) goes to the text check
+            const uint32_t matched = bm_b(meta) - bm_a(meta);
+            const bool to_v = has && a.verify_min && matched >= a.verify_min &&
+                              (info & 511u) - matched >= BD_VERIFY_LEFT;
+            const unsigned vmask = __ballot_sync(BFULL, to_v);
+            if (to_v) {
+                const uint32_t q = vtop + __popc(vmask & lt);
+                W.vl[q] = l; W.vlr[q] = lr; W.vm[q] = meta;
+            }
+            vtop += __popc(vmask);
+            const bool live_node = has && !to_v;
+            if (live_node) atomicAdd(&W.work[slot], 1u);
             if (live_node) {
                 const uint32_t m = info & 511u, k = (info >> 9) & 3u;
                 const uint32_t A = bm_a(meta), B = bm_b(meta), d = bm_d(meta), d0 = bm_d0(meta), j = bm_j(meta);
@@ -703,7 +813,38 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
                 W.sl[q] = nl; W.slr[q] = nlr; W.sm[q] = nmeta;
             }
             stop += __popc(bsm);
-            if (has && !child) atomicAdd(&W.live[slot], -1);
+            if (live_node && !child) atomicAdd(&W.live[slot], -1);
+        } else if (kind == 3) {
+            // ---- one-row nodes checked against the text: SA gives where the
+            // matched part lies, the text window decides the leaf, ISA its row
+            const uint32_t npop = min(vtop, 32u);
+            const bool has = (uint32_t)lane < npop;
+            uint32_t l = 0, meta = 0;
+            if (has) {
+                const uint32_t q = vtop - 1 - lane;
+                l = W.vl[q]; meta = W.vm[q];
+            }
+            vtop -= npop;
+            __syncwarp();
+            const uint32_t slot = bm_slot(meta);
+            const uint32_t info = __shfl_sync(BFULL, s_info, slot);
+            const uint32_t rid = __shfl_sync(BFULL, s_read, slot);
+            bool leaf = false;
+            uint32_t row = 0, dn = 0;
+            if (has) {
+                atomicAdd(&W.work[slot], 1u);
+                const uint32_t m = info & 511u, k = (info >> 9) & 3u;
+                const uint32_t t = __ldg(ix.sa_full + l);
+                uint32_t words = 0;
+                leaf = bd_check_window(ix.text, ix.n, W.pat[slot], m, W.bounds[slot], bm_j(meta), k, t, bm_a(meta),
+                                       dn, words);
+                if (leaf) row = __ldg(ix.isa + (t - bm_a(meta)));
+                c_verify++;
+                c_vbytes += 4u + 4u * words + (leaf ? 4u : 0u);
+            }
+            uint32_t cl[4] = {row, 0, 0, 0}, cs[4] = {1, 0, 0, 0}, cd[4] = {dn, 0, 0, 0};
+            bd_emit(a, leaf ? 1u : 0u, cl, cs, cd, leaf ? 1u : 0u, rid, (info >> 11) & 1u, lane);
+            if (has) atomicAdd(&W.live[slot], -1);
         } else {
             // ---- multi-row nodes: counts of all four symbols at both ends
             const uint32_t npop = min(mc, 32u);
@@ -806,6 +947,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
     if (lane == 0 && v) atomicAdd(&ctl->rank_blocks, v);
     v = (unsigned long long)c_seeds + c_nodes; for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(BFULL, v, o);
     if (lane == 0 && v) atomicAdd(&ctl->lane_ops, v);
+    v = c_verify; for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(BFULL, v, o);
+    if (lane == 0 && v) atomicAdd(&ctl->verified, v);
+    v = c_vbytes; for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(BFULL, v, o);
+    if (lane == 0 && v) atomicAdd(&ctl->verify_bytes, v);
     if (lane == 0) {
         atomicAdd(&ctl->rounds, (unsigned long long)c_rounds);
         if (c_deep) atomicAdd(&ctl->deep_moves, (unsigned long long)c_deep);
@@ -918,7 +1063,15 @@ static uint32_t bidir_deep_cap(Workspace &w, uint64_t warps)
 }
 
 static uint64_t redo_bits_bytes(uint64_t n) { return ((n + 31) / 32 * 4 + 15) & ~15ull; }
-static uint32_t frontier_cap(uint64_t n) { return (uint32_t)std::min<uint64_t>(std::max<uint64_t>(2 * n, 1u << 20), 1u << 28); }
+// Items per frontier buffer: 2n, at least 2^20, at most 2^28, and a multiple
+// of 4 so that the second buffer and both meta arrays (20 B per item in all)
+// start on a 16-byte boundary, as the kernel's 16-byte item loads and stores
+// require (an odd batch above 2^19 reads would otherwise put the second
+// buffer 8 bytes off).
+static uint32_t frontier_cap(uint64_t n)
+{
+    return (uint32_t)((std::min<uint64_t>(std::max<uint64_t>(2 * n, 1u << 20), 1u << 28) + 3) & ~3ull);
+}
 constexpr int BD_GRAPH_ROUNDS = 8;   // frontier rounds a captured batch runs (more: the regular path)
 constexpr int BD_MAX_ROUNDS = 64;
 static uint64_t redo_bytes(uint64_t n) { return redo_bits_bytes(n) + std::max<uint64_t>(n, 1) * 4 + 16; }
@@ -970,6 +1123,8 @@ static void bidir_args(const mica_index *idx, Workspace &w, const ReadsView &rd,
     ba.redo = (uint32_t *)w.redo.p;
     ba.budget = idx->tuning.bidir_budget ? idx->tuning.bidir_budget : BD_BUDGET;
     ba.fr_cap = frontier_cap(rd.n);
+    const uint32_t vmin = idx->tuning.bidir_verify ? idx->tuning.bidir_verify : BD_VERIFY_MIN;
+    ba.verify_min = (idx->view.sa_full && vmin < 256) ? vmin : 0u;
 }
 
 // Frontier buffer b (0 or 1): items, then meta words.
@@ -982,6 +1137,20 @@ static uint32_t *frontier_meta(Workspace &w, uint64_t n, int b)
     return (uint32_t *)(frontier_items(w, n, b) + frontier_cap(n));
 }
 
+// The kernel moves frontier items and overflow-stack entries as 16-byte
+// vectors: refuse a launch whose buffers are not on 16-byte boundaries.
+static int check_vector_alignment(const BidirArgs &ba)
+{
+    const void *ps[] = {ba.deep_m, ba.deep_s, ba.fr_in, ba.fr_out};
+    for (const void *p : ps)
+        if ((uintptr_t)p & 15) {
+            set_last_cuda_error(cudaErrorMisalignedAddress, "bidirectional search buffer alignment", __FILE__,
+                                __LINE__);
+            return MICA_ECUDA;
+        }
+    return 0;
+}
+
 // Launch frontier round r >= 1 (its tasks: the nodes round r - 1 exported).
 static int launch_round(const mica_index *idx, Workspace &w, const ReadsView &rd, int grid, int r, cudaStream_t s,
                         uint64_t &launches)
@@ -989,12 +1158,13 @@ static int launch_round(const mica_index *idx, Workspace &w, const ReadsView &rd
     const BidirShape &sh = g_bd_shapes[0];
     BidirArgs ba;
     bidir_args(idx, w, rd, grid, ba);
-    k_bd_round<<<1, 1, 0, s>>>(ba.ctl, ba.fr_cap);
     ba.mode = 1;
     ba.fr_in = frontier_items(w, rd.n, (r + 1) & 1);
     ba.fr_in_meta = frontier_meta(w, rd.n, (r + 1) & 1);
     ba.fr_out = frontier_items(w, rd.n, r & 1);
     ba.fr_out_meta = frontier_meta(w, rd.n, r & 1);
+    if (int rc = check_vector_alignment(ba)) return rc;
+    k_bd_round<<<1, 1, 0, s>>>(ba.ctl, ba.fr_cap);
     sh.fn<<<grid, sh.warps * 32, sh.smem, s>>>(ba);
     launches += 2;
     MICA_CUDA_TRY(cudaGetLastError());
@@ -1022,6 +1192,7 @@ int enqueue_bidir(const mica_index *idx, Workspace &w, const ReadsView &rd, int 
         ba.fr_in_meta = nullptr;
         ba.fr_out = frontier_items(w, rd.n, 0);
         ba.fr_out_meta = frontier_meta(w, rd.n, 0);
+        if (int rc = check_vector_alignment(ba)) return rc;
         sh.fn<<<grid, sh.warps * 32, sh.smem, s>>>(ba);
         launches++;
         MICA_CUDA_TRY(cudaGetLastError());
@@ -1112,6 +1283,8 @@ int run_search_bidir(const mica_index *idx, Workspace &w, mica_stats &st, const 
         st.warp_rounds = out.rounds;
         st.lane_ops = out.lane_ops;
         st.overflow_moves = out.deep_moves;
+        st.verified = out.verified;
+        st.verify_bytes = out.verify_bytes;
         st.spills = out.spills + out.fr_count;   // nodes exported to later rounds
         st.grid_ctas = (uint64_t)grid;
         w.bd_redo_seen = out.redo_reads > 0 || r > BD_GRAPH_ROUNDS;

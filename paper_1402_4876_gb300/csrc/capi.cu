@@ -167,6 +167,7 @@ static int validate_params(const mica_index_params &p)
     if (p.kmer_q < 1 || p.kmer_q > MAX_Q) return MICA_EINVAL;
     if (p.sa_sample < 1 || p.sa_sample > 256) return MICA_EINVAL;
     if (p.lower_bounds > 1) return MICA_EINVAL;
+    if (p.full_sa > 1) return MICA_EINVAL;
     return 0;
 }
 
@@ -196,7 +197,9 @@ static const char MAGIC[8] = {'M', 'I', 'C', 'A', 'I', 'D', 'X', '1'};
 
 struct FileHeader {
     char magic[8];
-    uint32_t version, kmer_q, sa_sample, reserved;
+    uint32_t version, kmer_q, sa_sample;
+    uint32_t flags;   // version 5: bit 0 = the index keeps the whole suffix array, its inverse and the text
+                      // (rebuilt at load, not stored); 0 before version 5
     uint64_t n, dollar_row;
     uint64_t C[5];
     uint64_t n_occ_blocks, n_super, n_mark_blocks, n_samples, table_len;
@@ -290,7 +293,8 @@ static int align_graph(const mica_index *idx, Workspace &w, mica_stats &st, cons
                                (uint64_t)w.big.p, (uint64_t)w.scan_tmp.p, w.hit_capacity, (uint64_t)w.iv_cap,
                                (uint64_t)w.spill_cap, (uint64_t)w.spill_seq.p, (uint64_t)w.deep.p,
                                (uint64_t)p.report | ((uint64_t)idx->tuning.bidir_budget << 32),
-                               ((uint64_t)idx->idle_limit << 32) | idx->spin_limit};
+                               ((uint64_t)idx->idle_limit << 32) | idx->spin_limit,
+                               (uint64_t)w.frontier.p, (uint64_t)w.redo.p, (uint64_t)idx->tuning.bidir_verify};
     if (!w.gexec || memcmp(key, w.gkey, sizeof(key)) != 0) {
         if (w.gexec) { cudaGraphExecDestroy(w.gexec); w.gexec = nullptr; }
         uint64_t L = 0;
@@ -356,6 +360,8 @@ static int align_graph(const mica_index *idx, Workspace &w, mica_stats &st, cons
     st.queue_wait_ns = out.wait_queue_ns;
     st.idle_wait_ns = out.wait_idle_ns;
     st.overflow_moves = out.deep_moves;
+    st.verified = out.verified;
+    st.verify_bytes = out.verify_bytes;
     st.grid_ctas = (uint64_t)grid;
     st.located = nhits;
     st.lf_steps = steps;
@@ -457,6 +463,7 @@ void mica_index_params_default(mica_index_params *p)
     p->kmer_q = 12;
     p->sa_sample = 16;
     p->lower_bounds = 1;
+    p->full_sa = 1;
 }
 
 void mica_align_params_default(mica_align_params *p)
@@ -519,9 +526,10 @@ int mica_index_save(const mica_index *idx, const char *path)
     if (!f) return MICA_EIO;
     FileHeader h{};
     memcpy(h.magic, MAGIC, 8);
-    h.version = 4;
+    h.version = 5;
     h.kmer_q = idx->params.kmer_q;
     h.sa_sample = idx->params.sa_sample;
+    h.flags = idx->has_full_sa ? 1u : 0u;
     h.n = idx->n;
     h.dollar_row = idx->view.dollar_row;
     for (int c = 0; c < 5; c++) h.C[c] = idx->view.C[c];
@@ -570,7 +578,7 @@ int mica_index_load(const char *path, int device, mica_index **out)
     FileHeader h{};
     FileHeaderRev hr{};
     FileHeaderRevTable ht{};
-    if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, MAGIC, 8) != 0 || h.version < 2 || h.version > 4 ||
+    if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, MAGIC, 8) != 0 || h.version < 2 || h.version > 5 || (h.version < 5 ? h.flags != 0 : h.flags > 1) ||
         (h.version >= 3 && (fread(&hr, sizeof(hr), 1, f) != 1 || hr.has_rev > 1)) ||
         (h.version >= 4 && (fread(&ht, sizeof(ht), 1, f) != 1 || ht.has_rev_table > hr.has_rev ||
                             (ht.has_rev_table && ht.rev_nshort != h.nshort))) ||
@@ -606,6 +614,7 @@ int mica_index_load(const char *path, int device, mica_index **out)
     fclose(f);
     idx->has_rev = hr.has_rev != 0;
     idx->params.lower_bounds = hr.has_rev;
+    idx->params.full_sa = h.flags & 1u;
     if (!rc) {
         IndexView &v = idx->view;
         v.occ = (const uint4 *)idx->occ.p;
@@ -639,6 +648,8 @@ int mica_index_load(const char *path, int device, mica_index **out)
         }
         for (uint32_t t = 0; t < v.rev.nshort; t++) v.rev.short_bloom |= 1ull << (v.rev.short_pad[t] & 63);
         rc = upload_variants(idx);
+        if (!rc && (h.flags & 1u)) rc = rebuild_full_sa(idx, 0);
+        set_full_sa_view(idx);
     }
     if (rc) { mica_index_free(idx); return rc; }
     *out = idx;
@@ -659,6 +670,9 @@ void mica_index_free(mica_index *idx)
     dev_release(idx->rocc);
     dev_release(idx->rsuper);
     dev_release(idx->rtable);
+    dev_release(idx->sa_full);
+    dev_release(idx->isa);
+    dev_release(idx->text);
     free_workspace(idx->ws);
     delete idx;
 }
@@ -680,6 +694,8 @@ int mica_index_get_info(const mica_index *idx, mica_index_info *info)
     info->lower_bounds = idx->has_rev ? 1u : 0u;
     info->rev_occ_bytes = idx->has_rev ? idx->n_occ_blocks * 32 + idx->n_super * 16 : 0;
     info->rev_table_bytes = idx->view.rev.table ? idx->table_len * 4 : 0;
+    info->full_sa = idx->has_full_sa ? 1u : 0u;
+    info->full_sa_bytes = idx->has_full_sa ? full_sa_bytes(idx->n) : 0;
     return 0;
 }
 
@@ -825,7 +841,6 @@ int mica_align_batch(mica_index *idx, const uint32_t *packed_reads, const uint64
     if (!idx || !out || !word_offsets || (n_reads && (!packed_reads || !lengths || !k))) return MICA_EINVAL;
     *out = nullptr;
     if (n_reads >= (1ull << 31)) return MICA_EINVAL;
-    if (int rc = validate_host_batch(idx, word_offsets, lengths, k, n_reads)) return rc;
     mica_align_params p;
     mica_align_params_default(&p);
     if (params) p = *params;
@@ -847,6 +862,12 @@ int mica_align_batch(mica_index *idx, const uint32_t *packed_reads, const uint64
     if (n_reads) {
         MICA_CUDA_TRY(cudaMemcpyAsync(w.reads_len.p, lengths, n_reads * 2, cudaMemcpyHostToDevice, s));
         MICA_CUDA_TRY(cudaMemcpyAsync(w.reads_k.p, k, n_reads, cudaMemcpyHostToDevice, s));
+    }
+    // the host threads check the batch while the copies run; nothing is launched before they pass,
+    // and a rejected batch waits for its copies so that the caller may free the buffers on return
+    if ((rc = validate_host_batch(idx, word_offsets, lengths, k, n_reads))) {
+        cudaStreamSynchronize(s);
+        return rc;
     }
     ReadsView rd{(const uint32_t *)w.reads_words.p, (const uint64_t *)w.reads_off.p,
                  (const uint16_t *)w.reads_len.p, (const uint8_t *)w.reads_k.p, n_reads};

@@ -502,6 +502,9 @@ int build_index_from_codes(const uint8_t *d_codes, uint64_t n, const mica_index_
     dev_release(mcnt);
     dev_release(mbase);
 
+    // the whole suffix array (this one), its inverse and the 2-bit text
+    if (p.full_sa && (rc = build_full_sa(idx, sa, d_codes, n, s))) { cleanup(); return rc; }
+
     // q-mer table
     uint64_t tl = (1ull << (2 * p.kmer_q)) + 1;
     {
@@ -521,7 +524,8 @@ int build_index_from_codes(const uint8_t *d_codes, uint64_t n, const mica_index_
         DevBuf rcodes;
         if ((rc = dev_reserve(rcodes, std::max<uint64_t>(n, 1)))) { cleanup(); return rc; }
         if (n) k_reverse_codes<<<grid_for(n), 256, 0, s>>>(d_codes, n, (uint8_t *)rcodes.p);
-        rc = build_suffix_array((const uint8_t *)rcodes.p, n, (uint32_t *)sa.p, s);
+        rc = dev_reserve(sa, rows * 4);   // (empty when the forward suffix array was kept)
+        if (!rc) rc = build_suffix_array((const uint8_t *)rcodes.p, n, (uint32_t *)sa.p, s);
         if (!rc) rc = build_occ((const uint8_t *)rcodes.p, n, (const uint32_t *)sa.p, idx->rocc, idx->rsuper,
                                 rdollar, rC, s);
         // and its q-mer table: the seed of a bidirectional search needs the
@@ -559,6 +563,7 @@ int build_index_from_codes(const uint8_t *d_codes, uint64_t n, const mica_index_
     v.rev.table = idx->has_rev ? (const uint32_t *)idx->rtable.p : nullptr;
     v.q = p.kmer_q;
     v.sa_sample = p.sa_sample;
+    set_full_sa_view(idx);
     return upload_variants(idx);
 }
 

@@ -78,6 +78,12 @@ struct IndexView {
         uint32_t short_len[MAX_Q];
         unsigned long long short_bloom;
     } rev;
+    // The whole suffix array SA[0, n], its inverse ISA[0, n] and the text G at
+    // 2 bits per base (16 per word, least-significant first, zero words past
+    // the end); all null when the index was built without them.
+    const uint32_t *sa_full;
+    const uint32_t *isa;
+    const uint32_t *text;
 };
 
 // Read batch in device memory.
@@ -136,6 +142,8 @@ struct SearchCtl {
     unsigned long long deep_moves;                    // nodes moved to per-warp overflow stacks
     unsigned int redo_reads;                          // bidirectional search: reads given up, to be re-searched
     unsigned int fr_count;                            // bidirectional search: nodes exported this round
+    unsigned long long verified, verify_bytes;        // bidirectional search: one-row intervals checked
+                                                      //   against the text, and the bytes that read
 };
 
 constexpr unsigned ERR_IV_OVERFLOW = 1u;
@@ -165,7 +173,7 @@ struct DeviceGuard {
     ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
 };
 
-constexpr int GRAPH_KEY = 28;   // words identifying a captured batch shape
+constexpr int GRAPH_KEY = 31;   // words identifying a captured batch shape
 
 // Per-index workspace reused across align calls.
 struct Workspace {
@@ -204,10 +212,12 @@ struct mica_index {
     mica::DevBuf occ, super, marks, samples, table, variants;
     mica::DevBuf rocc, rsuper;   // reversed genome's occurrence blocks (lower bounds, bidirectional search)
     mica::DevBuf rtable;         // reversed genome's q-mer table (bidirectional search)
+    mica::DevBuf sa_full, isa, text;   // whole suffix array, its inverse, 2-bit text (full_sa)
     bool has_rev = false;
+    bool has_full_sa = false;
     mica::Workspace ws;
     mica_stats stats{};
-    mica_tuning tuning{-1, 0, 0, {0, 0, 0, 0}, -1, 0};
+    mica_tuning tuning{-1, 0, 0, {0, 0, 0, 0}, -1, 0, 0};
     uint32_t idle_limit = 0, spin_limit = 0;   // persistent kernel wait bounds; 0 = built-in defaults
 };
 
@@ -251,6 +261,13 @@ inline float elapsed_ms(cudaEvent_t a, cudaEvent_t b)
 
 // index_build.cu
 int build_suffix_array(const uint8_t *d_codes, uint64_t n, uint32_t *d_sa, cudaStream_t s);
+// full_sa.cu: the whole suffix array, its inverse and the 2-bit text
+uint64_t full_sa_text_words(uint64_t n);   // text words incl. zero padding (a multiple of 4)
+uint64_t full_sa_bytes(uint64_t n);
+void set_full_sa_view(mica_index *idx);
+int build_full_sa(mica_index *idx, DevBuf &sa, const uint8_t *d_codes, uint64_t n, cudaStream_t s);
+int rebuild_full_sa(mica_index *idx, cudaStream_t s);
+
 int build_index_from_codes(const uint8_t *d_codes, uint64_t n, const mica_index_params &p,
                            mica_index *idx, cudaStream_t s);
 int upload_variants(mica_index *idx);

@@ -362,7 +362,7 @@ __global__ void k_locate(const IndexView ix, Hit *__restrict__ hits, const uint6
     uint32_t steps = 0;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nh;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        hits[i].pos = locate_row(ix, hits[i].pos, steps);
+        hits[i].pos = ix.sa_full ? __ldg(ix.sa_full + hits[i].pos) : locate_row(ix, hits[i].pos, steps);
     }
     unsigned mask = __activemask();
     unsigned s = __reduce_add_sync(mask, steps);

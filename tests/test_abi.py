@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -47,7 +48,10 @@ def test_strerror_and_defaults(lib):
     assert p.hit_cap == 1000 and p.kernel == mica.KERNELS["bidirectional"]
     q = mica.IndexParams()
     lib.mica_index_params_default(ctypes.byref(q))
-    assert (q.kmer_q, q.sa_sample) == (12, 16)
+    assert (q.kmer_q, q.sa_sample, q.lower_bounds, q.full_sa) == (12, 16, 1, 1)
+    bad = mica.IndexParams(12, 16, 1, 2)                      # full_sa is 0 or 1
+    assert lib.mica_index_build_resident(b"ACGT", 4, ctypes.byref(bad), 0, ctypes.byref(ctypes.c_void_p())) == \
+        mica.MICA_EINVAL
 
 
 def test_host_side_rejections_need_no_gpu():
@@ -69,6 +73,14 @@ def test_host_side_rejections_need_no_gpu():
     # pairing rejects an inverted insert window before touching a device
     assert lib.mica_pair_batch(0, None, None, None, 1, 700, 300, None) == mica.MICA_EINVAL
     assert lib.mica_pair_device(None, None, None, 1, 700, 300, None, None) == mica.MICA_EINVAL
+    # the binding checks the host arrays' sizes before the library reads them
+    idx = object.__new__(mica.Index)                  # no index: the check comes first
+    words, off = np.zeros(4, np.uint32), np.array([0, 4], np.uint64)
+    ln, kk = np.array([64], np.uint16), np.array([2], np.uint8)
+    for args in ((words[:3], off, ln, kk), (words, off[:1], ln, kk), (words, off, ln, kk[:0])):
+        with pytest.raises(mica.MicaError) as e:
+            idx.align(*args)
+        assert e.value.code == mica.MICA_EINVAL
     # defaults: pruning on, every placement reported
     p = mica.AlignParams()
     lib.mica_align_params_default(ctypes.byref(p))
@@ -138,10 +150,11 @@ def test_c_program_uses_the_host_calls(lib, tmp_path):
 
 
 class _IndexHeader(ctypes.Structure):
-    """The index file's leading header as the library writes it (version 4):
-    magic, version, q, sampling, the text's sizes and the short-suffix codes."""
+    """The index file's leading header as the library writes it (version 5):
+    magic, version, q, sampling, flags (version 5: bit 0 = the whole suffix
+    array is kept), the text's sizes and the short-suffix codes."""
     _fields_ = [("magic", ctypes.c_char * 8), ("version", ctypes.c_uint32), ("kmer_q", ctypes.c_uint32),
-                ("sa_sample", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("n", ctypes.c_uint64),
+                ("sa_sample", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("n", ctypes.c_uint64),
                 ("dollar_row", ctypes.c_uint64), ("C", ctypes.c_uint64 * 5), ("n_occ_blocks", ctypes.c_uint64),
                 ("n_super", ctypes.c_uint64), ("n_mark_blocks", ctypes.c_uint64), ("n_samples", ctypes.c_uint64),
                 ("table_len", ctypes.c_uint64), ("nshort", ctypes.c_uint32), ("short_pad", ctypes.c_uint32 * 12),
@@ -161,7 +174,7 @@ def _consistent_header(n=1000, q=8, s=16):
 
 
 @pytest.mark.parametrize("field,value", [
-    ("magic", b"MICAIDX9"), ("version", 5), ("kmer_q", 0), ("kmer_q", 13), ("sa_sample", 0),
+    ("magic", b"MICAIDX9"), ("version", 6), ("kmer_q", 0), ("kmer_q", 13), ("sa_sample", 0), ("flags", 1),
     ("n_occ_blocks", 5), ("n_super", 0), ("n_mark_blocks", 0), ("table_len", 17), ("n_samples", 2000),
     ("nshort", 3), ("n", 1 << 32),
 ])
@@ -188,6 +201,20 @@ def test_index_file_header_checked_before_any_device_call(tmp_path, field, value
     for blob in (b"", b"MICAIDX1", bytes(h)[:40]):          # empty and truncated files
         path.write_bytes(blob)
         assert lib.mica_index_load(str(path).encode(), 0, ctypes.byref(out)) == mica.MICA_EIO
+
+
+def test_index_file_flags_checked(tmp_path):
+    """Version 5 headers carry flags (bit 0 alone is defined); earlier versions
+    must have the field zero."""
+    import paper_1402_4876_gb300 as mica
+    lib = mica.lib()
+    out = ctypes.c_void_p()
+    path = tmp_path / "bad.mica"
+    for version, flags in ((5, 2), (5, 0x80000001), (4, 1), (2, 1)):
+        h = _consistent_header()
+        h.version, h.flags = version, flags
+        path.write_bytes(bytes(h) + bytes(4096))
+        assert lib.mica_index_load(str(path).encode(), 0, ctypes.byref(out)) == mica.MICA_EIO, (version, flags)
 
 
 def test_shape_table_and_defaults_need_no_gpu():

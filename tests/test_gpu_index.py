@@ -97,6 +97,74 @@ def test_save_load_roundtrip(tmp_path):
     assert np.array_equal(idx.debug_occ(rows), idx2.debug_occ(rows))
 
 
+def _decode_text(words, n):
+    return ((words[:, None] >> (2 * np.arange(16, dtype=np.uint32))) & 3).astype(np.uint8).ravel()[:n]
+
+
+def _check_full_sa(idx, g, sa):
+    n = g.size
+    got_sa = idx.debug_full_sa("sa")
+    assert np.array_equal(got_sa, sa)
+    isa = idx.debug_full_sa("isa")
+    assert np.array_equal(isa[sa.astype(np.int64)], np.arange(n + 1, dtype=np.uint32))
+    words = idx.debug_full_sa("text")
+    assert words.size % 4 == 0 and words.size * 16 >= n + 64          # zero padding past the end
+    assert np.array_equal(_decode_text(words, n), g)
+    tail = _decode_text(words, words.size * 16)[n:]
+    assert not tail.any()
+
+
+@pytest.mark.parametrize("sa_sample", [1, 5, 16, 32])
+@pytest.mark.parametrize("n", [1, 15, 16, 17, 33, 3001, 40_000])
+def test_full_sa_built_and_rebuilt_at_load(tmp_path, sa_sample, n):
+    """The whole suffix array, its inverse and the 2-bit text: at build time
+    from the index's own suffix array, after a save and load by LF steps from
+    the sampled rows (a walk from row 0 covers the positions above the last
+    multiple of s); both equal the definitions."""
+    rng = np.random.default_rng(n * 7 + sa_sample)
+    g = (rng.integers(0, 4, n) if n % 2 else np.resize(rng.integers(0, 4, 5), n)).astype(np.uint8)
+    m = gc.mica()
+    sa = oracle.sa_sort(g)
+    idx = m.Index.build(synth.to_acgt_bytes(g), kmer_q=min(8, max(1, n)), sa_sample=sa_sample)
+    info = idx.info()
+    assert info["full_sa"] == 1 and info["full_sa_bytes"] == 8 * (n + 1) + 4 * (((n + 15) // 16 + 7) // 4 * 4)
+    _check_full_sa(idx, g, sa)
+    path = str(tmp_path / "idx.mica")
+    idx.save(path)
+    idx2 = m.Index.load(path)
+    assert idx2.info() == info
+    _check_full_sa(idx2, g, sa)
+    rows = np.arange(n + 1, dtype=np.uint64)
+    assert np.array_equal(idx2.debug_locate(rows), sa)          # the LF walk still answers too
+    idx.free(); idx2.free()
+
+
+def test_full_sa_64m_and_without(tmp_path):
+    """At 64 Mbp: the built arrays against the oracle's suffix array, and the
+    arrays rebuilt from a saved file equal the built ones; an index built
+    without them reports none and refuses the debug copy."""
+    m = gc.mica()
+    g = gc.genome("64m").codes
+    idx = gc.gpu_index("64m")
+    _check_full_sa(idx, g, gc.oracle_index("64m").sa())
+    path = str(tmp_path / "idx64.mica")
+    idx.save(path)
+    idx2 = m.Index.load(path)
+    for which in ("sa", "isa", "text"):
+        assert np.array_equal(idx2.debug_full_sa(which), idx.debug_full_sa(which)), which
+    idx2.free()
+    small = g[:100_000]
+    idx3 = m.Index.build(synth.to_acgt_bytes(small), kmer_q=10, sa_sample=16, full_sa=False)
+    assert idx3.info()["full_sa"] == 0 and idx3.info()["full_sa_bytes"] == 0
+    with pytest.raises(m.MicaError) as e:
+        idx3.debug_full_sa("sa", 0, 10)
+    assert e.value.code == m.MICA_EINVAL
+    path3 = str(tmp_path / "idx_nofull.mica")
+    idx3.save(path3)
+    assert m.Index.load(path3).info()["full_sa"] == 0
+    idx3.free()
+
+
 def test_gather_ceiling_orders_l2_above_hbm():
     """The random-gather ceiling: a buffer that fits L2 serves 32-byte random
     loads faster than one twelve times L2's size, and both stay below a

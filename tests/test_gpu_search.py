@@ -215,6 +215,70 @@ def test_uneven_64m_100k_reads_equal_oracle():
     assert int(want.total.max()) > 1000 and np.count_nonzero(b.k == 3) > 20_000
 
 
+def test_bidirectional_text_check_settings():
+    """One-row intervals checked against the text (the whole suffix array,
+    its inverse and the 2-bit text resident): with the check after 1, 8 or the
+    default 20 matched bases, with it off (256), and on an index without the
+    arrays, every result equals the oracle, on the uneven 64 Mbp sample
+    (k 0..3, lengths 50..250, reads inside planted repeats) and on diverged
+    (AC)^n reads, with and without a cap and with small node budgets."""
+    g = gc.genome("64m")
+    b = synth.reads_uneven(g, n=200_000).subset(np.arange(0, 200_000, 100))   # 2,000 reads
+    want = gc.oracle_index("64m").align(b, cap=1000)
+    idx = gc.gpu_index("64m")
+    try:
+        for verify in (1, 8, 0, 256):
+            for budget in (0, 16):
+                idx.set_tuning(bidir_verify=verify, bidir_budget=budget)
+                got = idx.align_batch(b, hit_cap=1000, kernel="bidirectional")
+                gc.assert_same(got, want, f"verify {verify} budget {budget}")
+                st = idx.stats()
+                assert (st["verified"] > 0) == (verify < 256), (verify, st["verified"])
+                assert (st["verify_bytes"] > 0) == (verify < 256)
+    finally:
+        idx.set_tuning()
+    rng = np.random.default_rng(9)
+    core = np.resize(np.array([0, 1], np.uint8), 30_000)
+    mut = rng.random(core.size) < 0.04
+    core[mut] = (core[mut] + rng.integers(1, 4, size=int(mut.sum()))) & 3
+    tg = np.concatenate([rng.integers(0, 4, 20_000).astype(np.uint8), core, rng.integers(0, 4, 5_000).astype(np.uint8)])
+    reads = [tg[i: i + 60].copy() for i in range(0, 55_000 - 60, 2_300)]
+    tb = gc.batch_from_reads(reads, [2] * (len(reads) // 2) + [3] * (len(reads) - len(reads) // 2))
+    tfm = oracle.FMIndex(tg)
+    m = gc.mica()
+    for full_sa in (True, False):
+        tidx = m.Index.build(synth.to_acgt_bytes(tg), kmer_q=10, sa_sample=8, full_sa=full_sa)
+        for verify in (1, 0):
+            tidx.set_tuning(bidir_verify=verify)
+            for cap in (0, 7):
+                got = tidx.align_batch(tb, hit_cap=cap, kernel="bidirectional")
+                gc.assert_same(got, tfm.align(tb, cap=cap), f"tandem full_sa={full_sa} verify {verify} cap={cap}")
+                assert (tidx.stats()["verified"] > 0) == full_sa
+        tidx.free()
+
+
+def test_bidirectional_odd_batch_above_half_million():
+    """A batch of an odd number of reads above 2^19: each frontier buffer then
+    holds 2n items, and the second one must still start on a 16-byte
+    boundary for the kernel's 16-byte item loads and stores.  A budget of 8
+    nodes sends most reads through several rounds, which alternate between
+    the two buffers; the result equals the persistent kernel's."""
+    g = gc.genome("64m")
+    b = synth.reads_64m(g, n=600_001)
+    assert b.n % 2 == 1 and b.n > 1 << 19
+    idx = gc.gpu_index("64m")
+    want = idx.align_batch(b, hit_cap=1000, kernel="persistent")
+    try:
+        for budget in (8, 0):
+            idx.set_tuning(bidir_budget=budget)
+            got = idx.align_batch(b, hit_cap=1000, kernel="bidirectional")
+            gc.assert_same(got, want, f"budget {budget}")
+            if budget:
+                assert idx.stats()["spills"] > b.n          # most reads went through later rounds
+    finally:
+        idx.set_tuning()
+
+
 def test_bidirectional_frontier_rounds_and_give_up():
     """The bidirectional kernel's budget: a task over its node budget exports
     its pending nodes, and further launches continue them as tasks of their
