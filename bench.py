@@ -74,6 +74,25 @@ def search_alg_bytes(kernel: str, st: dict, read_bytes: int) -> int:
     return 32 * st["rank_blocks"] + 8 * st["seeds"] + 2 * read_bytes + 16 * st["intervals"]
 
 
+def gather_floor(kernel: str, st: dict, read_bytes: int, index_gbs: float, text_gbs: float, copy_gbs: float):
+    """The least time a search step's memory accesses can take at the measured
+    ceilings: every 32-byte sector it gathers from the index (occurrence
+    blocks, one q-mer table sector per table and seed, leaf writes) at the
+    random-gather rate of the level the index lives in (L2 when it fits, else
+    HBM), every sector of the text checks (SA, ISA, text windows: HBM) at the
+    HBM random-gather rate, and the packed reads streamed at copy bandwidth.
+    Returns (seconds, parts in ms)."""
+    seed_sectors = (2 if kernel == "bidirectional" else 1) * st["seeds"]
+    index_sectors = st["rank_blocks"] + seed_sectors + (st["intervals"] + 1) // 2
+    t_index = index_sectors * 32 / (index_gbs * 1e9)
+    t_text = st.get("verify_sectors", 0) * 32 / (text_gbs * 1e9)
+    t_reads = (read_bytes if kernel == "bidirectional" else 2 * read_bytes) / (copy_gbs * 1e9)
+    parts = {"index_gathers_ms": round(t_index * 1e3, 4), "text_check_gathers_ms": round(t_text * 1e3, 4),
+             "read_stream_ms": round(t_reads * 1e3, 4), "index_sectors": int(index_sectors),
+             "text_check_sectors": int(st.get("verify_sectors", 0))}
+    return t_index + t_text + t_reads, parts
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -245,13 +264,16 @@ def make_workload(n_reads: int, rank: int):
     return g, reads
 
 
-def gather_ceilings(mica, idx, device: int) -> dict:
+def gather_ceilings(mica, idx, device: int, kernel: str = "bidirectional") -> dict:
     """Random 32-byte gather ceilings measured after the timed region: one
     over a buffer the size of the search's hot index arrays (occurrence
-    blocks + q-mer table: the same L2/HBM mix as the search), one over
-    1.5 GiB (HBM)."""
+    blocks + q-mer tables, of both directions for the bidirectional kernel:
+    the same L2/HBM mix as the search), one over 1.5 GiB (HBM)."""
     info = idx.info()
-    hot = max(1 << 20, (info["occ_bytes"] + info["table_bytes"] + 31) // 32 * 32)
+    hot = info["occ_bytes"] + info["table_bytes"]
+    if kernel == "bidirectional":
+        hot += info["rev_occ_bytes"] + info["rev_table_bytes"]
+    hot = max(1 << 20, (hot + 31) // 32 * 32)
     a = mica.gather_ceiling(hot, 32, loads=1 << 27, repeats=3, device=device)
     b = mica.gather_ceiling(3 << 29, 32, loads=1 << 27, repeats=3, device=device)
     return {"load_bytes": 32, "index_sized_bytes": hot, "index_sized_gbs": round(a["gbs"], 1),
@@ -333,7 +355,11 @@ def run_ours(args):
     st = stats[-1]
     out["work_per_step"] = {k: int(st[k]) for k in ("seeds", "nodes", "rank_blocks", "intervals", "located",
                                                     "lf_steps", "spills", "lb_steps", "lb_dead_tasks",
-                                                    "verified", "verify_bytes")}
+                                                    "verified", "verify_bytes", "verify_sectors", "warp_rounds",
+                                                    "grid_ctas")}
+    if st["warp_rounds"]:
+        out["work_per_step"]["lanes_per_round"] = round(
+            (st["nodes"] + st["seeds"] + st["verified"]) / st["warp_rounds"], 2)
     out["gpu_launches"] = int(sum(s["launches"] for s in stats))
     out["graph_replays"] = int(sum(s["graph_replays"] for s in stats))
 
@@ -349,22 +375,29 @@ def run_ours(args):
     achieved = alg_bytes / kernel_s / 1e9
     traffic = profile_traffic(SEARCH_CU if args.kernel == "persistent" else BIDIR_CU,
                               PROFILE if args.kernel == "persistent" else PROFILE_BIDIR)
-    ceil = gather_ceilings(mica, idx, local)
+    ceil = gather_ceilings(mica, idx, local, args.kernel)
     gc_idx = ceil["index_sized_gbs"]
-    out["roofline"] = {"bound": "l2_random_gather", "achieved": round(achieved, 1), "peak": gc_idx, "unit": "GB/s",
-                       "frac": round(achieved / gc_idx, 4) if gc_idx else None, "traffic": traffic,
+    t_floor, floor_parts = gather_floor(args.kernel, st, read_bytes, gc_idx, ceil["hbm_gbs"], peaks["hbm_gbs"])
+    peak = alg_bytes / t_floor / 1e9
+    out["roofline"] = {"bound": "random_gather_l2_and_hbm", "achieved": round(achieved, 1), "peak": round(peak, 1),
+                       "unit": "GB/s", "frac": round(t_floor / kernel_s, 4), "traffic": traffic,
                        "kernel": KERNEL_NAMES[args.kernel] + " (one search step)",
                        "kernel_ms": round(kernel_s * 1e3, 3),
                        "alg_bytes_per_launch": int(alg_bytes),
                        "alg_bytes_what": ALG_LABEL[args.kernel],
-                       "peak_source": "measured in this run: mica_gather_ceiling, independent random 32 B loads "
-                                      "over a buffer of the index's size (L2-resident), full occupancy",
+                       "peak_source": "the step's algorithmic bytes / its gather floor: the least time its sectors "
+                                      "take at the random-gather ceilings measured in this run (index gathers at "
+                                      "the rate over an index-sized buffer, which stays in L2; text-check gathers "
+                                      "at the rate over 1.5 GiB, HBM; reads at the copy bandwidth); frac = floor / "
+                                      "kernel time",
+                       "floor_ms": round(t_floor * 1e3, 4), "floor_parts": floor_parts,
+                       "frac_of_index_gather_ceiling": round(achieved / gc_idx, 4) if gc_idx else None,
                        "hbm_copy_peak": peaks["hbm_gbs"],
                        "frac_of_hbm_copy": round(achieved / peaks["hbm_gbs"], 4),
                        "hbm_copy_peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json, copy bandwidth)",
                        "gather_ceiling": ceil,
-                       "note": "traffic (DRAM bytes per step, ncu) is far below the algorithmic bytes: the index "
-                               "stays in L2; the kernel is latency-bound on dependent gathers"}
+                       "note": "the index stays in L2 (DRAM traffic of the step is a fraction of its algorithmic "
+                               "bytes); the kernel is latency-bound on chains of dependent gathers"}
     out["clocks"] = clocks
     out["rank_blocks_per_s"] = round(st["rank_blocks"] / kernel_s, 1)
     out["mbp_per_s"] = round(value * float(np.mean(b.lengths)) / 1e6, 1)   # bases of reads aligned
@@ -380,7 +413,10 @@ def run_ours(args):
                   "kernel_ms": round(statistics.mean(okms), 3), "kernel": KERNEL_NAMES[other],
                   "search": SEARCH_LABEL[other], "nodes": int(ost["nodes"]), "seeds": int(ost["seeds"]),
                   "rank_blocks": int(ost["rank_blocks"]),
-                  "roofline_frac": round(oalg / (statistics.mean(okms) / 1e3) / 1e9 / gc_idx, 4) if gc_idx else None,
+                  "roofline_frac": round(gather_floor(other, ost, read_bytes,
+                                                      gather_ceilings(mica, idx, local, other)["index_sized_gbs"],
+                                                      ceil["hbm_gbs"], peaks["hbm_gbs"])[0]
+                                         / (statistics.mean(okms) / 1e3), 4),
                   f"{args.kernel}_over_{other}": round(value / oval, 3)}
 
     if not args.no_plain:
@@ -411,27 +447,49 @@ def run_ours(args):
                         "what": "one (read, strand) task per thread, lower-bound pruning, device re-queue"}
 
     if not args.no_e2e:
-        # end to end through the public host-buffer call: pinned inputs in, hits out
+        # end to end through the public host-buffer API: every step copies its
+        # batch in from pinned host memory and its result out (mica_align_submit /
+        # mica_align_collect: while one batch searches, the next one's copies and
+        # host checks run and the previous one's result comes back)
         pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
         hw, ho, hl, hk = pin(b.words), pin(b.word_off), pin(b.lengths), pin(b.k)
-        # warm-up in the timed loop's own form: the result of one call lives while the next runs,
-        # so the library's pinned result pool ends the warm-up holding the two blocks it cycles
-        res = None
-        for _ in range(max(2, args.warmup)):
-            res = idx.align(hw, ho, hl, hk, hit_cap=HIT_CAP, kernel=args.kernel, stream=stream)
+
+        def stream_steps(count):
+            prev, res = None, None
+            for _ in range(count):
+                t = idx.submit(hw, ho, hl, hk, hit_cap=HIT_CAP, kernel=args.kernel)
+                if prev is not None:
+                    res = idx.collect(prev)
+                prev = t
+            return idx.collect(prev)
+
+        stream_steps(max(3, args.warmup))      # both slots capture their launch sequence
         barrier(world)
+        e2e_steps = max(2, min(args.steps, 10))
         t = time.perf_counter()
-        e2e_steps = max(1, min(args.steps, 5))
-        for _ in range(e2e_steps):
-            res = idx.align(hw, ho, hl, hk, hit_cap=HIT_CAP, kernel=args.kernel, stream=stream)
-        torch.cuda.synchronize(dev)
+        res = stream_steps(e2e_steps)
         el = max_over_ranks(time.perf_counter() - t, world)
         h2d = hw.nbytes + ho.nbytes + hl.nbytes + hk.nbytes
         d2h = res.total.nbytes + res.offsets.nbytes + res.hits.nbytes
         out["e2e"] = {"value": round(world * b.n * e2e_steps / el, 1), "unit": "reads/s",
                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                      "api": "mica_align_batch (host buffers; pinned inputs, results in pinned memory)",
+                      "steps": e2e_steps,
+                      "api": "mica_align_submit / mica_align_collect (host buffers: each step copies its pinned "
+                             "input in and its result out; two batches in flight)",
                       "kernel": KERNEL_LABEL[args.kernel]}
+        # the one-call form (mica_align_batch: copies, search and result in series)
+        res = None
+        for _ in range(max(2, args.warmup)):
+            res = idx.align(hw, ho, hl, hk, hit_cap=HIT_CAP, kernel=args.kernel, stream=stream)
+        barrier(world)
+        one_steps = max(1, min(args.steps, 5))
+        t = time.perf_counter()
+        for _ in range(one_steps):
+            res = idx.align(hw, ho, hl, hk, hit_cap=HIT_CAP, kernel=args.kernel, stream=stream)
+        torch.cuda.synchronize(dev)
+        el1 = max_over_ranks(time.perf_counter() - t, world)
+        out["e2e"]["one_call"] = {"value": round(world * b.n * one_steps / el1, 1), "unit": "reads/s",
+                                  "api": "mica_align_batch (copies in, search, result out, in series)"}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(g, b)
@@ -505,7 +563,9 @@ def uneven_leg(mica, idx, g, n_reads, steps, warmup, stream, flush, headline="bi
         out[kernel] = {"value": round(b.n * len(ms) / (sum(ms) / 1e3), 1), "ms_per_step": round(statistics.mean(ms), 3),
                        "kernel_ms": round(statistics.mean(kms), 3), "launches": int(st["launches"]),
                        "nodes": int(st["nodes"]), "seeds": int(st["seeds"]), "rank_blocks": int(st["rank_blocks"]),
-                       "intervals": int(st["intervals"]), "retries": int(st["retries"]), "hits": int(r.n_hits)}
+                       "intervals": int(st["intervals"]), "retries": int(st["retries"]), "hits": int(r.n_hits),
+                       "verified": int(st["verified"]), "verify_bytes": int(st["verify_bytes"]),
+                       "verify_sectors": int(st["verify_sectors"])}
     h = out[headline]
     out["value"] = h["value"]
     out["kernel"] = KERNEL_LABEL[headline]
@@ -515,13 +575,20 @@ def uneven_leg(mica, idx, g, n_reads, steps, warmup, stream, flush, headline="bi
     read_bytes = 4 * int(np.sum((b.lengths.astype(np.int64) + 15) // 16))
     alg = search_alg_bytes(headline, h, read_bytes)
     info = idx.info()
-    ceil = mica.gather_ceiling(max(1 << 20, (info["occ_bytes"] + info["table_bytes"] + 31) // 32 * 32),
-                               32, loads=1 << 27, repeats=3)
+    hot = info["occ_bytes"] + info["table_bytes"] + info["rev_occ_bytes"] + info["rev_table_bytes"]
+    ceil = mica.gather_ceiling(max(1 << 20, (hot + 31) // 32 * 32), 32, loads=1 << 27, repeats=3)
+    hbm = mica.gather_ceiling(3 << 29, 32, loads=1 << 27, repeats=3)
+    peaks, _ = measured_peaks()
     ach = alg / (h["kernel_ms"] / 1e3) / 1e9
-    out["roofline"] = {"bound": "l2_random_gather", "achieved": round(ach, 1), "peak": round(ceil["gbs"], 1),
-                       "unit": "GB/s", "frac": round(ach / ceil["gbs"], 4), "kernel": KERNEL_NAMES[headline],
+    t_floor, parts = gather_floor(headline, h, read_bytes, ceil["gbs"], hbm["gbs"], peaks["hbm_gbs"])
+    out["roofline"] = {"bound": "random_gather_l2_and_hbm", "achieved": round(ach, 1),
+                       "peak": round(alg / t_floor / 1e9, 1), "unit": "GB/s",
+                       "frac": round(t_floor / (h["kernel_ms"] / 1e3), 4), "kernel": KERNEL_NAMES[headline],
                        "alg_bytes_per_launch": int(alg), "alg_bytes_what": ALG_LABEL[headline],
-                       "peak_source": "measured in this run: random 32 B gathers over an index-sized buffer"}
+                       "floor_ms": round(t_floor * 1e3, 4), "floor_parts": parts,
+                       "peak_source": "algorithmic bytes / gather floor at the random-gather rates measured in this "
+                                      "run (index-sized buffer: L2; 1.5 GiB: HBM, for the text checks)",
+                       "index_gather_gbs": round(ceil["gbs"], 1), "hbm_gather_gbs": round(hbm["gbs"], 1)}
     return out
 
 
@@ -569,6 +636,7 @@ def human_leg(mica, dev, stream, pairs: int, genome_bp: int, steps: int = 2, pla
     kernels = (headline, other) + (("plain",) if plain else ())
     for kernel in kernels:
         tot_ms, tot_kms, nodes, blocks, seeds, hits, ivs, retries = 0.0, 0.0, 0, 0, 0, 0, 0, 0
+        vbytes, vsect, verified = 0, 0, 0
         reps = steps if kernel != "plain" else 1
         for r0 in range(0, b.n, batch):
             sub = b.subset(np.arange(r0, min(b.n, r0 + batch))) if b.n > batch else b
@@ -595,10 +663,14 @@ def human_leg(mica, dev, stream, pairs: int, genome_bp: int, steps: int = 2, pla
             seeds += st["seeds"]
             ivs += st["intervals"]
             retries += st["retries"]
+            vbytes += st["verify_bytes"]
+            vsect += st["verify_sectors"]
+            verified += st["verified"]
             hits += r.n_hits
         res[kernel] = {"value": round(b.n / (tot_ms / 1e3), 1), "pairs_per_s": round(b.n / 2 / (tot_ms / 1e3), 1),
                        "ms_total": round(tot_ms, 1), "kernel_ms_total": round(tot_kms, 1), "nodes": int(nodes),
                        "rank_blocks": int(blocks), "seeds": int(seeds), "intervals": int(ivs),
+                       "verified": int(verified), "verify_bytes": int(vbytes), "verify_sectors": int(vsect),
                        "retries": int(retries), "hits": int(hits)}
     peaks, src = measured_peaks()
     p = res[headline]
@@ -607,6 +679,8 @@ def human_leg(mica, dev, stream, pairs: int, genome_bp: int, steps: int = 2, pla
     achieved = alg / (p["kernel_ms_total"] / 1e3) / 1e9
     hot = int(info["occ_bytes"] + info["rev_occ_bytes"] + info["table_bytes"] + info["rev_table_bytes"])
     ceil = mica.gather_ceiling((hot + 31) // 32 * 32, 32, loads=1 << 27, repeats=3)
+    t_floor, floor_parts = gather_floor(headline, p, read_bytes, ceil["gbs"], ceil["gbs"], peaks["hbm_gbs"])
+    peak = alg / t_floor / 1e9
     traffic = profile_traffic(BIDIR_CU if headline == "bidirectional" else SEARCH_CU,
                               PROFILE_BIDIR_HUMAN if headline == "bidirectional" else PROFILE_HUMAN,
                               "dram_bytes_search_step")
@@ -620,12 +694,18 @@ def human_leg(mica, dev, stream, pairs: int, genome_bp: int, steps: int = 2, pla
            headline: res[headline], other: res[other],
            f"{headline}_over_{other}": round(res[headline]["value"] / res[other]["value"], 3),
            "generate_s": round(gen_s, 1), "index_build_s": round(build_s, 1),
-           "roofline": {"bound": "hbm_random_gather", "achieved": round(achieved, 1), "peak": round(ceil["gbs"], 1),
-                        "unit": "GB/s", "frac": round(achieved / ceil["gbs"], 4),
+           "roofline": {"bound": "hbm_random_gather", "achieved": round(achieved, 1), "peak": round(peak, 1),
+                        "unit": "GB/s", "frac": round(t_floor / (p["kernel_ms_total"] / 1e3), 4),
                         "traffic": traffic, "kernel": KERNEL_NAMES[headline],
                         "alg_bytes_per_launch": int(alg / n_batches), "alg_bytes_what": ALG_LABEL[headline],
-                        "peak_source": f"measured in this run: random 32 B gathers over {hot >> 20} MiB "
-                                       "(the index's occurrence blocks and q-mer tables of both directions: HBM)",
+                        "peak_source": f"the step's algorithmic bytes / its gather floor: the least time its "
+                                       f"sectors take at the random 32 B gather rate measured in this run over "
+                                       f"{hot >> 20} MiB (the index's occurrence blocks and q-mer tables of both "
+                                       f"directions: HBM; the text-check arrays are HBM too), reads at the copy "
+                                       f"bandwidth; frac = floor / kernel time",
+                        "floor_ms": round(t_floor * 1e3, 3), "floor_parts": floor_parts,
+                        "random_gather_gbs": round(ceil["gbs"], 1),
+                        "frac_of_random_gather_by_bytes": round(achieved / ceil["gbs"], 4),
                         "hbm_copy_peak": peaks["hbm_gbs"], "frac_of_hbm_copy": round(achieved / peaks["hbm_gbs"], 4),
                         "hbm_copy_peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)"}}
     if "plain" in res:

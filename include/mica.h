@@ -57,8 +57,9 @@ enum {
     MICA_ECUDA = -4,      /* a CUDA runtime call failed */
     MICA_ETIMEOUT = -5,   /* a bounded device or host wait expired */
     MICA_EINTERNAL = -6,  /* an internal capacity retry did not converge (should not happen) */
-    MICA_EBUSY = -7,      /* serving: the request is not finished yet */
-    MICA_ENOTFOUND = -8   /* serving: unknown request id */
+    MICA_EBUSY = -7,      /* serving: the request is not finished yet; pipelined batches: both slots
+                             are in flight */
+    MICA_ENOTFOUND = -8   /* serving: unknown request id; pipelined batches: unknown ticket */
 };
 
 #define MICA_MAX_READ_LEN 256   /* bases per read */
@@ -164,6 +165,8 @@ typedef struct {
                                 warp whose overflow stack filled), searched again by the persistent kernel */
     uint64_t verified;       /* bidirectional kernel: one-row intervals checked against the genome's text */
     uint64_t verify_bytes;   /* bytes those checks read: suffix array and inverse entries, text words */
+    uint64_t verify_sectors; /* 32-byte sectors those reads touch (one per SA or ISA entry, the text
+                                window's span) */
     float search_ms;         /* device time of the search phase (kernel + its control copies) */
     float kernel_ms;         /* device time of the search kernel launch(es) alone, with the
                                 lower-bound pass when pruning */
@@ -237,6 +240,28 @@ int mica_align_batch(mica_index *idx, const uint32_t *packed_reads, const uint64
 void mica_result_free(mica_result *res);
 
 /*
+ * Pipelined host batches (Section 2: the host feeds the card the next batch
+ * of reads while it works on the current one).  mica_align_submit stages a
+ * batch given in host memory (same layout and checks as mica_align_batch) on
+ * one of the index's two pipeline slots, each with its own stream and
+ * workspace, queues its search and returns without waiting for the device;
+ * *ticket names the batch.  mica_align_collect waits for that batch, copies
+ * its result back and returns it as a new mica_result (free it with
+ * mica_result_free).  While one batch searches, the next one's copies and
+ * host checks run and the previous one's result comes back.  At most two
+ * batches are in flight per index: a third submit returns MICA_EBUSY;
+ * collecting an unknown or already collected ticket returns MICA_ENOTFOUND.
+ * The caller's host buffers must stay valid and unchanged until the batch is
+ * collected.  params->cuda_stream is not used (each slot has its own stream).
+ * Batches may be collected in any order.  Calls on one index are not
+ * thread-safe; mica_get_stats reports the last collected batch.
+ */
+int mica_align_submit(mica_index *idx, const uint32_t *packed_reads, const uint64_t *word_offsets,
+                      const uint16_t *lengths, const uint8_t *k, uint64_t n_reads,
+                      const mica_align_params *params, uint64_t *ticket);
+int mica_align_collect(mica_index *idx, uint64_t ticket, mica_result **out);
+
+/*
  * Align a batch already in DEVICE memory (same layout as mica_align_batch).
  * The result stays on the device (see mica_device_result).  The call returns
  * after the result is complete on the given stream.
@@ -266,7 +291,7 @@ typedef struct {
     uint32_t bidir_verify;  /* bidirectional kernel with full_sa: an interval of one row whose matched
                                part is at least this many bases (and which has at least 8 bases
                                left to match) is checked against the genome's text in one step
-                               instead of being extended base by base; 0 = 20, 256 or more = never */
+                               instead of being extended base by base; 0 = 12, 256 or more = never */
 } mica_tuning;
 
 /* Number of compiled persistent kernel shapes; mica_tuning_shape_info

@@ -68,7 +68,7 @@ class Stats(ctypes.Structure):
                  "spills", "retries", "launches", "warp_rounds", "lane_ops", "rounds_multi", "rounds_single",
                  "rounds_seed", "graph_captures", "graph_replays", "graph_fallbacks", "lb_steps",
                  "lb_dead_tasks", "queue_wait_ns", "idle_wait_ns", "overflow_moves", "grid_ctas", "fallback_reads",
-                 "verified", "verify_bytes")] + [("search_ms", ctypes.c_float), ("kernel_ms", ctypes.c_float),
+                 "verified", "verify_bytes", "verify_sectors")] + [("search_ms", ctypes.c_float), ("kernel_ms", ctypes.c_float),
                                                       ("total_ms", ctypes.c_float)]
 
     def as_dict(self) -> dict:
@@ -129,6 +129,8 @@ SIGNATURES = {
     "mica_index_get_info": (_i32, [P, P]),
     "mica_align_batch": (_i32, [P, P, P, P, P, _u64, P, P]),
     "mica_result_free": (None, [P]),
+    "mica_align_submit": (_i32, [P, P, P, P, P, _u64, P, P]),
+    "mica_align_collect": (_i32, [P, _u64, P]),
     "mica_align_device": (_i32, [P, P, P, P, P, _u64, P, P]),
     "mica_get_stats": (_i32, [P, P]),
     "mica_debug_suffix_array": (_i32, [P, _u64, _i32, P]),
@@ -311,6 +313,7 @@ class Index:
 
     def __init__(self, handle: int):
         self._h = ctypes.c_void_p(handle)
+        self._inflight = {}   # ticket -> the host arrays the library still reads
 
     @classmethod
     def build(cls, genome_acgt, kmer_q: int = 12, sa_sample: int = 16, device: int = 0,
@@ -405,9 +408,8 @@ class Index:
                            _stream_handle(stream), int(bool(prune)),
                            REPORTS[report] if isinstance(report, str) else int(report))
 
-    def align(self, words, word_off, lengths, k, hit_cap: int = 1000, kernel="bidirectional",
-              stream=None, prune: bool = True, report="all") -> Result:
-        """mica_align_batch on host arrays (copies in, searches, copies out)."""
+    @staticmethod
+    def _host_batch(what, words, word_off, lengths, k):
         words = np.ascontiguousarray(words, dtype=np.uint32)
         word_off = np.ascontiguousarray(word_off, dtype=np.uint64)
         lengths = np.ascontiguousarray(lengths, dtype=np.uint16)
@@ -415,15 +417,48 @@ class Index:
         n = lengths.size
         # the library reads word_off[n] words, n + 1 offsets and n budgets from these buffers
         if word_off.size != n + 1 or k.size != n or int(word_off[-1]) > words.size:
-            raise MicaError(MICA_EINVAL, f"mica_align_batch: {n} lengths need {n + 1} word offsets (got "
+            raise MicaError(MICA_EINVAL, f"{what}: {n} lengths need {n + 1} word offsets (got "
                                          f"{word_off.size}), {n} budgets (got {k.size}) and the words the "
                                          f"last offset names (got {words.size})")
+        return words, word_off, lengths, k, n
+
+    def align(self, words, word_off, lengths, k, hit_cap: int = 1000, kernel="bidirectional",
+              stream=None, prune: bool = True, report="all") -> Result:
+        """mica_align_batch on host arrays (copies in, searches, copies out)."""
+        words, word_off, lengths, k, n = self._host_batch("mica_align_batch", words, word_off, lengths, k)
         p = self._params(hit_cap, kernel, stream, prune, report)
         out = ctypes.POINTER(_Result)()
         _check(_lib.mica_align_batch(self._h, _ptr(words) if words.size else None, _ptr(word_off),
                                      _ptr(lengths) if n else None, _ptr(k) if n else None, n,
                                      ctypes.byref(p), ctypes.byref(out)), "mica_align_batch")
         return _take_result(out)
+
+    def submit(self, words, word_off, lengths, k, hit_cap: int = 1000, kernel="bidirectional",
+               prune: bool = True, report="all") -> int:
+        """mica_align_submit: stage a host batch on a free pipeline slot and
+        queue its search; returns the ticket for collect().  The arrays are
+        kept alive here until the batch is collected."""
+        words, word_off, lengths, k, n = self._host_batch("mica_align_submit", words, word_off, lengths, k)
+        p = self._params(hit_cap, kernel, None, prune, report)
+        t = ctypes.c_uint64()
+        _check(_lib.mica_align_submit(self._h, _ptr(words) if words.size else None, _ptr(word_off),
+                                      _ptr(lengths) if n else None, _ptr(k) if n else None, n,
+                                      ctypes.byref(p), ctypes.byref(t)), "mica_align_submit")
+        self._inflight[t.value] = (words, word_off, lengths, k)
+        return t.value
+
+    def collect(self, ticket: int) -> Result:
+        """mica_align_collect: wait for a submitted batch and return its result."""
+        out = ctypes.POINTER(_Result)()
+        rc = _lib.mica_align_collect(self._h, ticket, ctypes.byref(out))
+        if rc != MICA_ENOTFOUND:
+            self._inflight.pop(ticket, None)   # the library is done with the batch's host arrays
+        _check(rc, "mica_align_collect")
+        return _take_result(out)
+
+    def submit_batch(self, batch, **kw) -> int:
+        """submit() on any object with words/word_off/lengths/k arrays."""
+        return self.submit(batch.words, batch.word_off, batch.lengths, batch.k, **kw)
 
     def align_batch(self, batch, **kw) -> Result:
         """align() on any object with words/word_off/lengths/k arrays."""

@@ -59,7 +59,7 @@ constexpr uint32_t BD_ADMIT_LOW = 64;       // admit new tasks while fewer items
 constexpr uint32_t BD_DEEP_MIN = 8192;      // entries of each per-warp overflow stack, at least
 constexpr uint32_t SCHEME_FREE = 7;         // the single scheme of reads shorter than k + 1
 constexpr uint32_t BD_BUDGET = 1u << 12;    // node expansions a task may take before it exports its nodes
-constexpr uint32_t BD_VERIFY_MIN = 20;      // matched bases of a one-row node before it is checked against the text
+constexpr uint32_t BD_VERIFY_MIN = 12;      // matched bases of a one-row node before it is checked against the text
 constexpr uint32_t BD_VERIFY_LEFT = 8;      // ... when at least this many bases are left to match
 constexpr int VCAP = 64;                    // one-row nodes waiting for that check (at most 63: see the round choice)
 
@@ -241,12 +241,15 @@ __device__ __forceinline__ bool bd_allowed(uint32_t j, uint32_t a, uint32_t pos,
 // the window G[t - A, t - A + m) lies inside G and meets the scheme: at most
 // k mismatches in all, none in piece j, at least one in each piece left of j
 // (the free scheme of short reads: the budget alone).  The window's mismatch
-// count goes to d, the text words read to words.
+// count goes to d, the text words read to words and the 32-byte sectors
+// they span to sectors.
 __device__ __forceinline__ bool bd_check_window(const uint32_t *__restrict__ text, uint64_t n, const uint32_t *pat,
                                                 uint32_t m, unsigned long long bnds, uint32_t j, uint32_t k,
-                                                uint32_t t, uint32_t A, uint32_t &d, uint32_t &words)
+                                                uint32_t t, uint32_t A, uint32_t &d, uint32_t &words,
+                                                uint32_t &sectors)
 {
     words = 0;
+    sectors = 0;
     d = 0;
     if (t < A || (uint64_t)(t - A) + m > n) return false;
     const uint32_t s0 = t - A, w0 = s0 >> 4, sh = 2u * (s0 & 15u);
@@ -276,6 +279,7 @@ __device__ __forceinline__ bool bd_check_window(const uint32_t *__restrict__ tex
         }
     }
     words = Wn + 1;
+    sectors = ((w0 & 7u) * 4u + 4u * words + 31u) / 32u;
     d = tot;
     if (tot > k) return false;
     if (j == SCHEME_FREE) return true;
@@ -536,7 +540,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
     // budget: a warp left holding heavy trees hands them to the next round,
     // where every warp takes part, instead of working through them alone
     uint32_t budget = a.budget;
-    uint32_t c_seeds = 0, c_nodes = 0, c_blocks = 0, c_deep = 0, c_rounds = 0, c_verify = 0, c_vbytes = 0;
+    uint32_t c_seeds = 0, c_nodes = 0, c_blocks = 0, c_deep = 0, c_rounds = 0, c_verify = 0, c_vbytes = 0, c_vsect = 0;
     __syncwarp();
 
     for (uint32_t iter = 0;; iter++) {
@@ -835,12 +839,13 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
                 atomicAdd(&W.work[slot], 1u);
                 const uint32_t m = info & 511u, k = (info >> 9) & 3u;
                 const uint32_t t = __ldg(ix.sa_full + l);
-                uint32_t words = 0;
+                uint32_t words = 0, sectors = 0;
                 leaf = bd_check_window(ix.text, ix.n, W.pat[slot], m, W.bounds[slot], bm_j(meta), k, t, bm_a(meta),
-                                       dn, words);
+                                       dn, words, sectors);
                 if (leaf) row = __ldg(ix.isa + (t - bm_a(meta)));
                 c_verify++;
                 c_vbytes += 4u + 4u * words + (leaf ? 4u : 0u);
+                c_vsect += 1u + sectors + (leaf ? 1u : 0u);
             }
             uint32_t cl[4] = {row, 0, 0, 0}, cs[4] = {1, 0, 0, 0}, cd[4] = {dn, 0, 0, 0};
             bd_emit(a, leaf ? 1u : 0u, cl, cs, cd, leaf ? 1u : 0u, rid, (info >> 11) & 1u, lane);
@@ -951,6 +956,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
     if (lane == 0 && v) atomicAdd(&ctl->verified, v);
     v = c_vbytes; for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(BFULL, v, o);
     if (lane == 0 && v) atomicAdd(&ctl->verify_bytes, v);
+    v = c_vsect; for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(BFULL, v, o);
+    if (lane == 0 && v) atomicAdd(&ctl->verify_sectors, v);
     if (lane == 0) {
         atomicAdd(&ctl->rounds, (unsigned long long)c_rounds);
         if (c_deep) atomicAdd(&ctl->deep_moves, (unsigned long long)c_deep);
@@ -1285,6 +1292,7 @@ int run_search_bidir(const mica_index *idx, Workspace &w, mica_stats &st, const 
         st.overflow_moves = out.deep_moves;
         st.verified = out.verified;
         st.verify_bytes = out.verify_bytes;
+        st.verify_sectors = out.verify_sectors;
         st.spills = out.spills + out.fr_count;   // nodes exported to later rounds
         st.grid_ctas = (uint64_t)grid;
         w.bd_redo_seen = out.redo_reads > 0 || r > BD_GRAPH_ROUNDS;

@@ -258,10 +258,14 @@ static bool use_prefetch(const mica_index *idx)
 // addresses) is seen, then replayed with a single host synchronisation.  Any
 // overflow, error or read with more than 4096 listed hits sets done = false
 // and the caller runs the regular path, which recomputes the batch.
-static int align_graph(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd,
-                       const mica_align_params &p, cudaStream_t s, uint64_t *nh, bool &done)
+//
+// align_graph_launch queues the replay on s and returns (launched = false when
+// the batch cannot be captured); align_graph_finish waits for it and reads its
+// status.
+static int align_graph_launch(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd,
+                              const mica_align_params &p, cudaStream_t s, bool &launched)
 {
-    done = false;
+    launched = false;
     uint64_t n = rd.n;
     if (!w.pin_tmpl) {
         MICA_CUDA_TRY(cudaMallocHost(&w.pin_tmpl, 256));
@@ -321,6 +325,18 @@ static int align_graph(const mica_index *idx, Workspace &w, mica_stats &st, cons
     MICA_CUDA_TRY(cudaEventRecord(w.ev[0], s));
     MICA_CUDA_TRY(cudaGraphLaunch(w.gexec, s));
     MICA_CUDA_TRY(cudaEventRecord(w.ev[2], s));
+    w.g_grid = grid;
+    launched = true;
+    return 0;
+}
+
+static int align_graph_finish(Workspace &w, mica_stats &st, const ReadsView &rd, const mica_align_params &p,
+                              uint64_t *nh, bool &done)
+{
+    done = false;
+    const uint64_t n = rd.n;
+    const bool bidir = p.kernel == MICA_KERNEL_BIDIRECTIONAL;
+    const int grid = w.g_grid;
     MICA_CUDA_TRY(cudaEventSynchronize(w.ev[2]));
     SearchCtl out;
     memcpy(&out, w.pin_status, sizeof(out));
@@ -362,6 +378,7 @@ static int align_graph(const mica_index *idx, Workspace &w, mica_stats &st, cons
     st.overflow_moves = out.deep_moves;
     st.verified = out.verified;
     st.verify_bytes = out.verify_bytes;
+    st.verify_sectors = out.verify_sectors;
     st.grid_ctas = (uint64_t)grid;
     st.located = nhits;
     st.lf_steps = steps;
@@ -375,26 +392,56 @@ static int align_graph(const mica_index *idx, Workspace &w, mica_stats &st, cons
     return 0;
 }
 
-int align_on_device(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd,
-                    const mica_align_params &p_in, cudaStream_t s, uint64_t *nh, bool allow_graph)
+static int align_graph(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd,
+                       const mica_align_params &p, cudaStream_t s, uint64_t *nh, bool &done)
 {
-    // an index without the reversed genome's table runs the persistent kernel instead
+    done = false;
+    bool launched = false;
+    if (int rc = align_graph_launch(idx, w, st, rd, p, s, launched)) return rc;
+    return launched ? align_graph_finish(w, st, rd, p, nh, done) : 0;
+}
+
+// The kernel a call runs: an index without the reversed genome's table runs
+// the persistent kernel instead of the bidirectional one.
+static mica_align_params effective_params(const mica_index *idx, const mica_align_params &p_in)
+{
     mica_align_params p = p_in;
     if (p.kernel == MICA_KERNEL_BIDIRECTIONAL && !bidir_available(idx)) p.kernel = MICA_KERNEL_PERSISTENT;
+    return p;
+}
+
+static int create_events(Workspace &w)
+{
     for (auto &e : w.ev)
         if (!e) MICA_CUDA_TRY(cudaEventCreate(&e));
     for (auto &e : w.kev)
         if (!e) MICA_CUDA_TRY(cudaEventCreate(&e));
+    return 0;
+}
+
+// May the call run as a captured graph?  Best-stratum deepening has host
+// steps between its passes; a bidirectional batch that gave reads up needs
+// host steps after the kernel, so after one did, this workspace runs
+// bidirectional calls uncaptured.  (The budget that gives reads up is part of
+// the captured kernel's arguments.)
+static bool graph_eligible(const Workspace &w, const mica_align_params &p, const ReadsView &rd)
+{
+    const bool deepen = p.report == MICA_REPORT_BEST_STRATUM && p.kernel == MICA_KERNEL_PERSISTENT;
+    const bool graphable = p.kernel == MICA_KERNEL_PERSISTENT ||
+                           (p.kernel == MICA_KERNEL_BIDIRECTIONAL && !w.bd_redo_seen);
+    return !deepen && graphable && rd.n > 0;
+}
+
+int align_on_device(const mica_index *idx, Workspace &w, mica_stats &st, const ReadsView &rd,
+                    const mica_align_params &p_in, cudaStream_t s, uint64_t *nh, bool allow_graph)
+{
+    const mica_align_params p = effective_params(idx, p_in);
+    if (int rc = create_events(w)) return rc;
     uint64_t launches = st.launches;   // the batch check already counted
     st = mica_stats{};
     st.launches = launches;
     const bool deepen = p.report == MICA_REPORT_BEST_STRATUM && p.kernel == MICA_KERNEL_PERSISTENT && rd.n > 0;
-    // (the budget that gives reads up is part of the captured kernel's arguments)
-    // a bidirectional batch that gives reads up needs host steps after the
-    // kernel: after one did, this workspace runs bidirectional calls uncaptured
-    const bool graphable = p.kernel == MICA_KERNEL_PERSISTENT ||
-                           (p.kernel == MICA_KERNEL_BIDIRECTIONAL && !w.bd_redo_seen);
-    if (allow_graph && !deepen && graphable && rd.n > 0) {
+    if (allow_graph && graph_eligible(w, p, rd)) {
         bool done = false;
         if (int rc = align_graph(idx, w, st, rd, p, s, nh, done)) return rc;
         if (done) return 0;
@@ -674,6 +721,11 @@ void mica_index_free(mica_index *idx)
     dev_release(idx->isa);
     dev_release(idx->text);
     free_workspace(idx->ws);
+    for (PipeSlot &ps : idx->pipe) {
+        if (ps.stream) cudaStreamSynchronize(ps.stream);
+        free_workspace(ps.ws);
+        if (ps.stream) cudaStreamDestroy(ps.stream);
+    }
     delete idx;
 }
 
@@ -802,6 +854,65 @@ int validate_host_batch(const mica_index *idx, const uint64_t *off, const uint16
     return bad.load() ? MICA_EINVAL : 0;
 }
 
+// Defaults filled in and checked for a call with host buffers.
+int host_params(const mica_align_params *params, mica_align_params &p)
+{
+    mica_align_params_default(&p);
+    if (params) p = *params;
+    if (p.kernel < MICA_KERNEL_PERSISTENT || p.kernel > MICA_KERNEL_BIDIRECTIONAL) return MICA_EINVAL;
+    if (p.report > MICA_REPORT_BEST_STRATUM) return MICA_EINVAL;
+    return 0;
+}
+
+// Copy a batch from host memory into w's staging buffers on stream s; the
+// host threads check the batch while the copies run.  Nothing is launched
+// before the check passes, and a rejected batch waits for its copies so that
+// the caller may free the buffers on return.
+int stage_host_batch(const mica_index *idx, Workspace &w, const uint32_t *packed_reads, const uint64_t *word_offsets,
+                     const uint16_t *lengths, const uint8_t *k, uint64_t n_reads, cudaStream_t s, ReadsView &rd)
+{
+    const uint64_t nw = word_offsets[n_reads];
+    int rc;
+    if ((rc = dev_reserve(w.reads_words, std::max<uint64_t>(nw, 1) * 4)) ||
+        (rc = dev_reserve(w.reads_off, (n_reads + 1) * 8)) ||
+        (rc = dev_reserve(w.reads_len, std::max<uint64_t>(n_reads, 1) * 2)) ||
+        (rc = dev_reserve(w.reads_k, std::max<uint64_t>(n_reads, 1))))
+        return rc;
+    if (nw) MICA_CUDA_TRY(cudaMemcpyAsync(w.reads_words.p, packed_reads, nw * 4, cudaMemcpyHostToDevice, s));
+    MICA_CUDA_TRY(cudaMemcpyAsync(w.reads_off.p, word_offsets, (n_reads + 1) * 8, cudaMemcpyHostToDevice, s));
+    if (n_reads) {
+        MICA_CUDA_TRY(cudaMemcpyAsync(w.reads_len.p, lengths, n_reads * 2, cudaMemcpyHostToDevice, s));
+        MICA_CUDA_TRY(cudaMemcpyAsync(w.reads_k.p, k, n_reads, cudaMemcpyHostToDevice, s));
+    }
+    if ((rc = validate_host_batch(idx, word_offsets, lengths, k, n_reads))) {
+        cudaStreamSynchronize(s);
+        return rc;
+    }
+    rd = ReadsView{(const uint32_t *)w.reads_words.p, (const uint64_t *)w.reads_off.p,
+                   (const uint16_t *)w.reads_len.p, (const uint8_t *)w.reads_k.p, n_reads};
+    return 0;
+}
+
+// The result of the call just run on w (n reads, nh listed hits) copied into a
+// new host result on stream s.
+int copy_result(const Workspace &w, uint64_t n_reads, uint64_t nh, cudaStream_t s, mica_result **out)
+{
+    mica_result *r = result_new(n_reads, nh);
+    if (!r) return MICA_ENOMEM;
+    cudaError_t e = cudaSuccess;
+    if (n_reads) e = cudaMemcpyAsync(r->total, w.total.p, n_reads * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(r->offsets, w.hit_off.p, (n_reads + 1) * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && nh) e = cudaMemcpyAsync(r->hits, w.hits.p, nh * sizeof(mica_hit), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e, "result copy", __FILE__, __LINE__);
+        mica_result_free(r);
+        return MICA_ECUDA;
+    }
+    *out = r;
+    return 0;
+}
+
 }  // namespace mica
 
 extern "C" {
@@ -842,52 +953,85 @@ int mica_align_batch(mica_index *idx, const uint32_t *packed_reads, const uint64
     *out = nullptr;
     if (n_reads >= (1ull << 31)) return MICA_EINVAL;
     mica_align_params p;
-    mica_align_params_default(&p);
-    if (params) p = *params;
-    if (p.kernel < MICA_KERNEL_PERSISTENT || p.kernel > MICA_KERNEL_BIDIRECTIONAL) return MICA_EINVAL;
-    if (p.report > MICA_REPORT_BEST_STRATUM) return MICA_EINVAL;
+    if (int rc = host_params(params, p)) return rc;
     DeviceGuard g(idx->device);
     MICA_CUDA_TRY(cudaSetDevice(idx->device));
     cudaStream_t s = (cudaStream_t)p.cuda_stream;
     Workspace &w = idx->ws;
-    uint64_t nw = word_offsets[n_reads];
+    ReadsView rd;
     int rc;
-    if ((rc = dev_reserve(w.reads_words, std::max<uint64_t>(nw, 1) * 4)) ||
-        (rc = dev_reserve(w.reads_off, (n_reads + 1) * 8)) ||
-        (rc = dev_reserve(w.reads_len, std::max<uint64_t>(n_reads, 1) * 2)) ||
-        (rc = dev_reserve(w.reads_k, std::max<uint64_t>(n_reads, 1))))
-        return rc;
-    if (nw) MICA_CUDA_TRY(cudaMemcpyAsync(w.reads_words.p, packed_reads, nw * 4, cudaMemcpyHostToDevice, s));
-    MICA_CUDA_TRY(cudaMemcpyAsync(w.reads_off.p, word_offsets, (n_reads + 1) * 8, cudaMemcpyHostToDevice, s));
-    if (n_reads) {
-        MICA_CUDA_TRY(cudaMemcpyAsync(w.reads_len.p, lengths, n_reads * 2, cudaMemcpyHostToDevice, s));
-        MICA_CUDA_TRY(cudaMemcpyAsync(w.reads_k.p, k, n_reads, cudaMemcpyHostToDevice, s));
-    }
-    // the host threads check the batch while the copies run; nothing is launched before they pass,
-    // and a rejected batch waits for its copies so that the caller may free the buffers on return
-    if ((rc = validate_host_batch(idx, word_offsets, lengths, k, n_reads))) {
-        cudaStreamSynchronize(s);
-        return rc;
-    }
-    ReadsView rd{(const uint32_t *)w.reads_words.p, (const uint64_t *)w.reads_off.p,
-                 (const uint16_t *)w.reads_len.p, (const uint8_t *)w.reads_k.p, n_reads};
+    if ((rc = stage_host_batch(idx, w, packed_reads, word_offsets, lengths, k, n_reads, s, rd))) return rc;
     idx->stats.launches = 0;
     uint64_t nh = 0;
     if ((rc = align_on_device(idx, idx->ws, idx->stats, rd, p, s, &nh))) return rc;
-    mica_result *r = result_new(n_reads, nh);
-    if (!r) return MICA_ENOMEM;
-    cudaError_t e = cudaSuccess;
-    if (n_reads) e = cudaMemcpyAsync(r->total, w.total.p, n_reads * 8, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(r->offsets, w.hit_off.p, (n_reads + 1) * 8, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && nh) e = cudaMemcpyAsync(r->hits, w.hits.p, nh * sizeof(mica_hit), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) {
-        set_last_cuda_error(e, "result copy", __FILE__, __LINE__);
-        mica_result_free(r);
-        return MICA_ECUDA;
+    return copy_result(w, n_reads, nh, s, out);
+}
+
+// ---- pipelined host batches: two slots, each with its own stream and workspace ----
+
+int mica_align_submit(mica_index *idx, const uint32_t *packed_reads, const uint64_t *word_offsets,
+                      const uint16_t *lengths, const uint8_t *k, uint64_t n_reads,
+                      const mica_align_params *params, uint64_t *ticket)
+{
+    if (!idx || !ticket || !word_offsets || (n_reads && (!packed_reads || !lengths || !k))) return MICA_EINVAL;
+    *ticket = 0;
+    if (n_reads >= (1ull << 31)) return MICA_EINVAL;
+    mica_align_params p;
+    if (int rc = host_params(params, p)) return rc;
+    PipeSlot *slot = nullptr;
+    for (PipeSlot &ps : idx->pipe)
+        if (!ps.busy) { slot = &ps; break; }
+    if (!slot) return MICA_EBUSY;
+    DeviceGuard g(idx->device);
+    MICA_CUDA_TRY(cudaSetDevice(idx->device));
+    if (!slot->stream) MICA_CUDA_TRY(cudaStreamCreateWithFlags(&slot->stream, cudaStreamNonBlocking));
+    Workspace &w = slot->ws;
+    ReadsView rd;
+    int rc;
+    if ((rc = stage_host_batch(idx, w, packed_reads, word_offsets, lengths, k, n_reads, slot->stream, rd))) return rc;
+    p = effective_params(idx, p);
+    slot->st = mica_stats{};
+    slot->launched = false;
+    if (graph_eligible(w, p, rd)) {
+        if ((rc = create_events(w))) return rc;
+        if ((rc = align_graph_launch(idx, w, slot->st, rd, p, slot->stream, slot->launched))) return rc;
     }
-    *out = r;
+    slot->busy = true;
+    slot->p = p;
+    slot->n_reads = n_reads;
+    slot->ticket = *ticket = ++idx->next_ticket;
     return 0;
+}
+
+int mica_align_collect(mica_index *idx, uint64_t ticket, mica_result **out)
+{
+    if (!idx || !out) return MICA_EINVAL;
+    *out = nullptr;
+    PipeSlot *slot = nullptr;
+    for (PipeSlot &ps : idx->pipe)
+        if (ps.busy && ps.ticket == ticket) { slot = &ps; break; }
+    if (!slot) return MICA_ENOTFOUND;
+    DeviceGuard g(idx->device);
+    MICA_CUDA_TRY(cudaSetDevice(idx->device));
+    Workspace &w = slot->ws;
+    const uint64_t n = slot->n_reads;
+    ReadsView rd{(const uint32_t *)w.reads_words.p, (const uint64_t *)w.reads_off.p,
+                 (const uint16_t *)w.reads_len.p, (const uint8_t *)w.reads_k.p, n};
+    uint64_t nh = 0;
+    bool done = false;
+    int rc = 0;
+    if (slot->launched) rc = align_graph_finish(w, slot->st, rd, slot->p, &nh, done);
+    if (!rc && !done) {
+        // not captured, or the replay needs the regular path: run it now
+        rc = align_on_device(idx, w, slot->st, rd, slot->p, slot->stream, &nh, false);
+        if (slot->launched) slot->st.graph_fallbacks++;
+    }
+    if (!rc) rc = copy_result(w, n, nh, slot->stream, out);
+    else cudaStreamSynchronize(slot->stream);
+    idx->stats = slot->st;
+    slot->busy = false;
+    slot->launched = false;
+    return rc;
 }
 
 void mica_result_free(mica_result *res)

@@ -144,6 +144,7 @@ struct SearchCtl {
     unsigned int fr_count;                            // bidirectional search: nodes exported this round
     unsigned long long verified, verify_bytes;        // bidirectional search: one-row intervals checked
                                                       //   against the text, and the bytes that read
+    unsigned long long verify_sectors;                // ... and the 32-byte sectors those reads touch
 };
 
 constexpr unsigned ERR_IV_OVERFLOW = 1u;
@@ -199,6 +200,19 @@ struct Workspace {
     uint64_t gkey[GRAPH_KEY] = {};
     uint64_t hit_capacity = 0;
     uint64_t glaunches = 0;   // kernels in the captured graph
+    int g_grid = 0;           // grid of the launched replay's search kernel
+};
+
+// One of an index's two slots for pipelined host batches
+// (mica_align_submit / mica_align_collect).
+struct PipeSlot {
+    Workspace ws;
+    cudaStream_t stream = nullptr;
+    bool busy = false;       // submitted and not yet collected
+    bool launched = false;   // its captured replay is queued (else collect runs the search)
+    uint64_t ticket = 0, n_reads = 0;
+    mica_align_params p{};
+    mica_stats st{};
 };
 
 }  // namespace mica
@@ -219,6 +233,8 @@ struct mica_index {
     mica_stats stats{};
     mica_tuning tuning{-1, 0, 0, {0, 0, 0, 0}, -1, 0, 0};
     uint32_t idle_limit = 0, spin_limit = 0;   // persistent kernel wait bounds; 0 = built-in defaults
+    mica::PipeSlot pipe[2];                    // pipelined host batches
+    uint64_t next_ticket = 0;
 };
 
 namespace mica {

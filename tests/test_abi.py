@@ -73,14 +73,19 @@ def test_host_side_rejections_need_no_gpu():
     # pairing rejects an inverted insert window before touching a device
     assert lib.mica_pair_batch(0, None, None, None, 1, 700, 300, None) == mica.MICA_EINVAL
     assert lib.mica_pair_device(None, None, None, 1, 700, 300, None, None) == mica.MICA_EINVAL
+    # pipelined batches: arguments checked before any device call
+    t = ctypes.c_uint64()
+    assert lib.mica_align_submit(None, None, None, None, None, 0, None, ctypes.byref(t)) == mica.MICA_EINVAL
+    assert lib.mica_align_collect(None, 1, ctypes.byref(ctypes.c_void_p())) == mica.MICA_EINVAL
     # the binding checks the host arrays' sizes before the library reads them
     idx = object.__new__(mica.Index)                  # no index: the check comes first
     words, off = np.zeros(4, np.uint32), np.array([0, 4], np.uint64)
     ln, kk = np.array([64], np.uint16), np.array([2], np.uint8)
     for args in ((words[:3], off, ln, kk), (words, off[:1], ln, kk), (words, off, ln, kk[:0])):
-        with pytest.raises(mica.MicaError) as e:
-            idx.align(*args)
-        assert e.value.code == mica.MICA_EINVAL
+        for call in (idx.align, idx.submit):
+            with pytest.raises(mica.MicaError) as e:
+                call(*args)
+            assert e.value.code == mica.MICA_EINVAL
     # defaults: pruning on, every placement reported
     p = mica.AlignParams()
     lib.mica_align_params_default(ctypes.byref(p))

@@ -215,10 +215,55 @@ def test_uneven_64m_100k_reads_equal_oracle():
     assert int(want.total.max()) > 1000 and np.count_nonzero(b.k == 3) > 20_000
 
 
+def test_pipelined_submit_and_collect():
+    """Pipelined host batches: two slots in flight, results equal to the
+    one-call path and the oracle, collected in either order; a third submit
+    is refused (MICA_EBUSY) and a collected ticket is unknown (MICA_ENOTFOUND);
+    a bad batch is refused at submit without taking a slot; the persistent
+    and plain kernels and best-stratum reporting go through the same slots."""
+    m = gc.mica()
+    g = gc.genome("64m")
+    fm = gc.oracle_index("64m")
+    idx = gc.gpu_index("64m")
+    u = synth.reads_uneven(g, n=200_000)
+    parts = [u.subset(np.arange(i, 200_000, 400)) for i in range(4)]          # 4 x 500 reads
+    want = [fm.align(b, cap=1000) for b in parts]
+    t0 = idx.submit_batch(parts[0])
+    t1 = idx.submit_batch(parts[1])
+    with pytest.raises(m.MicaError) as e:
+        idx.submit_batch(parts[2])
+    assert e.value.code == m.MICA_EBUSY
+    gc.assert_same(idx.collect(t1), want[1], "second collected first")
+    t2 = idx.submit_batch(parts[2])
+    gc.assert_same(idx.collect(t0), want[0], "first")
+    with pytest.raises(m.MicaError) as e:
+        idx.collect(t0)
+    assert e.value.code == m.MICA_ENOTFOUND
+    bad = parts[3]
+    with pytest.raises(m.MicaError) as e:
+        idx.submit(bad.words, bad.word_off, np.full(bad.n, 300, np.uint16), bad.k)
+    assert e.value.code == m.MICA_EINVAL
+    t3 = idx.submit_batch(parts[3])
+    gc.assert_same(idx.collect(t2), want[2], "third")
+    gc.assert_same(idx.collect(t3), want[3], "fourth")
+    # a steady stream, as the benchmark runs it: submit the next, collect the previous
+    prev = None
+    for r in range(6):
+        t = idx.submit_batch(parts[r % 4], kernel=("bidirectional", "persistent", "plain")[r % 3])
+        if prev is not None:
+            gc.assert_same(idx.collect(prev[0]), want[prev[1]], f"stream {r}")
+        prev = (t, r % 4)
+    gc.assert_same(idx.collect(prev[0]), want[prev[1]], "stream end")
+    tb = idx.submit_batch(parts[0], kernel="persistent", report="best_stratum")
+    gc.assert_same(idx.collect(tb), fm.align_best_stratum(parts[0], cap=1000), "best stratum")
+    assert idx.stats()["tasks"] == 2 * parts[0].n
+
+
 def test_bidirectional_text_check_settings():
     """One-row intervals checked against the text (the whole suffix array,
-    its inverse and the 2-bit text resident): with the check after 1, 8 or the
-    default 20 matched bases, with it off (256), and on an index without the
+    its inverse and the 2-bit text resident): with the check after 1, 24 or the
+    default 12 matched bases (24: the one-row node first takes base-by-base
+    steps past the 12-base seed), with it off (256), and on an index without the
     arrays, every result equals the oracle, on the uneven 64 Mbp sample
     (k 0..3, lengths 50..250, reads inside planted repeats) and on diverged
     (AC)^n reads, with and without a cap and with small node budgets."""
@@ -227,7 +272,7 @@ def test_bidirectional_text_check_settings():
     want = gc.oracle_index("64m").align(b, cap=1000)
     idx = gc.gpu_index("64m")
     try:
-        for verify in (1, 8, 0, 256):
+        for verify in (1, 24, 0, 256):
             for budget in (0, 16):
                 idx.set_tuning(bidir_verify=verify, bidir_budget=budget)
                 got = idx.align_batch(b, hit_cap=1000, kernel="bidirectional")
