@@ -186,6 +186,10 @@ typedef struct {
     uint64_t rev_table_bytes; /* the reversed genome's q-mer table (bidirectional search; 0 without it) */
     uint32_t full_sa;        /* 1 if the whole suffix array, its inverse and the 2-bit text are resident */
     uint64_t full_sa_bytes;  /* their size (0 without them) */
+    uint32_t long_q;         /* q of the longer seed tables of G$ and G~$ the bidirectional search
+                                seeds from (built from the text with full_sa when log4 N + 1 exceeds
+                                kmer_q; at most 15); 0 without them */
+    uint64_t long_table_bytes; /* their size, both directions (0 without them) */
 } mica_index_info;
 
 const char *mica_strerror(int code);
@@ -740,6 +744,14 @@ int mica_debug_full_sa(const mica_index *idx, uint32_t which, uint64_t first, ui
    (host in/out; l == r when the len-mer does not occur). */
 int mica_debug_seed_interval(const mica_index *idx, const uint32_t *codes, uint32_t len, uint64_t n,
                              uint32_t *lr_out);
+
+/* The same from one of the index's seed tables: which = 0 the q-mer table of
+   G$, 1 that of the reversed genome G~$ (intervals of the reversed string's
+   rows), 2 and 3 the longer seed tables of G$ and G~$ (mica_index_info
+   long_q; built with full_sa); len <= that table's q.  MICA_EINVAL for a
+   table the index does not have. */
+int mica_debug_table_interval(const mica_index *idx, uint32_t which, const uint32_t *codes, uint32_t len,
+                              uint64_t n, uint32_t *lr_out);
 
 /* Mismatch lower bounds of every (read, strand) task as the pruned search
    computes them (host in/out; the index must have lower_bounds).  Task

@@ -111,7 +111,8 @@ class IndexInfo(ctypes.Structure):
                 ("sample_bytes", ctypes.c_uint64), ("table_bytes", ctypes.c_uint64), ("device", ctypes.c_int32),
                 ("lower_bounds", ctypes.c_uint32), ("rev_occ_bytes", ctypes.c_uint64),
                 ("rev_table_bytes", ctypes.c_uint64), ("full_sa", ctypes.c_uint32),
-                ("full_sa_bytes", ctypes.c_uint64)]
+                ("full_sa_bytes", ctypes.c_uint64), ("long_q", ctypes.c_uint32),
+                ("long_table_bytes", ctypes.c_uint64)]
 
 
 # exported symbol -> (restype, argtypes); the C ABI's full surface
@@ -137,6 +138,7 @@ SIGNATURES = {
     "mica_debug_occ": (_i32, [P, P, _u64, P]),
     "mica_debug_locate": (_i32, [P, P, _u64, P]),
     "mica_debug_full_sa": (_i32, [P, ctypes.c_uint32, _u64, _u64, P]),
+    "mica_debug_table_interval": (_i32, [P, ctypes.c_uint32, P, ctypes.c_uint32, _u64, P]),
     "mica_debug_seed_interval": (_i32, [P, P, _u32, _u64, P]),
     "mica_tuning_shapes": (_i32, []),
     "mica_tuning_shape_info": (_i32, [_i32, P, P, P]),
@@ -510,6 +512,16 @@ class Index:
         _check(_lib.mica_debug_lower_bounds(self._h, _ptr(words) if words.size else None, _ptr(off),
                                             _ptr(lens) if lens.size else None, _ptr(k) if k.size else None,
                                             lens.size, _ptr(out) if out.size else None), "mica_debug_lower_bounds")
+        return out
+
+    def debug_table_interval(self, which: str, codes, length: int) -> np.ndarray:
+        """[l, r) of each length-mer code from one seed table: "fwd", "rev" (the
+        q-mer tables of G$ and G~$), "long_fwd", "long_rev" (the longer ones)."""
+        w = {"fwd": 0, "rev": 1, "long_fwd": 2, "long_rev": 3}[which]
+        codes = np.ascontiguousarray(codes, dtype=np.uint32)
+        out = np.empty((codes.size, 2), dtype=np.uint32)
+        _check(_lib.mica_debug_table_interval(self._h, w, _ptr(codes) if codes.size else None, length, codes.size,
+                                              _ptr(out) if codes.size else None), "mica_debug_table_interval")
         return out
 
     def debug_seed_interval(self, codes, length: int) -> np.ndarray:

@@ -689,8 +689,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
         }
         c_rounds++;
 
-        // (a single-row round moves at most 32 nodes to the text-check stack
-        // and runs only while it holds fewer than 32: it never holds 64)
+        // (a single-row or seed round moves at most 32 nodes to the text-check
+        // stack and runs only while it holds fewer than 32: it never holds 64)
         int kind;
         const bool seed_room = mc + 32 <= (uint32_t)SCAP && sc + 32 <= (uint32_t)SCAP;
         if (vtop >= 32) kind = 3;
@@ -717,18 +717,28 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
                     meta = bd_meta((uint32_t)lane, m, m, 0, 0, SCHEME_FREE);
                     push = true;
                 } else {
+                    // from the longer seed tables when the index has them
+                    const bool longer = ix.lfwd.table != nullptr;
+                    const uint32_t tq = longer ? ix.lfwd.q : ix.q;
                     const uint32_t bj = bound_at(W.bounds[lane], j + 1), aj = bound_at(W.bounds[lane], j);
-                    const uint32_t qe = min(ix.q, bj - aj);
+                    const uint32_t qe = min(tq, bj - aj);
                     uint32_t code = 0, rcode = 0;
                     for (uint32_t t = 0; t < qe; t++) {
                         code = (code << 2) | pat_base(pat, bj - qe + t);
                         rcode = (rcode << 2) | pat_base(pat, bj - 1 - t);
                     }
                     uint32_t fl, fr, rl, rr;
-                    seed_interval_in(ix.table, ix.q, ix.nshort, ix.short_pad, ix.short_len, ix.short_bloom, code, qe,
-                                     fl, fr);
-                    seed_interval_in(ix.rev.table, ix.q, ix.rev.nshort, ix.rev.short_pad, ix.rev.short_len,
-                                     ix.rev.short_bloom, rcode, qe, rl, rr);
+                    if (longer) {
+                        seed_interval_in(ix.lfwd.table, tq, ix.lfwd.nshort, ix.lfwd.short_pad, ix.lfwd.short_len,
+                                         ix.lfwd.short_bloom, code, qe, fl, fr);
+                        seed_interval_in(ix.lrev.table, tq, ix.lrev.nshort, ix.lrev.short_pad, ix.lrev.short_len,
+                                         ix.lrev.short_bloom, rcode, qe, rl, rr);
+                    } else {
+                        seed_interval_in(ix.table, ix.q, ix.nshort, ix.short_pad, ix.short_len, ix.short_bloom, code,
+                                         qe, fl, fr);
+                        seed_interval_in(ix.rev.table, ix.q, ix.rev.nshort, ix.rev.short_pad, ix.rev.short_len,
+                                         ix.rev.short_bloom, rcode, qe, rl, rr);
+                    }
                     c_seeds++;
                     if (fl < fr) {
                         l = fl; lr = rl; sz = fr - fl;
@@ -742,17 +752,28 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
             uint32_t cl[4] = {l, 0, 0, 0}, cs[4] = {sz, 0, 0, 0}, cd[4] = {0, 0, 0, 0};
             bd_emit(a, leaf ? 1u : 0u, cl, cs, cd, leaf ? 1u : 0u, s_read, minus, lane);
             const bool single = sz == 1;
-            const unsigned bm = __ballot_sync(BFULL, push && !single), bs = __ballot_sync(BFULL, push && single);
+            // a one-row seed far enough in goes straight to the text check (at
+            // most 32 more: this round runs only while that stack holds fewer than 32)
+            const uint32_t matched = bm_b(meta) - bm_a(meta);
+            const bool to_v = push && single && a.verify_min && matched >= a.verify_min &&
+                              (s_info & 511u) - matched >= BD_VERIFY_LEFT;
+            const unsigned bm = __ballot_sync(BFULL, push && !single),
+                           bs = __ballot_sync(BFULL, push && single && !to_v), bv = __ballot_sync(BFULL, to_v);
             if (push && !single) {
                 uint32_t q = (mtop + __popc(bm & lt)) & (SCAP - 1);
                 W.ml[q] = l; W.mlr[q] = lr; W.msz[q] = sz; W.mm[q] = meta;
             }
-            if (push && single) {
+            if (push && single && !to_v) {
                 uint32_t q = (stop + __popc(bs & lt)) & (SCAP - 1);
                 W.sl[q] = l; W.slr[q] = lr; W.sm[q] = meta;
             }
+            if (to_v) {
+                const uint32_t q = vtop + __popc(bv & lt);
+                W.vl[q] = l; W.vlr[q] = lr; W.vm[q] = meta;
+            }
             mtop += __popc(bm);
             stop += __popc(bs);
+            vtop += __popc(bv);
             if (push) atomicAdd(&W.live[lane], 1);
         } else if (kind == 1) {
             // ---- single-row nodes: the one possible child is the row's symbol

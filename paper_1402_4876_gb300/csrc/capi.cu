@@ -697,6 +697,7 @@ int mica_index_load(const char *path, int device, mica_index **out)
         rc = upload_variants(idx);
         if (!rc && (h.flags & 1u)) rc = rebuild_full_sa(idx, 0);
         set_full_sa_view(idx);
+        if (!rc) rc = build_long_tables(idx, nullptr, 0);
     }
     if (rc) { mica_index_free(idx); return rc; }
     *out = idx;
@@ -720,6 +721,8 @@ void mica_index_free(mica_index *idx)
     dev_release(idx->sa_full);
     dev_release(idx->isa);
     dev_release(idx->text);
+    dev_release(idx->ltable);
+    dev_release(idx->lrtable);
     free_workspace(idx->ws);
     for (PipeSlot &ps : idx->pipe) {
         if (ps.stream) cudaStreamSynchronize(ps.stream);
@@ -748,6 +751,8 @@ int mica_index_get_info(const mica_index *idx, mica_index_info *info)
     info->rev_table_bytes = idx->view.rev.table ? idx->table_len * 4 : 0;
     info->full_sa = idx->has_full_sa ? 1u : 0u;
     info->full_sa_bytes = idx->has_full_sa ? full_sa_bytes(idx->n) : 0;
+    info->long_q = idx->view.lfwd.table ? idx->view.lfwd.q : 0;
+    info->long_table_bytes = idx->view.lfwd.table ? 2 * (((1ull << (2 * idx->view.lfwd.q)) + 1) * 4) : 0;
     return 0;
 }
 

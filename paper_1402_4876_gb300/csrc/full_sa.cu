@@ -15,6 +15,11 @@
 // LF(j) = C[c] + Occ(c, j) with c = BWT[j] = G[SA[j] - 1] gives
 // SA[LF(j)] = SA[j] - 1): from each row whose SA value is a multiple of s,
 // LF steps recover the s - 1 positions below it, their rows and the symbols.
+//
+// The text also gives the bidirectional seeds longer q-mer tables (of G$ and
+// of G~$, q about log4 N + 1, at most 15): a seed of that length is mostly a
+// single occurrence already, so the search goes from the table lookup to the
+// text check without the interval extensions in between.
 #include <algorithm>
 
 #include "search_common.cuh"
@@ -106,7 +111,78 @@ __global__ void k_invert_bwt(const IndexView ix, uint64_t n_mark_blocks, uint64_
     }
 }
 
+__global__ void k_unpack_text(const uint32_t *__restrict__ text, uint64_t n, int reverse, uint8_t *__restrict__ codes)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t p = reverse ? n - 1 - i : i;
+        codes[i] = (uint8_t)((text[p >> 4] >> (2 * (p & 15))) & 3u);
+    }
+}
+
+__global__ void k_reverse_bytes(const uint8_t *__restrict__ in, uint64_t n, uint8_t *__restrict__ out)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = in[n - 1 - i];
+}
+
+void set_qmer_view(QmerView &v, const DevBuf &table, uint32_t q, const QmerShort &sh)
+{
+    v = QmerView{};
+    v.table = (const uint32_t *)table.p;
+    v.q = q;
+    v.nshort = sh.nshort;
+    v.short_bloom = sh.bloom;
+    for (uint32_t t = 0; t < MAX_LQ; t++) {
+        v.short_pad[t] = sh.pad[t];
+        v.short_len[t] = sh.len[t];
+    }
+}
+
+__global__ void k_table_interval(const QmerView t, const uint32_t *__restrict__ codes, uint32_t len, uint64_t n,
+                                 uint32_t *__restrict__ out)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t l, r;
+        seed_interval_in(t.table, t.q, t.nshort, t.short_pad, t.short_len, t.short_bloom, codes[i], len, l, r);
+        out[2 * i] = l;
+        out[2 * i + 1] = r;
+    }
+}
+
 }  // namespace
+
+uint32_t long_seed_q(uint64_t n, uint32_t q)
+{
+    uint32_t l = 0;
+    while (l < 16 && (1ull << (2 * l)) < n + 1) l++;   // ceil(log4(n + 1))
+    return std::min(MAX_LQ, std::max(q, l + 1));
+}
+
+int build_long_tables(mica_index *idx, const uint8_t *d_codes, cudaStream_t s)
+{
+    idx->view.lfwd = QmerView{};
+    idx->view.lrev = QmerView{};
+    const uint64_t n = idx->n;
+    const uint32_t lq = long_seed_q(n, idx->params.kmer_q);
+    if (!idx->has_full_sa || !idx->has_rev || lq <= idx->params.kmer_q || n == 0) return 0;
+    DevBuf own, rcodes, tmp;
+    auto cleanup = [&]() { dev_release(own); dev_release(rcodes); dev_release(tmp); };
+    int rc;
+    if (!d_codes) {
+        if ((rc = dev_reserve(own, n))) return rc;
+        k_unpack_text<<<grid_of(n), 256, 0, s>>>((const uint32_t *)idx->text.p, n, 0, (uint8_t *)own.p);
+        d_codes = (const uint8_t *)own.p;
+    }
+    QmerShort fsh, rsh;
+    if ((rc = build_qmer_table(d_codes, n, lq, idx->ltable, fsh, tmp, s))) { cleanup(); return rc; }
+    if ((rc = dev_reserve(rcodes, n))) { cleanup(); return rc; }
+    k_reverse_bytes<<<grid_of(n), 256, 0, s>>>(d_codes, n, (uint8_t *)rcodes.p);
+    if ((rc = build_qmer_table((const uint8_t *)rcodes.p, n, lq, idx->lrtable, rsh, tmp, s))) { cleanup(); return rc; }
+    cleanup();
+    set_qmer_view(idx->view.lfwd, idx->ltable, lq, fsh);
+    set_qmer_view(idx->view.lrev, idx->lrtable, lq, rsh);
+    return 0;
+}
 
 uint64_t full_sa_text_words(uint64_t n) { return ((n + 15) / 16 + 4 + 3) & ~3ull; }
 
@@ -169,6 +245,44 @@ int rebuild_full_sa(mica_index *idx, cudaStream_t s)
 }  // namespace mica
 
 using namespace mica;
+
+extern "C" int mica_debug_table_interval(const mica_index *idx, uint32_t which, const uint32_t *codes, uint32_t len,
+                                         uint64_t n, uint32_t *lr_out)
+{
+    if (!idx || which > 3 || (n && (!codes || !lr_out))) return MICA_EINVAL;
+    QmerView t{};
+    const IndexView &v = idx->view;
+    if (which < 2) {
+        t.table = which == 0 ? v.table : v.rev.table;
+        t.q = v.q;
+        t.nshort = which == 0 ? v.nshort : v.rev.nshort;
+        t.short_bloom = which == 0 ? v.short_bloom : v.rev.short_bloom;
+        for (uint32_t i = 0; i < MAX_Q; i++) {
+            t.short_pad[i] = which == 0 ? v.short_pad[i] : v.rev.short_pad[i];
+            t.short_len[i] = which == 0 ? v.short_len[i] : v.rev.short_len[i];
+        }
+    } else {
+        t = which == 2 ? v.lfwd : v.lrev;
+    }
+    if (!t.table || len < 1 || len > t.q) return MICA_EINVAL;
+    for (uint64_t i = 0; i < n; i++)
+        if ((uint64_t)codes[i] >= (1ull << (2 * len))) return MICA_EINVAL;
+    if (n == 0) return 0;
+    DeviceGuard g(idx->device);
+    MICA_CUDA_TRY(cudaSetDevice(idx->device));
+    DevBuf dc, dout;
+    int rc = dev_reserve(dc, n * 4);
+    if (!rc) rc = dev_reserve(dout, n * 8);
+    if (!rc && cudaMemcpy(dc.p, codes, n * 4, cudaMemcpyHostToDevice) != cudaSuccess) rc = MICA_ECUDA;
+    if (!rc) {
+        k_table_interval<<<grid_of(n), 256>>>(t, (const uint32_t *)dc.p, len, n, (uint32_t *)dout.p);
+        if (cudaGetLastError() != cudaSuccess) rc = MICA_ECUDA;
+    }
+    if (!rc && cudaMemcpy(lr_out, dout.p, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess) rc = MICA_ECUDA;
+    dev_release(dc);
+    dev_release(dout);
+    return rc;
+}
 
 extern "C" int mica_debug_full_sa(const mica_index *idx, uint32_t which, uint64_t first, uint64_t n, uint32_t *out)
 {

@@ -564,6 +564,7 @@ int build_index_from_codes(const uint8_t *d_codes, uint64_t n, const mica_index_
     v.q = p.kmer_q;
     v.sa_sample = p.sa_sample;
     set_full_sa_view(idx);
+    if (int rc2 = build_long_tables(idx, d_codes, s)) return rc2;
     return upload_variants(idx);
 }
 

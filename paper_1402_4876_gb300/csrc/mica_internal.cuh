@@ -28,6 +28,17 @@ constexpr uint32_t SB_BLOCKS = 682;
 // words of mark bits (480 rows).
 constexpr uint32_t MARK_ROWS = 480;
 constexpr uint32_t MAX_Q = 12;
+constexpr uint32_t MAX_LQ = 15;   // longest q-mer of the bidirectional seed tables
+
+// A q-mer table of bounds (4^q + 1 uint32: entry x = suffixes smaller than
+// the q-mer x) with the short-suffix corrections that make its bounds exact.
+struct QmerView {
+    const uint32_t *table;
+    uint32_t q, nshort;
+    uint32_t short_pad[MAX_LQ];
+    uint32_t short_len[MAX_LQ];
+    unsigned long long short_bloom;
+};
 constexpr uint32_t MAX_WORDS = MICA_MAX_READ_LEN / 16;   // packed words per read
 
 // Seed variants: for budget k, every way to substitute <= k of the last q
@@ -84,6 +95,9 @@ struct IndexView {
     const uint32_t *sa_full;
     const uint32_t *isa;
     const uint32_t *text;
+    // Seed tables of a longer q (built from the text with full_sa, for the
+    // bidirectional kernel's seeds) of G$ and of G~$; table null when absent.
+    QmerView lfwd, lrev;
 };
 
 // Read batch in device memory.
@@ -227,6 +241,7 @@ struct mica_index {
     mica::DevBuf rocc, rsuper;   // reversed genome's occurrence blocks (lower bounds, bidirectional search)
     mica::DevBuf rtable;         // reversed genome's q-mer table (bidirectional search)
     mica::DevBuf sa_full, isa, text;   // whole suffix array, its inverse, 2-bit text (full_sa)
+    mica::DevBuf ltable, lrtable;      // longer seed tables of G$ and G~$ (with full_sa)
     bool has_rev = false;
     bool has_full_sa = false;
     mica::Workspace ws;
@@ -283,12 +298,16 @@ uint64_t full_sa_bytes(uint64_t n);
 void set_full_sa_view(mica_index *idx);
 int build_full_sa(mica_index *idx, DevBuf &sa, const uint8_t *d_codes, uint64_t n, cudaStream_t s);
 int rebuild_full_sa(mica_index *idx, cudaStream_t s);
+uint32_t long_seed_q(uint64_t n, uint32_t q);   // q of the longer seed tables (== q: none)
+// the longer seed tables from the genome's codes (or, when d_codes is null,
+// from the resident text)
+int build_long_tables(mica_index *idx, const uint8_t *d_codes, cudaStream_t s);
 
 int build_index_from_codes(const uint8_t *d_codes, uint64_t n, const mica_index_params &p,
                            mica_index *idx, cudaStream_t s);
 int upload_variants(mica_index *idx);
 struct QmerShort {
-    uint32_t nshort = 0, pad[MAX_Q] = {}, len[MAX_Q] = {};
+    uint32_t nshort = 0, pad[MAX_LQ] = {}, len[MAX_LQ] = {};
     unsigned long long bloom = 0;
 };
 int build_qmer_table(const uint8_t *d_codes, uint64_t n, uint32_t q, DevBuf &table, QmerShort &sh, DevBuf &tmp,

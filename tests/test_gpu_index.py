@@ -165,6 +165,53 @@ def test_full_sa_64m_and_without(tmp_path):
     idx3.free()
 
 
+def test_longer_seed_tables_are_sa_intervals(tmp_path):
+    """The longer seed tables (q = ceil(log4(N + 1)) + 1 = 13 for 5 Mbp) of
+    G$ and of G~$, built from the text at build time and again at load: every
+    length <= 13, including the codes of the genome's last bases (short
+    suffixes), gives the exact interval of backward search in the genome's
+    and the reversed genome's index; the q-mer tables answer the same."""
+    g = synth.repeat_genome(5_000_000, 7, copy_frac=0.1, copy_len=(500, 5000), tandem_frac=0.02).codes
+    m = gc.mica()
+    idx = m.Index.build(synth.to_acgt_bytes(g), kmer_q=12, sa_sample=16)
+    info = idx.info()
+    assert info["long_q"] == 13 and info["long_table_bytes"] == 2 * ((4 ** 13) + 1) * 4
+    fm, rfm = oracle.FMIndex(g, "sais"), oracle.FMIndex(g[::-1].copy(), "sais")
+    path = str(tmp_path / "idx5m.mica")
+    idx.save(path)
+    idx2 = m.Index.load(path)
+    assert idx2.info() == info
+    rng = np.random.default_rng(13)
+    for length in (1, 6, 12, 13):
+        ncode = 4 ** length
+        tail = [int("".join(str(int(c)) for c in g[len(g) - j:][:length]).ljust(length, "0"), 4)
+                for j in range(1, length + 1)]
+        # G~'s last bases are G's first ones reversed: its short suffixes, padded
+        head = [int("".join(str(int(c)) for c in g[:j][::-1]).ljust(length, "0"), 4) for j in range(1, length + 1)]
+        planted = [int("".join(str(int(c)) for c in g[p0:p0 + length]), 4)
+                   for p0 in rng.integers(0, len(g) - length, 300)]
+        codes = np.unique(np.concatenate([rng.integers(0, ncode, 300), [0, ncode - 1], tail, head,
+                                          planted])).astype(np.uint32)
+        pats = [np.array([(int(x) >> (2 * (length - 1 - t))) & 3 for t in range(length)], np.uint8) for x in codes]
+        want_f = [fm.exact_interval(p) for p in pats]
+        want_r = [rfm.exact_interval(p) for p in pats]
+        for which, want in (("long_fwd", want_f), ("long_rev", want_r)) + \
+                (((("fwd", want_f), ("rev", want_r))) if length <= 12 else ()):
+            for ix in (idx, idx2):
+                got = ix.debug_table_interval(which, codes, length)
+                for (l, r), (el, er) in zip(got, want):
+                    assert (r - l) == (er - el), (which, length)
+                    if el < er:
+                        assert (int(l), int(r)) == (el, er), (which, length)
+    with pytest.raises(m.MicaError):
+        idx.debug_table_interval("long_fwd", np.zeros(1, np.uint32), 14)
+    small = m.Index.build(synth.to_acgt_bytes(g[:100_000]), kmer_q=12, sa_sample=16)
+    assert small.info()["long_q"] == 0                         # log4 N + 1 <= 12: no longer tables
+    with pytest.raises(m.MicaError):
+        small.debug_table_interval("long_fwd", np.zeros(1, np.uint32), 1)
+    idx.free(); idx2.free(); small.free()
+
+
 def test_gather_ceiling_orders_l2_above_hbm():
     """The random-gather ceiling: a buffer that fits L2 serves 32-byte random
     loads faster than one twelve times L2's size, and both stay below a
