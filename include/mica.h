@@ -296,6 +296,10 @@ typedef struct {
                                part is at least this many bases (and which has at least 8 bases
                                left to match) is checked against the genome's text in one step
                                instead of being extended base by base; 0 = 12, 256 or more = never */
+    int32_t bidir_shape;    /* bidirectional kernel shape: 0 = 64 task slots per warp, 6 warps per CTA
+                               (fuller rounds when tasks are short); 1 = 32 slots, 8 warps (more warps
+                               to hide HBM latency); -1 = automatic (0 when the occurrence blocks fit in
+                               96 MiB and stay in L2, else 1) */
 } mica_tuning;
 
 /* Number of compiled persistent kernel shapes; mica_tuning_shape_info

@@ -78,7 +78,7 @@ class Stats(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("shape", ctypes.c_int32), ("plain_block", ctypes.c_uint32), ("plain_budget", ctypes.c_uint32),
                 ("plain_block_len", ctypes.c_uint32 * 4), ("prefetch", ctypes.c_int32),
-                ("bidir_budget", ctypes.c_uint32), ("bidir_verify", ctypes.c_uint32)]
+                ("bidir_budget", ctypes.c_uint32), ("bidir_verify", ctypes.c_uint32), ("bidir_shape", ctypes.c_int32)]
 
 
 def tuning_shapes() -> list:
@@ -361,9 +361,9 @@ class Index:
         return d
 
     def set_tuning(self, shape: int = -1, plain_block: int = 0, plain_budget: int = 0, plain_block_len=(0, 0, 0, 0),
-                   prefetch: int = -1, bidir_budget: int = 0, bidir_verify: int = 0):
+                   prefetch: int = -1, bidir_budget: int = 0, bidir_verify: int = 0, bidir_shape: int = -1):
         t = Tuning(shape, plain_block, plain_budget, (ctypes.c_uint32 * 4)(*plain_block_len), prefetch, bidir_budget,
-                   bidir_verify)
+                   bidir_verify, bidir_shape)
         _check(_lib.mica_set_tuning(self._h, ctypes.byref(t)), "mica_set_tuning")
 
     def autotune(self, batch, hit_cap: int = 1000, repeats: int = 2, cache: str | None = None) -> dict:
@@ -397,7 +397,7 @@ class Index:
         _check(_lib.mica_get_tuning(self._h, ctypes.byref(t)), "mica_get_tuning")
         return {"shape": t.shape, "plain_block": t.plain_block, "plain_budget": t.plain_budget,
                 "plain_block_len": list(t.plain_block_len), "prefetch": t.prefetch, "bidir_budget": t.bidir_budget,
-                "bidir_verify": t.bidir_verify}
+                "bidir_verify": t.bidir_verify, "bidir_shape": t.bidir_shape}
 
     def stats(self) -> dict:
         s = Stats()

@@ -55,26 +55,29 @@ namespace mica {
 namespace {
 
 constexpr unsigned BFULL = 0xffffffffu;
-constexpr uint32_t BD_ADMIT_LOW = 64;       // admit new tasks while fewer items are pending
 constexpr uint32_t BD_DEEP_MIN = 8192;      // entries of each per-warp overflow stack, at least
 constexpr uint32_t SCHEME_FREE = 7;         // the single scheme of reads shorter than k + 1
 constexpr uint32_t BD_BUDGET = 1u << 12;    // node expansions a task may take before it exports its nodes
 constexpr uint32_t BD_VERIFY_MIN = 12;      // matched bases of a one-row node before it is checked against the text
 constexpr uint32_t BD_VERIFY_LEFT = 8;      // ... when at least this many bases are left to match
 constexpr int VCAP = 64;                    // one-row nodes waiting for that check (at most 63: see the round choice)
+constexpr uint32_t NSLOT_MAX = 64;          // task slots per warp: 32 (one per lane) or 64 (two)
+constexpr uint32_t BD_ADMIT_LOW = 96;       // admit new tasks while fewer items are pending ...
+constexpr uint32_t BD_ADMIT_FREE = 16;      // ... and at least this many slots are free (or nothing is pending)
 
-// node meta: slot (5 bits) | a (9) | b (9) | d (2) | d0 (2) | scheme (3)
+// node meta: slot (6 bits) | a (9) | b (9) | d (2) | d0 (2) | scheme (3)
 __device__ __forceinline__ uint32_t bd_meta(uint32_t slot, uint32_t a, uint32_t b, uint32_t d, uint32_t d0,
                                             uint32_t j)
 {
-    return slot | (a << 5) | (b << 14) | (d << 23) | (d0 << 25) | (j << 27);
+    return slot | (a << 6) | (b << 15) | (d << 24) | (d0 << 26) | (j << 28);
 }
-__device__ __forceinline__ uint32_t bm_slot(uint32_t x) { return x & 31u; }
-__device__ __forceinline__ uint32_t bm_a(uint32_t x) { return (x >> 5) & 511u; }
-__device__ __forceinline__ uint32_t bm_b(uint32_t x) { return (x >> 14) & 511u; }
-__device__ __forceinline__ uint32_t bm_d(uint32_t x) { return (x >> 23) & 3u; }
-__device__ __forceinline__ uint32_t bm_d0(uint32_t x) { return (x >> 25) & 3u; }
-__device__ __forceinline__ uint32_t bm_j(uint32_t x) { return (x >> 27) & 7u; }
+constexpr uint32_t BM_SLOT_MASK = 63u;
+__device__ __forceinline__ uint32_t bm_slot(uint32_t x) { return x & BM_SLOT_MASK; }
+__device__ __forceinline__ uint32_t bm_a(uint32_t x) { return (x >> 6) & 511u; }
+__device__ __forceinline__ uint32_t bm_b(uint32_t x) { return (x >> 15) & 511u; }
+__device__ __forceinline__ uint32_t bm_d(uint32_t x) { return (x >> 24) & 3u; }
+__device__ __forceinline__ uint32_t bm_d0(uint32_t x) { return (x >> 26) & 3u; }
+__device__ __forceinline__ uint32_t bm_j(uint32_t x) { return (x >> 28) & 7u; }
 
 // piece boundaries of a pattern of m bases in p pieces
 __device__ __forceinline__ uint32_t bnd(uint32_t i, uint32_t m, uint32_t p) { return i * m / p; }
@@ -122,19 +125,29 @@ struct BidirArgs {
     uint32_t verify_min;
 };
 
-template <int SCAP>
+template <int SCAP, int NS>
 struct BdSmem {
     uint32_t ml[SCAP], mlr[SCAP], msz[SCAP], mm[SCAP];   // multi-row nodes
     uint32_t sl[SCAP], slr[SCAP], sm[SCAP];              // single-row nodes
     uint32_t vl[VCAP], vlr[VCAP], vm[VCAP];              // single-row nodes to check against the text
-    uint32_t pat[32][MAX_WORDS + 1];                     // pattern of each task slot
-    int live[32];                                        // nodes of each slot on the stacks
-    uint32_t work[32];                                   // node expansions of each slot's task
-    unsigned long long bounds[32];                       // piece boundaries of each slot's pattern
-    unsigned long long stage_off[32];                    // admission: word offset of each new slot's read,
-    uint32_t stage_m[32];                                //   its length | minus << 15,
-    uint8_t rank_lane[32];                               //   and the slot of the j-th new task
+    uint32_t pat[NS][MAX_WORDS + 1];                  // pattern of each task slot
+    // task slot s: read id, info = m | k << 9 | minus << 11 | p << 12 | end of
+    // its scheme range << 15, next scheme to seed
+    uint32_t sread[NS], sinfo[NS], snext[NS];
+    int live[NS];                                     // nodes of each slot on the stacks
+    uint32_t work[NS];                                // node expansions of each slot's task
+    unsigned long long bounds[NS];                    // piece boundaries of each slot's pattern
+    unsigned long long stage_off[NS];                 // admission: word offset of each new slot's read,
+    uint32_t stage_m[NS];                             //   its length | minus << 15,
+    uint8_t rank_lane[NS];                            //   and the slot of the j-th new task
+    uint8_t seed_list[32];                               // a seed round's slots
 };
+
+template <int SCAP, int NS>
+__device__ __forceinline__ uint32_t slot_task(const BdSmem<SCAP, NS> &W, uint32_t slot)
+{
+    return 2 * W.sread[slot] + ((W.sinfo[slot] >> 11) & 1u);
+}
 
 // Occ(c, row) for one symbol c on one side, from a loaded block.
 __device__ __forceinline__ uint32_t occ_single_side(const OccSide &ix, uint32_t b, uint32_t o, const uint4 &sup,
@@ -167,8 +180,8 @@ __device__ __forceinline__ uint32_t side_C(const OccSide &s, uint32_t c)
 // covers are dropped; a chunk that would reach outside the batch's words
 // array (its first or last read only) is read word by word.  Minus-strand
 // rows are stored word-reversed; the slot's own lane then complements them.
-template <int SCAP>
-__device__ __forceinline__ void bd_stage_patterns(BdSmem<SCAP> &W, const uint32_t *words, const uint32_t *words_end,
+template <int SCAP, int NS>
+__device__ __forceinline__ void bd_stage_patterns(BdSmem<SCAP, NS> &W, const uint32_t *words, const uint32_t *words_end,
                                                   uint32_t nnew, int lane)
 {
     const uint32_t quad = (uint32_t)lane >> 2, g = (uint32_t)lane & 3u;
@@ -289,8 +302,8 @@ __device__ __forceinline__ bool bd_check_window(const uint32_t *__restrict__ tex
 }
 
 // Move the n oldest nodes of a stack to the warp's overflow stack (n fits).
-template <int SCAP, bool SINGLE>
-__device__ __forceinline__ void bd_deep_push(BdSmem<SCAP> &W, uint4 *deep, uint32_t &dtop, uint32_t &bot, uint32_t n,
+template <int SCAP, int NS, bool SINGLE>
+__device__ __forceinline__ void bd_deep_push(BdSmem<SCAP, NS> &W, uint4 *deep, uint32_t &dtop, uint32_t &bot, uint32_t n,
                                              int lane)
 {
     for (uint32_t r0 = 0; r0 < n; r0 += 32) {
@@ -307,8 +320,8 @@ __device__ __forceinline__ void bd_deep_push(BdSmem<SCAP> &W, uint4 *deep, uint3
 }
 
 // Bring the n most recently moved nodes back under the stack's bottom.
-template <int SCAP, bool SINGLE>
-__device__ __forceinline__ void bd_deep_pop(BdSmem<SCAP> &W, const uint4 *deep, uint32_t &dtop, uint32_t &bot,
+template <int SCAP, int NS, bool SINGLE>
+__device__ __forceinline__ void bd_deep_pop(BdSmem<SCAP, NS> &W, const uint4 *deep, uint32_t &dtop, uint32_t &bot,
                                             uint32_t n, int lane)
 {
     for (uint32_t r0 = 0; r0 < n; r0 += 32) {
@@ -339,7 +352,7 @@ __device__ __forceinline__ void bd_export_one(const BidirArgs &a, uint32_t q, ui
 {
     if (q < a.fr_cap) {
         a.fr_out[q] = make_uint4(task, l, lr, sz);
-        a.fr_out_meta[q] = meta & ~31u;
+        a.fr_out_meta[q] = meta & ~BM_SLOT_MASK;
     } else {
         bd_give_up(a, task >> 1);
     }
@@ -347,11 +360,11 @@ __device__ __forceinline__ void bd_export_one(const BidirArgs &a, uint32_t q, ui
 
 // Move the nodes of the slots in `expm` out of one stack (the shared-memory
 // part [bot, top) or the overflow part deep[0, dtop)): exported nodes go to
-// the frontier buffer, the others are compacted in their order.  task[s] is
-// slot s's task (2 read + strand).  Returns the nodes kept.
-template <int SCAP, bool SINGLE, bool DEEP>
-__device__ __forceinline__ uint32_t bd_export_stack(BdSmem<SCAP> &W, const BidirArgs &a, uint4 *deep, uint32_t bot,
-                                                    uint32_t top, unsigned expm, uint32_t task_of_lane, int lane)
+// the frontier buffer, the others are compacted in their order.  Returns
+// the nodes kept.
+template <int SCAP, int NS, bool SINGLE, bool DEEP>
+__device__ __forceinline__ uint32_t bd_export_stack(BdSmem<SCAP, NS> &W, const BidirArgs &a, uint4 *deep, uint32_t bot,
+                                                    uint32_t top, unsigned long long expm, int lane)
 {
     const unsigned lt = (1u << lane) - 1u;
     uint32_t kept = 0;
@@ -371,8 +384,8 @@ __device__ __forceinline__ uint32_t bd_export_stack(BdSmem<SCAP> &W, const Bidir
             }
         }
         const uint32_t slot = bm_slot(meta);
-        const uint32_t task = __shfl_sync(BFULL, task_of_lane, slot);
-        const bool ex = has && ((expm >> slot) & 1u);
+        const bool ex = has && ((expm >> slot) & 1ull);
+        const uint32_t task = ex ? slot_task(W, slot) : 0u;
         const bool keep = has && !ex;
         const unsigned em = __ballot_sync(BFULL, ex), km = __ballot_sync(BFULL, keep);
         uint32_t base = 0;
@@ -399,9 +412,9 @@ __device__ __forceinline__ uint32_t bd_export_stack(BdSmem<SCAP> &W, const Bidir
 
 // The same for the stack of nodes waiting for the text check ([0, vtop),
 // no overflow part): they leave as single-row nodes.
-template <int SCAP>
-__device__ __forceinline__ uint32_t bd_export_verify(BdSmem<SCAP> &W, const BidirArgs &a, uint32_t vtop,
-                                                     unsigned expm, uint32_t task_of_lane, int lane)
+template <int SCAP, int NS>
+__device__ __forceinline__ uint32_t bd_export_verify(BdSmem<SCAP, NS> &W, const BidirArgs &a, uint32_t vtop,
+                                                     unsigned long long expm, int lane)
 {
     const unsigned lt = (1u << lane) - 1u;
     uint32_t kept = 0;
@@ -411,8 +424,8 @@ __device__ __forceinline__ uint32_t bd_export_verify(BdSmem<SCAP> &W, const Bidi
         uint32_t l = 0, lr = 0, meta = 0;
         if (has) { l = W.vl[e]; lr = W.vlr[e]; meta = W.vm[e]; }
         const uint32_t slot = bm_slot(meta);
-        const uint32_t task = __shfl_sync(BFULL, task_of_lane, slot);
-        const bool ex = has && ((expm >> slot) & 1u);
+        const bool ex = has && ((expm >> slot) & 1ull);
+        const uint32_t task = ex ? slot_task(W, slot) : 0u;
         const bool keep = has && !ex;
         const unsigned em = __ballot_sync(BFULL, ex), km = __ballot_sync(BFULL, keep);
         uint32_t base = 0;
@@ -434,17 +447,16 @@ __device__ __forceinline__ uint32_t bd_export_verify(BdSmem<SCAP> &W, const Bidi
 
 // Room for `add` more nodes on a stack: its oldest nodes go to the warp's
 // overflow stack, or, when that is full, to the frontier buffer as tasks of
-// the next round (task_of_lane: 2 read + strand of the lane's slot).
-template <int SCAP, bool SINGLE>
-__device__ __forceinline__ void bd_make_room(BdSmem<SCAP> &W, const BidirArgs &a, uint4 *deep, uint32_t &dtop,
-                                             uint32_t &bot, uint32_t top, uint32_t add, uint32_t task_of_lane,
-                                             int lane, uint32_t &c_deep)
+// the next round.
+template <int SCAP, int NS, bool SINGLE>
+__device__ __forceinline__ void bd_make_room(BdSmem<SCAP, NS> &W, const BidirArgs &a, uint4 *deep, uint32_t &dtop,
+                                             uint32_t &bot, uint32_t top, uint32_t add, int lane, uint32_t &c_deep)
 {
     if ((top - bot) + add <= (uint32_t)SCAP) return;
     uint32_t nsp = (top - bot) + add - SCAP + SCAP / 4;
     nsp = min((nsp + 31) & ~31u, top - bot);
     if (dtop + nsp <= a.deep_cap) {
-        bd_deep_push<SCAP, SINGLE>(W, deep, dtop, bot, nsp, lane);
+        bd_deep_push<SCAP, NS, SINGLE>(W, deep, dtop, bot, nsp, lane);
         c_deep += nsp;
         return;
     }
@@ -459,7 +471,7 @@ __device__ __forceinline__ void bd_make_room(BdSmem<SCAP> &W, const BidirArgs &a
             else { l = W.ml[q]; lr = W.mlr[q]; sz = W.msz[q]; meta = W.mm[q]; }
         }
         const uint32_t slot = bm_slot(meta);
-        const uint32_t task = __shfl_sync(BFULL, task_of_lane, slot);
+        const uint32_t task = has ? slot_task(W, slot) : 0u;
         const unsigned em = __ballot_sync(BFULL, has);
         uint32_t base = 0;
         if (lane == 0) base = atomicAdd(&a.ctl->fr_count, (unsigned)__popc(em));
@@ -509,16 +521,16 @@ __device__ __forceinline__ void bd_emit(const BidirArgs &a, uint32_t nleaf, cons
     }
 }
 
-template <int SCAP, int WARPS, int MINB>
+template <int SCAP, int WARPS, int MINB, int NS>
 __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
 {
     // a frontier round with nothing exported to it (most batches need none)
     const unsigned long long ntasks = *(volatile unsigned long long *)&a.ctl->ntasks;
     if (ntasks == 0) return;
     extern __shared__ uint4 bd_smem_raw[];
-    BdSmem<SCAP> *all = reinterpret_cast<BdSmem<SCAP> *>(bd_smem_raw);
+    BdSmem<SCAP, NS> *all = reinterpret_cast<BdSmem<SCAP, NS> *>(bd_smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    BdSmem<SCAP> &W = all[warp];
+    BdSmem<SCAP, NS> &W = all[warp];
     const IndexView &ix = a.ix;
     SearchCtl *ctl = a.ctl;
     const unsigned lt = (1u << lane) - 1u;
@@ -527,12 +539,18 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
     uint4 *deep_s = a.deep_s + (size_t)wg * a.deep_cap;
     const uint32_t *words_end = a.rd.words + a.rd.word_off[a.rd.n];
 
-    W.live[lane] = 0;
-    W.work[lane] = 0;
-    // task slot `lane`: read id, info = m | k << 9 | minus << 11 | p << 12 | scheme count << 15,
-    // next scheme to seed
-    uint32_t s_read = 0, s_info = 0, s_next = 0;
-    bool s_used = false;
+    // slot lane (and, with 64 slots, lane + 32) belong to this lane for the bookkeeping below
+    constexpr bool TWO = NS == 64;
+    constexpr uint32_t HS = TWO ? 2 : 1;
+    for (uint32_t h = 0; h < HS; h++) {
+        const uint32_t sl = (uint32_t)lane + 32 * h;
+        W.live[sl] = 0;
+        W.work[sl] = 0;
+        W.sread[sl] = 0;
+        W.sinfo[sl] = 0;
+        W.snext[sl] = 0;
+    }
+    unsigned used_lo = 0, used_hi = 0;   // slots holding a task (warp-uniform)
     uint32_t mbot = 0, mtop = 0, sbot = 0, stop = 0, dmt = 0, dst = 0;
     uint32_t vtop = 0;   // nodes waiting for the text check: W.v*[0, vtop)
     bool tasks_left = true;
@@ -545,18 +563,24 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
 
     for (uint32_t iter = 0;; iter++) {
         if ((iter & 15) == 0 && *(volatile unsigned *)&ctl->error != 0) break;
-        const uint32_t s_nsch = (s_info >> 15) & 7u;
-        if (s_used && W.live[lane] == 0 && s_next >= s_nsch) s_used = false;
-        const unsigned used = __ballot_sync(BFULL, s_used);
+        // a slot frees once its nodes are gone and its schemes are seeded
+        const uint32_t lane2 = TWO ? (uint32_t)lane + 32 : (uint32_t)lane;   // the lane's second slot
+        bool u0 = (used_lo >> lane) & 1u, u1 = TWO && ((used_hi >> lane) & 1u);
+        const uint32_t i0 = W.sinfo[lane], i1 = W.sinfo[lane2];
+        const uint32_t n0 = W.snext[lane], n1 = W.snext[lane2];
+        if (u0 && W.live[lane] == 0 && n0 >= ((i0 >> 15) & 7u)) u0 = false;
+        if (u1 && W.live[lane2] == 0 && n1 >= ((i1 >> 15) & 7u)) u1 = false;
+        used_lo = __ballot_sync(BFULL, u0);
+        used_hi = __ballot_sync(BFULL, u1);
         uint32_t mc = mtop - mbot, sc = stop - sbot;
         if (mc < 32 && dmt > 0) {
             uint32_t n = min(dmt, 64u);
-            bd_deep_pop<SCAP, false>(W, deep_m, dmt, mbot, n, lane);
+            bd_deep_pop<SCAP, NS, false>(W, deep_m, dmt, mbot, n, lane);
             mc += n;
         }
         if (sc < 32 && dst > 0) {
             uint32_t n = min(dst, 64u);
-            bd_deep_pop<SCAP, true>(W, deep_s, dst, sbot, n, lane);
+            bd_deep_pop<SCAP, NS, true>(W, deep_s, dst, sbot, n, lane);
             sc += n;
         }
         if ((iter & 63) == 63 && budget == a.budget) {
@@ -567,45 +591,55 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
         // ---- slots over their node budget hand their nodes to the next
         // round (one pass over both stacks), and their schemes not yet seeded
         // as seed items (size 0, the scheme in the meta word)
-        const bool over = s_used && W.work[lane] >= budget && (W.live[lane] > 0 || s_next < s_nsch);
-        const unsigned expm = __ballot_sync(BFULL, over);
-        if (expm) {
-            const uint32_t task = 2 * s_read + ((s_info >> 11) & 1u);
-            const uint32_t nseed = over ? s_nsch - s_next : 0u;
-            uint32_t pre = nseed;
+        const bool over0 = u0 && W.work[lane] >= budget && (W.live[lane] > 0 || n0 < ((i0 >> 15) & 7u));
+        const bool over1 = u1 && W.work[lane2] >= budget && (W.live[lane2] > 0 || n1 < ((i1 >> 15) & 7u));
+        const unsigned ex_lo = __ballot_sync(BFULL, over0), ex_hi = __ballot_sync(BFULL, over1);
+        if (ex_lo | ex_hi) {
+            const unsigned long long expm = (unsigned long long)ex_lo | ((unsigned long long)ex_hi << 32);
+            const uint32_t ns0 = over0 ? ((i0 >> 15) & 7u) - n0 : 0u, ns1 = over1 ? ((i1 >> 15) & 7u) - n1 : 0u;
+            uint32_t pre = ns0 + ns1;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 uint32_t y = __shfl_up_sync(BFULL, pre, o);
                 if (lane >= o) pre += y;
             }
             const uint32_t tot = __shfl_sync(BFULL, pre, 31);
-            pre -= nseed;
+            pre -= ns0 + ns1;
             if (tot) {
                 uint32_t base = 0;
                 if (lane == 0) base = atomicAdd(&ctl->fr_count, tot);
                 base = __shfl_sync(BFULL, base, 0);
-                for (uint32_t i = 0; i < nseed; i++)
-                    bd_export_one(a, base + pre + i, task, 0, 0, 0, bd_meta(0, 0, 0, 0, 0, s_next + i));
+                for (uint32_t i = 0; i < ns0; i++)
+                    bd_export_one(a, base + pre + i, slot_task(W, lane), 0, 0, 0, bd_meta(0, 0, 0, 0, 0, n0 + i));
+                for (uint32_t i = 0; i < ns1; i++)
+                    bd_export_one(a, base + pre + ns0 + i, slot_task(W, lane2), 0, 0, 0,
+                                  bd_meta(0, 0, 0, 0, 0, n1 + i));
             }
-            if (over) s_next = s_nsch;
-            mtop = mbot + bd_export_stack<SCAP, false, false>(W, a, nullptr, mbot, mtop, expm, task, lane);
-            stop = sbot + bd_export_stack<SCAP, true, false>(W, a, nullptr, sbot, stop, expm, task, lane);
-            if (dmt) dmt = bd_export_stack<SCAP, false, true>(W, a, deep_m, 0, dmt, expm, task, lane);
-            if (dst) dst = bd_export_stack<SCAP, true, true>(W, a, deep_s, 0, dst, expm, task, lane);
-            if (vtop) vtop = bd_export_verify<SCAP>(W, a, vtop, expm, task, lane);
-            if (over) W.live[lane] = 0;   // its nodes are gone: the slot frees below
+            if (over0) W.snext[lane] = (i0 >> 15) & 7u;
+            if (over1) W.snext[lane2] = (i1 >> 15) & 7u;
+            mtop = mbot + bd_export_stack<SCAP, NS, false, false>(W, a, nullptr, mbot, mtop, expm, lane);
+            stop = sbot + bd_export_stack<SCAP, NS, true, false>(W, a, nullptr, sbot, stop, expm, lane);
+            if (dmt) dmt = bd_export_stack<SCAP, NS, false, true>(W, a, deep_m, 0, dmt, expm, lane);
+            if (dst) dst = bd_export_stack<SCAP, NS, true, true>(W, a, deep_s, 0, dst, expm, lane);
+            if (vtop) vtop = bd_export_verify<SCAP, NS>(W, a, vtop, expm, lane);
+            if (over0) W.live[lane] = 0;   // their nodes are gone: the slots free above
+            if (over1) W.live[lane2] = 0;
             __syncwarp();
             continue;
         }
-        const uint32_t avail = (s_used && s_next < s_nsch) ? 1u : 0u;
-        const uint32_t seeds_total = __popc(__ballot_sync(BFULL, avail));
+        const bool av0 = u0 && n0 < ((i0 >> 15) & 7u), av1 = u1 && n1 < ((i1 >> 15) & 7u);
+        const unsigned avail_lo = __ballot_sync(BFULL, av0), avail_hi = __ballot_sync(BFULL, av1);
+        const uint32_t seeds_total = __popc(avail_lo) + __popc(avail_hi);
         const uint32_t cnt = mc + sc + vtop;
 
-        // ---- admission of fresh tasks into free slots
-        const unsigned freem = ~used;
-        if (tasks_left && freem != 0 && dmt + dst == 0 && cnt + seeds_total < BD_ADMIT_LOW &&
-            (cnt + seeds_total == 0 || __popc(freem) >= 8)) {
-            uint32_t want = __popc(freem), got = 0;
+        // ---- admission of fresh tasks (or of the last round's exported nodes) into free slots
+        const unsigned free_lo = ~used_lo, free_hi = TWO ? ~used_hi : 0u;
+        const uint32_t nfree = __popc(free_lo) + __popc(free_hi);
+        // the nodes of a frontier round's tasks go onto the stacks at once: room for them
+        const uint32_t room = a.mode == 1 ? (uint32_t)SCAP - max(mc, sc) : nfree;
+        if (tasks_left && nfree != 0 && dmt + dst == 0 && cnt + seeds_total < BD_ADMIT_LOW &&
+            (cnt + seeds_total == 0 || nfree >= BD_ADMIT_FREE) && room > 0) {
+            uint32_t want = min(nfree, room), got = 0;
             unsigned long long t0 = 0;
             if (lane == 0) {
                 if (*(volatile unsigned long long *)&ctl->task_head < ntasks) {
@@ -618,68 +652,82 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
             if (got == 0) {
                 tasks_left = false;
             } else {
-                const uint32_t jr = __popc(freem & lt);
-                const bool mine = ((freem >> lane) & 1u) && jr < got;
-                bool push = false;
-                if (mine) {
+                const uint32_t nlo = __popc(free_lo);
+                uint4 it[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+                uint32_t imeta[2] = {0, 0};
+                bool push[2] = {false, false};
+                uint32_t minus_new = 0;
+#pragma unroll
+                for (uint32_t h = 0; h < HS; h++) {
+                    const uint32_t sl = (uint32_t)lane + 32 * h;
+                    const bool fr = h == 0 ? ((free_lo >> lane) & 1u) : ((free_hi >> lane) & 1u);
+                    const uint32_t jr = h == 0 ? __popc(free_lo & lt) : nlo + __popc(free_hi & lt);
+                    if (!fr || jr >= got) continue;
                     unsigned long long t = t0 + jr;
                     uint32_t seed_j = 8;                   // 8: not a seed item
                     if (a.mode == 1) {                     // a node (or a scheme to seed) exported by the last round
-                        const uint4 it = a.fr_in[t];
-                        if (it.w == 0) seed_j = bm_j(a.fr_in_meta[t]);
-                        t = it.x;
+                        it[h] = a.fr_in[t];
+                        imeta[h] = a.fr_in_meta[t];
+                        if (it[h].w == 0) seed_j = bm_j(imeta[h]);
+                        t = it[h].x;
                     }
                     const uint32_t rid = (uint32_t)(t >> 1), minus = (uint32_t)(t & 1);
                     const uint32_t m = a.rd.len[rid], k = a.rd.k[rid];
                     const uint32_t p = m >= k + 1 ? k + 1 : 1u;
                     const uint32_t nsch = m >= k + 1 ? p : 1u;
-                    s_read = rid;
                     const bool given_up = a.mode == 1 && ((a.redo[rid >> 5] >> (rid & 31)) & 1u);
                     // a seed item seeds its one scheme: the slot's scheme range is [j, j + 1)
                     const uint32_t send = seed_j < 8 ? seed_j + 1 : nsch;
-                    s_info = m | (k << 9) | (minus << 11) | (p << 12) | (send << 15);
-                    s_next = a.mode == 0 ? 0 : (seed_j < 8 && !given_up ? seed_j : send);
-                    s_used = true;
+                    W.sread[sl] = rid;
+                    W.sinfo[sl] = m | (k << 9) | (minus << 11) | (p << 12) | (send << 15);
+                    W.snext[sl] = a.mode == 0 ? 0 : (seed_j < 8 && !given_up ? seed_j : send);
                     // the node of a read already given up is not continued
-                    push = a.mode == 1 && seed_j == 8 && !given_up;
-                    W.live[lane] = push ? 1 : 0;
-                    W.work[lane] = 0;
-                    W.bounds[lane] = pack_bounds(m, p);
-                    W.rank_lane[jr] = (uint8_t)lane;
-                    W.stage_off[lane] = a.rd.word_off[rid];
-                    W.stage_m[lane] = m | (minus << 15);
+                    push[h] = a.mode == 1 && seed_j == 8 && !given_up;
+                    W.live[sl] = push[h] ? 1 : 0;
+                    W.work[sl] = 0;
+                    W.bounds[sl] = pack_bounds(m, p);
+                    W.rank_lane[jr] = (uint8_t)sl;
+                    W.stage_off[sl] = a.rd.word_off[rid];
+                    W.stage_m[sl] = m | (minus << 15);
+                    if (minus) minus_new |= 1u << h;
+                    if (h == 0) u0 = true; else u1 = true;
                 }
+                used_lo = __ballot_sync(BFULL, u0);
+                used_hi = __ballot_sync(BFULL, u1);
                 __syncwarp();
-                bd_stage_patterns<SCAP>(W, a.rd.words, words_end, got, lane);
+                bd_stage_patterns<SCAP, NS>(W, a.rd.words, words_end, got, lane);
                 __syncwarp();
-                if (mine && ((s_info >> 11) & 1u)) bd_complement_row(W.pat[lane], s_info & 511u);
+                for (uint32_t h = 0; h < HS; h++)
+                    if ((minus_new >> h) & 1u) {
+                        const uint32_t sl = (uint32_t)lane + 32 * h;
+                        bd_complement_row(W.pat[sl], W.sinfo[sl] & 511u);
+                    }
                 if (a.mode == 1) {
-                    // the admitted nodes onto the stacks (fewer than 64 were pending: room for 32 more)
-                    uint4 it = make_uint4(0, 0, 0, 0);
-                    uint32_t imeta = 0;
-                    if (push) {
-                        it = a.fr_in[t0 + jr];
-                        imeta = a.fr_in_meta[t0 + jr] | (uint32_t)lane;
+                    // the admitted nodes onto the stacks
+#pragma unroll
+                    for (uint32_t h = 0; h < HS; h++) {
+                        const uint32_t sl = (uint32_t)lane + 32 * h;
+                        const bool single = it[h].w == 1;
+                        const unsigned bm = __ballot_sync(BFULL, push[h] && !single),
+                                       bs = __ballot_sync(BFULL, push[h] && single);
+                        if (push[h] && !single) {
+                            uint32_t q = (mtop + __popc(bm & lt)) & (SCAP - 1);
+                            W.ml[q] = it[h].y; W.mlr[q] = it[h].z; W.msz[q] = it[h].w; W.mm[q] = imeta[h] | sl;
+                        }
+                        if (push[h] && single) {
+                            uint32_t q = (stop + __popc(bs & lt)) & (SCAP - 1);
+                            W.sl[q] = it[h].y; W.slr[q] = it[h].z; W.sm[q] = imeta[h] | sl;
+                        }
+                        mtop += __popc(bm);
+                        stop += __popc(bs);
                     }
-                    const bool single = it.w == 1;
-                    const unsigned bm = __ballot_sync(BFULL, push && !single), bs = __ballot_sync(BFULL, push && single);
-                    if (push && !single) {
-                        uint32_t q = (mtop + __popc(bm & lt)) & (SCAP - 1);
-                        W.ml[q] = it.y; W.mlr[q] = it.z; W.msz[q] = it.w; W.mm[q] = imeta;
-                    }
-                    if (push && single) {
-                        uint32_t q = (stop + __popc(bs & lt)) & (SCAP - 1);
-                        W.sl[q] = it.y; W.slr[q] = it.z; W.sm[q] = imeta;
-                    }
-                    mtop += __popc(bm);
-                    stop += __popc(bs);
                 }
                 __syncwarp();
                 continue;
             }
         }
         if (cnt + seeds_total == 0) {
-            if (!tasks_left && __ballot_sync(BFULL, s_used) == 0) break;   // nothing held, nothing left
+            if (!tasks_left && (used_lo | used_hi) == 0) break;   // nothing held, nothing left
             if (!tasks_left) {
                 // slots held but no work: cannot happen while the counts are right
                 if (lane == 0) atomicOr(&ctl->error, ERR_TIMEOUT);
@@ -696,31 +744,40 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
         if (vtop >= 32) kind = 3;
         else if (mc >= 32) kind = 0;
         else if (sc >= 32) kind = 1;
-        else if (seeds_total > 0 && seed_room && (seeds_total >= 16 || cnt == 0)) kind = 2;
+        else if (seeds_total > 0 && seed_room && (seeds_total >= 32 || seeds_total >= max(max(mc, sc), vtop)))
+            kind = 2;
         else if (mc && mc >= sc && mc >= vtop) kind = 0;
         else if (sc && sc >= vtop) kind = 1;
         else if (vtop) kind = 3;
         else kind = 2;
 
         if (kind == 2) {
-            // ---- one scheme's seed per slot: piece j's last bases from both tables
+            // ---- one scheme's seed for each of up to 32 slots with schemes left:
+            // piece j's last bases from both tables
+            const uint32_t r0 = __popc(avail_lo & lt), r1 = __popc(avail_lo) + __popc(avail_hi & lt);
+            if (av0 && r0 < 32) W.seed_list[r0] = (uint8_t)lane;
+            if (av1 && r1 < 32) W.seed_list[r1] = (uint8_t)lane2;
+            __syncwarp();
+            const bool avail = (uint32_t)lane < min(seeds_total, 32u);
+            const uint32_t slot = avail ? W.seed_list[lane] : 0u;
+            const uint32_t info = W.sinfo[slot];
             bool push = false, leaf = false;
             uint32_t l = 0, lr = 0, sz = 0, meta = 0;
             if (avail) {
-                const uint32_t m = s_info & 511u, k = (s_info >> 9) & 3u, p = (s_info >> 12) & 7u;
-                const uint32_t nsch = (s_info >> 15) & 7u;
-                const uint32_t j = s_next++;
-                const uint32_t *pat = W.pat[lane];
+                const uint32_t m = info & 511u, k = (info >> 9) & 3u, p = (info >> 12) & 7u;
+                const uint32_t nsch = (info >> 15) & 7u;
+                const uint32_t j = W.snext[slot]++;
+                const uint32_t *pat = W.pat[slot];
                 if (nsch == 1 && p == 1 && k > 0) {
                     // a read shorter than k + 1 bases: the whole tree from the full interval
                     l = 0; lr = 0; sz = ix.rows;
-                    meta = bd_meta((uint32_t)lane, m, m, 0, 0, SCHEME_FREE);
+                    meta = bd_meta(slot, m, m, 0, 0, SCHEME_FREE);
                     push = true;
                 } else {
                     // from the longer seed tables when the index has them
                     const bool longer = ix.lfwd.table != nullptr;
                     const uint32_t tq = longer ? ix.lfwd.q : ix.q;
-                    const uint32_t bj = bound_at(W.bounds[lane], j + 1), aj = bound_at(W.bounds[lane], j);
+                    const uint32_t bj = bound_at(W.bounds[slot], j + 1), aj = bound_at(W.bounds[slot], j);
                     const uint32_t qe = min(tq, bj - aj);
                     uint32_t code = 0, rcode = 0;
                     for (uint32_t t = 0; t < qe; t++) {
@@ -744,19 +801,19 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
                         l = fl; lr = rl; sz = fr - fl;
                         const uint32_t a0 = bj - qe;
                         if (a0 == 0 && bj == m) leaf = true;
-                        else { meta = bd_meta((uint32_t)lane, a0, bj, 0, 0, j); push = true; }
+                        else { meta = bd_meta(slot, a0, bj, 0, 0, j); push = true; }
                     }
                 }
             }
-            const uint32_t minus = (s_info >> 11) & 1u;
+            const uint32_t minus = (info >> 11) & 1u;
             uint32_t cl[4] = {l, 0, 0, 0}, cs[4] = {sz, 0, 0, 0}, cd[4] = {0, 0, 0, 0};
-            bd_emit(a, leaf ? 1u : 0u, cl, cs, cd, leaf ? 1u : 0u, s_read, minus, lane);
+            bd_emit(a, leaf ? 1u : 0u, cl, cs, cd, leaf ? 1u : 0u, W.sread[slot], minus, lane);
             const bool single = sz == 1;
             // a one-row seed far enough in goes straight to the text check (at
             // most 32 more: this round runs only while that stack holds fewer than 32)
             const uint32_t matched = bm_b(meta) - bm_a(meta);
             const bool to_v = push && single && a.verify_min && matched >= a.verify_min &&
-                              (s_info & 511u) - matched >= BD_VERIFY_LEFT;
+                              (info & 511u) - matched >= BD_VERIFY_LEFT;
             const unsigned bm = __ballot_sync(BFULL, push && !single),
                            bs = __ballot_sync(BFULL, push && single && !to_v), bv = __ballot_sync(BFULL, to_v);
             if (push && !single) {
@@ -774,7 +831,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
             mtop += __popc(bm);
             stop += __popc(bs);
             vtop += __popc(bv);
-            if (push) atomicAdd(&W.live[lane], 1);
+            if (push) atomicAdd(&W.live[slot], 1);
         } else if (kind == 1) {
             // ---- single-row nodes: the one possible child is the row's symbol
             const uint32_t npop = min(sc, 32u);
@@ -787,8 +844,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
             stop -= npop;
             __syncwarp();
             const uint32_t slot = bm_slot(meta);
-            const uint32_t info = __shfl_sync(BFULL, s_info, slot);
-            const uint32_t rid = __shfl_sync(BFULL, s_read, slot);
+            const uint32_t info = W.sinfo[slot];
+            const uint32_t rid = W.sread[slot];
             bool child = false, leaf = false;
             uint32_t nl = l, nlr = lr, nmeta = 0, dn = 0;
             // a node far enough in (and far enough from the end) goes to the text check
@@ -852,8 +909,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
             vtop -= npop;
             __syncwarp();
             const uint32_t slot = bm_slot(meta);
-            const uint32_t info = __shfl_sync(BFULL, s_info, slot);
-            const uint32_t rid = __shfl_sync(BFULL, s_read, slot);
+            const uint32_t info = W.sinfo[slot];
+            const uint32_t rid = W.sread[slot];
             bool leaf = false;
             uint32_t row = 0, dn = 0;
             if (has) {
@@ -883,8 +940,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
             mtop -= npop;
             __syncwarp();
             const uint32_t slot = bm_slot(meta);
-            const uint32_t info = __shfl_sync(BFULL, s_info, slot);
-            const uint32_t rid = __shfl_sync(BFULL, s_read, slot);
+            const uint32_t info = W.sinfo[slot];
+            const uint32_t rid = W.sread[slot];
             uint32_t cl[4] = {0, 0, 0, 0}, clr[4] = {0, 0, 0, 0}, cs[4] = {0, 0, 0, 0}, cd[4] = {0, 0, 0, 0};
             uint32_t cmeta[4] = {0, 0, 0, 0};
             uint32_t leafmask = 0, nodemask = 0;
@@ -936,9 +993,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
             pre -= packed;
             const uint32_t tm = tot & 0xffu, ts = tot >> 8;
             if (tm | ts) {
-                const uint32_t my_task = 2 * s_read + ((s_info >> 11) & 1u);
-                if (tm) bd_make_room<SCAP, false>(W, a, deep_m, dmt, mbot, mtop, tm, my_task, lane, c_deep);
-                if (ts) bd_make_room<SCAP, true>(W, a, deep_s, dst, sbot, stop, ts, my_task, lane, c_deep);
+                if (tm) bd_make_room<SCAP, NS, false>(W, a, deep_m, dmt, mbot, mtop, tm, lane, c_deep);
+                if (ts) bd_make_room<SCAP, NS, true>(W, a, deep_s, dst, sbot, stop, ts, lane, c_deep);
             }
             if (nm | ns) {
                 uint32_t pm = mtop + (pre & 0xffu), ps = stop + (pre >> 8);
@@ -1037,14 +1093,18 @@ __global__ void k_bd_give_up_frontier(SearchCtl *ctl, const uint4 *__restrict__ 
 
 struct BidirShape {
     void (*fn)(BidirArgs);
-    int scap, warps, minb;
+    int scap, warps, minb, slots;
     size_t smem;
     int blocks_per_sm;
 };
 
-#define MICA_BD_SHAPE(S, W, B) {k_bidir<S, W, B>, S, W, B, sizeof(BdSmem<S>) * W, 0}
+// 0: 64 task slots per warp, 6 warps per CTA (fuller rounds when each task is
+// short: an index whose occurrence blocks stay in L2); 1: 32 slots, 8 warps
+// (more warps to hide HBM latency for the deep trees of a human-scale index)
+#define MICA_BD_SHAPE(S, W, B, N) {k_bidir<S, W, B, N>, S, W, B, N, sizeof(BdSmem<S, N>) * W, 0}
 BidirShape g_bd_shapes[] = {
-    MICA_BD_SHAPE(128, 8, 3),
+    MICA_BD_SHAPE(128, 6, 3, 64),
+    MICA_BD_SHAPE(128, 8, 3, 32),
 };
 #undef MICA_BD_SHAPE
 
@@ -1065,6 +1125,17 @@ int bidir_grid(int device, BidirShape &sh, int &grid)
 }
 
 }  // namespace
+
+// The compiled shape a call uses: the tuning's choice, else 64 slots per
+// warp when the genome's occurrence blocks stay in L2 (96 MiB or less) and
+// 32 when they live in HBM.
+int bidir_shape_index(const mica_index *idx)
+{
+    if (idx->tuning.bidir_shape >= 0) return idx->tuning.bidir_shape;
+    return idx->n_occ_blocks * 32 > (96ull << 20) ? 1 : 0;
+}
+
+int bidir_shape_count() { return (int)(sizeof(g_bd_shapes) / sizeof(g_bd_shapes[0])); }
 
 bool bidir_available(const mica_index *idx)
 {
@@ -1109,7 +1180,7 @@ static uint64_t redo_bytes(uint64_t n) { return redo_bits_bytes(n) + std::max<ui
 int prepare_bidir(const mica_index *idx, Workspace &w, uint64_t n, SearchCtl &tmpl, int &grid)
 {
     int rc;
-    BidirShape &sh = g_bd_shapes[0];
+    BidirShape &sh = g_bd_shapes[bidir_shape_index(idx)];
     if ((rc = bidir_grid(idx->device, sh, grid))) return rc;
     if ((rc = dev_reserve(w.ctl, sizeof(SearchCtl) + 64))) return rc;
     if ((rc = dev_reserve(w.iv_cnt, std::max<uint64_t>(n, 1) * 4))) return rc;
@@ -1129,7 +1200,7 @@ int prepare_bidir(const mica_index *idx, Workspace &w, uint64_t n, SearchCtl &tm
 
 static void bidir_args(const mica_index *idx, Workspace &w, const ReadsView &rd, int grid, BidirArgs &ba)
 {
-    const BidirShape &sh = g_bd_shapes[0];
+    const BidirShape &sh = g_bd_shapes[bidir_shape_index(idx)];
     ba.ix = idx->view;
     ba.fwd.occ = idx->view.occ;
     ba.fwd.super = idx->view.super;
@@ -1183,7 +1254,7 @@ static int check_vector_alignment(const BidirArgs &ba)
 static int launch_round(const mica_index *idx, Workspace &w, const ReadsView &rd, int grid, int r, cudaStream_t s,
                         uint64_t &launches)
 {
-    const BidirShape &sh = g_bd_shapes[0];
+    const BidirShape &sh = g_bd_shapes[bidir_shape_index(idx)];
     BidirArgs ba;
     bidir_args(idx, w, rd, grid, ba);
     ba.mode = 1;
@@ -1206,7 +1277,7 @@ static int launch_round(const mica_index *idx, Workspace &w, const ReadsView &rd
 int enqueue_bidir(const mica_index *idx, Workspace &w, const ReadsView &rd, int grid, const SearchCtl *tmpl_src,
                   cudaStream_t s, uint64_t &launches, int rounds)
 {
-    const BidirShape &sh = g_bd_shapes[0];
+    const BidirShape &sh = g_bd_shapes[bidir_shape_index(idx)];
     SearchCtl *d_ctl = (SearchCtl *)w.ctl.p;
     MICA_CUDA_TRY(cudaMemcpyAsync(d_ctl, tmpl_src, sizeof(SearchCtl), cudaMemcpyHostToDevice, s));
     MICA_CUDA_TRY(cudaMemsetAsync(w.iv_cnt.p, 0, std::max<uint64_t>(rd.n, 1) * 4, s));

@@ -277,7 +277,7 @@ static int align_graph_launch(const mica_index *idx, Workspace &w, mica_stats &s
     const bool bidir = p.kernel == MICA_KERNEL_BIDIRECTIONAL;
     if (bidir) {
         if ((rc = prepare_bidir(idx, w, n, tmpl, grid))) return rc;
-        shape = 1 << 8;   // distinguishes the bidirectional kernel in the key
+        shape = (1 << 8) | bidir_shape_index(idx);   // the bidirectional kernel and its shape, in the key
     } else if ((rc = prepare_persistent(idx, w, n, idx->tuning.shape, tmpl, grid, shape))) {
         return rc;
     }
@@ -780,6 +780,7 @@ int mica_set_tuning(mica_index *idx, const mica_tuning *t)
             (t->plain_block_len[c] < 32 || t->plain_block_len[c] > 512 || t->plain_block_len[c] % 32))
             return MICA_EINVAL;
     if (t->prefetch < -1 || t->prefetch > 1) return MICA_EINVAL;
+    if (t->bidir_shape < -1 || t->bidir_shape >= bidir_shape_count()) return MICA_EINVAL;
     idx->tuning = *t;
     return 0;
 }

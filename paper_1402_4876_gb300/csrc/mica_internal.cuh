@@ -246,7 +246,7 @@ struct mica_index {
     bool has_full_sa = false;
     mica::Workspace ws;
     mica_stats stats{};
-    mica_tuning tuning{-1, 0, 0, {0, 0, 0, 0}, -1, 0, 0};
+    mica_tuning tuning{-1, 0, 0, {0, 0, 0, 0}, -1, 0, 0, -1};
     uint32_t idle_limit = 0, spin_limit = 0;   // persistent kernel wait bounds; 0 = built-in defaults
     mica::PipeSlot pipe[2];                    // pipelined host batches
     uint64_t next_ticket = 0;
@@ -350,6 +350,8 @@ int search_workspace_bytes(const mica_index *idx, uint64_t n, uint64_t *bytes);
 // bidir.cu
 constexpr int BIDIR_FALLBACK = 2;   // run_search_bidir: an overflow stack filled; run the one-directional search
 bool bidir_available(const mica_index *idx);
+int bidir_shape_index(const mica_index *idx);   // compiled bidirectional shape a call uses
+int bidir_shape_count();
 int prepare_bidir(const mica_index *idx, Workspace &w, uint64_t n, SearchCtl &tmpl, int &grid);
 int enqueue_bidir_graph(const mica_index *idx, Workspace &w, const ReadsView &rd, int grid, const SearchCtl *tmpl_src,
                         cudaStream_t s, uint64_t &launches);

@@ -167,9 +167,9 @@ int mica_tuning_cache_store(const char *path, const mica_index *idx, uint32_t le
     FILE *f = fopen(path, "w");
     if (!f) return MICA_EIO;
     for (auto &s : keep) fputs(s.c_str(), f);
-    fprintf(f, "%s\t%d %u %u %u %u %u %u %d %u %u\n", key.c_str(), t->shape, t->plain_block, t->plain_budget,
+    fprintf(f, "%s\t%d %u %u %u %u %u %u %d %u %u %d\n", key.c_str(), t->shape, t->plain_block, t->plain_budget,
             t->plain_block_len[0], t->plain_block_len[1], t->plain_block_len[2], t->plain_block_len[3], t->prefetch,
-            t->bidir_budget, t->bidir_verify);
+            t->bidir_budget, t->bidir_verify, t->bidir_shape);
     return fclose(f) == 0 ? 0 : MICA_EIO;
 }
 
@@ -188,10 +188,12 @@ int mica_tuning_cache_lookup(const char *path, const mica_index *idx, uint32_t l
         // lines written before the bidirectional fields were added hold eight or nine numbers
         x.bidir_budget = 0;
         x.bidir_verify = 0;
-        if (sscanf(line + key.size(), "%d %u %u %u %u %u %u %d %u %u", &x.shape, &x.plain_block, &x.plain_budget,
+        x.bidir_shape = -1;
+        if (sscanf(line + key.size(), "%d %u %u %u %u %u %u %d %u %u %d", &x.shape, &x.plain_block, &x.plain_budget,
                    &x.plain_block_len[0], &x.plain_block_len[1], &x.plain_block_len[2], &x.plain_block_len[3],
-                   &x.prefetch, &x.bidir_budget, &x.bidir_verify) >= 8 &&
-            x.shape >= -1 && x.shape < search_shape_count() && x.prefetch >= -1 && x.prefetch <= 1) {
+                   &x.prefetch, &x.bidir_budget, &x.bidir_verify, &x.bidir_shape) >= 8 &&
+            x.shape >= -1 && x.shape < search_shape_count() && x.prefetch >= -1 && x.prefetch <= 1 &&
+            x.bidir_shape >= -1 && x.bidir_shape < bidir_shape_count()) {
             *t = x;
             rc = 0;
         }

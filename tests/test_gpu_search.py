@@ -280,6 +280,14 @@ def test_bidirectional_text_check_settings():
                 st = idx.stats()
                 assert (st["verified"] > 0) == (verify < 256), (verify, st["verified"])
                 assert (st["verify_bytes"] > 0) == (verify < 256)
+        # both compiled shapes (64 task slots per warp, 6 warps; 32 slots, 8 warps)
+        for shape in (0, 1):
+            for budget in (0, 16):
+                idx.set_tuning(bidir_shape=shape, bidir_budget=budget)
+                gc.assert_same(idx.align_batch(b, hit_cap=1000, kernel="bidirectional"), want,
+                               f"shape {shape} budget {budget}")
+        with pytest.raises(gc.mica().MicaError):
+            idx.set_tuning(bidir_shape=2)
     finally:
         idx.set_tuning()
     rng = np.random.default_rng(9)
