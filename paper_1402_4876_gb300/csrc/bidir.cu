@@ -60,7 +60,9 @@ constexpr uint32_t SCHEME_FREE = 7;         // the single scheme of reads shorte
 constexpr uint32_t BD_BUDGET = 1u << 12;    // node expansions a task may take before it exports its nodes
 constexpr uint32_t BD_VERIFY_MIN = 12;      // matched bases of a one-row node before it is checked against the text
 constexpr uint32_t BD_VERIFY_LEFT = 8;      // ... when at least this many bases are left to match
-constexpr int VCAP = 64;                    // one-row nodes waiting for that check (at most 63: see the round choice)
+constexpr int VCAP = 128;                   // rows waiting for that check (the round choice and the room
+                                            // checks below keep it from overflowing)
+constexpr uint32_t BD_SPLIT_MAX = 8;        // an interval of at most this many rows is checked row by row
 constexpr uint32_t NSLOT_MAX = 64;          // task slots per warp: 32 (one per lane) or 64 (two)
 constexpr uint32_t BD_ADMIT_LOW = 96;       // admit new tasks while fewer items are pending ...
 constexpr uint32_t BD_ADMIT_FREE = 16;      // ... and at least this many slots are free (or nothing is pending)
@@ -129,7 +131,7 @@ template <int SCAP, int NS>
 struct BdSmem {
     uint32_t ml[SCAP], mlr[SCAP], msz[SCAP], mm[SCAP];   // multi-row nodes
     uint32_t sl[SCAP], slr[SCAP], sm[SCAP];              // single-row nodes
-    uint32_t vl[VCAP], vlr[VCAP], vm[VCAP];              // single-row nodes to check against the text
+    uint32_t vl[VCAP], vm[VCAP];                         // rows to check against the text (row, meta)
     uint32_t pat[NS][MAX_WORDS + 1];                  // pattern of each task slot
     // task slot s: read id, info = m | k << 9 | minus << 11 | p << 12 | end of
     // its scheme range << 15, next scheme to seed
@@ -410,41 +412,6 @@ __device__ __forceinline__ uint32_t bd_export_stack(BdSmem<SCAP, NS> &W, const B
     return kept;
 }
 
-// The same for the stack of nodes waiting for the text check ([0, vtop),
-// no overflow part): they leave as single-row nodes.
-template <int SCAP, int NS>
-__device__ __forceinline__ uint32_t bd_export_verify(BdSmem<SCAP, NS> &W, const BidirArgs &a, uint32_t vtop,
-                                                     unsigned long long expm, int lane)
-{
-    const unsigned lt = (1u << lane) - 1u;
-    uint32_t kept = 0;
-    for (uint32_t r0 = 0; r0 < vtop; r0 += 32) {
-        const uint32_t e = r0 + (uint32_t)lane;
-        const bool has = e < vtop;
-        uint32_t l = 0, lr = 0, meta = 0;
-        if (has) { l = W.vl[e]; lr = W.vlr[e]; meta = W.vm[e]; }
-        const uint32_t slot = bm_slot(meta);
-        const bool ex = has && ((expm >> slot) & 1ull);
-        const uint32_t task = ex ? slot_task(W, slot) : 0u;
-        const bool keep = has && !ex;
-        const unsigned em = __ballot_sync(BFULL, ex), km = __ballot_sync(BFULL, keep);
-        uint32_t base = 0;
-        if (em) {
-            if (lane == 0) base = atomicAdd(&a.ctl->fr_count, (unsigned)__popc(em));
-            base = __shfl_sync(BFULL, base, 0);
-        }
-        __syncwarp();   // every lane has read its entry before any is overwritten below
-        if (ex) bd_export_one(a, base + __popc(em & lt), task, l, lr, 1u, meta);
-        if (keep) {
-            const uint32_t o = kept + __popc(km & lt);
-            W.vl[o] = l; W.vlr[o] = lr; W.vm[o] = meta;
-        }
-        kept += __popc(km);
-        __syncwarp();
-    }
-    return kept;
-}
-
 // Room for `add` more nodes on a stack: its oldest nodes go to the warp's
 // overflow stack, or, when that is full, to the frontier buffer as tasks of
 // the next round.
@@ -521,6 +488,24 @@ __device__ __forceinline__ void bd_emit(const BidirArgs &a, uint32_t nleaf, cons
     }
 }
 
+// Rows for the text-check stack: each lane asks for `want` rows (0: none).
+// Lanes are taken in lane order while their rows fit in the stack's room (the
+// taken lanes form a prefix, so their rows lie contiguously from vtop); a
+// lane gets its first position in pos.  vtop grows by the rows taken.
+__device__ __forceinline__ bool bd_take_rows(uint32_t want, uint32_t &vtop, uint32_t &pos, int lane)
+{
+    uint32_t end = want;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(BFULL, end, o);
+        if (lane >= o) end += y;
+    }
+    const bool ok = want > 0 && end <= (uint32_t)VCAP - vtop;
+    pos = vtop + end - want;
+    vtop += __reduce_max_sync(BFULL, ok ? end : 0u);
+    return ok;
+}
+
 template <int SCAP, int WARPS, int MINB, int NS>
 __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
 {
@@ -586,7 +571,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
         if ((iter & 63) == 63 && budget == a.budget) {
             int spent = 0;
             if (lane == 0) spent = *(volatile unsigned long long *)&ctl->task_head >= ntasks;
-            if (__shfl_sync(BFULL, spent, 0)) budget = max(a.budget >> 3, 32u);
+            if (__shfl_sync(BFULL, spent, 0)) budget = max(a.budget >> 3, min(a.budget, 32u));
         }
         // ---- slots over their node budget hand their nodes to the next
         // round (one pass over both stacks), and their schemes not yet seeded
@@ -621,9 +606,17 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
             stop = sbot + bd_export_stack<SCAP, NS, true, false>(W, a, nullptr, sbot, stop, expm, lane);
             if (dmt) dmt = bd_export_stack<SCAP, NS, false, true>(W, a, deep_m, 0, dmt, expm, lane);
             if (dst) dst = bd_export_stack<SCAP, NS, true, true>(W, a, deep_s, 0, dst, expm, lane);
-            if (vtop) vtop = bd_export_verify<SCAP, NS>(W, a, vtop, expm, lane);
-            if (over0) W.live[lane] = 0;   // their nodes are gone: the slots free above
+            if (over0) W.live[lane] = 0;   // their nodes are gone: the slots free above ...
             if (over1) W.live[lane2] = 0;
+            __syncwarp();
+            // ... once the rows they have waiting for the text check are done: those stay here (a row
+            // split from an interval has no row of the reversed genome to travel with)
+            for (uint32_t e = (uint32_t)lane; e < vtop; e += 32) {
+                const uint32_t sl = bm_slot(W.vm[e]);
+                if ((expm >> sl) & 1ull) atomicAdd(&W.live[sl], 1);
+            }
+            if (over0) W.work[lane] = 0;   // (so that this pass does not repeat while they wait)
+            if (over1) W.work[lane2] = 0;
             __syncwarp();
             continue;
         }
@@ -737,8 +730,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
         }
         c_rounds++;
 
-        // (a single-row or seed round moves at most 32 nodes to the text-check
-        // stack and runs only while it holds fewer than 32: it never holds 64)
+        // (rounds other than the text check's run only while fewer than 32
+        // rows wait for it; they add rows only while those fit)
         int kind;
         const bool seed_room = mc + 32 <= (uint32_t)SCAP && sc + 32 <= (uint32_t)SCAP;
         if (vtop >= 32) kind = 3;
@@ -809,14 +802,17 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
             uint32_t cl[4] = {l, 0, 0, 0}, cs[4] = {sz, 0, 0, 0}, cd[4] = {0, 0, 0, 0};
             bd_emit(a, leaf ? 1u : 0u, cl, cs, cd, leaf ? 1u : 0u, W.sread[slot], minus, lane);
             const bool single = sz == 1;
-            // a one-row seed far enough in goes straight to the text check (at
-            // most 32 more: this round runs only while that stack holds fewer than 32)
+            // a seed of a few rows, far enough in, goes straight to the text check row by row
             const uint32_t matched = bm_b(meta) - bm_a(meta);
-            const bool to_v = push && single && a.verify_min && matched >= a.verify_min &&
-                              (info & 511u) - matched >= BD_VERIFY_LEFT;
-            const unsigned bm = __ballot_sync(BFULL, push && !single),
-                           bs = __ballot_sync(BFULL, push && single && !to_v), bv = __ballot_sync(BFULL, to_v);
-            if (push && !single) {
+            const bool checkable = push && a.verify_min && sz <= BD_SPLIT_MAX && matched >= a.verify_min &&
+                                   (info & 511u) - matched >= BD_VERIFY_LEFT;
+            uint32_t vpos = 0;
+            const bool to_v = bd_take_rows(checkable ? sz : 0u, vtop, vpos, lane);
+            if (to_v)
+                for (uint32_t i = 0; i < sz; i++) { W.vl[vpos + i] = l + i; W.vm[vpos + i] = meta; }
+            const unsigned bm = __ballot_sync(BFULL, push && !single && !to_v),
+                           bs = __ballot_sync(BFULL, push && single && !to_v);
+            if (push && !single && !to_v) {
                 uint32_t q = (mtop + __popc(bm & lt)) & (SCAP - 1);
                 W.ml[q] = l; W.mlr[q] = lr; W.msz[q] = sz; W.mm[q] = meta;
             }
@@ -824,14 +820,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
                 uint32_t q = (stop + __popc(bs & lt)) & (SCAP - 1);
                 W.sl[q] = l; W.slr[q] = lr; W.sm[q] = meta;
             }
-            if (to_v) {
-                const uint32_t q = vtop + __popc(bv & lt);
-                W.vl[q] = l; W.vlr[q] = lr; W.vm[q] = meta;
-            }
             mtop += __popc(bm);
             stop += __popc(bs);
-            vtop += __popc(bv);
-            if (push) atomicAdd(&W.live[slot], 1);
+            if (push) atomicAdd(&W.live[slot], to_v ? (int)sz : 1);
         } else if (kind == 1) {
             // ---- single-row nodes: the one possible child is the row's symbol
             const uint32_t npop = min(sc, 32u);
@@ -850,14 +841,11 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
             uint32_t nl = l, nlr = lr, nmeta = 0, dn = 0;
             // a node far enough in (and far enough from the end) goes to the text check
             const uint32_t matched = bm_b(meta) - bm_a(meta);
-            const bool to_v = has && a.verify_min && matched >= a.verify_min &&
-                              (info & 511u) - matched >= BD_VERIFY_LEFT;
-            const unsigned vmask = __ballot_sync(BFULL, to_v);
-            if (to_v) {
-                const uint32_t q = vtop + __popc(vmask & lt);
-                W.vl[q] = l; W.vlr[q] = lr; W.vm[q] = meta;
-            }
-            vtop += __popc(vmask);
+            const bool checkable = has && a.verify_min && matched >= a.verify_min &&
+                                   (info & 511u) - matched >= BD_VERIFY_LEFT;
+            uint32_t vpos = 0;
+            const bool to_v = bd_take_rows(checkable ? 1u : 0u, vtop, vpos, lane);
+            if (to_v) { W.vl[vpos] = l; W.vm[vpos] = meta; }
             const bool live_node = has && !to_v;
             if (live_node) atomicAdd(&W.work[slot], 1u);
             if (live_node) {
@@ -945,12 +933,15 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
             uint32_t cl[4] = {0, 0, 0, 0}, clr[4] = {0, 0, 0, 0}, cs[4] = {0, 0, 0, 0}, cd[4] = {0, 0, 0, 0};
             uint32_t cmeta[4] = {0, 0, 0, 0};
             uint32_t leafmask = 0, nodemask = 0;
+            uint32_t cmatched = 0, cleft = 0;                // the children's matched bases and bases to go
             const bool live_node = has;
             if (has) atomicAdd(&W.work[slot], 1u);
             if (live_node) {
                 const uint32_t m = info & 511u, k = (info >> 9) & 3u;
                 const uint32_t A = bm_a(meta), B = bm_b(meta), d = bm_d(meta), d0 = bm_d0(meta), j = bm_j(meta);
                 const bool left = A > 0;
+                cmatched = B - A + 1;
+                cleft = m - cmatched;
                 const OccSide &sd = left ? a.fwd : a.rev;
                 const uint32_t pl = left ? l : lr;          // interval on the side being extended
                 uint32_t ol[4], orr[4];
@@ -979,6 +970,20 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
                 }
             }
             bd_emit(a, (uint32_t)__popc(leafmask), cl, cs, cd, leafmask, rid, (info >> 11) & 1u, lane);
+            // children of a few rows, far enough in, go to the text check row by row
+            uint32_t smask = 0, want = 0;
+            if (a.verify_min && cmatched >= a.verify_min && cleft >= BD_VERIFY_LEFT) {
+#pragma unroll
+                for (int c = 0; c < 4; c++)
+                    if ((nodemask >> c & 1u) && cs[c] <= BD_SPLIT_MAX) { smask |= 1u << c; want += cs[c]; }
+            }
+            uint32_t vpos = 0;
+            if (!bd_take_rows(want, vtop, vpos, lane)) { smask = 0; want = 0; }
+#pragma unroll
+            for (int c = 0; c < 4; c++)
+                if (smask >> c & 1u)
+                    for (uint32_t i = 0; i < cs[c]; i++) { W.vl[vpos] = cl[c] + i; W.vm[vpos] = cmeta[c]; vpos++; }
+            nodemask &= ~smask;
             uint32_t nm = 0, ns = 0;
 #pragma unroll
             for (int c = 0; c < 4; c++)
@@ -1013,7 +1018,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
             }
             mtop += tm;
             stop += ts;
-            const int delta = (int)(nm + ns) - 1;
+            const int delta = (int)(nm + ns + want) - 1;
             if (has && delta) atomicAdd(&W.live[slot], delta);
         }
         __syncwarp();

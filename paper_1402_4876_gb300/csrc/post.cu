@@ -22,6 +22,8 @@ constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 constexpr uint32_t SMALL_SORT = 32;
 constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t SMEM_SORT = 4096;
+constexpr uint32_t WARP_SORT = 1024;           // reads up to this many hits: one warp sorts each
+constexpr uint32_t WARP_SORT_WARPS = 4;        // warps per block of k_sort_warp (8 KB of shared memory each)
 
 // ---- exclusive scan (n values -> n + 1 offsets) ----
 
@@ -400,7 +402,47 @@ __global__ void k_sort_small(uint64_t *__restrict__ hits, const uint64_t *__rest
     }
 }
 
-// bitonic sort of one read's hits in shared memory (<= SMEM_SORT)
+// bitonic sort of one read's hits by one warp in its part of shared memory
+// (SMALL_SORT < hits <= WARP_SORT; larger listed reads are left to k_sort_big):
+// the keys padded to a power of two P, log2(P) (log2(P) + 1) / 2 phases of
+// compare-exchanges, each lane taking every 32nd pair, a warp barrier between
+// phases
+__global__ void __launch_bounds__(WARP_SORT_WARPS * 32) k_sort_warp(uint64_t *__restrict__ hits,
+                                                                    const uint64_t *__restrict__ hit_off,
+                                                                    const uint32_t *__restrict__ big,
+                                                                    const unsigned int *__restrict__ nbig_p)
+{
+    __shared__ uint64_t shw[WARP_SORT_WARPS][WARP_SORT];
+    const unsigned lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    uint64_t *sh = shw[wi];
+    const unsigned nbig = *nbig_p;
+    const unsigned warps = gridDim.x * WARP_SORT_WARPS;
+    for (unsigned bi = blockIdx.x * WARP_SORT_WARPS + wi; bi < nbig; bi += warps) {
+        const uint32_t r = big[bi];
+        const uint64_t b = hit_off[r], cnt = hit_off[r + 1] - b;
+        if (cnt > WARP_SORT) continue;
+        uint32_t P = 1;
+        while (P < cnt) P <<= 1;
+        // the packed hits themselves (below 2^48), padded with ~0, ordered by (pos, strand)
+        for (uint32_t i = lane; i < P; i += 32) sh[i] = i < cnt ? hits[b + i] : ~0ull;
+        __syncwarp();
+        for (uint32_t kk = 2; kk <= P; kk <<= 1)
+            for (uint32_t jj = kk >> 1; jj > 0; jj >>= 1) {
+                for (uint32_t t = lane; t < P / 2; t += 32) {
+                    // the t-th pair (i, i ^ jj) with i's jj bit clear
+                    const uint32_t i = ((t & ~(jj - 1)) << 1) | (t & (jj - 1)), q = i ^ jj;
+                    const uint64_t x = sh[i], y = sh[q];
+                    const uint64_t kx = x == ~0ull ? ~0ull : hit_key(x), ky = y == ~0ull ? ~0ull : hit_key(y);
+                    if ((kx > ky) == ((i & kk) == 0)) { sh[i] = y; sh[q] = x; }
+                }
+                __syncwarp();
+            }
+        for (uint32_t i = lane; i < cnt; i += 32) hits[b + i] = sh[i];
+        __syncwarp();
+    }
+}
+
+// bitonic sort of one read's hits in shared memory (WARP_SORT < hits <= SMEM_SORT)
 __global__ void __launch_bounds__(512) k_sort_big(uint64_t *__restrict__ hits, const uint64_t *__restrict__ hit_off,
                                                   const uint32_t *__restrict__ big, const unsigned int *__restrict__ nbig_p)
 {
@@ -409,6 +451,7 @@ __global__ void __launch_bounds__(512) k_sort_big(uint64_t *__restrict__ hits, c
     for (unsigned bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
         uint32_t r = big[bi];
         uint64_t b = hit_off[r], cnt = hit_off[r + 1] - b;
+        if (cnt <= WARP_SORT) continue;   // sorted by k_sort_warp
         uint32_t P = 1;
         while (P < cnt) P <<= 1;
         for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) sh[i] = i < cnt ? hits[b + i] : ~0ull;
@@ -575,8 +618,10 @@ int enqueue_post_device(const mica_index *idx, Workspace &w, const ReadsView &rd
     k_locate<<<G, 256, 0, s>>>(idx->view, (Hit *)w.hits.p, hit_off + n, hit_capacity, steps, &ctl->error);
     k_sort_small<<<grid1(n, 128), 128, 0, s>>>((uint64_t *)w.hits.p, hit_off, n, hit_capacity, (uint32_t *)w.big.p,
                                                nbig);
+    k_sort_warp<<<152 * 4, WARP_SORT_WARPS * 32, 0, s>>>((uint64_t *)w.hits.p, hit_off, (const uint32_t *)w.big.p,
+                                                        nbig);
     k_sort_big<<<152 * 4, 512, 0, s>>>((uint64_t *)w.hits.p, hit_off, (const uint32_t *)w.big.p, nbig);
-    L += 4;
+    L += 5;
     char *st = (char *)status;
     MICA_CUDA_TRY(cudaMemcpyAsync(st, ctl, sizeof(SearchCtl), cudaMemcpyDeviceToHost, s));
     MICA_CUDA_TRY(cudaMemcpyAsync(st + sizeof(SearchCtl), hit_off + n, 8, cudaMemcpyDeviceToHost, s));
@@ -658,9 +703,11 @@ int run_post(const mica_index *idx, Workspace &w, mica_stats &stt, const ReadsVi
     MICA_CUDA_TRY(cudaMemcpyAsync(hb, nbig, 8, cudaMemcpyDeviceToHost, s));
     MICA_CUDA_TRY(cudaStreamSynchronize(s));
     if (hb[0]) {
+        k_sort_warp<<<std::min((hb[0] + WARP_SORT_WARPS - 1) / WARP_SORT_WARPS, 152u * 4), WARP_SORT_WARPS * 32, 0,
+                      s>>>((uint64_t *)w.hits.p, hit_off, (const uint32_t *)w.big.p, nbig);
         k_sort_big<<<std::min(hb[0], 152u * 4), 512, 0, s>>>((uint64_t *)w.hits.p, hit_off,
                                                            (const uint32_t *)w.big.p, nbig);
-        L++;
+        L += 2;
     }
     if (hb[1]) {
         // reads above the shared-memory size (only without a cap or with a cap above it)
