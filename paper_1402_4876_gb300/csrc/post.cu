@@ -22,8 +22,9 @@ constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 constexpr uint32_t SMALL_SORT = 32;
 constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t SMEM_SORT = 4096;
-constexpr uint32_t WARP_SORT = 1024;           // reads up to this many hits: one warp sorts each
-constexpr uint32_t WARP_SORT_WARPS = 4;        // warps per block of k_sort_warp (8 KB of shared memory each)
+constexpr uint32_t WARP_SORT = 256;            // reads up to this many hits: one warp sorts each ...
+constexpr uint32_t WARP_SORT_WARPS = 8;        // ... 8 warps per block (2 KB of shared memory each);
+constexpr uint32_t BLOCK_SORT_THREADS = 128;   // larger ones (up to SMEM_SORT): a block of 128 threads each
 
 // ---- exclusive scan (n values -> n + 1 offsets) ----
 
@@ -402,22 +403,58 @@ __global__ void k_sort_small(uint64_t *__restrict__ hits, const uint64_t *__rest
     }
 }
 
-// bitonic sort of one read's hits by one warp in its part of shared memory
-// (SMALL_SORT < hits <= WARP_SORT; larger listed reads are left to k_sort_big):
-// the keys padded to a power of two P, log2(P) (log2(P) + 1) / 2 phases of
-// compare-exchanges, each lane taking every 32nd pair, a warp barrier between
-// phases
+// Bitonic sort of the packed hits sh[0, P) (P a power of two, padding ~0 last)
+// by (pos, strand), by the `nt` threads numbered `tid` of a warp (BLOCK false)
+// or a block (true), which meet at a barrier between phases: log2(P) (log2(P)
+// + 1) / 2 phases, each thread taking every nt-th compare-exchange pair
+// (i, i ^ jj) with i's jj bit clear (the pairs of a phase are disjoint); a
+// thread loads up to four pairs before it compares and stores any of them.
+template <bool BLOCK>
+__device__ __forceinline__ void bitonic_hits(uint64_t *sh, uint32_t P, uint32_t tid, uint32_t nt)
+{
+    for (uint32_t kk = 2; kk <= P; kk <<= 1)
+        for (uint32_t jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (uint32_t t0 = tid; t0 < P / 2; t0 += 4 * nt) {
+                uint32_t ii[4];
+                uint64_t xs[4], ys[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const uint32_t t = t0 + (uint32_t)u * nt;
+                    ii[u] = ((t & ~(jj - 1)) << 1) | (t & (jj - 1));
+                    if (t < P / 2) { xs[u] = sh[ii[u]]; ys[u] = sh[ii[u] ^ jj]; }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const uint32_t t = t0 + (uint32_t)u * nt;
+                    if (t < P / 2) {
+                        const uint64_t kx = xs[u] == ~0ull ? ~0ull : hit_key(xs[u]);
+                        const uint64_t ky = ys[u] == ~0ull ? ~0ull : hit_key(ys[u]);
+                        if ((kx > ky) == ((ii[u] & kk) == 0)) { sh[ii[u]] = ys[u]; sh[ii[u] ^ jj] = xs[u]; }
+                    }
+                }
+            }
+            if (BLOCK) __syncthreads(); else __syncwarp();
+        }
+}
+
+// Reads with SMALL_SORT < hits <= WARP_SORT: one warp each, taken from the
+// listed reads by a counter (reads differ a lot in size: a fixed stride left
+// one warp with the largest); larger listed reads are left to k_sort_block.
 __global__ void __launch_bounds__(WARP_SORT_WARPS * 32) k_sort_warp(uint64_t *__restrict__ hits,
                                                                     const uint64_t *__restrict__ hit_off,
                                                                     const uint32_t *__restrict__ big,
-                                                                    const unsigned int *__restrict__ nbig_p)
+                                                                    const unsigned int *__restrict__ nbig_p,
+                                                                    unsigned int *__restrict__ next)
 {
     __shared__ uint64_t shw[WARP_SORT_WARPS][WARP_SORT];
     const unsigned lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     uint64_t *sh = shw[wi];
     const unsigned nbig = *nbig_p;
-    const unsigned warps = gridDim.x * WARP_SORT_WARPS;
-    for (unsigned bi = blockIdx.x * WARP_SORT_WARPS + wi; bi < nbig; bi += warps) {
+    for (;;) {
+        unsigned bi = 0;
+        if (lane == 0) bi = atomicAdd(next, 1u);
+        bi = __shfl_sync(0xffffffffu, bi, 0);
+        if (bi >= nbig) break;
         const uint32_t r = big[bi];
         const uint64_t b = hit_off[r], cnt = hit_off[r + 1] - b;
         if (cnt > WARP_SORT) continue;
@@ -426,49 +463,37 @@ __global__ void __launch_bounds__(WARP_SORT_WARPS * 32) k_sort_warp(uint64_t *__
         // the packed hits themselves (below 2^48), padded with ~0, ordered by (pos, strand)
         for (uint32_t i = lane; i < P; i += 32) sh[i] = i < cnt ? hits[b + i] : ~0ull;
         __syncwarp();
-        for (uint32_t kk = 2; kk <= P; kk <<= 1)
-            for (uint32_t jj = kk >> 1; jj > 0; jj >>= 1) {
-                for (uint32_t t = lane; t < P / 2; t += 32) {
-                    // the t-th pair (i, i ^ jj) with i's jj bit clear
-                    const uint32_t i = ((t & ~(jj - 1)) << 1) | (t & (jj - 1)), q = i ^ jj;
-                    const uint64_t x = sh[i], y = sh[q];
-                    const uint64_t kx = x == ~0ull ? ~0ull : hit_key(x), ky = y == ~0ull ? ~0ull : hit_key(y);
-                    if ((kx > ky) == ((i & kk) == 0)) { sh[i] = y; sh[q] = x; }
-                }
-                __syncwarp();
-            }
+        bitonic_hits<false>(sh, P, lane, 32);
         for (uint32_t i = lane; i < cnt; i += 32) hits[b + i] = sh[i];
         __syncwarp();
     }
 }
 
-// bitonic sort of one read's hits in shared memory (WARP_SORT < hits <= SMEM_SORT)
-__global__ void __launch_bounds__(512) k_sort_big(uint64_t *__restrict__ hits, const uint64_t *__restrict__ hit_off,
-                                                  const uint32_t *__restrict__ big, const unsigned int *__restrict__ nbig_p)
+// Reads with WARP_SORT < hits <= SMEM_SORT: one block of 128 threads each,
+// taken by a counter.
+__global__ void __launch_bounds__(BLOCK_SORT_THREADS) k_sort_block(uint64_t *__restrict__ hits,
+                                                                   const uint64_t *__restrict__ hit_off,
+                                                                   const uint32_t *__restrict__ big,
+                                                                   const unsigned int *__restrict__ nbig_p,
+                                                                   unsigned int *__restrict__ next)
 {
     __shared__ uint64_t sh[SMEM_SORT];
-    unsigned nbig = *nbig_p;
-    for (unsigned bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
-        uint32_t r = big[bi];
-        uint64_t b = hit_off[r], cnt = hit_off[r + 1] - b;
-        if (cnt <= WARP_SORT) continue;   // sorted by k_sort_warp
+    __shared__ unsigned bi_s;
+    const unsigned nbig = *nbig_p;
+    for (;;) {
+        if (threadIdx.x == 0) bi_s = atomicAdd(next, 1u);
+        __syncthreads();
+        const unsigned bi = bi_s;
+        __syncthreads();
+        if (bi >= nbig) break;
+        const uint32_t r = big[bi];
+        const uint64_t b = hit_off[r], cnt = hit_off[r + 1] - b;
+        if (cnt <= WARP_SORT) continue;
         uint32_t P = 1;
         while (P < cnt) P <<= 1;
         for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) sh[i] = i < cnt ? hits[b + i] : ~0ull;
         __syncthreads();
-        for (uint32_t kk = 2; kk <= P; kk <<= 1)
-            for (uint32_t jj = kk >> 1; jj > 0; jj >>= 1) {
-                for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
-                    uint32_t p = i ^ jj;
-                    if (p > i) {
-                        uint64_t x = sh[i], y = sh[p];
-                        bool up = (i & kk) == 0;
-                        uint64_t kx = x == ~0ull ? ~0ull : hit_key(x), ky = y == ~0ull ? ~0ull : hit_key(y);
-                        if ((kx > ky) == up) { sh[i] = y; sh[p] = x; }
-                    }
-                }
-                __syncthreads();
-            }
+        bitonic_hits<true>(sh, P, threadIdx.x, blockDim.x);
         for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) hits[b + i] = sh[i];
         __syncthreads();
     }
@@ -558,13 +583,15 @@ static uint64_t big_list_bytes(uint64_t n)
 }
 
 // w.big holds: the sort lists (n u32), 64 bytes of counters (locate steps
-// u64, sort-list counts u32[2], many-interval count u32), then the list of
-// reads with many intervals (n u32).
+// u64, sort-list counts u32[2], many-interval count u32, the two sort
+// kernels' next-read counters u32[2]), then the list of reads with many
+// intervals (n u32).
 struct PostLists {
     uint32_t *sort_lists;
     unsigned long long *steps;
-    unsigned int *nbig;       // [0] reads for the shared-memory sort, [1] above it
+    unsigned int *nbig;       // [0] reads for the shared-memory sorts, [1] above them
     unsigned int *n_many;
+    unsigned int *sort_next;  // [0] k_sort_warp's next listed read, [1] k_sort_block's
     uint32_t *many;
 };
 
@@ -578,6 +605,7 @@ static PostLists post_lists(Workspace &w, uint64_t n)
     p.steps = (unsigned long long *)(base + big_list_bytes(n));
     p.nbig = (unsigned int *)(p.steps + 1);
     p.n_many = p.nbig + 2;
+    p.sort_next = p.nbig + 3;
     p.many = (uint32_t *)(base + big_list_bytes(n) + 64);
     return p;
 }
@@ -619,8 +647,9 @@ int enqueue_post_device(const mica_index *idx, Workspace &w, const ReadsView &rd
     k_sort_small<<<grid1(n, 128), 128, 0, s>>>((uint64_t *)w.hits.p, hit_off, n, hit_capacity, (uint32_t *)w.big.p,
                                                nbig);
     k_sort_warp<<<152 * 4, WARP_SORT_WARPS * 32, 0, s>>>((uint64_t *)w.hits.p, hit_off, (const uint32_t *)w.big.p,
-                                                        nbig);
-    k_sort_big<<<152 * 4, 512, 0, s>>>((uint64_t *)w.hits.p, hit_off, (const uint32_t *)w.big.p, nbig);
+                                                        nbig, pl.sort_next);
+    k_sort_block<<<152 * 8, BLOCK_SORT_THREADS, 0, s>>>((uint64_t *)w.hits.p, hit_off, (const uint32_t *)w.big.p,
+                                                        nbig, pl.sort_next + 1);
     L += 5;
     char *st = (char *)status;
     MICA_CUDA_TRY(cudaMemcpyAsync(st, ctl, sizeof(SearchCtl), cudaMemcpyDeviceToHost, s));
@@ -704,9 +733,9 @@ int run_post(const mica_index *idx, Workspace &w, mica_stats &stt, const ReadsVi
     MICA_CUDA_TRY(cudaStreamSynchronize(s));
     if (hb[0]) {
         k_sort_warp<<<std::min((hb[0] + WARP_SORT_WARPS - 1) / WARP_SORT_WARPS, 152u * 4), WARP_SORT_WARPS * 32, 0,
-                      s>>>((uint64_t *)w.hits.p, hit_off, (const uint32_t *)w.big.p, nbig);
-        k_sort_big<<<std::min(hb[0], 152u * 4), 512, 0, s>>>((uint64_t *)w.hits.p, hit_off,
-                                                           (const uint32_t *)w.big.p, nbig);
+                      s>>>((uint64_t *)w.hits.p, hit_off, (const uint32_t *)w.big.p, nbig, pl.sort_next);
+        k_sort_block<<<std::min(hb[0], 152u * 8), BLOCK_SORT_THREADS, 0, s>>>(
+            (uint64_t *)w.hits.p, hit_off, (const uint32_t *)w.big.p, nbig, pl.sort_next + 1);
         L += 2;
     }
     if (hb[1]) {
