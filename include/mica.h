@@ -320,10 +320,12 @@ int mica_get_tuning(const mica_index *idx, mica_tuning *t);
    call starts afresh.  Small values exist to exercise that path. */
 int mica_set_wait_limits(mica_index *idx, uint32_t idle_rounds, uint32_t ring_spins);
 
-/* Autotuner: time every persistent kernel shape and the plain kernel's block
-   size (over the batch and per read-length class, on that class's reads) on
-   a host sample batch, `repeats` timed runs after one warm-up each, and keep
-   the fastest in the index's tuning (also copied to *out unless NULL). */
+/* Autotuner: time every bidirectional kernel shape with node budgets of 1024
+   and 4096 (when the index has the reversed genome's table), every persistent
+   kernel shape and the plain kernel's block size (over the batch and per
+   read-length class, on that class's reads) on a host sample batch, `repeats`
+   timed runs after one warm-up each, and keep the fastest in the index's
+   tuning (also copied to *out unless NULL). */
 int mica_autotune(mica_index *idx, const uint32_t *packed_reads, const uint64_t *word_offsets,
                   const uint16_t *lengths, const uint8_t *k, uint64_t n_reads, uint32_t hit_cap, uint32_t repeats,
                   mica_tuning *out);

@@ -1,6 +1,7 @@
-// Autotuner for the search launch: times the compiled persistent-kernel
-// shapes and the plain kernel's block size per read-length class on a sample
-// batch and keeps the fastest in the index's tuning.  Tuning never changes
+// Autotuner for the search launch: times the bidirectional kernel's compiled
+// shapes and node budgets, the persistent kernel's shapes and the plain
+// kernel's block size per read-length class on a sample batch and keeps the
+// fastest in the index's tuning.  Tuning never changes
 // results, only speed.  A small text cache keyed by (GPU name, genome length,
 // length classes present, largest k) lets a later process skip the timing.
 #include <stdio.h>
@@ -92,8 +93,24 @@ int mica_autotune(mica_index *idx, const uint32_t *packed_reads, const uint64_t 
     {
         DeviceBatch all;
         if ((rc = all.upload(packed_reads, word_offsets, lengths, k, n_reads))) goto done;
-        // persistent shapes
         float tbest = 1e30f;
+        // bidirectional shapes (task slots and warps per CTA) and node budgets
+        if (bidir_available(idx)) {
+            const uint32_t budgets[] = {1024, 4096};
+            for (int s = 0; s < bidir_shape_count(); s++)
+                for (uint32_t b : budgets) {
+                    idx->tuning.bidir_shape = s;
+                    idx->tuning.bidir_budget = b;
+                    float t;
+                    if ((rc = time_search(idx, ws, all.view, MICA_KERNEL_BIDIRECTIONAL, hit_cap, repeats, &t)))
+                        goto done;
+                    if (t < tbest) { tbest = t; best.bidir_shape = s; best.bidir_budget = b; }
+                }
+            idx->tuning.bidir_shape = best.bidir_shape;
+            idx->tuning.bidir_budget = best.bidir_budget;
+        }
+        // persistent shapes
+        tbest = 1e30f;
         for (int s = 0; s < search_shape_count(); s++) {
             idx->tuning.shape = s;
             float t;

@@ -440,9 +440,10 @@ def test_autotune_cache_and_results_unchanged(tmp_path):
         assert 0 <= t["shape"] < len(m.tuning_shapes())
         assert t["plain_block"] in (64, 128, 256, 512)
         assert all(x in (64, 128, 256, 512) for x in t["plain_block_len"])    # all four classes present
+        assert t["bidir_shape"] in (0, 1) and t["bidir_budget"] in (1024, 4096)
         idx.set_tuning()
         assert idx.autotune(b, cache=cache) == t                               # served from the cache
-        for kernel in ("persistent", "plain", "plain_by_length"):
+        for kernel in ("persistent", "plain", "plain_by_length", "bidirectional"):
             gc.assert_same(idx.align_batch(b, hit_cap=1000, kernel=kernel), ref, kernel)
     finally:
         idx.set_tuning()
