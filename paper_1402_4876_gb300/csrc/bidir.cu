@@ -63,6 +63,7 @@ constexpr uint32_t BD_VERIFY_LEFT = 8;      // ... when at least this many bases
 constexpr int VCAP = 128;                   // rows waiting for that check (the round choice and the room
                                             // checks below keep it from overflowing)
 constexpr uint32_t BD_SPLIT_MAX = 8;        // an interval of at most this many rows is checked row by row
+constexpr uint32_t BD_CHAIN = 16;           // extension steps a lane may take on one multi-row node in a round
 constexpr uint32_t NSLOT_MAX = 64;          // task slots per warp: 32 (one per lane) or 64 (two)
 constexpr uint32_t BD_ADMIT_LOW = 96;       // admit new tasks while fewer items are pending ...
 constexpr uint32_t BD_ADMIT_FREE = 16;      // ... and at least this many slots are free (or nothing is pending)
@@ -930,8 +931,16 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
             if (has) atomicAdd(&W.live[slot], -1);
         } else {
             // ---- multi-row nodes: counts of all four symbols at both ends
+            // A node whose one child left to push has several rows (a chain
+            // through a repeat: the read's base continues, the few rows that
+            // differ go to the text check) is extended again in the same
+            // round, up to CHAIN steps, instead of a push and a pop per step;
+            // only while the next multi-row round would have idle lanes anyway,
+            // and only in the 64-slot shape (an HBM-resident index: heavier
+            // trees, fuller rounds, and a step that waits longer on memory).
+            constexpr uint32_t CHAIN = TWO ? BD_CHAIN : 1u;
             const uint32_t npop = min(mc, 32u);
-            const bool has = (uint32_t)lane < npop;
+            bool has = (uint32_t)lane < npop;
             uint32_t l = 0, lr = 0, sz = 0, meta = 0;
             if (has) {
                 uint32_t q = (mtop - 1 - lane) & (SCAP - 1);
@@ -939,99 +948,118 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_bidir(BidirArgs a)
             }
             mtop -= npop;
             __syncwarp();
-            const uint32_t slot = bm_slot(meta);
-            const uint32_t info = W.sinfo[slot];
-            const uint32_t rid = W.sread[slot];
-            uint32_t cl[4] = {0, 0, 0, 0}, clr[4] = {0, 0, 0, 0}, cs[4] = {0, 0, 0, 0}, cd[4] = {0, 0, 0, 0};
-            uint32_t cmeta[4] = {0, 0, 0, 0};
-            uint32_t leafmask = 0, nodemask = 0;
-            uint32_t cmatched = 0, cleft = 0;                // the children's matched bases and bases to go
-            const bool live_node = has;
-            if (has) atomicAdd(&W.work[slot], 1u);
-            if (live_node) {
-                const uint32_t m = info & 511u, k = (info >> 9) & 3u;
-                const uint32_t A = bm_a(meta), B = bm_b(meta), d = bm_d(meta), d0 = bm_d0(meta), j = bm_j(meta);
-                const bool left = A > 0;
-                cmatched = B - A + 1;
-                cleft = m - cmatched;
-                const OccSide &sd = left ? a.fwd : a.rev;
-                const uint32_t pl = left ? l : lr;          // interval on the side being extended
-                uint32_t ol[4], orr[4];
-                c_blocks += occ_pair(sd, pl, pl + sz, ol, orr);
-                c_nodes++;
-                const uint32_t pos = left ? A - 1 : B;
-                const uint32_t base = pat_base(W.pat[slot], pos);
-                const uint32_t nA = left ? pos : 0, nB = left ? B : pos + 1;
-                // the other side's interval start: rows of lower symbols (and a $) come first
-                uint32_t acc = (left ? lr : l) + ((sd.dollar_row >= pl && sd.dollar_row < pl + sz) ? 1u : 0u);
+            for (uint32_t step = 0; step < CHAIN; step++) {
+                const uint32_t slot = bm_slot(meta);
+                const uint32_t info = W.sinfo[slot];
+                const uint32_t rid = W.sread[slot];
+                uint32_t cl[4] = {0, 0, 0, 0}, clr[4] = {0, 0, 0, 0}, cs[4] = {0, 0, 0, 0}, cd[4] = {0, 0, 0, 0};
+                uint32_t cmeta[4] = {0, 0, 0, 0};
+                uint32_t leafmask = 0, nodemask = 0;
+                uint32_t cmatched = 0, cleft = 0;                // the children's matched bases and bases to go
+                const bool live_node = has;
+                if (has) atomicAdd(&W.work[slot], 1u);
+                if (live_node) {
+                    const uint32_t m = info & 511u, k = (info >> 9) & 3u;
+                    const uint32_t A = bm_a(meta), B = bm_b(meta), d = bm_d(meta), d0 = bm_d0(meta), j = bm_j(meta);
+                    const bool left = A > 0;
+                    cmatched = B - A + 1;
+                    cleft = m - cmatched;
+                    const OccSide &sd = left ? a.fwd : a.rev;
+                    const uint32_t pl = left ? l : lr;          // interval on the side being extended
+                    uint32_t ol[4], orr[4];
+                    c_blocks += occ_pair(sd, pl, pl + sz, ol, orr);
+                    c_nodes++;
+                    const uint32_t pos = left ? A - 1 : B;
+                    const uint32_t base = pat_base(W.pat[slot], pos);
+                    const uint32_t nA = left ? pos : 0, nB = left ? B : pos + 1;
+                    // the other side's interval start: rows of lower symbols (and a $) come first
+                    uint32_t acc = (left ? lr : l) + ((sd.dollar_row >= pl && sd.dollar_row < pl + sz) ? 1u : 0u);
 #pragma unroll
-                for (int c = 0; c < 4; c++) {
-                    const uint32_t n_c = orr[c] - ol[c];
-                    const uint32_t cost = (uint32_t)c != base ? 1u : 0u;
-                    uint32_t d0n;
-                    if (n_c > 0 && bd_allowed(j, A, pos, W.bounds[slot], k, d, d0, cost, d0n)) {
-                        const uint32_t start = side_C(sd, c) + ol[c];
-                        cl[c] = left ? start : acc;
-                        clr[c] = left ? acc : start;
-                        cs[c] = n_c;
-                        cd[c] = d + cost;
-                        if (nA == 0 && nB == m) leafmask |= 1u << c;
-                        else { nodemask |= 1u << c; cmeta[c] = bd_meta(slot, nA, nB, d + cost, d0n, j); }
+                    for (int c = 0; c < 4; c++) {
+                        const uint32_t n_c = orr[c] - ol[c];
+                        const uint32_t cost = (uint32_t)c != base ? 1u : 0u;
+                        uint32_t d0n;
+                        if (n_c > 0 && bd_allowed(j, A, pos, W.bounds[slot], k, d, d0, cost, d0n)) {
+                            const uint32_t start = side_C(sd, c) + ol[c];
+                            cl[c] = left ? start : acc;
+                            clr[c] = left ? acc : start;
+                            cs[c] = n_c;
+                            cd[c] = d + cost;
+                            if (nA == 0 && nB == m) leafmask |= 1u << c;
+                            else { nodemask |= 1u << c; cmeta[c] = bd_meta(slot, nA, nB, d + cost, d0n, j); }
+                        }
+                        acc += n_c;
                     }
-                    acc += n_c;
                 }
-            }
-            bd_emit(a, (uint32_t)__popc(leafmask), cl, cs, cd, leafmask, rid, (info >> 11) & 1u, lane);
-            // children of a few rows, far enough in, go to the text check row by row
-            uint32_t smask = 0, want = 0;
-            if (a.verify_min && cmatched >= a.verify_min && cleft >= BD_VERIFY_LEFT) {
+                bd_emit(a, (uint32_t)__popc(leafmask), cl, cs, cd, leafmask, rid, (info >> 11) & 1u, lane);
+                // children of a few rows, far enough in, go to the text check row by row
+                uint32_t smask = 0, want = 0;
+                if (a.verify_min && cmatched >= a.verify_min && cleft >= BD_VERIFY_LEFT) {
+#pragma unroll
+                    for (int c = 0; c < 4; c++)
+                        if ((nodemask >> c & 1u) && cs[c] <= BD_SPLIT_MAX) { smask |= 1u << c; want += cs[c]; }
+                }
+                uint32_t vpos = 0;
+                if (!bd_take_rows(want, vtop, vpos, lane)) { smask = 0; want = 0; }
 #pragma unroll
                 for (int c = 0; c < 4; c++)
-                    if ((nodemask >> c & 1u) && cs[c] <= BD_SPLIT_MAX) { smask |= 1u << c; want += cs[c]; }
-            }
-            uint32_t vpos = 0;
-            if (!bd_take_rows(want, vtop, vpos, lane)) { smask = 0; want = 0; }
+                    if (smask >> c & 1u)
+                        for (uint32_t i = 0; i < cs[c]; i++) { W.vl[vpos] = cl[c] + i; W.vm[vpos] = cmeta[c]; vpos++; }
+                nodemask &= ~smask;
+                bool cont = false;
+                uint32_t nl = 0, nlr = 0, nsz = 0, nmeta = 0;
+                if (step + 1 < CHAIN) {
 #pragma unroll
-            for (int c = 0; c < 4; c++)
-                if (smask >> c & 1u)
-                    for (uint32_t i = 0; i < cs[c]; i++) { W.vl[vpos] = cl[c] + i; W.vm[vpos] = cmeta[c]; vpos++; }
-            nodemask &= ~smask;
-            uint32_t nm = 0, ns = 0;
+                    for (int c = 0; c < 4; c++)
+                        if (nodemask == (1u << c) && cs[c] > 1) {
+                            cont = true; nl = cl[c]; nlr = clr[c]; nsz = cs[c]; nmeta = cmeta[c];
+                        }
+                    cont = cont && W.work[slot] < budget;
+                    // only while the next multi-row round would have idle lanes anyway
+                    if ((mtop - mbot) + dmt + __popc(__ballot_sync(BFULL, cont)) > 32u) cont = false;
+                    if (cont) nodemask = 0;
+                }
+                uint32_t nm = 0, ns = 0;
 #pragma unroll
-            for (int c = 0; c < 4; c++)
-                if (nodemask >> c & 1u) { if (cs[c] == 1) ns++; else nm++; }
-            uint32_t packed = nm | (ns << 8), pre = packed;
+                for (int c = 0; c < 4; c++)
+                    if (nodemask >> c & 1u) { if (cs[c] == 1) ns++; else nm++; }
+                uint32_t packed = nm | (ns << 8), pre = packed;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(BFULL, pre, o);
-                if (lane >= o) pre += y;
-            }
-            const uint32_t tot = __shfl_sync(BFULL, pre, 31);
-            pre -= packed;
-            const uint32_t tm = tot & 0xffu, ts = tot >> 8;
-            if (tm | ts) {
-                if (tm) bd_make_room<SCAP, NS, false>(W, a, deep_m, dmt, mbot, mtop, tm, lane, c_deep);
-                if (ts) bd_make_room<SCAP, NS, true>(W, a, deep_s, dst, sbot, stop, ts, lane, c_deep);
-            }
-            if (nm | ns) {
-                uint32_t pm = mtop + (pre & 0xffu), ps = stop + (pre >> 8);
+                for (int o = 1; o < 32; o <<= 1) {
+                    uint32_t y = __shfl_up_sync(BFULL, pre, o);
+                    if (lane >= o) pre += y;
+                }
+                const uint32_t tot = __shfl_sync(BFULL, pre, 31);
+                pre -= packed;
+                const uint32_t tm = tot & 0xffu, ts = tot >> 8;
+                if (tm | ts) {
+                    if (tm) bd_make_room<SCAP, NS, false>(W, a, deep_m, dmt, mbot, mtop, tm, lane, c_deep);
+                    if (ts) bd_make_room<SCAP, NS, true>(W, a, deep_s, dst, sbot, stop, ts, lane, c_deep);
+                }
+                if (nm | ns) {
+                    uint32_t pm = mtop + (pre & 0xffu), ps = stop + (pre >> 8);
 #pragma unroll
-                for (int c = 0; c < 4; c++) {
-                    if (nodemask >> c & 1u) {
-                        if (cs[c] == 1) {
-                            uint32_t q = ps++ & (SCAP - 1);
-                            W.sl[q] = cl[c]; W.slr[q] = clr[c]; W.sm[q] = cmeta[c];
-                        } else {
-                            uint32_t q = pm++ & (SCAP - 1);
-                            W.ml[q] = cl[c]; W.mlr[q] = clr[c]; W.msz[q] = cs[c]; W.mm[q] = cmeta[c];
+                    for (int c = 0; c < 4; c++) {
+                        if (nodemask >> c & 1u) {
+                            if (cs[c] == 1) {
+                                uint32_t q = ps++ & (SCAP - 1);
+                                W.sl[q] = cl[c]; W.slr[q] = clr[c]; W.sm[q] = cmeta[c];
+                            } else {
+                                uint32_t q = pm++ & (SCAP - 1);
+                                W.ml[q] = cl[c]; W.mlr[q] = clr[c]; W.msz[q] = cs[c]; W.mm[q] = cmeta[c];
+                            }
                         }
                     }
                 }
+                mtop += tm;
+                stop += ts;
+                const int delta = (int)(nm + ns + want) - (cont ? 0 : 1);
+                if (has && delta) atomicAdd(&W.live[slot], delta);
+                if (CHAIN == 1) break;
+                __syncwarp();                                   // this step's pushes before the next one's
+                if (!__any_sync(BFULL, cont)) break;
+                has = cont; l = nl; lr = nlr; sz = nsz; meta = nmeta;
             }
-            mtop += tm;
-            stop += ts;
-            const int delta = (int)(nm + ns + want) - 1;
-            if (has && delta) atomicAdd(&W.live[slot], delta);
         }
         __syncwarp();
     }
