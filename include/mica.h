@@ -256,7 +256,8 @@ void mica_result_free(mica_result *res);
  * batches are in flight per index: a third submit returns MICA_EBUSY;
  * collecting an unknown or already collected ticket returns MICA_ENOTFOUND.
  * The caller's host buffers must stay valid and unchanged until the batch is
- * collected.  params->cuda_stream is not used (each slot has its own stream).
+ * collected; a submit that fails gives no ticket and returns once its copies
+ * (if any were queued) have finished.  params->cuda_stream is not used (each slot has its own stream).
  * Batches may be collected in any order.  Calls on one index are not
  * thread-safe; mica_get_stats reports the last collected batch.
  */

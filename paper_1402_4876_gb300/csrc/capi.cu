@@ -969,7 +969,10 @@ int mica_align_batch(mica_index *idx, const uint32_t *packed_reads, const uint64
     if ((rc = stage_host_batch(idx, w, packed_reads, word_offsets, lengths, k, n_reads, s, rd))) return rc;
     idx->stats.launches = 0;
     uint64_t nh = 0;
-    if ((rc = align_on_device(idx, idx->ws, idx->stats, rd, p, s, &nh))) return rc;
+    if ((rc = align_on_device(idx, idx->ws, idx->stats, rd, p, s, &nh))) {
+        cudaStreamSynchronize(s);   // the caller's buffers are free to go on return
+        return rc;
+    }
     return copy_result(w, n_reads, nh, s, out);
 }
 
@@ -999,8 +1002,13 @@ int mica_align_submit(mica_index *idx, const uint32_t *packed_reads, const uint6
     slot->st = mica_stats{};
     slot->launched = false;
     if (graph_eligible(w, p, rd)) {
-        if ((rc = create_events(w))) return rc;
-        if ((rc = align_graph_launch(idx, w, slot->st, rd, p, slot->stream, slot->launched))) return rc;
+        if (!(rc = create_events(w))) rc = align_graph_launch(idx, w, slot->st, rd, p, slot->stream, slot->launched);
+        if (rc) {
+            // no ticket, so the caller may free its buffers on return: let the copies finish first
+            cudaStreamSynchronize(slot->stream);
+            slot->launched = false;
+            return rc;
+        }
     }
     slot->busy = true;
     slot->p = p;
