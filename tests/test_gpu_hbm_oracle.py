@@ -60,3 +60,20 @@ def test_hbm_unpruned_and_best_stratum_equal_oracle(hbm):
     gc.assert_same(got, fm.align(sub, cap=1000), "unpruned")
     got = idx.align_batch(sub, hit_cap=1000, kernel="persistent", report="best_stratum")
     gc.assert_same(got, fm.align_best_stratum(sub, cap=1000), "best stratum")
+
+
+@pytest.mark.parametrize("budget", [0, 16])
+def test_hbm_bidirectional_64_slot_shape_equals_oracle(hbm, budget):
+    """The 64-slot shape of the bidirectional kernel (chosen for indices whose
+    occurrence blocks stay in L2) on this HBM-resident index, by default and
+    with a node budget of 16: its multi-row rounds let a lane carry a node's
+    one multi-row child on for several steps, and the heavy trees of this
+    genome (tandem arrays, young repeat families) take that path with deep
+    stacks, overflow and exports to later rounds.  Every result equals the
+    oracle's."""
+    _, b, idx, _, want = hbm
+    try:
+        idx.set_tuning(bidir_shape=0, bidir_budget=budget)
+        gc.assert_same(idx.align_batch(b, hit_cap=1000, kernel="bidirectional"), want, f"64 slots, budget {budget}")
+    finally:
+        idx.set_tuning()
