@@ -223,6 +223,8 @@ int mica_index_build(const uint8_t *genome_acgt, uint64_t len,
 int mica_index_save(const mica_index *idx, const char *path);
 /* Read an index file and upload it to `device`, where it stays until freed. */
 int mica_index_load(const char *path, int device, mica_index **out);
+/* Release the index and its device memory; batches submitted and not yet
+   collected finish first (their results are dropped).  NULL is a no-op. */
 void mica_index_free(mica_index *idx);
 int mica_index_get_info(const mica_index *idx, mica_index_info *info);
 

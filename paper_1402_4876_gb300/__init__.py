@@ -344,8 +344,9 @@ class Index:
 
     def free(self):
         if self._h:
-            _lib.mica_index_free(self._h)
+            _lib.mica_index_free(self._h)   # waits for batches still in flight
             self._h = None
+            self._inflight.clear()
 
     def __del__(self):
         try:

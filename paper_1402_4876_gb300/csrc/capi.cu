@@ -709,6 +709,9 @@ void mica_index_free(mica_index *idx)
     if (!idx) return;
     DeviceGuard g(idx->device);
     cudaSetDevice(idx->device);
+    // batches still in flight on the pipeline slots finish before anything they read goes
+    for (PipeSlot &ps : idx->pipe)
+        if (ps.stream) cudaStreamSynchronize(ps.stream);
     dev_release(idx->occ);
     dev_release(idx->super);
     dev_release(idx->marks);
@@ -725,7 +728,6 @@ void mica_index_free(mica_index *idx)
     dev_release(idx->lrtable);
     free_workspace(idx->ws);
     for (PipeSlot &ps : idx->pipe) {
-        if (ps.stream) cudaStreamSynchronize(ps.stream);
         free_workspace(ps.ws);
         if (ps.stream) cudaStreamDestroy(ps.stream);
     }
