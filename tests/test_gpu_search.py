@@ -259,6 +259,24 @@ def test_pipelined_submit_and_collect():
     assert idx.stats()["tasks"] == 2 * parts[0].n
 
 
+def test_free_with_batches_in_flight():
+    """An index freed with two submitted batches never collected waits for
+    them (nothing they read is released under them) and leaves the device
+    usable: a new index of the same genome gives the oracle's result."""
+    m = gc.mica()
+    g = gc.genome("1m")
+    b = synth.reads_1m(g, n=2_000)
+    idx = m.Index.build(synth.to_acgt_bytes(g.codes), kmer_q=10, sa_sample=8)
+    idx.submit_batch(b)
+    idx.submit_batch(b, kernel="persistent")
+    idx.free()
+    idx2 = m.Index.build(synth.to_acgt_bytes(g.codes), kmer_q=10, sa_sample=8)
+    try:
+        gc.assert_same(idx2.align_batch(b, hit_cap=1000), gc.oracle_index("1m").align(b, cap=1000), "after free")
+    finally:
+        idx2.free()
+
+
 def test_bidirectional_text_check_settings():
     """One-row intervals checked against the text (the whole suffix array,
     its inverse and the 2-bit text resident): with the check after 1, 24 or the
