@@ -5,8 +5,9 @@ launch shape the human-scale benchmark uses.
 The oracle cannot build its index for 3.1 Gbp within a test, so sampled
 reads are checked one by one against its brute-force Hamming scan of both
 strands (exact totals; exact hit lists where the total is within the cap;
-listed hits a subset otherwise), and every read against properties that
-hold at any size."""
+listed hits a subset otherwise), for the persistent and the bidirectional
+kernel, every read against properties that hold at any size, and the
+kernels against each other on every mate."""
 import numpy as np
 import pytest
 
@@ -30,19 +31,20 @@ def human():
 
 def test_human_sampled_reads_equal_bruteforce(human):
     g, b, idx = human
-    res = idx.align_batch(b, hit_cap=1000, kernel="persistent")
     rng = np.random.default_rng(44)
     sample = np.sort(rng.choice(b.n, 16, replace=False))
     sub = b.subset(sample)
     bf = oracle.bruteforce(g.codes, sub)
-    for j, i in enumerate(sample):
-        got = res.hits_of(int(i))
-        want = bf.as_tuples(j)
-        assert int(res.total[i]) == len(want)
-        if len(want) <= 1000:
-            assert got == want
-        else:
-            assert len(got) == 1000 and set(got) <= set(want)
+    for kernel in ("persistent", "bidirectional"):
+        res = idx.align_batch(b, hit_cap=1000, kernel=kernel)
+        for j, i in enumerate(sample):
+            got = res.hits_of(int(i))
+            want = bf.as_tuples(j)
+            assert int(res.total[i]) == len(want), (kernel, int(i))
+            if len(want) <= 1000:
+                assert got == want, (kernel, int(i))
+            else:
+                assert len(got) == 1000 and set(got) <= set(want), (kernel, int(i))
 
 
 def test_human_properties_and_kernels_agree(human):
@@ -66,6 +68,8 @@ def test_human_properties_and_kernels_agree(human):
     sub = b.subset(np.arange(0, 4_000))
     gc.assert_same(idx.align_batch(sub, hit_cap=1000, kernel="plain"),
                    idx.align_batch(sub, hit_cap=1000, kernel="persistent"), "plain vs persistent")
+    # the bidirectional kernel (text checks over the whole SA, rows past 2^31) on every mate
+    gc.assert_same(idx.align_batch(b, hit_cap=1000, kernel="bidirectional"), res, "bidirectional vs persistent")
 
 
 def test_human_serving_alone_equals_mix(human):
